@@ -1,0 +1,185 @@
+/*
+ * dbscan_gb300.h -- C ABI of a GB300-native (sm_103a) exact Euclidean DBSCAN.
+ *
+ * The library implements the grid method of Wang, Gu and Shun, "Theoretically-
+ * Efficient and Practical Parallel DBSCAN" (SIGMOD 2020): points go into cells
+ * of side eps/sqrt(d) (Sec. 3, Algorithm 1; Sec. 4.1), core points are marked
+ * by range counts over neighbouring cells (Sec. 4.3, Algorithm 2), core cells
+ * are joined by bichromatic-closest-pair tests with early exit and a lock-free
+ * union-find (Sec. 4.4, Algorithm 3), and border points collect the clusters of
+ * the core points within eps (Sec. 4.5, Algorithm 4).  The result is the one
+ * fixed by the DBSCAN definition of Sec. 2, with these conventions:
+ *
+ *   - within(p, q) is  sum_i (p_i - q_i)^2 <= fl(eps*eps)  evaluated in IEEE
+ *     FP64, left to right, without fused multiply-add.  FP32 inputs are widened
+ *     exactly.  In the FP32 precision mode the library first decides each pair
+ *     in FP32 and recomputes in FP64 any pair whose FP32 value lies inside a
+ *     forward-error band around eps^2, so the decisions are those of the FP64
+ *     predicate in both modes.
+ *   - a point is core iff at least min_pts points (itself included) are
+ *     within eps of it;
+ *   - a cluster is named by the smallest input index of its core points;
+ *   - labels[p] is the cluster of a core point, the smallest cluster of a
+ *     border point, and -1 for noise;
+ *   - the full cluster set of each non-core point is returned as CSR, sorted
+ *     ascending (core points have an empty entry there; their one cluster is
+ *     labels[p]).
+ *
+ * Conventions for every call:
+ *   - pointers named d_* are device pointers, h_* are host pointers;
+ *   - the caller owns all input and output buffers; the context owns its
+ *     device workspace, which it allocates in dbscan_create();
+ *   - all device work is ordered on the caller's CUDA stream (a cudaStream_t
+ *     passed as void*; NULL = legacy default stream);
+ *   - errors are returned as dbscan_status codes; no C++ exception crosses
+ *     the ABI; a context stays usable after any error it returns;
+ *   - a context is not thread-safe: one call at a time per context.
+ */
+#ifndef DBSCAN_GB300_H
+#define DBSCAN_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DBSCAN_OK = 0,
+    DBSCAN_ERR_INVALID_ARG = 1,     /* bad size, pointer, eps, min_pts or non-finite coordinate */
+    DBSCAN_ERR_UNSUPPORTED_DIM = 2, /* d outside the supported range */
+    DBSCAN_ERR_OOM = 3,             /* device or pinned allocation failed */
+    DBSCAN_ERR_KEY_OVERFLOW = 4,    /* the grid needs more cells per dimension than the key holds */
+    DBSCAN_ERR_CAPACITY = 5,        /* a data-dependent buffer of the context is too small */
+    DBSCAN_ERR_CUDA = 6,            /* a CUDA runtime call failed */
+    DBSCAN_ERR_DEVICE_TIMEOUT = 7,  /* a bounded device retry loop gave up */
+    DBSCAN_ERR_STATE = 8            /* call out of order (e.g. border ids before a run) */
+} dbscan_status;
+
+/* Element type of the input coordinates. */
+enum { DBSCAN_F32 = 0, DBSCAN_F64 = 1 };
+
+/* Options for dbscan_set_option(). */
+enum {
+    /* value: DBSCAN_PREC_FP32_RECHECK (default) or DBSCAN_PREC_FP64 */
+    DBSCAN_OPT_PRECISION = 0,
+    /* value: DBSCAN_SCHED_SIZE (default), DBSCAN_SCHED_NONE */
+    DBSCAN_OPT_SCHEDULE = 1,
+    /* value: 0 (default) or 1: count distance evaluations in dbscan_stats */
+    DBSCAN_OPT_COLLECT_STATS = 2,
+    /* value: iteration limit of every bounded device retry loop (default 1<<22) */
+    DBSCAN_OPT_MAX_ITERS = 3,
+    /* value: 0 (default) or 1: record CUDA events around each phase and report
+       the phase durations in dbscan_stats.phase_ms */
+    DBSCAN_OPT_PHASE_TIMING = 4
+};
+enum { DBSCAN_PREC_FP64 = 0, DBSCAN_PREC_FP32_RECHECK = 1 };
+/* SIZE: core-cell pairs are tested in order of non-increasing core count of the
+ * owning cell (Sec. 4.4, "Reducing Cell Connectivity Queries").
+ * NONE: pairs are tested in cell order (ablation). */
+enum { DBSCAN_SCHED_SIZE = 0, DBSCAN_SCHED_NONE = 1 };
+
+typedef struct dbscan_ctx dbscan_ctx;
+
+/* Counters of the last run (filled by dbscan_get_stats). */
+typedef struct {
+    int64_t n;                      /* points */
+    int32_t d;                      /* dimension */
+    int32_t precision;              /* mode actually used (FP32 mode falls back to FP64
+                                       when eps^2 lies outside [2^-60, 2^60]) */
+    int32_t key_bits;               /* bits of the packed cell key */
+    int32_t radix_passes;           /* 8-bit passes of the key sort */
+    int64_t num_cells;              /* non-empty cells */
+    int64_t num_core_cells;         /* cells with at least one core point */
+    int64_t num_neighbor_entries;   /* cached neighbour-cell list length */
+    int64_t num_candidate_pairs;    /* core-cell pairs, each unordered pair once */
+    int64_t num_pairs_tested;       /* BCP tests run */
+    int64_t num_pairs_skipped;      /* pairs skipped because union-find had joined them */
+    int64_t num_pairs_connected;    /* BCP tests that found a pair within eps */
+    int64_t num_core_points;
+    int64_t num_border_points;
+    int64_t num_noise_points;
+    int64_t num_border_memberships; /* total length of the border sets */
+    int64_t band_rechecks;          /* FP32 decisions recomputed in FP64 */
+    int64_t distance_evals;         /* pair distances evaluated (only with COLLECT_STATS) */
+    int64_t distance_evals_phase[3];/* of which in MarkCore, BCP tests, border assignment */
+    float band_lo, band_hi;         /* FP32 band around eps^2 (FP32 mode) */
+    int64_t kernel_launches;        /* CUDA kernels the run launched */
+    /* Phase durations in ms (only with PHASE_TIMING), from CUDA events on the
+       run's stream: 0 bounding box, 1 host read of the box, 2 keys and sort,
+       3 cells, hash and neighbour lists, 4 MarkCore, 5 core compaction and
+       pair schedule, 6 BCP connectivity with union-find, 7 labels and border
+       counts. */
+    float phase_ms[8];
+} dbscan_stats;
+
+/*
+ * Create a context able to cluster up to max_points points of dimension up to
+ * max_dim.  Allocates the device workspace on the current device (its size
+ * grows linearly with max_points and with the number of candidate
+ * neighbouring cells of max_dim).  1 <= max_dim <= 4; 0 <= max_points < 2^31-1.
+ * Returns OK, INVALID_ARG, UNSUPPORTED_DIM, OOM or CUDA.  *ctx is NULL on error.
+ */
+dbscan_status dbscan_create(dbscan_ctx **ctx, int64_t max_points, int max_dim);
+
+/* Free the context and its workspace (synchronises the device). NULL is a no-op. */
+void dbscan_destroy(dbscan_ctx *ctx);
+
+/* Set one DBSCAN_OPT_* option; INVALID_ARG for unknown options or values. */
+dbscan_status dbscan_set_option(dbscan_ctx *ctx, int option, int64_t value);
+
+/*
+ * Exact DBSCAN (Algorithm 1) of d_points [n, d], row-major, element type dtype
+ * (DBSCAN_F32 or DBSCAN_F64), on the given stream.
+ *   eps      > 0 and finite;  min_pts >= 1;  0 <= n <= max_points;
+ *   1 <= d <= max_dim; every coordinate finite.
+ * Outputs (device, caller-allocated, indexed like the input):
+ *   d_core   [n] uint8:  1 iff core (Algorithm 2);
+ *   d_labels [n] int32:  cluster name as described above;
+ *   d_border_offsets [n+1] int64 or NULL: CSR offsets of the border sets.
+ * *num_border_memberships (host, may be NULL) receives the total set length,
+ * which is the capacity dbscan_border_ids() needs.
+ * The call synchronises the stream twice: once after the bounding-box
+ * reduction (its result sizes the cell key) and once at the end to read the
+ * device status.  Returns OK, INVALID_ARG, UNSUPPORTED_DIM, KEY_OVERFLOW,
+ * CAPACITY, DEVICE_TIMEOUT or CUDA; outputs are undefined unless OK.
+ */
+dbscan_status dbscan_run(dbscan_ctx *ctx, const void *d_points, int64_t n, int d, int dtype,
+                         double eps, int64_t min_pts, uint8_t *d_core, int32_t *d_labels,
+                         int64_t *d_border_offsets, int64_t *num_border_memberships,
+                         void *stream);
+
+/*
+ * Fill d_ids with the border sets of the last successful dbscan_run() on this
+ * context (Algorithm 4), in the CSR layout of its d_border_offsets: the entry of
+ * point p is d_ids[off[p] .. off[p+1]), ascending cluster names.  capacity is
+ * the length of d_ids and must be >= the run's num_border_memberships.
+ * The input points of that run must still be unchanged in device memory.
+ * Returns OK, STATE (no run), CAPACITY, INVALID_ARG or CUDA.  Synchronises.
+ */
+dbscan_status dbscan_border_ids(dbscan_ctx *ctx, int32_t *d_ids, int64_t capacity, void *stream);
+
+/*
+ * Same as dbscan_run() but with host buffers: copies h_points to the device,
+ * runs, and copies core flags and labels back (pinned host memory gives
+ * asynchronous copies; pageable memory works but is staged by the driver).
+ * Border sets are not returned.  The device copies live in the context.
+ */
+dbscan_status dbscan_run_host(dbscan_ctx *ctx, const void *h_points, int64_t n, int d, int dtype,
+                              double eps, int64_t min_pts, uint8_t *h_core, int32_t *h_labels,
+                              void *stream);
+
+/* Counters of the last run (host copy; no device work). */
+dbscan_status dbscan_get_stats(const dbscan_ctx *ctx, dbscan_stats *out);
+
+/* Static English text for a status code. */
+const char *dbscan_status_string(int status);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int dbscan_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DBSCAN_GB300_H */

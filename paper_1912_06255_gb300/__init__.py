@@ -1,0 +1,145 @@
+"""GB300-native exact Euclidean DBSCAN (grid method of Wang, Gu and Shun, SIGMOD 2020).
+
+Python front end of the C ABI declared in include/dbscan_gb300.h.  PyTorch
+provides device memory and streams; every clustering step runs in the CUDA
+library ``libdbscan_gb300.so``.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+from . import _lib
+from ._lib import DbscanError, Stats
+
+__all__ = ["DBSCAN", "Result", "dbscan", "DbscanError", "Stats"]
+
+
+@dataclass
+class Result:
+    """Outputs indexed like the input points.
+
+    core:            uint8 [n], 1 for core points (Sec. 2)
+    labels:          int32 [n], cluster name (smallest core index of the cluster)
+                     for core points, smallest cluster of a border point, -1 noise
+    border_offsets:  int64 [n+1] CSR offsets of the border sets (None if not asked)
+    border_ids:      int32 [K] ascending cluster names of each non-core point
+    stats:           counters of the run
+    """
+    core: "object"
+    labels: "object"
+    border_offsets: "object" = None
+    border_ids: "object" = None
+    stats: dict | None = None
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class DBSCAN:
+    """A reusable context (device workspace sized for max_points x max_dim)."""
+
+    def __init__(self, max_points: int, max_dim: int, precision: str = "fp32",
+                 schedule: str = "size", collect_stats: bool = False, max_iters: int | None = None):
+        self.lib = _lib.load()
+        self.ctx = ctypes.c_void_p()
+        _lib.check(self.lib.dbscan_create(ctypes.byref(self.ctx), int(max_points), int(max_dim)),
+                   "dbscan_create")
+        self.max_points, self.max_dim = int(max_points), int(max_dim)
+        prec = {"fp32": _lib.PREC_FP32_RECHECK, "fp64": _lib.PREC_FP64}[precision]
+        sched = {"size": _lib.SCHED_SIZE, "none": _lib.SCHED_NONE}[schedule]
+        self.set_option(_lib.OPT_PRECISION, prec)
+        self.set_option(_lib.OPT_SCHEDULE, sched)
+        self.set_option(_lib.OPT_COLLECT_STATS, int(bool(collect_stats)))
+        if max_iters is not None:
+            self.set_option(_lib.OPT_MAX_ITERS, int(max_iters))
+
+    def set_option(self, option: int, value: int) -> None:
+        _lib.check(self.lib.dbscan_set_option(self.ctx, option, int(value)), "dbscan_set_option")
+
+    def close(self) -> None:
+        if self.ctx:
+            self.lib.dbscan_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        st = Stats()
+        _lib.check(self.lib.dbscan_get_stats(self.ctx, ctypes.byref(st)), "dbscan_get_stats")
+        return st.as_dict()
+
+    def run(self, points, eps: float, min_pts: int, border: bool = True, out=None, stream=None) -> Result:
+        """Cluster a CUDA tensor [n, d] of float32 or float64 on the current stream.
+
+        ``out`` may supply preallocated (core u8[n], labels i32[n], offsets i64[n+1])."""
+        torch = _torch()
+        if not (isinstance(points, torch.Tensor) and points.is_cuda and points.dim() == 2):
+            raise ValueError("points must be a CUDA tensor [n, d]")
+        if points.dtype not in (torch.float32, torch.float64):
+            raise ValueError("points must be float32 or float64")
+        pts = points.contiguous()
+        n, d = pts.shape
+        dev = pts.device
+        if out is None:
+            core = torch.empty(n, dtype=torch.uint8, device=dev)
+            labels = torch.empty(n, dtype=torch.int32, device=dev)
+            offs = torch.empty(n + 1, dtype=torch.int64, device=dev) if border else None
+        else:
+            core, labels, offs = out
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        k = ctypes.c_int64(0)
+        dtype = _lib.F32 if pts.dtype == torch.float32 else _lib.F64
+        st = self.lib.dbscan_run(self.ctx, pts.data_ptr(), n, d, dtype, float(eps), int(min_pts),
+                                 core.data_ptr(), labels.data_ptr(),
+                                 offs.data_ptr() if offs is not None else None,
+                                 ctypes.byref(k), s.cuda_stream)
+        _lib.check(st, "dbscan_run")
+        ids = None
+        if border:
+            ids = torch.empty(max(int(k.value), 1), dtype=torch.int32, device=dev)
+            _lib.check(self.lib.dbscan_border_ids(self.ctx, ids.data_ptr(), ids.numel(), s.cuda_stream),
+                       "dbscan_border_ids")
+            ids = ids[: int(k.value)]
+        return Result(core, labels, offs, ids, self.stats())
+
+    def run_host(self, points, eps: float, min_pts: int, core=None, labels=None, stream=None):
+        """Cluster host memory (numpy array or CPU tensor, ideally pinned) through
+        dbscan_run_host: the copies to and from the device are part of the call."""
+        torch = _torch()
+        import numpy as np
+        if isinstance(points, np.ndarray):
+            pts = torch.from_numpy(np.ascontiguousarray(points))
+        else:
+            pts = points.contiguous()
+        if pts.dtype not in (torch.float32, torch.float64) or pts.dim() != 2:
+            raise ValueError("points must be float32/float64 [n, d]")
+        n, d = pts.shape
+        if core is None:
+            core = torch.empty(n, dtype=torch.uint8)
+        if labels is None:
+            labels = torch.empty(n, dtype=torch.int32)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        dtype = _lib.F32 if pts.dtype == torch.float32 else _lib.F64
+        _lib.check(self.lib.dbscan_run_host(self.ctx, pts.data_ptr(), n, d, dtype, float(eps), int(min_pts),
+                                            core.data_ptr(), labels.data_ptr(), s.cuda_stream),
+                   "dbscan_run_host")
+        return core, labels
+
+
+def dbscan(points, eps: float, min_pts: int, precision: str = "fp32", schedule: str = "size",
+           border: bool = True, collect_stats: bool = False) -> Result:
+    """One-shot exact DBSCAN of a CUDA tensor [n, d] (float32 or float64)."""
+    n, d = points.shape
+    ctx = DBSCAN(max(int(n), 1), int(d), precision=precision, schedule=schedule,
+                 collect_stats=collect_stats)
+    try:
+        return ctx.run(points, eps, min_pts, border=border)
+    finally:
+        ctx.close()

@@ -1,0 +1,532 @@
+// C ABI: context, workspace and the run sequence of Algorithm 1.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "geom.cuh"
+#include "grid.cuh"
+
+using namespace gbdb;
+
+namespace {
+
+constexpr int kVersion = 100;  // 0.1.0
+
+// Candidate neighbour offsets of a d-dimensional cell (d <= 4): integer delta
+// != 0 with sum_j max(|delta_j| - 1, 0)^2 <= d.  A pair within eps spans cells
+// whose coordinates differ by delta with sum_j (|delta_j| - 1)_+^2 * s^2 < eps^2
+// = d * s^2 for the exact side s = eps / sqrt(d); the side used is shrunk by
+// 2^-20, which absorbs the rounding of the FP64 cell coordinates, so "<= d"
+// keeps every such cell.  Sorted nearest first.
+std::vector<signed char> offset_table(int d) {
+    const int r = 1 + (int)std::floor(std::sqrt((double)d));
+    std::vector<std::vector<int>> offs;
+    std::vector<int> cur(d, -r);
+    for (;;) {
+        int bound = 0, nz = 0;
+        for (int j = 0; j < d; ++j) {
+            int a = std::abs(cur[j]) - 1;
+            if (a > 0) bound += a * a;
+            nz |= cur[j];
+        }
+        if (nz && bound <= d) offs.push_back(cur);
+        int j = 0;
+        while (j < d && ++cur[j] > r) cur[j++] = -r;
+        if (j == d) break;
+    }
+    auto key = [d](const std::vector<int> &o) {
+        int b = 0, e = 0;
+        for (int j = 0; j < d; ++j) {
+            int a = std::abs(o[j]) - 1;
+            if (a > 0) b += a * a;
+            e += o[j] * o[j];
+        }
+        return std::make_pair(b, e);
+    };
+    std::stable_sort(offs.begin(), offs.end(),
+                     [&](const std::vector<int> &a, const std::vector<int> &b) { return key(a) < key(b); });
+    std::vector<signed char> tab(offs.size() * kMaxEnumDim, 0);
+    for (size_t i = 0; i < offs.size(); ++i)
+        for (int j = 0; j < d; ++j) tab[i * kMaxEnumDim + j] = (signed char)offs[i][j];
+    return tab;
+}
+
+int num_offsets(int d) { return (int)(offset_table(d).size() / kMaxEnumDim); }
+
+// FP32 band around T = fl(eps^2).  f is the FP32 value of sum (p'_i - q'_i)^2
+// for coordinates p', q' rounded to FP32 (each within E_coord of the input);
+// E is the resulting bound on |‖p'-q'‖ - ‖p-q‖|.  With the forward-error bounds
+// |f - ‖p'-q'‖^2| <= g32 ‖p'-q'‖^2 and |fl64(d^2) - d^2| <= g64 d^2 (sums of
+// non-negative rounded terms), f <= lo implies the FP64 predicate holds and
+// f > hi implies it fails:
+//   lo = (1 - g32) (sqrt(T / (1 + g64)) - E)^2,  hi = (1 + g32) (sqrt(T / (1 - g64)) + E)^2.
+// Rounding of this host arithmetic is absorbed by 2^-40 margins.
+bool fp32_band(double T, int d, double E, float *lo, float *hi) {
+    if (!(T >= 0x1p-60 && T <= 0x1p60)) return false;
+    const double g32 = 2.0 * (d + 2) * 0x1p-24, g64 = 2.0 * (d + 2) * 0x1p-53;
+    const double rT = std::sqrt(T);
+    if (!(E <= 0.25 * rT)) return false;
+    const double a = std::sqrt(T / (1.0 + g64)) * (1.0 - 0x1p-40) - E;
+    const double b = std::sqrt(T / (1.0 - g64)) * (1.0 + 0x1p-40) + E;
+    const double lo_d = (1.0 - g32) * a * a * (1.0 - 0x1p-40);
+    const double hi_d = (1.0 + g32) * b * b * (1.0 + 0x1p-40);
+    float l = (float)lo_d, h = (float)hi_d;
+    if ((double)l > lo_d) l = std::nextafter(l, -INFINITY);
+    if ((double)h < hi_d) h = std::nextafter(h, INFINITY);
+    if (!(l > 0.0f) || !std::isfinite(h)) return false;
+    *lo = l;
+    *hi = h;
+    return true;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct dbscan_ctx {
+    int device = 0;
+    int64_t max_points = 0;
+    int max_dim = 0;
+    int sd_max = 2;
+    int noff_max = 0;
+    // options
+    int precision = DBSCAN_PREC_FP32_RECHECK;
+    int sched = DBSCAN_SCHED_SIZE;
+    int collect_stats = 0;
+    int max_iters = 1 << 22;
+    int phase_timing = 0;
+    cudaEvent_t ev[9] = {};
+    // workspace
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    uint32_t *v0 = nullptr, *v1 = nullptr;
+    unsigned *hist = nullptr;
+    long long *part = nullptr;
+    int *flags = nullptr, *cid = nullptr;
+    float *pf = nullptr, *cpf = nullptr;
+    double *pd = nullptr, *cpd = nullptr;
+    int *orig = nullptr, *cell_of = nullptr, *cell_start = nullptr;
+    uint64_t *cell_key = nullptr;
+    uint64_t *hk = nullptr;
+    int *hv = nullptr;
+    long long *nbr_cnt = nullptr, *nbr_off = nullptr;
+    int *nbr = nullptr;
+    long long nbr_cap = 0;
+    int *core_s = nullptr, *core_pos = nullptr, *ccs = nullptr, *core_orig = nullptr, *core_cell = nullptr;
+    int *rank = nullptr;
+    long long *pcnt = nullptr, *poff = nullptr;
+    int2 *pairs = nullptr;
+    long long pair_cap = 0;
+    int *parent = nullptr, *compmin = nullptr;
+    long long *bcount = nullptr, *boff = nullptr;
+    double *bbox_part = nullptr;
+    int *bbox_bad = nullptr;
+    double *bbox_out = nullptr;
+    signed char *offs = nullptr;  // [kMaxEnumDim][kMaxOffsets][kMaxEnumDim]
+    int noff[kMaxEnumDim + 1] = {0};
+    DevCounters *ctr = nullptr;
+    // pinned host
+    DevCounters *h_ctr = nullptr;
+    double *h_bbox = nullptr;
+    // host-buffer entry point
+    void *d_in = nullptr;
+    size_t d_in_bytes = 0;
+    uint8_t *d_core_h = nullptr;
+    int32_t *d_lab_h = nullptr;
+    // last run
+    bool have_run = false;
+    RunParams last{};
+    int last_D = 0, last_mode = 0;
+    const void *last_points = nullptr;
+    int last_dtype = 0;
+    dbscan_stats stats{};
+};
+
+static dbscan_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return DBSCAN_OK;
+    if (e == cudaErrorMemoryAllocation) return DBSCAN_ERR_OOM;
+    return DBSCAN_ERR_CUDA;
+}
+
+#define CK(x)                                                  \
+    do {                                                       \
+        cudaError_t e_ = (x);                                  \
+        if (e_ != cudaSuccess) { (void)cudaGetLastError(); return cuda_status(e_); } \
+    } while (0)
+
+static Bufs make_bufs(dbscan_ctx *c, bool f64) {
+    Bufs B{};
+    B.pf = c->pf;
+    B.pd = f64 ? c->pd : nullptr;
+    B.orig = c->orig;
+    B.cell_of = c->cell_of;
+    B.cell_start = c->cell_start;
+    B.nbr_off = c->nbr_off;
+    B.nbr = c->nbr;
+    B.core_s = c->core_s;
+    B.core_pos = c->core_pos;
+    B.ccs = c->ccs;
+    B.cpf = c->cpf;
+    B.cpd = f64 ? c->cpd : nullptr;
+    B.core_orig = c->core_orig;
+    B.core_cell = c->core_cell;
+    B.sk0 = c->k0;
+    B.sk1 = c->k1;
+    B.sv0 = c->v0;
+    B.sv1 = c->v1;
+    B.hist = c->hist;
+    B.rank = c->rank;
+    B.pcnt = c->pcnt;
+    B.poff = c->poff;
+    B.pairs = c->pairs;
+    B.pair_cap = c->pair_cap;
+    B.parent = c->parent;
+    B.compmin = c->compmin;
+    B.bcount = c->bcount;
+    B.boff = c->boff;
+    B.part = c->part;
+    B.n_max = c->max_points;
+    return B;
+}
+
+extern "C" {
+
+const char *dbscan_status_string(int s) {
+    switch (s) {
+    case DBSCAN_OK: return "ok";
+    case DBSCAN_ERR_INVALID_ARG: return "invalid argument";
+    case DBSCAN_ERR_UNSUPPORTED_DIM: return "unsupported dimension";
+    case DBSCAN_ERR_OOM: return "out of memory";
+    case DBSCAN_ERR_KEY_OVERFLOW: return "cell key overflow";
+    case DBSCAN_ERR_CAPACITY: return "workspace capacity exceeded";
+    case DBSCAN_ERR_CUDA: return "CUDA error";
+    case DBSCAN_ERR_DEVICE_TIMEOUT: return "device retry limit reached";
+    case DBSCAN_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+    }
+}
+
+int dbscan_version(void) { return kVersion; }
+
+void dbscan_destroy(dbscan_ctx *c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    cudaFree(c->arena);
+    cudaFree(c->d_in);
+    cudaFree(c->d_core_h);
+    cudaFree(c->d_lab_h);
+    cudaFreeHost(c->h_ctr);
+    cudaFreeHost(c->h_bbox);
+    for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+    delete c;
+}
+
+dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
+    if (!out) return DBSCAN_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (max_points < 0 || max_points >= 0x7ffffffell) return DBSCAN_ERR_INVALID_ARG;
+    if (max_dim < 1 || max_dim > kMaxEnumDim) return DBSCAN_ERR_UNSUPPORTED_DIM;
+    dbscan_ctx *c = new (std::nothrow) dbscan_ctx();
+    if (!c) return DBSCAN_ERR_OOM;
+    cudaGetDevice(&c->device);
+    const int64_t N = std::max<int64_t>(max_points, 1);
+    c->max_points = max_points;
+    c->max_dim = max_dim;
+    c->sd_max = max_dim <= 2 ? 2 : (max_dim <= 4 ? 4 : 8);
+    for (int d = 1; d <= kMaxEnumDim; ++d) c->noff[d] = num_offsets(d);
+    int noff_max = 0;
+    for (int d = 1; d <= max_dim; ++d) noff_max = std::max(noff_max, c->noff[d]);
+    c->noff_max = noff_max;
+    c->nbr_cap = (long long)noff_max * N + 1;
+    c->pair_cap = c->nbr_cap / 2 + 1;
+    const int64_t hsz = radix_hist_size(N);
+    const int64_t npart = scan_partials(std::max<int64_t>(N + 1, hsz)) + 2;
+    const uint64_t hcap = hash_capacity((int)N);
+    const int SD = c->sd_max;
+
+    // Carve one arena.
+    struct Item { void **p; size_t bytes; };
+    std::vector<Item> items = {
+        {(void **)&c->k0, 8 * (size_t)N}, {(void **)&c->k1, 8 * (size_t)N},
+        {(void **)&c->v0, 4 * (size_t)N}, {(void **)&c->v1, 4 * (size_t)N},
+        {(void **)&c->hist, 4 * (size_t)hsz}, {(void **)&c->part, 8 * (size_t)npart},
+        {(void **)&c->flags, 4 * (size_t)(N + 1)}, {(void **)&c->cid, 4 * (size_t)(N + 1)},
+        {(void **)&c->pf, 4 * (size_t)N * SD}, {(void **)&c->pd, 8 * (size_t)N * SD},
+        {(void **)&c->cpf, 4 * (size_t)N * SD}, {(void **)&c->cpd, 8 * (size_t)N * SD},
+        {(void **)&c->orig, 4 * (size_t)N}, {(void **)&c->cell_of, 4 * (size_t)N},
+        {(void **)&c->cell_start, 4 * (size_t)(N + 1)}, {(void **)&c->cell_key, 8 * (size_t)N},
+        {(void **)&c->hk, 8 * (size_t)hcap}, {(void **)&c->hv, 4 * (size_t)hcap},
+        {(void **)&c->nbr_cnt, 8 * (size_t)(N + 1)}, {(void **)&c->nbr_off, 8 * (size_t)(N + 1)},
+        {(void **)&c->nbr, 4 * (size_t)c->nbr_cap},
+        {(void **)&c->core_s, 4 * (size_t)N}, {(void **)&c->core_pos, 4 * (size_t)(N + 1)},
+        {(void **)&c->ccs, 4 * (size_t)(N + 1)}, {(void **)&c->core_orig, 4 * (size_t)N},
+        {(void **)&c->core_cell, 4 * (size_t)N}, {(void **)&c->rank, 4 * (size_t)N},
+        {(void **)&c->pcnt, 8 * (size_t)(N + 1)}, {(void **)&c->poff, 8 * (size_t)(N + 1)},
+        {(void **)&c->pairs, 8 * (size_t)c->pair_cap},
+        {(void **)&c->parent, 4 * (size_t)N}, {(void **)&c->compmin, 4 * (size_t)N},
+        {(void **)&c->bcount, 8 * (size_t)N}, {(void **)&c->boff, 8 * (size_t)(N + 1)},
+        {(void **)&c->bbox_part, 8 * (size_t)1024 * 2 * kMaxDim}, {(void **)&c->bbox_bad, 4},
+        {(void **)&c->bbox_out, 8 * (2 * kMaxDim + 1)},
+        {(void **)&c->offs, (size_t)kMaxEnumDim * kMaxOffsets * kMaxEnumDim},
+        {(void **)&c->ctr, sizeof(DevCounters)},
+    };
+    size_t total = 0;
+    for (auto &it : items) total += align_up(it.bytes);
+    cudaError_t e = cudaMalloc(&c->arena, total);
+    if (e != cudaSuccess) { (void)cudaGetLastError(); delete c; return cuda_status(e); }
+    c->arena_bytes = total;
+    size_t at = 0;
+    for (auto &it : items) { *it.p = (char *)c->arena + at; at += align_up(it.bytes); }
+    e = cudaMallocHost((void **)&c->h_ctr, sizeof(DevCounters));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_bbox, sizeof(double) * (2 * kMaxDim + 1));
+    for (int k = 0; k < 9 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
+    for (int d = 1; d <= kMaxEnumDim && e == cudaSuccess; ++d) {
+        std::vector<signed char> t = offset_table(d);
+        e = cudaMemcpy(c->offs + (size_t)(d - 1) * kMaxOffsets * kMaxEnumDim, t.data(), t.size(),
+                       cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        dbscan_destroy(c);
+        return cuda_status(e);
+    }
+    *out = c;
+    return DBSCAN_OK;
+}
+
+dbscan_status dbscan_set_option(dbscan_ctx *c, int option, int64_t value) {
+    if (!c) return DBSCAN_ERR_INVALID_ARG;
+    switch (option) {
+    case DBSCAN_OPT_PRECISION:
+        if (value != DBSCAN_PREC_FP64 && value != DBSCAN_PREC_FP32_RECHECK) return DBSCAN_ERR_INVALID_ARG;
+        c->precision = (int)value;
+        return DBSCAN_OK;
+    case DBSCAN_OPT_SCHEDULE:
+        if (value != DBSCAN_SCHED_SIZE && value != DBSCAN_SCHED_NONE) return DBSCAN_ERR_INVALID_ARG;
+        c->sched = (int)value;
+        return DBSCAN_OK;
+    case DBSCAN_OPT_COLLECT_STATS:
+        if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
+        c->collect_stats = (int)value;
+        return DBSCAN_OK;
+    case DBSCAN_OPT_PHASE_TIMING:
+        if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
+        c->phase_timing = (int)value;
+        return DBSCAN_OK;
+    case DBSCAN_OPT_MAX_ITERS:
+        if (value < 1 || value > (1ll << 30)) return DBSCAN_ERR_INVALID_ARG;
+        c->max_iters = (int)value;
+        return DBSCAN_OK;
+    default:
+        return DBSCAN_ERR_INVALID_ARG;
+    }
+}
+
+dbscan_status dbscan_get_stats(const dbscan_ctx *c, dbscan_stats *out) {
+    if (!c || !out) return DBSCAN_ERR_INVALID_ARG;
+    *out = c->stats;
+    return DBSCAN_OK;
+}
+
+// Neighbour-offset table of dimension d inside the context.
+static const signed char *offs_for(const dbscan_ctx *c, int d) {
+    return c->offs + (size_t)(d - 1) * kMaxOffsets * kMaxEnumDim;
+}
+
+dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, int dtype, double eps,
+                         int64_t min_pts, uint8_t *d_core, int32_t *d_labels, int64_t *d_border_offsets,
+                         int64_t *num_border_memberships, void *stream) {
+    if (!c) return DBSCAN_ERR_INVALID_ARG;
+    c->have_run = false;
+    if (num_border_memberships) *num_border_memberships = 0;
+    if (n < 0 || n > c->max_points) return DBSCAN_ERR_INVALID_ARG;
+    if (d < 1 || d > c->max_dim) return DBSCAN_ERR_UNSUPPORTED_DIM;
+    if (dtype != DBSCAN_F32 && dtype != DBSCAN_F64) return DBSCAN_ERR_INVALID_ARG;
+    if (!(eps > 0.0) || !std::isfinite(eps) || min_pts < 1) return DBSCAN_ERR_INVALID_ARG;
+    if (n > 0 && (!d_points || !d_core || !d_labels)) return DBSCAN_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::memset(&c->stats, 0, sizeof(c->stats));
+    c->stats.n = n;
+    c->stats.d = d;
+    if (n == 0) {
+        if (d_border_offsets) CK(cudaMemsetAsync(d_border_offsets, 0, sizeof(int64_t), s));
+        CK(cudaStreamSynchronize(s));
+        return DBSCAN_OK;
+    }
+    const bool f64 = dtype == DBSCAN_F64;
+    const int D = d <= 2 ? 2 : (d <= 3 ? 3 : 4);
+    const long long launches0 = g_launches;
+    auto mark = [&](int k) {
+        if (c->phase_timing) cudaEventRecord(c->ev[k], s);
+    };
+    mark(0);
+    const int SD = D == 2 ? 2 : 4;  // storage width of Store<D>
+
+    // 1. bounding box (one sync: it sizes the cell key)
+    CK(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
+    CK(cudaMemsetAsync(c->bbox_bad, 0, sizeof(int), s));
+    const int nbb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (n + 255) / 256));
+    launch_bbox(d_points, dtype, (int)n, d, c->bbox_part, nbb, c->bbox_bad, c->bbox_out, s);
+    mark(1);
+    CK(cudaMemcpyAsync(c->h_bbox, c->bbox_out, sizeof(double) * (2 * kMaxDim + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    if (c->h_bbox[2 * kMaxDim] != 0.0) return DBSCAN_ERR_INVALID_ARG;
+
+    // 2. grid parameters: side s = eps/sqrt(d) * (1 - 2^-20) (Sec. 3)
+    RunParams P{};
+    P.n = (int)n;
+    P.d = d;
+    P.min_pts = (int)std::min<int64_t>(min_pts, n + 1);
+    P.max_iters = c->max_iters;
+    P.stats = c->collect_stats;
+    P.eps2 = eps * eps;
+    const double side = (eps / std::sqrt((double)d)) * (1.0 - 0x1p-20);
+    P.inv_s = 1.0 / side;
+    int kmax_all = 0;
+    double M = 0.0;
+    for (int j = 0; j < d; ++j) {
+        const double lo = c->h_bbox[j], hi = c->h_bbox[kMaxDim + j];
+        P.origin[j] = lo;
+        const double t = (hi - lo) * P.inv_s;
+        if (!(t < 0x1p30)) return DBSCAN_ERR_KEY_OVERFLOW;
+        P.kmax[j] = (int)std::floor(t);
+        kmax_all = std::max(kmax_all, P.kmax[j]);
+        M = std::max(M, std::max(std::fabs(lo), std::fabs(hi)));
+    }
+    int bits = 1;
+    while (bits < 31 && (1 << bits) <= kmax_all) ++bits;
+    P.bits = bits;
+    if (d * bits > 63) return DBSCAN_ERR_KEY_OVERFLOW;
+    c->stats.key_bits = d * bits;
+    c->stats.radix_passes = (d * bits + 7) / 8;
+
+    // precision mode and FP32 band
+    int mode = f64 ? kF64FromF64 : kF64FromF32;
+    if (c->precision == DBSCAN_PREC_FP32_RECHECK) {
+        const double E = f64 ? std::sqrt((double)d) * (2.0 * M * 0x1p-24 + 0x1p-148) : 0.0;
+        if (fp32_band(P.eps2, d, E, &P.lo, &P.hi)) mode = f64 ? kF32FromF64 : kF32FromF32;
+    }
+    c->stats.precision = (mode == kF32FromF32 || mode == kF32FromF64) ? DBSCAN_PREC_FP32_RECHECK : DBSCAN_PREC_FP64;
+    c->stats.band_lo = P.lo;
+    c->stats.band_hi = P.hi;
+
+    // 3. keys and sort (semisort role, Sec. 4.1)
+    mark(2);
+    launch_keys(d_points, dtype, P, c->k0, c->v0, s);
+    const int which = radix_sort_u64(c->k0, c->v0, c->k1, c->v1, (int)n, nullptr, n, d * bits, c->hist, c->part, s);
+    const uint64_t *K = which ? c->k1 : c->k0;
+    const uint32_t *V = which ? c->v1 : c->v0;
+
+    // 4. cells, hash, neighbour lists
+    mark(3);
+    launch_cells(d_points, dtype, (int)n, d, SD, K, V, c->flags, c->cid, c->part, c->pf, f64 ? c->pd : nullptr,
+                 c->orig, c->cell_of, c->cell_start, c->cell_key, c->ctr, s);
+    launch_hash(c->hk, c->hv, c->cell_key, c->ctr, s);
+    launch_neighbors(c->cell_key, c->hk, c->hv, P, offs_for(c, d), c->noff[d], c->nbr_cnt, c->nbr_off, c->nbr,
+                     c->nbr_cap, c->part, n, c->ctr, s);
+
+    // 5. MarkCore, 6. compaction, 7. schedule, 8. connect, 9. labels, 10. border
+    Bufs B = make_bufs(c, f64);
+    B.n_max = n;
+    mark(4);
+    launch_markcore(D, mode, P, B, c->ctr, s);
+    mark(5);
+    launch_core_compact(SD, P, B, c->ctr, s);
+    launch_schedule(c->sched, P, B, c->ctr, s);
+    mark(6);
+    launch_connect(D, mode, P, B, c->ctr, s);
+    mark(7);
+    launch_labels(P, B, d_core, d_labels, c->ctr, s);
+    launch_border(D, mode, false, P, B, d_labels, nullptr, 0, c->ctr, s);
+    mark(8);
+    if (d_border_offsets)
+        CK(cudaMemcpyAsync(d_border_offsets, c->boff, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const DevCounters &h = *c->h_ctr;
+    dbscan_stats &st = c->stats;
+    st.num_cells = h.m;
+    st.num_core_cells = h.m_core;
+    st.num_neighbor_entries = h.E;
+    st.num_candidate_pairs = h.P;
+    st.num_pairs_tested = (int64_t)h.pairs_tested;
+    st.num_pairs_skipped = (int64_t)h.pairs_skipped;
+    st.num_pairs_connected = (int64_t)h.pairs_linked;
+    st.num_core_points = h.n_core;
+    st.num_border_points = h.n_border;
+    st.num_noise_points = n - h.n_core - h.n_border;
+    st.num_border_memberships = h.K;
+    st.band_rechecks = (int64_t)h.band_rechecks;
+    for (int k = 0; k < 3; ++k) st.distance_evals_phase[k] = (int64_t)h.dist_evals[k];
+    st.distance_evals = st.distance_evals_phase[0] + st.distance_evals_phase[1] + st.distance_evals_phase[2];
+    st.kernel_launches = g_launches - launches0;
+    if (c->phase_timing)
+        for (int k = 0; k < 8; ++k) cudaEventElapsedTime(&st.phase_ms[k], c->ev[k], c->ev[k + 1]);
+    if (h.err) return (dbscan_status)h.err;
+    if (num_border_memberships) *num_border_memberships = h.K;
+    c->have_run = true;
+    c->last = P;
+    c->last_D = D;
+    c->last_mode = mode;
+    c->last_points = d_points;
+    c->last_dtype = dtype;
+    return DBSCAN_OK;
+}
+
+dbscan_status dbscan_border_ids(dbscan_ctx *c, int32_t *d_ids, int64_t capacity, void *stream) {
+    if (!c || capacity < 0) return DBSCAN_ERR_INVALID_ARG;
+    if (!c->have_run) return DBSCAN_ERR_STATE;
+    if (capacity < c->stats.num_border_memberships) return DBSCAN_ERR_CAPACITY;
+    if (c->stats.num_border_memberships == 0) return DBSCAN_OK;
+    if (!d_ids) return DBSCAN_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool f64 = c->last_dtype == DBSCAN_F64;
+    Bufs B = make_bufs(c, f64);
+    B.n_max = c->last.n;
+    CK(cudaMemsetAsync(&c->ctr->err, 0, sizeof(int), s));
+    launch_border(c->last_D, c->last_mode, true, c->last, B, nullptr, d_ids, capacity, c->ctr, s);
+    CK(cudaGetLastError());
+    int err = 0;
+    CK(cudaMemcpyAsync(&c->h_ctr->err, &c->ctr->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    err = c->h_ctr->err;
+    return err ? (dbscan_status)err : DBSCAN_OK;
+}
+
+dbscan_status dbscan_run_host(dbscan_ctx *c, const void *h_points, int64_t n, int d, int dtype, double eps,
+                              int64_t min_pts, uint8_t *h_core, int32_t *h_labels, void *stream) {
+    if (!c) return DBSCAN_ERR_INVALID_ARG;
+    if (n < 0 || n > c->max_points || d < 1 || d > c->max_dim) return DBSCAN_ERR_INVALID_ARG;
+    if (dtype != DBSCAN_F32 && dtype != DBSCAN_F64) return DBSCAN_ERR_INVALID_ARG;
+    if (n > 0 && (!h_points || !h_core || !h_labels)) return DBSCAN_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = (size_t)n * d * (dtype == DBSCAN_F64 ? 8 : 4);
+    const size_t need = (size_t)c->max_points * c->max_dim * 8;
+    if (!c->d_in) {
+        CK(cudaMalloc(&c->d_in, std::max<size_t>(need, 8)));
+        c->d_in_bytes = std::max<size_t>(need, 8);
+        CK(cudaMalloc((void **)&c->d_core_h, std::max<int64_t>(c->max_points, 1)));
+        CK(cudaMalloc((void **)&c->d_lab_h, 4 * std::max<int64_t>(c->max_points, 1)));
+    }
+    if (n > 0) CK(cudaMemcpyAsync(c->d_in, h_points, bytes, cudaMemcpyHostToDevice, s));
+    dbscan_status st = dbscan_run(c, c->d_in, n, d, dtype, eps, min_pts, c->d_core_h, c->d_lab_h, nullptr,
+                                  nullptr, stream);
+    if (st != DBSCAN_OK) return st;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(h_core, c->d_core_h, (size_t)n, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h_labels, c->d_lab_h, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return DBSCAN_OK;
+}
+
+}  // extern "C"

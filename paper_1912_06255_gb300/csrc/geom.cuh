@@ -1,0 +1,251 @@
+// Device helpers shared by the distance kernels: point loads, the exact FP64
+// predicate, the FP32 band test, Morton packing of cell coordinates, the cell
+// hash and the union-find.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+
+namespace gbdb {
+
+// ------------------------------------------------------------ point loads
+template <int D> __device__ __forceinline__ void load_f(const float *__restrict__ pf, int64_t i, float (&x)[D]) {
+    constexpr int SD = Store<D>::SD;
+    const float *p = pf + i * SD;
+    if constexpr (SD == 2) {
+        float2 a = *reinterpret_cast<const float2 *>(p);
+        x[0] = a.x;
+        if constexpr (D > 1) x[1] = a.y;
+    } else if constexpr (SD == 4) {
+        float4 a = *reinterpret_cast<const float4 *>(p);
+        x[0] = a.x;
+        if constexpr (D > 1) x[1] = a.y;
+        if constexpr (D > 2) x[2] = a.z;
+        if constexpr (D > 3) x[3] = a.w;
+    } else {
+        float4 a = *reinterpret_cast<const float4 *>(p);
+        float4 b = *reinterpret_cast<const float4 *>(p + 4);
+        float t[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int j = 0; j < D; ++j) x[j] = t[j];
+    }
+}
+
+template <int D> __device__ __forceinline__ void load_d(const double *__restrict__ pd, int64_t i, double (&x)[D]) {
+    constexpr int SD = Store<D>::SD;
+    const double *p = pd + i * SD;
+#pragma unroll
+    for (int j = 0; j < D; j += 2) {
+        double2 a = *reinterpret_cast<const double2 *>(p + j);
+        x[j] = a.x;
+        if (j + 1 < D) x[j + 1] = a.y;
+    }
+}
+
+// Sec. 2 predicate, d(p,q) <= eps, as  sum_i (p_i - q_i)^2 <= fl(eps^2)  in
+// FP64: left to right, each subtraction, product and sum rounded to nearest,
+// no fused multiply-add.  Zero-padded coordinates add exact zeros.
+template <int D>
+__device__ __forceinline__ bool pred64(const double (&a)[D], const double (&b)[D], double eps2) {
+    double t = __dsub_rn(a[0], b[0]);
+    double s = __dmul_rn(t, t);
+#pragma unroll
+    for (int j = 1; j < D; ++j) {
+        double u = __dsub_rn(a[j], b[j]);
+        s = __dadd_rn(s, __dmul_rn(u, u));
+    }
+    return s <= eps2;
+}
+
+// Squared distance in FP32 (its error bound is what the band is derived from).
+template <int D> __device__ __forceinline__ float d2f(const float (&a)[D], const float (&b)[D]) {
+    float t = a[0] - b[0];
+    float s = t * t;
+#pragma unroll
+    for (int j = 1; j < D; ++j) {
+        float u = a[j] - b[j];
+        s = __fmaf_rn(u, u, s);
+    }
+    return s;
+}
+
+// A point held in registers: FP32 coordinates, or FP64 in the FP64-storage
+// FP64-predicate mode.
+template <int D, int M> struct Pt {
+    static constexpr bool kDouble = (M == kF64FromF64);
+    float f[kDouble ? 1 : D];
+    double x[kDouble ? D : 1];
+};
+
+template <int D, int M>
+__device__ __forceinline__ void load_pt(Pt<D, M> &p, const float *__restrict__ pf,
+                                        const double *__restrict__ pd, int64_t i) {
+    if constexpr (M == kF64FromF64) load_d<D>(pd, i, p.x);
+    else load_f<D>(pf, i, p.f);
+}
+
+// within(p, q).  ip/iq index p and q in pdp/pdq, the FP64 copies consulted by
+// the recheck of the FP32-band mode on FP64 storage.  *rechecks counts FP32
+// decisions sent to FP64.
+template <int D, int M>
+__device__ __forceinline__ bool within(const Pt<D, M> &p, const Pt<D, M> &q, const RunParams &P,
+                                       const double *__restrict__ pdp, int64_t ip,
+                                       const double *__restrict__ pdq, int64_t iq,
+                                       unsigned &rechecks) {
+    if constexpr (M == kF64FromF64) {
+        return pred64<D>(p.x, q.x, P.eps2);
+    } else if constexpr (M == kF64FromF32) {
+        double a[D], b[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) { a[j] = (double)p.f[j]; b[j] = (double)q.f[j]; }
+        return pred64<D>(a, b, P.eps2);
+    } else {
+        float s = d2f<D>(p.f, q.f);
+        if (s <= P.lo) return true;
+        if (s > P.hi) return false;
+        ++rechecks;
+        double a[D], b[D];
+        if constexpr (M == kF32FromF32) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) { a[j] = (double)p.f[j]; b[j] = (double)q.f[j]; }
+        } else {
+            load_d<D>(pdp, ip, a);
+            load_d<D>(pdq, iq, b);
+        }
+        return pred64<D>(a, b, P.eps2);
+    }
+}
+
+// ------------------------------------------------------------ Morton keys
+__host__ __device__ __forceinline__ uint64_t spread2(uint64_t x) {
+    x &= 0xffffffffull;
+    x = (x | (x << 16)) & 0x0000ffff0000ffffull;
+    x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
+    x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
+    x = (x | (x << 2)) & 0x3333333333333333ull;
+    x = (x | (x << 1)) & 0x5555555555555555ull;
+    return x;
+}
+__host__ __device__ __forceinline__ uint64_t compact2(uint64_t x) {
+    x &= 0x5555555555555555ull;
+    x = (x | (x >> 1)) & 0x3333333333333333ull;
+    x = (x | (x >> 2)) & 0x0f0f0f0f0f0f0f0full;
+    x = (x | (x >> 4)) & 0x00ff00ff00ff00ffull;
+    x = (x | (x >> 8)) & 0x0000ffff0000ffffull;
+    x = (x | (x >> 16)) & 0x00000000ffffffffull;
+    return x;
+}
+__host__ __device__ __forceinline__ uint64_t spread3(uint64_t x) {
+    x &= 0x1fffffull;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+__host__ __device__ __forceinline__ uint64_t compact3(uint64_t x) {
+    x &= 0x1249249249249249ull;
+    x = (x | (x >> 2)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x >> 4)) & 0x100f00f00f00f00full;
+    x = (x | (x >> 8)) & 0x001f0000ff0000ffull;
+    x = (x | (x >> 16)) & 0x001f00000000ffffull;
+    x = (x | (x >> 32)) & 0x1fffffull;
+    return x;
+}
+
+// Interleave d cell coordinates of `bits` bits each (bit b of dimension j goes
+// to key bit b*d + j).  d*bits <= 63.
+__host__ __device__ __forceinline__ uint64_t morton_encode(const int *c, int d, int bits) {
+    if (d == 1) return (uint64_t)c[0];
+    if (d == 2) return spread2((uint64_t)c[0]) | (spread2((uint64_t)c[1]) << 1);
+    if (d == 3)
+        return spread3((uint64_t)c[0]) | (spread3((uint64_t)c[1]) << 1) |
+               (spread3((uint64_t)c[2]) << 2);
+    uint64_t k = 0;
+    for (int b = 0; b < bits; ++b)
+        for (int j = 0; j < d; ++j) k |= (uint64_t)((c[j] >> b) & 1) << (b * d + j);
+    return k;
+}
+
+__host__ __device__ __forceinline__ void morton_decode(uint64_t k, int d, int bits, int *c) {
+    if (d == 1) { c[0] = (int)k; return; }
+    if (d == 2) { c[0] = (int)compact2(k); c[1] = (int)compact2(k >> 1); return; }
+    if (d == 3) {
+        c[0] = (int)compact3(k);
+        c[1] = (int)compact3(k >> 1);
+        c[2] = (int)compact3(k >> 2);
+        return;
+    }
+    for (int j = 0; j < d; ++j) c[j] = 0;
+    for (int b = 0; b < bits; ++b)
+        for (int j = 0; j < d; ++j) c[j] |= (int)((k >> (b * d + j)) & 1) << b;
+}
+
+// ------------------------------------------------------------ cell hash
+// Open addressing with linear probing, keyed by the packed cell key (Sec. 4.1
+// stores the non-empty cells in a hash table).  Capacity: power of two >= 2m.
+__host__ __device__ __forceinline__ uint64_t hash_capacity(int m) {
+    uint64_t c = 16;
+    while (c < 2ull * (uint64_t)m) c <<= 1;
+    return c;
+}
+__device__ __forceinline__ uint32_t hash_slot(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return (uint32_t)k;
+}
+__device__ __forceinline__ int hash_find(const uint64_t *__restrict__ hk, const int *__restrict__ hv,
+                                         uint64_t key, uint64_t mask) {
+    uint64_t s = hash_slot(key) & mask;
+    for (uint64_t it = 0; it <= mask; ++it) {
+        uint64_t k = hk[s];
+        if (k == key) return hv[s];
+        if (k == kEmptyKey) return -1;
+        s = (s + 1) & mask;
+    }
+    return -1;
+}
+
+// ------------------------------------------------------------ union-find
+// Lock-free union-find over cells (Algorithm 3).  Link hooks the larger root
+// under the smaller one, so parent[x] <= x always and every root is the
+// smallest cell of its set.  Find halves paths with plain stores: each store
+// replaces a parent by one of its ancestors, which keeps the forest valid
+// under races.
+__device__ __forceinline__ int uf_load(const int *p) { return *(const volatile int *)p; }
+
+__device__ __forceinline__ int uf_find(int *parent, int x, int max_iters, DevCounters *ctr) {
+    for (int it = 0; it < max_iters; ++it) {
+        int p = uf_load(parent + x);
+        if (p == x) return x;
+        int g = uf_load(parent + p);
+        if (g != p) *(volatile int *)(parent + x) = g;
+        x = g;
+    }
+    set_error(ctr, DBSCAN_ERR_DEVICE_TIMEOUT, 1);
+    return x;
+}
+
+__device__ __forceinline__ void uf_link(int *parent, int a, int b, int max_iters, DevCounters *ctr) {
+    for (int it = 0; it < max_iters; ++it) {
+        int ra = uf_find(parent, a, max_iters, ctr);
+        int rb = uf_find(parent, b, max_iters, ctr);
+        if (ra == rb) return;
+        if (ra < rb) { int t = ra; ra = rb; rb = t; }  // ra is the larger root
+        if (atomicCAS(parent + ra, ra, rb) == ra) return;
+    }
+    set_error(ctr, DBSCAN_ERR_DEVICE_TIMEOUT, 2);
+}
+
+__device__ __forceinline__ int warp_id_global() {
+    return (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+}
+__device__ __forceinline__ int warps_global() { return (int)((gridDim.x * (int64_t)blockDim.x) >> 5); }
+
+}  // namespace gbdb

@@ -1,0 +1,89 @@
+// Internal declarations shared by the translation units of the CUDA library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dbscan_gb300.h"
+
+namespace gbdb {
+
+constexpr int kMaxDim = 8;        // widest point storage
+constexpr int kMaxEnumDim = 4;    // neighbour cells by offset enumeration (Sec. 4.1)
+constexpr int kMaxOffsets = 840;  // candidate offsets for d = 4
+constexpr uint64_t kEmptyKey = ~0ull;
+constexpr int kBorderSetCap = 256;  // >= kissing number of R^8 (240), see border.cu
+
+// Device-resident status and counters of one run (zeroed at the start).
+struct DevCounters {
+    int err;         // first error code (dbscan_status), 0 if none
+    int err_info;    // kernel-specific detail of the first error
+    int m;           // non-empty cells
+    int m_core;      // core cells
+    int n_core;      // core points
+    int n_border;    // border points
+    long long E;     // neighbour list entries
+    long long P;     // candidate core-cell pairs
+    long long K;     // border memberships
+    unsigned long long pair_next;  // BCP work counter
+    unsigned long long pairs_tested, pairs_skipped, pairs_linked;
+    unsigned long long band_rechecks;
+    unsigned long long dist_evals[3];  // MarkCore, BCP, border
+};
+
+// Per-run scalars passed by value to the kernels.
+struct RunParams {
+    int n;        // points
+    int d;        // real dimension
+    int min_pts;  // clamped to n + 1
+    int bits;     // Morton bits per dimension
+    int max_iters;
+    int stats;    // count distance evaluations
+    double eps2;  // fl(eps * eps), the FP64 threshold
+    float lo, hi; // FP32 band: <= lo is in, > hi is out, otherwise FP64 recheck
+    double inv_s; // 1 / cell side
+    double origin[kMaxDim];
+    int kmax[kMaxDim];  // largest cell coordinate per dimension
+};
+
+// Storage width of a point: 2, 4 or 8 coordinates (zero padded).
+template <int D> struct Store { static constexpr int SD = D <= 2 ? 2 : (D <= 4 ? 4 : 8); };
+
+// Precision/storage modes of the distance kernels.
+enum Mode : int {
+    kF64FromF32 = 0,  // FP64 predicate on widened FP32 storage
+    kF64FromF64 = 1,  // FP64 predicate on FP64 storage
+    kF32FromF32 = 2,  // FP32 band test, FP64 recheck on widened FP32 storage
+    kF32FromF64 = 3   // FP32 band test, FP64 recheck on FP64 storage
+};
+
+__device__ __forceinline__ void set_error(DevCounters *c, int code, int info) {
+    if (atomicCAS(&c->err, 0, code) == 0) c->err_info = info;
+}
+
+// ---------------------------------------------------------------- primitives
+// Exclusive scan of in[0..n) into out[0..n], out[n] = total.  n = *n_dev when
+// n_dev is non-null, else n_host; n_max bounds n and sizes the grid.  out may
+// alias in.  part must hold scan_partials(n_max) entries.
+int64_t scan_partials(int64_t n_max);
+void scan_i32_to_i32(const int *in, int *out, int64_t n_host, const int *n_dev, int64_t n_max,
+                     long long *part, cudaStream_t s);
+void scan_i64_to_i64(const long long *in, long long *out, int64_t n_host, const int *n_dev,
+                     int64_t n_max, long long *part, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) on key bits [0, bits), 8 bits a pass.
+// Ping-pongs between (k0, v0) and (k1, v1); returns 0 if the result is in
+// (k0, v0), 1 if in (k1, v1).  hist must hold radix_hist_size(n_max) entries.
+int64_t radix_hist_size(int64_t n_max);
+int radix_sort_u64(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int n_host,
+                   const int *n_dev, int64_t n_max, int bits, unsigned *hist, long long *part,
+                   cudaStream_t s);
+
+// Kernel launches issued by this thread (read before and after a run).
+extern thread_local long long g_launches;
+inline void count_launch() { ++g_launches; }
+
+// Persistent-grid size for a kernel: resident blocks per SM x SM count.
+int grid_for(const void *kernel, int threads, size_t smem = 0);
+
+}  // namespace gbdb

@@ -1,0 +1,67 @@
+"""The C-ABI library loads and exports every function include/*.h declares.
+
+No compute call is made here (no GPU in this environment)."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+def _declared():
+    names = set()
+    for h in (ROOT / "include").glob("*.h"):
+        text = re.sub(r"/\*.*?\*/", "", h.read_text(), flags=re.S)
+        for m in re.finditer(r"\b(dbscan_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1912_06255_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    assert {"dbscan_create", "dbscan_run", "dbscan_border_ids", "dbscan_destroy"} <= names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+    from paper_1912_06255_gb300 import _lib
+    assert _declared() <= set(_lib.SIGNATURES)
+
+
+def test_status_strings_and_version(lib):
+    from paper_1912_06255_gb300 import _lib
+    for code in _lib.STATUS:
+        assert lib.dbscan_status_string(code)
+    assert lib.dbscan_status_string(99) == b"unknown status"
+    assert lib.dbscan_version() >= 100
+
+
+def test_stats_struct_layout_matches_header():
+    """The ctypes mirror of dbscan_stats lists the header's fields in order."""
+    from paper_1912_06255_gb300 import _lib
+    text = (ROOT / "include" / "dbscan_gb300.h").read_text()
+    body = text[text.index("typedef struct {"): text.index("} dbscan_stats;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(\w+)\s*(?:\[\d+\])?\s*[,;]", body.split("{", 1)[1])
+    assert fields == [f for f, _ in _lib.Stats._fields_]
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    """Argument checks happen on the host before any device call."""
+    assert lib.dbscan_set_option(None, 0, 1) == 1
+    assert lib.dbscan_get_stats(None, None) == 1
+    assert lib.dbscan_border_ids(None, None, 0, None) == 1
+    out = ctypes.c_void_p()
+    assert lib.dbscan_create(ctypes.byref(out), -1, 3) == 1
+    assert lib.dbscan_create(ctypes.byref(out), 10, 9) == 2
+    assert not out.value

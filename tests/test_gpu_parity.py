@@ -1,0 +1,198 @@
+"""Parity of the CUDA library with the CPU oracle, element by element.
+
+Every case compares core flags, labels and the border-set CSR bit for bit
+(the result of exact DBSCAN is unique, Sec. 2, and both sides name clusters by
+their smallest core index).  Inputs are seeded; the oracle runs on the CPU.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_06255_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1912_06255_gb300 import DBSCAN, DbscanError, dbscan  # noqa: E402
+
+
+def _run(X, eps, mp, **kw):
+    t = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    r = dbscan(t, eps, mp, **kw)
+    torch.cuda.synchronize()
+    return (r.core.cpu().numpy(), r.labels.cpu().numpy(), r.border_offsets.cpu().numpy(),
+            r.border_ids.cpu().numpy(), r.stats)
+
+
+def _assert_same(X, eps, mp, **kw):
+    got = _run(X, eps, mp, **kw)
+    exp = oracle.dbscan(X, eps, mp)
+    names = ("core", "labels", "border_offsets", "border_ids")
+    for name, g, e in zip(names, got[:4], exp):
+        if not np.array_equal(g, e):
+            bad = np.flatnonzero(g != e)[:10] if g.shape == e.shape else "shape"
+            raise AssertionError(f"{name} differs at {bad} (n={len(X)}, eps={eps}, minPts={mp}, {kw})")
+    return got[4]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_hand_example(precision, dtype):
+    import json, os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "two_plus_2d.json")))
+    X = np.array(g["points"], dtype=dtype)
+    core, labels, off, ids, _ = _run(X, g["eps"], g["min_pts"], precision=precision)
+    assert core.tolist() == g["core"] and labels.tolist() == g["labels"]
+    sets = [ids[off[i]:off[i + 1]].tolist() for i in range(len(X))]
+    assert sets == g["border_sets"]
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_lattice_exact_eps(d, precision, dtype):
+    """Every axis neighbour sits at exactly eps: the FP32 band must send those
+    pairs to the FP64 recheck and keep them."""
+    L = {1: 40, 2: 12, 3: 7, 4: 5}[d]
+    grid = np.stack(np.meshgrid(*[np.arange(L)] * d, indexing="ij"), -1).reshape(-1, d)
+    X = (grid * 0.75 + 3.0).astype(dtype)
+    st = _assert_same(X, 0.75, 2 * d + 1, precision=precision)
+    if precision == "fp32":
+        assert st["band_rechecks"] > 0
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+@pytest.mark.parametrize("seed", [0, 1])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_random_mixed(d, seed, precision, dtype):
+    X = synth.random_small(300 + 10 * seed + d, 5000 + 777 * seed, d, dtype=dtype)
+    for eps, mp in ((0.15, 4), (0.3, 12), (0.6, 40)):
+        _assert_same(X, eps, mp, precision=precision)
+
+
+@pytest.mark.parametrize("schedule", ["size", "none"])
+def test_schedules_agree(schedule):
+    X = synth.random_small(77, 20000, 3, dtype=np.float32)
+    st = _assert_same(X, 0.25, 10, schedule=schedule)
+    assert st["num_pairs_tested"] + st["num_pairs_skipped"] == st["num_candidate_pairs"]
+
+
+def test_blobs_2d_20k_fp64():
+    """Gaussian blobs in 2D, FP64 input, eps 0.5, minPts 10."""
+    I = synth.blobs_2d_20k()
+    for precision in ("fp64", "fp32"):
+        _assert_same(I.points, I.eps, I.min_pts, precision=precision)
+
+
+def test_spreader_3d_scaled():
+    """The 3D seed-spreader workload at 1/10 size (several tiles, ragged tail)."""
+    I = synth.spreader_3d_2m(n=200_003)
+    st = _assert_same(I.points, I.eps, I.min_pts)
+    assert st["num_cells"] > 1000 and st["num_pairs_tested"] > 0
+
+
+@pytest.mark.slow
+def test_spreader_3d_full_size():
+    """The full 2,000,000-point 3D workload (FP32 input, FP32 band + FP64
+    recheck), in the configuration the benchmark times, against the full
+    oracle run."""
+    I = synth.spreader_3d_2m()
+    t = torch.from_numpy(I.points).cuda()
+    ctx = DBSCAN(len(I.points), 3)
+    r = ctx.run(t, I.eps, I.min_pts, border=True)
+    torch.cuda.synchronize()
+    core, labels, off, ids = oracle.dbscan(I.points, I.eps, I.min_pts)
+    assert np.array_equal(r.core.cpu().numpy(), core)
+    assert np.array_equal(r.labels.cpu().numpy(), labels)
+    assert np.array_equal(r.border_offsets.cpu().numpy(), off)
+    assert np.array_equal(r.border_ids.cpu().numpy(), ids)
+
+
+def test_edge_cases():
+    rng = np.random.default_rng(5)
+    # empty
+    ctx = DBSCAN(100, 3)
+    r = ctx.run(torch.zeros((0, 3), device="cuda"), 1.0, 3)
+    assert r.core.numel() == 0 and r.border_offsets.cpu().tolist() == [0]
+    # one point
+    _assert_same(np.array([[1.0, 2.0]]), 0.5, 1)
+    _assert_same(np.array([[1.0, 2.0]]), 0.5, 2)
+    # all identical
+    _assert_same(np.full((500, 3), 7.5, np.float32), 0.1, 500)
+    _assert_same(np.full((500, 3), 7.5, np.float32), 0.1, 501)
+    # minPts = 1 (every point core) and minPts > n (all noise)
+    X = rng.random((3000, 2))
+    _assert_same(X, 0.02, 1)
+    _assert_same(X, 0.02, 4000)
+    # eps above the diameter: one cell, one cluster
+    _assert_same(X.astype(np.float32), 5.0, 100)
+    # negative and large coordinates, ragged size
+    Y = (rng.standard_normal((4099, 3)) * 1e4 - 5e4).astype(np.float32)
+    _assert_same(Y, 900.0, 5)
+
+
+def test_host_entry_point_matches_device():
+    X = synth.random_small(8, 10000, 3, dtype=np.float32)
+    ctx = DBSCAN(len(X), 3)
+    pinned = torch.from_numpy(X).pin_memory()
+    core, labels = ctx.run_host(pinned, 0.3, 8, core=torch.empty(len(X), dtype=torch.uint8).pin_memory(),
+                                labels=torch.empty(len(X), dtype=torch.int32).pin_memory())
+    exp = oracle.dbscan(X, 0.3, 8)
+    assert np.array_equal(core.numpy(), exp[0]) and np.array_equal(labels.numpy(), exp[1])
+
+
+def test_invalid_arguments():
+    ctx = DBSCAN(1000, 3)
+    X = torch.zeros((10, 3), device="cuda")
+    with pytest.raises(DbscanError) as e:
+        ctx.run(X, -1.0, 3)
+    assert e.value.status == 1
+    with pytest.raises(DbscanError) as e:
+        ctx.run(X, float("nan"), 3)
+    assert e.value.status == 1
+    with pytest.raises(DbscanError) as e:
+        ctx.run(X, 1.0, 0)
+    assert e.value.status == 1
+    Xn = X.clone()
+    Xn[3, 1] = float("nan")
+    with pytest.raises(DbscanError) as e:
+        ctx.run(Xn, 1.0, 3)
+    assert e.value.status == 1
+    Xi = X.clone()
+    Xi[4, 0] = float("inf")
+    with pytest.raises(DbscanError) as e:
+        ctx.run(Xi, 1.0, 3)
+    assert e.value.status == 1
+    with pytest.raises(DbscanError) as e:
+        ctx.run(torch.zeros((2000, 3), device="cuda"), 1.0, 3)
+    assert e.value.status == 1
+    with pytest.raises(DbscanError) as e:
+        ctx.run(torch.zeros((10, 4), device="cuda"), 1.0, 3)
+    assert e.value.status == 2
+    # a grid wider than 2^30 cells in one dimension
+    Xw = torch.tensor([[0.0, 0.0, 0.0], [1e12, 0.0, 0.0]], device="cuda", dtype=torch.float64)
+    with pytest.raises(DbscanError) as e:
+        ctx.run(Xw, 1e-3, 2)
+    assert e.value.status == 4
+    # the context stays usable after errors
+    _ = ctx.run(torch.rand((500, 3), device="cuda"), 0.2, 3)
+
+
+def test_context_reuse_and_determinism():
+    X = synth.random_small(21, 8000, 2, dtype=np.float32)
+    ctx = DBSCAN(len(X), 2)
+    t = torch.from_numpy(X).cuda()
+    a = ctx.run(t, 0.2, 6)
+    b = ctx.run(t, 0.2, 6)
+    for u, v in ((a.core, b.core), (a.labels, b.labels), (a.border_offsets, b.border_offsets),
+                 (a.border_ids, b.border_ids)):
+        assert torch.equal(u, v)
+    c = ctx.run(t[:5000], 0.35, 9)
+    exp = oracle.dbscan(X[:5000], 0.35, 9)
+    assert np.array_equal(c.labels.cpu().numpy(), exp[1])
