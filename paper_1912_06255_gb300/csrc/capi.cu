@@ -358,6 +358,8 @@ dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, 
     if (n == 0) {
         if (d_border_offsets) CK(cudaMemsetAsync(d_border_offsets, 0, sizeof(int64_t), s));
         CK(cudaStreamSynchronize(s));
+        c->have_run = true;
+        c->last = RunParams{};
         return DBSCAN_OK;
     }
     const bool f64 = dtype == DBSCAN_F64;
