@@ -170,6 +170,33 @@ dbscan_status dbscan_run_host(dbscan_ctx *ctx, const void *h_points, int64_t n, 
                               double eps, int64_t min_pts, uint8_t *h_core, int32_t *h_labels,
                               void *stream);
 
+/*
+ * Exact DBSCAN like dbscan_run(), without any allocation, for callers that
+ * cannot allocate device memory (code running inside another framework's
+ * memory pool, plugins whose host forbids device allocation after start-up,
+ * callers that must avoid the implicit synchronisation of cudaMalloc/cudaFree).
+ * The paper has no counterpart: this is a packaging of the same run.
+ *
+ * Working memory is one fixed __device__ array of the library (20 MiB), held by
+ * every GPU that loads the library until the process exits.  Limits:
+ * n <= 16384 points and d <= 3; larger n returns DBSCAN_ERR_CAPACITY, larger d
+ * DBSCAN_ERR_UNSUPPORTED_DIM.  The caller passes the input d_points [n, d]
+ * (DBSCAN_F32 or DBSCAN_F64) and the outputs d_core [n] and d_labels [n], with
+ * the meaning they have in dbscan_run(); border sets are not returned.
+ * Precision is the FP32 band with FP64 recheck, schedule SIZE.
+ *
+ * No cudaMalloc, cudaFree, pinned allocation or allocating library routine is
+ * called.  The first call on a device sets the array up (resolves its device
+ * address and copies the neighbour-offset tables into it, with synchronous
+ * copies), so make that first call before any stream capture.  The array is
+ * shared by every call on a device and keeps the last call's contents (each
+ * call clears what must start at zero): calls that overlap on the GPU, from
+ * any thread or stream, race and corrupt each other.  Synchronises the stream
+ * like dbscan_run().
+ */
+dbscan_status dbscan_run_static(const void *d_points, int64_t n, int d, int dtype, double eps,
+                                int64_t min_pts, uint8_t *d_core, int32_t *d_labels, void *stream);
+
 /* Counters of the last run (host copy; no device work). */
 dbscan_status dbscan_get_stats(const dbscan_ctx *ctx, dbscan_stats *out);
 

@@ -55,6 +55,7 @@ SIGNATURES = {
     "dbscan_run": (_I32, [_P, _P, _I64, _I32, _I32, _D, _I64, _P, _P, _P, ctypes.POINTER(_I64), _P]),
     "dbscan_border_ids": (_I32, [_P, _P, _I64, _P]),
     "dbscan_run_host": (_I32, [_P, _P, _I64, _I32, _I32, _D, _I64, _P, _P, _P]),
+    "dbscan_run_static": (_I32, [_P, _I64, _I32, _I32, _D, _I64, _P, _P, _P]),
     "dbscan_get_stats": (_I32, [_P, ctypes.POINTER(Stats)]),
     "dbscan_status_string": (ctypes.c_char_p, [_I32]),
     "dbscan_version": (_I32, []),

@@ -8,14 +8,13 @@
 #include <new>
 #include <vector>
 
+#include "ctx.cuh"
 #include "geom.cuh"
 #include "grid.cuh"
 
 using namespace gbdb;
 
-namespace {
-
-constexpr int kVersion = 100;  // 0.1.0
+namespace gbdb {
 
 // Candidate neighbour offsets of a d-dimensional cell (d <= 4): integer delta
 // != 0 with sum_j max(|delta_j| - 1, 0)^2 <= d.  A pair within eps spans cells
@@ -58,6 +57,13 @@ std::vector<signed char> offset_table(int d) {
 
 int num_offsets(int d) { return (int)(offset_table(d).size() / kMaxEnumDim); }
 
+}  // namespace gbdb
+
+namespace {
+
+constexpr int kVersion = 100;  // 0.1.0
+
+
 // FP32 band around T = fl(eps^2).  f is the FP32 value of sum (p'_i - q'_i)^2
 // for coordinates p', q' rounded to FP32 (each within E_coord of the input);
 // E is the resulting bound on |‖p'-q'‖ - ‖p-q‖|.  With the forward-error bounds
@@ -88,65 +94,6 @@ size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
-struct dbscan_ctx {
-    int device = 0;
-    int64_t max_points = 0;
-    int max_dim = 0;
-    int sd_max = 2;
-    int noff_max = 0;
-    // options
-    int precision = DBSCAN_PREC_FP32_RECHECK;
-    int sched = DBSCAN_SCHED_SIZE;
-    int collect_stats = 0;
-    int max_iters = 1 << 22;
-    int phase_timing = 0;
-    cudaEvent_t ev[9] = {};
-    // workspace
-    void *arena = nullptr;
-    size_t arena_bytes = 0;
-    uint64_t *k0 = nullptr, *k1 = nullptr;
-    uint32_t *v0 = nullptr, *v1 = nullptr;
-    unsigned *hist = nullptr;
-    long long *part = nullptr;
-    int *flags = nullptr, *cid = nullptr;
-    float *pf = nullptr, *cpf = nullptr;
-    double *pd = nullptr, *cpd = nullptr;
-    int *orig = nullptr, *cell_of = nullptr, *cell_start = nullptr;
-    uint64_t *cell_key = nullptr;
-    uint64_t *hk = nullptr;
-    int *hv = nullptr;
-    long long *nbr_cnt = nullptr, *nbr_off = nullptr;
-    int *nbr = nullptr;
-    long long nbr_cap = 0;
-    int *core_s = nullptr, *core_pos = nullptr, *ccs = nullptr, *core_orig = nullptr, *core_cell = nullptr;
-    int *rank = nullptr;
-    long long *pcnt = nullptr, *poff = nullptr;
-    int2 *pairs = nullptr;
-    long long pair_cap = 0;
-    int *parent = nullptr, *compmin = nullptr;
-    long long *bcount = nullptr, *boff = nullptr;
-    double *bbox_part = nullptr;
-    int *bbox_bad = nullptr;
-    double *bbox_out = nullptr;
-    signed char *offs = nullptr;  // [kMaxEnumDim][kMaxOffsets][kMaxEnumDim]
-    int noff[kMaxEnumDim + 1] = {0};
-    DevCounters *ctr = nullptr;
-    // pinned host
-    DevCounters *h_ctr = nullptr;
-    double *h_bbox = nullptr;
-    // host-buffer entry point
-    void *d_in = nullptr;
-    size_t d_in_bytes = 0;
-    uint8_t *d_core_h = nullptr;
-    int32_t *d_lab_h = nullptr;
-    // last run
-    bool have_run = false;
-    RunParams last{};
-    int last_D = 0, last_mode = 0;
-    const void *last_points = nullptr;
-    int last_dtype = 0;
-    dbscan_stats stats{};
-};
 
 static dbscan_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return DBSCAN_OK;

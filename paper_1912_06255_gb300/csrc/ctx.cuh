@@ -1,0 +1,75 @@
+// Host-side state of a dbscan_ctx (shared by the C-ABI translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "internal.cuh"
+
+namespace gbdb {
+// Neighbour-offset table of dimension d (<= kMaxEnumDim), kMaxEnumDim bytes per
+// offset, nearest first; and its number of offsets.
+std::vector<signed char> offset_table(int d);
+int num_offsets(int d);
+}  // namespace gbdb
+
+struct dbscan_ctx {
+    int device = 0;
+    int64_t max_points = 0;
+    int max_dim = 0;
+    int sd_max = 2;
+    int noff_max = 0;
+    // options
+    int precision = DBSCAN_PREC_FP32_RECHECK;
+    int sched = DBSCAN_SCHED_SIZE;
+    int collect_stats = 0;
+    int max_iters = 1 << 22;
+    int phase_timing = 0;
+    cudaEvent_t ev[9] = {};
+    // workspace
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    uint32_t *v0 = nullptr, *v1 = nullptr;
+    unsigned *hist = nullptr;
+    long long *part = nullptr;
+    int *flags = nullptr, *cid = nullptr;
+    float *pf = nullptr, *cpf = nullptr;
+    double *pd = nullptr, *cpd = nullptr;
+    int *orig = nullptr, *cell_of = nullptr, *cell_start = nullptr;
+    uint64_t *cell_key = nullptr;
+    uint64_t *hk = nullptr;
+    int *hv = nullptr;
+    long long *nbr_cnt = nullptr, *nbr_off = nullptr;
+    int *nbr = nullptr;
+    long long nbr_cap = 0;
+    int *core_s = nullptr, *core_pos = nullptr, *ccs = nullptr, *core_orig = nullptr, *core_cell = nullptr;
+    int *rank = nullptr;
+    long long *pcnt = nullptr, *poff = nullptr;
+    int2 *pairs = nullptr;
+    long long pair_cap = 0;
+    int *parent = nullptr, *compmin = nullptr;
+    long long *bcount = nullptr, *boff = nullptr;
+    double *bbox_part = nullptr;
+    int *bbox_bad = nullptr;
+    double *bbox_out = nullptr;
+    signed char *offs = nullptr;  // [kMaxEnumDim][kMaxOffsets][kMaxEnumDim]
+    int noff[gbdb::kMaxEnumDim + 1] = {0};
+    gbdb::DevCounters *ctr = nullptr;
+    // pinned host
+    gbdb::DevCounters *h_ctr = nullptr;
+    double *h_bbox = nullptr;
+    // host-buffer entry point
+    void *d_in = nullptr;
+    size_t d_in_bytes = 0;
+    uint8_t *d_core_h = nullptr;
+    int32_t *d_lab_h = nullptr;
+    // last run
+    bool have_run = false;
+    gbdb::RunParams last{};
+    int last_D = 0, last_mode = 0;
+    const void *last_points = nullptr;
+    int last_dtype = 0;
+    dbscan_stats stats{};
+};
