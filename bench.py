@@ -41,9 +41,12 @@ def _dist():
     return ws, rank, local
 
 
+_N = 2_000_000
+
+
 def _workload():
     from paper_1912_06255_gb300 import synth
-    return synth.spreader_3d_2m()
+    return synth.spreader_3d_2m(n=_N)
 
 
 def _cpu_sample(I):
@@ -164,6 +167,14 @@ def run_gpu(args):
     def step():
         ctx.run(X, I.eps, I.min_pts, border=False, out=(core, labels, offs))
 
+    if args.profile:
+        # profiling mode (for ncu): warm-up and timed steps only, no extra runs
+        for _ in range(args.warmup + args.steps):
+            step()
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile": I.name, "steps": args.steps, "warmup": args.warmup}), flush=True)
+        return
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -241,6 +252,7 @@ def run_gpu(args):
     te2e = max_over_ranks(sum(e2e_ms) / len(e2e_ms))
     if rank == 0:
         ph = [sum(p[i] for p in phases) / len(phases) for i in range(8)]
+        pair_tests = {"markcore": _PAIR_EVALS.get(4), "connect": _PAIR_EVALS.get(6)}
         names = ["bbox", "bbox_readback", "keys_sort", "cells_hash_neighbors", "markcore",
                  "compact_schedule", "connect_bcp_uf", "labels_border"]
         # dominant kernel: the MarkCore launch (one kernel, phase 4) or the BCP launch (phase 6)
@@ -263,6 +275,7 @@ def run_gpu(args):
             "gpu_launches": int(launches),
             "phase_ms": dict(zip(names, [round(x, 4) for x in ph])),
             "roofline": roof,
+            "pair_tests": pair_tests,
             "run_stats": {k: stats[k] for k in ("num_cells", "num_core_cells", "num_candidate_pairs",
                                                  "num_pairs_tested", "num_pairs_skipped", "num_core_points",
                                                  "num_border_points", "band_rechecks", "key_bits")},
@@ -320,7 +333,13 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--schedule", default="size", choices=["size", "none"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="run warm-up + timed steps only and print no bench line (for ncu)")
+    ap.add_argument("--n", type=int, default=2_000_000,
+                    help="points of the seed-spreader workload (the bench line is defined at 2,000,000)")
     args = ap.parse_args()
+    global _N
+    _N = args.n
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -256,10 +256,12 @@ __device__ __forceinline__ bool bcp_warp(int r0, int nr, int c0, int nc, const f
     return false;
 }
 
-// ClusterCore's pair loop (Algorithm 3): warps take pairs in list order from a
-// global counter; a pair whose cells union-find already joined is skipped
-// ("Reducing Cell Connectivity Queries"), otherwise BCP decides and a hit links
-// the two cells.
+// ClusterCore's pair loop (Algorithm 3): a warp takes the next 32 pairs of
+// the priority-ordered list with one atomic, checks all 32 against the
+// union-find in parallel (one pair per lane), and runs BCP on the survivors
+// one at a time, re-checking each just before its test because earlier links
+// may have joined it meanwhile ("Reducing Cell Connectivity Queries").  A hit
+// links the two cells.
 template <int D, int M>
 __global__ void __launch_bounds__(256)
 k_connect(RunParams P, const int2 *__restrict__ pairs, const int *__restrict__ ccs,
@@ -269,23 +271,37 @@ k_connect(RunParams P, const int2 *__restrict__ pairs, const int *__restrict__ c
     unsigned rech = 0;
     unsigned long long evals = 0, tested = 0, skipped = 0, linked = 0;
     for (;;) {
-        unsigned long long idx = 0;
-        if (lane == 0) idx = atomicAdd(&ctr->pair_next, 1ull);
-        idx = __shfl_sync(0xffffffffu, idx, 0);
-        if (idx >= np) break;
-        const int2 pr = pairs[idx];
-        int same = 0;
-        if (lane == 0) same = uf_find(parent, pr.x, P.max_iters, ctr) == uf_find(parent, pr.y, P.max_iters, ctr);
-        same = __shfl_sync(0xffffffffu, same, 0);
-        if (same) { ++skipped; continue; }
-        ++tested;
-        const int a0 = ccs[pr.x], na = ccs[pr.x + 1] - a0;
-        const int b0 = ccs[pr.y], nb = ccs[pr.y + 1] - b0;
-        const bool hit = na >= nb ? bcp_warp<D, M>(a0, na, b0, nb, cpf, cpd, P, rech, evals)
-                                  : bcp_warp<D, M>(b0, nb, a0, na, cpf, cpd, P, rech, evals);
-        if (hit) {
-            ++linked;
-            if (lane == 0) uf_link(parent, pr.x, pr.y, P.max_iters, ctr);
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&ctr->pair_next, 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= np) break;
+        const unsigned long long idx = base + lane;
+        const bool valid = idx < np;
+        int2 pr = make_int2(0, 0);
+        bool same = true;
+        if (valid) {
+            pr = pairs[idx];
+            same = uf_find(parent, pr.x, P.max_iters, ctr) == uf_find(parent, pr.y, P.max_iters, ctr);
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, !same);
+        skipped += __popc(__ballot_sync(0xffffffffu, valid && same));
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int a = __shfl_sync(0xffffffffu, pr.x, src);
+            const int b = __shfl_sync(0xffffffffu, pr.y, src);
+            int again = 0;
+            if (lane == 0) again = uf_find(parent, a, P.max_iters, ctr) == uf_find(parent, b, P.max_iters, ctr);
+            if (__shfl_sync(0xffffffffu, again, 0)) { ++skipped; continue; }
+            ++tested;
+            const int a0 = ccs[a], na = ccs[a + 1] - a0;
+            const int b0 = ccs[b], nb = ccs[b + 1] - b0;
+            const bool hit = na >= nb ? bcp_warp<D, M>(a0, na, b0, nb, cpf, cpd, P, rech, evals)
+                                      : bcp_warp<D, M>(b0, nb, a0, na, cpf, cpd, P, rech, evals);
+            if (hit) {
+                ++linked;
+                if (lane == 0) uf_link(parent, a, b, P.max_iters, ctr);
+            }
         }
     }
     if (lane == 0) {

@@ -49,17 +49,39 @@ k_bbox(const T *__restrict__ X, int n, int d, double *__restrict__ part, int *__
     }
 }
 
-__global__ void k_bbox_final(const double *__restrict__ part, int nb, const int *bad, double *out) {
-    const int j = threadIdx.x;
-    if (j < 2 * kMaxDim) {
-        double v = part[j];
-        for (int b = 1; b < nb; ++b) {
-            double w = part[b * 2 * kMaxDim + j];
-            v = j < kMaxDim ? fmin(v, w) : fmax(v, w);
+// Reduce the per-block extremes: 256 threads stride over the blocks, then a
+// warp-shuffle and shared-memory reduction per coordinate.
+__global__ void __launch_bounds__(256) k_bbox_final(const double *__restrict__ part, int nb, const int *bad, double *out) {
+    __shared__ double sh[8][2 * kMaxDim];
+    double v[2 * kMaxDim];
+#pragma unroll
+    for (int j = 0; j < 2 * kMaxDim; ++j)
+        v[j] = j < kMaxDim ? __longlong_as_double(0x7ff0000000000000ll) : __longlong_as_double(0xfff0000000000000ll);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+#pragma unroll
+        for (int j = 0; j < 2 * kMaxDim; ++j) {
+            const double w = part[b * 2 * kMaxDim + j];
+            v[j] = j < kMaxDim ? fmin(v[j], w) : fmax(v[j], w);
         }
-        out[j] = v;
     }
-    if (j == 0) out[2 * kMaxDim] = (double)*bad;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < 2 * kMaxDim; ++j) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_xor_sync(0xffffffffu, v[j], o);
+            v[j] = j < kMaxDim ? fmin(v[j], w) : fmax(v[j], w);
+        }
+        if (lane == 0) sh[warp][j] = v[j];
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * kMaxDim) {
+        const int j = threadIdx.x;
+        double r = sh[0][j];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = j < kMaxDim ? fmin(r, sh[w][j]) : fmax(r, sh[w][j]);
+        out[j] = r;
+    }
+    if (threadIdx.x == 0) out[2 * kMaxDim] = (double)*bad;
 }
 
 void launch_bbox(const void *X, int dtype, int n, int d, double *part, int nb, int *bad,
@@ -69,7 +91,7 @@ void launch_bbox(const void *X, int dtype, int n, int d, double *part, int nb, i
     else
         k_bbox<double><<<nb, BB_THREADS, 0, s>>>((const double *)X, n, d, part, bad);
     count_launch();
-    k_bbox_final<<<1, 32, 0, s>>>(part, nb, bad, out); count_launch();
+    k_bbox_final<<<1, 256, 0, s>>>(part, nb, bad, out); count_launch();
 }
 
 // ---------------------------------------------------------------- keys
