@@ -72,7 +72,12 @@ enum {
     DBSCAN_OPT_MAX_ITERS = 3,
     /* value: 0 (default) or 1: record CUDA events around each phase and report
        the phase durations in dbscan_stats.phase_ms */
-    DBSCAN_OPT_PHASE_TIMING = 4
+    DBSCAN_OPT_PHASE_TIMING = 4,
+    /* value: 1 (default) or 0: in the FP32-band mode, decide whole cells by
+       the bounding boxes of their points where the boxes settle the question
+       (all pairs within eps, or none), as the quadtree range counts of
+       Sec. 5.2 do; 0 tests every pair point by point */
+    DBSCAN_OPT_CELL_BOUNDS = 5
 };
 enum { DBSCAN_PREC_FP64 = 0, DBSCAN_PREC_FP32_RECHECK = 1 };
 /* SIZE: core-cell pairs are tested in order of non-increasing core count of the
@@ -96,7 +101,8 @@ typedef struct {
     int64_t num_candidate_pairs;    /* core-cell pairs, each unordered pair once */
     int64_t num_pairs_tested;       /* BCP tests run */
     int64_t num_pairs_skipped;      /* pairs skipped because union-find had joined them */
-    int64_t num_pairs_connected;    /* BCP tests that found a pair within eps */
+    int64_t num_pairs_connected;    /* pairs found connected (by BCP or by their boxes) */
+    int64_t num_pairs_box_decided;  /* pairs settled by the core-point bounding boxes alone */
     int64_t num_core_points;
     int64_t num_border_points;
     int64_t num_noise_points;

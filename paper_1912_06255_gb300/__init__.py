@@ -42,7 +42,8 @@ class DBSCAN:
     """A reusable context (device workspace sized for max_points x max_dim)."""
 
     def __init__(self, max_points: int, max_dim: int, precision: str = "fp32",
-                 schedule: str = "size", collect_stats: bool = False, max_iters: int | None = None):
+                 schedule: str = "size", collect_stats: bool = False, max_iters: int | None = None,
+                 cell_bounds: bool = True):
         self.lib = _lib.load()
         self.ctx = ctypes.c_void_p()
         _lib.check(self.lib.dbscan_create(ctypes.byref(self.ctx), int(max_points), int(max_dim)),
@@ -53,6 +54,7 @@ class DBSCAN:
         self.set_option(_lib.OPT_PRECISION, prec)
         self.set_option(_lib.OPT_SCHEDULE, sched)
         self.set_option(_lib.OPT_COLLECT_STATS, int(bool(collect_stats)))
+        self.set_option(_lib.OPT_CELL_BOUNDS, int(bool(cell_bounds)))
         if max_iters is not None:
             self.set_option(_lib.OPT_MAX_ITERS, int(max_iters))
 
@@ -134,11 +136,11 @@ class DBSCAN:
 
 
 def dbscan(points, eps: float, min_pts: int, precision: str = "fp32", schedule: str = "size",
-           border: bool = True, collect_stats: bool = False) -> Result:
+           border: bool = True, collect_stats: bool = False, cell_bounds: bool = True) -> Result:
     """One-shot exact DBSCAN of a CUDA tensor [n, d] (float32 or float64)."""
     n, d = points.shape
     ctx = DBSCAN(max(int(n), 1), int(d), precision=precision, schedule=schedule,
-                 collect_stats=collect_stats)
+                 collect_stats=collect_stats, cell_bounds=cell_bounds)
     try:
         return ctx.run(points, eps, min_pts, border=border)
     finally:

@@ -19,7 +19,7 @@ STATUS = {
     6: "DBSCAN_ERR_CUDA", 7: "DBSCAN_ERR_DEVICE_TIMEOUT", 8: "DBSCAN_ERR_STATE",
 }
 F32, F64 = 0, 1
-OPT_PRECISION, OPT_SCHEDULE, OPT_COLLECT_STATS, OPT_MAX_ITERS, OPT_PHASE_TIMING = 0, 1, 2, 3, 4
+OPT_PRECISION, OPT_SCHEDULE, OPT_COLLECT_STATS, OPT_MAX_ITERS, OPT_PHASE_TIMING, OPT_CELL_BOUNDS = 0, 1, 2, 3, 4, 5
 PREC_FP64, PREC_FP32_RECHECK = 0, 1
 SCHED_SIZE, SCHED_NONE = 0, 1
 
@@ -34,7 +34,8 @@ class Stats(ctypes.Structure):
         ("num_cells", ctypes.c_int64), ("num_core_cells", ctypes.c_int64),
         ("num_neighbor_entries", ctypes.c_int64), ("num_candidate_pairs", ctypes.c_int64),
         ("num_pairs_tested", ctypes.c_int64), ("num_pairs_skipped", ctypes.c_int64),
-        ("num_pairs_connected", ctypes.c_int64), ("num_core_points", ctypes.c_int64),
+        ("num_pairs_connected", ctypes.c_int64), ("num_pairs_box_decided", ctypes.c_int64),
+        ("num_core_points", ctypes.c_int64),
         ("num_border_points", ctypes.c_int64), ("num_noise_points", ctypes.c_int64),
         ("num_border_memberships", ctypes.c_int64), ("band_rechecks", ctypes.c_int64),
         ("distance_evals", ctypes.c_int64), ("distance_evals_phase", ctypes.c_int64 * 3), ("band_lo", ctypes.c_float), ("band_hi", ctypes.c_float),

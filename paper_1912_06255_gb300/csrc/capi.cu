@@ -114,7 +114,8 @@ static Bufs make_bufs(dbscan_ctx *c, bool f64) {
     B.orig = c->orig;
     B.cell_of = c->cell_of;
     B.cell_start = c->cell_start;
-    B.nbr_off = c->nbr_off;
+    B.nbr_cnt = c->nbr_cnt;
+    B.nbr_near = c->nbr_near;
     B.nbr = c->nbr;
     B.core_s = c->core_s;
     B.core_pos = c->core_pos;
@@ -123,18 +124,20 @@ static Bufs make_bufs(dbscan_ctx *c, bool f64) {
     B.cpd = f64 ? c->cpd : nullptr;
     B.core_orig = c->core_orig;
     B.core_cell = c->core_cell;
+    B.blo = c->blo;
+    B.bhi = c->bhi;
+    B.cblo = c->cblo;
+    B.cbhi = c->cbhi;
     B.sk0 = c->k0;
     B.sk1 = c->k1;
     B.sv0 = c->v0;
     B.sv1 = c->v1;
-    B.hist = c->hist;
+    B.sort_scratch = c->sort_scratch;
+    B.max_iters = c->max_iters;
     B.rank = c->rank;
-    B.pcnt = c->pcnt;
-    B.poff = c->poff;
-    B.pairs = c->pairs;
-    B.pair_cap = c->pair_cap;
     B.parent = c->parent;
     B.compmin = c->compmin;
+    B.noncore = c->noncore;
     B.bcount = c->bcount;
     B.boff = c->boff;
     B.part = c->part;
@@ -192,9 +195,7 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
     for (int d = 1; d <= max_dim; ++d) noff_max = std::max(noff_max, c->noff[d]);
     c->noff_max = noff_max;
     c->nbr_cap = (long long)noff_max * N + 1;
-    c->pair_cap = c->nbr_cap / 2 + 1;
-    const int64_t hsz = radix_hist_size(N);
-    const int64_t npart = scan_partials(std::max<int64_t>(N + 1, hsz)) + 2;
+    const int64_t npart = scan_partials(N + 1) + 2;
     const uint64_t hcap = hash_capacity((int)N);
     const int SD = c->sd_max;
 
@@ -203,23 +204,23 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
     std::vector<Item> items = {
         {(void **)&c->k0, 8 * (size_t)N}, {(void **)&c->k1, 8 * (size_t)N},
         {(void **)&c->v0, 4 * (size_t)N}, {(void **)&c->v1, 4 * (size_t)N},
-        {(void **)&c->hist, 4 * (size_t)hsz}, {(void **)&c->part, 8 * (size_t)npart},
+        {(void **)&c->sort_scratch, sort_scratch_bytes(N)}, {(void **)&c->part, 8 * (size_t)npart},
         {(void **)&c->flags, 4 * (size_t)(N + 1)}, {(void **)&c->cid, 4 * (size_t)(N + 1)},
         {(void **)&c->pf, 4 * (size_t)N * SD}, {(void **)&c->pd, 8 * (size_t)N * SD},
         {(void **)&c->cpf, 4 * (size_t)N * SD}, {(void **)&c->cpd, 8 * (size_t)N * SD},
         {(void **)&c->orig, 4 * (size_t)N}, {(void **)&c->cell_of, 4 * (size_t)N},
         {(void **)&c->cell_start, 4 * (size_t)(N + 1)}, {(void **)&c->cell_key, 8 * (size_t)N},
-        {(void **)&c->hk, 8 * (size_t)hcap}, {(void **)&c->hv, 4 * (size_t)hcap},
-        {(void **)&c->nbr_cnt, 8 * (size_t)(N + 1)}, {(void **)&c->nbr_off, 8 * (size_t)(N + 1)},
+        {(void **)&c->ht, 16 * (size_t)hcap},
+        {(void **)&c->nbr_cnt, 4 * (size_t)(N + 1)}, {(void **)&c->nbr_near, 4 * (size_t)(N + 1)},
         {(void **)&c->nbr, 4 * (size_t)c->nbr_cap},
         {(void **)&c->core_s, 4 * (size_t)N}, {(void **)&c->core_pos, 4 * (size_t)(N + 1)},
         {(void **)&c->ccs, 4 * (size_t)(N + 1)}, {(void **)&c->core_orig, 4 * (size_t)N},
         {(void **)&c->core_cell, 4 * (size_t)N}, {(void **)&c->rank, 4 * (size_t)N},
-        {(void **)&c->pcnt, 8 * (size_t)(N + 1)}, {(void **)&c->poff, 8 * (size_t)(N + 1)},
-        {(void **)&c->pairs, 8 * (size_t)c->pair_cap},
+        {(void **)&c->blo, 16 * (size_t)N}, {(void **)&c->bhi, 16 * (size_t)N},
+        {(void **)&c->cblo, 16 * (size_t)N}, {(void **)&c->cbhi, 16 * (size_t)N},
         {(void **)&c->parent, 4 * (size_t)N}, {(void **)&c->compmin, 4 * (size_t)N},
+        {(void **)&c->noncore, 4 * (size_t)N},
         {(void **)&c->bcount, 8 * (size_t)N}, {(void **)&c->boff, 8 * (size_t)(N + 1)},
-        {(void **)&c->bbox_part, 8 * (size_t)1024 * 2 * kMaxDim}, {(void **)&c->bbox_bad, 4},
         {(void **)&c->bbox_out, 8 * (2 * kMaxDim + 1)},
         {(void **)&c->offs, (size_t)kMaxEnumDim * kMaxOffsets * kMaxEnumDim},
         {(void **)&c->ctr, sizeof(DevCounters)},
@@ -232,7 +233,7 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
     size_t at = 0;
     for (auto &it : items) { *it.p = (char *)c->arena + at; at += align_up(it.bytes); }
     e = cudaMallocHost((void **)&c->h_ctr, sizeof(DevCounters));
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_bbox, sizeof(double) * (2 * kMaxDim + 1));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_bbox, sizeof(long long) * (2 * kMaxDim + 1));
     for (int k = 0; k < 9 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
     for (int d = 1; d <= kMaxEnumDim && e == cudaSuccess; ++d) {
         std::vector<signed char> t = offset_table(d);
@@ -262,6 +263,10 @@ dbscan_status dbscan_set_option(dbscan_ctx *c, int option, int64_t value) {
     case DBSCAN_OPT_COLLECT_STATS:
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
         c->collect_stats = (int)value;
+        return DBSCAN_OK;
+    case DBSCAN_OPT_CELL_BOUNDS:
+        if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
+        c->cell_bounds = (int)value;
         return DBSCAN_OK;
     case DBSCAN_OPT_PHASE_TIMING:
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
@@ -320,14 +325,13 @@ dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, 
 
     // 1. bounding box (one sync: it sizes the cell key)
     CK(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
-    CK(cudaMemsetAsync(c->bbox_bad, 0, sizeof(int), s));
-    const int nbb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (n + 255) / 256));
-    launch_bbox(d_points, dtype, (int)n, d, c->bbox_part, nbb, c->bbox_bad, c->bbox_out, s);
+    const int nbb = (int)std::min<int64_t>(4 * 152, std::max<int64_t>(1, (n + 255) / 256));
+    launch_bbox(d_points, dtype, (int)n, d, nbb, c->bbox_out, s);
     mark(1);
-    CK(cudaMemcpyAsync(c->h_bbox, c->bbox_out, sizeof(double) * (2 * kMaxDim + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->h_bbox, c->bbox_out, sizeof(long long) * (2 * kMaxDim + 1), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
-    if (c->h_bbox[2 * kMaxDim] != 0.0) return DBSCAN_ERR_INVALID_ARG;
+    if (c->h_bbox[2 * kMaxDim] != 0) return DBSCAN_ERR_INVALID_ARG;
 
     // 2. grid parameters: side s = eps/sqrt(d) * (1 - 2^-20) (Sec. 3)
     RunParams P{};
@@ -342,7 +346,7 @@ dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, 
     int kmax_all = 0;
     double M = 0.0;
     for (int j = 0; j < d; ++j) {
-        const double lo = c->h_bbox[j], hi = c->h_bbox[kMaxDim + j];
+        const double lo = bbox_key_to_double(c->h_bbox[j]), hi = bbox_key_to_double(c->h_bbox[kMaxDim + j]);
         P.origin[j] = lo;
         const double t = (hi - lo) * P.inv_s;
         if (!(t < 0x1p30)) return DBSCAN_ERR_KEY_OVERFLOW;
@@ -364,34 +368,45 @@ dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, 
         if (fp32_band(P.eps2, d, E, &P.lo, &P.hi)) mode = f64 ? kF32FromF64 : kF32FromF32;
     }
     c->stats.precision = (mode == kF32FromF32 || mode == kF32FromF64) ? DBSCAN_PREC_FP32_RECHECK : DBSCAN_PREC_FP64;
+    P.box = c->stats.precision == DBSCAN_PREC_FP32_RECHECK && c->cell_bounds ? 1 : 0;
     c->stats.band_lo = P.lo;
     c->stats.band_hi = P.hi;
 
-    // 3. keys and sort (semisort role, Sec. 4.1)
+    // 3. keys and sort (semisort role, Sec. 4.1).  When the cell key and the
+    // point index fit together in 64 bits they are packed and sorted as one.
+    int ib = 1;
+    while (ib < 31 && (1ll << ib) < n) ++ib;
+    if (d * bits + ib > 64) ib = 0;
+    P.ib = ib;
     mark(2);
     launch_keys(d_points, dtype, P, c->k0, c->v0, s);
-    const int which = radix_sort_u64(c->k0, c->v0, c->k1, c->v1, (int)n, nullptr, n, d * bits, c->hist, c->part, s);
+    const int which = radix_sort_u64(c->k0, ib ? nullptr : c->v0, c->k1, ib ? nullptr : c->v1, (int)n, nullptr, n,
+                                     ib, d * bits, c->sort_scratch, c->ctr, c->max_iters, s);
     const uint64_t *K = which ? c->k1 : c->k0;
     const uint32_t *V = which ? c->v1 : c->v0;
 
     // 4. cells, hash, neighbour lists
     mark(3);
-    launch_cells(d_points, dtype, (int)n, d, SD, K, V, c->flags, c->cid, c->part, c->pf, f64 ? c->pd : nullptr,
+    launch_cells(d_points, dtype, (int)n, d, SD, ib, K, V, c->flags, c->cid, c->part, c->pf, f64 ? c->pd : nullptr,
                  c->orig, c->cell_of, c->cell_start, c->cell_key, c->ctr, s);
-    launch_hash(c->hk, c->hv, c->cell_key, c->ctr, s);
-    launch_neighbors(c->cell_key, c->hk, c->hv, P, offs_for(c, d), c->noff[d], c->nbr_cnt, c->nbr_off, c->nbr,
-                     c->nbr_cap, c->part, n, c->ctr, s);
+    if (P.box) launch_boxes(SD, c->pf, c->cell_start, c->ctr, c->blo, c->bhi, s);
+    launch_hash(c->ht, c->cell_key, c->ctr, s);
+    int n_near = 1;
+    for (int j = 0; j < d; ++j) n_near *= 3;
+    launch_neighbors(c->cell_key, c->ht, P, offs_for(c, d), c->noff[d], n_near - 1, c->blo, c->bhi, c->nbr_cnt,
+                     c->nbr_near, c->nbr, c->ctr, s);
 
     // 5. MarkCore, 6. compaction, 7. schedule, 8. connect, 9. labels, 10. border
     Bufs B = make_bufs(c, f64);
     B.n_max = n;
+    B.nbr_stride = c->noff[d];
     mark(4);
     launch_markcore(D, mode, P, B, c->ctr, s);
     mark(5);
     launch_core_compact(SD, P, B, c->ctr, s);
-    launch_schedule(c->sched, P, B, c->ctr, s);
+    const uint32_t *order = launch_schedule(c->sched, P, B, c->ctr, s);
     mark(6);
-    launch_connect(D, mode, P, B, c->ctr, s);
+    launch_connect(D, mode, order, P, B, c->ctr, s);
     mark(7);
     launch_labels(P, B, d_core, d_labels, c->ctr, s);
     launch_border(D, mode, false, P, B, d_labels, nullptr, 0, c->ctr, s);
@@ -410,6 +425,7 @@ dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, 
     st.num_pairs_tested = (int64_t)h.pairs_tested;
     st.num_pairs_skipped = (int64_t)h.pairs_skipped;
     st.num_pairs_connected = (int64_t)h.pairs_linked;
+    st.num_pairs_box_decided = (int64_t)h.pairs_box;
     st.num_core_points = h.n_core;
     st.num_border_points = h.n_border;
     st.num_noise_points = n - h.n_core - h.n_border;
@@ -441,6 +457,7 @@ dbscan_status dbscan_border_ids(dbscan_ctx *c, int32_t *d_ids, int64_t capacity,
     const bool f64 = c->last_dtype == DBSCAN_F64;
     Bufs B = make_bufs(c, f64);
     B.n_max = c->last.n;
+    B.nbr_stride = c->noff[c->last.d];
     CK(cudaMemsetAsync(&c->ctr->err, 0, sizeof(int), s));
     launch_border(c->last_D, c->last_mode, true, c->last, B, nullptr, d_ids, capacity, c->ctr, s);
     CK(cudaGetLastError());

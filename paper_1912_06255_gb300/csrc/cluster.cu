@@ -14,67 +14,179 @@ __device__ __forceinline__ void flush_counter(unsigned long long *dst, unsigned 
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
 }
 
+#define GBDB_DISPATCH(D, MODE, ...)                                     \
+    do {                                                                \
+        switch ((D) * 4 + (MODE)) {                                     \
+        case 8: { constexpr int DD = 2, MM = 0; __VA_ARGS__; } break;   \
+        case 9: { constexpr int DD = 2, MM = 1; __VA_ARGS__; } break;   \
+        case 10: { constexpr int DD = 2, MM = 2; __VA_ARGS__; } break;  \
+        case 11: { constexpr int DD = 2, MM = 3; __VA_ARGS__; } break;  \
+        case 12: { constexpr int DD = 3, MM = 0; __VA_ARGS__; } break;  \
+        case 13: { constexpr int DD = 3, MM = 1; __VA_ARGS__; } break;  \
+        case 14: { constexpr int DD = 3, MM = 2; __VA_ARGS__; } break;  \
+        case 15: { constexpr int DD = 3, MM = 3; __VA_ARGS__; } break;  \
+        case 16: { constexpr int DD = 4, MM = 0; __VA_ARGS__; } break;  \
+        case 17: { constexpr int DD = 4, MM = 1; __VA_ARGS__; } break;  \
+        case 18: { constexpr int DD = 4, MM = 2; __VA_ARGS__; } break;  \
+        case 19: { constexpr int DD = 4, MM = 3; __VA_ARGS__; } break;  \
+        default: break;                                                 \
+        }                                                               \
+    } while (0)
+
 // ----------------------------------------------------------------- MarkCore
 // A cell with at least minPts points marks all of them core (all its points
-// are within eps of each other).  In a sparser cell g each point p counts
+// are within eps of each other).  In a sparser cell g every point p counts
 // |g| plus RangeCount(p, eps, h) over the neighbouring cells h, scanning their
-// points, and stops as soon as the count reaches minPts.  One thread per point,
-// points in cell order, so the threads of a warp mostly share cells.
-template <int D, int M>
-__global__ void __launch_bounds__(256)
-k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__ pd,
-           const int *__restrict__ cell_of, const int *__restrict__ cell_start,
-           const long long *__restrict__ nbr_off, const int *__restrict__ nbr,
-           int *__restrict__ core_s, DevCounters *ctr) {
-    unsigned rech = 0;
-    unsigned long long evals = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-        const int c = cell_of[i];
-        int count = cell_start[c + 1] - cell_start[c];
-        if (count >= P.min_pts) { core_s[i] = 1; continue; }
-        Pt<D, M> p;
-        load_pt(p, pf, pd, i);
-        const long long e1 = nbr_off[c + 1];
-        for (long long e = nbr_off[c]; e < e1 && count < P.min_pts; ++e) {
-            const int h = nbr[e];
-            const int t1 = cell_start[h + 1];
-            for (int t = cell_start[h]; t < t1; ++t) {
+// points, and stops once the count reaches minPts.
+//
+// One warp per cell.  The cell's own points (up to MC_OWN at a time) sit in
+// shared memory and, one per lane, in registers.  In the FP32-band mode each
+// neighbouring cell h is first classified per own point against h's bounding
+// box (Sec. 5.2 counts whole quadtree cells the same way): entirely within eps
+// -> add |h|; entirely beyond -> skip; otherwise the warp streams h 32 points
+// at a time, one per lane, and for every such own point tests all 32 at once
+// and adds the vote count.  The lanes stay converged, the loads coalesce, and
+// the cell stops once all its points reached minPts.
+constexpr int MC_THREADS = 256, MC_WARPS = MC_THREADS / 32, MC_OWN = 128;
+
+// One batch of kb <= 32*NS own points of a sparse cell whose k points start at
+// s0 (the batch starts at own index b0); own[] holds the batch.
+template <int D, int M, int NS>
+__device__ __forceinline__ void mc_batch(const RunParams &P, const float *__restrict__ pf, const double *__restrict__ pd,
+                                         const int *__restrict__ cell_start, const int *__restrict__ nl, int ne,
+                                         const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
+                                         const Pt<D, M> *own, int s0, int b0, int k, int kb, int *__restrict__ core_s,
+                                         unsigned &rech, unsigned long long &evals) {
+    constexpr bool BOX = (M == kF32FromF32 || M == kF32FromF64);
+    const int lane = threadIdx.x & 31;
+    const bool use_box = BOX && P.box;
+    int cnt[NS];
+    unsigned done[NS];
+    Pt<D, M> mine[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        cnt[s] = k;
+        const int left = kb - s * 32;
+        done[s] = left <= 0 ? 0xffffffffu : (left >= 32 ? 0u : ~((1u << left) - 1u));
+        if (use_box && s * 32 + lane < kb) mine[s] = own[s * 32 + lane];
+    }
+    bool all = false;
+    for (int e0 = 0; e0 < ne && !all; e0 += 32) {
+        // one lane per neighbour: fetch its range (and warm its box in L1) at once
+        int h_t0 = 0, h_t1 = 0, h = 0;
+        if (e0 + lane < ne) {
+            h = nl[e0 + lane];
+            h_t0 = cell_start[h];
+            h_t1 = cell_start[h + 1];
+        }
+        const int ecount = min(32, ne - e0);
+        for (int j = 0; j < ecount && !all; ++j) {
+            const int t0 = __shfl_sync(0xffffffffu, h_t0, j), t1 = __shfl_sync(0xffffffffu, h_t1, j);
+            unsigned part[NS];
+            if (use_box) {
+                const int hj = __shfl_sync(0xffffffffu, h, j);
+                const float4 lo = blo[hj], hi = bhi[hj];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    bool partial = false;
+                    if (!((done[s] >> lane) & 1u)) {
+                        if constexpr (BOX) {
+                            if (box_max_d2<D>(mine[s].f, lo, hi) <= P.lo) cnt[s] += t1 - t0;
+                            else partial = box_min_d2<D>(mine[s].f, lo, hi) <= P.hi;
+                        }
+                    }
+                    part[s] = __ballot_sync(0xffffffffu, partial);
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < NS; ++s) part[s] = ~done[s];
+            }
+            unsigned any = 0;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) any |= part[s];
+            for (int tb = t0; tb < t1 && any; tb += 32) {
+                const int t = tb + lane;
+                const bool qv = t < t1;
                 Pt<D, M> q;
-                load_pt(q, pf, pd, t);
-                if (P.stats) ++evals;
-                if (within(p, q, P, pd, i, pd, t, rech) && ++count >= P.min_pts) break;
+                if (qv) load_pt(q, pf, pd, t);
+                any = 0;
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    unsigned todo = part[s];
+                    while (todo) {
+                        const int src = __ffs(todo) - 1;
+                        todo &= todo - 1;
+                        const int i = s * 32 + src;
+                        bool hit = false;
+                        if (qv) {
+                            if (P.stats) ++evals;
+                            hit = within(own[i], q, P, pd, s0 + b0 + i, pd, t, rech);
+                        }
+                        const int got = __popc(__ballot_sync(0xffffffffu, hit));
+                        if (lane == src) cnt[s] += got;
+                    }
+                    part[s] &= ~__ballot_sync(0xffffffffu, cnt[s] >= P.min_pts);
+                    any |= part[s];
+                }
+            }
+            all = true;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                done[s] |= __ballot_sync(0xffffffffu, cnt[s] >= P.min_pts);
+                all = all && done[s] == 0xffffffffu;
             }
         }
-        core_s[i] = count >= P.min_pts ? 1 : 0;
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int i = s * 32 + lane;
+        if (i < kb) core_s[s0 + b0 + i] = cnt[s] >= P.min_pts ? 1 : 0;
+    }
+}
+
+template <int D, int M>
+__global__ void __launch_bounds__(MC_THREADS)
+k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__ pd,
+           const int *__restrict__ cell_start, const int *__restrict__ nbr_cnt, const int *__restrict__ nbr,
+           int stride, const float4 *__restrict__ blo, const float4 *__restrict__ bhi, int *__restrict__ core_s,
+           DevCounters *ctr) {
+    __shared__ Pt<D, M> own[MC_WARPS][MC_OWN];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int m = ctr->m;
+    unsigned rech = 0;
+    unsigned long long evals = 0;
+    for (int c = warp_id_global(); c < m; c += warps_global()) {
+        const int s0 = cell_start[c], k = cell_start[c + 1] - s0;
+        if (k >= P.min_pts) {
+            for (int i = lane; i < k; i += 32) core_s[s0 + i] = 1;
+            continue;
+        }
+        const int ne = nbr_cnt[c];
+        const int *nl = nbr + (int64_t)c * stride;
+        for (int b0 = 0; b0 < k; b0 += MC_OWN) {
+            const int kb = min(MC_OWN, k - b0);
+            __syncwarp();
+            for (int i = lane; i < kb; i += 32) load_pt(own[w][i], pf, pd, s0 + b0 + i);
+            __syncwarp();
+            if (kb <= 32)
+                mc_batch<D, M, 1>(P, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, rech, evals);
+            else if (kb <= 64)
+                mc_batch<D, M, 2>(P, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, rech, evals);
+            else
+                mc_batch<D, M, 4>(P, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, rech, evals);
+        }
     }
     flush_counter(&ctr->band_rechecks, rech);
     if (P.stats) flush_counter(&ctr->dist_evals[0], evals);
 }
 
-#define GBDB_DISPATCH(D, MODE, ...)                                          \
-    do {                                                                      \
-        switch ((D) * 4 + (MODE)) {                                           \
-        case 8: { constexpr int DD = 2, MM = 0; __VA_ARGS__; } break;                \
-        case 9: { constexpr int DD = 2, MM = 1; __VA_ARGS__; } break;                \
-        case 10: { constexpr int DD = 2, MM = 2; __VA_ARGS__; } break;               \
-        case 11: { constexpr int DD = 2, MM = 3; __VA_ARGS__; } break;               \
-        case 12: { constexpr int DD = 3, MM = 0; __VA_ARGS__; } break;               \
-        case 13: { constexpr int DD = 3, MM = 1; __VA_ARGS__; } break;               \
-        case 14: { constexpr int DD = 3, MM = 2; __VA_ARGS__; } break;               \
-        case 15: { constexpr int DD = 3, MM = 3; __VA_ARGS__; } break;               \
-        case 16: { constexpr int DD = 4, MM = 0; __VA_ARGS__; } break;               \
-        case 17: { constexpr int DD = 4, MM = 1; __VA_ARGS__; } break;               \
-        case 18: { constexpr int DD = 4, MM = 2; __VA_ARGS__; } break;               \
-        case 19: { constexpr int DD = 4, MM = 3; __VA_ARGS__; } break;               \
-        default: break;                                                       \
-        }                                                                     \
-    } while (0)
-
 void launch_markcore(int D, int mode, const RunParams &P, const Bufs &B, DevCounters *ctr, cudaStream_t s) {
     GBDB_DISPATCH(D, mode, {
         auto k = k_markcore<DD, MM>;
-        int g = grid_for((const void *)k, 256);
-        k<<<g, 256, 0, s>>>(P, B.pf, B.pd, B.cell_of, B.cell_start, B.nbr_off, B.nbr, B.core_s, ctr); count_launch();
+        int g = grid_for((const void *)k, MC_THREADS);
+        k<<<g, MC_THREADS, 0, s>>>(P, B.pf, B.pd, B.cell_start, B.nbr_cnt, B.nbr, B.nbr_stride, B.blo, B.bhi,
+                                   B.core_s, ctr);
+        count_launch();
     });
 }
 
@@ -108,8 +220,14 @@ k_core_compact(RunParams P, const float *__restrict__ pf, const double *__restri
         core_orig[k] = orig[i];
         core_cell[k] = cell_of[i];
     }
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= m; c += stride)
+    int ncc = 0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= m; c += stride) {
         ccs[c] = c < m ? core_pos[cell_start[c]] : core_pos[P.n];
+        if (c < m && core_pos[cell_start[c + 1]] > core_pos[cell_start[c]]) ++ncc;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ncc += __shfl_xor_sync(0xffffffffu, ncc, o);
+    if ((threadIdx.x & 31) == 0 && ncc) atomicAdd(&ctr->m_core, ncc);
     if (blockIdx.x == 0 && threadIdx.x == 0) ctr->n_core = core_pos[P.n];
 }
 
@@ -118,90 +236,55 @@ void launch_core_compact(int SD, const RunParams &P, const Bufs &B, DevCounters 
     auto go = [&](auto k) {
         int g = grid_for((const void *)k, 256);
         k<<<g, 256, 0, s>>>(P, B.pf, B.pd, B.orig, B.cell_of, B.cell_start, B.core_s, B.core_pos,
-                            B.cpf, B.cpd, B.core_orig, B.core_cell, B.ccs, ctr); count_launch();
+                            B.cpf, B.cpd, B.core_orig, B.core_cell, B.ccs, ctr);
+        count_launch();
     };
     if (SD == 2) go(k_core_compact<2>);
     else if (SD == 4) go(k_core_compact<4>);
     else go(k_core_compact<8>);
+    if (P.box) launch_boxes(SD, B.cpf, B.ccs, ctr, B.cblo, B.cbhi, s);
 }
 
 // ----------------------------------------------------------------- schedule
-// SortBySize (Algorithm 3): core cells in order of non-increasing core count.
-// Each unordered pair of neighbouring core cells is owned by the cell that
-// comes first in that order ("g > h" in Algorithm 3), and the pair list is
-// written owner by owner, so list order is test priority.
+// SortBySize (Algorithm 3): cells in order of non-increasing core count
+// (counts saturate at 65535; ties keep cell order).  rank[c] is the position
+// of cell c; the pair {g, h} of neighbouring core cells is tested by whichever
+// of the two comes first ("g > h" in Algorithm 3).
+constexpr int kSizeKeyBits = 16;
+
 __global__ void __launch_bounds__(256)
-k_size_keys(const int *__restrict__ ccs, int nkey, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
-            const DevCounters *ctr) {
+k_size_keys(const int *__restrict__ ccs, uint64_t *__restrict__ keys, const DevCounters *ctr) {
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
-        keys[c] = (uint64_t)(nkey - (ccs[c + 1] - ccs[c]));
-        vals[c] = (uint32_t)c;
+        const int nc = min(ccs[c + 1] - ccs[c], (1 << kSizeKeyBits) - 1);
+        keys[c] = ((uint64_t)(((1 << kSizeKeyBits) - 1) - nc) << 32) | (uint64_t)c;
     }
 }
 
+// rank[c] = position of cell c in the test order; order[r] = cell at r.
 __global__ void __launch_bounds__(256)
-k_rank(const uint32_t *__restrict__ order, int *__restrict__ rank, const DevCounters *ctr) {
+k_rank(const uint64_t *__restrict__ sorted, uint32_t *__restrict__ order, int *__restrict__ rank,
+       const DevCounters *ctr) {
     const int m = ctr->m;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x)
-        rank[order ? (int)order[r] : r] = r;
-}
-
-template <bool FILL>
-__global__ void __launch_bounds__(256)
-k_pairs(const uint32_t *__restrict__ order, const int *__restrict__ rank, const int *__restrict__ ccs,
-        const long long *__restrict__ nbr_off, const int *__restrict__ nbr, long long *__restrict__ cnt_or_off,
-        int2 *__restrict__ pairs, long long cap, DevCounters *ctr) {
-    const int m = ctr->m;
-    int ncc = 0;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
-        const int a = order ? (int)order[r] : r;
-        long long cnt = 0;
-        const long long base = FILL ? cnt_or_off[r] : 0;
-        if (ccs[a + 1] > ccs[a]) {
-            ++ncc;
-            const long long e1 = nbr_off[a + 1];
-            for (long long e = nbr_off[a]; e < e1; ++e) {
-                const int b = nbr[e];
-                if (ccs[b + 1] > ccs[b] && rank[b] > r) {
-                    if (FILL) {
-                        if (base + cnt < cap) pairs[base + cnt] = make_int2(a, b);
-                        else set_error(ctr, DBSCAN_ERR_CAPACITY, 20);
-                    }
-                    ++cnt;
-                }
-            }
-        }
-        if (!FILL) cnt_or_off[r] = cnt;
-    }
-    if (!FILL) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ncc += __shfl_xor_sync(0xffffffffu, ncc, o);
-        if ((threadIdx.x & 31) == 0 && ncc) atomicAdd(&ctr->m_core, ncc);
+        const int c = sorted ? (int)(sorted[r] & 0xffffffffu) : r;
+        if (sorted) order[r] = (uint32_t)c;
+        rank[c] = r;
     }
 }
 
-__global__ void k_store_P(const long long *off, DevCounters *ctr) { ctr->P = off[ctr->m]; }
-
-void launch_schedule(int sched, const RunParams &P, const Bufs &B, DevCounters *ctr, cudaStream_t s) {
-    const uint32_t *order = nullptr;
-    const int *m_dev = &ctr->m;
+const uint32_t *launch_schedule(int sched, const RunParams &P, const Bufs &B, DevCounters *ctr, cudaStream_t s) {
+    const uint64_t *sorted = nullptr;
     if (sched == DBSCAN_SCHED_SIZE) {
-        int bits = 1;
-        while ((1ll << bits) <= (long long)P.n) ++bits;
-        const int nkey = (int)((1ll << bits) - 1);
         int g = grid_for((const void *)k_size_keys, 256);
-        k_size_keys<<<g, 256, 0, s>>>(B.ccs, nkey, B.sk0, B.sv0, ctr); count_launch();
-        int which = radix_sort_u64(B.sk0, B.sv0, B.sk1, B.sv1, 0, m_dev, B.n_max, bits, B.hist, B.part, s);
-        order = which ? B.sv1 : B.sv0;
+        k_size_keys<<<g, 256, 0, s>>>(B.ccs, B.sk0, ctr); count_launch();
+        int which = radix_sort_u64(B.sk0, nullptr, B.sk1, nullptr, 0, &ctr->m, B.n_max, 32, kSizeKeyBits,
+                                   B.sort_scratch, ctr, P.max_iters, s);
+        sorted = which ? B.sk1 : B.sk0;
     }
     int g = grid_for((const void *)k_rank, 256);
-    k_rank<<<g, 256, 0, s>>>(order, B.rank, ctr); count_launch();
-    g = grid_for((const void *)k_pairs<false>, 256);
-    k_pairs<false><<<g, 256, 0, s>>>(order, B.rank, B.ccs, B.nbr_off, B.nbr, B.pcnt, nullptr, 0, ctr); count_launch();
-    scan_i64_to_i64(B.pcnt, B.poff, 0, m_dev, B.n_max, B.part, s);
-    k_store_P<<<1, 1, 0, s>>>(B.poff, ctr); count_launch();
-    k_pairs<true><<<g, 256, 0, s>>>(order, B.rank, B.ccs, B.nbr_off, B.nbr, B.poff, B.pairs, B.pair_cap, ctr); count_launch();
+    k_rank<<<g, 256, 0, s>>>(sorted, B.sv0, B.rank, ctr); count_launch();
+    return sorted ? B.sv0 : nullptr;
 }
 
 // ----------------------------------------------------------------- connect
@@ -256,51 +339,116 @@ __device__ __forceinline__ bool bcp_warp(int r0, int nr, int c0, int nc, const f
     return false;
 }
 
-// ClusterCore's pair loop (Algorithm 3): a warp takes the next 32 pairs of
-// the priority-ordered list with one atomic, checks all 32 against the
-// union-find in parallel (one pair per lane), and runs BCP on the survivors
-// one at a time, re-checking each just before its test because earlier links
-// may have joined it meanwhile ("Reducing Cell Connectivity Queries").  A hit
-// links the two cells.
-template <int D, int M>
-__global__ void __launch_bounds__(256)
-k_connect(RunParams P, const int2 *__restrict__ pairs, const int *__restrict__ ccs,
-          const float *__restrict__ cpf, const double *__restrict__ cpd, int *parent, DevCounters *ctr) {
+// ClusterCore's pair loop (Algorithm 3).  A warp takes the next CN_CELLS core
+// cells in SortBySize order with one atomic; each cell owns its pairs with
+// neighbouring core cells that come later in that order.  The warp flattens
+// those pairs over its lanes (one (g, h) pair per lane, whatever cell it
+// belongs to), so the loads of 32 pairs are in flight together; each lane
+// checks its pair against the two cells' core-point boxes and the union-find;
+// the survivors get a BCP test one at a time, each re-checked just before its
+// test because a link made meanwhile may already join the two ("Reducing Cell
+// Connectivity Queries").  A hit links the two cells.
+constexpr int CN_CELLS = 4;  // cells per work item: ~4x13 near pairs fill two lane rounds
+
+template <int D, int M, int WAVE>
+__global__ void __launch_bounds__(256, 2)
+k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict__ rank,
+          const int *__restrict__ ccs, const int *__restrict__ nbr_cnt, const int *__restrict__ nbr_near,
+          const int *__restrict__ nbr, int stride, const float *__restrict__ cpf, const double *__restrict__ cpd,
+          const float4 *__restrict__ cblo, const float4 *__restrict__ cbhi, int *parent, DevCounters *ctr) {
+    constexpr bool BOX = (M == kF32FromF32 || M == kF32FromF64);
     const int lane = threadIdx.x & 31;
-    const unsigned long long np = (unsigned long long)ctr->P;
+    const int m = ctr->m;
+    const bool use_box = BOX && P.box;
+    int *next = WAVE == 0 ? &ctr->cell_next : &ctr->cell_next2;
     unsigned rech = 0;
-    unsigned long long evals = 0, tested = 0, skipped = 0, linked = 0;
+    unsigned long long evals = 0, tested = 0, skipped = 0, linked = 0, cand_pairs = 0, boxed = 0;
     for (;;) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&ctr->pair_next, 32ull);
+        int base = 0;
+        if (lane == 0) base = atomicAdd(next, CN_CELLS);
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= np) break;
-        const unsigned long long idx = base + lane;
-        const bool valid = idx < np;
-        int2 pr = make_int2(0, 0);
-        bool same = true;
-        if (valid) {
-            pr = pairs[idx];
-            same = uf_find(parent, pr.x, P.max_iters, ctr) == uf_find(parent, pr.y, P.max_iters, ctr);
+        if (base >= m) break;
+        // lane l < CN_CELLS: the cell at rank base + l and the range of its pair list
+        int ca = 0, ca0 = 0, cna = 0, cbeg = 0, ccnt = 0;
+        if (lane < CN_CELLS && base + lane < m) {
+            ca = order ? (int)order[base + lane] : base + lane;
+            ca0 = ccs[ca];
+            cna = ccs[ca + 1] - ca0;
+            if (cna > 0) {
+                const int near = nbr_near[ca];
+                cbeg = WAVE == 0 ? 0 : near;
+                ccnt = (WAVE == 0 ? near : nbr_cnt[ca]) - cbeg;
+            }
         }
-        unsigned todo = __ballot_sync(0xffffffffu, !same);
-        skipped += __popc(__ballot_sync(0xffffffffu, valid && same));
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int a = __shfl_sync(0xffffffffu, pr.x, src);
-            const int b = __shfl_sync(0xffffffffu, pr.y, src);
-            int again = 0;
-            if (lane == 0) again = uf_find(parent, a, P.max_iters, ctr) == uf_find(parent, b, P.max_iters, ctr);
-            if (__shfl_sync(0xffffffffu, again, 0)) { ++skipped; continue; }
-            ++tested;
-            const int a0 = ccs[a], na = ccs[a + 1] - a0;
-            const int b0 = ccs[b], nb = ccs[b + 1] - b0;
-            const bool hit = na >= nb ? bcp_warp<D, M>(a0, na, b0, nb, cpf, cpd, P, rech, evals)
-                                      : bcp_warp<D, M>(b0, nb, a0, na, cpf, cpd, P, rech, evals);
-            if (hit) {
-                ++linked;
-                if (lane == 0) uf_link(parent, a, b, P.max_iters, ctr);
+        int incl = ccnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        const int cexcl = incl - ccnt;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int f0 = 0; f0 < total; f0 += 32) {
+            const int f = f0 + lane;
+            // owner lane: the last lane whose range starts at or before f
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int ex = __shfl_sync(0xffffffffu, cexcl, (j + step) & 31);
+                if (j + step < 32 && ex <= f) j += step;
+            }
+            const int a = __shfl_sync(0xffffffffu, ca, j);
+            const int a0 = __shfl_sync(0xffffffffu, ca0, j);
+            const int na = __shfl_sync(0xffffffffu, cna, j);
+            const int e = __shfl_sync(0xffffffffu, cbeg, j) + f - __shfl_sync(0xffffffffu, cexcl, j);
+            const int r = base + j;
+            int b = 0, b0 = 0, nb = 0;
+            bool cand = false;
+            if (f < total) {
+                b = nbr[(int64_t)a * stride + e];
+                b0 = ccs[b];
+                nb = ccs[b + 1] - b0;
+                cand = nb > 0 && rank[b] > r;
+            }
+            // bounding boxes of the two cells' core points: every pair beyond
+            // eps -> not connected; every pair within eps -> connected
+            int verdict = 0;
+            if (use_box && cand) {
+                const float4 alo = cblo[a], ahi = cbhi[a], blo = cblo[b], bhi = cbhi[b];
+                if (boxes_min_d2<D>(alo, ahi, blo, bhi) > P.hi) verdict = -1;
+                else if (boxes_max_d2<D>(alo, ahi, blo, bhi) <= P.lo) verdict = 1;
+            }
+            // union-find check: in the near wave only the current parents are
+            // compared (trees are being built); the far wave runs after every
+            // path was compressed, so its finds are short
+            bool same = true;
+            if (cand && verdict >= 0) {
+                if (WAVE == 0) same = uf_load(parent + a) == uf_load(parent + b);
+                else same = uf_find(parent, a, P.max_iters, ctr) == uf_find(parent, b, P.max_iters, ctr);
+            }
+            if (cand && verdict > 0 && !same) uf_link(parent, a, b, P.max_iters, ctr);
+            cand_pairs += __popc(__ballot_sync(0xffffffffu, cand));
+            boxed += __popc(__ballot_sync(0xffffffffu, cand && (verdict < 0 || (verdict > 0 && !same))));
+            linked += __popc(__ballot_sync(0xffffffffu, cand && verdict > 0 && !same));
+            skipped += __popc(__ballot_sync(0xffffffffu, cand && verdict >= 0 && same));
+            unsigned todo = __ballot_sync(0xffffffffu, cand && verdict == 0 && !same);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int sa = __shfl_sync(0xffffffffu, a, src), sa0 = __shfl_sync(0xffffffffu, a0, src);
+                const int sna = __shfl_sync(0xffffffffu, na, src);
+                const int sb = __shfl_sync(0xffffffffu, b, src), sb0 = __shfl_sync(0xffffffffu, b0, src);
+                const int snb = __shfl_sync(0xffffffffu, nb, src);
+                int again = 0;
+                if (lane == 0) again = uf_find(parent, sa, P.max_iters, ctr) == uf_find(parent, sb, P.max_iters, ctr);
+                if (__shfl_sync(0xffffffffu, again, 0)) { ++skipped; continue; }
+                ++tested;
+                const bool hit = sna >= snb ? bcp_warp<D, M>(sa0, sna, sb0, snb, cpf, cpd, P, rech, evals)
+                                            : bcp_warp<D, M>(sb0, snb, sa0, sna, cpf, cpd, P, rech, evals);
+                if (hit) {
+                    ++linked;
+                    if (lane == 0) uf_link(parent, sa, sb, P.max_iters, ctr);
+                }
             }
         }
     }
@@ -308,9 +456,18 @@ k_connect(RunParams P, const int2 *__restrict__ pairs, const int *__restrict__ c
         if (tested) atomicAdd(&ctr->pairs_tested, tested);
         if (skipped) atomicAdd(&ctr->pairs_skipped, skipped);
         if (linked) atomicAdd(&ctr->pairs_linked, linked);
+        if (boxed) atomicAdd(&ctr->pairs_box, boxed);
+        if (cand_pairs) atomicAdd((unsigned long long *)&ctr->P, cand_pairs);
     }
     flush_counter(&ctr->band_rechecks, rech);
     if (P.stats) flush_counter(&ctr->dist_evals[1], evals);
+}
+
+// Full path compression between the two waves.
+__global__ void __launch_bounds__(256) k_uf_compress(int *parent, DevCounters *ctr, int max_iters) {
+    const int m = ctr->m;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x)
+        parent[c] = uf_find(parent, c, max_iters, ctr);
 }
 
 __global__ void __launch_bounds__(256) k_uf_init(int *parent, const DevCounters *ctr) {
@@ -318,19 +475,33 @@ __global__ void __launch_bounds__(256) k_uf_init(int *parent, const DevCounters 
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) parent[c] = c;
 }
 
-void launch_connect(int D, int mode, const RunParams &P, const Bufs &B, DevCounters *ctr, cudaStream_t s) {
+// Two waves over the priority order (the batches of "bucketing", Sec. 4.4):
+// first every core cell's pairs with the adjacent cells (|delta|_inf <= 1),
+// which are the likeliest to connect, then, after full path compression, the
+// pairs with the farther cells, most of which union-find then skips.
+void launch_connect(int D, int mode, const uint32_t *order, const RunParams &P, const Bufs &B, DevCounters *ctr,
+                    cudaStream_t s) {
     int g = grid_for((const void *)k_uf_init, 256);
     k_uf_init<<<g, 256, 0, s>>>(B.parent, ctr); count_launch();
     GBDB_DISPATCH(D, mode, {
-        auto k = k_connect<DD, MM>;
-        int gg = grid_for((const void *)k, 256);
-        k<<<gg, 256, 0, s>>>(P, B.pairs, B.ccs, B.cpf, B.cpd, B.parent, ctr); count_launch();
+        auto k0 = k_connect<DD, MM, 0>;
+        int gg = grid_for((const void *)k0, 256);
+        k0<<<gg, 256, 0, s>>>(P, order, B.rank, B.ccs, B.nbr_cnt, B.nbr_near, B.nbr, B.nbr_stride, B.cpf, B.cpd,
+                              B.cblo, B.cbhi, B.parent, ctr);
+        count_launch();
+        int gc = grid_for((const void *)k_uf_compress, 256);
+        k_uf_compress<<<gc, 256, 0, s>>>(B.parent, ctr, P.max_iters); count_launch();
+        auto k1 = k_connect<DD, MM, 1>;
+        k1<<<gg, 256, 0, s>>>(P, order, B.rank, B.ccs, B.nbr_cnt, B.nbr_near, B.nbr, B.nbr_stride, B.cpf, B.cpd,
+                              B.cblo, B.cbhi, B.parent, ctr);
+        count_launch();
     });
 }
 
 // ----------------------------------------------------------------- labels
 // clusters[p] := Find(g) for core p (Algorithm 3), renamed to the smallest
-// input index of a core point in the component.
+// input index of a core point in the component.  The same pass lists the
+// non-core points for ClusterBorder.
 __global__ void __launch_bounds__(256) k_uf_flatten(int *parent, int *compmin, DevCounters *ctr, int max_iters) {
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
@@ -355,12 +526,29 @@ k_comp_min(const int *__restrict__ ccs, const int *__restrict__ core_orig, const
 __global__ void __launch_bounds__(256)
 k_label_core(RunParams P, const int *__restrict__ core_s, const int *__restrict__ orig,
              const int *__restrict__ cell_of, const int *__restrict__ parent, const int *__restrict__ compmin,
-             uint8_t *__restrict__ core_out, int32_t *__restrict__ labels_out) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-        const int o = orig[i];
-        const int cf = core_s[i];
-        core_out[o] = (uint8_t)cf;
-        if (cf) labels_out[o] = compmin[parent[cell_of[i]]];
+             uint8_t *__restrict__ core_out, int32_t *__restrict__ labels_out, int *__restrict__ noncore,
+             DevCounters *ctr) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    // trip count rounded up to whole warps so the ballot below is warp-uniform
+    const int stride = gridDim.x * blockDim.x;
+    const int nr = (P.n + 31) & ~31;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += stride) {
+        bool nc = false;
+        if (i < P.n) {
+            const int o = orig[i];
+            const int cf = core_s[i];
+            core_out[o] = (uint8_t)cf;
+            if (cf) labels_out[o] = compmin[parent[cell_of[i]]];
+            nc = !cf;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, nc);
+        if (bal) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&ctr->n_noncore, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (nc) noncore[base + __popc(bal & lt)] = i;
+        }
     }
 }
 
@@ -371,79 +559,103 @@ void launch_labels(const RunParams &P, const Bufs &B, uint8_t *core_out, int32_t
     g = grid_for((const void *)k_comp_min, 256);
     k_comp_min<<<g, 256, 0, s>>>(B.ccs, B.core_orig, B.parent, B.compmin, ctr); count_launch();
     g = grid_for((const void *)k_label_core, 256);
-    k_label_core<<<g, 256, 0, s>>>(P, B.core_s, B.orig, B.cell_of, B.parent, B.compmin, core_out, labels_out); count_launch();
+    // border counts start at zero (core points keep it); ClusterBorder writes the others
+    cudaMemsetAsync(B.bcount, 0, sizeof(long long) * (size_t)P.n, s);
+    k_label_core<<<g, 256, 0, s>>>(P, B.core_s, B.orig, B.cell_of, B.parent, B.compmin, core_out, labels_out,
+                                   B.noncore, ctr);
+    count_launch();
 }
 
 // ----------------------------------------------------------------- border
 // ClusterBorder (Algorithm 4): a non-core point p of cell g joins the cluster
 // of every cell h in {g} and NeighborCells(g) that has a core point within eps
-// of p.  The scan of h stops at its first hit, and h is not scanned at all when
-// its cluster is already in p's set.  The set stays sorted in a local array:
-// the core points of distinct clusters seen by p are pairwise farther than eps
-// apart and all within eps of p, so there are at most kissing-number many of
-// them (240 in R^8), under kBorderSetCap.
+// of p.  One warp per non-core point; the core points of h are tested 32 at a
+// time and h's scan stops at its first hit; h is skipped when its cluster is
+// already in p's set.  The set is kept sorted in shared memory.  The core
+// points of distinct clusters seen by p are pairwise farther than eps apart
+// and all within eps of p, so there are at most kissing-number many of them
+// (240 in R^8), under kBorderSetCap.
+constexpr int BD_THREADS = 256, BD_WARPS = BD_THREADS / 32;
+
 template <int D, int M, bool FILL>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(BD_THREADS)
 k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restrict__ ids,
          long long ids_cap, DevCounters *ctr) {
+    __shared__ int sset[BD_WARPS][kBorderSetCap];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nn = ctr->n_noncore;
     unsigned rech = 0;
     unsigned long long evals = 0, nborder = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-        const int o = B.orig[i];
-        if (B.core_s[i]) {
-            if (!FILL) B.bcount[o] = 0;
-            continue;
-        }
+    for (int t = warp_id_global(); t < nn; t += warps_global()) {
+        const int i = B.noncore[t];
         const int g = B.cell_of[i];
+        const int o = B.orig[i];
         Pt<D, M> p;
         load_pt(p, B.pf, B.pd, i);
-        int set[kBorderSetCap];
         int ns = 0;
-        const long long e0 = B.nbr_off[g], e1 = B.nbr_off[g + 1];
-        for (long long e = e0 - 1; e < e1; ++e) {
-            const int h = e < e0 ? g : B.nbr[e];
+        const int ne = B.nbr_cnt[g];
+        const int *nl = B.nbr + (int64_t)g * B.nbr_stride;
+        for (int e = -1; e < ne; ++e) {
+            const int h = e < 0 ? g : nl[e];
             const int k0 = B.ccs[h], k1 = B.ccs[h + 1];
             if (k0 == k1) continue;
             const int L = B.compmin[B.parent[h]];
             bool have = false;
-            for (int t = 0; t < ns; ++t) have = have || set[t] == L;
-            if (have) continue;
-            for (int k = k0; k < k1; ++k) {
-                Pt<D, M> q;
-                load_pt(q, B.cpf, B.cpd, k);
-                if (P.stats) ++evals;
-                if (within(p, q, P, B.pd, i, B.cpd, k, rech)) {
-                    if (ns < kBorderSetCap) {
-                        int t = ns++;
-                        while (t > 0 && set[t - 1] > L) { set[t] = set[t - 1]; --t; }
-                        set[t] = L;
-                    } else {
-                        set_error(ctr, DBSCAN_ERR_CAPACITY, 30);
-                    }
-                    break;
+            for (int u = lane; u < ns; u += 32) have = have || sset[w][u] == L;
+            if (__any_sync(0xffffffffu, have)) continue;
+            bool found = false;
+            if constexpr (M == kF32FromF32 || M == kF32FromF64) {
+                if (P.box) {
+                    const float4 lo = B.cblo[h], hi = B.cbhi[h];
+                    if (box_min_d2<D>(p.f, lo, hi) > P.hi) continue;  // no core point of h within eps
+                    found = box_max_d2<D>(p.f, lo, hi) <= P.lo;      // every core point of h within eps
                 }
+            }
+            for (int kb = k0; kb < k1 && !found; kb += 32) {
+                const int k = kb + lane;
+                bool hit = false;
+                if (k < k1) {
+                    Pt<D, M> q;
+                    load_pt(q, B.cpf, B.cpd, k);
+                    if (P.stats) ++evals;
+                    hit = within(p, q, P, B.pd, i, B.cpd, k, rech);
+                }
+                found = __any_sync(0xffffffffu, hit);
+            }
+            if (found) {
+                if (ns < kBorderSetCap) {
+                    if (lane == 0) {
+                        int u = ns;
+                        while (u > 0 && sset[w][u - 1] > L) { sset[w][u] = sset[w][u - 1]; --u; }
+                        sset[w][u] = L;
+                    }
+                    ++ns;
+                } else if (lane == 0) {
+                    set_error(ctr, DBSCAN_ERR_CAPACITY, 30);
+                }
+                __syncwarp();
             }
         }
         if (!FILL) {
-            B.bcount[o] = ns;
-            labels_out[o] = ns ? set[0] : -1;
+            if (lane == 0) {
+                B.bcount[o] = ns;
+                labels_out[o] = ns ? sset[w][0] : -1;
+            }
             nborder += ns ? 1 : 0;
         } else {
             const long long at = B.boff[o];
             if (at + ns <= ids_cap) {
-                for (int t = 0; t < ns; ++t) ids[at + t] = set[t];
-            } else {
+                for (int u = lane; u < ns; u += 32) ids[at + u] = sset[w][u];
+            } else if (lane == 0) {
                 set_error(ctr, DBSCAN_ERR_CAPACITY, 31);
             }
         }
+        __syncwarp();
     }
     if (!FILL) {
         flush_counter(&ctr->band_rechecks, rech);
         if (P.stats) flush_counter(&ctr->dist_evals[2], evals);
-        unsigned long long nb = nborder;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) nb += __shfl_xor_sync(0xffffffffu, nb, o);
-        if ((threadIdx.x & 31) == 0 && nb) atomicAdd((unsigned *)&ctr->n_border, (unsigned)nb);
+        if (lane == 0 && nborder) atomicAdd((unsigned *)&ctr->n_border, (unsigned)nborder);
     }
 }
 
@@ -454,16 +666,18 @@ void launch_border(int D, int mode, bool fill, const RunParams &P, const Bufs &B
     if (!fill) {
         GBDB_DISPATCH(D, mode, {
             auto k = k_border<DD, MM, false>;
-            int g = grid_for((const void *)k, 128);
-            k<<<g, 128, 0, s>>>(P, B, labels_out, nullptr, 0, ctr); count_launch();
+            int g = grid_for((const void *)k, BD_THREADS);
+            k<<<g, BD_THREADS, 0, s>>>(P, B, labels_out, nullptr, 0, ctr);
+            count_launch();
         });
         scan_i64_to_i64(B.bcount, B.boff, P.n, nullptr, P.n, B.part, s);
         k_store_K<<<1, 1, 0, s>>>(B.boff, P.n, ctr); count_launch();
     } else {
         GBDB_DISPATCH(D, mode, {
             auto k = k_border<DD, MM, true>;
-            int g = grid_for((const void *)k, 128);
-            k<<<g, 128, 0, s>>>(P, B, labels_out, ids, ids_cap, ctr); count_launch();
+            int g = grid_for((const void *)k, BD_THREADS);
+            k<<<g, BD_THREADS, 0, s>>>(P, B, labels_out, ids, ids_cap, ctr);
+            count_launch();
         });
     }
 }

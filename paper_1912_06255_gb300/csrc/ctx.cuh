@@ -26,40 +26,38 @@ struct dbscan_ctx {
     int collect_stats = 0;
     int max_iters = 1 << 22;
     int phase_timing = 0;
+    int cell_bounds = 1;
     cudaEvent_t ev[9] = {};
     // workspace
     void *arena = nullptr;
     size_t arena_bytes = 0;
     uint64_t *k0 = nullptr, *k1 = nullptr;
     uint32_t *v0 = nullptr, *v1 = nullptr;
-    unsigned *hist = nullptr;
+    void *sort_scratch = nullptr;
     long long *part = nullptr;
     int *flags = nullptr, *cid = nullptr;
     float *pf = nullptr, *cpf = nullptr;
     double *pd = nullptr, *cpd = nullptr;
     int *orig = nullptr, *cell_of = nullptr, *cell_start = nullptr;
     uint64_t *cell_key = nullptr;
-    uint64_t *hk = nullptr;
-    int *hv = nullptr;
-    long long *nbr_cnt = nullptr, *nbr_off = nullptr;
+    ulonglong2 *ht = nullptr;  // cell hash: 16-byte slots {key, cell id}
+    int *nbr_cnt = nullptr;  // neighbours per cell; ids at nbr[c * noff(d)]
+    int *nbr_near = nullptr; // of which adjacent (|delta|_inf <= 1), listed first
     int *nbr = nullptr;
     long long nbr_cap = 0;
     int *core_s = nullptr, *core_pos = nullptr, *ccs = nullptr, *core_orig = nullptr, *core_cell = nullptr;
     int *rank = nullptr;
-    long long *pcnt = nullptr, *poff = nullptr;
-    int2 *pairs = nullptr;
-    long long pair_cap = 0;
+    float4 *blo = nullptr, *bhi = nullptr, *cblo = nullptr, *cbhi = nullptr;  // cell / core-point boxes
     int *parent = nullptr, *compmin = nullptr;
+    int *noncore = nullptr;
     long long *bcount = nullptr, *boff = nullptr;
-    double *bbox_part = nullptr;
-    int *bbox_bad = nullptr;
-    double *bbox_out = nullptr;
+    long long *bbox_out = nullptr;  // [2*kMaxDim + 1], see launch_bbox
     signed char *offs = nullptr;  // [kMaxEnumDim][kMaxOffsets][kMaxEnumDim]
     int noff[gbdb::kMaxEnumDim + 1] = {0};
     gbdb::DevCounters *ctr = nullptr;
     // pinned host
     gbdb::DevCounters *h_ctr = nullptr;
-    double *h_bbox = nullptr;
+    long long *h_bbox = nullptr;
     // host-buffer entry point
     void *d_in = nullptr;
     size_t d_in_bytes = 0;

@@ -71,13 +71,11 @@ template <int D> __device__ __forceinline__ float d2f(const float (&a)[D], const
     return s;
 }
 
-// A point held in registers: FP32 coordinates, or FP64 in the FP64-storage
-// FP64-predicate mode.
-template <int D, int M> struct Pt {
-    static constexpr bool kDouble = (M == kF64FromF64);
-    float f[kDouble ? 1 : D];
-    double x[kDouble ? D : 1];
-};
+// A point held in registers or shared memory: FP32 coordinates, or FP64 in
+// the FP64-storage FP64-predicate mode.
+template <int D, int M, bool DBL = (M == kF64FromF64)> struct Pt;
+template <int D, int M> struct alignas(D >= 3 ? 16 : 8) Pt<D, M, false> { float f[D]; };
+template <int D, int M> struct alignas(16) Pt<D, M, true> { double x[D]; };
 
 template <int D, int M>
 __device__ __forceinline__ void load_pt(Pt<D, M> &p, const float *__restrict__ pf,
@@ -116,6 +114,65 @@ __device__ __forceinline__ bool within(const Pt<D, M> &p, const Pt<D, M> &q, con
         }
         return pred64<D>(a, b, P.eps2);
     }
+}
+
+// ------------------------------------------------------------ box bounds
+// Cell-level pruning (a one-level form of the range counting of Sec. 5.2): for
+// an axis-aligned box [lo, hi] that contains every point of a cell, bounds of
+// the squared distance from a point (or another box) to all of those points.
+// Each coordinate term is one FP32 subtraction of exact FP32 values (the max
+// and the clamp at 0 are exact), squared and summed like d2f, so the value
+// carries the same forward-error bound as d2f and the FP32 band applies:
+// max_d2 <= lo means every pair passes the FP64 predicate, min_d2 > hi that
+// none does.
+template <int D> __device__ __forceinline__ float cget(const float4 &v, int j) {
+    return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+}
+
+template <int D>
+__device__ __forceinline__ float box_max_d2(const float (&p)[D], const float4 &lo, const float4 &hi) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const float a = fmaxf(p[j] - cget<D>(lo, j), cget<D>(hi, j) - p[j]);
+        s = j == 0 ? a * a : __fmaf_rn(a, a, s);
+    }
+    return s;
+}
+
+template <int D>
+__device__ __forceinline__ float box_min_d2(const float (&p)[D], const float4 &lo, const float4 &hi) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const float a = fmaxf(fmaxf(cget<D>(lo, j) - p[j], p[j] - cget<D>(hi, j)), 0.f);
+        s = j == 0 ? a * a : __fmaf_rn(a, a, s);
+    }
+    return s;
+}
+
+template <int D>
+__device__ __forceinline__ float boxes_min_d2(const float4 &alo, const float4 &ahi, const float4 &blo,
+                                              const float4 &bhi) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const float a = fmaxf(fmaxf(cget<D>(blo, j) - cget<D>(ahi, j), cget<D>(alo, j) - cget<D>(bhi, j)), 0.f);
+        s = j == 0 ? a * a : __fmaf_rn(a, a, s);
+    }
+    return s;
+}
+
+template <int D>
+__device__ __forceinline__ float boxes_max_d2(const float4 &alo, const float4 &ahi, const float4 &blo,
+                                              const float4 &bhi) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const float a = fmaxf(cget<D>(bhi, j) - cget<D>(alo, j), cget<D>(ahi, j) - cget<D>(blo, j));
+        s = j == 0 ? a * a : __fmaf_rn(a, a, s);
+    }
+    return s;
 }
 
 // ------------------------------------------------------------ Morton keys
@@ -192,24 +249,48 @@ __host__ __device__ __forceinline__ uint64_t hash_capacity(int m) {
     while (c < 2ull * (uint64_t)m) c <<= 1;
     return c;
 }
-__device__ __forceinline__ uint32_t hash_slot(uint64_t k) {
-    k ^= k >> 33;
-    k *= 0xff51afd7ed558ccdull;
-    k ^= k >> 33;
-    k *= 0xc4ceb9fe1a85ec53ull;
-    k ^= k >> 33;
-    return (uint32_t)k;
+__host__ __device__ __forceinline__ int hash_log2(uint64_t cap) {
+    int l = 0;
+    while ((1ull << l) < cap) ++l;
+    return l;
 }
-__device__ __forceinline__ int hash_find(const uint64_t *__restrict__ hk, const int *__restrict__ hv,
-                                         uint64_t key, uint64_t mask) {
-    uint64_t s = hash_slot(key) & mask;
+// Multiplicative (Fibonacci) hashing: the top lg bits of key * 2^64/phi.
+__device__ __forceinline__ uint64_t hash_slot(uint64_t k, int lg) {
+    return (k * 0x9e3779b97f4a7c15ull) >> (64 - lg);
+}
+
+// A slot is 16 bytes: .x the key (kEmptyKey when free), .y the cell id, so a
+// probe is one load.
+__device__ __forceinline__ int hash_find(const ulonglong2 *__restrict__ ht, uint64_t key, uint64_t mask, int lg) {
+    uint64_t s = hash_slot(key, lg);
     for (uint64_t it = 0; it <= mask; ++it) {
-        uint64_t k = hk[s];
-        if (k == key) return hv[s];
-        if (k == kEmptyKey) return -1;
+        const ulonglong2 e = ht[s];
+        if (e.x == key) return (int)e.y;
+        if (e.x == kEmptyKey) return -1;
         s = (s + 1) & mask;
     }
     return -1;
+}
+
+// Morton key of the cell at c + delta from the key of c (D = 2 or 3), by
+// dilated-integer addition: per dimension, the key's bits of that dimension
+// with the other bits set to one (for +) or zero (for -) absorb the carries
+// or borrows.  |delta_j| <= 3 and c + delta stays inside the grid.
+template <int D>
+__device__ __forceinline__ uint64_t morton_offset(uint64_t key, const int (&delta)[D]) {
+    uint64_t out = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const uint64_t M = (D == 3 ? 0x1249249249249249ull : 0x5555555555555555ull) << j;
+        uint64_t part = key & M;
+        const int dj = delta[j];
+        const int a = dj < 0 ? -dj : dj;
+        const uint64_t v = (uint64_t)((a & 1) | ((a & 2) << (D - 1))) << j;
+        if (dj > 0) part = ((part | ~M) + v) & M;
+        else if (dj < 0) part = (part - v) & M;
+        out |= part;
+    }
+    return out;
 }
 
 // ------------------------------------------------------------ union-find

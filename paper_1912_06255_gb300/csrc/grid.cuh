@@ -6,17 +6,27 @@
 namespace gbdb {
 
 // ---- cells (grid.cu)
-void launch_bbox(const void *X, int dtype, int n, int d, double *part, int nb, int *bad,
-                 double *out, cudaStream_t s);
+// out: [2*kMaxDim + 1] int64: order-preserving keys of the per-dimension
+// minima and maxima (see bbox_key_to_double) and a non-finite flag.
+void launch_bbox(const void *X, int dtype, int n, int d, int nb, long long *out, cudaStream_t s);
+inline double bbox_key_to_double(long long k) {
+    const long long b = k >= 0 ? k : (k ^ 0x7fffffffffffffffll);
+    double x;
+    __builtin_memcpy(&x, &b, sizeof x);
+    return x;
+}
 void launch_keys(const void *X, int dtype, const RunParams &P, uint64_t *keys, uint32_t *vals,
                  cudaStream_t s);
-void launch_cells(const void *X, int dtype, int n, int d, int SD, const uint64_t *K, const uint32_t *V,
+void launch_cells(const void *X, int dtype, int n, int d, int SD, int ib, const uint64_t *K, const uint32_t *V,
                   int *flags, int *cid, long long *part, float *pf, double *pd, int *orig,
                   int *cell_of, int *cell_start, uint64_t *cell_key, DevCounters *ctr, cudaStream_t s);
-void launch_hash(uint64_t *hk, int *hv, const uint64_t *cell_key, DevCounters *ctr, cudaStream_t s);
-void launch_neighbors(const uint64_t *cell_key, const uint64_t *hk, const int *hv, const RunParams &P,
-                      const signed char *offs, int noff, long long *cnt, long long *off, int *nbr, long long nbr_cap,
-                      long long *part, int64_t n_max, DevCounters *ctr, cudaStream_t s);
+void launch_hash(ulonglong2 *ht, const uint64_t *cell_key, DevCounters *ctr, cudaStream_t s);
+void launch_neighbors(const uint64_t *cell_key, const ulonglong2 *ht, const RunParams &P,
+                      const signed char *offs, int noff, int n_near, const float4 *blo, const float4 *bhi,
+                      int *nbr_cnt, int *nbr_near, int *nbr, DevCounters *ctr, cudaStream_t s);
+// per-cell FP32 bounding boxes of pts[start[c] .. start[c+1])
+void launch_boxes(int SD, const float *pts, const int *start, const DevCounters *ctr, float4 *lo, float4 *hi,
+                  cudaStream_t s);
 
 // Device arrays of one run, shared by the cluster phases.
 struct Bufs {
@@ -24,8 +34,10 @@ struct Bufs {
     const float *pf;
     const double *pd;  // null unless FP64 input
     const int *orig, *cell_of, *cell_start;
-    const long long *nbr_off;
+    const int *nbr_cnt;  // [m] neighbours of cell c: nbr[c*nbr_stride .. + nbr_cnt[c])
+    const int *nbr_near; // [m] how many of them are at |delta|_inf <= 1 (listed first)
     const int *nbr;
+    int nbr_stride;
     // MarkCore / compaction
     int *core_s;        // [n] 0/1 in cell order
     int *core_pos;      // [n+1] exclusive scan of core_s
@@ -34,17 +46,18 @@ struct Bufs {
     double *cpd;
     int *core_orig;     // input index of compacted core point
     int *core_cell;     // cell of compacted core point
+    const float4 *blo, *bhi;  // per-cell bounding box of all points
+    float4 *cblo, *cbhi;      // per-cell bounding box of the core points
     // schedule
     uint64_t *sk0, *sk1;
     uint32_t *sv0, *sv1;
-    unsigned *hist;
+    void *sort_scratch;
+    int max_iters;
     int *rank;          // [m] position of the cell in test order
-    long long *pcnt, *poff;
-    int2 *pairs;
-    long long pair_cap;
     // union-find and labels
     int *parent, *compmin, *cell_label;
     // border
+    int *noncore;       // [n_noncore] cell-order indices of the non-core points
     long long *bcount, *boff;
     long long *part;
     int64_t n_max;
@@ -53,8 +66,10 @@ struct Bufs {
 // ---- clusters (cluster.cu)
 void launch_markcore(int D, int mode, const RunParams &P, const Bufs &B, DevCounters *ctr, cudaStream_t s);
 void launch_core_compact(int SD, const RunParams &P, const Bufs &B, DevCounters *ctr, cudaStream_t s);
-void launch_schedule(int sched, const RunParams &P, const Bufs &B, DevCounters *ctr, cudaStream_t s);
-void launch_connect(int D, int mode, const RunParams &P, const Bufs &B, DevCounters *ctr, cudaStream_t s);
+// returns the test order of the cells (null: cell order)
+const uint32_t *launch_schedule(int sched, const RunParams &P, const Bufs &B, DevCounters *ctr, cudaStream_t s);
+void launch_connect(int D, int mode, const uint32_t *order, const RunParams &P, const Bufs &B, DevCounters *ctr,
+                    cudaStream_t s);
 void launch_labels(const RunParams &P, const Bufs &B, uint8_t *core_out, int32_t *labels_out,
                    DevCounters *ctr, cudaStream_t s);
 // count pass (fill = false) or fill pass (fill = true, ids != null)

@@ -22,11 +22,14 @@ struct DevCounters {
     int m_core;      // core cells
     int n_core;      // core points
     int n_border;    // border points
+    int n_noncore;   // non-core points (border candidates)
+    int cell_next;   // BCP work counters (ranked cells taken), near and far wave
+    int cell_next2;
     long long E;     // neighbour list entries
     long long P;     // candidate core-cell pairs
     long long K;     // border memberships
     unsigned long long pair_next;  // BCP work counter
-    unsigned long long pairs_tested, pairs_skipped, pairs_linked;
+    unsigned long long pairs_tested, pairs_skipped, pairs_linked, pairs_box;
     unsigned long long band_rechecks;
     unsigned long long dist_evals[3];  // MarkCore, BCP, border
 };
@@ -37,8 +40,10 @@ struct RunParams {
     int d;        // real dimension
     int min_pts;  // clamped to n + 1
     int bits;     // Morton bits per dimension
+    int ib;       // bits of the point index packed under the cell key (0: separate values)
     int max_iters;
     int stats;    // count distance evaluations
+    int box;      // cell bounding boxes prune pairs (FP32-band mode only)
     double eps2;  // fl(eps * eps), the FP64 threshold
     float lo, hi; // FP32 band: <= lo is in, > hi is out, otherwise FP64 recheck
     double inv_s; // 1 / cell side
@@ -71,12 +76,14 @@ void scan_i32_to_i32(const int *in, int *out, int64_t n_host, const int *n_dev, 
 void scan_i64_to_i64(const long long *in, long long *out, int64_t n_host, const int *n_dev,
                      int64_t n_max, long long *part, cudaStream_t s);
 
-// Stable LSD radix sort of (key, value) on key bits [0, bits), 8 bits a pass.
+// Stable LSD radix sort of 64-bit keys on key bits [lo, lo + bits), 8 bits a
+// pass, optionally carrying 32-bit values (v0/v1 null: keys only).
 // Ping-pongs between (k0, v0) and (k1, v1); returns 0 if the result is in
-// (k0, v0), 1 if in (k1, v1).  hist must hold radix_hist_size(n_max) entries.
-int64_t radix_hist_size(int64_t n_max);
-int radix_sort_u64(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int n_host,
-                   const int *n_dev, int64_t n_max, int bits, unsigned *hist, long long *part,
+// (k0, v0), 1 if in (k1, v1).  scratch holds sort_scratch_bytes(n_max) bytes.
+// Look-back waits are bounded by max_iters (DEVICE_TIMEOUT in ctr->err).
+size_t sort_scratch_bytes(int64_t n_max);
+int radix_sort_u64(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int n_host, const int *n_dev,
+                   int64_t n_max, int lo, int bits, void *scratch, DevCounters *ctr, int max_iters,
                    cudaStream_t s);
 
 // Kernel launches issued by this thread (read before and after a run).

@@ -42,7 +42,7 @@ struct StaticState {
     bool ready = false;
     dbscan_ctx ctx;                // views into g_static_scratch of this device
     gbdb::DevCounters h_ctr;       // host copies read back by the run
-    double h_bbox[2 * kMaxDim + 1];
+    long long h_bbox[2 * kMaxDim + 1];
 };
 
 StaticState g_state[kMaxDevices];
@@ -64,31 +64,29 @@ size_t carve(dbscan_ctx *c, unsigned char *base) {
     for (int d = 1; d <= kStaticMaxDim; ++d) noff_max = noff_max > c->noff[d] ? noff_max : c->noff[d];
     c->noff_max = noff_max;
     c->nbr_cap = (long long)noff_max * N + 1;
-    c->pair_cap = c->nbr_cap / 2 + 1;
-    const int64_t hsz = radix_hist_size(N);
-    const int64_t npart = scan_partials((N + 1) > hsz ? (N + 1) : hsz) + 2;
+    const int64_t npart = scan_partials(N + 1) + 2;
     const uint64_t hcap = hash_capacity((int)N);
     struct Item { void **p; size_t bytes; };
     const Item items[] = {
         {(void **)&c->k0, 8 * (size_t)N}, {(void **)&c->k1, 8 * (size_t)N},
         {(void **)&c->v0, 4 * (size_t)N}, {(void **)&c->v1, 4 * (size_t)N},
-        {(void **)&c->hist, 4 * (size_t)hsz}, {(void **)&c->part, 8 * (size_t)npart},
+        {(void **)&c->sort_scratch, sort_scratch_bytes(N)}, {(void **)&c->part, 8 * (size_t)npart},
         {(void **)&c->flags, 4 * (size_t)(N + 1)}, {(void **)&c->cid, 4 * (size_t)(N + 1)},
         {(void **)&c->pf, 4 * (size_t)N * SD}, {(void **)&c->pd, 8 * (size_t)N * SD},
         {(void **)&c->cpf, 4 * (size_t)N * SD}, {(void **)&c->cpd, 8 * (size_t)N * SD},
         {(void **)&c->orig, 4 * (size_t)N}, {(void **)&c->cell_of, 4 * (size_t)N},
         {(void **)&c->cell_start, 4 * (size_t)(N + 1)}, {(void **)&c->cell_key, 8 * (size_t)N},
-        {(void **)&c->hk, 8 * (size_t)hcap}, {(void **)&c->hv, 4 * (size_t)hcap},
-        {(void **)&c->nbr_cnt, 8 * (size_t)(N + 1)}, {(void **)&c->nbr_off, 8 * (size_t)(N + 1)},
+        {(void **)&c->ht, 16 * (size_t)hcap},
+        {(void **)&c->nbr_cnt, 4 * (size_t)(N + 1)}, {(void **)&c->nbr_near, 4 * (size_t)(N + 1)},
         {(void **)&c->nbr, 4 * (size_t)c->nbr_cap},
         {(void **)&c->core_s, 4 * (size_t)N}, {(void **)&c->core_pos, 4 * (size_t)(N + 1)},
         {(void **)&c->ccs, 4 * (size_t)(N + 1)}, {(void **)&c->core_orig, 4 * (size_t)N},
         {(void **)&c->core_cell, 4 * (size_t)N}, {(void **)&c->rank, 4 * (size_t)N},
-        {(void **)&c->pcnt, 8 * (size_t)(N + 1)}, {(void **)&c->poff, 8 * (size_t)(N + 1)},
-        {(void **)&c->pairs, 8 * (size_t)c->pair_cap},
+        {(void **)&c->blo, 16 * (size_t)N}, {(void **)&c->bhi, 16 * (size_t)N},
+        {(void **)&c->cblo, 16 * (size_t)N}, {(void **)&c->cbhi, 16 * (size_t)N},
         {(void **)&c->parent, 4 * (size_t)N}, {(void **)&c->compmin, 4 * (size_t)N},
+        {(void **)&c->noncore, 4 * (size_t)N},
         {(void **)&c->bcount, 8 * (size_t)N}, {(void **)&c->boff, 8 * (size_t)(N + 1)},
-        {(void **)&c->bbox_part, 8 * (size_t)1024 * 2 * kMaxDim}, {(void **)&c->bbox_bad, 4},
         {(void **)&c->bbox_out, 8 * (2 * kMaxDim + 1)},
         {(void **)&c->offs, (size_t)kMaxEnumDim * kMaxOffsets * kMaxEnumDim},
         {(void **)&c->ctr, sizeof(DevCounters)},

@@ -148,55 +148,86 @@ void scan_i64_to_i64(const long long *in, long long *out, int64_t n_host, const 
 }
 
 // ------------------------------------------------------------- radix sort
-// One pass = histogram per tile, scan of the digit-major histogram, stable
-// scatter.  A tile is 4096 keys: 8 warps x 16 items x 32 lanes, item j of lane
-// l of warp w at tile offset w*512 + j*32 + l, so (warp, item, lane) order is
-// input order and ranks taken in that order keep the sort stable.
+// Stable LSD radix sort of 64-bit keys (optionally carrying 32-bit values) on
+// the key bits [lo, lo + bits), 8 bits a pass -- the integer sort that groups
+// points by cell (Sec. 4.1).
+//
+// One-sweep layout: one kernel counts the digits of every pass at once; each
+// pass is then a single scatter kernel.  A scatter block takes the next tile of
+// 4096 keys from an atomic tile counter (so tiles start in order and every
+// earlier tile belongs to a block that is already running), ranks its keys
+// stably per digit inside the tile, publishes its per-digit count, and looks
+// back over the earlier tiles' published counts to find its global offset
+// (decoupled look-back).  The look-back waits on flags written by other
+// blocks; each wait is bounded by max_iters and raises DEVICE_TIMEOUT instead
+// of spinning on.
+//
+// Tile layout: 8 warps x 16 items x 32 lanes; item j of lane l of warp w sits
+// at tile offset w*512 + j*32 + l, so (warp, item, lane) order is input order
+// and ranks taken in that order keep the sort stable.
 constexpr int RS_THREADS = 256, RS_WARPS = 8, RS_ITEMS = 16;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RS_BINS = 256;
+constexpr int RS_MAX_PASSES = 8;
+constexpr int RS_LOOK = 16;  // look-back window (tiles read per step)
+constexpr unsigned long long ST_AGG = 1ull << 62, ST_INC = 2ull << 62, ST_VAL = (1ull << 62) - 1;
 
-int64_t radix_hist_size(int64_t n_max) {
-    int64_t nb = (n_max + RS_TILE - 1) / RS_TILE;
-    if (nb == 0) nb = 1;
-    return nb * RS_BINS + 1;
+static int64_t rs_tiles(int64_t n_max) {
+    int64_t t = (n_max + RS_TILE - 1) / RS_TILE;
+    return t > 0 ? t : 1;
+}
+
+// scratch: [passes][256] u32 digit offsets | [passes] u32 tile counters (padded
+// to 256 B) | [passes][tiles][256] u64 tile status
+size_t sort_scratch_bytes(int64_t n_max) {
+    return (size_t)RS_MAX_PASSES * RS_BINS * 4 + 256 + (size_t)RS_MAX_PASSES * rs_tiles(n_max) * RS_BINS * 8;
 }
 
 __global__ void __launch_bounds__(RS_THREADS)
-k_radix_hist(const uint64_t *__restrict__ keys, int n_host, const int *n_dev, int shift,
-             unsigned *__restrict__ hist, int nblk) {
-    __shared__ unsigned cnt[RS_BINS];
+k_radix_hist(const uint64_t *__restrict__ keys, int n_host, const int *n_dev, int lo, int passes,
+             unsigned *__restrict__ ghist) {
+    __shared__ unsigned sh[RS_MAX_PASSES][RS_BINS];
     const int n = n_dev ? *n_dev : n_host;
-    for (int i = threadIdx.x; i < RS_BINS; i += RS_THREADS) cnt[i] = 0;
+    for (int i = threadIdx.x; i < RS_MAX_PASSES * RS_BINS; i += RS_THREADS) (&sh[0][0])[i] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    if (base < n) {
-#pragma unroll 4
-        for (int j = 0; j < RS_ITEMS; ++j) {
-            int64_t i = base + (int64_t)j * RS_THREADS + threadIdx.x;
-            unsigned dig = i < n ? (unsigned)((keys[i] >> shift) & 255u) : 0xffffffffu;
-            unsigned peers = __match_any_sync(0xffffffffu, dig);
-            int leader = __ffs(peers) - 1;
-            if (dig != 0xffffffffu && (int)(threadIdx.x & 31) == leader)
-                atomicAdd(&cnt[dig], (unsigned)__popc(peers));
-        }
+    for (int64_t i = blockIdx.x * (int64_t)RS_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RS_THREADS) {
+        const uint64_t k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(unsigned)(k >> (lo + 8 * p)) & 255u], 1u);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < RS_BINS; i += RS_THREADS) hist[(int64_t)i * nblk + blockIdx.x] = cnt[i];
+    for (int i = threadIdx.x; i < passes * RS_BINS; i += RS_THREADS) {
+        const unsigned v = (&sh[0][0])[i];
+        if (v) atomicAdd(ghist + i, v);
+    }
 }
 
+// Exclusive scan of each pass's 256 digit counts (one block).
+__global__ void __launch_bounds__(RS_BINS) k_radix_offsets(unsigned *ghist, int passes) {
+    __shared__ long long sh[33];
+    for (int p = 0; p < passes; ++p) {
+        const unsigned v = ghist[p * RS_BINS + threadIdx.x];
+        long long tot;
+        const long long ex = block_excl_scan<long long>((long long)v, sh, &tot);
+        ghist[p * RS_BINS + threadIdx.x] = (unsigned)ex;
+    }
+}
+
+template <bool KV>
 __global__ void __launch_bounds__(RS_THREADS)
 k_radix_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-                uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int n_host,
-                const int *n_dev, int shift, const int *__restrict__ offs, int nblk) {
+                uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int n_host, const int *n_dev,
+                int shift, const unsigned *__restrict__ goff, unsigned long long *status, int *tile_ctr,
+                DevCounters *ctr, int max_iters) {
     __shared__ int wcnt[RS_WARPS][RS_BINS];
-    __shared__ int gbase[RS_BINS];
+    __shared__ int s_tile;
     const int n = n_dev ? *n_dev : n_host;
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    if (base >= n) return;  // whole block uniform
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1);
+    __syncthreads();
+    const int tile = s_tile;
+    const int64_t base = (int64_t)tile * RS_TILE;
+    if (base >= n) return;  // uniform per block; no later tile has keys either
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
-    for (int i = threadIdx.x; i < RS_BINS; i += RS_THREADS) gbase[i] = offs[(int64_t)i * nblk + blockIdx.x];
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
     const int64_t wbase = base + (int64_t)warp * (32 * RS_ITEMS);
@@ -205,57 +236,118 @@ k_radix_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ v
     int r[RS_ITEMS];
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {
-        int64_t i = wbase + j * 32 + lane;
-        bool ok = i < n;
+        const int64_t i = wbase + j * 32 + lane;
+        const bool ok = i < n;
         k[j] = ok ? kin[i] : 0;
-        v[j] = ok ? vin[i] : 0;
-        unsigned dig = ok ? (unsigned)((k[j] >> shift) & 255u) : 0xffffffffu;
-        unsigned peers = __match_any_sync(0xffffffffu, dig);
-        int before = ok ? wcnt[warp][dig] : 0;
+        if (KV) v[j] = ok ? vin[i] : 0;
+        const unsigned dig = ok ? (unsigned)((k[j] >> shift) & 255u) : 0xffffffffu;
+        const unsigned peers = __match_any_sync(0xffffffffu, dig);
+        const int before = ok ? wcnt[warp][dig] : 0;
         __syncwarp();
         if (ok && lane == __ffs(peers) - 1) wcnt[warp][dig] = before + __popc(peers);
         __syncwarp();
         r[j] = ok ? before + __popc(peers & lt) : -1;
     }
     __syncthreads();
-    // Exclusive prefix over warps for each digit, plus the block's global base.
-    for (int dgt = threadIdx.x; dgt < RS_BINS; dgt += RS_THREADS) {
-        int run = gbase[dgt];
+    // One thread per digit: exclusive prefix over warps, tile total, publish,
+    // look back, publish the inclusive prefix, and fold the global base into
+    // the per-warp offsets.
+    {
+        const int dgt = threadIdx.x;
+        int run = 0;
 #pragma unroll
         for (int w = 0; w < RS_WARPS; ++w) {
-            int c = wcnt[w][dgt];
+            const int c = wcnt[w][dgt];
             wcnt[w][dgt] = run;
             run += c;
         }
+        volatile unsigned long long *st = status + (int64_t)tile * RS_BINS + dgt;
+        long long excl = 0;
+        if (tile == 0) {
+            *st = ST_INC | (unsigned long long)run;
+        } else {
+            *st = ST_AGG | (unsigned long long)run;
+            // Look back RS_LOOK tiles at a time: the window's loads are issued
+            // together, then summed nearest first up to the first inclusive
+            // prefix; a tile not yet published is polled (bounded).
+            bool found = false;
+            for (int t0 = tile - 1; t0 >= 0 && !found; t0 -= RS_LOOK) {
+                unsigned long long x[RS_LOOK];
+#pragma unroll
+                for (int j = 0; j < RS_LOOK; ++j)
+                    x[j] = t0 - j >= 0 ? *(volatile unsigned long long *)(status + (int64_t)(t0 - j) * RS_BINS + dgt)
+                                       : (unsigned long long)(2ull << 62);
+#pragma unroll
+                for (int j = 0; j < RS_LOOK; ++j) {
+                    if (!found) {
+                        if ((x[j] & ~ST_VAL) == 0) {
+                            volatile unsigned long long *src = status + (int64_t)(t0 - j) * RS_BINS + dgt;
+                            int it = 0;
+                            while ((x[j] & ~ST_VAL) == 0 && it < max_iters) { x[j] = *src; ++it; }
+                            if ((x[j] & ~ST_VAL) == 0) {
+                                set_error(ctr, DBSCAN_ERR_DEVICE_TIMEOUT, 40);
+                                x[j] = 2ull << 62;
+                            }
+                        }
+                        excl += (long long)(x[j] & ST_VAL);
+                        found = (x[j] & ~ST_VAL) == ST_INC;
+                    }
+                }
+            }
+            *st = ST_INC | (unsigned long long)(excl + run);
+        }
+        const int gb = (int)(goff[dgt] + excl);
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) wcnt[w][dgt] += gb;
     }
     __syncthreads();
+    // After a timed-out wait the offsets are unknown: write nothing (the run
+    // reports DEVICE_TIMEOUT); positions are also checked against n.
+    if (*(volatile int *)&ctr->err == DBSCAN_ERR_DEVICE_TIMEOUT) return;
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {
         if (r[j] >= 0) {
-            unsigned dig = (unsigned)((k[j] >> shift) & 255u);
-            int pos = wcnt[warp][dig] + r[j];
-            kout[pos] = k[j];
-            vout[pos] = v[j];
+            const unsigned dig = (unsigned)((k[j] >> shift) & 255u);
+            const int pos = wcnt[warp][dig] + r[j];
+            if (pos >= 0 && pos < n) {
+                kout[pos] = k[j];
+                if (KV) vout[pos] = v[j];
+            }
         }
     }
 }
 
-int radix_sort_u64(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int n_host,
-                   const int *n_dev, int64_t n_max, int bits, unsigned *hist, long long *part,
+int radix_sort_u64(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int n_host, const int *n_dev,
+                   int64_t n_max, int lo, int bits, void *scratch, DevCounters *ctr, int max_iters,
                    cudaStream_t s) {
-    int nblk = (int)((n_max + RS_TILE - 1) / RS_TILE);
-    if (nblk == 0 || bits <= 0) return 0;
-    const int64_t hsz = (int64_t)nblk * RS_BINS;
-    int *offs = reinterpret_cast<int *>(hist);  // scanned in place (counts fit in int)
+    const int passes = (bits + 7) / 8;
+    if (passes <= 0) return 0;
+    const int64_t tiles = rs_tiles(n_max);
+    unsigned *ghist = reinterpret_cast<unsigned *>(scratch);
+    int *tile_ctr = reinterpret_cast<int *>(ghist + RS_MAX_PASSES * RS_BINS);
+    unsigned long long *status =
+        reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(scratch) + RS_MAX_PASSES * RS_BINS * 4 + 256);
+    cudaMemsetAsync(scratch, 0,
+                    (size_t)RS_MAX_PASSES * RS_BINS * 4 + 256 + (size_t)passes * tiles * RS_BINS * 8, s);
+    const int gh = grid_for((const void *)k_radix_hist, RS_THREADS);
+    k_radix_hist<<<gh, RS_THREADS, 0, s>>>(k0, n_host, n_dev, lo, passes, ghist); count_launch();
+    k_radix_offsets<<<1, RS_BINS, 0, s>>>(ghist, passes); count_launch();
     int cur = 0;
-    for (int shift = 0; shift < bits; shift += 8) {
+    for (int p = 0; p < passes; ++p) {
         const uint64_t *ki = cur ? k1 : k0;
         const uint32_t *vi = cur ? v1 : v0;
         uint64_t *ko = cur ? k0 : k1;
         uint32_t *vo = cur ? v0 : v1;
-        k_radix_hist<<<nblk, RS_THREADS, 0, s>>>(ki, n_host, n_dev, shift, hist, nblk); count_launch();
-        scan_i32_to_i32(offs, offs, hsz, nullptr, hsz, part, s);
-        k_radix_scatter<<<nblk, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n_host, n_dev, shift, offs, nblk); count_launch();
+        unsigned long long *st = status + (size_t)p * tiles * RS_BINS;
+        if (v0)
+            k_radix_scatter<true><<<(int)tiles, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n_host, n_dev, lo + 8 * p,
+                                                                     ghist + p * RS_BINS, st, tile_ctr + p, ctr,
+                                                                     max_iters);
+        else
+            k_radix_scatter<false><<<(int)tiles, RS_THREADS, 0, s>>>(ki, nullptr, ko, nullptr, n_host, n_dev,
+                                                                      lo + 8 * p, ghist + p * RS_BINS, st,
+                                                                      tile_ctr + p, ctr, max_iters);
+        count_launch();
         cur ^= 1;
     }
     return cur;

@@ -76,11 +76,23 @@ def test_random_mixed(d, seed, precision, dtype):
         _assert_same(X, eps, mp, precision=precision)
 
 
+@pytest.mark.parametrize("cell_bounds", [True, False])
 @pytest.mark.parametrize("schedule", ["size", "none"])
-def test_schedules_agree(schedule):
+def test_schedules_agree(schedule, cell_bounds):
     X = synth.random_small(77, 20000, 3, dtype=np.float32)
-    st = _assert_same(X, 0.25, 10, schedule=schedule)
-    assert st["num_pairs_tested"] + st["num_pairs_skipped"] == st["num_candidate_pairs"]
+    st = _assert_same(X, 0.25, 10, schedule=schedule, cell_bounds=cell_bounds)
+    assert (st["num_pairs_tested"] + st["num_pairs_skipped"] + st["num_pairs_box_decided"]
+            == st["num_candidate_pairs"])
+    if not cell_bounds:
+        assert st["num_pairs_box_decided"] == 0
+
+
+@pytest.mark.parametrize("d", [2, 3, 4])
+def test_cell_bounds_off_matches(d):
+    """Point-by-point tests without the box shortcuts give the same result."""
+    X = synth.random_small(500 + d, 6000, d, dtype=np.float32)
+    for eps, mp in ((0.2, 5), (0.5, 30)):
+        _assert_same(X, eps, mp, cell_bounds=False)
 
 
 def test_blobs_2d_20k_fp64():
