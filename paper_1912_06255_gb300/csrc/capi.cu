@@ -205,7 +205,8 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
         {(void **)&c->k0, 8 * (size_t)N}, {(void **)&c->k1, 8 * (size_t)N},
         {(void **)&c->v0, 4 * (size_t)N}, {(void **)&c->v1, 4 * (size_t)N},
         {(void **)&c->sort_scratch, sort_scratch_bytes(N)}, {(void **)&c->part, 8 * (size_t)npart},
-        {(void **)&c->flags, 4 * (size_t)(N + 1)}, {(void **)&c->cid, 4 * (size_t)(N + 1)},
+        {(void **)&c->slot_of, 4 * (size_t)N}, {(void **)&c->rank_of, 4 * (size_t)N},
+        {(void **)&c->slots, 4 * (size_t)N}, {(void **)&c->hcnt, 4 * (size_t)hcap},
         {(void **)&c->pf, 4 * (size_t)N * SD}, {(void **)&c->pd, 8 * (size_t)N * SD},
         {(void **)&c->cpf, 4 * (size_t)N * SD}, {(void **)&c->cpd, 8 * (size_t)N * SD},
         {(void **)&c->orig, 4 * (size_t)N}, {(void **)&c->cell_of, 4 * (size_t)N},
@@ -240,6 +241,10 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
         e = cudaMemcpy(c->offs + (size_t)(d - 1) * kMaxOffsets * kMaxEnumDim, t.data(), t.size(),
                        cudaMemcpyHostToDevice);
     }
+    c->hcap = hcap;
+    if (e == cudaSuccess) e = cudaMemset(c->ht, 0xff, sizeof(ulonglong2) * hcap);
+    if (e == cudaSuccess) e = cudaMemset(c->hcnt, 0, sizeof(unsigned) * hcap);
+    c->table_clean = e == cudaSuccess;
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         dbscan_destroy(c);
@@ -343,11 +348,13 @@ dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, 
     P.eps2 = eps * eps;
     const double side = (eps / std::sqrt((double)d)) * (1.0 - 0x1p-20);
     P.inv_s = 1.0 / side;
+    P.inv_s32 = (float)P.inv_s;
     int kmax_all = 0;
     double M = 0.0;
     for (int j = 0; j < d; ++j) {
         const double lo = bbox_key_to_double(c->h_bbox[j]), hi = bbox_key_to_double(c->h_bbox[kMaxDim + j]);
         P.origin[j] = lo;
+        P.origin32[j] = (float)lo;
         const double t = (hi - lo) * P.inv_s;
         if (!(t < 0x1p30)) return DBSCAN_ERR_KEY_OVERFLOW;
         P.kmax[j] = (int)std::floor(t);
@@ -372,29 +379,42 @@ dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, 
     c->stats.band_lo = P.lo;
     c->stats.band_hi = P.hi;
 
-    // 3. keys and sort (semisort role, Sec. 4.1).  When the cell key and the
-    // point index fit together in 64 bits they are packed and sorted as one.
-    int ib = 1;
-    while (ib < 31 && (1ll << ib) < n) ++ib;
-    if (d * bits + ib > 64) ib = 0;
-    P.ib = ib;
+    // 3. cells: group the points by cell (semisort, Sec. 4.1) through the cell hash
     mark(2);
-    launch_keys(d_points, dtype, P, c->k0, c->v0, s);
-    const int which = radix_sort_u64(c->k0, ib ? nullptr : c->v0, c->k1, ib ? nullptr : c->v1, (int)n, nullptr, n,
-                                     ib, d * bits, c->sort_scratch, c->ctr, c->max_iters, s);
-    const uint64_t *K = which ? c->k1 : c->k0;
-    const uint32_t *V = which ? c->v1 : c->v0;
+    if (!c->table_clean) {
+        CK(cudaMemsetAsync(c->ht, 0xff, sizeof(ulonglong2) * c->hcap, s));
+        CK(cudaMemsetAsync(c->hcnt, 0, sizeof(unsigned) * c->hcap, s));
+    }
+    c->table_clean = false;
+    Semisort S{};
+    S.ht = c->ht;
+    S.hcnt = c->hcnt;
+    S.hcap = c->hcap;
+    S.slot_of = c->slot_of;
+    S.rank_of = c->rank_of;
+    S.slots = c->slots;
+    S.k0 = c->k0;
+    S.k1 = c->k1;
+    S.v0 = c->v0;
+    S.v1 = c->v1;
+    S.sort_scratch = c->sort_scratch;
+    S.part = c->part;
+    S.cell_key = c->cell_key;
+    S.count = c->core_pos;  // scratch until the compaction
+    S.cell_start = c->cell_start;
+    S.pf = c->pf;
+    S.pd = f64 ? c->pd : nullptr;
+    S.orig = c->orig;
+    S.cell_of = c->cell_of;
+    launch_semisort(d_points, dtype, P, SD, S, c->ctr, s);
 
-    // 4. cells, hash, neighbour lists
+    // 4. cell boxes, neighbour lists
     mark(3);
-    launch_cells(d_points, dtype, (int)n, d, SD, ib, K, V, c->flags, c->cid, c->part, c->pf, f64 ? c->pd : nullptr,
-                 c->orig, c->cell_of, c->cell_start, c->cell_key, c->ctr, s);
     if (P.box) launch_boxes(SD, c->pf, c->cell_start, c->ctr, c->blo, c->bhi, s);
-    launch_hash(c->ht, c->cell_key, c->ctr, s);
     int n_near = 1;
     for (int j = 0; j < d; ++j) n_near *= 3;
-    launch_neighbors(c->cell_key, c->ht, P, offs_for(c, d), c->noff[d], n_near - 1, c->blo, c->bhi, c->nbr_cnt,
-                     c->nbr_near, c->nbr, c->ctr, s);
+    launch_neighbors(c->cell_key, c->ht, c->hcap, P, offs_for(c, d), c->noff[d], n_near - 1, c->blo, c->bhi,
+                     c->nbr_cnt, c->nbr_near, c->nbr, c->ctr, s);
 
     // 5. MarkCore, 6. compaction, 7. schedule, 8. connect, 9. labels, 10. border
     Bufs B = make_bufs(c, f64);
@@ -411,11 +431,13 @@ dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, 
     launch_labels(P, B, d_core, d_labels, c->ctr, s);
     launch_border(D, mode, false, P, B, d_labels, nullptr, 0, c->ctr, s);
     mark(8);
+    launch_table_reset(S, c->ctr, s);
     if (d_border_offsets)
         CK(cudaMemcpyAsync(d_border_offsets, c->boff, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    c->table_clean = c->h_ctr->err == 0;
     const DevCounters &h = *c->h_ctr;
     dbscan_stats &st = c->stats;
     st.num_cells = h.m;

@@ -35,7 +35,10 @@ struct dbscan_ctx {
     uint32_t *v0 = nullptr, *v1 = nullptr;
     void *sort_scratch = nullptr;
     long long *part = nullptr;
-    int *flags = nullptr, *cid = nullptr;
+    uint32_t *slot_of = nullptr, *rank_of = nullptr, *slots = nullptr;  // cell grouping
+    unsigned *hcnt = nullptr;
+    uint64_t hcap = 0;
+    bool table_clean = false;  // every slot of ht empty and every hcnt zero
     float *pf = nullptr, *cpf = nullptr;
     double *pd = nullptr, *cpd = nullptr;
     int *orig = nullptr, *cell_of = nullptr, *cell_start = nullptr;

@@ -109,124 +109,227 @@ void launch_bbox(const void *X, int dtype, int n, int d, int nb, long long *out,
     count_launch();
 }
 
-// ---------------------------------------------------------------- keys
-// Cell coordinate k_j = floor(fl(fl(x_j - origin_j) * (1/s))), then Morton
-// packed.  Keys are computed in FP64 for every input type.
+// ------------------------------------------------------------ semisort
+// Grouping the points by cell (Sec. 4.1): the paper semisorts (cell, point)
+// pairs and keeps the non-empty cells in a hash table, since only grouping
+// matters, not order.  Here each point computes its cell coordinates in FP64,
+// k_j = floor(fl(fl(x_j - origin_j) * (1/s))), Morton-packs them, inserts the
+// key into the cell hash (one slot per non-empty cell) and takes the next free
+// position of its cell with an atomic increment.  Only the m distinct cell
+// keys are then sorted, which lays the cells out along the Z-curve; the points
+// are finally moved to their cell's range in one pass.  Slot = {key, cell id};
+// the table is reset to empty after each run by k_table_reset, so a run only
+// touches the slots it uses.
+// Cell coordinate of coordinate j of a point: floor(fl64(fl64(x - o) * inv_s)),
+// clamped to [0, kmax].  For FP32 input the FP32 estimate
+// t32 = fl32(fl32(x - o) * fl32(inv_s)) is within eps_t = t * 3.01 * 2^-24 (+ the
+// FP64 value's own 3 * 2^-53 * t) of the FP64 value t64 (x and o = the minimum
+// of FP32 values are exact FP32 numbers), so when t32 is farther than eps_t
+// from an integer both floors agree; only the rest is recomputed in FP64.
+template <typename T>
+__device__ __forceinline__ int cell_coord(T x, const RunParams &P, int j) {
+    if constexpr (sizeof(T) == 4) {
+        const float t32 = __fmul_rn(__fsub_rn(x, P.origin32[j]), P.inv_s32);
+        const float fl = floorf(t32);
+        const float e = t32 * 1.8e-7f + 1e-30f;
+        if (t32 - fl > e && (fl + 1.0f) - t32 > e) {
+            const int k = (int)fl;
+            return k < 0 ? 0 : (k > P.kmax[j] ? P.kmax[j] : k);
+        }
+    }
+    const double t = __dmul_rn(__dsub_rn((double)x, P.origin[j]), P.inv_s);
+    const int k = (int)floor(t);
+    return k < 0 ? 0 : (k > P.kmax[j] ? P.kmax[j] : k);
+}
+
+constexpr int INS_U = 4;  // points per thread per step (their probes overlap)
+
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_keys(const T *__restrict__ X, RunParams P, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-        int c[kMaxDim];
+k_insert(const T *__restrict__ X, RunParams P, ulonglong2 *__restrict__ ht, unsigned *__restrict__ hcnt,
+         uint64_t hmask, int hlg, uint32_t *__restrict__ slot_of, uint32_t *__restrict__ rank_of,
+         uint32_t *__restrict__ slots, DevCounters *ctr) {
+    const int T_ = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < P.n; i0 += T_ * INS_U) {
+        uint64_t key[INS_U], s[INS_U];
+        unsigned long long cur[INS_U];
 #pragma unroll
-        for (int j = 0; j < kMaxDim; ++j) {
-            if (j < P.d) {
-                double x = (double)X[(int64_t)i * P.d + j];
-                double t = __dmul_rn(__dsub_rn(x, P.origin[j]), P.inv_s);
-                int k = (int)floor(t);
-                c[j] = k < 0 ? 0 : (k > P.kmax[j] ? P.kmax[j] : k);
-            } else {
-                c[j] = 0;
+        for (int u = 0; u < INS_U; ++u) {
+            const int i = i0 + u * T_;
+            key[u] = 0;
+            s[u] = 0;
+            if (i < P.n) {
+                int c[kMaxDim];
+#pragma unroll
+                for (int j = 0; j < kMaxDim; ++j) c[j] = j < P.d ? cell_coord<T>(X[(int64_t)i * P.d + j], P, j) : 0;
+                key[u] = morton_encode(c, P.d, P.bits);
+                s[u] = hash_slot(key[u], hlg);
             }
         }
-        const uint64_t key = morton_encode(c, P.d, P.bits);
-        if (P.ib) {
-            keys[i] = (key << P.ib) | (uint64_t)i;
-        } else {
-            keys[i] = key;
-            vals[i] = (uint32_t)i;
+#pragma unroll
+        for (int u = 0; u < INS_U; ++u) cur[u] = i0 + u * T_ < P.n ? ht[s[u]].x : 0;
+        unsigned rk[INS_U];
+#pragma unroll
+        for (int u = 0; u < INS_U; ++u) {
+            const int i = i0 + u * T_;
+            rk[u] = 0;
+            if (i >= P.n) continue;
+            bool ok = false;
+            for (uint64_t it = 0; it <= hmask; ++it) {
+                if (cur[u] == kEmptyKey) {
+                    cur[u] = atomicCAS(&ht[s[u]].x, (unsigned long long)kEmptyKey, (unsigned long long)key[u]);
+                    if (cur[u] == kEmptyKey) {
+                        slots[atomicAdd(&ctr->m, 1)] = (uint32_t)s[u];  // a new non-empty cell
+                        ok = true;
+                        break;
+                    }
+                }
+                if (cur[u] == key[u]) { ok = true; break; }
+                s[u] = (s[u] + 1) & hmask;
+                cur[u] = ht[s[u]].x;
+            }
+            if (!ok) {
+                set_error(ctr, DBSCAN_ERR_CAPACITY, 10);
+                s[u] = ~0ull;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < INS_U; ++u) {
+            const int i = i0 + u * T_;
+            if (i < P.n && s[u] != ~0ull) rk[u] = atomicAdd(hcnt + s[u], 1u);
+        }
+#pragma unroll
+        for (int u = 0; u < INS_U; ++u) {
+            const int i = i0 + u * T_;
+            if (i < P.n && s[u] != ~0ull) {
+                slot_of[i] = (uint32_t)s[u];
+                rank_of[i] = rk[u];
+            }
         }
     }
 }
 
-void launch_keys(const void *X, int dtype, const RunParams &P, uint64_t *keys, uint32_t *vals,
-                 cudaStream_t s) {
-    if (dtype == DBSCAN_F32) {
-        int g = grid_for((const void *)k_keys<float>, 256);
-        k_keys<float><<<g, 256, 0, s>>>((const float *)X, P, keys, vals); count_launch();
-    } else {
-        int g = grid_for((const void *)k_keys<double>, 256);
-        k_keys<double><<<g, 256, 0, s>>>((const double *)X, P, keys, vals); count_launch();
+// Sort input: (cell key, slot) of the m non-empty cells.
+__global__ void __launch_bounds__(256)
+k_cell_keys(const ulonglong2 *__restrict__ ht, const uint32_t *__restrict__ slots, uint64_t *__restrict__ keys,
+            uint32_t *__restrict__ vals, const DevCounters *ctr) {
+    const int m = ctr->m;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+        const uint32_t s = slots[c];
+        keys[c] = ht[s].x;
+        vals[c] = s;
     }
 }
 
-// ---------------------------------------------------------------- cells
+// Cell c (in key order) owns slot vals[c]: record its id in the slot, its key
+// and its point count.
 __global__ void __launch_bounds__(256)
-k_cell_flags(const uint64_t *__restrict__ K, int n, int ib, int *__restrict__ flags) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        flags[i] = (i == 0 || (K[i] >> ib) != (K[i - 1] >> ib)) ? 1 : 0;
+k_cell_table(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, ulonglong2 *__restrict__ ht,
+             const unsigned *__restrict__ hcnt, uint64_t *__restrict__ cell_key, int *__restrict__ count,
+             const DevCounters *ctr) {
+    const int m = ctr->m;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+        const uint32_t s = vals[c];
+        ht[s].y = (unsigned long long)c;
+        cell_key[c] = keys[c];
+        count[c] = (int)hcnt[s];
+    }
 }
 
-// Gather the points into cell order, zero padded to the storage width, and
-// record the cell table: cell_start[m+1], cell_key[m], cell_of[n], orig[n].
+// Move every point to its cell's range: coalesced reads of the input, one
+// scattered write per point.  Points are stored zero padded to SD coordinates.
 template <typename T, int SD>
 __global__ void __launch_bounds__(256)
-k_gather(const T *__restrict__ X, int n, int d, int ib, const uint64_t *__restrict__ K,
-         const uint32_t *__restrict__ V, const int *__restrict__ flags, const int *__restrict__ cid,
-         float *__restrict__ pf, double *__restrict__ pd, int *__restrict__ orig,
-         int *__restrict__ cell_of, int *__restrict__ cell_start, uint64_t *__restrict__ cell_key,
-         DevCounters *ctr) {
+k_scatter_points(const T *__restrict__ X, int n, int d, const ulonglong2 *__restrict__ ht,
+                 const uint32_t *__restrict__ slot_of, const uint32_t *__restrict__ rank_of,
+                 const int *__restrict__ cell_start, float *__restrict__ pf, double *__restrict__ pd,
+                 int *__restrict__ orig, int *__restrict__ cell_of, const DevCounters *ctr) {
+    if (ctr->err) return;  // a failed insert left slot_of undefined
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint64_t key = K[i];
-        const int o = ib ? (int)(key & ((1ull << ib) - 1)) : (int)V[i];
-        const int c = cid[i] + flags[i] - 1;
-        orig[i] = o;
-        cell_of[i] = c;
-        if (flags[i]) { cell_start[c] = i; cell_key[c] = key >> ib; }
-        if (i == 0) {
-            const int m = cid[n];
-            ctr->m = m;
-            cell_start[m] = n;
-        }
+        const int c = (int)ht[slot_of[i]].y;
+        const int dst = cell_start[c] + (int)rank_of[i];
+        orig[dst] = i;
+        cell_of[dst] = c;
         float f[SD];
         double x[SD];
 #pragma unroll
         for (int j = 0; j < SD; ++j) {
-            x[j] = j < d ? (double)X[(int64_t)o * d + j] : 0.0;
+            x[j] = j < d ? (double)X[(int64_t)i * d + j] : 0.0;
             f[j] = (float)x[j];
         }
         if constexpr (SD == 2) {
-            reinterpret_cast<float2 *>(pf)[i] = make_float2(f[0], f[1]);
+            reinterpret_cast<float2 *>(pf)[dst] = make_float2(f[0], f[1]);
         } else {
 #pragma unroll
             for (int j = 0; j < SD; j += 4)
-                reinterpret_cast<float4 *>(pf)[(int64_t)i * (SD / 4) + j / 4] =
+                reinterpret_cast<float4 *>(pf)[(int64_t)dst * (SD / 4) + j / 4] =
                     make_float4(f[j], f[j + 1], f[j + 2], f[j + 3]);
         }
         if (pd) {
 #pragma unroll
             for (int j = 0; j < SD; j += 2)
-                reinterpret_cast<double2 *>(pd)[(int64_t)i * (SD / 2) + j / 2] = make_double2(x[j], x[j + 1]);
+                reinterpret_cast<double2 *>(pd)[(int64_t)dst * (SD / 2) + j / 2] = make_double2(x[j], x[j + 1]);
         }
     }
 }
 
-template <int SD>
-static void gather_sd(const void *X, int dtype, int n, int d, int ib, const uint64_t *K, const uint32_t *V,
-                      const int *flags, const int *cid, float *pf, double *pd, int *orig, int *cell_of,
-                      int *cell_start, uint64_t *cell_key, DevCounters *ctr, cudaStream_t s) {
-    if (dtype == DBSCAN_F32) {
-        int g = grid_for((const void *)k_gather<float, SD>, 256);
-        k_gather<float, SD><<<g, 256, 0, s>>>((const float *)X, n, d, ib, K, V, flags, cid, pf, nullptr, orig,
-                                              cell_of, cell_start, cell_key, ctr); count_launch();
-    } else {
-        int g = grid_for((const void *)k_gather<double, SD>, 256);
-        k_gather<double, SD><<<g, 256, 0, s>>>((const double *)X, n, d, ib, K, V, flags, cid, pf, pd, orig,
-                                               cell_of, cell_start, cell_key, ctr); count_launch();
+// Return the slots this run used to empty.
+__global__ void __launch_bounds__(256)
+k_table_reset(ulonglong2 *__restrict__ ht, unsigned *__restrict__ hcnt, const uint32_t *__restrict__ slots,
+              const DevCounters *ctr) {
+    const int m = ctr->m;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+        const uint32_t s = slots[c];
+        ht[s] = make_ulonglong2(kEmptyKey, 0);
+        hcnt[s] = 0;
     }
 }
 
-void launch_cells(const void *X, int dtype, int n, int d, int SD, int ib, const uint64_t *K, const uint32_t *V,
-                  int *flags, int *cid, long long *part, float *pf, double *pd, int *orig,
-                  int *cell_of, int *cell_start, uint64_t *cell_key, DevCounters *ctr, cudaStream_t s) {
-    int g = grid_for((const void *)k_cell_flags, 256);
-    k_cell_flags<<<g, 256, 0, s>>>(K, n, ib, flags); count_launch();
-    scan_i32_to_i32(flags, cid, n, nullptr, n, part, s);
-    if (SD == 2)
-        gather_sd<2>(X, dtype, n, d, ib, K, V, flags, cid, pf, pd, orig, cell_of, cell_start, cell_key, ctr, s);
-    else if (SD == 4)
-        gather_sd<4>(X, dtype, n, d, ib, K, V, flags, cid, pf, pd, orig, cell_of, cell_start, cell_key, ctr, s);
-    else
-        gather_sd<8>(X, dtype, n, d, ib, K, V, flags, cid, pf, pd, orig, cell_of, cell_start, cell_key, ctr, s);
+void launch_semisort(const void *X, int dtype, const RunParams &P, int SD, const Semisort &S, DevCounters *ctr,
+                     cudaStream_t s) {
+    const int lg = hash_log2(S.hcap);
+    const uint64_t hmask = S.hcap - 1;
+    if (dtype == DBSCAN_F32) {
+        int g = grid_for((const void *)k_insert<float>, 256);
+        k_insert<float><<<g, 256, 0, s>>>((const float *)X, P, S.ht, S.hcnt, hmask, lg, S.slot_of, S.rank_of,
+                                          S.slots, ctr);
+    } else {
+        int g = grid_for((const void *)k_insert<double>, 256);
+        k_insert<double><<<g, 256, 0, s>>>((const double *)X, P, S.ht, S.hcnt, hmask, lg, S.slot_of, S.rank_of,
+                                           S.slots, ctr);
+    }
+    count_launch();
+    int g = grid_for((const void *)k_cell_keys, 256);
+    k_cell_keys<<<g, 256, 0, s>>>(S.ht, S.slots, S.k0, S.v0, ctr); count_launch();
+    const int which = radix_sort_u64(S.k0, S.v0, S.k1, S.v1, 0, &ctr->m, P.n, 0, P.d * P.bits, S.sort_scratch,
+                                     ctr, P.max_iters, s);
+    const uint64_t *K = which ? S.k1 : S.k0;
+    const uint32_t *V = which ? S.v1 : S.v0;
+    g = grid_for((const void *)k_cell_table, 256);
+    k_cell_table<<<g, 256, 0, s>>>(K, V, S.ht, S.hcnt, S.cell_key, S.count, ctr); count_launch();
+    scan_i32_to_i32(S.count, S.cell_start, 0, &ctr->m, P.n, S.part, s);
+    auto scat = [&](auto k, auto xp) {
+        int gg = grid_for((const void *)k, 256);
+        k<<<gg, 256, 0, s>>>(xp, P.n, P.d, S.ht, S.slot_of, S.rank_of, S.cell_start, S.pf, S.pd, S.orig, S.cell_of,
+                             ctr);
+        count_launch();
+    };
+    const float *xf = (const float *)X;
+    const double *xd = (const double *)X;
+    if (dtype == DBSCAN_F32) {
+        if (SD == 2) scat(k_scatter_points<float, 2>, xf);
+        else if (SD == 4) scat(k_scatter_points<float, 4>, xf);
+        else scat(k_scatter_points<float, 8>, xf);
+    } else {
+        if (SD == 2) scat(k_scatter_points<double, 2>, xd);
+        else if (SD == 4) scat(k_scatter_points<double, 4>, xd);
+        else scat(k_scatter_points<double, 8>, xd);
+    }
+}
+
+void launch_table_reset(const Semisort &S, DevCounters *ctr, cudaStream_t s) {
+    int g = grid_for((const void *)k_table_reset, 256);
+    k_table_reset<<<g, 256, 0, s>>>(S.ht, S.hcnt, S.slots, ctr); count_launch();
 }
 
 // ---------------------------------------------------------------- boxes
@@ -282,39 +385,6 @@ void launch_boxes(int SD, const float *pts, const int *start, const DevCounters 
     count_launch();
 }
 
-// ---------------------------------------------------------------- hash
-__global__ void __launch_bounds__(256) k_hash_clear(ulonglong2 *__restrict__ ht, const DevCounters *ctr) {
-    const uint64_t cap = hash_capacity(ctr->m);
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cap;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        ht[i] = make_ulonglong2(kEmptyKey, 0);
-}
-
-__global__ void __launch_bounds__(256)
-k_hash_insert(ulonglong2 *__restrict__ ht, const uint64_t *__restrict__ cell_key, DevCounters *ctr) {
-    const int m = ctr->m;
-    const uint64_t mask = hash_capacity(m) - 1;
-    const int lg = hash_log2(mask + 1);
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
-        const uint64_t key = cell_key[c];
-        uint64_t s = hash_slot(key, lg);
-        bool done = false;
-        for (uint64_t it = 0; it <= mask; ++it) {
-            unsigned long long prev = atomicCAS(&ht[s].x, (unsigned long long)kEmptyKey, (unsigned long long)key);
-            if (prev == kEmptyKey) { ht[s].y = (unsigned long long)c; done = true; break; }
-            s = (s + 1) & mask;
-        }
-        if (!done) set_error(ctr, DBSCAN_ERR_CAPACITY, 10);
-    }
-}
-
-void launch_hash(ulonglong2 *ht, const uint64_t *cell_key, DevCounters *ctr, cudaStream_t s) {
-    int g = grid_for((const void *)k_hash_clear, 256);
-    k_hash_clear<<<g, 256, 0, s>>>(ht, ctr); count_launch();
-    g = grid_for((const void *)k_hash_insert, 256);
-    k_hash_insert<<<g, 256, 0, s>>>(ht, cell_key, ctr); count_launch();
-}
-
 // ---------------------------------------------------------------- neighbours
 // NeighborCells(g) (Algorithm 2): every non-empty cell h != g whose integer
 // offset delta from g satisfies sum_j max(|delta_j| - 1, 0)^2 <= d, looked up
@@ -328,13 +398,12 @@ constexpr int NB_U = 4;
 
 template <int D>
 __global__ void __launch_bounds__(256)
-k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict__ ht, RunParams P,
+k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict__ ht, uint64_t mask, int lg,
+            RunParams P,
             const signed char *__restrict__ offs, int noff, int n_near, const float4 *__restrict__ blo,
             const float4 *__restrict__ bhi, int *__restrict__ nbr_cnt, int *__restrict__ nbr_near,
             int *__restrict__ nbr, DevCounters *ctr) {
     const int m = ctr->m;
-    const uint64_t mask = hash_capacity(m) - 1;
-    const int lg = hash_log2(mask + 1);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     long long total = 0;
@@ -406,12 +475,14 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
     if (lane == 0 && total) atomicAdd((unsigned long long *)&ctr->E, (unsigned long long)total);
 }
 
-void launch_neighbors(const uint64_t *cell_key, const ulonglong2 *ht, const RunParams &P,
+void launch_neighbors(const uint64_t *cell_key, const ulonglong2 *ht, uint64_t hcap, const RunParams &P,
                       const signed char *offs, int noff, int n_near, const float4 *blo, const float4 *bhi,
                       int *nbr_cnt, int *nbr_near, int *nbr, DevCounters *ctr, cudaStream_t s) {
+    const uint64_t mask = hcap - 1;
+    const int lg = hash_log2(hcap);
     auto go = [&](auto k) {
         int g = grid_for((const void *)k, 256);
-        k<<<g, 256, 0, s>>>(cell_key, ht, P, offs, noff, n_near, blo, bhi, nbr_cnt, nbr_near, nbr, ctr);
+        k<<<g, 256, 0, s>>>(cell_key, ht, mask, lg, P, offs, noff, n_near, blo, bhi, nbr_cnt, nbr_near, nbr, ctr);
         count_launch();
     };
     switch (P.d) {

@@ -17,11 +17,32 @@ inline double bbox_key_to_double(long long k) {
 }
 void launch_keys(const void *X, int dtype, const RunParams &P, uint64_t *keys, uint32_t *vals,
                  cudaStream_t s);
-void launch_cells(const void *X, int dtype, int n, int d, int SD, int ib, const uint64_t *K, const uint32_t *V,
-                  int *flags, int *cid, long long *part, float *pf, double *pd, int *orig,
-                  int *cell_of, int *cell_start, uint64_t *cell_key, DevCounters *ctr, cudaStream_t s);
-void launch_hash(ulonglong2 *ht, const uint64_t *cell_key, DevCounters *ctr, cudaStream_t s);
-void launch_neighbors(const uint64_t *cell_key, const ulonglong2 *ht, const RunParams &P,
+// Buffers of the cell grouping (semisort) of one run.
+struct Semisort {
+    const void *unused;
+    ulonglong2 *ht;       // cell hash, hcap slots {key, cell id}; empty between runs
+    unsigned *hcnt;       // points per slot; zero between runs
+    uint64_t hcap;        // power of two >= 2 * max points
+    uint32_t *slot_of, *rank_of;  // [n] slot of each point, its position in the cell
+    uint32_t *slots;      // [m] slots of the non-empty cells, in insertion order
+    uint64_t *k0, *k1;    // sort of the m cell keys
+    uint32_t *v0, *v1;
+    void *sort_scratch;
+    long long *part;
+    uint64_t *cell_key;   // [m] keys in Z order
+    int *count;           // [m+1] points per cell (scratch for the scan)
+    int *cell_start;      // [m+1]
+    float *pf;
+    double *pd;           // null unless FP64 input
+    int *orig, *cell_of;
+};
+// Group the points by cell: fills cell_key, cell_start, pf/pd, orig, cell_of,
+// ctr->m, and the slots' cell ids.
+void launch_semisort(const void *X, int dtype, const RunParams &P, int SD, const Semisort &S, DevCounters *ctr,
+                     cudaStream_t s);
+// Empty the slots the run used (keeps the table clean for the next run).
+void launch_table_reset(const Semisort &S, DevCounters *ctr, cudaStream_t s);
+void launch_neighbors(const uint64_t *cell_key, const ulonglong2 *ht, uint64_t hcap, const RunParams &P,
                       const signed char *offs, int noff, int n_near, const float4 *blo, const float4 *bhi,
                       int *nbr_cnt, int *nbr_near, int *nbr, DevCounters *ctr, cudaStream_t s);
 // per-cell FP32 bounding boxes of pts[start[c] .. start[c+1])

@@ -40,14 +40,15 @@ struct RunParams {
     int d;        // real dimension
     int min_pts;  // clamped to n + 1
     int bits;     // Morton bits per dimension
-    int ib;       // bits of the point index packed under the cell key (0: separate values)
     int max_iters;
     int stats;    // count distance evaluations
     int box;      // cell bounding boxes prune pairs (FP32-band mode only)
     double eps2;  // fl(eps * eps), the FP64 threshold
     float lo, hi; // FP32 band: <= lo is in, > hi is out, otherwise FP64 recheck
     double inv_s; // 1 / cell side
+    float inv_s32;  // fl32(inv_s), for the FP32 estimate of the cell coordinates
     double origin[kMaxDim];
+    float origin32[kMaxDim];  // fl32(origin): exact for FP32 input (a minimum of FP32 values)
     int kmax[kMaxDim];  // largest cell coordinate per dimension
 };
 

@@ -71,7 +71,8 @@ size_t carve(dbscan_ctx *c, unsigned char *base) {
         {(void **)&c->k0, 8 * (size_t)N}, {(void **)&c->k1, 8 * (size_t)N},
         {(void **)&c->v0, 4 * (size_t)N}, {(void **)&c->v1, 4 * (size_t)N},
         {(void **)&c->sort_scratch, sort_scratch_bytes(N)}, {(void **)&c->part, 8 * (size_t)npart},
-        {(void **)&c->flags, 4 * (size_t)(N + 1)}, {(void **)&c->cid, 4 * (size_t)(N + 1)},
+        {(void **)&c->slot_of, 4 * (size_t)N}, {(void **)&c->rank_of, 4 * (size_t)N},
+        {(void **)&c->slots, 4 * (size_t)N}, {(void **)&c->hcnt, 4 * (size_t)hcap},
         {(void **)&c->pf, 4 * (size_t)N * SD}, {(void **)&c->pd, 8 * (size_t)N * SD},
         {(void **)&c->cpf, 4 * (size_t)N * SD}, {(void **)&c->cpd, 8 * (size_t)N * SD},
         {(void **)&c->orig, 4 * (size_t)N}, {(void **)&c->cell_of, 4 * (size_t)N},
@@ -124,6 +125,14 @@ dbscan_status setup_device(int dev) {
             return DBSCAN_ERR_CUDA;
         }
     }
+    c.hcap = hash_capacity((int)kStaticMaxPoints);
+    e = cudaMemset(c.ht, 0xff, sizeof(ulonglong2) * c.hcap);
+    if (e == cudaSuccess) e = cudaMemset(c.hcnt, 0, sizeof(unsigned) * c.hcap);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return DBSCAN_ERR_CUDA;
+    }
+    c.table_clean = true;
     c.h_ctr = &st.h_ctr;
     c.h_bbox = st.h_bbox;
     st.ready = true;

@@ -234,12 +234,17 @@ k_radix_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ v
     uint64_t k[RS_ITEMS];
     uint32_t v[RS_ITEMS];
     int r[RS_ITEMS];
+    // issue every load of the tile before ranking, so they overlap
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; ++j) {
+        const int64_t i = wbase + j * 32 + lane;
+        k[j] = i < n ? kin[i] : 0;
+        if (KV) v[j] = i < n ? vin[i] : 0;
+    }
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {
         const int64_t i = wbase + j * 32 + lane;
         const bool ok = i < n;
-        k[j] = ok ? kin[i] : 0;
-        if (KV) v[j] = ok ? vin[i] : 0;
         const unsigned dig = ok ? (unsigned)((k[j] >> shift) & 255u) : 0xffffffffu;
         const unsigned peers = __match_any_sync(0xffffffffu, dig);
         const int before = ok ? wcnt[warp][dig] : 0;
