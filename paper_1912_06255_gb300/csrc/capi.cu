@@ -11,6 +11,7 @@
 #include "ctx.cuh"
 #include "geom.cuh"
 #include "grid.cuh"
+#include "inst.cuh"
 
 using namespace gbdb;
 
@@ -63,32 +64,6 @@ namespace {
 
 constexpr int kVersion = 100;  // 0.1.0
 
-
-// FP32 band around T = fl(eps^2).  f is the FP32 value of sum (p'_i - q'_i)^2
-// for coordinates p', q' rounded to FP32 (each within E_coord of the input);
-// E is the resulting bound on |‖p'-q'‖ - ‖p-q‖|.  With the forward-error bounds
-// |f - ‖p'-q'‖^2| <= g32 ‖p'-q'‖^2 and |fl64(d^2) - d^2| <= g64 d^2 (sums of
-// non-negative rounded terms), f <= lo implies the FP64 predicate holds and
-// f > hi implies it fails:
-//   lo = (1 - g32) (sqrt(T / (1 + g64)) - E)^2,  hi = (1 + g32) (sqrt(T / (1 - g64)) + E)^2.
-// Rounding of this host arithmetic is absorbed by 2^-40 margins.
-bool fp32_band(double T, int d, double E, float *lo, float *hi) {
-    if (!(T >= 0x1p-60 && T <= 0x1p60)) return false;
-    const double g32 = 2.0 * (d + 2) * 0x1p-24, g64 = 2.0 * (d + 2) * 0x1p-53;
-    const double rT = std::sqrt(T);
-    if (!(E <= 0.25 * rT)) return false;
-    const double a = std::sqrt(T / (1.0 + g64)) * (1.0 - 0x1p-40) - E;
-    const double b = std::sqrt(T / (1.0 - g64)) * (1.0 + 0x1p-40) + E;
-    const double lo_d = (1.0 - g32) * a * a * (1.0 - 0x1p-40);
-    const double hi_d = (1.0 + g32) * b * b * (1.0 + 0x1p-40);
-    float l = (float)lo_d, h = (float)hi_d;
-    if ((double)l > lo_d) l = std::nextafter(l, -INFINITY);
-    if ((double)h < hi_d) h = std::nextafter(h, INFINITY);
-    if (!(l > 0.0f) || !std::isfinite(h)) return false;
-    *lo = l;
-    *hi = h;
-    return true;
-}
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -173,6 +148,7 @@ void dbscan_destroy(dbscan_ctx *c) {
     cudaFree(c->d_lab_h);
     cudaFreeHost(c->h_ctr);
     cudaFreeHost(c->h_bbox);
+    cudaFreeHost(c->h_inst);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
     delete c;
@@ -217,6 +193,7 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
         {(void **)&c->core_s, 4 * (size_t)N}, {(void **)&c->core_pos, 4 * (size_t)(N + 1)},
         {(void **)&c->ccs, 4 * (size_t)(N + 1)}, {(void **)&c->core_orig, 4 * (size_t)N},
         {(void **)&c->core_cell, 4 * (size_t)N}, {(void **)&c->rank, 4 * (size_t)N},
+        {(void **)&c->cell_inst, 4 * (size_t)N}, {(void **)&c->d_inst, sizeof(Inst)},
         {(void **)&c->blo, 16 * (size_t)N}, {(void **)&c->bhi, 16 * (size_t)N},
         {(void **)&c->cblo, 16 * (size_t)N}, {(void **)&c->cbhi, 16 * (size_t)N},
         {(void **)&c->parent, 4 * (size_t)N}, {(void **)&c->compmin, 4 * (size_t)N},
@@ -235,6 +212,7 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
     for (auto &it : items) { *it.p = (char *)c->arena + at; at += align_up(it.bytes); }
     e = cudaMallocHost((void **)&c->h_ctr, sizeof(DevCounters));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_bbox, sizeof(long long) * (2 * kMaxDim + 1));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_inst, sizeof(Inst));
     for (int k = 0; k < 9 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
     for (int d = 1; d <= kMaxEnumDim && e == cudaSuccess; ++d) {
         std::vector<signed char> t = offset_table(d);
@@ -338,42 +316,39 @@ dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, 
     CK(cudaGetLastError());
     if (c->h_bbox[2 * kMaxDim] != 0) return DBSCAN_ERR_INVALID_ARG;
 
-    // 2. grid parameters: side s = eps/sqrt(d) * (1 - 2^-20) (Sec. 3)
+    // 2. grid parameters (Sec. 3), built on the host from the box
     RunParams P{};
     P.n = (int)n;
     P.d = d;
-    P.min_pts = (int)std::min<int64_t>(min_pts, n + 1);
     P.max_iters = c->max_iters;
     P.stats = c->collect_stats;
-    P.eps2 = eps * eps;
-    const double side = (eps / std::sqrt((double)d)) * (1.0 - 0x1p-20);
-    P.inv_s = 1.0 / side;
-    P.inv_s32 = (float)P.inv_s;
-    int kmax_all = 0;
-    double M = 0.0;
-    for (int j = 0; j < d; ++j) {
-        const double lo = bbox_key_to_double(c->h_bbox[j]), hi = bbox_key_to_double(c->h_bbox[kMaxDim + j]);
-        P.origin[j] = lo;
-        P.origin32[j] = (float)lo;
-        const double t = (hi - lo) * P.inv_s;
-        if (!(t < 0x1p30)) return DBSCAN_ERR_KEY_OVERFLOW;
-        P.kmax[j] = (int)std::floor(t);
-        kmax_all = std::max(kmax_all, P.kmax[j]);
-        M = std::max(M, std::max(std::fabs(lo), std::fabs(hi)));
+    P.ninst = 1;
+    P.inst_shift = 64;
+    {
+        double lo[kMaxDim], hi[kMaxDim];
+        for (int j = 0; j < d; ++j) {
+            lo[j] = bbox_key_to_double(c->h_bbox[j]);
+            hi[j] = bbox_key_to_double(c->h_bbox[kMaxDim + j]);
+        }
+        int fp32 = 0;
+        Inst &I = c->h_inst[0];
+        const int st = build_inst(I, eps, min_pts, (int)n, d, lo, hi, f64, c->precision == DBSCAN_PREC_FP32_RECHECK,
+                                  63, &fp32);
+        if (st != DBSCAN_OK) return (dbscan_status)st;
+        I.row0 = 0;
+        P.min_pts = I.thr.min_pts;
+        P.eps2 = I.thr.eps2;
+        P.lo = I.thr.lo;
+        P.hi = I.thr.hi;
+        c->stats.key_bits = d * I.bits;
+        c->stats.radix_passes = (d * I.bits + 7) / 8;
+        const int mode_sel = fp32 ? (f64 ? kF32FromF64 : kF32FromF32) : (f64 ? kF64FromF64 : kF64FromF32);
+        c->last_mode_sel = mode_sel;
     }
-    int bits = 1;
-    while (bits < 31 && (1 << bits) <= kmax_all) ++bits;
-    P.bits = bits;
-    if (d * bits > 63) return DBSCAN_ERR_KEY_OVERFLOW;
-    c->stats.key_bits = d * bits;
-    c->stats.radix_passes = (d * bits + 7) / 8;
-
-    // precision mode and FP32 band
-    int mode = f64 ? kF64FromF64 : kF64FromF32;
-    if (c->precision == DBSCAN_PREC_FP32_RECHECK) {
-        const double E = f64 ? std::sqrt((double)d) * (2.0 * M * 0x1p-24 + 0x1p-148) : 0.0;
-        if (fp32_band(P.eps2, d, E, &P.lo, &P.hi)) mode = f64 ? kF32FromF64 : kF32FromF32;
-    }
+    const int mode = c->last_mode_sel;
+    CK(cudaMemcpyAsync(c->d_inst, c->h_inst, sizeof(Inst), cudaMemcpyHostToDevice, s));
+    P.inst = c->d_inst;
+    P.cell_inst = c->cell_inst;
     c->stats.precision = (mode == kF32FromF32 || mode == kF32FromF64) ? DBSCAN_PREC_FP32_RECHECK : DBSCAN_PREC_FP64;
     P.box = c->stats.precision == DBSCAN_PREC_FP32_RECHECK && c->cell_bounds ? 1 : 0;
     c->stats.band_lo = P.lo;
@@ -406,6 +381,8 @@ dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, 
     S.pd = f64 ? c->pd : nullptr;
     S.orig = c->orig;
     S.cell_of = c->cell_of;
+    S.cell_inst = c->cell_inst;
+    S.key_bits = c->stats.key_bits;
     launch_semisort(d_points, dtype, P, SD, S, c->ctr, s);
 
     // 4. cell boxes, neighbour lists

@@ -52,7 +52,8 @@ constexpr int MC_THREADS = 256, MC_WARPS = MC_THREADS / 32, MC_OWN = 128;
 // One batch of kb <= 32*NS own points of a sparse cell whose k points start at
 // s0 (the batch starts at own index b0); own[] holds the batch.
 template <int D, int M, int NS>
-__device__ __forceinline__ void mc_batch(const RunParams &P, const float *__restrict__ pf, const double *__restrict__ pd,
+__device__ __forceinline__ void mc_batch(const RunParams &P, const Thr &T, const float *__restrict__ pf,
+                                         const double *__restrict__ pd,
                                          const int *__restrict__ cell_start, const int *__restrict__ nl, int ne,
                                          const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
                                          const Pt<D, M> *own, int s0, int b0, int k, int kb, int *__restrict__ core_s,
@@ -91,8 +92,8 @@ __device__ __forceinline__ void mc_batch(const RunParams &P, const float *__rest
                     bool partial = false;
                     if (!((done[s] >> lane) & 1u)) {
                         if constexpr (BOX) {
-                            if (box_max_d2<D>(mine[s].f, lo, hi) <= P.lo) cnt[s] += t1 - t0;
-                            else partial = box_min_d2<D>(mine[s].f, lo, hi) <= P.hi;
+                            if (box_max_d2<D>(mine[s].f, lo, hi) <= T.lo) cnt[s] += t1 - t0;
+                            else partial = box_min_d2<D>(mine[s].f, lo, hi) <= T.hi;
                         }
                     }
                     part[s] = __ballot_sync(0xffffffffu, partial);
@@ -120,19 +121,19 @@ __device__ __forceinline__ void mc_batch(const RunParams &P, const float *__rest
                         bool hit = false;
                         if (qv) {
                             if (P.stats) ++evals;
-                            hit = within(own[i], q, P, pd, s0 + b0 + i, pd, t, rech);
+                            hit = within(own[i], q, T, pd, s0 + b0 + i, pd, t, rech);
                         }
                         const int got = __popc(__ballot_sync(0xffffffffu, hit));
                         if (lane == src) cnt[s] += got;
                     }
-                    part[s] &= ~__ballot_sync(0xffffffffu, cnt[s] >= P.min_pts);
+                    part[s] &= ~__ballot_sync(0xffffffffu, cnt[s] >= T.min_pts);
                     any |= part[s];
                 }
             }
             all = true;
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-                done[s] |= __ballot_sync(0xffffffffu, cnt[s] >= P.min_pts);
+                done[s] |= __ballot_sync(0xffffffffu, cnt[s] >= T.min_pts);
                 all = all && done[s] == 0xffffffffu;
             }
         }
@@ -140,7 +141,7 @@ __device__ __forceinline__ void mc_batch(const RunParams &P, const float *__rest
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         const int i = s * 32 + lane;
-        if (i < kb) core_s[s0 + b0 + i] = cnt[s] >= P.min_pts ? 1 : 0;
+        if (i < kb) core_s[s0 + b0 + i] = cnt[s] >= T.min_pts ? 1 : 0;
     }
 }
 
@@ -157,7 +158,8 @@ k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__
     unsigned long long evals = 0;
     for (int c = warp_id_global(); c < m; c += warps_global()) {
         const int s0 = cell_start[c], k = cell_start[c + 1] - s0;
-        if (k >= P.min_pts) {
+        const Thr T = P.inst[inst_of_cell(P, c)].thr;
+        if (k >= T.min_pts) {
             for (int i = lane; i < k; i += 32) core_s[s0 + i] = 1;
             continue;
         }
@@ -169,11 +171,11 @@ k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__
             for (int i = lane; i < kb; i += 32) load_pt(own[w][i], pf, pd, s0 + b0 + i);
             __syncwarp();
             if (kb <= 32)
-                mc_batch<D, M, 1>(P, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, rech, evals);
+                mc_batch<D, M, 1>(P, T, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, rech, evals);
             else if (kb <= 64)
-                mc_batch<D, M, 2>(P, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, rech, evals);
+                mc_batch<D, M, 2>(P, T, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, rech, evals);
             else
-                mc_batch<D, M, 4>(P, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, rech, evals);
+                mc_batch<D, M, 4>(P, T, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, rech, evals);
         }
     }
     flush_counter(&ctr->band_rechecks, rech);
@@ -295,7 +297,7 @@ const uint32_t *launch_schedule(int sched, const RunParams &P, const Bufs &B, De
 // warp covers 32/L rows per step (L = lanes per row).
 template <int D, int M>
 __device__ __forceinline__ bool bcp_warp(int r0, int nr, int c0, int nc, const float *__restrict__ cpf,
-                                         const double *__restrict__ cpd, const RunParams &P,
+                                         const double *__restrict__ cpd, const RunParams &P, const Thr &T,
                                          unsigned &rech, unsigned long long &evals) {
     const int lane = threadIdx.x & 31;
     if (nc <= 32) {
@@ -314,7 +316,7 @@ __device__ __forceinline__ bool bcp_warp(int r0, int nr, int c0, int nc, const f
                 Pt<D, M> p;
                 load_pt(p, cpf, cpd, r0 + r);
                 if (P.stats) ++evals;
-                t = within(p, q, P, cpd, r0 + r, cpd, c0 + j, rech);
+                t = within(p, q, T, cpd, r0 + r, cpd, c0 + j, rech);
             }
             if (__any_sync(0xffffffffu, t)) return true;
         }
@@ -331,7 +333,7 @@ __device__ __forceinline__ bool bcp_warp(int r0, int nr, int c0, int nc, const f
                 Pt<D, M> p;
                 load_pt(p, cpf, cpd, r0 + r);
                 if (P.stats) ++evals;
-                t = within(p, q, P, cpd, r0 + r, cpd, c0 + j, rech);
+                t = within(p, q, T, cpd, r0 + r, cpd, c0 + j, rech);
             }
             if (__any_sync(0xffffffffu, t)) return true;
         }
@@ -414,9 +416,10 @@ k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict
             // eps -> not connected; every pair within eps -> connected
             int verdict = 0;
             if (use_box && cand) {
+                const Thr T = P.inst[inst_of_cell(P, a)].thr;
                 const float4 alo = cblo[a], ahi = cbhi[a], blo = cblo[b], bhi = cbhi[b];
-                if (boxes_min_d2<D>(alo, ahi, blo, bhi) > P.hi) verdict = -1;
-                else if (boxes_max_d2<D>(alo, ahi, blo, bhi) <= P.lo) verdict = 1;
+                if (boxes_min_d2<D>(alo, ahi, blo, bhi) > T.hi) verdict = -1;
+                else if (boxes_max_d2<D>(alo, ahi, blo, bhi) <= T.lo) verdict = 1;
             }
             // union-find check: in the near wave only the current parents are
             // compared (trees are being built); the far wave runs after every
@@ -443,8 +446,9 @@ k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict
                 if (lane == 0) again = uf_find(parent, sa, P.max_iters, ctr) == uf_find(parent, sb, P.max_iters, ctr);
                 if (__shfl_sync(0xffffffffu, again, 0)) { ++skipped; continue; }
                 ++tested;
-                const bool hit = sna >= snb ? bcp_warp<D, M>(sa0, sna, sb0, snb, cpf, cpd, P, rech, evals)
-                                            : bcp_warp<D, M>(sb0, snb, sa0, sna, cpf, cpd, P, rech, evals);
+                const Thr T = P.inst[inst_of_cell(P, sa)].thr;
+                const bool hit = sna >= snb ? bcp_warp<D, M>(sa0, sna, sb0, snb, cpf, cpd, P, T, rech, evals)
+                                            : bcp_warp<D, M>(sb0, snb, sa0, sna, cpf, cpd, P, T, rech, evals);
                 if (hit) {
                     ++linked;
                     if (lane == 0) uf_link(parent, sa, sb, P.max_iters, ctr);
@@ -539,7 +543,10 @@ k_label_core(RunParams P, const int *__restrict__ core_s, const int *__restrict_
             const int o = orig[i];
             const int cf = core_s[i];
             core_out[o] = (uint8_t)cf;
-            if (cf) labels_out[o] = compmin[parent[cell_of[i]]];
+            if (cf) {
+                const int c = cell_of[i];
+                labels_out[o] = compmin[parent[c]] - P.inst[inst_of_cell(P, c)].row0;
+            }
             nc = !cf;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, nc);
@@ -590,6 +597,9 @@ k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restr
         const int i = B.noncore[t];
         const int g = B.cell_of[i];
         const int o = B.orig[i];
+        const Inst &I = P.inst[inst_of_cell(P, g)];
+        const Thr T = I.thr;
+        const int row0 = I.row0;
         Pt<D, M> p;
         load_pt(p, B.pf, B.pd, i);
         int ns = 0;
@@ -599,7 +609,7 @@ k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restr
             const int h = e < 0 ? g : nl[e];
             const int k0 = B.ccs[h], k1 = B.ccs[h + 1];
             if (k0 == k1) continue;
-            const int L = B.compmin[B.parent[h]];
+            const int L = B.compmin[B.parent[h]] - row0;
             bool have = false;
             for (int u = lane; u < ns; u += 32) have = have || sset[w][u] == L;
             if (__any_sync(0xffffffffu, have)) continue;
@@ -607,8 +617,8 @@ k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restr
             if constexpr (M == kF32FromF32 || M == kF32FromF64) {
                 if (P.box) {
                     const float4 lo = B.cblo[h], hi = B.cbhi[h];
-                    if (box_min_d2<D>(p.f, lo, hi) > P.hi) continue;  // no core point of h within eps
-                    found = box_max_d2<D>(p.f, lo, hi) <= P.lo;      // every core point of h within eps
+                    if (box_min_d2<D>(p.f, lo, hi) > T.hi) continue;  // no core point of h within eps
+                    found = box_max_d2<D>(p.f, lo, hi) <= T.lo;      // every core point of h within eps
                 }
             }
             for (int kb = k0; kb < k1 && !found; kb += 32) {
@@ -618,7 +628,7 @@ k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restr
                     Pt<D, M> q;
                     load_pt(q, B.cpf, B.cpd, k);
                     if (P.stats) ++evals;
-                    hit = within(p, q, P, B.pd, i, B.cpd, k, rech);
+                    hit = within(p, q, T, B.pd, i, B.cpd, k, rech);
                 }
                 found = __any_sync(0xffffffffu, hit);
             }

@@ -50,6 +50,10 @@ struct dbscan_ctx {
     long long nbr_cap = 0;
     int *core_s = nullptr, *core_pos = nullptr, *ccs = nullptr, *core_orig = nullptr, *core_cell = nullptr;
     int *rank = nullptr;
+    int *cell_inst = nullptr;      // [N] instance of each cell (batches)
+    gbdb::Inst *d_inst = nullptr;  // instance table (device), one entry for single runs
+    gbdb::Inst *h_inst = nullptr;  // pinned host copy
+    int last_mode_sel = 0;
     float4 *blo = nullptr, *bhi = nullptr, *cblo = nullptr, *cbhi = nullptr;  // cell / core-point boxes
     int *parent = nullptr, *compmin = nullptr;
     int *noncore = nullptr;

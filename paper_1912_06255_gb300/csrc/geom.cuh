@@ -88,7 +88,7 @@ __device__ __forceinline__ void load_pt(Pt<D, M> &p, const float *__restrict__ p
 // the recheck of the FP32-band mode on FP64 storage.  *rechecks counts FP32
 // decisions sent to FP64.
 template <int D, int M>
-__device__ __forceinline__ bool within(const Pt<D, M> &p, const Pt<D, M> &q, const RunParams &P,
+__device__ __forceinline__ bool within(const Pt<D, M> &p, const Pt<D, M> &q, const Thr &P,
                                        const double *__restrict__ pdp, int64_t ip,
                                        const double *__restrict__ pdq, int64_t iq,
                                        unsigned &rechecks) {

@@ -127,19 +127,37 @@ void launch_bbox(const void *X, int dtype, int n, int d, int nb, long long *out,
 // of FP32 values are exact FP32 numbers), so when t32 is farther than eps_t
 // from an integer both floors agree; only the rest is recomputed in FP64.
 template <typename T>
-__device__ __forceinline__ int cell_coord(T x, const RunParams &P, int j) {
+__device__ __forceinline__ int cell_coord(T x, const Inst &I, int j) {
     if constexpr (sizeof(T) == 4) {
-        const float t32 = __fmul_rn(__fsub_rn(x, P.origin32[j]), P.inv_s32);
+        const float t32 = __fmul_rn(__fsub_rn(x, I.origin32[j]), I.inv_s32);
         const float fl = floorf(t32);
         const float e = t32 * 1.8e-7f + 1e-30f;
         if (t32 - fl > e && (fl + 1.0f) - t32 > e) {
             const int k = (int)fl;
-            return k < 0 ? 0 : (k > P.kmax[j] ? P.kmax[j] : k);
+            return k < 0 ? 0 : (k > I.kmax[j] ? I.kmax[j] : k);
         }
     }
-    const double t = __dmul_rn(__dsub_rn((double)x, P.origin[j]), P.inv_s);
+    const double t = __dmul_rn(__dsub_rn((double)x, I.origin[j]), I.inv_s);
     const int k = (int)floor(t);
-    return k < 0 ? 0 : (k > P.kmax[j] ? P.kmax[j] : k);
+    return k < 0 ? 0 : (k > I.kmax[j] ? I.kmax[j] : k);
+}
+
+// Instance of input row i: the last instance whose first row is <= i.
+__device__ __forceinline__ int inst_of_row(const RunParams &P, int i) {
+    int lo = 0, hi = P.ninst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.inst[mid].row0 <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Cell key: Morton code of the cell coordinates, under the instance id when
+// the run holds several instances.
+__device__ __forceinline__ uint64_t cell_key_of(const RunParams &P, int inst, const int *c, int bits) {
+    const uint64_t k = morton_encode(c, P.d, bits);
+    return P.ninst > 1 ? (((uint64_t)inst << P.inst_shift) | k) : k;
 }
 
 constexpr int INS_U = 4;  // points per thread per step (their probes overlap)
@@ -159,10 +177,13 @@ k_insert(const T *__restrict__ X, RunParams P, ulonglong2 *__restrict__ ht, unsi
             key[u] = 0;
             s[u] = 0;
             if (i < P.n) {
+                const int ii = P.ninst > 1 ? inst_of_row(P, i) : 0;
+                const Inst &I = P.inst[ii];
                 int c[kMaxDim];
 #pragma unroll
-                for (int j = 0; j < kMaxDim; ++j) c[j] = j < P.d ? cell_coord<T>(X[(int64_t)i * P.d + j], P, j) : 0;
-                key[u] = morton_encode(c, P.d, P.bits);
+                for (int j = 0; j < kMaxDim; ++j)
+                    c[j] = j < I.d ? cell_coord<T>(X[(int64_t)i * P.d + j], I, j) : 0;
+                key[u] = cell_key_of(P, ii, c, I.bits);
                 s[u] = hash_slot(key[u], hlg);
             }
         }
@@ -224,15 +245,16 @@ k_cell_keys(const ulonglong2 *__restrict__ ht, const uint32_t *__restrict__ slot
 // Cell c (in key order) owns slot vals[c]: record its id in the slot, its key
 // and its point count.
 __global__ void __launch_bounds__(256)
-k_cell_table(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, ulonglong2 *__restrict__ ht,
-             const unsigned *__restrict__ hcnt, uint64_t *__restrict__ cell_key, int *__restrict__ count,
-             const DevCounters *ctr) {
+k_cell_table(RunParams P, const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+             ulonglong2 *__restrict__ ht, const unsigned *__restrict__ hcnt, uint64_t *__restrict__ cell_key,
+             int *__restrict__ count, int *__restrict__ cell_inst, const DevCounters *ctr) {
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
         const uint32_t s = vals[c];
         ht[s].y = (unsigned long long)c;
         cell_key[c] = keys[c];
         count[c] = (int)hcnt[s];
+        if (P.ninst > 1) cell_inst[c] = (int)(keys[c] >> P.inst_shift);
     }
 }
 
@@ -301,12 +323,12 @@ void launch_semisort(const void *X, int dtype, const RunParams &P, int SD, const
     count_launch();
     int g = grid_for((const void *)k_cell_keys, 256);
     k_cell_keys<<<g, 256, 0, s>>>(S.ht, S.slots, S.k0, S.v0, ctr); count_launch();
-    const int which = radix_sort_u64(S.k0, S.v0, S.k1, S.v1, 0, &ctr->m, P.n, 0, P.d * P.bits, S.sort_scratch,
-                                     ctr, P.max_iters, s);
+    const int which = radix_sort_u64(S.k0, S.v0, S.k1, S.v1, 0, &ctr->m, P.n, 0, S.key_bits, S.sort_scratch, ctr,
+                                     P.max_iters, s);
     const uint64_t *K = which ? S.k1 : S.k0;
     const uint32_t *V = which ? S.v1 : S.v0;
     g = grid_for((const void *)k_cell_table, 256);
-    k_cell_table<<<g, 256, 0, s>>>(K, V, S.ht, S.hcnt, S.cell_key, S.count, ctr); count_launch();
+    k_cell_table<<<g, 256, 0, s>>>(P, K, V, S.ht, S.hcnt, S.cell_key, S.count, S.cell_inst, ctr); count_launch();
     scan_i32_to_i32(S.count, S.cell_start, 0, &ctr->m, P.n, S.part, s);
     auto scat = [&](auto k, auto xp) {
         int gg = grid_for((const void *)k, 256);
@@ -408,17 +430,21 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
     const unsigned lt = (1u << lane) - 1u;
     long long total = 0;
     for (int c = warp_id_global(); c < m; c += warps_global()) {
-        const uint64_t ckey = cell_key[c];
+        const int ii = inst_of_cell(P, c);
+        const Inst &I = P.inst[ii];
+        const uint64_t ibits = P.ninst > 1 ? ((uint64_t)ii << P.inst_shift) : 0;
+        const uint64_t ckey = cell_key[c] ^ ibits;  // Morton part
         int cc[D];
         {
             int tmp[kMaxDim];
-            morton_decode(ckey, D, P.bits, tmp);
+            morton_decode(ckey, D, I.bits, tmp);
 #pragma unroll
             for (int j = 0; j < D; ++j) cc[j] = tmp[j];
         }
         const long long base = (long long)c * noff;
         float4 clo = make_float4(0.f, 0.f, 0.f, 0.f), chi = clo;
         if (P.box) { clo = blo[c]; chi = bhi[c]; }
+        const float hi_thr = I.thr.hi;
         int cnt = 0, near = 0;
         for (int o0 = 0; o0 < noff; o0 += 32 * NB_U) {
             uint64_t key[NB_U], slot[NB_U];
@@ -435,11 +461,11 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
                     for (int j = 0; j < D; ++j) {
                         dl[j] = (int)offs[o * kMaxEnumDim + j];
                         nc[j] = cc[j] + dl[j];
-                        act[u] = act[u] && nc[j] >= 0 && nc[j] <= P.kmax[j];
+                        act[u] = act[u] && nc[j] >= 0 && nc[j] <= I.kmax[j];
                     }
                     if (act[u]) {
-                        if constexpr (D == 2 || D == 3) key[u] = morton_offset<D>(ckey, dl);
-                        else key[u] = morton_encode(nc, D, P.bits);
+                        if constexpr (D == 2 || D == 3) key[u] = morton_offset<D>(ckey, dl) | ibits;
+                        else key[u] = morton_encode(nc, D, I.bits) | ibits;
                         slot[u] = hash_slot(key[u], lg);
                     }
                 }
@@ -459,7 +485,7 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
                         e[u] = ht[s];
                     }
                     // drop cells whose points are all farther than eps from all of c's
-                    if (h >= 0 && P.box && boxes_min_d2<D>(clo, chi, blo[h], bhi[h]) > P.hi) h = -1;
+                    if (h >= 0 && P.box && boxes_min_d2<D>(clo, chi, blo[h], bhi[h]) > hi_thr) h = -1;
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, h >= 0);
                 if (h >= 0) nbr[base + cnt + __popc(bal & lt)] = h;

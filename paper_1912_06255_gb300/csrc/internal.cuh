@@ -34,23 +34,47 @@ struct DevCounters {
     unsigned long long dist_evals[3];  // MarkCore, BCP, border
 };
 
+// Decision thresholds of one problem instance.
+struct Thr {
+    double eps2;  // fl(eps * eps), the FP64 threshold
+    float lo, hi; // FP32 band: <= lo is in, > hi is out, otherwise FP64 recheck
+    int min_pts;  // clamped to n + 1
+};
+
+// Grid and thresholds of one problem instance (one entry per instance of a
+// batch; a single run has one).
+struct Inst {
+    double origin[kMaxDim];   // per-dimension minimum of the instance's points
+    float origin32[kMaxDim];  // fl32(origin): exact for FP32 input (a minimum of FP32 values)
+    double inv_s;             // 1 / cell side
+    float inv_s32;            // fl32(inv_s), for the FP32 estimate of the cell coordinates
+    int kmax[kMaxDim];        // largest cell coordinate per dimension
+    int bits;                 // Morton bits per dimension
+    int d;                    // the instance's dimension (<= the storage dimension)
+    int row0, n;              // rows [row0, row0 + n) of the input
+    Thr thr;
+};
+
 // Per-run scalars passed by value to the kernels.
 struct RunParams {
-    int n;        // points
-    int d;        // real dimension
-    int min_pts;  // clamped to n + 1
-    int bits;     // Morton bits per dimension
+    int n;        // points (all instances)
+    int d;        // storage dimension (padded coordinates are zero)
     int max_iters;
     int stats;    // count distance evaluations
     int box;      // cell bounding boxes prune pairs (FP32-band mode only)
-    double eps2;  // fl(eps * eps), the FP64 threshold
-    float lo, hi; // FP32 band: <= lo is in, > hi is out, otherwise FP64 recheck
-    double inv_s; // 1 / cell side
-    float inv_s32;  // fl32(inv_s), for the FP32 estimate of the cell coordinates
-    double origin[kMaxDim];
-    float origin32[kMaxDim];  // fl32(origin): exact for FP32 input (a minimum of FP32 values)
-    int kmax[kMaxDim];  // largest cell coordinate per dimension
+    int ninst;    // instances; 1 for a single run
+    int inst_shift;  // instance id sits in key bits >= inst_shift (ninst > 1)
+    const Inst *inst;     // [ninst] device
+    const int *cell_inst; // [m] device: instance of each cell (ninst > 1)
+    // copies of instance 0 for single runs (host side convenience)
+    int min_pts;
+    double eps2;
+    float lo, hi;
 };
+
+__device__ __forceinline__ int inst_of_cell(const RunParams &P, int c) {
+    return P.ninst > 1 ? P.cell_inst[c] : 0;
+}
 
 // Storage width of a point: 2, 4 or 8 coordinates (zero padded).
 template <int D> struct Store { static constexpr int SD = D <= 2 ? 2 : (D <= 4 ? 4 : 8); };

@@ -43,6 +43,7 @@ struct StaticState {
     dbscan_ctx ctx;                // views into g_static_scratch of this device
     gbdb::DevCounters h_ctr;       // host copies read back by the run
     long long h_bbox[2 * kMaxDim + 1];
+    gbdb::Inst h_inst;
 };
 
 StaticState g_state[kMaxDevices];
@@ -83,6 +84,7 @@ size_t carve(dbscan_ctx *c, unsigned char *base) {
         {(void **)&c->core_s, 4 * (size_t)N}, {(void **)&c->core_pos, 4 * (size_t)(N + 1)},
         {(void **)&c->ccs, 4 * (size_t)(N + 1)}, {(void **)&c->core_orig, 4 * (size_t)N},
         {(void **)&c->core_cell, 4 * (size_t)N}, {(void **)&c->rank, 4 * (size_t)N},
+        {(void **)&c->cell_inst, 4 * (size_t)N}, {(void **)&c->d_inst, sizeof(Inst)},
         {(void **)&c->blo, 16 * (size_t)N}, {(void **)&c->bhi, 16 * (size_t)N},
         {(void **)&c->cblo, 16 * (size_t)N}, {(void **)&c->cbhi, 16 * (size_t)N},
         {(void **)&c->parent, 4 * (size_t)N}, {(void **)&c->compmin, 4 * (size_t)N},
@@ -135,6 +137,7 @@ dbscan_status setup_device(int dev) {
     c.table_clean = true;
     c.h_ctr = &st.h_ctr;
     c.h_bbox = st.h_bbox;
+    c.h_inst = &st.h_inst;
     st.ready = true;
     return DBSCAN_OK;
 }
