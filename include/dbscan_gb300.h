@@ -77,7 +77,10 @@ enum {
        the bounding boxes of their points where the boxes settle the question
        (all pairs within eps, or none), as the quadtree range counts of
        Sec. 5.2 do; 0 tests every pair point by point */
-    DBSCAN_OPT_CELL_BOUNDS = 5
+    DBSCAN_OPT_CELL_BOUNDS = 5,
+    /* value: 1 (default) or 0: dbscan_run_batch captures its sequence as a CUDA
+       graph and replays it; 0 enqueues the kernels directly every call */
+    DBSCAN_OPT_BATCH_GRAPH = 6
 };
 enum { DBSCAN_PREC_FP64 = 0, DBSCAN_PREC_FP32_RECHECK = 1 };
 /* SIZE: core-cell pairs are tested in order of non-increasing core count of the
@@ -165,6 +168,42 @@ dbscan_status dbscan_run(dbscan_ctx *ctx, const void *d_points, int64_t n, int d
  * Returns OK, STATE (no run), CAPACITY, INVALID_ARG or CUDA.  Synchronises.
  */
 dbscan_status dbscan_border_ids(dbscan_ctx *ctx, int32_t *d_ids, int64_t capacity, void *stream);
+
+/* One problem of a batch: rows [row0, row0 + n) of the batch's point array,
+ * using the first d of its ld columns. */
+typedef struct {
+    int64_t row0;     /* first row; instance i+1 starts where instance i ends (row0 of 0 is 0) */
+    int64_t n;        /* rows of this instance (0 allowed) */
+    int32_t d;        /* dimension of this instance, 1 <= d <= ld */
+    int32_t reserved; /* set to 0 */
+    double eps;       /* > 0, finite */
+    int64_t min_pts;  /* >= 1 */
+} dbscan_instance;
+
+/*
+ * Exact DBSCAN of count independent instances at once (the batched use of
+ * Algorithm 1): d_points [N, ld] row-major (N = sum of the instances' n, at
+ * most the context's max_points; ld <= max_dim, ld <= 3), element type dtype.
+ * Each instance is clustered on its own, with its own eps and min_pts; the
+ * outputs are indexed by row like the input:
+ *   d_core [N], d_labels [N]: as in dbscan_run(), with cluster names local to
+ *     the instance (the smallest core index counted from the instance's row0);
+ *   d_border_offsets [N+1] or NULL: border-set CSR over all rows (the names in
+ *     it are instance-local too); dbscan_border_ids() fills it afterwards.
+ * All instances go through the same kernels in one pass: each gets its own
+ * grid and thresholds built on the device from its own bounding box.  The
+ * whole sequence is captured as one CUDA graph on the first call and replayed
+ * by later calls with the same count, sizes, pointers, dtype and options (the
+ * coordinates, eps and min_pts may change between calls).  Precision: the FP32
+ * band with FP64 recheck for FP32 input when every eps^2 lies in
+ * [2^-60, 2^60], otherwise FP64.  Synchronises the stream once at the end.
+ * Returns OK, INVALID_ARG, UNSUPPORTED_DIM, KEY_OVERFLOW (an instance's grid
+ * exceeds its share of the 63-bit cell key), CAPACITY, DEVICE_TIMEOUT, OOM or
+ * CUDA.
+ */
+dbscan_status dbscan_run_batch(dbscan_ctx *ctx, const dbscan_instance *h_instances, int count,
+                               const void *d_points, int ld, int dtype, uint8_t *d_core, int32_t *d_labels,
+                               int64_t *d_border_offsets, int64_t *num_border_memberships, void *stream);
 
 /*
  * Same as dbscan_run() but with host buffers: copies h_points to the device,

@@ -43,7 +43,7 @@ class DBSCAN:
 
     def __init__(self, max_points: int, max_dim: int, precision: str = "fp32",
                  schedule: str = "size", collect_stats: bool = False, max_iters: int | None = None,
-                 cell_bounds: bool = True):
+                 cell_bounds: bool = True, graph: bool = True):
         self.lib = _lib.load()
         self.ctx = ctypes.c_void_p()
         _lib.check(self.lib.dbscan_create(ctypes.byref(self.ctx), int(max_points), int(max_dim)),
@@ -55,6 +55,7 @@ class DBSCAN:
         self.set_option(_lib.OPT_SCHEDULE, sched)
         self.set_option(_lib.OPT_COLLECT_STATS, int(bool(collect_stats)))
         self.set_option(_lib.OPT_CELL_BOUNDS, int(bool(cell_bounds)))
+        self.set_option(_lib.OPT_BATCH_GRAPH, int(bool(graph)))
         if max_iters is not None:
             self.set_option(_lib.OPT_MAX_ITERS, int(max_iters))
 
@@ -103,6 +104,46 @@ class DBSCAN:
                                  offs.data_ptr() if offs is not None else None,
                                  ctypes.byref(k), s.cuda_stream)
         _lib.check(st, "dbscan_run")
+        ids = None
+        if border:
+            ids = torch.empty(max(int(k.value), 1), dtype=torch.int32, device=dev)
+            _lib.check(self.lib.dbscan_border_ids(self.ctx, ids.data_ptr(), ids.numel(), s.cuda_stream),
+                       "dbscan_border_ids")
+            ids = ids[: int(k.value)]
+        return Result(core, labels, offs, ids, self.stats())
+
+    def run_batch(self, points, instances, border: bool = True, out=None, stream=None) -> Result:
+        """Cluster independent instances stored one after another in a CUDA
+        tensor [N, ld] (float32 or float64).  ``instances`` lists (n, d, eps,
+        min_pts) in row order; cluster names in the outputs are local to each
+        instance (smallest core index counted from the instance's first row)."""
+        torch = _torch()
+        if not (isinstance(points, torch.Tensor) and points.is_cuda and points.dim() == 2):
+            raise ValueError("points must be a CUDA tensor [N, ld]")
+        pts = points.contiguous()
+        N, ld = pts.shape
+        arr = (_lib.Instance * len(instances))()
+        row = 0
+        for k, (n, d, eps, mp) in enumerate(instances):
+            arr[k].row0, arr[k].n, arr[k].d = row, int(n), int(d)
+            arr[k].reserved, arr[k].eps, arr[k].min_pts = 0, float(eps), int(mp)
+            row += int(n)
+        if row != N:
+            raise ValueError("instance sizes must add up to the number of rows")
+        dev = pts.device
+        if out is None:
+            core = torch.empty(N, dtype=torch.uint8, device=dev)
+            labels = torch.empty(N, dtype=torch.int32, device=dev)
+            offs = torch.empty(N + 1, dtype=torch.int64, device=dev) if border else None
+        else:
+            core, labels, offs = out
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        k = ctypes.c_int64(0)
+        dtype = _lib.F32 if pts.dtype == torch.float32 else _lib.F64
+        _lib.check(self.lib.dbscan_run_batch(self.ctx, arr, len(instances), pts.data_ptr(), ld, dtype,
+                                             core.data_ptr(), labels.data_ptr(),
+                                             offs.data_ptr() if offs is not None else None,
+                                             ctypes.byref(k), s.cuda_stream), "dbscan_run_batch")
         ids = None
         if border:
             ids = torch.empty(max(int(k.value), 1), dtype=torch.int32, device=dev)

@@ -20,6 +20,7 @@ STATUS = {
 }
 F32, F64 = 0, 1
 OPT_PRECISION, OPT_SCHEDULE, OPT_COLLECT_STATS, OPT_MAX_ITERS, OPT_PHASE_TIMING, OPT_CELL_BOUNDS = 0, 1, 2, 3, 4, 5
+OPT_BATCH_GRAPH = 6
 PREC_FP64, PREC_FP32_RECHECK = 0, 1
 SCHED_SIZE, SCHED_NONE = 0, 1
 
@@ -49,6 +50,11 @@ class Stats(ctypes.Structure):
         return out
 
 
+class Instance(ctypes.Structure):
+    _fields_ = [("row0", ctypes.c_int64), ("n", ctypes.c_int64), ("d", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("eps", ctypes.c_double), ("min_pts", ctypes.c_int64)]
+
+
 SIGNATURES = {
     "dbscan_create": (_I32, [ctypes.POINTER(_P), _I64, _I32]),
     "dbscan_destroy": (None, [_P]),
@@ -57,6 +63,8 @@ SIGNATURES = {
     "dbscan_border_ids": (_I32, [_P, _P, _I64, _P]),
     "dbscan_run_host": (_I32, [_P, _P, _I64, _I32, _I32, _D, _I64, _P, _P, _P]),
     "dbscan_run_static": (_I32, [_P, _I64, _I32, _I32, _D, _I64, _P, _P, _P]),
+    "dbscan_run_batch": (_I32, [_P, ctypes.POINTER(Instance), _I32, _P, _I32, _I32, _P, _P, _P,
+                                ctypes.POINTER(_I64), _P]),
     "dbscan_get_stats": (_I32, [_P, ctypes.POINTER(Stats)]),
     "dbscan_status_string": (ctypes.c_char_p, [_I32]),
     "dbscan_version": (_I32, []),

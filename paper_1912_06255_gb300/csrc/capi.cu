@@ -120,6 +120,125 @@ static Bufs make_bufs(dbscan_ctx *c, bool f64) {
     return B;
 }
 
+// Neighbour-offset table of dimension d inside the context.
+static const signed char *offs_for(const dbscan_ctx *c, int d) {
+    return c->offs + (size_t)(d - 1) * kMaxOffsets * kMaxEnumDim;
+}
+
+dbscan_status gbdb_enqueue_batch_prologue(dbscan_ctx *c, const void *d_points, int ld, int dtype, int count,
+                                          long long n_total, int want_fp32, int key_limit, cudaStream_t s);
+dbscan_status gbdb_batch_buffers(dbscan_ctx *c, const dbscan_instance *h, int count);
+void gbdb_batch_free(dbscan_ctx *c);
+
+// Steps 3-10 of a run (cells, boxes, neighbour lists, MarkCore, compaction,
+// schedule, BCP connectivity, labels, border counts), then the reset of the
+// cell hash and the read-back of the device counters, all enqueued on s
+// without a host synchronisation (so a batch can be captured in a graph).
+template <typename MarkFn>
+static dbscan_status enqueue_core(dbscan_ctx *c, const RunParams &P, int D, int SD, int mode, const void *d_points,
+                                  int dtype, int d_enum, int sort_lo, int sort_bits, uint8_t *d_core,
+                                  int32_t *d_labels, int64_t *d_border_offsets, cudaStream_t s, MarkFn mark) {
+    const bool f64 = dtype == DBSCAN_F64;
+    const int64_t n = P.n;
+    // 3. cells: group the points by cell (semisort, Sec. 4.1) through the cell hash
+    mark(2);
+    if (!c->table_clean) {
+        CK(cudaMemsetAsync(c->ht, 0xff, sizeof(ulonglong2) * c->hcap, s));
+        CK(cudaMemsetAsync(c->hcnt, 0, sizeof(unsigned) * c->hcap, s));
+    }
+    c->table_clean = false;
+    Semisort S{};
+    S.ht = c->ht;
+    S.hcnt = c->hcnt;
+    S.hcap = c->hcap;
+    S.slot_of = c->slot_of;
+    S.rank_of = c->rank_of;
+    S.slots = c->slots;
+    S.k0 = c->k0;
+    S.k1 = c->k1;
+    S.v0 = c->v0;
+    S.v1 = c->v1;
+    S.sort_scratch = c->sort_scratch;
+    S.part = c->part;
+    S.cell_key = c->cell_key;
+    S.count = c->core_pos;  // scratch until the compaction
+    S.cell_start = c->cell_start;
+    S.pf = c->pf;
+    S.pd = f64 ? c->pd : nullptr;
+    S.orig = c->orig;
+    S.cell_of = c->cell_of;
+    S.cell_inst = c->cell_inst;
+    S.key_lo = sort_lo;
+    S.key_bits = sort_bits;
+    launch_semisort(d_points, dtype, P, SD, S, c->ctr, s);
+
+    // 4. cell boxes, neighbour lists
+    mark(3);
+    if (P.box) launch_boxes(SD, c->pf, c->cell_start, c->ctr, c->blo, c->bhi, s);
+    int n_near = 1;
+    for (int j = 0; j < d_enum; ++j) n_near *= 3;
+    launch_neighbors(c->cell_key, c->ht, c->hcap, P, offs_for(c, d_enum), c->noff[d_enum], n_near - 1, c->blo,
+                     c->bhi, c->nbr_cnt, c->nbr_near, c->nbr, c->ctr, s);
+
+    // 5. MarkCore, 6. compaction, 7. schedule, 8. connect, 9. labels, 10. border
+    Bufs B = make_bufs(c, f64);
+    B.n_max = n;
+    B.nbr_stride = c->noff[d_enum];
+    mark(4);
+    launch_markcore(D, mode, P, B, c->ctr, s);
+    mark(5);
+    launch_core_compact(SD, P, B, c->ctr, s);
+    const uint32_t *order = launch_schedule(c->sched, P, B, c->ctr, s);
+    mark(6);
+    launch_connect(D, mode, order, P, B, c->ctr, s);
+    mark(7);
+    launch_labels(P, B, d_core, d_labels, c->ctr, s);
+    launch_border(D, mode, false, P, B, d_labels, nullptr, 0, c->ctr, s);
+    mark(8);
+    launch_table_reset(S, c->ctr, s);
+    if (d_border_offsets)
+        CK(cudaMemcpyAsync(d_border_offsets, c->boff, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    return DBSCAN_OK;
+}
+
+// After the stream has been synchronised: counters into stats, state for
+// dbscan_border_ids, status of the run.
+static dbscan_status finish_run(dbscan_ctx *c, const RunParams &P, int D, int mode, const void *d_points, int dtype,
+                                int64_t n, int64_t *num_border_memberships, long long launches0) {
+    c->table_clean = c->h_ctr->err == 0;
+    const DevCounters &h = *c->h_ctr;
+    dbscan_stats &st = c->stats;
+    st.num_cells = h.m;
+    st.num_core_cells = h.m_core;
+    st.num_neighbor_entries = h.E;
+    st.num_candidate_pairs = h.P;
+    st.num_pairs_tested = (int64_t)h.pairs_tested;
+    st.num_pairs_skipped = (int64_t)h.pairs_skipped;
+    st.num_pairs_connected = (int64_t)h.pairs_linked;
+    st.num_pairs_box_decided = (int64_t)h.pairs_box;
+    st.num_core_points = h.n_core;
+    st.num_border_points = h.n_border;
+    st.num_noise_points = n - h.n_core - h.n_border;
+    st.num_border_memberships = h.K;
+    st.band_rechecks = (int64_t)h.band_rechecks;
+    for (int k = 0; k < 3; ++k) st.distance_evals_phase[k] = (int64_t)h.dist_evals[k];
+    st.distance_evals = st.distance_evals_phase[0] + st.distance_evals_phase[1] + st.distance_evals_phase[2];
+    st.kernel_launches = g_launches - launches0;
+    if (c->phase_timing)
+        for (int k = 0; k < 8; ++k) cudaEventElapsedTime(&st.phase_ms[k], c->ev[k], c->ev[k + 1]);
+    if (h.err) return (dbscan_status)h.err;
+    if (num_border_memberships) *num_border_memberships = h.K;
+    c->have_run = true;
+    c->last = P;
+    c->last_D = D;
+    c->last_mode = mode;
+    c->last_points = d_points;
+    c->last_dtype = dtype;
+    return DBSCAN_OK;
+}
+
 extern "C" {
 
 const char *dbscan_status_string(int s) {
@@ -149,6 +268,8 @@ void dbscan_destroy(dbscan_ctx *c) {
     cudaFreeHost(c->h_ctr);
     cudaFreeHost(c->h_bbox);
     cudaFreeHost(c->h_inst);
+    gbdb_batch_free(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
     delete c;
@@ -251,6 +372,10 @@ dbscan_status dbscan_set_option(dbscan_ctx *c, int option, int64_t value) {
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
         c->cell_bounds = (int)value;
         return DBSCAN_OK;
+    case DBSCAN_OPT_BATCH_GRAPH:
+        if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
+        c->use_graph = (int)value;
+        return DBSCAN_OK;
     case DBSCAN_OPT_PHASE_TIMING:
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
         c->phase_timing = (int)value;
@@ -270,10 +395,6 @@ dbscan_status dbscan_get_stats(const dbscan_ctx *c, dbscan_stats *out) {
     return DBSCAN_OK;
 }
 
-// Neighbour-offset table of dimension d inside the context.
-static const signed char *offs_for(const dbscan_ctx *c, int d) {
-    return c->offs + (size_t)(d - 1) * kMaxOffsets * kMaxEnumDim;
-}
 
 dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, int dtype, double eps,
                          int64_t min_pts, uint8_t *d_core, int32_t *d_labels, int64_t *d_border_offsets,
@@ -354,96 +475,121 @@ dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, 
     c->stats.band_lo = P.lo;
     c->stats.band_hi = P.hi;
 
-    // 3. cells: group the points by cell (semisort, Sec. 4.1) through the cell hash
-    mark(2);
+    dbscan_status st = enqueue_core(c, P, D, SD, mode, d_points, dtype, d, 0, c->stats.key_bits, d_core, d_labels,
+                                    d_border_offsets, s, mark);
+    if (st != DBSCAN_OK) return st;
+    CK(cudaStreamSynchronize(s));
+    return finish_run(c, P, D, mode, d_points, dtype, n, num_border_memberships, launches0);
+}
+
+dbscan_status dbscan_run_batch(dbscan_ctx *c, const dbscan_instance *hi, int count, const void *d_points, int ld,
+                               int dtype, uint8_t *d_core, int32_t *d_labels, int64_t *d_border_offsets,
+                               int64_t *num_border_memberships, void *stream) {
+    if (!c || !hi || count < 1) return DBSCAN_ERR_INVALID_ARG;
+    c->have_run = false;
+    if (num_border_memberships) *num_border_memberships = 0;
+    if (ld < 1 || ld > c->max_dim || ld > 3) return DBSCAN_ERR_UNSUPPORTED_DIM;
+    if (dtype != DBSCAN_F32 && dtype != DBSCAN_F64) return DBSCAN_ERR_INVALID_ARG;
+    int64_t total = 0;
+    bool fp32_all = dtype == DBSCAN_F32 && c->precision == DBSCAN_PREC_FP32_RECHECK;
+    for (int i = 0; i < count; ++i) {
+        const dbscan_instance &I = hi[i];
+        if (I.row0 != total || I.n < 0 || I.d < 1 || I.d > ld || !(I.eps > 0.0) || !std::isfinite(I.eps) ||
+            I.min_pts < 1)
+            return DBSCAN_ERR_INVALID_ARG;
+        total += I.n;
+        const double T = I.eps * I.eps;
+        if (!(T >= 0x1p-60 && T <= 0x1p60)) fp32_all = false;
+    }
+    if (total > c->max_points) return DBSCAN_ERR_INVALID_ARG;
+    if (total > 0 && (!d_points || !d_core || !d_labels)) return DBSCAN_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::memset(&c->stats, 0, sizeof(c->stats));
+    c->stats.n = total;
+    c->stats.d = ld;
+    if (total == 0) {
+        if (d_border_offsets) CK(cudaMemsetAsync(d_border_offsets, 0, sizeof(int64_t), s));
+        CK(cudaStreamSynchronize(s));
+        c->have_run = true;
+        c->last = RunParams{};
+        return DBSCAN_OK;
+    }
+    dbscan_status st = gbdb_batch_buffers(c, hi, count);
+    if (st != DBSCAN_OK) return st;
+    const bool f64 = dtype == DBSCAN_F64;
+    const int D = ld <= 2 ? 2 : 3;
+    const int SD = D == 2 ? 2 : 4;
+    const int mode = fp32_all ? kF32FromF32 : (f64 ? kF64FromF64 : kF64FromF32);
+    int inst_bits = 1;
+    while ((1 << inst_bits) < count) ++inst_bits;
+    RunParams P{};
+    P.n = (int)total;
+    P.d = ld;
+    P.max_iters = c->max_iters;
+    P.stats = c->collect_stats;
+    P.box = fp32_all && c->cell_bounds ? 1 : 0;
+    P.ninst = count;
+    P.inst_shift = 63 - inst_bits;
+    P.inst = c->d_binst;
+    P.cell_inst = c->cell_inst;
+    c->stats.precision = fp32_all ? DBSCAN_PREC_FP32_RECHECK : DBSCAN_PREC_FP64;
+    c->stats.key_bits = 63;
+    c->stats.radix_passes = 4;
+    const long long launches0 = g_launches;
     if (!c->table_clean) {
         CK(cudaMemsetAsync(c->ht, 0xff, sizeof(ulonglong2) * c->hcap, s));
         CK(cudaMemsetAsync(c->hcnt, 0, sizeof(unsigned) * c->hcap, s));
+        c->table_clean = true;
     }
-    c->table_clean = false;
-    Semisort S{};
-    S.ht = c->ht;
-    S.hcnt = c->hcnt;
-    S.hcap = c->hcap;
-    S.slot_of = c->slot_of;
-    S.rank_of = c->rank_of;
-    S.slots = c->slots;
-    S.k0 = c->k0;
-    S.k1 = c->k1;
-    S.v0 = c->v0;
-    S.v1 = c->v1;
-    S.sort_scratch = c->sort_scratch;
-    S.part = c->part;
-    S.cell_key = c->cell_key;
-    S.count = c->core_pos;  // scratch until the compaction
-    S.cell_start = c->cell_start;
-    S.pf = c->pf;
-    S.pd = f64 ? c->pd : nullptr;
-    S.orig = c->orig;
-    S.cell_of = c->cell_of;
-    S.cell_inst = c->cell_inst;
-    S.key_bits = c->stats.key_bits;
-    launch_semisort(d_points, dtype, P, SD, S, c->ctr, s);
-
-    // 4. cell boxes, neighbour lists
-    mark(3);
-    if (P.box) launch_boxes(SD, c->pf, c->cell_start, c->ctr, c->blo, c->bhi, s);
-    int n_near = 1;
-    for (int j = 0; j < d; ++j) n_near *= 3;
-    launch_neighbors(c->cell_key, c->ht, c->hcap, P, offs_for(c, d), c->noff[d], n_near - 1, c->blo, c->bhi,
-                     c->nbr_cnt, c->nbr_near, c->nbr, c->ctr, s);
-
-    // 5. MarkCore, 6. compaction, 7. schedule, 8. connect, 9. labels, 10. border
-    Bufs B = make_bufs(c, f64);
-    B.n_max = n;
-    B.nbr_stride = c->noff[d];
-    mark(4);
-    launch_markcore(D, mode, P, B, c->ctr, s);
-    mark(5);
-    launch_core_compact(SD, P, B, c->ctr, s);
-    const uint32_t *order = launch_schedule(c->sched, P, B, c->ctr, s);
-    mark(6);
-    launch_connect(D, mode, order, P, B, c->ctr, s);
-    mark(7);
-    launch_labels(P, B, d_core, d_labels, c->ctr, s);
-    launch_border(D, mode, false, P, B, d_labels, nullptr, 0, c->ctr, s);
-    mark(8);
-    launch_table_reset(S, c->ctr, s);
-    if (d_border_offsets)
-        CK(cudaMemcpyAsync(d_border_offsets, c->boff, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    // The cell sort orders by the top 32 key bits (instance, then coarse Z
+    // order): enough for locality; the grouping itself is exact.
+    auto enqueue = [&]() -> dbscan_status {
+        dbscan_status e = gbdb_enqueue_batch_prologue(c, d_points, ld, dtype, count, total, fp32_all ? 1 : 0,
+                                                      P.inst_shift, s);
+        if (e != DBSCAN_OK) return e;
+        return enqueue_core(c, P, D, SD, mode, d_points, dtype, ld, 31, 32, d_core, d_labels, d_border_offsets, s,
+                            [](int) {});
+    };
+    const unsigned long long key[12] = {(unsigned long long)count, (unsigned long long)total,
+                                        (unsigned long long)(uintptr_t)d_points, (unsigned long long)ld,
+                                        (unsigned long long)dtype, (unsigned long long)(uintptr_t)d_core,
+                                        (unsigned long long)(uintptr_t)d_labels,
+                                        (unsigned long long)(uintptr_t)d_border_offsets,
+                                        (unsigned long long)(mode | (c->sched << 4) | (P.box << 8) | (P.stats << 9)),
+                                        0ull, (unsigned long long)c->max_iters, 1ull};
+    if (!c->use_graph) {
+        st = enqueue();
+        if (st != DBSCAN_OK) return st;
+    } else {
+        if (!c->graph_exec || std::memcmp(key, c->graph_key, sizeof key) != 0) {
+            if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+            c->graph_exec = nullptr;
+            // capture on a private stream (the legacy default stream cannot be
+            // captured); the graph then runs on the caller's stream
+            if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            const cudaStream_t user = s;
+            s = c->cap_stream;
+            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+            st = enqueue();
+            cudaError_t e = cudaStreamEndCapture(s, &graph);
+            s = user;
+            if (st != DBSCAN_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                (void)cudaGetLastError();
+                return st;
+            }
+            CK(e);
+            e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            CK(e);
+            std::memcpy(c->graph_key, key, sizeof key);
+        }
+        c->table_clean = false;
+        CK(cudaGraphLaunch(c->graph_exec, s));
+    }
     CK(cudaStreamSynchronize(s));
-    c->table_clean = c->h_ctr->err == 0;
-    const DevCounters &h = *c->h_ctr;
-    dbscan_stats &st = c->stats;
-    st.num_cells = h.m;
-    st.num_core_cells = h.m_core;
-    st.num_neighbor_entries = h.E;
-    st.num_candidate_pairs = h.P;
-    st.num_pairs_tested = (int64_t)h.pairs_tested;
-    st.num_pairs_skipped = (int64_t)h.pairs_skipped;
-    st.num_pairs_connected = (int64_t)h.pairs_linked;
-    st.num_pairs_box_decided = (int64_t)h.pairs_box;
-    st.num_core_points = h.n_core;
-    st.num_border_points = h.n_border;
-    st.num_noise_points = n - h.n_core - h.n_border;
-    st.num_border_memberships = h.K;
-    st.band_rechecks = (int64_t)h.band_rechecks;
-    for (int k = 0; k < 3; ++k) st.distance_evals_phase[k] = (int64_t)h.dist_evals[k];
-    st.distance_evals = st.distance_evals_phase[0] + st.distance_evals_phase[1] + st.distance_evals_phase[2];
-    st.kernel_launches = g_launches - launches0;
-    if (c->phase_timing)
-        for (int k = 0; k < 8; ++k) cudaEventElapsedTime(&st.phase_ms[k], c->ev[k], c->ev[k + 1]);
-    if (h.err) return (dbscan_status)h.err;
-    if (num_border_memberships) *num_border_memberships = h.K;
-    c->have_run = true;
-    c->last = P;
-    c->last_D = D;
-    c->last_mode = mode;
-    c->last_points = d_points;
-    c->last_dtype = dtype;
-    return DBSCAN_OK;
+    return finish_run(c, P, D, mode, d_points, dtype, total, num_border_memberships, launches0);
 }
 
 dbscan_status dbscan_border_ids(dbscan_ctx *c, int32_t *d_ids, int64_t capacity, void *stream) {

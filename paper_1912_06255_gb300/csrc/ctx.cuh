@@ -27,6 +27,7 @@ struct dbscan_ctx {
     int max_iters = 1 << 22;
     int phase_timing = 0;
     int cell_bounds = 1;
+    int use_graph = 1;
     cudaEvent_t ev[9] = {};
     // workspace
     void *arena = nullptr;
@@ -54,6 +55,14 @@ struct dbscan_ctx {
     gbdb::Inst *d_inst = nullptr;  // instance table (device), one entry for single runs
     gbdb::Inst *h_inst = nullptr;  // pinned host copy
     int last_mode_sel = 0;
+    // batches
+    int batch_cap = 0;
+    dbscan_instance *d_bdesc = nullptr, *h_bdesc = nullptr;
+    gbdb::Inst *d_binst = nullptr;
+    long long *d_bbox = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    unsigned long long graph_key[12] = {0};
     float4 *blo = nullptr, *bhi = nullptr, *cblo = nullptr, *cbhi = nullptr;  // cell / core-point boxes
     int *parent = nullptr, *compmin = nullptr;
     int *noncore = nullptr;

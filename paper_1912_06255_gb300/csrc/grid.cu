@@ -262,21 +262,24 @@ k_cell_table(RunParams P, const uint64_t *__restrict__ keys, const uint32_t *__r
 // scattered write per point.  Points are stored zero padded to SD coordinates.
 template <typename T, int SD>
 __global__ void __launch_bounds__(256)
-k_scatter_points(const T *__restrict__ X, int n, int d, const ulonglong2 *__restrict__ ht,
+k_scatter_points(const T *__restrict__ X, RunParams P, const ulonglong2 *__restrict__ ht,
                  const uint32_t *__restrict__ slot_of, const uint32_t *__restrict__ rank_of,
                  const int *__restrict__ cell_start, float *__restrict__ pf, double *__restrict__ pd,
                  int *__restrict__ orig, int *__restrict__ cell_of, const DevCounters *ctr) {
     if (ctr->err) return;  // a failed insert left slot_of undefined
+    const int n = P.n, ld = P.d;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int c = (int)ht[slot_of[i]].y;
         const int dst = cell_start[c] + (int)rank_of[i];
+        // coordinates beyond the instance's own dimension are stored as zero
+        const int d = P.ninst > 1 ? P.inst[P.cell_inst[c]].d : ld;
         orig[dst] = i;
         cell_of[dst] = c;
         float f[SD];
         double x[SD];
 #pragma unroll
         for (int j = 0; j < SD; ++j) {
-            x[j] = j < d ? (double)X[(int64_t)i * d + j] : 0.0;
+            x[j] = j < d ? (double)X[(int64_t)i * ld + j] : 0.0;
             f[j] = (float)x[j];
         }
         if constexpr (SD == 2) {
@@ -323,8 +326,8 @@ void launch_semisort(const void *X, int dtype, const RunParams &P, int SD, const
     count_launch();
     int g = grid_for((const void *)k_cell_keys, 256);
     k_cell_keys<<<g, 256, 0, s>>>(S.ht, S.slots, S.k0, S.v0, ctr); count_launch();
-    const int which = radix_sort_u64(S.k0, S.v0, S.k1, S.v1, 0, &ctr->m, P.n, 0, S.key_bits, S.sort_scratch, ctr,
-                                     P.max_iters, s);
+    const int which = radix_sort_u64(S.k0, S.v0, S.k1, S.v1, 0, &ctr->m, P.n, S.key_lo, S.key_bits, S.sort_scratch,
+                                     ctr, P.max_iters, s);
     const uint64_t *K = which ? S.k1 : S.k0;
     const uint32_t *V = which ? S.v1 : S.v0;
     g = grid_for((const void *)k_cell_table, 256);
@@ -332,8 +335,7 @@ void launch_semisort(const void *X, int dtype, const RunParams &P, int SD, const
     scan_i32_to_i32(S.count, S.cell_start, 0, &ctr->m, P.n, S.part, s);
     auto scat = [&](auto k, auto xp) {
         int gg = grid_for((const void *)k, 256);
-        k<<<gg, 256, 0, s>>>(xp, P.n, P.d, S.ht, S.slot_of, S.rank_of, S.cell_start, S.pf, S.pd, S.orig, S.cell_of,
-                             ctr);
+        k<<<gg, 256, 0, s>>>(xp, P, S.ht, S.slot_of, S.rank_of, S.cell_start, S.pf, S.pd, S.orig, S.cell_of, ctr);
         count_launch();
     };
     const float *xf = (const float *)X;

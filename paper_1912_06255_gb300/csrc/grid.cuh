@@ -36,7 +36,7 @@ struct Semisort {
     double *pd;           // null unless FP64 input
     int *orig, *cell_of;
     int *cell_inst;       // [m] instance of each cell (several instances only)
-    int key_bits;         // significant bits of the cell keys
+    int key_lo, key_bits; // key bits the cell sort orders by
 };
 // Group the points by cell: fills cell_key, cell_start, pf/pd, orig, cell_of,
 // ctr->m, and the slots' cell ids.

@@ -1,0 +1,102 @@
+"""Batched runs (many independent instances in one pass) against the oracle.
+
+Each instance of a batch must come out exactly as if clustered alone: core
+flags, labels (named by the smallest core index within the instance) and
+border sets, bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_06255_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1912_06255_gb300 import DBSCAN  # noqa: E402
+
+
+def _instances(seed, count, lo, hi, dtype=np.float32):
+    """Blob-plus-noise instances like the 256-instance workload, smaller."""
+    rng = np.random.default_rng(seed)
+    parts, desc = [], []
+    for i in range(count):
+        d = 2 if i % 2 == 0 else 3
+        n = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi))))) if i % 7 else [0, 1, 2][i % 3]
+        X = synth.gaussian_blobs(rng, n, d, max(1, n // 300), 10.0 * (n / 2000 + 0.1) ** (1 / d), 1.0, 0.1) \
+            if n > 0 else np.zeros((0, d))
+        eps = float(rng.uniform(0.2, 1.0))
+        mp = int(rng.integers(2, 20))
+        pad = np.zeros((n, 3), dtype=np.float64)
+        pad[:, :d] = X
+        # the unused third column of 2D instances holds garbage on purpose
+        if d == 2 and n:
+            pad[:, 2] = rng.normal(size=n) * 1e3
+        parts.append(pad)
+        desc.append((n, d, eps, mp, X))
+    return np.concatenate(parts, 0).astype(dtype), desc
+
+
+def _check(res, desc):
+    core = res.core.cpu().numpy()
+    labels = res.labels.cpu().numpy()
+    off = res.border_offsets.cpu().numpy()
+    ids = res.border_ids.cpu().numpy()
+    row = 0
+    for n, d, eps, mp, X in desc:
+        ec, el, eo, ei = oracle.dbscan(X.astype(np.float64) if X.dtype != np.float32 else X, eps, mp)
+        sl = slice(row, row + n)
+        assert np.array_equal(core[sl], ec), (row, n, d)
+        assert np.array_equal(labels[sl], el), (row, n, d)
+        got_o = off[row:row + n + 1] - off[row]
+        assert np.array_equal(got_o, eo), (row, n, d)
+        assert np.array_equal(ids[off[row]:off[row + n]], ei), (row, n, d)
+        row += n
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_matches_per_instance_oracle(graph):
+    P, desc = _instances(11, 40, 30, 6000)
+    # the oracle sees each instance's own FP32 coordinates
+    desc = [(n, d, eps, mp, P[sum(x[0] for x in desc[:k]):sum(x[0] for x in desc[:k]) + n, :d])
+            for k, (n, d, eps, mp, X) in enumerate(desc)]
+    ctx = DBSCAN(len(P), 3, graph=graph)
+    t = torch.from_numpy(P).cuda()
+    inst = [(n, d, eps, mp) for n, d, eps, mp, _ in desc]
+    r1 = ctx.run_batch(t, inst)
+    _check(r1, desc)
+    # a second call replays the captured graph
+    r2 = ctx.run_batch(t, inst)
+    _check(r2, desc)
+    # new coordinates in the same buffer, same graph
+    P2 = P.copy()
+    P2[:, :2] *= 1.5
+    t.copy_(torch.from_numpy(P2))
+    desc2 = [(n, d, eps, mp, X * np.array([1.5, 1.5, 1.0][:d], dtype=np.float32)) for n, d, eps, mp, X in desc]
+    r3 = ctx.run_batch(t, inst)
+    _check(r3, desc2)
+
+
+def test_batch_fp64_input():
+    P, desc = _instances(12, 12, 50, 3000, dtype=np.float64)
+    desc = [(n, d, eps, mp, P[sum(x[0] for x in desc[:k]):sum(x[0] for x in desc[:k]) + n, :d])
+            for k, (n, d, eps, mp, X) in enumerate(desc)]
+    ctx = DBSCAN(len(P), 3)
+    r = ctx.run_batch(torch.from_numpy(P).cuda(), [(n, d, eps, mp) for n, d, eps, mp, _ in desc])
+    _check(r, desc)
+    assert r.stats["precision"] == 0  # FP64 input batches decide in FP64
+
+
+def test_batch_of_one_equals_single_run():
+    I = synth.blobs_2d_20k()
+    X = I.points.astype(np.float32)
+    ctx = DBSCAN(len(X), 2)
+    t = torch.from_numpy(X).cuda()
+    a = ctx.run(t, I.eps, I.min_pts)
+    b = ctx.run_batch(t, [(len(X), 2, I.eps, I.min_pts)])
+    for u, v in ((a.core, b.core), (a.labels, b.labels), (a.border_offsets, b.border_offsets),
+                 (a.border_ids, b.border_ids)):
+        assert torch.equal(u, v)
