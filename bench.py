@@ -1,18 +1,24 @@
 """Benchmark: exact DBSCAN throughput (Mpts/s) on one GB300 per rank.
 
-Workload: 3D seed-spreader points, n = 2,000,000, stored FP32, eps = 100,
-minPts = 100 (100 random walkers in [0,1e5]^3, ball radius 100, step 50 per
-100 points, 0.01% noise).  One step = one full run of the hot path (cells,
-MarkCore, BCP connectivity with union-find, labels, border counts) through the
-C ABI on inputs resident in device memory.  The 24 MB input fits in L2, so L2
-is flushed (256 MiB write) before every timed step, outside the timed interval.
+Default workload (``--workload spreader3d``): 3D seed-spreader points,
+n = 2,000,000, stored FP32, eps = 100, minPts = 100 (100 random walkers in
+[0,1e5]^3, ball radius 100, step 50 per 100 points, 0.01% noise).  One step =
+one full run of the hot path (cells, MarkCore, BCP connectivity with
+union-find, labels, border counts) through the C ABI on inputs resident in
+device memory.  The 24 MB input fits in L2, so L2 is flushed (256 MiB write)
+before every timed step, outside the timed interval.
+
+``--workload batch256``: 256 independent 2D/3D blob-plus-noise instances with
+log-uniform sizes in [1e3, 1e6] (about 36M points), per-instance eps in
+[0.2, 1.0] and minPts in [5, 50], FP32, in one dbscan_run_batch call (one
+replayed CUDA graph).
 
 ``--impl reference`` times the CPU oracle (FP64, OpenMP on the host cores) on
 a bounded sample of the same workload instead.
 
 Under torchrun (N > 1) every rank runs its own replica of the workload on its
-own GPU (the problem is one instance, so the ranks share nothing); value =
-N * n / (max over ranks of the step time).
+own GPU (the problem does not shard, so the ranks share nothing); value =
+N * points / (max over ranks of the step time).
 """
 from __future__ import annotations
 
@@ -29,11 +35,116 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "exact DBSCAN Mpts/s on 1 GB300 (3D seed spreader n=2e6, eps=100, minPts=100)"
 UNIT = "Mpts/s"
-SAMPLE_SLAB = 5e3  # CPU sample: points with x < 5e3 (5% of the box, same local density)
+PHASES = ["bbox", "bbox_readback", "cells", "boxes_neighbors", "markcore", "compact_schedule",
+          "connect_bcp_uf", "labels_border"]
 
 
+# ----------------------------------------------------------------- workloads
+class Spreader3D:
+    """The single 2M-point 3D instance."""
+    metric = "exact DBSCAN Mpts/s on 1 GB300 (3D seed spreader n=2e6, eps=100, minPts=100)"
+    SLAB = 5e3  # CPU sample: points with x < 5e3 (5% of the box, same local density)
+
+    def __init__(self, n):
+        from paper_1912_06255_gb300 import synth
+        self.I = synth.spreader_3d_2m(n=n)
+        self.n = len(self.I.points)
+        self.name = self.I.name
+        self.config = {"workload": self.I.name, "n": self.n, "d": 3, "eps": self.I.eps, "min_pts": self.I.min_pts}
+
+    def make_ctx(self, DBSCAN, **kw):
+        return DBSCAN(self.n, 3, **kw)
+
+    def device_input(self, dev):
+        import torch
+        return torch.from_numpy(self.I.points).to(dev)
+
+    def run(self, ctx, X, out):
+        ctx.run(X, self.I.eps, self.I.min_pts, border=False, out=out)
+
+    def run_e2e(self, ctx, hbuf):
+        ctx.run_host(hbuf["X"], self.I.eps, self.I.min_pts, core=hbuf["core"], labels=hbuf["labels"])
+
+    def host_buffers(self):
+        import torch
+        return {"X": torch.from_numpy(self.I.points).pin_memory(),
+                "core": torch.empty(self.n, dtype=torch.uint8).pin_memory(),
+                "labels": torch.empty(self.n, dtype=torch.int32).pin_memory()}
+
+    def h2d_bytes(self):
+        return int(self.I.points.nbytes)
+
+    def cpu_sample(self):
+        X = np.ascontiguousarray(self.I.points[self.I.points[:, 0] < self.SLAB])
+        desc = (f"{len(X)} points with x < {self.SLAB:g} of the {self.n}-point workload (same local density), "
+                f"one full oracle run")
+        return [(X, self.I.eps, self.I.min_pts)], desc
+
+
+class Batch256:
+    """256 independent 2D/3D instances in one batched call."""
+    metric = "exact DBSCAN Mpts/s on 1 GB300 (batch of 256 2D/3D instances, about 36M points)"
+
+    def __init__(self, n):
+        from paper_1912_06255_gb300 import synth
+        self.B = synth.batch_256()
+        self.n = sum(len(b.points) for b in self.B)
+        P = np.zeros((self.n, 3), np.float32)
+        row = 0
+        for b in self.B:
+            P[row:row + len(b.points), :b.points.shape[1]] = b.points
+            row += len(b.points)
+        self.P = P
+        self.inst = [(len(b.points), b.points.shape[1], b.eps, b.min_pts) for b in self.B]
+        self.name = f"batch256-n{self.n}-f32"
+        self.config = {"workload": self.name, "instances": len(self.B), "n": self.n, "d": "2/3",
+                       "eps": "U[0.2,1.0]", "min_pts": "U{5..50}"}
+
+    def make_ctx(self, DBSCAN, **kw):
+        return DBSCAN(self.n, 3, **kw)
+
+    def device_input(self, dev):
+        import torch
+        return torch.from_numpy(self.P).to(dev)
+
+    def run(self, ctx, X, out):
+        ctx.run_batch(X, self.inst, border=False, out=out)
+
+    def run_e2e(self, ctx, hbuf):
+        # the public API path: pinned host -> device, batched run, results -> pinned host
+        hbuf["dX"].copy_(hbuf["X"], non_blocking=True)
+        ctx.run_batch(hbuf["dX"], self.inst, border=False, out=hbuf["out"])
+        hbuf["core"].copy_(hbuf["out"][0], non_blocking=True)
+        hbuf["labels"].copy_(hbuf["out"][1], non_blocking=True)
+
+    def host_buffers(self):
+        import torch
+        return {"X": torch.from_numpy(self.P).pin_memory(), "dX": torch.empty_like(torch.from_numpy(self.P)).cuda(),
+                "out": (torch.empty(self.n, dtype=torch.uint8, device="cuda"),
+                        torch.empty(self.n, dtype=torch.int32, device="cuda"), None),
+                "core": torch.empty(self.n, dtype=torch.uint8).pin_memory(),
+                "labels": torch.empty(self.n, dtype=torch.int32).pin_memory()}
+
+    def h2d_bytes(self):
+        return int(self.P.nbytes)
+
+    def cpu_sample(self):
+        order = sorted(range(len(self.B)), key=lambda i: len(self.B[i].points))
+        pick, tot = [], 0
+        for i in order[::8]:  # every 8th instance by size: a spread of sizes
+            if tot + len(self.B[i].points) > 400_000:
+                break
+            pick.append(i)
+            tot += len(self.B[i].points)
+        desc = f"{len(pick)} of the 256 instances (every 8th by size), {tot} points, one oracle run each"
+        return [(self.B[i].points, self.B[i].eps, self.B[i].min_pts) for i in pick], desc
+
+
+WORKLOADS = {"spreader3d": Spreader3D, "batch256": Batch256}
+
+
+# ----------------------------------------------------------------- helpers
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -41,28 +152,15 @@ def _dist():
     return ws, rank, local
 
 
-_N = 2_000_000
-
-
-def _workload():
-    from paper_1912_06255_gb300 import synth
-    return synth.spreader_3d_2m(n=_N)
-
-
-def _cpu_sample(I):
-    sel = I.points[:, 0] < SAMPLE_SLAB
-    return np.ascontiguousarray(I.points[sel])
-
-
-def _time_oracle(X, eps, mp, reps=1):
+def _time_oracle(samples):
     import oracle
     oracle.build()
-    ts = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
+    n = 0
+    t0 = time.perf_counter()
+    for X, eps, mp in samples:
         oracle.dbscan(X, eps, mp)
-        ts.append(time.perf_counter() - t0)
-    return ts, oracle.num_threads()
+        n += len(X)
+    return n, time.perf_counter() - t0, oracle.num_threads()
 
 
 class ClockSampler:
@@ -73,7 +171,6 @@ class ClockSampler:
 
     def __init__(self, gpu_index: int):
         self.proc = None
-        self.gpu = gpu_index
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
@@ -110,28 +207,51 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _roofline(kernel, ms, pair_tests, d_flops):
+    """Roofline of the dominant kernel.  MarkCore and BCP are pair-distance
+    loops bound by the FP32 pipe: achieved = pair tests executed x 3d flop /
+    kernel time (pair tests counted in a separate counting run), peak = 152
+    SMs x 128 FP32 lanes x 2 flop x max SM clock."""
+    peaks, kind = _peaks()
+    clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak_tflops = 152 * 128 * 2 * clk / 1e12
+    if not pair_tests or ms <= 0:
+        return None
+    achieved = pair_tests * 3 * d_flops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "traffic": None, "kernel": kernel,
+            "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x max SM clock ({kind} clock)"}
+
+
+# ----------------------------------------------------------------- arms
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    I = _workload()
-    X = _cpu_sample(I)
-    ts, cores = [], 1
+    W = WORKLOADS[args.workload](args.n)
+    samples, desc = W.cpu_sample()
+    ts, npts, cores = [], 0, 1
     for i in range(args.warmup + args.steps):
-        t, cores = _time_oracle(X, I.eps, I.min_pts)
+        npts, t, cores = _time_oracle(samples)
         if i >= args.warmup:
-            ts.append(t[0])
+            ts.append(t)
     t = statistics.median(ts)
-    v = len(X) / t / 1e6
-    sample = (f"all {len(X)} points with x < {SAMPLE_SLAB:g} of the {len(I.points)}-point workload "
-              f"(same local density); full oracle run per step")
+    v = npts / t / 1e6
     line = {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": W.metric, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": I.name, "n": len(I.points), "d": 3, "eps": I.eps, "min_pts": I.min_pts,
-                   "sample_n": len(X)},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "config": dict(W.config, sample_n=npts),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -149,14 +269,13 @@ def run_gpu(args):
     from paper_1912_06255_gb300 import DBSCAN, build
 
     build.build()
-    I = _workload()
-    n = len(I.points)
+    W = WORKLOADS[args.workload](args.n)
+    n = W.n
     dev = torch.device("cuda", local)
-    X = torch.from_numpy(I.points).to(dev)
-    ctx = DBSCAN(n, 3, precision=args.precision, schedule=args.schedule)
-    core = torch.empty(n, dtype=torch.uint8, device=dev)
-    labels = torch.empty(n, dtype=torch.int32, device=dev)
-    offs = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    X = W.device_input(dev)
+    ctx = W.make_ctx(DBSCAN, precision=args.precision, schedule=args.schedule)
+    out = (torch.empty(n, dtype=torch.uint8, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
+           torch.empty(n + 1, dtype=torch.int64, device=dev))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -165,7 +284,7 @@ def run_gpu(args):
             dist.barrier()
 
     def step():
-        ctx.run(X, I.eps, I.min_pts, border=False, out=(core, labels, offs))
+        W.run(ctx, X, out)
 
     if args.profile:
         # profiling mode (for ncu): warm-up and timed steps only, no extra runs
@@ -173,23 +292,33 @@ def run_gpu(args):
             step()
         torch.cuda.synchronize()
         if rank == 0:
-            print(json.dumps({"profile": I.name, "steps": args.steps, "warmup": args.warmup}), flush=True)
+            print(json.dumps({"profile": W.name, "steps": args.steps, "warmup": args.warmup}), flush=True)
         return
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
     # pair tests per kernel, counted once in an untimed run
-    cctx = DBSCAN(n, 3, precision=args.precision, schedule=args.schedule, collect_stats=True)
-    cctx.run(X, I.eps, I.min_pts, border=False)
+    cctx = W.make_ctx(DBSCAN, precision=args.precision, schedule=args.schedule, collect_stats=True)
+    W.run(cctx, X, out)
     ev_phase = cctx.stats()["distance_evals_phase"]
-    _PAIR_EVALS[4], _PAIR_EVALS[6] = ev_phase[0], ev_phase[1]
     cctx.close()
 
-    # timed region: device time per step with CUDA events; L2 flushed before each step
-    ctx.set_option(4, 1)  # phase timing
+    # timed region: device time per step with CUDA events; L2 flushed before each step.
+    # Phase timing records events inside the run; a batch runs its captured graph
+    # in the timed steps and takes its phase split from one extra direct run.
+    batched = isinstance(W, Batch256)
+    if batched:
+        ctx.set_option(4, 1)
+        step()
+        torch.cuda.synchronize()
+        batch_phases = ctx.stats()["phase_ms"]
+        ctx.set_option(4, 0)
+        step()
+    else:
+        ctx.set_option(4, 1)
+    torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    phases = []
-    launches = 0
+    phases, launches = [], 0
     clocks = ClockSampler(local) if rank == 0 else None
     barrier()
     torch.cuda.synchronize()
@@ -199,7 +328,7 @@ def run_gpu(args):
         step()
         evs[k][1].record(stream)
         st = ctx.stats()
-        phases.append(st["phase_ms"])
+        phases.append(batch_phases if batched else st["phase_ms"])
         launches += st["kernel_launches"]
     torch.cuda.synchronize()
     barrier()
@@ -210,32 +339,31 @@ def run_gpu(args):
     ctx.set_option(4, 0)
 
     # the plain FP64 path on the same input (a few steps, same flush rule)
-    ctx64 = DBSCAN(n, 3, precision="fp64", schedule=args.schedule)
+    ctx64 = W.make_ctx(DBSCAN, precision="fp64", schedule=args.schedule)
     for _ in range(3):
-        ctx64.run(X, I.eps, I.min_pts, border=False, out=(core, labels, offs))
+        W.run(ctx64, X, out)
     ms64 = []
     for k in range(max(3, min(args.steps, 5))):
         flush.fill_(float(k))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        ctx64.run(X, I.eps, I.min_pts, border=False, out=(core, labels, offs))
+        W.run(ctx64, X, out)
         b.record(stream)
         torch.cuda.synchronize()
         ms64.append(a.elapsed_time(b))
     ctx64.close()
 
-    # end to end through the host-buffer entry point (pinned host memory)
-    hX = torch.from_numpy(I.points).pin_memory()
-    hcore = torch.empty(n, dtype=torch.uint8).pin_memory()
-    hlab = torch.empty(n, dtype=torch.int32).pin_memory()
+    # end to end through the public API from pinned host memory
+    hbuf = W.host_buffers()
     for _ in range(2):
-        ctx.run_host(hX, I.eps, I.min_pts, core=hcore, labels=hlab)
+        W.run_e2e(ctx, hbuf)
+    torch.cuda.synchronize()
     e2e_ms = []
     for k in range(args.steps):
         flush.fill_(float(k))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        ctx.run_host(hX, I.eps, I.min_pts, core=hcore, labels=hlab)
+        W.run_e2e(ctx, hbuf)
         b.record(stream)
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
@@ -252,76 +380,41 @@ def run_gpu(args):
     te2e = max_over_ranks(sum(e2e_ms) / len(e2e_ms))
     if rank == 0:
         ph = [sum(p[i] for p in phases) / len(phases) for i in range(8)]
-        pair_tests = {"markcore": _PAIR_EVALS.get(4), "connect": _PAIR_EVALS.get(6)}
-        names = ["bbox", "bbox_readback", "keys_sort", "cells_hash_neighbors", "markcore",
-                 "compact_schedule", "connect_bcp_uf", "labels_border"]
-        # dominant kernel: the MarkCore launch (one kernel, phase 4) or the BCP launch (phase 6)
         dom = 4 if ph[4] >= ph[6] else 6
-        roof = _roofline(dom, ph[dom], stats, n)
+        roof = _roofline("k_markcore" if dom == 4 else "k_connect", ph[dom],
+                         ev_phase[0] if dom == 4 else ev_phase[1], 3)
         line = {
-            "metric": METRIC,
+            "metric": W.metric,
             "value": ws * n / (t_ms * 1e-3) / 1e6,
             "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f64",
             "data": "synthetic",
-            "config": {"workload": I.name, "n": n, "d": 3, "eps": I.eps, "min_pts": I.min_pts,
-                       "precision": "fp32 band + fp64 recheck" if args.precision == "fp32" else "fp64",
-                       "schedule": args.schedule, "parallelism": f"replicas{ws}",
-                       "l2": "flushed (256 MiB write) before every timed step"},
+            "config": dict(W.config, precision="fp32 band + fp64 recheck" if args.precision == "fp32" else "fp64",
+                           schedule=args.schedule, parallelism=f"replicas{ws}",
+                           l2="flushed (256 MiB write) before every timed step"),
             "fp64_path": {"value": ws * n / (t64 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": t64},
             "e2e": {"value": ws * n / (te2e * 1e-3) / 1e6, "unit": UNIT,
-                    "h2d_bytes_per_step": int(I.points.nbytes), "d2h_bytes_per_step": int(n * 5)},
+                    "h2d_bytes_per_step": W.h2d_bytes(), "d2h_bytes_per_step": int(n * 5)},
             "gpu_launches": int(launches),
-            "phase_ms": dict(zip(names, [round(x, 4) for x in ph])),
+            "phase_ms": dict(zip(PHASES, [round(x, 4) for x in ph])),
             "roofline": roof,
-            "pair_tests": pair_tests,
+            "pair_tests": {"markcore": ev_phase[0], "connect": ev_phase[1], "border": ev_phase[2]},
             "run_stats": {k: stats[k] for k in ("num_cells", "num_core_cells", "num_candidate_pairs",
-                                                 "num_pairs_tested", "num_pairs_skipped", "num_core_points",
-                                                 "num_border_points", "band_rechecks", "key_bits")},
+                                                 "num_pairs_tested", "num_pairs_skipped", "num_pairs_box_decided",
+                                                 "num_core_points", "num_border_points", "band_rechecks",
+                                                 "key_bits")},
         }
         if clk:
             line["clocks"] = clk
         if not args.no_cpu_baseline:
-            Xs = _cpu_sample(I)
-            ts, cores = _time_oracle(Xs, I.eps, I.min_pts)
-            line["cpu_baseline"] = {"value": len(Xs) / ts[0] / 1e6, "unit": UNIT, "cores": cores,
-                                    "kind": "oracle",
-                                    "sample": f"{len(Xs)} points with x < {SAMPLE_SLAB:g} (same local density), "
-                                              f"one full oracle run"}
+            samples, desc = W.cpu_sample()
+            npts, t, cores = _time_oracle(samples)
+            line["cpu_baseline"] = {"value": npts / t / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": desc}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
-
-
-def _peaks():
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    try:
-        with open(p) as f:
-            return json.load(f), "measured"
-    except Exception:
-        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
-
-
-def _roofline(phase, ms, stats, n):
-    """Roofline of the dominant kernel.  MarkCore and BCP are pair-distance
-    loops bound by the FP32 pipe: achieved = pair tests x 3d flop / kernel time
-    (pair tests counted by a separate counting run), peak = 152 SMs x 128 FP32
-    lanes x 2 flop x max SM clock."""
-    peaks, kind = _peaks()
-    clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    peak_tflops = 152 * 128 * 2 * clk / 1e12
-    evals = _PAIR_EVALS.get(phase)
-    if evals is None or ms <= 0:
-        return None
-    achieved = evals * 9.0 / (ms * 1e-3) / 1e12  # 3d flop per pair test, d = 3
-    return {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops, "traffic": None,
-            "kernel": "k_markcore" if phase == 4 else "k_connect",
-            "peak_source": f"FP32 lanes x max SM clock ({kind} clock)"}
-
-
-_PAIR_EVALS = {}
 
 
 def main():
@@ -330,6 +423,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="spreader3d", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--schedule", default="size", choices=["size", "none"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -338,8 +432,6 @@ def main():
     ap.add_argument("--n", type=int, default=2_000_000,
                     help="points of the seed-spreader workload (the bench line is defined at 2,000,000)")
     args = ap.parse_args()
-    global _N
-    _N = args.n
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -226,8 +226,11 @@ static dbscan_status finish_run(dbscan_ctx *c, const RunParams &P, int D, int mo
     for (int k = 0; k < 3; ++k) st.distance_evals_phase[k] = (int64_t)h.dist_evals[k];
     st.distance_evals = st.distance_evals_phase[0] + st.distance_evals_phase[1] + st.distance_evals_phase[2];
     st.kernel_launches = g_launches - launches0;
-    if (c->phase_timing)
-        for (int k = 0; k < 8; ++k) cudaEventElapsedTime(&st.phase_ms[k], c->ev[k], c->ev[k + 1]);
+    if (c->phase_timing) {
+        for (int k = 0; k < 8; ++k)
+            if (cudaEventElapsedTime(&st.phase_ms[k], c->ev[k], c->ev[k + 1]) != cudaSuccess) st.phase_ms[k] = 0.f;
+        (void)cudaGetLastError();
+    }
     if (h.err) return (dbscan_status)h.err;
     if (num_border_memberships) *num_border_memberships = h.K;
     c->have_run = true;
@@ -544,11 +547,15 @@ dbscan_status dbscan_run_batch(dbscan_ctx *c, const dbscan_instance *hi, int cou
     // The cell sort orders by the top 32 key bits (instance, then coarse Z
     // order): enough for locality; the grouping itself is exact.
     auto enqueue = [&]() -> dbscan_status {
+        if (c->phase_timing) cudaEventRecord(c->ev[0], s);
+        if (c->phase_timing) cudaEventRecord(c->ev[1], s);
         dbscan_status e = gbdb_enqueue_batch_prologue(c, d_points, ld, dtype, count, total, fp32_all ? 1 : 0,
                                                       P.inst_shift, s);
         if (e != DBSCAN_OK) return e;
         return enqueue_core(c, P, D, SD, mode, d_points, dtype, ld, 31, 32, d_core, d_labels, d_border_offsets, s,
-                            [](int) {});
+                            [&](int k) {
+                                if (c->phase_timing) cudaEventRecord(c->ev[k], s);
+                            });
     };
     const unsigned long long key[12] = {(unsigned long long)count, (unsigned long long)total,
                                         (unsigned long long)(uintptr_t)d_points, (unsigned long long)ld,
@@ -556,8 +563,10 @@ dbscan_status dbscan_run_batch(dbscan_ctx *c, const dbscan_instance *hi, int cou
                                         (unsigned long long)(uintptr_t)d_labels,
                                         (unsigned long long)(uintptr_t)d_border_offsets,
                                         (unsigned long long)(mode | (c->sched << 4) | (P.box << 8) | (P.stats << 9)),
-                                        0ull, (unsigned long long)c->max_iters, 1ull};
-    if (!c->use_graph) {
+                                        (unsigned long long)c->phase_timing, (unsigned long long)c->max_iters, 1ull};
+    // phase timing records events between the steps: that run is enqueued
+    // directly instead of replaying the graph
+    if (!c->use_graph || c->phase_timing) {
         st = enqueue();
         if (st != DBSCAN_OK) return st;
     } else {
@@ -571,7 +580,9 @@ dbscan_status dbscan_run_batch(dbscan_ctx *c, const dbscan_instance *hi, int cou
             const cudaStream_t user = s;
             s = c->cap_stream;
             CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+            const long long l0 = g_launches;
             st = enqueue();
+            c->graph_launches = g_launches - l0;
             cudaError_t e = cudaStreamEndCapture(s, &graph);
             s = user;
             if (st != DBSCAN_OK) {
@@ -587,6 +598,7 @@ dbscan_status dbscan_run_batch(dbscan_ctx *c, const dbscan_instance *hi, int cou
         }
         c->table_clean = false;
         CK(cudaGraphLaunch(c->graph_exec, s));
+        g_launches += c->graph_launches;  // kernels the replay runs
     }
     CK(cudaStreamSynchronize(s));
     return finish_run(c, P, D, mode, d_points, dtype, total, num_border_memberships, launches0);

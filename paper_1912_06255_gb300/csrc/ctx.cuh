@@ -62,6 +62,7 @@ struct dbscan_ctx {
     long long *d_bbox = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t cap_stream = nullptr;
+    long long graph_launches = 0;  // kernel nodes of the captured graph
     unsigned long long graph_key[12] = {0};
     float4 *blo = nullptr, *bhi = nullptr, *cblo = nullptr, *cbhi = nullptr;  // cell / core-point boxes
     int *parent = nullptr, *compmin = nullptr;

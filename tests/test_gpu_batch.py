@@ -100,3 +100,30 @@ def test_batch_of_one_equals_single_run():
     for u, v in ((a.core, b.core), (a.labels, b.labels), (a.border_offsets, b.border_offsets),
                  (a.border_ids, b.border_ids)):
         assert torch.equal(u, v)
+
+
+@pytest.mark.slow
+def test_batch256_full_size_sampled():
+    """The full 256-instance batch (about 36M points) in the configuration the
+    benchmark times; the oracle checks the largest and smallest instances and
+    every 32nd by size."""
+    B = synth.batch_256()
+    N = sum(len(b.points) for b in B)
+    P = np.zeros((N, 3), np.float32)
+    rows, row = [], 0
+    for b in B:
+        P[row:row + len(b.points), :b.points.shape[1]] = b.points
+        rows.append(row)
+        row += len(b.points)
+    ctx = DBSCAN(N, 3)
+    r = ctx.run_batch(torch.from_numpy(P).cuda(), [(len(b.points), b.points.shape[1], b.eps, b.min_pts) for b in B])
+    core, labels = r.core.cpu().numpy(), r.labels.cpu().numpy()
+    off, ids = r.border_offsets.cpu().numpy(), r.border_ids.cpu().numpy()
+    order = sorted(range(len(B)), key=lambda i: len(B[i].points))
+    for i in sorted(set([order[0], order[-1]] + order[::32])):
+        b, r0, n = B[i], rows[i], len(B[i].points)
+        ec, el, eo, ei = oracle.dbscan(b.points, b.eps, b.min_pts)
+        assert np.array_equal(core[r0:r0 + n], ec), i
+        assert np.array_equal(labels[r0:r0 + n], el), i
+        assert np.array_equal(off[r0:r0 + n + 1] - off[r0], eo), i
+        assert np.array_equal(ids[off[r0]:off[r0 + n]], ei), i
