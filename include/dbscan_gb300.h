@@ -80,13 +80,23 @@ enum {
     DBSCAN_OPT_CELL_BOUNDS = 5,
     /* value: 1 (default) or 0: dbscan_run_batch captures its sequence as a CUDA
        graph and replays it; 0 enqueues the kernels directly every call */
-    DBSCAN_OPT_BATCH_GRAPH = 6
+    DBSCAN_OPT_BATCH_GRAPH = 6,
+    /* value: capacity (records) of the pair log, 0 (default) = off.  While on,
+       runs use the learned schedule's pair list in logging mode: every pair
+       the core-point boxes do not settle gets an exact BCP test (no union-find
+       skipping) and its features and outcome are recorded, for
+       dbscan_train_scheduler() */
+    DBSCAN_OPT_PAIR_LOG = 7
 };
 enum { DBSCAN_PREC_FP64 = 0, DBSCAN_PREC_FP32_RECHECK = 1 };
 /* SIZE: core-cell pairs are tested in order of non-increasing core count of the
- * owning cell (Sec. 4.4, "Reducing Cell Connectivity Queries").
- * NONE: pairs are tested in cell order (ablation). */
-enum { DBSCAN_SCHED_SIZE = 0, DBSCAN_SCHED_NONE = 1 };
+ * owning cell (Sec. 4.4, "Reducing Cell Connectivity Queries"), adjacent cells
+ * first, then (after path compression) the farther ones.
+ * NONE: pairs are tested in cell order (ablation).
+ * LEARNED: the pairs the core-point boxes do not settle are scored by the
+ * context's network and tested likeliest-connected first (extends the size
+ * heuristic of Sec. 4.4; exact BCP decides every pair as before). */
+enum { DBSCAN_SCHED_SIZE = 0, DBSCAN_SCHED_NONE = 1, DBSCAN_SCHED_LEARNED = 2 };
 
 typedef struct dbscan_ctx dbscan_ctx;
 
@@ -106,6 +116,7 @@ typedef struct {
     int64_t num_pairs_skipped;      /* pairs skipped because union-find had joined them */
     int64_t num_pairs_connected;    /* pairs found connected (by BCP or by their boxes) */
     int64_t num_pairs_box_decided;  /* pairs settled by the core-point bounding boxes alone */
+    int64_t num_pairs_listed;       /* learned schedule: pairs left for BCP after the boxes */
     int64_t num_core_points;
     int64_t num_border_points;
     int64_t num_noise_points;
@@ -241,6 +252,42 @@ dbscan_status dbscan_run_host(dbscan_ctx *ctx, const void *h_points, int64_t n, 
  */
 dbscan_status dbscan_run_static(const void *d_points, int64_t n, int d, int dtype, double eps,
                                 int64_t min_pts, uint8_t *d_core, int32_t *d_labels, void *stream);
+
+/*
+ * Learned pair scheduler (an extension of the priority order of Sec. 4.4; the
+ * paper trains nothing).  The context holds a network of 6 inputs, two hidden
+ * layers of 32 ReLU units and one logit output (1313 FP32 parameters,
+ * initialised deterministically at dbscan_create).  Its inputs per pair of
+ * core cells: log2(1 + larger core count), log2(1 + smaller core count), the
+ * distance between the core centroids, the minimum and maximum distance
+ * between the core-point boxes (all three divided by eps), and smaller over
+ * larger core count.
+ *
+ * dbscan_train_scheduler: re-initialise the network from seed and fit it with
+ * Adam (learning rate lr, mini-batches of `batch` records, `epochs` passes) to
+ * the binary cross-entropy of the records logged by the last run made with
+ * DBSCAN_OPT_PAIR_LOG; h_losses (host, `epochs` floats, may be NULL) receives
+ * the mean loss of each epoch.  Returns STATE if nothing is logged.
+ * Synchronises the device.
+ */
+dbscan_status dbscan_train_scheduler(dbscan_ctx *ctx, int epochs, int batch, float lr, uint64_t seed,
+                                     float *h_losses);
+
+/* Copy the network's 1313 parameters to (set = 0) or from (set = 1) h_weights.
+ * Layout: W1[32][6], b1[32], W2[32][32], b2[32], w3[32], b3. */
+dbscan_status dbscan_scheduler_weights(dbscan_ctx *ctx, float *h_weights, int count, int set);
+
+/* Mean binary cross-entropy (with logits) of the network on n records
+ * d_features [n][6], d_labels [n] (0/1) and its gradient, h_grad [1313]
+ * (same layout as the parameters).  Synchronises the device. */
+dbscan_status dbscan_scheduler_loss_grad(dbscan_ctx *ctx, const float *d_features, const uint8_t *d_labels,
+                                         int64_t n, float *h_loss, float *h_grad);
+
+/* Copy the pair log of the last logging run to d_features [capacity][6] and
+ * d_labels [capacity]; *count receives the number of records.  CAPACITY if
+ * capacity is too small.  Synchronises the device. */
+dbscan_status dbscan_get_pair_log(dbscan_ctx *ctx, float *d_features, uint8_t *d_labels, int64_t capacity,
+                                  int64_t *count);
 
 /* Counters of the last run (host copy; no device work). */
 dbscan_status dbscan_get_stats(const dbscan_ctx *ctx, dbscan_stats *out);

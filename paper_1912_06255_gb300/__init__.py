@@ -50,7 +50,7 @@ class DBSCAN:
                    "dbscan_create")
         self.max_points, self.max_dim = int(max_points), int(max_dim)
         prec = {"fp32": _lib.PREC_FP32_RECHECK, "fp64": _lib.PREC_FP64}[precision]
-        sched = {"size": _lib.SCHED_SIZE, "none": _lib.SCHED_NONE}[schedule]
+        sched = {"size": _lib.SCHED_SIZE, "none": _lib.SCHED_NONE, "learned": _lib.SCHED_LEARNED}[schedule]
         self.set_option(_lib.OPT_PRECISION, prec)
         self.set_option(_lib.OPT_SCHEDULE, sched)
         self.set_option(_lib.OPT_COLLECT_STATS, int(bool(collect_stats)))
@@ -72,6 +72,56 @@ class DBSCAN:
             self.close()
         except Exception:
             pass
+
+    # ---- learned pair scheduler
+    def enable_pair_log(self, capacity: int) -> None:
+        """Log (features, outcome) of every pair the next runs test (0 = off)."""
+        self.set_option(_lib.OPT_PAIR_LOG, int(capacity))
+
+    def pair_log(self):
+        """The records of the last logging run: (features [k, 6] f32, labels [k] u8) on the GPU."""
+        torch = _torch()
+        k = ctypes.c_int64(0)
+        k0 = ctypes.c_int64(0)
+        st = self.lib.dbscan_get_pair_log(self.ctx, None, None, 0, ctypes.byref(k0))
+        if st not in (_lib.OK, 5):
+            _lib.check(st, "dbscan_get_pair_log")
+        n = int(k0.value)
+        feat = torch.empty((max(n, 1), 6), dtype=torch.float32, device="cuda")
+        lab = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
+        if n:
+            _lib.check(self.lib.dbscan_get_pair_log(self.ctx, feat.data_ptr(), lab.data_ptr(), n, ctypes.byref(k)),
+                       "dbscan_get_pair_log")
+        return feat[:n], lab[:n]
+
+    def train_scheduler(self, epochs: int = 20, batch: int = 4096, lr: float = 3e-3, seed: int = 0) -> list:
+        """Fit the scheduler network to the last logging run; returns the loss per epoch."""
+        import numpy as np
+        losses = np.zeros(epochs, dtype=np.float32)
+        _lib.check(self.lib.dbscan_train_scheduler(self.ctx, int(epochs), int(batch), float(lr), int(seed),
+                                                   losses.ctypes.data), "dbscan_train_scheduler")
+        return losses.tolist()
+
+    def scheduler_weights(self):
+        import numpy as np
+        w = np.zeros(_lib.MLP_PARAMS, dtype=np.float32)
+        _lib.check(self.lib.dbscan_scheduler_weights(self.ctx, w.ctypes.data, w.size, 0), "dbscan_scheduler_weights")
+        return w
+
+    def set_scheduler_weights(self, w) -> None:
+        import numpy as np
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float32))
+        _lib.check(self.lib.dbscan_scheduler_weights(self.ctx, w.ctypes.data, w.size, 1), "dbscan_scheduler_weights")
+
+    def scheduler_loss_grad(self, feat, lab):
+        """Mean BCE loss and gradient of the network on CUDA tensors feat [n, 6] f32, lab [n] u8."""
+        import numpy as np
+        g = np.zeros(_lib.MLP_PARAMS, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        feat, lab = feat.contiguous(), lab.contiguous()
+        _lib.check(self.lib.dbscan_scheduler_loss_grad(self.ctx, feat.data_ptr(), lab.data_ptr(), feat.shape[0],
+                                                       loss.ctypes.data, g.ctypes.data), "dbscan_scheduler_loss_grad")
+        return float(loss[0]), g
 
     def stats(self) -> dict:
         st = Stats()

@@ -20,9 +20,10 @@ STATUS = {
 }
 F32, F64 = 0, 1
 OPT_PRECISION, OPT_SCHEDULE, OPT_COLLECT_STATS, OPT_MAX_ITERS, OPT_PHASE_TIMING, OPT_CELL_BOUNDS = 0, 1, 2, 3, 4, 5
-OPT_BATCH_GRAPH = 6
+OPT_BATCH_GRAPH, OPT_PAIR_LOG = 6, 7
+MLP_PARAMS = 1313
 PREC_FP64, PREC_FP32_RECHECK = 0, 1
-SCHED_SIZE, SCHED_NONE = 0, 1
+SCHED_SIZE, SCHED_NONE, SCHED_LEARNED = 0, 1, 2
 
 # Every symbol the header declares, with its ctypes signature.
 _P, _I64, _I32, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
@@ -36,6 +37,7 @@ class Stats(ctypes.Structure):
         ("num_neighbor_entries", ctypes.c_int64), ("num_candidate_pairs", ctypes.c_int64),
         ("num_pairs_tested", ctypes.c_int64), ("num_pairs_skipped", ctypes.c_int64),
         ("num_pairs_connected", ctypes.c_int64), ("num_pairs_box_decided", ctypes.c_int64),
+        ("num_pairs_listed", ctypes.c_int64),
         ("num_core_points", ctypes.c_int64),
         ("num_border_points", ctypes.c_int64), ("num_noise_points", ctypes.c_int64),
         ("num_border_memberships", ctypes.c_int64), ("band_rechecks", ctypes.c_int64),
@@ -66,6 +68,10 @@ SIGNATURES = {
     "dbscan_run_batch": (_I32, [_P, ctypes.POINTER(Instance), _I32, _P, _I32, _I32, _P, _P, _P,
                                 ctypes.POINTER(_I64), _P]),
     "dbscan_get_stats": (_I32, [_P, ctypes.POINTER(Stats)]),
+    "dbscan_train_scheduler": (_I32, [_P, _I32, _I32, ctypes.c_float, ctypes.c_uint64, _P]),
+    "dbscan_scheduler_weights": (_I32, [_P, _P, _I32, _I32]),
+    "dbscan_scheduler_loss_grad": (_I32, [_P, _P, _P, _I64, _P, _P]),
+    "dbscan_get_pair_log": (_I32, [_P, _P, _P, _I64, ctypes.POINTER(_I64)]),
     "dbscan_status_string": (ctypes.c_char_p, [_I32]),
     "dbscan_version": (_I32, []),
 }

@@ -12,6 +12,7 @@
 #include "geom.cuh"
 #include "grid.cuh"
 #include "inst.cuh"
+#include "learned.cuh"
 
 using namespace gbdb;
 
@@ -103,11 +104,13 @@ static Bufs make_bufs(dbscan_ctx *c, bool f64) {
     B.bhi = c->bhi;
     B.cblo = c->cblo;
     B.cbhi = c->cbhi;
+    B.ccent = (c->sched == DBSCAN_SCHED_LEARNED || c->log_cap > 0) ? c->ccent : nullptr;
     B.sk0 = c->k0;
     B.sk1 = c->k1;
     B.sv0 = c->v0;
     B.sv1 = c->v1;
     B.sort_scratch = c->sort_scratch;
+    B.sort_scratch_size = c->sort_scratch_size;
     B.max_iters = c->max_iters;
     B.rank = c->rank;
     B.parent = c->parent;
@@ -123,6 +126,66 @@ static Bufs make_bufs(dbscan_ctx *c, bool f64) {
 // Neighbour-offset table of dimension d inside the context.
 static const signed char *offs_for(const dbscan_ctx *c, int d) {
     return c->offs + (size_t)(d - 1) * kMaxOffsets * kMaxEnumDim;
+}
+
+// Xavier-uniform weights, zero biases, from a splitmix64 stream of the seed;
+// clears the Adam state.
+static cudaError_t init_mlp(dbscan_ctx *c, uint64_t seed) {
+    std::vector<float> h(4 * kMlpParams + 1, 0.f);
+    uint64_t st = seed * 0x9e3779b97f4a7c15ull + 1;
+    auto next = [&]() {
+        uint64_t z = (st += 0x9e3779b97f4a7c15ull);
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * 0x1p-53;  // [0, 1)
+    };
+    auto fill = [&](int off, int fan_in, int fan_out) {
+        const double a = std::sqrt(6.0 / (fan_in + fan_out));
+        for (int i = 0; i < fan_in * fan_out; ++i) h[off + i] = (float)((2.0 * next() - 1.0) * a);
+    };
+    fill(kOW1, kMlpIn, kMlpHid);
+    fill(kOW2, kMlpHid, kMlpHid);
+    fill(kOW3, kMlpHid, 1);
+    return cudaMemcpy(c->mlp, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice);
+}
+
+static Learned learned_state(dbscan_ctx *c) {
+    Learned L{};
+    L.w = c->mlp;
+    L.pairs = c->lpairs;
+    L.k0 = c->lk0;
+    L.k1 = c->lk1;
+    L.scratch = c->lscratch;
+    L.scratch_size = c->lscratch_size;
+    L.cap = c->lcap;
+    L.log_feat = c->log_feat;
+    L.log_lab = c->log_lab;
+    L.log_cap = c->log_cap;
+    return L;
+}
+
+// Pair list of the learned schedule: 16 pairs per point of capacity.
+static cudaError_t ensure_learned(dbscan_ctx *c) {
+    if (c->lpairs) return cudaSuccess;
+    const long long cap = 16 * std::max<int64_t>(c->max_points, 1);
+    cudaError_t e = cudaMalloc((void **)&c->lpairs, sizeof(int2) * cap);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->lk0, sizeof(uint64_t) * cap);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->lk1, sizeof(uint64_t) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&c->lscratch, sort_scratch_bytes(cap));
+    if (e == cudaSuccess) {
+        c->lscratch_size = sort_scratch_bytes(cap);
+        c->lcap = cap;
+        return cudaSuccess;
+    }
+    cudaFree(c->lpairs);
+    cudaFree(c->lk0);
+    cudaFree(c->lk1);
+    cudaFree(c->lscratch);
+    c->lpairs = nullptr;
+    c->lk0 = c->lk1 = nullptr;
+    c->lscratch = nullptr;
+    return e;
 }
 
 dbscan_status gbdb_enqueue_batch_prologue(dbscan_ctx *c, const void *d_points, int ld, int dtype, int count,
@@ -159,6 +222,7 @@ static dbscan_status enqueue_core(dbscan_ctx *c, const RunParams &P, int D, int 
     S.v0 = c->v0;
     S.v1 = c->v1;
     S.sort_scratch = c->sort_scratch;
+    S.sort_scratch_size = c->sort_scratch_size;
     S.part = c->part;
     S.cell_key = c->cell_key;
     S.count = c->core_pos;  // scratch until the compaction
@@ -188,9 +252,19 @@ static dbscan_status enqueue_core(dbscan_ctx *c, const RunParams &P, int D, int 
     launch_markcore(D, mode, P, B, c->ctr, s);
     mark(5);
     launch_core_compact(SD, P, B, c->ctr, s);
-    const uint32_t *order = launch_schedule(c->sched, P, B, c->ctr, s);
-    mark(6);
-    launch_connect(D, mode, order, P, B, c->ctr, s);
+    if (B.ccent) {
+        // learned schedule (or a logging run for its training)
+        if (ensure_learned(c) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return DBSCAN_ERR_OOM;
+        }
+        mark(6);
+        launch_connect_learned(D, mode, c->log_cap > 0, P, B, learned_state(c), c->ctr, s);
+    } else {
+        const uint32_t *order = launch_schedule(c->sched, P, B, c->ctr, s);
+        mark(6);
+        launch_connect(D, mode, order, P, B, c->ctr, s);
+    }
     mark(7);
     launch_labels(P, B, d_core, d_labels, c->ctr, s);
     launch_border(D, mode, false, P, B, d_labels, nullptr, 0, c->ctr, s);
@@ -231,6 +305,8 @@ static dbscan_status finish_run(dbscan_ctx *c, const RunParams &P, int D, int mo
             if (cudaEventElapsedTime(&st.phase_ms[k], c->ev[k], c->ev[k + 1]) != cudaSuccess) st.phase_ms[k] = 0.f;
         (void)cudaGetLastError();
     }
+    if (c->log_cap > 0) c->log_count = std::min<long long>(h.P_list, c->log_cap);
+    st.num_pairs_listed = h.P_list;
     if (h.err) return (dbscan_status)h.err;
     if (num_border_memberships) *num_border_memberships = h.K;
     c->have_run = true;
@@ -272,6 +348,12 @@ void dbscan_destroy(dbscan_ctx *c) {
     cudaFreeHost(c->h_bbox);
     cudaFreeHost(c->h_inst);
     gbdb_batch_free(c);
+    cudaFree(c->lpairs);
+    cudaFree(c->lk0);
+    cudaFree(c->lk1);
+    cudaFree(c->lscratch);
+    cudaFree(c->log_feat);
+    cudaFree(c->log_lab);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
@@ -297,6 +379,7 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
     c->nbr_cap = (long long)noff_max * N + 1;
     const int64_t npart = scan_partials(N + 1) + 2;
     const uint64_t hcap = hash_capacity((int)N);
+    c->sort_scratch_size = sort_scratch_bytes(N);
     const int SD = c->sd_max;
 
     // Carve one arena.
@@ -318,6 +401,7 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
         {(void **)&c->ccs, 4 * (size_t)(N + 1)}, {(void **)&c->core_orig, 4 * (size_t)N},
         {(void **)&c->core_cell, 4 * (size_t)N}, {(void **)&c->rank, 4 * (size_t)N},
         {(void **)&c->cell_inst, 4 * (size_t)N}, {(void **)&c->d_inst, sizeof(Inst)},
+        {(void **)&c->ccent, 16 * (size_t)N}, {(void **)&c->mlp, sizeof(float) * (4 * kMlpParams + 1)},
         {(void **)&c->blo, 16 * (size_t)N}, {(void **)&c->bhi, 16 * (size_t)N},
         {(void **)&c->cblo, 16 * (size_t)N}, {(void **)&c->cbhi, 16 * (size_t)N},
         {(void **)&c->parent, 4 * (size_t)N}, {(void **)&c->compmin, 4 * (size_t)N},
@@ -344,6 +428,7 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
                        cudaMemcpyHostToDevice);
     }
     c->hcap = hcap;
+    if (e == cudaSuccess) e = init_mlp(c, 1);
     if (e == cudaSuccess) e = cudaMemset(c->ht, 0xff, sizeof(ulonglong2) * hcap);
     if (e == cudaSuccess) e = cudaMemset(c->hcnt, 0, sizeof(unsigned) * hcap);
     c->table_clean = e == cudaSuccess;
@@ -364,7 +449,8 @@ dbscan_status dbscan_set_option(dbscan_ctx *c, int option, int64_t value) {
         c->precision = (int)value;
         return DBSCAN_OK;
     case DBSCAN_OPT_SCHEDULE:
-        if (value != DBSCAN_SCHED_SIZE && value != DBSCAN_SCHED_NONE) return DBSCAN_ERR_INVALID_ARG;
+        if (value != DBSCAN_SCHED_SIZE && value != DBSCAN_SCHED_NONE && value != DBSCAN_SCHED_LEARNED)
+            return DBSCAN_ERR_INVALID_ARG;
         c->sched = (int)value;
         return DBSCAN_OK;
     case DBSCAN_OPT_COLLECT_STATS:
@@ -375,6 +461,27 @@ dbscan_status dbscan_set_option(dbscan_ctx *c, int option, int64_t value) {
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
         c->cell_bounds = (int)value;
         return DBSCAN_OK;
+    case DBSCAN_OPT_PAIR_LOG: {
+        if (value < 0 || value > (1ll << 31)) return DBSCAN_ERR_INVALID_ARG;
+        cudaFree(c->log_feat);
+        cudaFree(c->log_lab);
+        c->log_feat = nullptr;
+        c->log_lab = nullptr;
+        c->log_cap = 0;
+        c->log_count = 0;
+        if (value > 0) {
+            cudaError_t e = cudaMalloc((void **)&c->log_feat, sizeof(float) * kMlpIn * value);
+            if (e == cudaSuccess) e = cudaMalloc((void **)&c->log_lab, (size_t)value);
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                cudaFree(c->log_feat);
+                c->log_feat = nullptr;
+                return DBSCAN_ERR_OOM;
+            }
+            c->log_cap = value;
+        }
+        return DBSCAN_OK;
+    }
     case DBSCAN_OPT_BATCH_GRAPH:
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
         c->use_graph = (int)value;
@@ -602,6 +709,64 @@ dbscan_status dbscan_run_batch(dbscan_ctx *c, const dbscan_instance *hi, int cou
     }
     CK(cudaStreamSynchronize(s));
     return finish_run(c, P, D, mode, d_points, dtype, total, num_border_memberships, launches0);
+}
+
+dbscan_status dbscan_train_scheduler(dbscan_ctx *c, int epochs, int batch, float lr, uint64_t seed, float *h_losses) {
+    if (!c || epochs < 1 || batch < 1 || !(lr > 0.f)) return DBSCAN_ERR_INVALID_ARG;
+    const long long n = c->log_count;
+    if (n <= 0) return DBSCAN_ERR_STATE;
+    CK(init_mlp(c, seed));
+    float *w = c->mlp, *g = c->mlp + kMlpParams, *m1 = g + kMlpParams, *m2 = m1 + kMlpParams, *loss = m2 + kMlpParams;
+    const long long nb = std::min<long long>(batch, n);
+    const long long steps = (n + nb - 1) / nb;
+    int t = 0;
+    uint64_t st = seed ^ 0x5bd1e995ull;
+    for (int ep = 0; ep < epochs; ++ep) {
+        CK(cudaMemset(loss, 0, sizeof(float)));
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        const long long start = (long long)((st >> 17) % (uint64_t)n);
+        for (long long k = 0; k < steps; ++k) {
+            CK(cudaMemsetAsync(g, 0, sizeof(float) * kMlpParams, 0));
+            mlp_loss_grad(w, c->log_feat, c->log_lab, (start + k * nb) % n, nb, n, g, loss, 0);
+            mlp_adam(w, g, m1, m2, lr, ++t, 0);
+        }
+        float l = 0.f;
+        CK(cudaMemcpy(&l, loss, sizeof(float), cudaMemcpyDeviceToHost));
+        if (h_losses) h_losses[ep] = l / (float)steps;
+    }
+    CK(cudaGetLastError());
+    return DBSCAN_OK;
+}
+
+dbscan_status dbscan_scheduler_weights(dbscan_ctx *c, float *h_weights, int count, int set) {
+    if (!c || !h_weights || count != kMlpParams) return DBSCAN_ERR_INVALID_ARG;
+    CK(cudaMemcpy(set ? (void *)c->mlp : (void *)h_weights, set ? (const void *)h_weights : (const void *)c->mlp,
+                  sizeof(float) * kMlpParams, set ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost));
+    return DBSCAN_OK;
+}
+
+dbscan_status dbscan_scheduler_loss_grad(dbscan_ctx *c, const float *d_features, const uint8_t *d_labels,
+                                         int64_t n, float *h_loss, float *h_grad) {
+    if (!c || !d_features || !d_labels || n < 1 || !h_loss || !h_grad) return DBSCAN_ERR_INVALID_ARG;
+    float *g = c->mlp + kMlpParams, *loss = c->mlp + 4 * kMlpParams;
+    CK(cudaMemset(g, 0, sizeof(float) * kMlpParams));
+    CK(cudaMemset(loss, 0, sizeof(float)));
+    mlp_loss_grad(c->mlp, d_features, d_labels, 0, n, n, g, loss, 0);
+    CK(cudaGetLastError());
+    CK(cudaMemcpy(h_grad, g, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(h_loss, loss, sizeof(float), cudaMemcpyDeviceToHost));
+    return DBSCAN_OK;
+}
+
+dbscan_status dbscan_get_pair_log(dbscan_ctx *c, float *d_features, uint8_t *d_labels, int64_t capacity,
+                                  int64_t *count) {
+    if (!c || !count) return DBSCAN_ERR_INVALID_ARG;
+    *count = c->log_count;
+    if (c->log_count == 0) return DBSCAN_OK;
+    if (capacity < c->log_count || !d_features || !d_labels) return DBSCAN_ERR_CAPACITY;
+    CK(cudaMemcpy(d_features, c->log_feat, sizeof(float) * kMlpIn * c->log_count, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(d_labels, c->log_lab, (size_t)c->log_count, cudaMemcpyDeviceToDevice));
+    return DBSCAN_OK;
 }
 
 dbscan_status dbscan_border_ids(dbscan_ctx *c, int32_t *d_ids, int64_t capacity, void *stream) {

@@ -2,6 +2,7 @@
 // (Algorithm 4) on the cell structure built by grid.cu.
 #include <climits>
 
+#include "bcp.cuh"
 #include "geom.cuh"
 #include "grid.cuh"
 
@@ -13,25 +14,6 @@ __device__ __forceinline__ void flush_counter(unsigned long long *dst, unsigned 
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
 }
-
-#define GBDB_DISPATCH(D, MODE, ...)                                     \
-    do {                                                                \
-        switch ((D) * 4 + (MODE)) {                                     \
-        case 8: { constexpr int DD = 2, MM = 0; __VA_ARGS__; } break;   \
-        case 9: { constexpr int DD = 2, MM = 1; __VA_ARGS__; } break;   \
-        case 10: { constexpr int DD = 2, MM = 2; __VA_ARGS__; } break;  \
-        case 11: { constexpr int DD = 2, MM = 3; __VA_ARGS__; } break;  \
-        case 12: { constexpr int DD = 3, MM = 0; __VA_ARGS__; } break;  \
-        case 13: { constexpr int DD = 3, MM = 1; __VA_ARGS__; } break;  \
-        case 14: { constexpr int DD = 3, MM = 2; __VA_ARGS__; } break;  \
-        case 15: { constexpr int DD = 3, MM = 3; __VA_ARGS__; } break;  \
-        case 16: { constexpr int DD = 4, MM = 0; __VA_ARGS__; } break;  \
-        case 17: { constexpr int DD = 4, MM = 1; __VA_ARGS__; } break;  \
-        case 18: { constexpr int DD = 4, MM = 2; __VA_ARGS__; } break;  \
-        case 19: { constexpr int DD = 4, MM = 3; __VA_ARGS__; } break;  \
-        default: break;                                                 \
-        }                                                               \
-    } while (0)
 
 // ----------------------------------------------------------------- MarkCore
 // A cell with at least minPts points marks all of them core (all its points
@@ -244,7 +226,7 @@ void launch_core_compact(int SD, const RunParams &P, const Bufs &B, DevCounters 
     if (SD == 2) go(k_core_compact<2>);
     else if (SD == 4) go(k_core_compact<4>);
     else go(k_core_compact<8>);
-    if (P.box) launch_boxes(SD, B.cpf, B.ccs, ctr, B.cblo, B.cbhi, s);
+    if (P.box || B.ccent) launch_boxes(SD, B.cpf, B.ccs, ctr, B.cblo, B.cbhi, s, B.ccent);
 }
 
 // ----------------------------------------------------------------- schedule
@@ -281,7 +263,7 @@ const uint32_t *launch_schedule(int sched, const RunParams &P, const Bufs &B, De
         int g = grid_for((const void *)k_size_keys, 256);
         k_size_keys<<<g, 256, 0, s>>>(B.ccs, B.sk0, ctr); count_launch();
         int which = radix_sort_u64(B.sk0, nullptr, B.sk1, nullptr, 0, &ctr->m, B.n_max, 32, kSizeKeyBits,
-                                   B.sort_scratch, ctr, P.max_iters, s);
+                                   B.sort_scratch, B.sort_scratch_size, ctr, P.max_iters, s);
         sorted = which ? B.sk1 : B.sk0;
     }
     int g = grid_for((const void *)k_rank, 256);
@@ -290,57 +272,6 @@ const uint32_t *launch_schedule(int sched, const RunParams &P, const Bufs &B, De
 }
 
 // ----------------------------------------------------------------- connect
-// Connected(g, h) over core points (Sec. 4.4, BCP-based cell graph): stop at
-// the first pair within eps.  The warp tests a block of 32 point pairs per
-// step and leaves on a warp vote.  The smaller cell's points stay in
-// registers: with nc <= 32 columns, each lane holds one column point and the
-// warp covers 32/L rows per step (L = lanes per row).
-template <int D, int M>
-__device__ __forceinline__ bool bcp_warp(int r0, int nr, int c0, int nc, const float *__restrict__ cpf,
-                                         const double *__restrict__ cpd, const RunParams &P, const Thr &T,
-                                         unsigned &rech, unsigned long long &evals) {
-    const int lane = threadIdx.x & 31;
-    if (nc <= 32) {
-        int lg = 0;
-        while ((1 << lg) < nc) ++lg;
-        const int L = 1 << lg;
-        const int R = 32 >> lg;
-        const int j = lane & (L - 1), rr = lane >> lg;
-        const bool qv = j < nc;
-        Pt<D, M> q;
-        if (qv) load_pt(q, cpf, cpd, c0 + j);
-        for (int rb = 0; rb < nr; rb += R) {
-            const int r = rb + rr;
-            bool t = false;
-            if (qv && r < nr) {
-                Pt<D, M> p;
-                load_pt(p, cpf, cpd, r0 + r);
-                if (P.stats) ++evals;
-                t = within(p, q, T, cpd, r0 + r, cpd, c0 + j, rech);
-            }
-            if (__any_sync(0xffffffffu, t)) return true;
-        }
-        return false;
-    }
-    for (int cb = 0; cb < nc; cb += 32) {
-        const int j = cb + lane;
-        const bool qv = j < nc;
-        Pt<D, M> q;
-        if (qv) load_pt(q, cpf, cpd, c0 + j);
-        for (int r = 0; r < nr; ++r) {
-            bool t = false;
-            if (qv) {
-                Pt<D, M> p;
-                load_pt(p, cpf, cpd, r0 + r);
-                if (P.stats) ++evals;
-                t = within(p, q, T, cpd, r0 + r, cpd, c0 + j, rech);
-            }
-            if (__any_sync(0xffffffffu, t)) return true;
-        }
-    }
-    return false;
-}
-
 // ClusterCore's pair loop (Algorithm 3).  A warp takes the next CN_CELLS core
 // cells in SortBySize order with one atomic; each cell owns its pairs with
 // neighbouring core cells that come later in that order.  The warp flattens
@@ -472,6 +403,12 @@ __global__ void __launch_bounds__(256) k_uf_compress(int *parent, DevCounters *c
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x)
         parent[c] = uf_find(parent, c, max_iters, ctr);
+}
+
+void launch_uf_compress(int *parent, DevCounters *ctr, int max_iters, cudaStream_t s) {
+    const int g = grid_for((const void *)k_uf_compress, 256);
+    k_uf_compress<<<g, 256, 0, s>>>(parent, ctr, max_iters);
+    count_launch();
 }
 
 __global__ void __launch_bounds__(256) k_uf_init(int *parent, const DevCounters *ctr) {

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "learned.cuh"
 
 namespace gbdb {
 // Neighbour-offset table of dimension d (<= kMaxEnumDim), kMaxEnumDim bytes per
@@ -35,6 +36,7 @@ struct dbscan_ctx {
     uint64_t *k0 = nullptr, *k1 = nullptr;
     uint32_t *v0 = nullptr, *v1 = nullptr;
     void *sort_scratch = nullptr;
+    size_t sort_scratch_size = 0;
     long long *part = nullptr;
     uint32_t *slot_of = nullptr, *rank_of = nullptr, *slots = nullptr;  // cell grouping
     unsigned *hcnt = nullptr;
@@ -65,6 +67,17 @@ struct dbscan_ctx {
     long long graph_launches = 0;  // kernel nodes of the captured graph
     unsigned long long graph_key[12] = {0};
     float4 *blo = nullptr, *bhi = nullptr, *cblo = nullptr, *cbhi = nullptr;  // cell / core-point boxes
+    float4 *ccent = nullptr;  // core-point centroids (learned schedule)
+    // learned schedule: network (device), its Adam state, pair list, pair log
+    float *mlp = nullptr;     // [4 * kMlpParams + 1]: weights, grad, m1, m2, loss
+    int2 *lpairs = nullptr;
+    void *lscratch = nullptr;
+    size_t lscratch_size = 0;
+    uint64_t *lk0 = nullptr, *lk1 = nullptr;
+    long long lcap = 0;
+    float *log_feat = nullptr;
+    unsigned char *log_lab = nullptr;
+    long long log_cap = 0, log_count = 0;
     int *parent = nullptr, *compmin = nullptr;
     int *noncore = nullptr;
     long long *bcount = nullptr, *boff = nullptr;

@@ -327,7 +327,7 @@ void launch_semisort(const void *X, int dtype, const RunParams &P, int SD, const
     int g = grid_for((const void *)k_cell_keys, 256);
     k_cell_keys<<<g, 256, 0, s>>>(S.ht, S.slots, S.k0, S.v0, ctr); count_launch();
     const int which = radix_sort_u64(S.k0, S.v0, S.k1, S.v1, 0, &ctr->m, P.n, S.key_lo, S.key_bits, S.sort_scratch,
-                                     ctr, P.max_iters, s);
+                                     S.sort_scratch_size, ctr, P.max_iters, s);
     const uint64_t *K = which ? S.k1 : S.k0;
     const uint32_t *V = which ? S.v1 : S.v0;
     g = grid_for((const void *)k_cell_table, 256);
@@ -363,12 +363,13 @@ void launch_table_reset(const Semisort &S, DevCounters *ctr, cudaStream_t s) {
 template <int SD>
 __global__ void __launch_bounds__(256)
 k_boxes(const float *__restrict__ pts, const int *__restrict__ start, const DevCounters *ctr,
-        float4 *__restrict__ lo, float4 *__restrict__ hi) {
+        float4 *__restrict__ lo, float4 *__restrict__ hi, float4 *__restrict__ cent) {
     const int m = ctr->m;
     const int lane = threadIdx.x & 31;
     for (int c = warp_id_global(); c < m; c += warps_global()) {
         const int s0 = start[c], s1 = start[c + 1];
         float l[4] = {INFINITY, INFINITY, INFINITY, INFINITY}, h[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        float sm[4] = {0.f, 0.f, 0.f, 0.f};
         for (int t = s0 + lane; t < s1; t += 32) {
             float x[4] = {0.f, 0.f, 0.f, 0.f};
             if constexpr (SD == 2) {
@@ -380,7 +381,7 @@ k_boxes(const float *__restrict__ pts, const int *__restrict__ start, const DevC
                 x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) { l[j] = fminf(l[j], x[j]); h[j] = fmaxf(h[j], x[j]); }
+            for (int j = 0; j < 4; ++j) { l[j] = fminf(l[j], x[j]); h[j] = fmaxf(h[j], x[j]); sm[j] += x[j]; }
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -388,23 +389,28 @@ k_boxes(const float *__restrict__ pts, const int *__restrict__ start, const DevC
             for (int o = 16; o > 0; o >>= 1) {
                 l[j] = fminf(l[j], __shfl_xor_sync(0xffffffffu, l[j], o));
                 h[j] = fmaxf(h[j], __shfl_xor_sync(0xffffffffu, h[j], o));
+                if (cent) sm[j] += __shfl_xor_sync(0xffffffffu, sm[j], o);
             }
         }
         if (lane == 0) {
             lo[c] = make_float4(l[0], l[1], l[2], l[3]);
             hi[c] = make_float4(h[0], h[1], h[2], h[3]);
+            if (cent) {
+                const float inv = s1 > s0 ? 1.f / (float)(s1 - s0) : 0.f;
+                cent[c] = make_float4(sm[0] * inv, sm[1] * inv, sm[2] * inv, sm[3] * inv);
+            }
         }
     }
 }
 
 void launch_boxes(int SD, const float *pts, const int *start, const DevCounters *ctr, float4 *lo, float4 *hi,
-                  cudaStream_t s) {
+                  cudaStream_t s, float4 *cent) {
     if (SD == 2) {
         int g = grid_for((const void *)k_boxes<2>, 256);
-        k_boxes<2><<<g, 256, 0, s>>>(pts, start, ctr, lo, hi);
+        k_boxes<2><<<g, 256, 0, s>>>(pts, start, ctr, lo, hi, cent);
     } else {
         int g = grid_for((const void *)k_boxes<4>, 256);
-        k_boxes<4><<<g, 256, 0, s>>>(pts, start, ctr, lo, hi);
+        k_boxes<4><<<g, 256, 0, s>>>(pts, start, ctr, lo, hi, cent);
     }
     count_launch();
 }

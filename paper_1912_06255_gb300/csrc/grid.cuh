@@ -28,6 +28,7 @@ struct Semisort {
     uint64_t *k0, *k1;    // sort of the m cell keys
     uint32_t *v0, *v1;
     void *sort_scratch;
+    size_t sort_scratch_size;
     long long *part;
     uint64_t *cell_key;   // [m] keys in Z order
     int *count;           // [m+1] points per cell (scratch for the scan)
@@ -47,9 +48,10 @@ void launch_table_reset(const Semisort &S, DevCounters *ctr, cudaStream_t s);
 void launch_neighbors(const uint64_t *cell_key, const ulonglong2 *ht, uint64_t hcap, const RunParams &P,
                       const signed char *offs, int noff, int n_near, const float4 *blo, const float4 *bhi,
                       int *nbr_cnt, int *nbr_near, int *nbr, DevCounters *ctr, cudaStream_t s);
-// per-cell FP32 bounding boxes of pts[start[c] .. start[c+1])
+// per-cell FP32 bounding boxes of pts[start[c] .. start[c+1]) (and the
+// centroids when cent is not null)
 void launch_boxes(int SD, const float *pts, const int *start, const DevCounters *ctr, float4 *lo, float4 *hi,
-                  cudaStream_t s);
+                  cudaStream_t s, float4 *cent = nullptr);
 
 // Device arrays of one run, shared by the cluster phases.
 struct Bufs {
@@ -71,10 +73,12 @@ struct Bufs {
     int *core_cell;     // cell of compacted core point
     const float4 *blo, *bhi;  // per-cell bounding box of all points
     float4 *cblo, *cbhi;      // per-cell bounding box of the core points
+    float4 *ccent;            // per-cell centroid of the core points (learned schedule)
     // schedule
     uint64_t *sk0, *sk1;
     uint32_t *sv0, *sv1;
     void *sort_scratch;
+    size_t sort_scratch_size;
     int max_iters;
     int *rank;          // [m] position of the cell in test order
     // union-find and labels
@@ -93,6 +97,8 @@ void launch_core_compact(int SD, const RunParams &P, const Bufs &B, DevCounters 
 const uint32_t *launch_schedule(int sched, const RunParams &P, const Bufs &B, DevCounters *ctr, cudaStream_t s);
 void launch_connect(int D, int mode, const uint32_t *order, const RunParams &P, const Bufs &B, DevCounters *ctr,
                     cudaStream_t s);
+// full path compression of the cell union-find
+void launch_uf_compress(int *parent, DevCounters *ctr, int max_iters, cudaStream_t s);
 void launch_labels(const RunParams &P, const Bufs &B, uint8_t *core_out, int32_t *labels_out,
                    DevCounters *ctr, cudaStream_t s);
 // count pass (fill = false) or fill pass (fill = true, ids != null)

@@ -25,10 +25,12 @@ struct DevCounters {
     int n_noncore;   // non-core points (border candidates)
     int cell_next;   // BCP work counters (ranked cells taken), near and far wave
     int cell_next2;
+    int P_list;      // undecided pairs listed by the learned schedule
+    int P_pos;       // ... of which the network predicts connected
     long long E;     // neighbour list entries
     long long P;     // candidate core-cell pairs
     long long K;     // border memberships
-    unsigned long long pair_next;  // BCP work counter
+    unsigned long long pair_next, pair_next2;  // BCP work counters of the pair waves
     unsigned long long pairs_tested, pairs_skipped, pairs_linked, pairs_box;
     unsigned long long band_rechecks;
     unsigned long long dist_evals[3];  // MarkCore, BCP, border
@@ -104,11 +106,13 @@ void scan_i64_to_i64(const long long *in, long long *out, int64_t n_host, const 
 // Stable LSD radix sort of 64-bit keys on key bits [lo, lo + bits), 8 bits a
 // pass, optionally carrying 32-bit values (v0/v1 null: keys only).
 // Ping-pongs between (k0, v0) and (k1, v1); returns 0 if the result is in
-// (k0, v0), 1 if in (k1, v1).  scratch holds sort_scratch_bytes(n_max) bytes.
-// Look-back waits are bounded by max_iters (DEVICE_TIMEOUT in ctr->err).
+// (k0, v0), 1 if in (k1, v1).  scratch holds scratch_bytes bytes, at least
+// sort_scratch_bytes(n_max); a smaller scratch sorts nothing and raises
+// CAPACITY in ctr->err.  Look-back waits are bounded by max_iters
+// (DEVICE_TIMEOUT in ctr->err).
 size_t sort_scratch_bytes(int64_t n_max);
 int radix_sort_u64(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int n_host, const int *n_dev,
-                   int64_t n_max, int lo, int bits, void *scratch, DevCounters *ctr, int max_iters,
+                   int64_t n_max, int lo, int bits, void *scratch, size_t scratch_bytes, DevCounters *ctr, int max_iters,
                    cudaStream_t s);
 
 // Kernel launches issued by this thread (read before and after a run).

@@ -67,6 +67,7 @@ size_t carve(dbscan_ctx *c, unsigned char *base) {
     c->nbr_cap = (long long)noff_max * N + 1;
     const int64_t npart = scan_partials(N + 1) + 2;
     const uint64_t hcap = hash_capacity((int)N);
+    c->sort_scratch_size = sort_scratch_bytes(N);
     struct Item { void **p; size_t bytes; };
     const Item items[] = {
         {(void **)&c->k0, 8 * (size_t)N}, {(void **)&c->k1, 8 * (size_t)N},

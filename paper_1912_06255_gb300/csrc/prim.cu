@@ -183,6 +183,8 @@ size_t sort_scratch_bytes(int64_t n_max) {
     return (size_t)RS_MAX_PASSES * RS_BINS * 4 + 256 + (size_t)RS_MAX_PASSES * rs_tiles(n_max) * RS_BINS * 8;
 }
 
+__global__ void k_flag_error(DevCounters *ctr, int code, int info) { set_error(ctr, code, info); }
+
 __global__ void __launch_bounds__(RS_THREADS)
 k_radix_hist(const uint64_t *__restrict__ keys, int n_host, const int *n_dev, int lo, int passes,
              unsigned *__restrict__ ghist) {
@@ -323,10 +325,15 @@ k_radix_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ v
 }
 
 int radix_sort_u64(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int n_host, const int *n_dev,
-                   int64_t n_max, int lo, int bits, void *scratch, DevCounters *ctr, int max_iters,
-                   cudaStream_t s) {
+                   int64_t n_max, int lo, int bits, void *scratch, size_t scratch_bytes, DevCounters *ctr,
+                   int max_iters, cudaStream_t s) {
     const int passes = (bits + 7) / 8;
     if (passes <= 0) return 0;
+    if (scratch_bytes < sort_scratch_bytes(n_max)) {
+        k_flag_error<<<1, 1, 0, s>>>(ctr, DBSCAN_ERR_CAPACITY, 60);
+        count_launch();
+        return 0;
+    }
     const int64_t tiles = rs_tiles(n_max);
     unsigned *ghist = reinterpret_cast<unsigned *>(scratch);
     int *tile_ctr = reinterpret_cast<int *>(ghist + RS_MAX_PASSES * RS_BINS);
