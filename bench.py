@@ -75,6 +75,14 @@ class Spreader3D:
     def h2d_bytes(self):
         return int(self.I.points.nbytes)
 
+    def log_run(self, ctx, dev):
+        """One run on a held-out input of the same family (seed 2001), for the scheduler's training log."""
+        import torch
+        from paper_1912_06255_gb300 import synth
+        T = synth.spreader_3d_2m(seed=2001, n=self.n)
+        ctx.run(torch.from_numpy(T.points).to(dev), T.eps, T.min_pts, border=False)
+        return T.name
+
     def cpu_sample(self):
         X = np.ascontiguousarray(self.I.points[self.I.points[:, 0] < self.SLAB])
         desc = (f"{len(X)} points with x < {self.SLAB:g} of the {self.n}-point workload (same local density), "
@@ -128,6 +136,21 @@ class Batch256:
 
     def h2d_bytes(self):
         return int(self.P.nbytes)
+
+    def log_run(self, ctx, dev):
+        """A held-out batch of 48 instances of the same family (seed 2003), for the training log."""
+        import torch
+        from paper_1912_06255_gb300 import synth
+        B = synth.batch_256(seed=2003, count=48)
+        n = sum(len(b.points) for b in B)
+        P = np.zeros((n, 3), np.float32)
+        row = 0
+        for b in B:
+            P[row:row + len(b.points), :b.points.shape[1]] = b.points
+            row += len(b.points)
+        ctx.run_batch(torch.from_numpy(P).to(dev), [(len(b.points), b.points.shape[1], b.eps, b.min_pts) for b in B],
+                      border=False)
+        return f"batch_256(seed=2003, count=48), {n} points"
 
     def cpu_sample(self):
         order = sorted(range(len(self.B)), key=lambda i: len(self.B[i].points))
@@ -257,6 +280,50 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+SCHED_CODES = {"size": 0, "none": 1, "learned": 2}
+
+
+def _train_scheduler(W, ctx, dev):
+    """Log every undecided core-cell pair of a held-out input with its exact BCP
+    outcome, then fit the scheduler network to the log on the GPU."""
+    import torch
+    t0 = time.perf_counter()
+    ctx.enable_pair_log(1 << 24)
+    src = W.log_run(ctx, dev)
+    torch.cuda.synchronize()
+    records = ctx.stats()["num_pairs_listed"]
+    losses = ctx.train_scheduler(epochs=30, batch=4096, lr=3e-3, seed=1)
+    ctx.enable_pair_log(0)
+    return {"log_source": src, "records": int(min(records, 1 << 24)), "epochs": 30,
+            "loss_first": round(losses[0], 4), "loss_last": round(losses[-1], 4),
+            "seconds": round(time.perf_counter() - t0, 2)}
+
+
+def _compare_schedules(W, ctx, X, out, flush, stream, steps):
+    """Device time and BCP test counts of each pair schedule on the timed input."""
+    import torch
+    res = {}
+    for name, code in SCHED_CODES.items():
+        ctx.set_option(1, code)
+        for _ in range(2):
+            W.run(ctx, X, out)
+        ms = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            W.run(ctx, X, out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        st = ctx.stats()
+        res[name] = {"ms_per_step": round(sum(ms) / len(ms), 4), "value": round(W.n / (sum(ms) / len(ms) * 1e-3) / 1e6, 1),
+                     "pairs_tested": st["num_pairs_tested"], "pairs_skipped": st["num_pairs_skipped"],
+                     "pairs_box_decided": st["num_pairs_box_decided"], "pairs_listed": st["num_pairs_listed"],
+                     "bcp_distance_evals": st["distance_evals_phase"][1]}
+    return res
+
+
 def run_gpu(args):
     import torch
 
@@ -273,7 +340,9 @@ def run_gpu(args):
     n = W.n
     dev = torch.device("cuda", local)
     X = W.device_input(dev)
-    ctx = W.make_ctx(DBSCAN, precision=args.precision, schedule=args.schedule)
+    ctx = W.make_ctx(DBSCAN, precision=args.precision, schedule="size")
+    training = _train_scheduler(W, ctx, dev) if not args.profile or args.schedule == "learned" else None
+    ctx.set_option(1, SCHED_CODES[args.schedule])
     out = (torch.empty(n, dtype=torch.uint8, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
            torch.empty(n + 1, dtype=torch.int64, device=dev))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -299,6 +368,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     # pair tests per kernel, counted once in an untimed run
     cctx = W.make_ctx(DBSCAN, precision=args.precision, schedule=args.schedule, collect_stats=True)
+    cctx.set_scheduler_weights(ctx.scheduler_weights())
     W.run(cctx, X, out)
     ev_phase = cctx.stats()["distance_evals_phase"]
     cctx.close()
@@ -340,6 +410,7 @@ def run_gpu(args):
 
     # the plain FP64 path on the same input (a few steps, same flush rule)
     ctx64 = W.make_ctx(DBSCAN, precision="fp64", schedule=args.schedule)
+    ctx64.set_scheduler_weights(ctx.scheduler_weights())
     for _ in range(3):
         W.run(ctx64, X, out)
     ms64 = []
@@ -367,6 +438,9 @@ def run_gpu(args):
         b.record(stream)
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
+
+    schedules = _compare_schedules(W, ctx, X, out, flush, stream, max(3, min(args.steps, 5)))
+    ctx.set_option(1, SCHED_CODES[args.schedule])
 
     def max_over_ranks(x):
         if dist is None:
@@ -399,6 +473,7 @@ def run_gpu(args):
             "gpu_launches": int(launches),
             "phase_ms": dict(zip(PHASES, [round(x, 4) for x in ph])),
             "roofline": roof,
+            "schedules": dict(schedules, training=training),
             "pair_tests": {"markcore": ev_phase[0], "connect": ev_phase[1], "border": ev_phase[2]},
             "run_stats": {k: stats[k] for k in ("num_cells", "num_core_cells", "num_candidate_pairs",
                                                  "num_pairs_tested", "num_pairs_skipped", "num_pairs_box_decided",
@@ -425,7 +500,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="spreader3d", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--schedule", default="size", choices=["size", "none"])
+    ap.add_argument("--schedule", default="size", choices=["size", "none", "learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="run warm-up + timed steps only and print no bench line (for ncu)")
