@@ -138,7 +138,11 @@ typedef struct {
  * Create a context able to cluster up to max_points points of dimension up to
  * max_dim.  Allocates the device workspace on the current device (its size
  * grows linearly with max_points and with the number of candidate
- * neighbouring cells of max_dim).  1 <= max_dim <= 4; 0 <= max_points < 2^31-1.
+ * neighbouring cells of min(max_dim, 4)).  1 <= max_dim <= 8;
+ * 0 <= max_points < 2^31-1.  Runs of d >= 5 find neighbouring cells with a
+ * tree over the non-empty cells (Sec. 4.2) instead of offset enumeration;
+ * their tree and neighbour-list buffers are allocated at the first such run
+ * (OOM there if the device is full).
  * Returns OK, INVALID_ARG, UNSUPPORTED_DIM, OOM or CUDA.  *ctx is NULL on error.
  */
 dbscan_status dbscan_create(dbscan_ctx **ctx, int64_t max_points, int max_dim);
@@ -162,8 +166,11 @@ dbscan_status dbscan_set_option(dbscan_ctx *ctx, int option, int64_t value);
  * which is the capacity dbscan_border_ids() needs.
  * The call synchronises the stream twice: once after the bounding-box
  * reduction (its result sizes the cell key) and once at the end to read the
- * device status.  Returns OK, INVALID_ARG, UNSUPPORTED_DIM, KEY_OVERFLOW,
- * CAPACITY, DEVICE_TIMEOUT or CUDA; outputs are undefined unless OK.
+ * device status; for d >= 5 once more after the neighbour counts (their total
+ * sizes the neighbour lists).  Returns OK, INVALID_ARG, UNSUPPORTED_DIM,
+ * KEY_OVERFLOW (d <= 4: more than 2^30 cells in a dimension or more than 63
+ * key bits; d >= 5: more than 2^15 cells in a dimension), CAPACITY,
+ * DEVICE_TIMEOUT or CUDA; outputs are undefined unless OK.
  */
 dbscan_status dbscan_run(dbscan_ctx *ctx, const void *d_points, int64_t n, int d, int dtype,
                          double eps, int64_t min_pts, uint8_t *d_core, int32_t *d_labels,

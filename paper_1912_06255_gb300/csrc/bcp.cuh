@@ -1,5 +1,7 @@
 // BCP connectivity test of two cells' core points and the (D, mode) kernel
 // dispatch, shared by the size-ordered and the learned pair schedules.
+// D is the compiled width: 2, 3 or 4 for d <= 4, and 8 for 5 <= d <= 8
+// (zero-padded coordinates add exact zeros to every sum).
 #pragma once
 
 #include "geom.cuh"
@@ -21,6 +23,10 @@ namespace gbdb {
         case 17: { constexpr int DD = 4, MM = 1; __VA_ARGS__; } break;  \
         case 18: { constexpr int DD = 4, MM = 2; __VA_ARGS__; } break;  \
         case 19: { constexpr int DD = 4, MM = 3; __VA_ARGS__; } break;  \
+        case 32: { constexpr int DD = 8, MM = 0; __VA_ARGS__; } break;  \
+        case 33: { constexpr int DD = 8, MM = 1; __VA_ARGS__; } break;  \
+        case 34: { constexpr int DD = 8, MM = 2; __VA_ARGS__; } break;  \
+        case 35: { constexpr int DD = 8, MM = 3; __VA_ARGS__; } break;  \
         default: break;                                                 \
         }                                                               \
     } while (0)

@@ -92,7 +92,8 @@ static Bufs make_bufs(dbscan_ctx *c, bool f64) {
     B.cell_start = c->cell_start;
     B.nbr_cnt = c->nbr_cnt;
     B.nbr_near = c->nbr_near;
-    B.nbr = c->nbr;
+    B.nbr = c->nbr_cur ? c->nbr_cur : c->nbr;
+    B.nbr_off = c->nbr_off_cur;
     B.core_s = c->core_s;
     B.core_pos = c->core_pos;
     B.ccs = c->ccs;
@@ -193,16 +194,83 @@ dbscan_status gbdb_enqueue_batch_prologue(dbscan_ctx *c, const void *d_points, i
 dbscan_status gbdb_batch_buffers(dbscan_ctx *c, const dbscan_instance *h, int count);
 void gbdb_batch_free(dbscan_ctx *c);
 
-// Steps 3-10 of a run (cells, boxes, neighbour lists, MarkCore, compaction,
-// schedule, BCP connectivity, labels, border counts), then the reset of the
-// cell hash and the read-back of the device counters, all enqueued on s
-// without a host synchronisation (so a batch can be captured in a graph).
+// Buffers of the tree-based neighbour search (5 <= d <= 8), one allocation.
+static cudaError_t ensure_hd(dbscan_ctx *c) {
+    if (c->hd_arena) return cudaSuccess;
+    const size_t N = (size_t)std::max<int64_t>(c->max_points, 1);
+    HdBufs &H = c->hd;
+    struct Item { void **p; size_t bytes; };
+    const Item items[] = {
+        {(void **)&H.klo, 8 * N}, {(void **)&H.khi, 8 * N}, {(void **)&H.ckey_lo, 8 * N},
+        {(void **)&H.ckey_hi, 8 * N}, {(void **)&H.ccoord, 16 * N}, {(void **)&H.child, 8 * N},
+        {(void **)&H.parent, 4 * 2 * N}, {(void **)&H.flag, 4 * N}, {(void **)&H.nlo, 16 * N},
+        {(void **)&H.nhi, 16 * N}, {(void **)&H.cnt64, 8 * N}, {(void **)&H.nbr_off, 8 * (N + 1)},
+    };
+    size_t total = 0;
+    for (const auto &it : items) total += align_up(it.bytes);
+    const cudaError_t e = cudaMalloc(&c->hd_arena, total);
+    if (e != cudaSuccess) {
+        c->hd_arena = nullptr;
+        return e;
+    }
+    size_t at = 0;
+    for (const auto &it : items) {
+        *it.p = (char *)c->hd_arena + at;
+        at += align_up(it.bytes);
+    }
+    return cudaSuccess;
+}
+
+// Steps 3-4 for 5 <= d <= 8: cells by a 128-bit key sort, the tree over the
+// cells, neighbour counts, one read-back of the total to size the lists, then
+// the lists themselves (CSR).  Synchronises the stream once.
 template <typename MarkFn>
-static dbscan_status enqueue_core(dbscan_ctx *c, const RunParams &P, int D, int SD, int mode, const void *d_points,
-                                  int dtype, int d_enum, int sort_lo, int sort_bits, uint8_t *d_core,
-                                  int32_t *d_labels, int64_t *d_border_offsets, cudaStream_t s, MarkFn mark) {
+static dbscan_status enqueue_hd_cells(dbscan_ctx *c, const RunParams &P, const void *d_points, int dtype,
+                                      int key_bits, cudaStream_t s, MarkFn mark) {
+    if (ensure_hd(c) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return DBSCAN_ERR_OOM;
+    }
+    Bufs B = make_bufs(c, dtype == DBSCAN_F64);
+    B.n_max = P.n;
+    mark(2);
+    hd_cells_and_counts(d_points, dtype, P, key_bits, c->hd, B, c->ctr, s);
+    CK(cudaGetLastError());
+    mark(3);
+    CK(cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (c->h_ctr->err) return (dbscan_status)c->h_ctr->err;
+    const long long E = c->h_ctr->E;
+    int *nbr = c->nbr;
+    if (E > c->nbr_cap) {
+        if (E > c->hd_nbr_cap) {
+            cudaFree(c->hd_nbr);
+            c->hd_nbr = nullptr;
+            c->hd_nbr_cap = 0;
+            const long long cap = E + E / 4;
+            if (cudaMalloc((void **)&c->hd_nbr, sizeof(int) * (size_t)cap) != cudaSuccess) {
+                (void)cudaGetLastError();
+                c->hd_nbr = nullptr;
+                return DBSCAN_ERR_OOM;
+            }
+            c->hd_nbr_cap = cap;
+        }
+        nbr = c->hd_nbr;
+    }
+    hd_fill(P, c->hd, B, nbr, c->ctr, s);
+    CK(cudaGetLastError());
+    c->nbr_cur = nbr;
+    c->nbr_off_cur = c->hd.nbr_off;
+    return DBSCAN_OK;
+}
+
+// Steps 3-4 for d <= 4: cells by the hash semisort, neighbour lists by
+// offset enumeration through the hash (fixed stride per cell).
+template <typename MarkFn>
+static dbscan_status enqueue_hash_cells(dbscan_ctx *c, const RunParams &P, int SD, const void *d_points, int dtype,
+                                        int d_enum, int sort_lo, int sort_bits, Semisort &S, cudaStream_t s,
+                                        MarkFn mark) {
     const bool f64 = dtype == DBSCAN_F64;
-    const int64_t n = P.n;
     // 3. cells: group the points by cell (semisort, Sec. 4.1) through the cell hash
     mark(2);
     if (!c->table_clean) {
@@ -210,7 +278,6 @@ static dbscan_status enqueue_core(dbscan_ctx *c, const RunParams &P, int D, int 
         CK(cudaMemsetAsync(c->hcnt, 0, sizeof(unsigned) * c->hcap, s));
     }
     c->table_clean = false;
-    Semisort S{};
     S.ht = c->ht;
     S.hcnt = c->hcnt;
     S.hcap = c->hcap;
@@ -243,11 +310,36 @@ static dbscan_status enqueue_core(dbscan_ctx *c, const RunParams &P, int D, int 
     for (int j = 0; j < d_enum; ++j) n_near *= 3;
     launch_neighbors(c->cell_key, c->ht, c->hcap, P, offs_for(c, d_enum), c->noff[d_enum], n_near - 1, c->blo,
                      c->bhi, c->nbr_cnt, c->nbr_near, c->nbr, c->ctr, s);
+    c->nbr_cur = c->nbr;
+    c->nbr_off_cur = nullptr;
+    return DBSCAN_OK;
+}
+
+// Steps 3-10 of a run (cells, boxes, neighbour lists, MarkCore, compaction,
+// schedule, BCP connectivity, labels, border counts), then the reset of the
+// cell hash and the read-back of the device counters, all enqueued on s
+// without a host synchronisation (so a batch can be captured in a graph).
+template <typename MarkFn>
+static dbscan_status enqueue_core(dbscan_ctx *c, const RunParams &P, int D, int SD, int mode, const void *d_points,
+                                  int dtype, int d_enum, int sort_lo, int sort_bits, uint8_t *d_core,
+                                  int32_t *d_labels, int64_t *d_border_offsets, cudaStream_t s, MarkFn mark) {
+    const bool f64 = dtype == DBSCAN_F64;
+    const int64_t n = P.n;
+    const bool hashed = P.d <= kMaxEnumDim;
+    Semisort S{};
+    if (!hashed) {
+        // 3-4. cells by key sort, neighbour lists by the tree over the cells
+        const dbscan_status st = enqueue_hd_cells(c, P, d_points, dtype, sort_bits, s, mark);
+        if (st != DBSCAN_OK) return st;
+    } else {
+        const dbscan_status st = enqueue_hash_cells(c, P, SD, d_points, dtype, d_enum, sort_lo, sort_bits, S, s, mark);
+        if (st != DBSCAN_OK) return st;
+    }
 
     // 5. MarkCore, 6. compaction, 7. schedule, 8. connect, 9. labels, 10. border
     Bufs B = make_bufs(c, f64);
     B.n_max = n;
-    B.nbr_stride = c->noff[d_enum];
+    B.nbr_stride = hashed ? c->noff[d_enum] : 0;
     mark(4);
     launch_markcore(D, mode, P, B, c->ctr, s);
     mark(5);
@@ -269,7 +361,7 @@ static dbscan_status enqueue_core(dbscan_ctx *c, const RunParams &P, int D, int 
     launch_labels(P, B, d_core, d_labels, c->ctr, s);
     launch_border(D, mode, false, P, B, d_labels, nullptr, 0, c->ctr, s);
     mark(8);
-    launch_table_reset(S, c->ctr, s);
+    if (hashed) launch_table_reset(S, c->ctr, s);
     if (d_border_offsets)
         CK(cudaMemcpyAsync(d_border_offsets, c->boff, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
     CK(cudaGetLastError());
@@ -281,7 +373,7 @@ static dbscan_status enqueue_core(dbscan_ctx *c, const RunParams &P, int D, int 
 // dbscan_border_ids, status of the run.
 static dbscan_status finish_run(dbscan_ctx *c, const RunParams &P, int D, int mode, const void *d_points, int dtype,
                                 int64_t n, int64_t *num_border_memberships, long long launches0) {
-    c->table_clean = c->h_ctr->err == 0;
+    if (P.d <= kMaxEnumDim) c->table_clean = c->h_ctr->err == 0;  // runs of d >= 5 leave the hash alone
     const DevCounters &h = *c->h_ctr;
     dbscan_stats &st = c->stats;
     st.num_cells = h.m;
@@ -352,6 +444,8 @@ void dbscan_destroy(dbscan_ctx *c) {
     cudaFree(c->lk0);
     cudaFree(c->lk1);
     cudaFree(c->lscratch);
+    cudaFree(c->hd_arena);
+    cudaFree(c->hd_nbr);
     cudaFree(c->log_feat);
     cudaFree(c->log_lab);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -364,7 +458,7 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
     if (!out) return DBSCAN_ERR_INVALID_ARG;
     *out = nullptr;
     if (max_points < 0 || max_points >= 0x7ffffffell) return DBSCAN_ERR_INVALID_ARG;
-    if (max_dim < 1 || max_dim > kMaxEnumDim) return DBSCAN_ERR_UNSUPPORTED_DIM;
+    if (max_dim < 1 || max_dim > kMaxDim) return DBSCAN_ERR_UNSUPPORTED_DIM;
     dbscan_ctx *c = new (std::nothrow) dbscan_ctx();
     if (!c) return DBSCAN_ERR_OOM;
     cudaGetDevice(&c->device);
@@ -374,13 +468,14 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
     c->sd_max = max_dim <= 2 ? 2 : (max_dim <= 4 ? 4 : 8);
     for (int d = 1; d <= kMaxEnumDim; ++d) c->noff[d] = num_offsets(d);
     int noff_max = 0;
-    for (int d = 1; d <= max_dim; ++d) noff_max = std::max(noff_max, c->noff[d]);
+    for (int d = 1; d <= std::min(max_dim, kMaxEnumDim); ++d) noff_max = std::max(noff_max, c->noff[d]);
     c->noff_max = noff_max;
     c->nbr_cap = (long long)noff_max * N + 1;
     const int64_t npart = scan_partials(N + 1) + 2;
     const uint64_t hcap = hash_capacity((int)N);
     c->sort_scratch_size = sort_scratch_bytes(N);
     const int SD = c->sd_max;
+    const size_t BW = SD == 8 ? 2 : 1;  // float4 values per cell box
 
     // Carve one arena.
     struct Item { void **p; size_t bytes; };
@@ -401,9 +496,9 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
         {(void **)&c->ccs, 4 * (size_t)(N + 1)}, {(void **)&c->core_orig, 4 * (size_t)N},
         {(void **)&c->core_cell, 4 * (size_t)N}, {(void **)&c->rank, 4 * (size_t)N},
         {(void **)&c->cell_inst, 4 * (size_t)N}, {(void **)&c->d_inst, sizeof(Inst)},
-        {(void **)&c->ccent, 16 * (size_t)N}, {(void **)&c->mlp, sizeof(float) * (4 * kMlpParams + 1)},
-        {(void **)&c->blo, 16 * (size_t)N}, {(void **)&c->bhi, 16 * (size_t)N},
-        {(void **)&c->cblo, 16 * (size_t)N}, {(void **)&c->cbhi, 16 * (size_t)N},
+        {(void **)&c->ccent, BW * 16 * (size_t)N}, {(void **)&c->mlp, sizeof(float) * (4 * kMlpParams + 1)},
+        {(void **)&c->blo, BW * 16 * (size_t)N}, {(void **)&c->bhi, BW * 16 * (size_t)N},
+        {(void **)&c->cblo, BW * 16 * (size_t)N}, {(void **)&c->cbhi, BW * 16 * (size_t)N},
         {(void **)&c->parent, 4 * (size_t)N}, {(void **)&c->compmin, 4 * (size_t)N},
         {(void **)&c->noncore, 4 * (size_t)N},
         {(void **)&c->bcount, 8 * (size_t)N}, {(void **)&c->boff, 8 * (size_t)(N + 1)},
@@ -529,13 +624,13 @@ dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, 
         return DBSCAN_OK;
     }
     const bool f64 = dtype == DBSCAN_F64;
-    const int D = d <= 2 ? 2 : (d <= 3 ? 3 : 4);
+    const int D = d <= 2 ? 2 : (d <= 3 ? 3 : (d <= 4 ? 4 : 8));
     const long long launches0 = g_launches;
     auto mark = [&](int k) {
         if (c->phase_timing) cudaEventRecord(c->ev[k], s);
     };
     mark(0);
-    const int SD = D == 2 ? 2 : 4;  // storage width of Store<D>
+    const int SD = D == 2 ? 2 : (D == 8 ? 8 : 4);  // storage width of Store<D>
 
     // 1. bounding box (one sync: it sizes the cell key)
     CK(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
@@ -563,8 +658,10 @@ dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, 
         }
         int fp32 = 0;
         Inst &I = c->h_inst[0];
+        // 64-bit keys below 5 dimensions, 128-bit keys of at most 15 bits per dimension above
+        const int key_limit = d <= kMaxEnumDim ? 63 : 15 * d;
         const int st = build_inst(I, eps, min_pts, (int)n, d, lo, hi, f64, c->precision == DBSCAN_PREC_FP32_RECHECK,
-                                  63, &fp32);
+                                  key_limit, &fp32);
         if (st != DBSCAN_OK) return (dbscan_status)st;
         I.row0 = 0;
         P.min_pts = I.thr.min_pts;
@@ -779,7 +876,7 @@ dbscan_status dbscan_border_ids(dbscan_ctx *c, int32_t *d_ids, int64_t capacity,
     const bool f64 = c->last_dtype == DBSCAN_F64;
     Bufs B = make_bufs(c, f64);
     B.n_max = c->last.n;
-    B.nbr_stride = c->noff[c->last.d];
+    B.nbr_stride = c->last.d <= kMaxEnumDim ? c->noff[c->last.d] : 0;
     CK(cudaMemsetAsync(&c->ctr->err, 0, sizeof(int), s));
     launch_border(c->last_D, c->last_mode, true, c->last, B, nullptr, d_ids, capacity, c->ctr, s);
     CK(cudaGetLastError());

@@ -68,7 +68,7 @@ __device__ __forceinline__ void mc_batch(const RunParams &P, const Thr &T, const
             unsigned part[NS];
             if (use_box) {
                 const int hj = __shfl_sync(0xffffffffu, h, j);
-                const float4 lo = blo[hj], hi = bhi[hj];
+                const Bx<D> lo = load_box<D>(blo, hj), hi = load_box<D>(bhi, hj);
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
                     bool partial = false;
@@ -131,9 +131,10 @@ template <int D, int M>
 __global__ void __launch_bounds__(MC_THREADS)
 k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__ pd,
            const int *__restrict__ cell_start, const int *__restrict__ nbr_cnt, const int *__restrict__ nbr,
-           int stride, const float4 *__restrict__ blo, const float4 *__restrict__ bhi, int *__restrict__ core_s,
-           DevCounters *ctr) {
-    __shared__ Pt<D, M> own[MC_WARPS][MC_OWN];
+           int stride, const long long *__restrict__ nbr_off, const float4 *__restrict__ blo,
+           const float4 *__restrict__ bhi, int *__restrict__ core_s, DevCounters *ctr) {
+    constexpr int OWN = D == 8 ? 64 : MC_OWN;  // 8-wide points: at most two slots in registers
+    __shared__ Pt<D, M> own[MC_WARPS][OWN];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int m = ctr->m;
     unsigned rech = 0;
@@ -146,18 +147,19 @@ k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__
             continue;
         }
         const int ne = nbr_cnt[c];
-        const int *nl = nbr + (int64_t)c * stride;
-        for (int b0 = 0; b0 < k; b0 += MC_OWN) {
-            const int kb = min(MC_OWN, k - b0);
+        const int *nl = nbr_list<D>(nbr, nbr_off, stride, c);
+        for (int b0 = 0; b0 < k; b0 += OWN) {
+            const int kb = min(OWN, k - b0);
             __syncwarp();
             for (int i = lane; i < kb; i += 32) load_pt(own[w][i], pf, pd, s0 + b0 + i);
             __syncwarp();
             if (kb <= 32)
                 mc_batch<D, M, 1>(P, T, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, rech, evals);
-            else if (kb <= 64)
+            else if (OWN <= 64 || kb <= 64)
                 mc_batch<D, M, 2>(P, T, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, rech, evals);
             else
-                mc_batch<D, M, 4>(P, T, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, rech, evals);
+                mc_batch<D, M, (OWN > 64 ? 4 : 2)>(P, T, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb,
+                                                   core_s, rech, evals);
         }
     }
     flush_counter(&ctr->band_rechecks, rech);
@@ -168,8 +170,8 @@ void launch_markcore(int D, int mode, const RunParams &P, const Bufs &B, DevCoun
     GBDB_DISPATCH(D, mode, {
         auto k = k_markcore<DD, MM>;
         int g = grid_for((const void *)k, MC_THREADS);
-        k<<<g, MC_THREADS, 0, s>>>(P, B.pf, B.pd, B.cell_start, B.nbr_cnt, B.nbr, B.nbr_stride, B.blo, B.bhi,
-                                   B.core_s, ctr);
+        k<<<g, MC_THREADS, 0, s>>>(P, B.pf, B.pd, B.cell_start, B.nbr_cnt, B.nbr, B.nbr_stride, B.nbr_off,
+                                   B.blo, B.bhi, B.core_s, ctr);
         count_launch();
     });
 }
@@ -287,8 +289,9 @@ template <int D, int M, int WAVE>
 __global__ void __launch_bounds__(256, 2)
 k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict__ rank,
           const int *__restrict__ ccs, const int *__restrict__ nbr_cnt, const int *__restrict__ nbr_near,
-          const int *__restrict__ nbr, int stride, const float *__restrict__ cpf, const double *__restrict__ cpd,
-          const float4 *__restrict__ cblo, const float4 *__restrict__ cbhi, int *parent, DevCounters *ctr) {
+          const int *__restrict__ nbr, int stride, const long long *__restrict__ nbr_off,
+          const float *__restrict__ cpf, const double *__restrict__ cpd, const float4 *__restrict__ cblo,
+          const float4 *__restrict__ cbhi, int *parent, DevCounters *ctr) {
     constexpr bool BOX = (M == kF32FromF32 || M == kF32FromF64);
     const int lane = threadIdx.x & 31;
     const int m = ctr->m;
@@ -338,7 +341,7 @@ k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict
             int b = 0, b0 = 0, nb = 0;
             bool cand = false;
             if (f < total) {
-                b = nbr[(int64_t)a * stride + e];
+                b = nbr_list<D>(nbr, nbr_off, stride, a)[e];
                 b0 = ccs[b];
                 nb = ccs[b + 1] - b0;
                 cand = nb > 0 && rank[b] > r;
@@ -348,7 +351,8 @@ k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict
             int verdict = 0;
             if (use_box && cand) {
                 const Thr T = P.inst[inst_of_cell(P, a)].thr;
-                const float4 alo = cblo[a], ahi = cbhi[a], blo = cblo[b], bhi = cbhi[b];
+                const Bx<D> alo = load_box<D>(cblo, a), ahi = load_box<D>(cbhi, a);
+                const Bx<D> blo = load_box<D>(cblo, b), bhi = load_box<D>(cbhi, b);
                 if (boxes_min_d2<D>(alo, ahi, blo, bhi) > T.hi) verdict = -1;
                 else if (boxes_max_d2<D>(alo, ahi, blo, bhi) <= T.lo) verdict = 1;
             }
@@ -427,13 +431,13 @@ void launch_connect(int D, int mode, const uint32_t *order, const RunParams &P, 
     GBDB_DISPATCH(D, mode, {
         auto k0 = k_connect<DD, MM, 0>;
         int gg = grid_for((const void *)k0, 256);
-        k0<<<gg, 256, 0, s>>>(P, order, B.rank, B.ccs, B.nbr_cnt, B.nbr_near, B.nbr, B.nbr_stride, B.cpf, B.cpd,
+        k0<<<gg, 256, 0, s>>>(P, order, B.rank, B.ccs, B.nbr_cnt, B.nbr_near, B.nbr, B.nbr_stride, B.nbr_off, B.cpf, B.cpd,
                               B.cblo, B.cbhi, B.parent, ctr);
         count_launch();
         int gc = grid_for((const void *)k_uf_compress, 256);
         k_uf_compress<<<gc, 256, 0, s>>>(B.parent, ctr, P.max_iters); count_launch();
         auto k1 = k_connect<DD, MM, 1>;
-        k1<<<gg, 256, 0, s>>>(P, order, B.rank, B.ccs, B.nbr_cnt, B.nbr_near, B.nbr, B.nbr_stride, B.cpf, B.cpd,
+        k1<<<gg, 256, 0, s>>>(P, order, B.rank, B.ccs, B.nbr_cnt, B.nbr_near, B.nbr, B.nbr_stride, B.nbr_off, B.cpf, B.cpd,
                               B.cblo, B.cbhi, B.parent, ctr);
         count_launch();
     });
@@ -541,7 +545,7 @@ k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restr
         load_pt(p, B.pf, B.pd, i);
         int ns = 0;
         const int ne = B.nbr_cnt[g];
-        const int *nl = B.nbr + (int64_t)g * B.nbr_stride;
+        const int *nl = nbr_list<D>(B.nbr, B.nbr_off, B.nbr_stride, g);
         for (int e = -1; e < ne; ++e) {
             const int h = e < 0 ? g : nl[e];
             const int k0 = B.ccs[h], k1 = B.ccs[h + 1];
@@ -553,7 +557,7 @@ k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restr
             bool found = false;
             if constexpr (M == kF32FromF32 || M == kF32FromF64) {
                 if (P.box) {
-                    const float4 lo = B.cblo[h], hi = B.cbhi[h];
+                    const Bx<D> lo = load_box<D>(B.cblo, h), hi = load_box<D>(B.cbhi, h);
                     if (box_min_d2<D>(p.f, lo, hi) > T.hi) continue;  // no core point of h within eps
                     found = box_max_d2<D>(p.f, lo, hi) <= T.lo;      // every core point of h within eps
                 }

@@ -84,6 +84,13 @@ struct dbscan_ctx {
     long long *bbox_out = nullptr;  // [2*kMaxDim + 1], see launch_bbox
     signed char *offs = nullptr;  // [kMaxEnumDim][kMaxOffsets][kMaxEnumDim]
     int noff[gbdb::kMaxEnumDim + 1] = {0};
+    // 5 <= d <= 8: cells, tree and CSR neighbour lists (allocated at the first such run)
+    gbdb::HdBufs hd{};
+    void *hd_arena = nullptr;
+    int *hd_nbr = nullptr;  // lists that outgrow the arena's nbr buffer
+    long long hd_nbr_cap = 0;
+    int *nbr_cur = nullptr;                  // where the last run's neighbour lists live
+    const long long *nbr_off_cur = nullptr;  // their CSR offsets (null: fixed stride)
     gbdb::DevCounters *ctr = nullptr;
     // pinned host
     gbdb::DevCounters *h_ctr = nullptr;

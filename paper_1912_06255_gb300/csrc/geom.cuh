@@ -125,54 +125,97 @@ __device__ __forceinline__ bool within(const Pt<D, M> &p, const Pt<D, M> &q, con
 // carries the same forward-error bound as d2f and the FP32 band applies:
 // max_d2 <= lo means every pair passes the FP64 predicate, min_d2 > hi that
 // none does.
-template <int D> __device__ __forceinline__ float cget(const float4 &v, int j) {
+// Boxes are stored per cell as box_w<D>() float4 values (one for d <= 4, two
+// above), zero-padded past the instance's own dimension.
+template <int D> __host__ __device__ constexpr int box_w() { return D <= 4 ? 1 : 2; }
+template <int D> struct Bx { float4 v[box_w<D>()]; };
+
+__device__ __forceinline__ float cget(const float4 &v, int j) {
     return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
 }
+template <int D> __device__ __forceinline__ float bget(const Bx<D> &b, int j) { return cget(b.v[j >> 2], j & 3); }
+
+template <int D> __device__ __forceinline__ Bx<D> load_box(const float4 *__restrict__ base, int64_t c) {
+    Bx<D> r;
+#pragma unroll
+    for (int k = 0; k < box_w<D>(); ++k) r.v[k] = base[c * box_w<D>() + k];
+    return r;
+}
+template <int D> __device__ __forceinline__ Bx<D> zero_box() {
+    Bx<D> r;
+#pragma unroll
+    for (int k = 0; k < box_w<D>(); ++k) r.v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return r;
+}
 
 template <int D>
-__device__ __forceinline__ float box_max_d2(const float (&p)[D], const float4 &lo, const float4 &hi) {
+__device__ __forceinline__ float box_max_d2(const float (&p)[D], const Bx<D> &lo, const Bx<D> &hi) {
     float s = 0.f;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        const float a = fmaxf(p[j] - cget<D>(lo, j), cget<D>(hi, j) - p[j]);
+        const float a = fmaxf(p[j] - bget<D>(lo, j), bget<D>(hi, j) - p[j]);
         s = j == 0 ? a * a : __fmaf_rn(a, a, s);
     }
     return s;
 }
 
 template <int D>
-__device__ __forceinline__ float box_min_d2(const float (&p)[D], const float4 &lo, const float4 &hi) {
+__device__ __forceinline__ float box_min_d2(const float (&p)[D], const Bx<D> &lo, const Bx<D> &hi) {
     float s = 0.f;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        const float a = fmaxf(fmaxf(cget<D>(lo, j) - p[j], p[j] - cget<D>(hi, j)), 0.f);
+        const float a = fmaxf(fmaxf(bget<D>(lo, j) - p[j], p[j] - bget<D>(hi, j)), 0.f);
         s = j == 0 ? a * a : __fmaf_rn(a, a, s);
     }
     return s;
 }
 
 template <int D>
-__device__ __forceinline__ float boxes_min_d2(const float4 &alo, const float4 &ahi, const float4 &blo,
-                                              const float4 &bhi) {
+__device__ __forceinline__ float boxes_min_d2(const Bx<D> &alo, const Bx<D> &ahi, const Bx<D> &blo,
+                                              const Bx<D> &bhi) {
     float s = 0.f;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        const float a = fmaxf(fmaxf(cget<D>(blo, j) - cget<D>(ahi, j), cget<D>(alo, j) - cget<D>(bhi, j)), 0.f);
+        const float a =
+            fmaxf(fmaxf(bget<D>(blo, j) - bget<D>(ahi, j), bget<D>(alo, j) - bget<D>(bhi, j)), 0.f);
         s = j == 0 ? a * a : __fmaf_rn(a, a, s);
     }
     return s;
 }
 
 template <int D>
-__device__ __forceinline__ float boxes_max_d2(const float4 &alo, const float4 &ahi, const float4 &blo,
-                                              const float4 &bhi) {
+__device__ __forceinline__ float boxes_max_d2(const Bx<D> &alo, const Bx<D> &ahi, const Bx<D> &blo,
+                                              const Bx<D> &bhi) {
     float s = 0.f;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        const float a = fmaxf(cget<D>(bhi, j) - cget<D>(alo, j), cget<D>(ahi, j) - cget<D>(blo, j));
+        const float a = fmaxf(bget<D>(bhi, j) - bget<D>(alo, j), bget<D>(ahi, j) - bget<D>(blo, j));
         s = j == 0 ? a * a : __fmaf_rn(a, a, s);
     }
     return s;
+}
+
+// ------------------------------------------------------------ cell coordinates
+// Cell coordinate of coordinate j of a point: floor(fl64(fl64(x - o) * inv_s)),
+// clamped to [0, kmax].  For FP32 input the FP32 estimate
+// t32 = fl32(fl32(x - o) * fl32(inv_s)) is within eps_t = t * 3.01 * 2^-24 (+ the
+// FP64 value's own 3 * 2^-53 * t) of the FP64 value t64 (x and o = the minimum
+// of FP32 values are exact FP32 numbers), so when t32 is farther than eps_t
+// from an integer both floors agree; only the rest is recomputed in FP64.
+template <typename T>
+__device__ __forceinline__ int cell_coord(T x, const Inst &I, int j) {
+    if constexpr (sizeof(T) == 4) {
+        const float t32 = __fmul_rn(__fsub_rn(x, I.origin32[j]), I.inv_s32);
+        const float fl = floorf(t32);
+        const float e = t32 * 1.8e-7f + 1e-30f;
+        if (t32 - fl > e && (fl + 1.0f) - t32 > e) {
+            const int k = (int)fl;
+            return k < 0 ? 0 : (k > I.kmax[j] ? I.kmax[j] : k);
+        }
+    }
+    const double t = __dmul_rn(__dsub_rn((double)x, I.origin[j]), I.inv_s);
+    const int k = (int)floor(t);
+    return k < 0 ? 0 : (k > I.kmax[j] ? I.kmax[j] : k);
 }
 
 // ------------------------------------------------------------ Morton keys
@@ -322,6 +365,14 @@ __device__ __forceinline__ void uf_link(int *parent, int a, int b, int max_iters
         if (atomicCAS(parent + ra, ra, rb) == ra) return;
     }
     set_error(ctr, DBSCAN_ERR_DEVICE_TIMEOUT, 2);
+}
+
+// Neighbour list of cell c: CSR offsets for d >= 5 (compiled width 8), a
+// fixed stride per cell below.
+template <int D>
+__device__ __forceinline__ const int *nbr_list(const int *nbr, const long long *off, int stride, int c) {
+    if constexpr (D == 8) return nbr + off[c];
+    else return nbr + (long long)c * stride;
 }
 
 __device__ __forceinline__ int warp_id_global() {

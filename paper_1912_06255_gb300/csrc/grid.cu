@@ -120,28 +120,6 @@ void launch_bbox(const void *X, int dtype, int n, int d, int nb, long long *out,
 // are finally moved to their cell's range in one pass.  Slot = {key, cell id};
 // the table is reset to empty after each run by k_table_reset, so a run only
 // touches the slots it uses.
-// Cell coordinate of coordinate j of a point: floor(fl64(fl64(x - o) * inv_s)),
-// clamped to [0, kmax].  For FP32 input the FP32 estimate
-// t32 = fl32(fl32(x - o) * fl32(inv_s)) is within eps_t = t * 3.01 * 2^-24 (+ the
-// FP64 value's own 3 * 2^-53 * t) of the FP64 value t64 (x and o = the minimum
-// of FP32 values are exact FP32 numbers), so when t32 is farther than eps_t
-// from an integer both floors agree; only the rest is recomputed in FP64.
-template <typename T>
-__device__ __forceinline__ int cell_coord(T x, const Inst &I, int j) {
-    if constexpr (sizeof(T) == 4) {
-        const float t32 = __fmul_rn(__fsub_rn(x, I.origin32[j]), I.inv_s32);
-        const float fl = floorf(t32);
-        const float e = t32 * 1.8e-7f + 1e-30f;
-        if (t32 - fl > e && (fl + 1.0f) - t32 > e) {
-            const int k = (int)fl;
-            return k < 0 ? 0 : (k > I.kmax[j] ? I.kmax[j] : k);
-        }
-    }
-    const double t = __dmul_rn(__dsub_rn((double)x, I.origin[j]), I.inv_s);
-    const int k = (int)floor(t);
-    return k < 0 ? 0 : (k > I.kmax[j] ? I.kmax[j] : k);
-}
-
 // Instance of input row i: the last instance whose first row is <= i.
 __device__ __forceinline__ int inst_of_row(const RunParams &P, int i) {
     int lo = 0, hi = P.ninst - 1;
@@ -358,33 +336,42 @@ void launch_table_reset(const Semisort &S, DevCounters *ctr, cudaStream_t s) {
 
 // ---------------------------------------------------------------- boxes
 // Per-cell FP32 bounding box of the points pts[start[c] .. start[c+1]) (exact
-// min/max of the stored FP32 coordinates).  One warp per cell.  Empty ranges
-// get an empty box (+inf, -inf).
+// min/max of the stored FP32 coordinates), and optionally their centroid.  One
+// warp per cell.  Boxes hold BW = SD/4 float4 values per cell (at least one;
+// coordinates past the stored width are zero).  Empty ranges get an empty box
+// (+inf, -inf).
 template <int SD>
 __global__ void __launch_bounds__(256)
 k_boxes(const float *__restrict__ pts, const int *__restrict__ start, const DevCounters *ctr,
         float4 *__restrict__ lo, float4 *__restrict__ hi, float4 *__restrict__ cent) {
+    constexpr int W = SD == 8 ? 8 : 4, BW = W / 4;
     const int m = ctr->m;
     const int lane = threadIdx.x & 31;
     for (int c = warp_id_global(); c < m; c += warps_global()) {
         const int s0 = start[c], s1 = start[c + 1];
-        float l[4] = {INFINITY, INFINITY, INFINITY, INFINITY}, h[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
-        float sm[4] = {0.f, 0.f, 0.f, 0.f};
+        float l[W], h[W], sm[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) { l[j] = INFINITY; h[j] = -INFINITY; sm[j] = 0.f; }
         for (int t = s0 + lane; t < s1; t += 32) {
-            float x[4] = {0.f, 0.f, 0.f, 0.f};
+            float x[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) x[j] = 0.f;
             if constexpr (SD == 2) {
                 const float2 a = reinterpret_cast<const float2 *>(pts)[t];
                 x[0] = a.x;
                 x[1] = a.y;
             } else {
-                const float4 a = reinterpret_cast<const float4 *>(pts)[t];
-                x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+#pragma unroll
+                for (int b = 0; b < BW; ++b) {
+                    const float4 a = reinterpret_cast<const float4 *>(pts)[(int64_t)t * BW + b];
+                    x[4 * b] = a.x; x[4 * b + 1] = a.y; x[4 * b + 2] = a.z; x[4 * b + 3] = a.w;
+                }
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) { l[j] = fminf(l[j], x[j]); h[j] = fmaxf(h[j], x[j]); sm[j] += x[j]; }
+            for (int j = 0; j < W; ++j) { l[j] = fminf(l[j], x[j]); h[j] = fmaxf(h[j], x[j]); sm[j] += x[j]; }
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < W; ++j) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 l[j] = fminf(l[j], __shfl_xor_sync(0xffffffffu, l[j], o));
@@ -392,12 +379,14 @@ k_boxes(const float *__restrict__ pts, const int *__restrict__ start, const DevC
                 if (cent) sm[j] += __shfl_xor_sync(0xffffffffu, sm[j], o);
             }
         }
-        if (lane == 0) {
-            lo[c] = make_float4(l[0], l[1], l[2], l[3]);
-            hi[c] = make_float4(h[0], h[1], h[2], h[3]);
+        if (lane < BW) {
+            const int b = lane;
+            lo[(int64_t)c * BW + b] = make_float4(l[4 * b], l[4 * b + 1], l[4 * b + 2], l[4 * b + 3]);
+            hi[(int64_t)c * BW + b] = make_float4(h[4 * b], h[4 * b + 1], h[4 * b + 2], h[4 * b + 3]);
             if (cent) {
                 const float inv = s1 > s0 ? 1.f / (float)(s1 - s0) : 0.f;
-                cent[c] = make_float4(sm[0] * inv, sm[1] * inv, sm[2] * inv, sm[3] * inv);
+                cent[(int64_t)c * BW + b] =
+                    make_float4(sm[4 * b] * inv, sm[4 * b + 1] * inv, sm[4 * b + 2] * inv, sm[4 * b + 3] * inv);
             }
         }
     }
@@ -405,14 +394,14 @@ k_boxes(const float *__restrict__ pts, const int *__restrict__ start, const DevC
 
 void launch_boxes(int SD, const float *pts, const int *start, const DevCounters *ctr, float4 *lo, float4 *hi,
                   cudaStream_t s, float4 *cent) {
-    if (SD == 2) {
-        int g = grid_for((const void *)k_boxes<2>, 256);
-        k_boxes<2><<<g, 256, 0, s>>>(pts, start, ctr, lo, hi, cent);
-    } else {
-        int g = grid_for((const void *)k_boxes<4>, 256);
-        k_boxes<4><<<g, 256, 0, s>>>(pts, start, ctr, lo, hi, cent);
-    }
-    count_launch();
+    auto go = [&](auto k) {
+        const int g = grid_for((const void *)k, 256);
+        k<<<g, 256, 0, s>>>(pts, start, ctr, lo, hi, cent);
+        count_launch();
+    };
+    if (SD == 2) go(k_boxes<2>);
+    else if (SD == 4) go(k_boxes<4>);
+    else go(k_boxes<8>);
 }
 
 // ---------------------------------------------------------------- neighbours
@@ -450,8 +439,8 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
             for (int j = 0; j < D; ++j) cc[j] = tmp[j];
         }
         const long long base = (long long)c * noff;
-        float4 clo = make_float4(0.f, 0.f, 0.f, 0.f), chi = clo;
-        if (P.box) { clo = blo[c]; chi = bhi[c]; }
+        Bx<D> clo = zero_box<D>(), chi = clo;
+        if (P.box) { clo = load_box<D>(blo, c); chi = load_box<D>(bhi, c); }
         const float hi_thr = I.thr.hi;
         int cnt = 0, near = 0;
         for (int o0 = 0; o0 < noff; o0 += 32 * NB_U) {
@@ -493,7 +482,8 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
                         e[u] = ht[s];
                     }
                     // drop cells whose points are all farther than eps from all of c's
-                    if (h >= 0 && P.box && boxes_min_d2<D>(clo, chi, blo[h], bhi[h]) > hi_thr) h = -1;
+                    if (h >= 0 && P.box && boxes_min_d2<D>(clo, chi, load_box<D>(blo, h), load_box<D>(bhi, h)) > hi_thr)
+                        h = -1;
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, h >= 0);
                 if (h >= 0) nbr[base + cnt + __popc(bal & lt)] = h;

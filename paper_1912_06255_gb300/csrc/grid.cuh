@@ -15,8 +15,6 @@ inline double bbox_key_to_double(long long k) {
     __builtin_memcpy(&x, &b, sizeof x);
     return x;
 }
-void launch_keys(const void *X, int dtype, const RunParams &P, uint64_t *keys, uint32_t *vals,
-                 cudaStream_t s);
 // Buffers of the cell grouping (semisort) of one run.
 struct Semisort {
     const void *unused;
@@ -63,6 +61,7 @@ struct Bufs {
     const int *nbr_near; // [m] how many of them are at |delta|_inf <= 1 (listed first)
     const int *nbr;
     int nbr_stride;
+    const long long *nbr_off;  // [m] CSR offsets of the lists (d >= 5); null: fixed stride
     // MarkCore / compaction
     int *core_s;        // [n] 0/1 in cell order
     int *core_pos;      // [n+1] exclusive scan of core_s
@@ -97,6 +96,25 @@ void launch_core_compact(int SD, const RunParams &P, const Bufs &B, DevCounters 
 const uint32_t *launch_schedule(int sched, const RunParams &P, const Bufs &B, DevCounters *ctr, cudaStream_t s);
 void launch_connect(int D, int mode, const uint32_t *order, const RunParams &P, const Bufs &B, DevCounters *ctr,
                     cudaStream_t s);
+// ---- cells and neighbour lists for 5 <= d <= 8 (hd.cu)
+struct HdBufs {
+    uint64_t *klo, *khi;          // [n] 128-bit Morton key of each point's cell (low, high word)
+    uint64_t *ckey_lo, *ckey_hi;  // [m] cell keys, Z order
+    int4 *ccoord;                 // [m] cell coordinates, 8 x 16 bits
+    int2 *child;                  // [m-1] children of the internal tree nodes (leaf of cell c: m-1+c)
+    int *parent;                  // [2m-1] parent of each node (-1 at the root)
+    int *flag;                    // [m-1] arrival counters of the bottom-up pass
+    int4 *nlo, *nhi;              // [m-1] node bounds in cell coordinates, 8 x 16 bits
+    long long *cnt64;             // [m] neighbours per cell
+    long long *nbr_off;           // [m+1] CSR offsets of the neighbour lists
+};
+// Cells of the sorted points, their tree and the neighbour counts; ctr->E
+// receives the total (read it back to size the lists).  key_bits = d * bits.
+void hd_cells_and_counts(const void *X, int dtype, const RunParams &P, int key_bits, const HdBufs &H,
+                         const Bufs &B, DevCounters *ctr, cudaStream_t s);
+// The neighbour lists at H.nbr_off into nbr.
+void hd_fill(const RunParams &P, const HdBufs &H, const Bufs &B, int *nbr, DevCounters *ctr, cudaStream_t s);
+
 // full path compression of the cell union-find
 void launch_uf_compress(int *parent, DevCounters *ctr, int max_iters, cudaStream_t s);
 void launch_labels(const RunParams &P, const Bufs &B, uint8_t *core_out, int32_t *labels_out,

@@ -1,0 +1,414 @@
+// Cells and neighbour lists for 5 <= d <= 8.
+//
+// Enumerating neighbour offsets does not scale with d: the rule
+// sum_j max(|delta_j| - 1, 0)^2 <= d admits 6,095 offsets in 5D and 257,675
+// in 7D, almost all of them empty cells.  Sec. 4.2 therefore finds the
+// neighbouring cells of high-dimensional inputs with a spatial tree over the
+// non-empty cells.  This file builds that tree the GPU way:
+//   1. every point gets a 128-bit Morton key of its cell coordinates (at most
+//      15 bits per dimension);
+//   2. a stable LSD radix sort orders the points by key (low word, then high
+//      word), which groups them by cell and lays the cells out in Z order;
+//   3. a linear BVH over the cells in that order (each internal node splits at
+//      the highest differing key bit, built for all nodes at once), with
+//      integer cell-coordinate bounds set bottom-up;
+//   4. one traversal per cell lists the cells that satisfy the offset rule
+//      exactly (integer arithmetic), in two passes: counts, then the lists at
+//      CSR offsets, cells at |delta|_inf <= 1 first.
+#include <cuda_runtime.h>
+
+#include "geom.cuh"
+#include "grid.cuh"
+
+namespace gbdb {
+
+namespace {
+
+constexpr int kStack = 160;  // >= depth of the tree (at most key bits + 1)
+
+// Cell coordinates are packed as 8 unsigned 16-bit values in an int4
+// (component k holds dimensions 2k and 2k + 1).
+__device__ __forceinline__ int unpack16(const int4 &v, int j) {
+    const int w = (j >> 1) == 0 ? v.x : ((j >> 1) == 1 ? v.y : ((j >> 1) == 2 ? v.z : v.w));
+    return (j & 1) ? ((unsigned)w >> 16) : (w & 0xffff);
+}
+__device__ __forceinline__ int4 pack16(const int (&c)[8]) {
+    return make_int4(c[0] | (c[1] << 16), c[2] | (c[3] << 16), c[4] | (c[5] << 16), c[6] | (c[7] << 16));
+}
+
+// Bit b of dimension j goes to key bit b*d + j of the 128-bit key (hi:lo).
+__device__ __forceinline__ void morton128(const int (&c)[8], int d, int bits, uint64_t &lo, uint64_t &hi) {
+    lo = 0;
+    hi = 0;
+    for (int b = 0; b < bits; ++b)
+        for (int j = 0; j < d; ++j) {
+            const uint64_t bit = (uint64_t)((c[j] >> b) & 1);
+            const int p = b * d + j;
+            if (p < 64) lo |= bit << p;
+            else hi |= bit << (p - 64);
+        }
+}
+
+__device__ __forceinline__ void unmorton128(uint64_t lo, uint64_t hi, int d, int bits, int (&c)[8]) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) c[j] = 0;
+    for (int b = 0; b < bits; ++b)
+        for (int j = 0; j < d; ++j) {
+            const int p = b * d + j;
+            const int bit = (int)((p < 64 ? (lo >> p) : (hi >> (p - 64))) & 1);
+            c[j] |= bit << b;
+        }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_hd_keys(const T *__restrict__ X, RunParams P, uint64_t *__restrict__ klo, uint64_t *__restrict__ khi,
+          uint64_t *__restrict__ k0, uint32_t *__restrict__ v0) {
+    const Inst &I = P.inst[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+        int c[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) c[j] = j < P.d ? cell_coord<T>(X[(int64_t)i * P.d + j], I, j) : 0;
+        uint64_t lo, hi;
+        morton128(c, P.d, I.bits, lo, hi);
+        klo[i] = lo;
+        khi[i] = hi;
+        k0[i] = lo;
+        v0[i] = (uint32_t)i;
+    }
+}
+
+// kh[t] = khi[idx[t]]: the high words in the order of the low-word sort.
+__global__ void __launch_bounds__(256)
+k_hd_gather_hi(const uint64_t *__restrict__ khi, const uint32_t *__restrict__ idx, uint64_t *__restrict__ kh, int n) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) kh[t] = khi[idx[t]];
+}
+
+// flag[t] = 1 where a new cell starts in the sorted order.
+__global__ void __launch_bounds__(256)
+k_hd_flags(const uint64_t *__restrict__ klo, const uint64_t *__restrict__ khi, const uint32_t *__restrict__ idx,
+           int *__restrict__ flag, int n) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        int f = 1;
+        if (t > 0) {
+            const uint32_t a = idx[t], b = idx[t - 1];
+            f = (klo[a] != klo[b] || khi[a] != khi[b]) ? 1 : 0;
+        }
+        flag[t] = f;
+    }
+}
+
+// Cells in sorted order: cell ids, starts, keys and coordinates; the points
+// move to cell order (FP32 copy zero-padded to 8, FP64 copy when kept).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_hd_cells(const T *__restrict__ X, RunParams P, const uint32_t *__restrict__ idx, const uint64_t *__restrict__ klo,
+           const uint64_t *__restrict__ khi, const int *__restrict__ flag, const int *__restrict__ cpos,
+           int *__restrict__ cell_start, uint64_t *__restrict__ ckey_lo, uint64_t *__restrict__ ckey_hi,
+           int4 *__restrict__ ccoord, float *__restrict__ pf, double *__restrict__ pd, int *__restrict__ orig,
+           int *__restrict__ cell_of, DevCounters *ctr) {
+    const int n = P.n, d = P.d;
+    const Inst &I = P.inst[0];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int i = (int)idx[t];
+        const int f = flag[t];
+        const int c = cpos[t] + f - 1;
+        orig[t] = i;
+        cell_of[t] = c;
+        float x32[8];
+        double x64[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            x64[j] = j < d ? (double)X[(int64_t)i * d + j] : 0.0;
+            x32[j] = (float)x64[j];
+        }
+        reinterpret_cast<float4 *>(pf)[(int64_t)t * 2] = make_float4(x32[0], x32[1], x32[2], x32[3]);
+        reinterpret_cast<float4 *>(pf)[(int64_t)t * 2 + 1] = make_float4(x32[4], x32[5], x32[6], x32[7]);
+        if (pd) {
+#pragma unroll
+            for (int j = 0; j < 8; j += 2)
+                reinterpret_cast<double2 *>(pd)[(int64_t)t * 4 + j / 2] = make_double2(x64[j], x64[j + 1]);
+        }
+        if (f) {
+            const uint64_t lo = klo[i], hi = khi[i];
+            cell_start[c] = t;
+            ckey_lo[c] = lo;
+            ckey_hi[c] = hi;
+            int cc[8];
+            unmorton128(lo, hi, d, I.bits, cc);
+            ccoord[c] = pack16(cc);
+        }
+        if (t == 0) {
+            const int m = cpos[n];
+            ctr->m = m;
+            cell_start[m] = n;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ LBVH
+// Nodes 0 .. m-2 are internal (node 0 is the root), node m-1+c is the leaf of
+// cell c.  Internal node i covers a key range with i at one end; its other end
+// and its split are found by binary search over common-prefix lengths.
+__device__ __forceinline__ int prefix(const uint64_t *__restrict__ lo, const uint64_t *__restrict__ hi, int m, int i,
+                                      long long j) {
+    if (j < 0 || j >= m) return -1;
+    const uint64_t a = hi[i] ^ hi[j];
+    if (a) return __clzll((long long)a);
+    return 64 + __clzll((long long)(lo[i] ^ lo[j]));  // keys are distinct
+}
+
+__global__ void __launch_bounds__(256)
+k_lbvh_nodes(const uint64_t *__restrict__ klo, const uint64_t *__restrict__ khi, int2 *__restrict__ child,
+             int *__restrict__ parent, int *__restrict__ flag, const DevCounters *ctr) {
+    const int m = ctr->m;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m - 1; i += gridDim.x * blockDim.x) {
+        flag[i] = 0;
+        const int dir = prefix(klo, khi, m, i, i + 1) > prefix(klo, khi, m, i, i - 1) ? 1 : -1;
+        const int dmin = prefix(klo, khi, m, i, i - dir);
+        long long lmax = 2;
+        while (lmax <= m && prefix(klo, khi, m, i, i + lmax * dir) > dmin) lmax <<= 1;
+        long long l = 0;
+        for (long long t = lmax >> 1; t >= 1; t >>= 1)
+            if (prefix(klo, khi, m, i, i + (l + t) * dir) > dmin) l += t;
+        const int j = (int)(i + l * dir);
+        const int dnode = prefix(klo, khi, m, i, j);
+        long long s = 0;
+        for (long long t = (l + 1) >> 1;; t = (t + 1) >> 1) {
+            if (prefix(klo, khi, m, i, i + (s + t) * dir) > dnode) s += t;
+            if (t <= 1) break;
+        }
+        const int g = (int)(i + s * dir + (dir < 0 ? -1 : 0));
+        const int lo = i < j ? i : j, hi = i < j ? j : i;
+        const int left = lo == g ? (m - 1) + g : g;
+        const int right = hi == g + 1 ? (m - 1) + g + 1 : g + 1;
+        child[i] = make_int2(left, right);
+        parent[left] = i;
+        parent[right] = i;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) parent[0] = -1;  // the root (or the only leaf when m == 1)
+}
+
+// Bounds bottom-up: a leaf's thread climbs while it is the second child to
+// arrive at the parent (atomic counter), so each node is merged once, after
+// both children are final.
+__global__ void __launch_bounds__(256)
+k_lbvh_bounds(const int2 *__restrict__ child, const int *__restrict__ parent, int *__restrict__ flag,
+              const int4 *__restrict__ ccoord, int4 *__restrict__ nlo, int4 *__restrict__ nhi, int d,
+              DevCounters *ctr) {
+    const int m = ctr->m;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+        int node = (m - 1) + c;
+        for (int it = 0;; ++it) {
+            if (it > kStack) {
+                set_error(ctr, DBSCAN_ERR_CAPACITY, 71);
+                break;
+            }
+            const int p = m > 1 ? parent[node] : -1;
+            if (p < 0) break;
+            __threadfence();
+            if (atomicAdd(flag + p, 1) == 0) break;  // the sibling's subtree is not finished yet
+            __threadfence();
+            const int2 ch = child[p];
+            int lo[8], hi[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) { lo[j] = 0x7fffffff; hi[j] = 0; }
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int q = k ? ch.y : ch.x;
+                int4 a, b;
+                if (q >= m - 1) {
+                    a = b = ccoord[q - (m - 1)];
+                } else {
+                    a = __ldcg(nlo + q);
+                    b = __ldcg(nhi + q);
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    lo[j] = min(lo[j], unpack16(a, j));
+                    hi[j] = max(hi[j], unpack16(b, j));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j >= d) lo[j] = hi[j] = 0;
+            __stcg(nlo + p, pack16(lo));
+            __stcg(nhi + p, pack16(hi));
+            node = p;
+        }
+    }
+}
+
+// Smallest sum over the node of max(|delta_j| - 1, 0)^2 against cell
+// coordinates c, with each term capped at 81 (any term above 8 already fails).
+__device__ __forceinline__ int gap2(const int (&c)[8], const int4 &lo, const int4 &hi, int d) {
+    int s = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (j < d) {
+            int g = max(max(unpack16(lo, j) - c[j] - 1, c[j] - unpack16(hi, j) - 1), 0);
+            g = min(g, 9);
+            s += g * g;
+        }
+    }
+    return s;
+}
+
+// NeighborCells(g) for every cell g.  FILL = false: counts (nbr_cnt, nbr_near,
+// and the count as int64 in cnt64 for the offset scan); FILL = true: the ids
+// at off[g], the |delta|_inf <= 1 cells first.  In the FP32-band mode cells
+// whose point boxes are farther than eps apart are dropped, as in the
+// enumeration of low dimensions.
+template <bool FILL>
+__global__ void __launch_bounds__(128)
+k_lbvh_query(RunParams P, const int2 *__restrict__ child, const int4 *__restrict__ nlo, const int4 *__restrict__ nhi,
+             const int4 *__restrict__ ccoord, const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
+             int *__restrict__ nbr_cnt, int *__restrict__ nbr_near, long long *__restrict__ cnt64,
+             const long long *__restrict__ off, int *__restrict__ nbr, DevCounters *ctr) {
+    const int m = ctr->m, d = P.d;
+    const float hi_thr = P.inst[0].thr.hi;
+    long long total = 0;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < m; g += gridDim.x * blockDim.x) {
+        int c[8];
+        const int4 cg = ccoord[g];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) c[j] = unpack16(cg, j);
+        Bx<8> glo = zero_box<8>(), ghi = glo;
+        if (P.box) { glo = load_box<8>(blo, g); ghi = load_box<8>(bhi, g); }
+        int n_near = 0, n_far = 0;
+        int near_at = 0, far_at = 0;
+        long long base = 0;
+        if (FILL) {
+            base = off[g];
+            near_at = 0;
+            far_at = nbr_near[g];
+        }
+        int stack[kStack];
+        int sp = 0;
+        if (m > 1) stack[sp++] = 0;
+        while (sp > 0) {
+            const int node = stack[--sp];
+            const int2 ch = child[node];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int q = k ? ch.y : ch.x;
+                if (q >= m - 1) {
+                    const int h = q - (m - 1);
+                    if (h == g) continue;
+                    const int4 ch4 = ccoord[h];
+                    int s = 0, inf = 0;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (j < d) {
+                            const int dj = abs(unpack16(ch4, j) - c[j]);
+                            inf = max(inf, dj);
+                            const int gj = min(max(dj - 1, 0), 9);
+                            s += gj * gj;
+                        }
+                    }
+                    if (s > d) continue;
+                    if (P.box && boxes_min_d2<8>(glo, ghi, load_box<8>(blo, h), load_box<8>(bhi, h)) > hi_thr)
+                        continue;
+                    if (inf <= 1) {
+                        if (FILL) nbr[base + near_at++] = h;
+                        ++n_near;
+                    } else {
+                        if (FILL) nbr[base + far_at++] = h;
+                        ++n_far;
+                    }
+                } else if (gap2(c, nlo[q], nhi[q], d) <= d) {
+                    if (sp < kStack) stack[sp++] = q;
+                    else set_error(ctr, DBSCAN_ERR_CAPACITY, 72);
+                }
+            }
+        }
+        if (!FILL) {
+            nbr_cnt[g] = n_near + n_far;
+            nbr_near[g] = n_near;
+            cnt64[g] = n_near + n_far;
+            total += n_near + n_far;
+        }
+    }
+    if (!FILL && total) atomicAdd((unsigned long long *)&ctr->E, (unsigned long long)total);
+}
+
+template <typename T> void hd_launch_keys(const void *X, const RunParams &P, const HdBufs &H, const Bufs &B,
+                                       cudaStream_t s) {
+    const int g = grid_for((const void *)k_hd_keys<T>, 256);
+    k_hd_keys<T><<<g, 256, 0, s>>>((const T *)X, P, H.klo, H.khi, B.sk0, B.sv0);
+    count_launch();
+}
+
+template <typename T> void hd_launch_cells(const void *X, const RunParams &P, const HdBufs &H, const Bufs &B,
+                                        const uint32_t *idx, DevCounters *ctr, cudaStream_t s) {
+    const int g = grid_for((const void *)k_hd_cells<T>, 256);
+    // the cell table and the sorted points are this step's outputs
+    k_hd_cells<T><<<g, 256, 0, s>>>((const T *)X, P, idx, H.klo, H.khi, B.core_s, B.core_pos,
+                                    const_cast<int *>(B.cell_start), H.ckey_lo, H.ckey_hi, H.ccoord,
+                                    const_cast<float *>(B.pf), const_cast<double *>(B.pd),
+                                    const_cast<int *>(B.orig), const_cast<int *>(B.cell_of), ctr);
+    count_launch();
+}
+
+}  // namespace
+
+// Steps 1-3 above plus the count pass of step 4; the offsets are scanned into
+// H.nbr_off and the total neighbour count is left in ctr->E.
+void hd_cells_and_counts(const void *X, int dtype, const RunParams &P, int key_bits, const HdBufs &H,
+                         const Bufs &B, DevCounters *ctr, cudaStream_t s) {
+    const int n = P.n;
+    const int bits = key_bits;
+    if (dtype == DBSCAN_F32) hd_launch_keys<float>(X, P, H, B, s);
+    else hd_launch_keys<double>(X, P, H, B, s);
+    // stable LSD sort by (hi, lo): the low word first, then the high word
+    const int lo_bits = bits < 64 ? bits : 64;
+    int which = radix_sort_u64(B.sk0, B.sv0, B.sk1, B.sv1, n, nullptr, n, 0, lo_bits, B.sort_scratch,
+                               B.sort_scratch_size, ctr, P.max_iters, s);
+    const uint32_t *idx = which ? B.sv1 : B.sv0;
+    if (bits > 64) {
+        uint64_t *kh = which ? B.sk0 : B.sk1;  // the free key buffer
+        uint32_t *vin = which ? B.sv1 : B.sv0;
+        uint32_t *vout = which ? B.sv0 : B.sv1;
+        uint64_t *kother = which ? B.sk1 : B.sk0;
+        int g = grid_for((const void *)k_hd_gather_hi, 256);
+        k_hd_gather_hi<<<g, 256, 0, s>>>(H.khi, vin, kh, n);
+        count_launch();
+        const int w2 = radix_sort_u64(kh, vin, kother, vout, n, nullptr, n, 0, bits - 64, B.sort_scratch,
+                                      B.sort_scratch_size, ctr, P.max_iters, s);
+        idx = w2 ? vout : vin;
+    }
+    {
+        int g = grid_for((const void *)k_hd_flags, 256);
+        k_hd_flags<<<g, 256, 0, s>>>(H.klo, H.khi, idx, B.core_s, n);
+        count_launch();
+    }
+    scan_i32_to_i32(B.core_s, B.core_pos, n, nullptr, n, B.part, s);
+    if (dtype == DBSCAN_F32) hd_launch_cells<float>(X, P, H, B, idx, ctr, s);
+    else hd_launch_cells<double>(X, P, H, B, idx, ctr, s);
+    if (P.box) launch_boxes(8, B.pf, B.cell_start, ctr, const_cast<float4 *>(B.blo), const_cast<float4 *>(B.bhi), s);
+    {
+        int g = grid_for((const void *)k_lbvh_nodes, 256);
+        k_lbvh_nodes<<<g, 256, 0, s>>>(H.ckey_lo, H.ckey_hi, H.child, H.parent, H.flag, ctr);
+        count_launch();
+        g = grid_for((const void *)k_lbvh_bounds, 256);
+        k_lbvh_bounds<<<g, 256, 0, s>>>(H.child, H.parent, H.flag, H.ccoord, H.nlo, H.nhi, P.d, ctr);
+        count_launch();
+        g = grid_for((const void *)k_lbvh_query<false>, 128);
+        k_lbvh_query<false><<<g, 128, 0, s>>>(P, H.child, H.nlo, H.nhi, H.ccoord, B.blo, B.bhi,
+                                              const_cast<int *>(B.nbr_cnt), const_cast<int *>(B.nbr_near), H.cnt64,
+                                              nullptr, nullptr, ctr);
+        count_launch();
+    }
+    scan_i64_to_i64(H.cnt64, H.nbr_off, 0, &ctr->m, n, B.part, s);
+}
+
+// Step 4's fill pass, into nbr (which holds at least ctr->E entries).
+void hd_fill(const RunParams &P, const HdBufs &H, const Bufs &B, int *nbr, DevCounters *ctr, cudaStream_t s) {
+    const int g = grid_for((const void *)k_lbvh_query<true>, 128);
+    k_lbvh_query<true><<<g, 128, 0, s>>>(P, H.child, H.nlo, H.nhi, H.ccoord, B.blo, B.bhi,
+                                         const_cast<int *>(B.nbr_cnt), const_cast<int *>(B.nbr_near), nullptr,
+                                         H.nbr_off, nbr, ctr);
+    count_launch();
+}
+
+}  // namespace gbdb

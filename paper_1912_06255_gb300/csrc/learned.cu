@@ -44,19 +44,27 @@ __global__ void k_clamp_pairs(DevCounters *ctr, long long cap) {
 // Symmetric in the two cells: log2(1 + larger core count), log2(1 + smaller
 // core count), core-centroid distance / eps, core-box minimum and maximum
 // distance / eps, smaller / larger core count.
+template <int D>
 __device__ __forceinline__ void pair_features(int a, int b, const int *__restrict__ ccs,
                                               const float4 *__restrict__ cent, const float4 *__restrict__ cblo,
                                               const float4 *__restrict__ cbhi, float eps, float (&f)[kMlpIn]) {
     const int na = ccs[a + 1] - ccs[a], nb = ccs[b + 1] - ccs[b];
     const int big = na > nb ? na : nb, small = na > nb ? nb : na;
-    const float4 ca = cent[a], cb = cent[b];
-    const float dx = ca.x - cb.x, dy = ca.y - cb.y, dz = ca.z - cb.z, dw = ca.w - cb.w;
+    const Bx<D> ca = load_box<D>(cent, a), cb = load_box<D>(cent, b);
+    float c2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const float t = bget<D>(ca, j) - bget<D>(cb, j);
+        c2 = __fmaf_rn(t, t, c2);
+    }
+    const Bx<D> alo = load_box<D>(cblo, a), ahi = load_box<D>(cbhi, a);
+    const Bx<D> blo = load_box<D>(cblo, b), bhi = load_box<D>(cbhi, b);
     const float inv = 1.f / eps;
     f[0] = log2f(1.f + (float)big);
     f[1] = log2f(1.f + (float)small);
-    f[2] = sqrtf(dx * dx + dy * dy + dz * dz + dw * dw) * inv;
-    f[3] = sqrtf(boxes_min_d2<4>(cblo[a], cbhi[a], cblo[b], cbhi[b])) * inv;
-    f[4] = sqrtf(boxes_max_d2<4>(cblo[a], cbhi[a], cblo[b], cbhi[b])) * inv;
+    f[2] = sqrtf(c2) * inv;
+    f[3] = sqrtf(boxes_min_d2<D>(alo, ahi, blo, bhi)) * inv;
+    f[4] = sqrtf(boxes_max_d2<D>(alo, ahi, blo, bhi)) * inv;
     f[5] = big > 0 ? (float)small / (float)big : 0.f;
 }
 
@@ -185,9 +193,11 @@ void mlp_adam(float *w, const float *g, float *m1, float *m2, float lr, int t, c
 // Every pair of neighbouring core cells (a, b), a < b, once.  The core-point
 // boxes settle some outright (all pairs within eps: link; none: drop); the
 // rest are appended to the pair list.
+template <int D>
 __global__ void __launch_bounds__(256)
 k_collect_pairs(RunParams P, const int *__restrict__ ccs, const int *__restrict__ nbr_cnt,
-                const int *__restrict__ nbr, int stride, const float4 *__restrict__ cblo,
+                const int *__restrict__ nbr, int stride, const long long *__restrict__ nbr_off,
+                const float4 *__restrict__ cblo,
                 const float4 *__restrict__ cbhi, int *parent, int2 *__restrict__ pairs, long long cap,
                 DevCounters *ctr) {
     const int m = ctr->m;
@@ -197,9 +207,9 @@ k_collect_pairs(RunParams P, const int *__restrict__ ccs, const int *__restrict_
     for (int a = warp_id_global(); a < m; a += warps_global()) {
         if (ccs[a + 1] == ccs[a]) continue;
         const Thr T = P.inst[inst_of_cell(P, a)].thr;
-        const float4 alo = cblo[a], ahi = cbhi[a];
+        const Bx<D> alo = load_box<D>(cblo, a), ahi = load_box<D>(cbhi, a);
         const int ne = nbr_cnt[a];
-        const int *nl = nbr + (int64_t)a * stride;
+        const int *nl = nbr_list<D>(nbr, nbr_off, stride, a);
         for (int e0 = 0; e0 < ne; e0 += 32) {
             const int e = e0 + lane;
             int b = 0;
@@ -209,9 +219,9 @@ k_collect_pairs(RunParams P, const int *__restrict__ ccs, const int *__restrict_
                 b = nl[e];
                 cand = b > a && ccs[b + 1] > ccs[b];
                 if (cand && P.box) {
-                    const float4 blo = cblo[b], bhi = cbhi[b];
-                    if (boxes_min_d2<4>(alo, ahi, blo, bhi) > T.hi) verdict = -1;
-                    else if (boxes_max_d2<4>(alo, ahi, blo, bhi) <= T.lo) verdict = 1;
+                    const Bx<D> blo = load_box<D>(cblo, b), bhi = load_box<D>(cbhi, b);
+                    if (boxes_min_d2<D>(alo, ahi, blo, bhi) > T.hi) verdict = -1;
+                    else if (boxes_max_d2<D>(alo, ahi, blo, bhi) <= T.lo) verdict = 1;
                 }
             }
             if (cand && verdict > 0) uf_link(parent, a, b, P.max_iters, ctr);
@@ -242,6 +252,7 @@ k_collect_pairs(RunParams P, const int *__restrict__ ccs, const int *__restrict_
 // network predicts connected (logit > 0) are exactly those with a score below
 // 2^15; they are counted in P_pos.  Each cell also keeps the smallest key of
 // its pairs among those (best[], 64-bit atomicMin): its likeliest link.
+template <int D>
 __global__ void __launch_bounds__(256)
 k_score_pairs(RunParams P, const int2 *__restrict__ pairs, const float *__restrict__ w, const int *__restrict__ ccs,
               const float4 *__restrict__ cent, const float4 *__restrict__ cblo, const float4 *__restrict__ cbhi,
@@ -259,7 +270,7 @@ k_score_pairs(RunParams P, const int2 *__restrict__ pairs, const float *__restri
             const int2 pr = pairs[k];
             const float eps = sqrtf((float)P.inst[inst_of_cell(P, pr.x)].thr.eps2);
             float x[kMlpIn], h1[kMlpHid], h2[kMlpHid];
-            pair_features(pr.x, pr.y, ccs, cent, cblo, cbhi, eps, x);
+            pair_features<D>(pr.x, pr.y, ccs, cent, cblo, cbhi, eps, x);
             const float z = mlp_forward(sw, x, h1, h2);
             const unsigned q = (unsigned)fminf(fmaxf((16.f - z) * 2048.f, 0.f), 65535.f);
             const uint64_t key = ((uint64_t)q << 32) | (uint64_t)k;
@@ -364,7 +375,7 @@ k_test_pairs(RunParams P, const int2 *__restrict__ pairs, const uint64_t *__rest
                 const long long slot = (long long)base + src;
                 if (slot < log_cap) {
                     float x[kMlpIn];
-                    pair_features(sa, sb, ccs, cent, cblo, cbhi, sqrtf((float)T.eps2), x);
+                    pair_features<D>(sa, sb, ccs, cent, cblo, cbhi, sqrtf((float)T.eps2), x);
 #pragma unroll
                     for (int i = 0; i < kMlpIn; ++i) log_feat[slot * kMlpIn + i] = x[i];
                     log_lab[slot] = hit ? 1 : 0;
@@ -386,10 +397,21 @@ void launch_connect_learned(int D, int mode, bool log, const RunParams &P, const
     unsigned long long *best = reinterpret_cast<unsigned long long *>(B.sk0);  // per cell, free in this schedule
     int g = grid_for((const void *)k_uf_reset, 256);
     k_uf_reset<<<g, 256, 0, s>>>(B.parent, B.sk0, ctr); count_launch();
-    g = grid_for((const void *)k_collect_pairs, 256);
-    k_collect_pairs<<<g, 256, 0, s>>>(P, B.ccs, B.nbr_cnt, B.nbr, B.nbr_stride, B.cblo, B.cbhi, B.parent, L.pairs,
-                                      L.cap, ctr);
-    count_launch();
+    auto collect = [&](auto k) {
+        const int gc = grid_for((const void *)k, 256);
+        k<<<gc, 256, 0, s>>>(P, B.ccs, B.nbr_cnt, B.nbr, B.nbr_stride, B.nbr_off, B.cblo, B.cbhi, B.parent, L.pairs,
+                             L.cap, ctr);
+        count_launch();
+    };
+    auto score = [&](auto k) {
+        const int gs = grid_for((const void *)k, 256);
+        k<<<gs, 256, 0, s>>>(P, L.pairs, L.w, B.ccs, B.ccent, B.cblo, B.cbhi, L.k0, best, ctr);
+        count_launch();
+    };
+    if (D == 8) collect(k_collect_pairs<8>);
+    else if (D == 4) collect(k_collect_pairs<4>);
+    else if (D == 3) collect(k_collect_pairs<3>);
+    else collect(k_collect_pairs<2>);
     k_clamp_pairs<<<1, 1, 0, s>>>(ctr, L.cap); count_launch();
     if (log) {
         GBDB_DISPATCH(D, mode, {
@@ -401,9 +423,10 @@ void launch_connect_learned(int D, int mode, bool log, const RunParams &P, const
         });
         return;
     }
-    g = grid_for((const void *)k_score_pairs, 256);
-    k_score_pairs<<<g, 256, 0, s>>>(P, L.pairs, L.w, B.ccs, B.ccent, B.cblo, B.cbhi, L.k0, best, ctr);
-    count_launch();
+    if (D == 8) score(k_score_pairs<8>);
+    else if (D == 4) score(k_score_pairs<4>);
+    else if (D == 3) score(k_score_pairs<3>);
+    else score(k_score_pairs<2>);
     const int which = radix_sort_u64(L.k0, nullptr, L.k1, nullptr, 0, &ctr->P_list, L.cap, 32, 16, L.scratch,
                                      L.scratch_size, ctr, P.max_iters, s);
     const uint64_t *sorted = which ? L.k1 : L.k0;

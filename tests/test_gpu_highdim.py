@@ -1,0 +1,151 @@
+"""Parity for 5 <= d <= 8 (cells by 128-bit key sort, neighbours by the tree
+over the cells) against the CPU oracle, element by element, plus the 5D and
+7D workloads at full size on sampled outputs."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_06255_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1912_06255_gb300 import DBSCAN, DbscanError, dbscan  # noqa: E402
+
+
+def _assert_same(X, eps, mp, **kw):
+    t = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    r = dbscan(t, eps, mp, **kw)
+    torch.cuda.synchronize()
+    got = (r.core.cpu().numpy(), r.labels.cpu().numpy(), r.border_offsets.cpu().numpy(), r.border_ids.cpu().numpy())
+    exp = oracle.dbscan(X, eps, mp)
+    for name, g, e in zip(("core", "labels", "border_offsets", "border_ids"), got, exp):
+        if not np.array_equal(g, e):
+            bad = np.flatnonzero(g != e)[:10] if g.shape == e.shape else "shape"
+            raise AssertionError(f"{name} differs at {bad} (n={len(X)}, d={X.shape[1]}, eps={eps}, {kw})")
+    return r.stats
+
+
+@pytest.mark.parametrize("d", [5, 6, 7, 8])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_random_mixed_highdim(d, precision, dtype):
+    X = synth.random_small(700 + d, 6000, d, dtype=dtype)
+    for eps, mp in ((0.4, 4), (0.8, 12), (1.6, 40)):
+        st = _assert_same(X, eps, mp, precision=precision)
+        assert st["num_neighbor_entries"] >= 0
+
+
+@pytest.mark.parametrize("d", [5, 6, 7, 8])
+def test_lattice_exact_eps_highdim(d):
+    """Axis neighbours at exactly eps: core iff interior (count 2d+1)."""
+    L = 4 if d <= 5 else 3
+    grid = np.stack(np.meshgrid(*[np.arange(L)] * d, indexing="ij"), -1).reshape(-1, d)
+    X = (grid * 0.75 + 3.0).astype(np.float32)
+    for precision in ("fp32", "fp64"):
+        st = _assert_same(X, 0.75, 2 * d + 1, precision=precision)
+        if precision == "fp32":
+            assert st["band_rechecks"] > 0
+
+
+@pytest.mark.parametrize("schedule", ["size", "none", "learned"])
+@pytest.mark.parametrize("cell_bounds", [True, False])
+def test_highdim_schedules(schedule, cell_bounds):
+    X = synth.random_small(91, 12000, 6, dtype=np.float32)
+    st = _assert_same(X, 0.9, 10, schedule=schedule, cell_bounds=cell_bounds)
+    assert (st["num_pairs_tested"] + st["num_pairs_skipped"] + st["num_pairs_box_decided"]
+            == st["num_candidate_pairs"])
+
+
+def test_highdim_uniform_sparse():
+    """Isolated points in 5D (every cell its own, no neighbours) and a few
+    duplicates; one cell; minPts 1."""
+    rng = np.random.default_rng(12)
+    X = (rng.random((20000, 5)) * 1e4).astype(np.float32)
+    _assert_same(X, 1.0, 2)
+    _assert_same(X, 1.0, 1)
+    Y = np.concatenate([X[:100], X[:100], X[:50]])  # pairs and triples of identical points
+    _assert_same(Y, 5.0, 3)
+    _assert_same(np.full((300, 7), 2.5, np.float32), 0.1, 300)
+
+
+def test_spreader_5d_scaled():
+    I = synth.spreader_5d_10m(n=100_000, eps=800.0)
+    st = _assert_same(I.points, I.eps, I.min_pts)
+    assert st["num_cells"] > 1000
+
+
+@pytest.mark.parametrize("eps", [1000.0, 2000.0])
+def test_spreader_7d_scaled(eps):
+    I = synth.spreader_7d_10m(n=100_000, eps=eps)
+    _assert_same(I.points, I.eps, I.min_pts)
+
+
+def test_highdim_key_overflow_and_reuse():
+    ctx = DBSCAN(1000, 8)
+    X = torch.zeros((10, 6), device="cuda", dtype=torch.float64)
+    X[1, 0] = 1e6
+    with pytest.raises(DbscanError) as e:
+        ctx.run(X, 1.0, 2)  # 2.4e6 cells in one dimension > 2^15
+    assert e.value.status == 4
+    # the same context alternates between tree and hash paths
+    for d in (3, 7, 2, 5):
+        Y = synth.random_small(30 + d, 900, d, dtype=np.float32)
+        r = ctx.run(torch.from_numpy(Y).cuda(), 0.5, 5)
+        exp = oracle.dbscan(Y, 0.5, 5)
+        assert np.array_equal(r.labels.cpu().numpy(), exp[1]), d
+        assert np.array_equal(r.border_ids.cpu().numpy(), exp[3]), d
+
+
+def _sampled_invariants(X, eps, mp, core, labels, off, ids, samples):
+    """Checks at any size: the core flag by a count, equal labels across core
+    pairs within eps, border sets, noise, and canonical cluster names."""
+    cnt = oracle.sample_counts(X, eps, samples)
+    assert np.array_equal(core[samples], (cnt >= mp).astype(np.uint8))
+    for p in samples[:300]:
+        nb = oracle.neighbors(X, eps, int(p))
+        cn = nb[core[nb] == 1]
+        if core[p]:
+            assert np.all(labels[cn] == labels[p]), p
+        else:
+            exp = np.unique(labels[cn])
+            assert np.array_equal(ids[off[p]:off[p + 1]], exp), p
+            assert labels[p] == (exp[0] if len(exp) else -1), p
+    # cluster names: the smallest core index of the cluster, itself core
+    cl = labels[core == 1]
+    idx = np.flatnonzero(core == 1)
+    first = np.full(len(X), np.iinfo(np.int64).max)
+    np.minimum.at(first, cl, idx)
+    names = np.unique(cl)
+    assert np.array_equal(first[names], names)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("eps", [200.0, 800.0])
+def test_spreader_5d_full_size_sampled(eps):
+    """The 10M-point 5D mixed workload (FP32, minPts 10) on sampled outputs."""
+    I = synth.spreader_5d_10m(eps=eps)
+    ctx = DBSCAN(len(I.points), 5)
+    r = ctx.run(torch.from_numpy(I.points).cuda(), I.eps, I.min_pts)
+    core, labels = r.core.cpu().numpy(), r.labels.cpu().numpy()
+    off, ids = r.border_offsets.cpu().numpy(), r.border_ids.cpu().numpy()
+    rng = np.random.default_rng(5)
+    samples = np.sort(rng.choice(len(I.points), 2000, replace=False))
+    _sampled_invariants(I.points, I.eps, I.min_pts, core, labels, off, ids, samples)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("eps", [1000.0, 2000.0])
+def test_spreader_7d_full_size_sampled(eps):
+    """The 10M-point 7D varying-density workload (FP32, minPts 100) on sampled outputs."""
+    I = synth.spreader_7d_10m(eps=eps)
+    ctx = DBSCAN(len(I.points), 7)
+    r = ctx.run(torch.from_numpy(I.points).cuda(), I.eps, I.min_pts)
+    core, labels = r.core.cpu().numpy(), r.labels.cpu().numpy()
+    off, ids = r.border_offsets.cpu().numpy(), r.border_ids.cpu().numpy()
+    rng = np.random.default_rng(7)
+    samples = np.sort(rng.choice(len(I.points), 2000, replace=False))
+    _sampled_invariants(I.points, I.eps, I.min_pts, core, labels, off, ids, samples)
