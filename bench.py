@@ -41,20 +41,20 @@ PHASES = ["bbox", "bbox_readback", "cells", "boxes_neighbors", "markcore", "comp
 
 
 # ----------------------------------------------------------------- workloads
-class Spreader3D:
-    """The single 2M-point 3D instance."""
-    metric = "exact DBSCAN Mpts/s on 1 GB300 (3D seed spreader n=2e6, eps=100, minPts=100)"
-    SLAB = 5e3  # CPU sample: points with x < 5e3 (5% of the box, same local density)
+class SingleInstance:
+    """One instance of a seed-spreader workload in one call."""
+    SLAB = 5e3  # CPU sample: points with x0 < SLAB (same local density)
 
     def __init__(self, n):
-        from paper_1912_06255_gb300 import synth
-        self.I = synth.spreader_3d_2m(n=n)
+        self.I = self.make(n if n else self.DEFAULT_N)
         self.n = len(self.I.points)
+        self.d = self.I.points.shape[1]
         self.name = self.I.name
-        self.config = {"workload": self.I.name, "n": self.n, "d": 3, "eps": self.I.eps, "min_pts": self.I.min_pts}
+        self.config = {"workload": self.I.name, "n": self.n, "d": self.d, "eps": self.I.eps,
+                       "min_pts": self.I.min_pts}
 
     def make_ctx(self, DBSCAN, **kw):
-        return DBSCAN(self.n, 3, **kw)
+        return DBSCAN(self.n, self.d, **kw)
 
     def device_input(self, dev):
         import torch
@@ -75,19 +75,66 @@ class Spreader3D:
     def h2d_bytes(self):
         return int(self.I.points.nbytes)
 
-    def log_run(self, ctx, dev):
-        """One run on a held-out input of the same family (seed 2001), for the scheduler's training log."""
+    def heldout(self, dev):
+        """A held-out input of the same family (another seed), on the device."""
         import torch
-        from paper_1912_06255_gb300 import synth
-        T = synth.spreader_3d_2m(seed=2001, n=self.n)
-        ctx.run(torch.from_numpy(T.points).to(dev), T.eps, T.min_pts, border=False)
+        if getattr(self, "_held", None) is None:
+            T = self.make(self.n, seed=self.TRAIN_SEED)
+            self._held = (T, torch.from_numpy(T.points).to(dev))
+        return self._held
+
+    def log_run(self, ctx, dev):
+        """One run on the held-out input, for the scheduler's training log."""
+        T, X = self.heldout(dev)
+        ctx.run(X, T.eps, T.min_pts, border=False)
         return T.name
+
+    def autotune(self, ctx, dev):
+        T, X = self.heldout(dev)
+        return ctx.autotune(X, T.eps, T.min_pts, reps=2), T.name
 
     def cpu_sample(self):
         X = np.ascontiguousarray(self.I.points[self.I.points[:, 0] < self.SLAB])
-        desc = (f"{len(X)} points with x < {self.SLAB:g} of the {self.n}-point workload (same local density), "
+        desc = (f"{len(X)} points with x0 < {self.SLAB:g} of the {self.n}-point workload (same local density), "
                 f"one full oracle run")
         return [(X, self.I.eps, self.I.min_pts)], desc
+
+
+class Spreader3D(SingleInstance):
+    """The 2M-point 3D instance (eps 100, minPts 100)."""
+    metric = "exact DBSCAN Mpts/s on 1 GB300 (3D seed spreader n=2e6, eps=100, minPts=100)"
+    TRAIN_SEED = 2001
+    DEFAULT_N = 2_000_000
+
+    def make(self, n, seed=1001):
+        from paper_1912_06255_gb300 import synth
+        return synth.spreader_3d_2m(seed=seed, n=n)
+
+
+class Mixed5D(SingleInstance):
+    """The 10M-point 5D instance: half uniform, half seed spreader (minPts 10)."""
+    metric = "exact DBSCAN Mpts/s on 1 GB300 (5D mixed uniform + spreader n=1e7, minPts=10)"
+    TRAIN_SEED = 2002
+    DEFAULT_N = 10_000_000
+    EPS = 200.0
+    SLAB = 1e3
+
+    def make(self, n, seed=1002):
+        from paper_1912_06255_gb300 import synth
+        return synth.spreader_5d_10m(seed=seed, n=n, eps=self.EPS)
+
+
+class VarDen7D(SingleInstance):
+    """The 10M-point 7D varying-density instance (minPts 100)."""
+    metric = "exact DBSCAN Mpts/s on 1 GB300 (7D varying-density spreader n=1e7, minPts=100)"
+    TRAIN_SEED = 2004
+    DEFAULT_N = 10_000_000
+    EPS = 1000.0
+    SLAB = 2e3
+
+    def make(self, n, seed=1004):
+        from paper_1912_06255_gb300 import synth
+        return synth.spreader_7d_10m(seed=seed, n=n, eps=self.EPS)
 
 
 class Batch256:
@@ -137,20 +184,30 @@ class Batch256:
     def h2d_bytes(self):
         return int(self.P.nbytes)
 
-    def log_run(self, ctx, dev):
-        """A held-out batch of 48 instances of the same family (seed 2003), for the training log."""
+    def heldout(self, dev):
+        """A held-out batch of 48 instances of the same family (seed 2003), on the device."""
         import torch
         from paper_1912_06255_gb300 import synth
-        B = synth.batch_256(seed=2003, count=48)
-        n = sum(len(b.points) for b in B)
-        P = np.zeros((n, 3), np.float32)
-        row = 0
-        for b in B:
-            P[row:row + len(b.points), :b.points.shape[1]] = b.points
-            row += len(b.points)
-        ctx.run_batch(torch.from_numpy(P).to(dev), [(len(b.points), b.points.shape[1], b.eps, b.min_pts) for b in B],
-                      border=False)
-        return f"batch_256(seed=2003, count=48), {n} points"
+        if getattr(self, "_held", None) is None:
+            B = synth.batch_256(seed=2003, count=48)
+            n = sum(len(b.points) for b in B)
+            P = np.zeros((n, 3), np.float32)
+            row = 0
+            for b in B:
+                P[row:row + len(b.points), :b.points.shape[1]] = b.points
+                row += len(b.points)
+            inst = [(len(b.points), b.points.shape[1], b.eps, b.min_pts) for b in B]
+            self._held = (torch.from_numpy(P).to(dev), inst, f"batch_256(seed=2003, count=48), {n} points")
+        return self._held
+
+    def log_run(self, ctx, dev):
+        X, inst, name = self.heldout(dev)
+        ctx.run_batch(X, inst, border=False)
+        return name
+
+    def autotune(self, ctx, dev):
+        X, inst, name = self.heldout(dev)
+        return ctx.autotune_batch(X, inst, reps=2), name
 
     def cpu_sample(self):
         order = sorted(range(len(self.B)), key=lambda i: len(self.B[i].points))
@@ -164,7 +221,7 @@ class Batch256:
         return [(self.B[i].points, self.B[i].eps, self.B[i].min_pts) for i in pick], desc
 
 
-WORKLOADS = {"spreader3d": Spreader3D, "batch256": Batch256}
+WORKLOADS = {"spreader3d": Spreader3D, "batch256": Batch256, "mixed5d": Mixed5D, "varden7d": VarDen7D}
 
 
 # ----------------------------------------------------------------- helpers
@@ -239,20 +296,38 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def _roofline(kernel, ms, pair_tests, d_flops):
+# DRAM bytes per launch of the dominant kernel, from one ncu capture of the
+# same command (dram__bytes_read.sum + dram__bytes_write.sum); None when the
+# kernel changed after the capture.  Keyed by (kernel, workload name).
+TRAFFIC = {
+    # profiles/k_markcore_k_connect_spreader3d_n2m.md (default setting, 2 connect waves)
+    ("k_markcore", "spreader3d-n2000000-eps100-minpts100-f32"): 50528768 + 206592,
+}
+
+
+def _roofline(kernel, ms, work_pairs, d, workload, executed_pairs=None):
     """Roofline of the dominant kernel.  MarkCore and BCP are pair-distance
-    loops bound by the FP32 pipe: achieved = pair tests executed x 3d flop /
-    kernel time (pair tests counted in a separate counting run), peak = 152
-    SMs x 128 FP32 lanes x 2 flop x max SM clock."""
+    loops bound by the FP32 pipe: achieved = algorithmic pair tests x 3d flop
+    (d subtractions and d multiply-adds) / the kernel's time, measured with
+    CUDA events on the run's stream in the timed steps.  MarkCore's
+    algorithmic work is the scan without early exit (the sum over cells
+    with fewer than minPts points of |g| times the points of their
+    neighbouring cells); BCP's is the pair tests the schedule ran.
+    Peak = 152 SMs x 128 FP32 lanes x 2 flop x max SM clock."""
     peaks, kind = _peaks()
     clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     peak_tflops = 152 * 128 * 2 * clk / 1e12
-    if not pair_tests or ms <= 0:
+    if not work_pairs or ms <= 0:
         return None
-    achieved = pair_tests * 3 * d_flops / (ms * 1e-3) / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops, "traffic": None, "kernel": kernel,
-            "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x max SM clock ({kind} clock)"}
+    achieved = work_pairs * 3 * d / (ms * 1e-3) / 1e12
+    out = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+           "frac": achieved / peak_tflops, "traffic": TRAFFIC.get((kernel, workload)), "kernel": kernel,
+           "work_pair_tests": int(work_pairs), "kernel_ms": ms}
+    if executed_pairs is not None:
+        ex = executed_pairs * 3 * d / (ms * 1e-3) / 1e12
+        out.update(executed_pair_tests=int(executed_pairs), executed_achieved=ex, executed_frac=ex / peak_tflops)
+    out["peak_source"] = f"152 SMs x 128 FP32 lanes x 2 flop x max SM clock ({kind} clock)"
+    return out
 
 
 # ----------------------------------------------------------------- arms
@@ -343,6 +418,15 @@ def run_gpu(args):
     ctx = W.make_ctx(DBSCAN, precision=args.precision, schedule="size")
     training = _train_scheduler(W, ctx, dev) if not args.profile or args.schedule == "learned" else None
     ctx.set_option(1, SCHED_CODES[args.schedule])
+    tuned = None
+    if args.tuning:
+        ctx.set_tuning(json.loads(args.tuning))
+    elif args.autotune and not args.profile:
+        # the autotuner picks schedule, box decisions, waves, work-item size
+        # and blocks per SM on the held-out input; the timed runs use its choice
+        choice, src = W.autotune(ctx, dev)
+        tuned = dict(choice, tuned_on=src)
+    setting = ctx.tuning()
     out = (torch.empty(n, dtype=torch.uint8, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
            torch.empty(n + 1, dtype=torch.int64, device=dev))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -369,8 +453,10 @@ def run_gpu(args):
     # pair tests per kernel, counted once in an untimed run
     cctx = W.make_ctx(DBSCAN, precision=args.precision, schedule=args.schedule, collect_stats=True)
     cctx.set_scheduler_weights(ctx.scheduler_weights())
+    cctx.set_tuning(setting)
     W.run(cctx, X, out)
     ev_phase = cctx.stats()["distance_evals_phase"]
+    mc_bound = cctx.stats()["markcore_pair_bound"]
     cctx.close()
 
     # timed region: device time per step with CUDA events; L2 flushed before each step.
@@ -411,6 +497,7 @@ def run_gpu(args):
     # the plain FP64 path on the same input (a few steps, same flush rule)
     ctx64 = W.make_ctx(DBSCAN, precision="fp64", schedule=args.schedule)
     ctx64.set_scheduler_weights(ctx.scheduler_weights())
+    ctx64.set_tuning({k: v for k, v in setting.items() if k != "cell_bounds"})
     for _ in range(3):
         W.run(ctx64, X, out)
     ms64 = []
@@ -440,7 +527,7 @@ def run_gpu(args):
         e2e_ms.append(a.elapsed_time(b))
 
     schedules = _compare_schedules(W, ctx, X, out, flush, stream, max(3, min(args.steps, 5)))
-    ctx.set_option(1, SCHED_CODES[args.schedule])
+    ctx.set_tuning(setting)
 
     def max_over_ranks(x):
         if dist is None:
@@ -455,8 +542,11 @@ def run_gpu(args):
     if rank == 0:
         ph = [sum(p[i] for p in phases) / len(phases) for i in range(8)]
         dom = 4 if ph[4] >= ph[6] else 6
-        roof = _roofline("k_markcore" if dom == 4 else "k_connect", ph[dom],
-                         ev_phase[0] if dom == 4 else ev_phase[1], 3)
+        dd = getattr(W, "d", 3)
+        roof_mc = _roofline("k_markcore", ph[4], mc_bound, dd, W.name, executed_pairs=ev_phase[0])
+        roof_cn = _roofline("k_test_pairs" if setting["schedule"] == 2 else "k_connect", ph[6], ev_phase[1], dd,
+                            W.name)
+        roof = roof_mc if dom == 4 else roof_cn
         line = {
             "metric": W.metric,
             "value": ws * n / (t_ms * 1e-3) / 1e6,
@@ -465,7 +555,8 @@ def run_gpu(args):
             "dtype": "f32" if args.precision == "fp32" else "f64",
             "data": "synthetic",
             "config": dict(W.config, precision="fp32 band + fp64 recheck" if args.precision == "fp32" else "fp64",
-                           schedule=args.schedule, parallelism=f"replicas{ws}",
+                           schedule={v: k for k, v in SCHED_CODES.items()}[setting["schedule"]],
+                           tuning=setting, parallelism=f"replicas{ws}",
                            l2="flushed (256 MiB write) before every timed step"),
             "fp64_path": {"value": ws * n / (t64 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": t64},
             "e2e": {"value": ws * n / (te2e * 1e-3) / 1e6, "unit": UNIT,
@@ -473,8 +564,11 @@ def run_gpu(args):
             "gpu_launches": int(launches),
             "phase_ms": dict(zip(PHASES, [round(x, 4) for x in ph])),
             "roofline": roof,
+            "roofline_other": roof_cn if dom == 4 else roof_mc,
             "schedules": dict(schedules, training=training),
-            "pair_tests": {"markcore": ev_phase[0], "connect": ev_phase[1], "border": ev_phase[2]},
+            "autotune": tuned,
+            "pair_tests": {"markcore": ev_phase[0], "markcore_without_early_exit": mc_bound,
+                           "connect": ev_phase[1], "border": ev_phase[2]},
             "run_stats": {k: stats[k] for k in ("num_cells", "num_core_cells", "num_candidate_pairs",
                                                  "num_pairs_tested", "num_pairs_skipped", "num_pairs_box_decided",
                                                  "num_core_points", "num_border_points", "band_rechecks",
@@ -502,11 +596,19 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--schedule", default="size", choices=["size", "none", "learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
+                    help="pick the run settings with the library's autotuner on a held-out input first")
+    ap.add_argument("--tuning", default=None,
+                    help='explicit settings instead of the autotuner, e.g. \'{"connect_waves": 1, "connect_cells": 8}\'')
     ap.add_argument("--profile", action="store_true",
                     help="run warm-up + timed steps only and print no bench line (for ncu)")
-    ap.add_argument("--n", type=int, default=2_000_000,
-                    help="points of the seed-spreader workload (the bench line is defined at 2,000,000)")
+    ap.add_argument("--n", type=int, default=None,
+                    help="points of a single-instance workload (default: its defined size, 2e6 in 3D, 1e7 in 5D/7D)")
+    ap.add_argument("--eps", type=float, default=None, help="eps of the 5D or 7D workload (default 200 / 1000)")
     args = ap.parse_args()
+    if args.eps is not None:
+        for cls in (Mixed5D, VarDen7D):
+            cls.EPS = args.eps
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -86,7 +86,18 @@ enum {
        the core-point boxes do not settle gets an exact BCP test (no union-find
        skipping) and its features and outcome are recorded, for
        dbscan_train_scheduler() */
-    DBSCAN_OPT_PAIR_LOG = 7
+    DBSCAN_OPT_PAIR_LOG = 7,
+    /* value: 1, 2, 4 (default) or 8: core cells a warp of the connectivity
+       kernel takes from the work counter at once (their pair lists are
+       flattened across the warp's lanes) */
+    DBSCAN_OPT_CONNECT_CELLS = 8,
+    /* value: 2 (default) or 1: with SIZE or NONE, test the adjacent-cell pairs
+       first, compress the union-find, then the farther pairs (2); or all pairs
+       in one wave (1) */
+    DBSCAN_OPT_CONNECT_WAVES = 9,
+    /* value: 0 (default: as many as fit) or 1..32: resident blocks per SM of
+       the persistent (grid-stride, work-counter) kernels */
+    DBSCAN_OPT_BLOCKS_PER_SM = 10
 };
 enum { DBSCAN_PREC_FP64 = 0, DBSCAN_PREC_FP32_RECHECK = 1 };
 /* SIZE: core-cell pairs are tested in order of non-increasing core count of the
@@ -132,6 +143,10 @@ typedef struct {
        pair schedule, 6 BCP connectivity with union-find, 7 labels and border
        counts. */
     float phase_ms[8];
+    /* Algorithmic work of MarkCore (only with COLLECT_STATS): the sum over the
+       cells with fewer than minPts points of |g| times the points of all their
+       neighbouring cells, the distance tests a scan without early exit makes. */
+    int64_t markcore_pair_bound;
 } dbscan_stats;
 
 /*
@@ -295,6 +310,42 @@ dbscan_status dbscan_scheduler_loss_grad(dbscan_ctx *ctx, const float *d_feature
  * capacity is too small.  Synchronises the device. */
 dbscan_status dbscan_get_pair_log(dbscan_ctx *ctx, float *d_features, uint8_t *d_labels, int64_t capacity,
                                   int64_t *count);
+
+/* Read back one DBSCAN_OPT_* option (INVALID_ARG for unknown options). */
+dbscan_status dbscan_get_option(const dbscan_ctx *ctx, int option, int64_t *value);
+
+/* The configuration an autotuner run chose, and what it measured. */
+typedef struct {
+    int32_t schedule;       /* DBSCAN_OPT_SCHEDULE */
+    int32_t cell_bounds;    /* DBSCAN_OPT_CELL_BOUNDS */
+    int32_t connect_waves;  /* DBSCAN_OPT_CONNECT_WAVES */
+    int32_t connect_cells;  /* DBSCAN_OPT_CONNECT_CELLS */
+    int32_t blocks_per_sm;  /* DBSCAN_OPT_BLOCKS_PER_SM */
+    int32_t trials;         /* configurations timed */
+    float best_ms;          /* wall time of one call with the chosen configuration (best of reps) */
+    float default_ms;       /* the same for the configuration the context had before */
+} dbscan_tuning;
+
+/*
+ * Autotuner (the tile and schedule choice of the batched persistent kernels):
+ * time dbscan_run on this input for candidate settings of the pair schedule,
+ * the cell-box decisions (FP32 mode only), one or two connectivity waves, the
+ * core cells per work item of the connectivity kernel and the resident blocks
+ * per SM of the persistent kernels, by coordinate descent from the context's
+ * current setting (one warm-up and `reps` timed calls per candidate, the
+ * fastest kept), and leave the fastest setting in the context.  None of the
+ * settings changes the result.  Arguments as for dbscan_run; the outputs go
+ * to scratch buffers the call allocates and frees.  out (host, may be NULL)
+ * receives the choice.  Returns the first failing run's status, OOM, or OK.
+ */
+dbscan_status dbscan_autotune(dbscan_ctx *ctx, const void *d_points, int64_t n, int d, int dtype, double eps,
+                              int64_t min_pts, int reps, dbscan_tuning *out, void *stream);
+
+/* The same for dbscan_run_batch (arguments as there; the graph is recaptured
+ * for every candidate). */
+dbscan_status dbscan_autotune_batch(dbscan_ctx *ctx, const dbscan_instance *host_desc, int count,
+                                    const void *d_points, int ld, int dtype, int reps, dbscan_tuning *out,
+                                    void *stream);
 
 /* Counters of the last run (host copy; no device work). */
 dbscan_status dbscan_get_stats(const dbscan_ctx *ctx, dbscan_stats *out);

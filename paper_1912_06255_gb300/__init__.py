@@ -38,6 +38,18 @@ def _torch():
     return torch
 
 
+def _instances(instances, N):
+    arr = (_lib.Instance * len(instances))()
+    row = 0
+    for k, (n, d, eps, mp) in enumerate(instances):
+        arr[k].row0, arr[k].n, arr[k].d = row, int(n), int(d)
+        arr[k].reserved, arr[k].eps, arr[k].min_pts = 0, float(eps), int(mp)
+        row += int(n)
+    if row != N:
+        raise ValueError("instance sizes must add up to the number of rows")
+    return arr
+
+
 class DBSCAN:
     """A reusable context (device workspace sized for max_points x max_dim)."""
 
@@ -72,6 +84,52 @@ class DBSCAN:
             self.close()
         except Exception:
             pass
+
+    # ---- autotuner
+    def get_option(self, option: int) -> int:
+        v = ctypes.c_int64(0)
+        _lib.check(self.lib.dbscan_get_option(self.ctx, option, ctypes.byref(v)), "dbscan_get_option")
+        return int(v.value)
+
+    def tuning(self) -> dict:
+        """The tunable options as set now."""
+        return {"schedule": self.get_option(_lib.OPT_SCHEDULE), "cell_bounds": self.get_option(_lib.OPT_CELL_BOUNDS),
+                "connect_waves": self.get_option(_lib.OPT_CONNECT_WAVES),
+                "connect_cells": self.get_option(_lib.OPT_CONNECT_CELLS),
+                "blocks_per_sm": self.get_option(_lib.OPT_BLOCKS_PER_SM)}
+
+    def set_tuning(self, t: dict) -> None:
+        for key, opt in (("schedule", _lib.OPT_SCHEDULE), ("cell_bounds", _lib.OPT_CELL_BOUNDS),
+                         ("connect_waves", _lib.OPT_CONNECT_WAVES), ("connect_cells", _lib.OPT_CONNECT_CELLS),
+                         ("blocks_per_sm", _lib.OPT_BLOCKS_PER_SM)):
+            if key in t:
+                self.set_option(opt, int(t[key]))
+
+    def autotune(self, points, eps: float, min_pts: int, reps: int = 3, stream=None) -> dict:
+        """dbscan_autotune on a CUDA tensor [n, d]; the choice stays set in the context."""
+        torch = _torch()
+        pts = points.contiguous()
+        n, d = pts.shape
+        s = stream if stream is not None else torch.cuda.current_stream(pts.device)
+        out = _lib.Tuning()
+        dtype = _lib.F32 if pts.dtype == torch.float32 else _lib.F64
+        _lib.check(self.lib.dbscan_autotune(self.ctx, pts.data_ptr(), n, d, dtype, float(eps), int(min_pts),
+                                            int(reps), ctypes.byref(out), s.cuda_stream), "dbscan_autotune")
+        return out.as_dict()
+
+    def autotune_batch(self, points, instances, reps: int = 3, stream=None) -> dict:
+        """dbscan_autotune_batch; arguments as for run_batch."""
+        torch = _torch()
+        pts = points.contiguous()
+        N, ld = pts.shape
+        arr = _instances(instances, N)
+        s = stream if stream is not None else torch.cuda.current_stream(pts.device)
+        out = _lib.Tuning()
+        dtype = _lib.F32 if pts.dtype == torch.float32 else _lib.F64
+        _lib.check(self.lib.dbscan_autotune_batch(self.ctx, arr, len(instances), pts.data_ptr(), ld, dtype,
+                                                  int(reps), ctypes.byref(out), s.cuda_stream),
+                   "dbscan_autotune_batch")
+        return out.as_dict()
 
     # ---- learned pair scheduler
     def enable_pair_log(self, capacity: int) -> None:
@@ -172,14 +230,7 @@ class DBSCAN:
             raise ValueError("points must be a CUDA tensor [N, ld]")
         pts = points.contiguous()
         N, ld = pts.shape
-        arr = (_lib.Instance * len(instances))()
-        row = 0
-        for k, (n, d, eps, mp) in enumerate(instances):
-            arr[k].row0, arr[k].n, arr[k].d = row, int(n), int(d)
-            arr[k].reserved, arr[k].eps, arr[k].min_pts = 0, float(eps), int(mp)
-            row += int(n)
-        if row != N:
-            raise ValueError("instance sizes must add up to the number of rows")
+        arr = _instances(instances, N)
         dev = pts.device
         if out is None:
             core = torch.empty(N, dtype=torch.uint8, device=dev)

@@ -21,6 +21,7 @@ STATUS = {
 F32, F64 = 0, 1
 OPT_PRECISION, OPT_SCHEDULE, OPT_COLLECT_STATS, OPT_MAX_ITERS, OPT_PHASE_TIMING, OPT_CELL_BOUNDS = 0, 1, 2, 3, 4, 5
 OPT_BATCH_GRAPH, OPT_PAIR_LOG = 6, 7
+OPT_CONNECT_CELLS, OPT_CONNECT_WAVES, OPT_BLOCKS_PER_SM = 8, 9, 10
 MLP_PARAMS = 1313
 PREC_FP64, PREC_FP32_RECHECK = 0, 1
 SCHED_SIZE, SCHED_NONE, SCHED_LEARNED = 0, 1, 2
@@ -43,6 +44,7 @@ class Stats(ctypes.Structure):
         ("num_border_memberships", ctypes.c_int64), ("band_rechecks", ctypes.c_int64),
         ("distance_evals", ctypes.c_int64), ("distance_evals_phase", ctypes.c_int64 * 3), ("band_lo", ctypes.c_float), ("band_hi", ctypes.c_float),
         ("kernel_launches", ctypes.c_int64), ("phase_ms", ctypes.c_float * 8),
+        ("markcore_pair_bound", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -50,6 +52,16 @@ class Stats(ctypes.Structure):
         out["phase_ms"] = list(self.phase_ms)
         out["distance_evals_phase"] = list(self.distance_evals_phase)
         return out
+
+
+class Tuning(ctypes.Structure):
+    """dbscan_tuning."""
+    _fields_ = [("schedule", ctypes.c_int32), ("cell_bounds", ctypes.c_int32), ("connect_waves", ctypes.c_int32),
+                ("connect_cells", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("trials", ctypes.c_int32),
+                ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class Instance(ctypes.Structure):
@@ -72,6 +84,9 @@ SIGNATURES = {
     "dbscan_scheduler_weights": (_I32, [_P, _P, _I32, _I32]),
     "dbscan_scheduler_loss_grad": (_I32, [_P, _P, _P, _I64, _P, _P]),
     "dbscan_get_pair_log": (_I32, [_P, _P, _P, _I64, ctypes.POINTER(_I64)]),
+    "dbscan_get_option": (_I32, [_P, _I32, ctypes.POINTER(_I64)]),
+    "dbscan_autotune": (_I32, [_P, _P, _I64, _I32, _I32, ctypes.c_double, _I64, _I32, _P, _P]),
+    "dbscan_autotune_batch": (_I32, [_P, ctypes.POINTER(Instance), _I32, _P, _I32, _I32, _I32, _P, _P]),
     "dbscan_status_string": (ctypes.c_char_p, [_I32]),
     "dbscan_version": (_I32, []),
 }

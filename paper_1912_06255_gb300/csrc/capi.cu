@@ -205,6 +205,7 @@ static cudaError_t ensure_hd(dbscan_ctx *c) {
         {(void **)&H.ckey_hi, 8 * N}, {(void **)&H.ccoord, 16 * N}, {(void **)&H.child, 8 * N},
         {(void **)&H.parent, 4 * 2 * N}, {(void **)&H.flag, 4 * N}, {(void **)&H.nlo, 16 * N},
         {(void **)&H.nhi, 16 * N}, {(void **)&H.cnt64, 8 * N}, {(void **)&H.nbr_off, 8 * (N + 1)},
+        {(void **)&H.nblo, 32 * N}, {(void **)&H.nbhi, 32 * N},
     };
     size_t total = 0;
     for (const auto &it : items) total += align_up(it.bytes);
@@ -391,6 +392,7 @@ static dbscan_status finish_run(dbscan_ctx *c, const RunParams &P, int D, int mo
     st.band_rechecks = (int64_t)h.band_rechecks;
     for (int k = 0; k < 3; ++k) st.distance_evals_phase[k] = (int64_t)h.dist_evals[k];
     st.distance_evals = st.distance_evals_phase[0] + st.distance_evals_phase[1] + st.distance_evals_phase[2];
+    st.markcore_pair_bound = (int64_t)h.mc_bound;
     st.kernel_launches = g_launches - launches0;
     if (c->phase_timing) {
         for (int k = 0; k < 8; ++k)
@@ -581,6 +583,18 @@ dbscan_status dbscan_set_option(dbscan_ctx *c, int option, int64_t value) {
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
         c->use_graph = (int)value;
         return DBSCAN_OK;
+    case DBSCAN_OPT_CONNECT_CELLS:
+        if (value != 1 && value != 2 && value != 4 && value != 8) return DBSCAN_ERR_INVALID_ARG;
+        c->cn_cells = (int)value;
+        return DBSCAN_OK;
+    case DBSCAN_OPT_CONNECT_WAVES:
+        if (value != 1 && value != 2) return DBSCAN_ERR_INVALID_ARG;
+        c->waves = (int)value;
+        return DBSCAN_OK;
+    case DBSCAN_OPT_BLOCKS_PER_SM:
+        if (value < 0 || value > 32) return DBSCAN_ERR_INVALID_ARG;
+        c->blocks_per_sm = (int)value;
+        return DBSCAN_OK;
     case DBSCAN_OPT_PHASE_TIMING:
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
         c->phase_timing = (int)value;
@@ -591,6 +605,24 @@ dbscan_status dbscan_set_option(dbscan_ctx *c, int option, int64_t value) {
         return DBSCAN_OK;
     default:
         return DBSCAN_ERR_INVALID_ARG;
+    }
+}
+
+dbscan_status dbscan_get_option(const dbscan_ctx *c, int option, int64_t *value) {
+    if (!c || !value) return DBSCAN_ERR_INVALID_ARG;
+    switch (option) {
+    case DBSCAN_OPT_PRECISION: *value = c->precision; return DBSCAN_OK;
+    case DBSCAN_OPT_SCHEDULE: *value = c->sched; return DBSCAN_OK;
+    case DBSCAN_OPT_COLLECT_STATS: *value = c->collect_stats; return DBSCAN_OK;
+    case DBSCAN_OPT_MAX_ITERS: *value = c->max_iters; return DBSCAN_OK;
+    case DBSCAN_OPT_PHASE_TIMING: *value = c->phase_timing; return DBSCAN_OK;
+    case DBSCAN_OPT_CELL_BOUNDS: *value = c->cell_bounds; return DBSCAN_OK;
+    case DBSCAN_OPT_BATCH_GRAPH: *value = c->use_graph; return DBSCAN_OK;
+    case DBSCAN_OPT_PAIR_LOG: *value = c->log_cap; return DBSCAN_OK;
+    case DBSCAN_OPT_CONNECT_CELLS: *value = c->cn_cells; return DBSCAN_OK;
+    case DBSCAN_OPT_CONNECT_WAVES: *value = c->waves; return DBSCAN_OK;
+    case DBSCAN_OPT_BLOCKS_PER_SM: *value = c->blocks_per_sm; return DBSCAN_OK;
+    default: return DBSCAN_ERR_INVALID_ARG;
     }
 }
 
@@ -647,6 +679,9 @@ dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, 
     P.n = (int)n;
     P.d = d;
     P.max_iters = c->max_iters;
+    P.cn_cells = c->cn_cells;
+    P.waves = c->waves;
+    set_grid_cap(c->blocks_per_sm);
     P.stats = c->collect_stats;
     P.ninst = 1;
     P.inst_shift = 64;
@@ -733,6 +768,9 @@ dbscan_status dbscan_run_batch(dbscan_ctx *c, const dbscan_instance *hi, int cou
     P.n = (int)total;
     P.d = ld;
     P.max_iters = c->max_iters;
+    P.cn_cells = c->cn_cells;
+    P.waves = c->waves;
+    set_grid_cap(c->blocks_per_sm);
     P.stats = c->collect_stats;
     P.box = fp32_all && c->cell_bounds ? 1 : 0;
     P.ninst = count;
@@ -766,7 +804,9 @@ dbscan_status dbscan_run_batch(dbscan_ctx *c, const dbscan_instance *hi, int cou
                                         (unsigned long long)dtype, (unsigned long long)(uintptr_t)d_core,
                                         (unsigned long long)(uintptr_t)d_labels,
                                         (unsigned long long)(uintptr_t)d_border_offsets,
-                                        (unsigned long long)(mode | (c->sched << 4) | (P.box << 8) | (P.stats << 9)),
+                                        (unsigned long long)(mode | (c->sched << 4) | (P.box << 8) | (P.stats << 9) |
+                                                             ((c->log_cap > 0) << 10) | (c->cn_cells << 12) |
+                                                             (c->waves << 20) | (c->blocks_per_sm << 24)),
                                         (unsigned long long)c->phase_timing, (unsigned long long)c->max_iters, 1ull};
     // phase timing records events between the steps: that run is enqueued
     // directly instead of replaying the graph

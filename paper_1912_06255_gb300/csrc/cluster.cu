@@ -138,7 +138,7 @@ k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int m = ctr->m;
     unsigned rech = 0;
-    unsigned long long evals = 0;
+    unsigned long long evals = 0, mc_bound = 0;
     for (int c = warp_id_global(); c < m; c += warps_global()) {
         const int s0 = cell_start[c], k = cell_start[c + 1] - s0;
         const Thr T = P.inst[inst_of_cell(P, c)].thr;
@@ -148,6 +148,13 @@ k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__
         }
         const int ne = nbr_cnt[c];
         const int *nl = nbr_list<D>(nbr, nbr_off, stride, c);
+        if (P.stats) {
+            // algorithmic work: |g| times the points of all neighbouring cells
+            // (the own cell counts |g| without tests, Algorithm 2)
+            unsigned long long pts = 0;
+            for (int e = lane; e < ne; e += 32) pts += cell_start[nl[e] + 1] - cell_start[nl[e]];
+            mc_bound += (unsigned long long)k * pts;
+        }
         for (int b0 = 0; b0 < k; b0 += OWN) {
             const int kb = min(OWN, k - b0);
             __syncwarp();
@@ -163,7 +170,10 @@ k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__
         }
     }
     flush_counter(&ctr->band_rechecks, rech);
-    if (P.stats) flush_counter(&ctr->dist_evals[0], evals);
+    if (P.stats) {
+        flush_counter(&ctr->dist_evals[0], evals);
+        flush_counter(&ctr->mc_bound, mc_bound);
+    }
 }
 
 void launch_markcore(int D, int mode, const RunParams &P, const Bufs &B, DevCounters *ctr, cudaStream_t s) {
@@ -274,8 +284,8 @@ const uint32_t *launch_schedule(int sched, const RunParams &P, const Bufs &B, De
 }
 
 // ----------------------------------------------------------------- connect
-// ClusterCore's pair loop (Algorithm 3).  A warp takes the next CN_CELLS core
-// cells in SortBySize order with one atomic; each cell owns its pairs with
+// ClusterCore's pair loop (Algorithm 3).  A warp takes the next P.cn_cells
+// core cells in SortBySize order with one atomic; each cell owns its pairs with
 // neighbouring core cells that come later in that order.  The warp flattens
 // those pairs over its lanes (one (g, h) pair per lane, whatever cell it
 // belongs to), so the loads of 32 pairs are in flight together; each lane
@@ -283,7 +293,6 @@ const uint32_t *launch_schedule(int sched, const RunParams &P, const Bufs &B, De
 // the survivors get a BCP test one at a time, each re-checked just before its
 // test because a link made meanwhile may already join the two ("Reducing Cell
 // Connectivity Queries").  A hit links the two cells.
-constexpr int CN_CELLS = 4;  // cells per work item: ~4x13 near pairs fill two lane rounds
 
 template <int D, int M, int WAVE>
 __global__ void __launch_bounds__(256, 2)
@@ -296,23 +305,26 @@ k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict
     const int lane = threadIdx.x & 31;
     const int m = ctr->m;
     const bool use_box = BOX && P.box;
-    int *next = WAVE == 0 ? &ctr->cell_next : &ctr->cell_next2;
+    // WAVE 0: adjacent-cell pairs (current parents compared); 1: farther pairs
+    // after compression (finds); 2: all pairs in one wave (finds)
+    int *next = WAVE == 1 ? &ctr->cell_next2 : &ctr->cell_next;
+    const int cells = P.cn_cells;
     unsigned rech = 0;
     unsigned long long evals = 0, tested = 0, skipped = 0, linked = 0, cand_pairs = 0, boxed = 0;
     for (;;) {
         int base = 0;
-        if (lane == 0) base = atomicAdd(next, CN_CELLS);
+        if (lane == 0) base = atomicAdd(next, cells);
         base = __shfl_sync(0xffffffffu, base, 0);
         if (base >= m) break;
-        // lane l < CN_CELLS: the cell at rank base + l and the range of its pair list
+        // lane l < cells: the cell at rank base + l and the range of its pair list
         int ca = 0, ca0 = 0, cna = 0, cbeg = 0, ccnt = 0;
-        if (lane < CN_CELLS && base + lane < m) {
+        if (lane < cells && base + lane < m) {
             ca = order ? (int)order[base + lane] : base + lane;
             ca0 = ccs[ca];
             cna = ccs[ca + 1] - ca0;
             if (cna > 0) {
                 const int near = nbr_near[ca];
-                cbeg = WAVE == 0 ? 0 : near;
+                cbeg = WAVE == 1 ? near : 0;
                 ccnt = (WAVE == 0 ? near : nbr_cnt[ca]) - cbeg;
             }
         }
@@ -429,6 +441,14 @@ void launch_connect(int D, int mode, const uint32_t *order, const RunParams &P, 
     int g = grid_for((const void *)k_uf_init, 256);
     k_uf_init<<<g, 256, 0, s>>>(B.parent, ctr); count_launch();
     GBDB_DISPATCH(D, mode, {
+        if (P.waves == 1) {
+            auto k2 = k_connect<DD, MM, 2>;
+            const int g2 = grid_for((const void *)k2, 256);
+            k2<<<g2, 256, 0, s>>>(P, order, B.rank, B.ccs, B.nbr_cnt, B.nbr_near, B.nbr, B.nbr_stride, B.nbr_off,
+                                  B.cpf, B.cpd, B.cblo, B.cbhi, B.parent, ctr);
+            count_launch();
+            break;
+        }
         auto k0 = k_connect<DD, MM, 0>;
         int gg = grid_for((const void *)k0, 256);
         k0<<<gg, 256, 0, s>>>(P, order, B.rank, B.ccs, B.nbr_cnt, B.nbr_near, B.nbr, B.nbr_stride, B.nbr_off, B.cpf, B.cpd,

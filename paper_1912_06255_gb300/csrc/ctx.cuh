@@ -29,6 +29,9 @@ struct dbscan_ctx {
     int phase_timing = 0;
     int cell_bounds = 1;
     int use_graph = 1;
+    int cn_cells = 4;       // DBSCAN_OPT_CONNECT_CELLS
+    int waves = 2;          // DBSCAN_OPT_CONNECT_WAVES
+    int blocks_per_sm = 0;  // DBSCAN_OPT_BLOCKS_PER_SM
     cudaEvent_t ev[9] = {};
     // workspace
     void *arena = nullptr;

@@ -105,6 +105,7 @@ struct HdBufs {
     int *parent;                  // [2m-1] parent of each node (-1 at the root)
     int *flag;                    // [m-1] arrival counters of the bottom-up pass
     int4 *nlo, *nhi;              // [m-1] node bounds in cell coordinates, 8 x 16 bits
+    float4 *nblo, *nbhi;          // [m-1] x 2: node bounding boxes of the points (FP32-band mode)
     long long *cnt64;             // [m] neighbours per cell
     long long *nbr_off;           // [m+1] CSR offsets of the neighbour lists
 };

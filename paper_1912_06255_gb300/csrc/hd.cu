@@ -24,7 +24,9 @@ namespace gbdb {
 
 namespace {
 
-constexpr int kStack = 160;  // >= depth of the tree (at most key bits + 1)
+// Stack of the tree walks: a walk that expands up to 4 nodes a step keeps at
+// most 4 pending nodes per level of the tree (at most key bits + 1 levels).
+constexpr int kStack = 4 * 132;
 
 // Cell coordinates are packed as 8 unsigned 16-bit values in an int4
 // (component k holds dimensions 2k and 2k + 1).
@@ -195,7 +197,8 @@ k_lbvh_nodes(const uint64_t *__restrict__ klo, const uint64_t *__restrict__ khi,
 __global__ void __launch_bounds__(256)
 k_lbvh_bounds(const int2 *__restrict__ child, const int *__restrict__ parent, int *__restrict__ flag,
               const int4 *__restrict__ ccoord, int4 *__restrict__ nlo, int4 *__restrict__ nhi, int d,
-              DevCounters *ctr) {
+              const float4 *__restrict__ blo, const float4 *__restrict__ bhi, float4 *__restrict__ nblo,
+              float4 *__restrict__ nbhi, DevCounters *ctr) {
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
         int node = (m - 1) + c;
@@ -234,6 +237,32 @@ k_lbvh_bounds(const int2 *__restrict__ child, const int *__restrict__ parent, in
                 if (j >= d) lo[j] = hi[j] = 0;
             __stcg(nlo + p, pack16(lo));
             __stcg(nhi + p, pack16(hi));
+            if (nblo) {
+                // point boxes: the union of the children's (cells' or nodes') boxes
+                float4 l0 = make_float4(INFINITY, INFINITY, INFINITY, INFINITY), l1 = l0;
+                float4 h0 = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY), h1 = h0;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int q = k ? ch.y : ch.x;
+                    float4 a0, a1, b0, b1;
+                    if (q >= m - 1) {
+                        const int64_t cq = q - (m - 1);
+                        a0 = blo[cq * 2]; a1 = blo[cq * 2 + 1];
+                        b0 = bhi[cq * 2]; b1 = bhi[cq * 2 + 1];
+                    } else {
+                        a0 = __ldcg(nblo + (int64_t)q * 2); a1 = __ldcg(nblo + (int64_t)q * 2 + 1);
+                        b0 = __ldcg(nbhi + (int64_t)q * 2); b1 = __ldcg(nbhi + (int64_t)q * 2 + 1);
+                    }
+                    l0 = make_float4(fminf(l0.x, a0.x), fminf(l0.y, a0.y), fminf(l0.z, a0.z), fminf(l0.w, a0.w));
+                    l1 = make_float4(fminf(l1.x, a1.x), fminf(l1.y, a1.y), fminf(l1.z, a1.z), fminf(l1.w, a1.w));
+                    h0 = make_float4(fmaxf(h0.x, b0.x), fmaxf(h0.y, b0.y), fmaxf(h0.z, b0.z), fmaxf(h0.w, b0.w));
+                    h1 = make_float4(fmaxf(h1.x, b1.x), fmaxf(h1.y, b1.y), fmaxf(h1.z, b1.z), fmaxf(h1.w, b1.w));
+                }
+                __stcg(nblo + (int64_t)p * 2, l0);
+                __stcg(nblo + (int64_t)p * 2 + 1, l1);
+                __stcg(nbhi + (int64_t)p * 2, h0);
+                __stcg(nbhi + (int64_t)p * 2 + 1, h1);
+            }
             node = p;
         }
     }
@@ -254,82 +283,124 @@ __device__ __forceinline__ int gap2(const int (&c)[8], const int4 &lo, const int
     return s;
 }
 
-// NeighborCells(g) for every cell g.  FILL = false: counts (nbr_cnt, nbr_near,
-// and the count as int64 in cnt64 for the offset scan); FILL = true: the ids
-// at off[g], the |delta|_inf <= 1 cells first.  In the FP32-band mode cells
-// whose point boxes are farther than eps apart are dropped, as in the
-// enumeration of low dimensions.
+// NeighborCells(g) for every cell g (Algorithm 2), as a packet traversal: a
+// warp walks the tree once for 32 consecutive cells in Z order (one per
+// lane), which are close in space and so share most of the walk.  A node is
+// entered when it may hold a neighbour of any lane's cell; at a leaf every
+// lane applies the exact offset rule to its own cell.  In the FP32-band mode
+// nodes and cells whose point boxes are farther than eps apart are skipped,
+// as in the enumeration of low dimensions.  FILL = false: counts (nbr_cnt,
+// nbr_near, and as int64 in cnt64 for the offset scan); FILL = true: the ids
+// at off[g], cells at |delta|_inf <= 1 first.
+constexpr int QW = 4;  // warps per block of the query
+constexpr int QK = 1;  // nodes a warp expands per step (more did not pay: the walk is issue-bound)
+
 template <bool FILL>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(32 * QW)
 k_lbvh_query(RunParams P, const int2 *__restrict__ child, const int4 *__restrict__ nlo, const int4 *__restrict__ nhi,
-             const int4 *__restrict__ ccoord, const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
+             const float4 *__restrict__ nblo, const float4 *__restrict__ nbhi, const int4 *__restrict__ ccoord,
+             const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
              int *__restrict__ nbr_cnt, int *__restrict__ nbr_near, long long *__restrict__ cnt64,
              const long long *__restrict__ off, int *__restrict__ nbr, DevCounters *ctr) {
+    __shared__ int stk[QW][kStack];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int m = ctr->m, d = P.d;
     const float hi_thr = P.inst[0].thr.hi;
     long long total = 0;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < m; g += gridDim.x * blockDim.x) {
+    const int packets = (m + 31) >> 5;
+    for (int pk = warp_id_global(); pk < packets; pk += warps_global()) {
+        const int g = pk * 32 + lane;
+        const bool valid = g < m;
         int c[8];
-        const int4 cg = ccoord[g];
+        {
+            const int4 cg = valid ? ccoord[g] : make_int4(0, 0, 0, 0);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) c[j] = unpack16(cg, j);
+            for (int j = 0; j < 8; ++j) c[j] = unpack16(cg, j);
+        }
         Bx<8> glo = zero_box<8>(), ghi = glo;
-        if (P.box) { glo = load_box<8>(blo, g); ghi = load_box<8>(bhi, g); }
-        int n_near = 0, n_far = 0;
-        int near_at = 0, far_at = 0;
+        if (P.box && valid) { glo = load_box<8>(blo, g); ghi = load_box<8>(bhi, g); }
+        int n_near = 0, n_far = 0, near_at = 0, far_at = 0;
         long long base = 0;
-        if (FILL) {
+        if (FILL && valid) {
             base = off[g];
-            near_at = 0;
             far_at = nbr_near[g];
         }
-        int stack[kStack];
         int sp = 0;
-        if (m > 1) stack[sp++] = 0;
+        if (m > 1) {
+            if (lane == 0) stk[w][0] = 0;
+            sp = 1;
+        }
+        __syncwarp();
         while (sp > 0) {
-            const int node = stack[--sp];
-            const int2 ch = child[node];
+            // up to QK nodes per step, so their loads overlap
+            const int kk = sp < QK ? sp : QK;
+            int2 ch[QK];
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int q = k ? ch.y : ch.x;
-                if (q >= m - 1) {
-                    const int h = q - (m - 1);
-                    if (h == g) continue;
-                    const int4 ch4 = ccoord[h];
-                    int s = 0, inf = 0;
+            for (int u = 0; u < QK; ++u) {
+                const int node = u < kk ? stk[w][sp - 1 - u] : -1;
+                ch[u] = node >= 0 ? child[node] : make_int2(-1, -1);
+            }
+            sp -= kk;
+            __syncwarp();
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        if (j < d) {
-                            const int dj = abs(unpack16(ch4, j) - c[j]);
-                            inf = max(inf, dj);
-                            const int gj = min(max(dj - 1, 0), 9);
-                            s += gj * gj;
+            for (int u = 0; u < QK; ++u) {
+#pragma unroll
+                for (int k = 1; k >= 0; --k) {  // right child pushed first, so the left one is popped first
+                    const int q = k ? ch[u].y : ch[u].x;
+                    if (q < 0) continue;
+                    if (q >= m - 1) {
+                        const int h = q - (m - 1);
+                        if (!valid || h == g) continue;
+                        const int4 ch4 = ccoord[h];
+                        int s = 0, inf = 0;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            if (j < d) {
+                                const int dj = abs(unpack16(ch4, j) - c[j]);
+                                inf = max(inf, dj);
+                                const int gj = min(max(dj - 1, 0), 9);
+                                s += gj * gj;
+                            }
+                        }
+                        if (s > d) continue;
+                        if (P.box && boxes_min_d2<8>(glo, ghi, load_box<8>(blo, h), load_box<8>(bhi, h)) > hi_thr)
+                            continue;
+                        if (inf <= 1) {
+                            if (FILL) nbr[base + near_at++] = h;
+                            ++n_near;
+                        } else {
+                            if (FILL) nbr[base + far_at++] = h;
+                            ++n_far;
+                        }
+                    } else {
+                        bool enter = valid && gap2(c, nlo[q], nhi[q], d) <= d;
+                        if (enter && P.box)
+                            enter = boxes_min_d2<8>(glo, ghi, load_box<8>(nblo, q), load_box<8>(nbhi, q)) <= hi_thr;
+                        if (__any_sync(0xffffffffu, enter)) {
+                            if (sp < kStack) {
+                                if (lane == 0) stk[w][sp] = q;
+                                ++sp;
+                            } else if (lane == 0) {
+                                set_error(ctr, DBSCAN_ERR_CAPACITY, 72);
+                            }
                         }
                     }
-                    if (s > d) continue;
-                    if (P.box && boxes_min_d2<8>(glo, ghi, load_box<8>(blo, h), load_box<8>(bhi, h)) > hi_thr)
-                        continue;
-                    if (inf <= 1) {
-                        if (FILL) nbr[base + near_at++] = h;
-                        ++n_near;
-                    } else {
-                        if (FILL) nbr[base + far_at++] = h;
-                        ++n_far;
-                    }
-                } else if (gap2(c, nlo[q], nhi[q], d) <= d) {
-                    if (sp < kStack) stack[sp++] = q;
-                    else set_error(ctr, DBSCAN_ERR_CAPACITY, 72);
                 }
             }
+            __syncwarp();
         }
-        if (!FILL) {
+        if (!FILL && valid) {
             nbr_cnt[g] = n_near + n_far;
             nbr_near[g] = n_near;
             cnt64[g] = n_near + n_far;
             total += n_near + n_far;
         }
     }
-    if (!FILL && total) atomicAdd((unsigned long long *)&ctr->E, (unsigned long long)total);
+    if (!FILL) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+        if (lane == 0 && total) atomicAdd((unsigned long long *)&ctr->E, (unsigned long long)total);
+    }
 }
 
 template <typename T> void hd_launch_keys(const void *X, const RunParams &P, const HdBufs &H, const Bufs &B,
@@ -391,10 +462,11 @@ void hd_cells_and_counts(const void *X, int dtype, const RunParams &P, int key_b
         k_lbvh_nodes<<<g, 256, 0, s>>>(H.ckey_lo, H.ckey_hi, H.child, H.parent, H.flag, ctr);
         count_launch();
         g = grid_for((const void *)k_lbvh_bounds, 256);
-        k_lbvh_bounds<<<g, 256, 0, s>>>(H.child, H.parent, H.flag, H.ccoord, H.nlo, H.nhi, P.d, ctr);
+        k_lbvh_bounds<<<g, 256, 0, s>>>(H.child, H.parent, H.flag, H.ccoord, H.nlo, H.nhi, P.d, B.blo, B.bhi,
+                                        P.box ? H.nblo : nullptr, P.box ? H.nbhi : nullptr, ctr);
         count_launch();
-        g = grid_for((const void *)k_lbvh_query<false>, 128);
-        k_lbvh_query<false><<<g, 128, 0, s>>>(P, H.child, H.nlo, H.nhi, H.ccoord, B.blo, B.bhi,
+        g = grid_for((const void *)k_lbvh_query<false>, 32 * QW);
+        k_lbvh_query<false><<<g, 32 * QW, 0, s>>>(P, H.child, H.nlo, H.nhi, H.nblo, H.nbhi, H.ccoord, B.blo, B.bhi,
                                               const_cast<int *>(B.nbr_cnt), const_cast<int *>(B.nbr_near), H.cnt64,
                                               nullptr, nullptr, ctr);
         count_launch();
@@ -404,8 +476,8 @@ void hd_cells_and_counts(const void *X, int dtype, const RunParams &P, int key_b
 
 // Step 4's fill pass, into nbr (which holds at least ctr->E entries).
 void hd_fill(const RunParams &P, const HdBufs &H, const Bufs &B, int *nbr, DevCounters *ctr, cudaStream_t s) {
-    const int g = grid_for((const void *)k_lbvh_query<true>, 128);
-    k_lbvh_query<true><<<g, 128, 0, s>>>(P, H.child, H.nlo, H.nhi, H.ccoord, B.blo, B.bhi,
+    const int g = grid_for((const void *)k_lbvh_query<true>, 32 * QW);
+    k_lbvh_query<true><<<g, 32 * QW, 0, s>>>(P, H.child, H.nlo, H.nhi, H.nblo, H.nbhi, H.ccoord, B.blo, B.bhi,
                                          const_cast<int *>(B.nbr_cnt), const_cast<int *>(B.nbr_near), nullptr,
                                          H.nbr_off, nbr, ctr);
     count_launch();

@@ -34,6 +34,7 @@ struct DevCounters {
     unsigned long long pairs_tested, pairs_skipped, pairs_linked, pairs_box;
     unsigned long long band_rechecks;
     unsigned long long dist_evals[3];  // MarkCore, BCP, border
+    unsigned long long mc_bound;       // MarkCore pair tests without early exit
 };
 
 // Decision thresholds of one problem instance.
@@ -68,6 +69,8 @@ struct RunParams {
     int inst_shift;  // instance id sits in key bits >= inst_shift (ninst > 1)
     const Inst *inst;     // [ninst] device
     const int *cell_inst; // [m] device: instance of each cell (ninst > 1)
+    int cn_cells;   // core cells per work item of the connectivity kernel
+    int waves;      // 2: adjacent pairs, compression, farther pairs; 1: one wave
     // copies of instance 0 for single runs (host side convenience)
     int min_pts;
     double eps2;
@@ -119,7 +122,9 @@ int radix_sort_u64(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int n
 extern thread_local long long g_launches;
 inline void count_launch() { ++g_launches; }
 
-// Persistent-grid size for a kernel: resident blocks per SM x SM count.
+// Persistent-grid size for a kernel: resident blocks per SM x SM count,
+// capped by the blocks-per-SM limit this thread set (0 = no cap).
 int grid_for(const void *kernel, int threads, size_t smem = 0);
+void set_grid_cap(int blocks_per_sm);
 
 }  // namespace gbdb

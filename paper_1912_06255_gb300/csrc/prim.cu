@@ -12,7 +12,11 @@ namespace gbdb {
 // ------------------------------------------------------------------ helpers
 thread_local long long g_launches = 0;
 
+static thread_local int t_grid_cap = 0;
+void set_grid_cap(int blocks_per_sm) { t_grid_cap = blocks_per_sm; }
+
 int grid_for(const void *kernel, int threads, size_t smem) {
+    const int cap = t_grid_cap;
     static std::mutex mu;
     static std::unordered_map<const void *, int> cache;
     static int sms = 0;
@@ -23,15 +27,18 @@ int grid_for(const void *kernel, int threads, size_t smem) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 1;
     }
-    auto it = cache.find(kernel);
-    if (it != cache.end()) return it->second;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
-            cudaSuccess || per_sm <= 0)
-        per_sm = 1;
-    int g = per_sm * sms;
-    cache[kernel] = g;
-    return g;
+    auto it = cache.find(kernel);
+    if (it != cache.end()) {
+        per_sm = it->second;
+    } else {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+            per_sm <= 0)
+            per_sm = 1;
+        cache[kernel] = per_sm;
+    }
+    if (cap > 0 && cap < per_sm) per_sm = cap;
+    return per_sm * sms;
 }
 
 template <typename T> __device__ __forceinline__ T warp_incl_scan(T v) {

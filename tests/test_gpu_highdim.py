@@ -78,10 +78,22 @@ def test_spreader_5d_scaled():
     assert st["num_cells"] > 1000
 
 
-@pytest.mark.parametrize("eps", [1000.0, 2000.0])
+@pytest.mark.parametrize("eps", [500.0, 1000.0, 2000.0])
 def test_spreader_7d_scaled(eps):
     I = synth.spreader_7d_10m(n=100_000, eps=eps)
     _assert_same(I.points, I.eps, I.min_pts)
+
+
+@pytest.mark.parametrize("d", [7, 8])
+def test_keys_wider_than_64_bits(d):
+    """More than 64 key bits (the two-word sort): 10 bits per dimension."""
+    X = synth.random_small(800 + d, 8000, d, dtype=np.float32)
+    rng = np.random.default_rng(d)
+    X = np.concatenate([X, X[:2000] + (rng.standard_normal((2000, d)) * 0.01).astype(np.float32)])
+    eps = 10.0 * np.sqrt(d) / 700.0  # about 800 cells per dimension
+    st = _assert_same(X, eps, 2)
+    assert st["key_bits"] > 64
+    _assert_same(X, eps * 8, 3, precision="fp64")
 
 
 def test_highdim_key_overflow_and_reuse():

@@ -1,0 +1,87 @@
+"""Runtime knobs of the persistent kernels and the autotuner on the GPU.
+
+No knob may change the result (it only orders or groups exact tests); the
+autotuner keeps the fastest of the settings it timed, starting with the one
+the context had.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_06255_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1912_06255_gb300 import DBSCAN, DbscanError, _lib  # noqa: E402
+
+
+def _check(ctx, X, eps, mp):
+    r = ctx.run(torch.from_numpy(X).cuda(), eps, mp)
+    exp = oracle.dbscan(X, eps, mp)
+    assert np.array_equal(r.core.cpu().numpy(), exp[0])
+    assert np.array_equal(r.labels.cpu().numpy(), exp[1])
+    assert np.array_equal(r.border_offsets.cpu().numpy(), exp[2])
+    assert np.array_equal(r.border_ids.cpu().numpy(), exp[3])
+    return ctx.stats()
+
+
+@pytest.mark.parametrize("cells", [1, 2, 4, 8])
+@pytest.mark.parametrize("waves", [1, 2])
+@pytest.mark.parametrize("blocks", [0, 1, 3])
+def test_knobs_keep_the_result(cells, waves, blocks):
+    X = synth.random_small(55, 15000, 3, dtype=np.float32)
+    ctx = DBSCAN(len(X), 3)
+    ctx.set_tuning({"connect_cells": cells, "connect_waves": waves, "blocks_per_sm": blocks})
+    assert ctx.tuning()["connect_cells"] == cells and ctx.tuning()["connect_waves"] == waves
+    st = _check(ctx, X, 0.25, 10)
+    assert st["num_pairs_tested"] + st["num_pairs_skipped"] + st["num_pairs_box_decided"] == st["num_candidate_pairs"]
+
+
+def test_knob_validation():
+    ctx = DBSCAN(100, 3)
+    for opt, bad in ((_lib.OPT_CONNECT_CELLS, 3), (_lib.OPT_CONNECT_WAVES, 0), (_lib.OPT_BLOCKS_PER_SM, -1),
+                     (_lib.OPT_BLOCKS_PER_SM, 33)):
+        with pytest.raises(DbscanError):
+            ctx.set_option(opt, bad)
+    with pytest.raises(DbscanError):
+        ctx.get_option(99)
+
+
+@pytest.mark.parametrize("d", [3, 6])
+def test_autotune_single(d):
+    X = synth.random_small(66 + d, 40000, d, dtype=np.float32)
+    eps = 0.25 if d == 3 else 0.9
+    ctx = DBSCAN(len(X), d)
+    t = ctx.autotune(torch.from_numpy(X).cuda(), eps, 10, reps=2)
+    assert t["trials"] >= 10 and 0 < t["best_ms"] <= t["default_ms"]
+    assert t["connect_cells"] in (1, 2, 4, 8) and t["connect_waves"] in (1, 2) and t["schedule"] in (0, 1, 2)
+    assert ctx.tuning() == {k: t[k] for k in ("schedule", "cell_bounds", "connect_waves", "connect_cells",
+                                                "blocks_per_sm")}
+    _check(ctx, X, eps, 10)
+
+
+def test_autotune_batch():
+    B = synth.batch_256(seed=77, count=12, lo=1e3, hi=3e4)
+    N = sum(len(b.points) for b in B)
+    P = np.zeros((N, 3), np.float32)
+    row = 0
+    for b in B:
+        P[row:row + len(b.points), :b.points.shape[1]] = b.points
+        row += len(b.points)
+    inst = [(len(b.points), b.points.shape[1], b.eps, b.min_pts) for b in B]
+    ctx = DBSCAN(N, 3)
+    X = torch.from_numpy(P).cuda()
+    t = ctx.autotune_batch(X, inst, reps=2)
+    assert t["trials"] >= 10 and t["best_ms"] <= t["default_ms"]
+    r = ctx.run_batch(X, inst)
+    core, labels = r.core.cpu().numpy(), r.labels.cpu().numpy()
+    row = 0
+    for b in B:
+        n = len(b.points)
+        exp = oracle.dbscan(b.points, b.eps, b.min_pts)
+        assert np.array_equal(core[row:row + n], exp[0]) and np.array_equal(labels[row:row + n], exp[1])
+        row += n
