@@ -232,6 +232,16 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(x, dist, dev):
+    """The largest of every rank's x (the step time of the slowest replica)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _time_oracle(samples):
     import oracle
     oracle.build()
@@ -335,7 +345,7 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    W = WORKLOADS[args.workload](args.n)
+    W = WORKLOADS[args.workload](args.points)
     samples, desc = W.cpu_sample()
     ts, npts, cores = [], 0, 1
     for i in range(args.warmup + args.steps):
@@ -411,7 +421,7 @@ def run_gpu(args):
     from paper_1912_06255_gb300 import DBSCAN, build
 
     build.build()
-    W = WORKLOADS[args.workload](args.n)
+    W = WORKLOADS[args.workload](args.points)
     n = W.n
     dev = torch.device("cuda", local)
     X = W.device_input(dev)
@@ -530,11 +540,7 @@ def run_gpu(args):
     ctx.set_tuning(setting)
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return _max_over_ranks(x, dist, dev)
 
     t_ms = max_over_ranks(t_ms)
     t64 = max_over_ranks(sum(ms64) / len(ms64))
@@ -602,7 +608,7 @@ def main():
                     help='explicit settings instead of the autotuner, e.g. \'{"connect_waves": 1, "connect_cells": 8}\'')
     ap.add_argument("--profile", action="store_true",
                     help="run warm-up + timed steps only and print no bench line (for ncu)")
-    ap.add_argument("--n", type=int, default=None,
+    ap.add_argument("--points", type=int, default=None,
                     help="points of a single-instance workload (default: its defined size, 2e6 in 3D, 1e7 in 5D/7D)")
     ap.add_argument("--eps", type=float, default=None, help="eps of the 5D or 7D workload (default 200 / 1000)")
     args = ap.parse_args()
