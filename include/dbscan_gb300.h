@@ -97,7 +97,12 @@ enum {
     DBSCAN_OPT_CONNECT_WAVES = 9,
     /* value: 0 (default: as many as fit) or 1..32: resident blocks per SM of
        the persistent (grid-stride, work-counter) kernels */
-    DBSCAN_OPT_BLOCKS_PER_SM = 10
+    DBSCAN_OPT_BLOCKS_PER_SM = 10,
+    /* value: 0 (default: off) or a limit L: MarkCore counts for the points of
+       sparse cells with fewer than 8 points and at most L points in their
+       neighbouring cells with one thread per point instead of one warp per
+       cell (faster on sparse inputs) */
+    DBSCAN_OPT_SMALL_CELLS = 11
 };
 enum { DBSCAN_PREC_FP64 = 0, DBSCAN_PREC_FP32_RECHECK = 1 };
 /* SIZE: core-cell pairs are tested in order of non-increasing core count of the
@@ -321,6 +326,7 @@ typedef struct {
     int32_t connect_waves;  /* DBSCAN_OPT_CONNECT_WAVES */
     int32_t connect_cells;  /* DBSCAN_OPT_CONNECT_CELLS */
     int32_t blocks_per_sm;  /* DBSCAN_OPT_BLOCKS_PER_SM */
+    int32_t small_cells;    /* DBSCAN_OPT_SMALL_CELLS */
     int32_t trials;         /* configurations timed */
     float best_ms;          /* wall time of one call with the chosen configuration (best of reps) */
     float default_ms;       /* the same for the configuration the context had before */
@@ -330,8 +336,8 @@ typedef struct {
  * Autotuner (the tile and schedule choice of the batched persistent kernels):
  * time dbscan_run on this input for candidate settings of the pair schedule,
  * the cell-box decisions (FP32 mode only), one or two connectivity waves, the
- * core cells per work item of the connectivity kernel and the resident blocks
- * per SM of the persistent kernels, by coordinate descent from the context's
+ * core cells per work item of the connectivity kernel, the resident blocks
+ * per SM of the persistent kernels and MarkCore's thread-per-point limit, by coordinate descent from the context's
  * current setting (one warm-up and `reps` timed calls per candidate, the
  * fastest kept), and leave the fastest setting in the context.  None of the
  * settings changes the result.  Arguments as for dbscan_run; the outputs go

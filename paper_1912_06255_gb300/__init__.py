@@ -96,12 +96,13 @@ class DBSCAN:
         return {"schedule": self.get_option(_lib.OPT_SCHEDULE), "cell_bounds": self.get_option(_lib.OPT_CELL_BOUNDS),
                 "connect_waves": self.get_option(_lib.OPT_CONNECT_WAVES),
                 "connect_cells": self.get_option(_lib.OPT_CONNECT_CELLS),
-                "blocks_per_sm": self.get_option(_lib.OPT_BLOCKS_PER_SM)}
+                "blocks_per_sm": self.get_option(_lib.OPT_BLOCKS_PER_SM),
+                "small_cells": self.get_option(_lib.OPT_SMALL_CELLS)}
 
     def set_tuning(self, t: dict) -> None:
         for key, opt in (("schedule", _lib.OPT_SCHEDULE), ("cell_bounds", _lib.OPT_CELL_BOUNDS),
                          ("connect_waves", _lib.OPT_CONNECT_WAVES), ("connect_cells", _lib.OPT_CONNECT_CELLS),
-                         ("blocks_per_sm", _lib.OPT_BLOCKS_PER_SM)):
+                         ("blocks_per_sm", _lib.OPT_BLOCKS_PER_SM), ("small_cells", _lib.OPT_SMALL_CELLS)):
             if key in t:
                 self.set_option(opt, int(t[key]))
 

@@ -94,6 +94,7 @@ static Bufs make_bufs(dbscan_ctx *c, bool f64) {
     B.nbr_near = c->nbr_near;
     B.nbr = c->nbr_cur ? c->nbr_cur : c->nbr;
     B.nbr_off = c->nbr_off_cur;
+    B.nbr_pts = c->nbr_pts;
     B.core_s = c->core_s;
     B.core_pos = c->core_pos;
     B.ccs = c->ccs;
@@ -302,6 +303,11 @@ static dbscan_status enqueue_hash_cells(dbscan_ctx *c, const RunParams &P, int S
     S.cell_inst = c->cell_inst;
     S.key_lo = sort_lo;
     S.key_bits = sort_bits;
+    // the Bloom filter pays only when the hash table does not fit in L2
+    const bool use_bloom = 16 * c->hcap > ((uint64_t)96 << 20);
+    S.bloom = use_bloom ? c->bloom : nullptr;
+    S.bloom_lg = c->bloom_lg;
+    if (use_bloom) CK(cudaMemsetAsync(c->bloom, 0, ((size_t)1 << c->bloom_lg) / 8, s));
     launch_semisort(d_points, dtype, P, SD, S, c->ctr, s);
 
     // 4. cell boxes, neighbour lists
@@ -309,8 +315,9 @@ static dbscan_status enqueue_hash_cells(dbscan_ctx *c, const RunParams &P, int S
     if (P.box) launch_boxes(SD, c->pf, c->cell_start, c->ctr, c->blo, c->bhi, s);
     int n_near = 1;
     for (int j = 0; j < d_enum; ++j) n_near *= 3;
-    launch_neighbors(c->cell_key, c->ht, c->hcap, P, offs_for(c, d_enum), c->noff[d_enum], n_near - 1, c->blo,
-                     c->bhi, c->nbr_cnt, c->nbr_near, c->nbr, c->ctr, s);
+    launch_neighbors(c->cell_key, c->ht, c->hcap, S.bloom, c->bloom_lg, P, offs_for(c, d_enum), c->noff[d_enum],
+                     n_near - 1, c->blo, c->bhi, c->cell_start, c->nbr_cnt, c->nbr_near,
+                     P.mc_small_nbr > 0 && P.mc_small_nbr < (1 << 30) ? c->nbr_pts : nullptr, c->nbr, c->ctr, s);
     c->nbr_cur = c->nbr;
     c->nbr_off_cur = nullptr;
     return DBSCAN_OK;
@@ -476,6 +483,7 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
     const int64_t npart = scan_partials(N + 1) + 2;
     const uint64_t hcap = hash_capacity((int)N);
     c->sort_scratch_size = sort_scratch_bytes(N);
+    c->bloom_lg = bloom_log2(N);
     const int SD = c->sd_max;
     const size_t BW = SD == 8 ? 2 : 1;  // float4 values per cell box
 
@@ -491,8 +499,9 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
         {(void **)&c->cpf, 4 * (size_t)N * SD}, {(void **)&c->cpd, 8 * (size_t)N * SD},
         {(void **)&c->orig, 4 * (size_t)N}, {(void **)&c->cell_of, 4 * (size_t)N},
         {(void **)&c->cell_start, 4 * (size_t)(N + 1)}, {(void **)&c->cell_key, 8 * (size_t)N},
-        {(void **)&c->ht, 16 * (size_t)hcap},
+        {(void **)&c->ht, 16 * (size_t)hcap}, {(void **)&c->bloom, ((size_t)1 << bloom_log2(N)) / 8},
         {(void **)&c->nbr_cnt, 4 * (size_t)(N + 1)}, {(void **)&c->nbr_near, 4 * (size_t)(N + 1)},
+        {(void **)&c->nbr_pts, 4 * (size_t)(N + 1)},
         {(void **)&c->nbr, 4 * (size_t)c->nbr_cap},
         {(void **)&c->core_s, 4 * (size_t)N}, {(void **)&c->core_pos, 4 * (size_t)(N + 1)},
         {(void **)&c->ccs, 4 * (size_t)(N + 1)}, {(void **)&c->core_orig, 4 * (size_t)N},
@@ -595,6 +604,10 @@ dbscan_status dbscan_set_option(dbscan_ctx *c, int option, int64_t value) {
         if (value < 0 || value > 32) return DBSCAN_ERR_INVALID_ARG;
         c->blocks_per_sm = (int)value;
         return DBSCAN_OK;
+    case DBSCAN_OPT_SMALL_CELLS:
+        if (value < 0 || value > (1ll << 30)) return DBSCAN_ERR_INVALID_ARG;
+        c->mc_small_nbr = (int)value;
+        return DBSCAN_OK;
     case DBSCAN_OPT_PHASE_TIMING:
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
         c->phase_timing = (int)value;
@@ -622,6 +635,7 @@ dbscan_status dbscan_get_option(const dbscan_ctx *c, int option, int64_t *value)
     case DBSCAN_OPT_CONNECT_CELLS: *value = c->cn_cells; return DBSCAN_OK;
     case DBSCAN_OPT_CONNECT_WAVES: *value = c->waves; return DBSCAN_OK;
     case DBSCAN_OPT_BLOCKS_PER_SM: *value = c->blocks_per_sm; return DBSCAN_OK;
+    case DBSCAN_OPT_SMALL_CELLS: *value = c->mc_small_nbr; return DBSCAN_OK;
     default: return DBSCAN_ERR_INVALID_ARG;
     }
 }
@@ -681,6 +695,7 @@ dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, 
     P.max_iters = c->max_iters;
     P.cn_cells = c->cn_cells;
     P.waves = c->waves;
+    P.mc_small_nbr = c->mc_small_nbr;
     set_grid_cap(c->blocks_per_sm);
     P.stats = c->collect_stats;
     P.ninst = 1;
@@ -770,6 +785,7 @@ dbscan_status dbscan_run_batch(dbscan_ctx *c, const dbscan_instance *hi, int cou
     P.max_iters = c->max_iters;
     P.cn_cells = c->cn_cells;
     P.waves = c->waves;
+    P.mc_small_nbr = c->mc_small_nbr;
     set_grid_cap(c->blocks_per_sm);
     P.stats = c->collect_stats;
     P.box = fp32_all && c->cell_bounds ? 1 : 0;
@@ -779,27 +795,28 @@ dbscan_status dbscan_run_batch(dbscan_ctx *c, const dbscan_instance *hi, int cou
     P.cell_inst = c->cell_inst;
     c->stats.precision = fp32_all ? DBSCAN_PREC_FP32_RECHECK : DBSCAN_PREC_FP64;
     c->stats.key_bits = 63;
-    c->stats.radix_passes = 4;
+    c->stats.radix_passes = 8;
     const long long launches0 = g_launches;
     if (!c->table_clean) {
         CK(cudaMemsetAsync(c->ht, 0xff, sizeof(ulonglong2) * c->hcap, s));
         CK(cudaMemsetAsync(c->hcnt, 0, sizeof(unsigned) * c->hcap, s));
         c->table_clean = true;
     }
-    // The cell sort orders by the top 32 key bits (instance, then coarse Z
-    // order): enough for locality; the grouping itself is exact.
+    // The cell sort orders by all 63 key bits: instance, then Z order inside
+    // it.  (An instance's Morton code occupies only the low d * bits, so a sort
+    // of the top bits alone would leave each instance's cells unordered.)
     auto enqueue = [&]() -> dbscan_status {
         if (c->phase_timing) cudaEventRecord(c->ev[0], s);
         if (c->phase_timing) cudaEventRecord(c->ev[1], s);
         dbscan_status e = gbdb_enqueue_batch_prologue(c, d_points, ld, dtype, count, total, fp32_all ? 1 : 0,
                                                       P.inst_shift, s);
         if (e != DBSCAN_OK) return e;
-        return enqueue_core(c, P, D, SD, mode, d_points, dtype, ld, 31, 32, d_core, d_labels, d_border_offsets, s,
+        return enqueue_core(c, P, D, SD, mode, d_points, dtype, ld, 0, 63, d_core, d_labels, d_border_offsets, s,
                             [&](int k) {
                                 if (c->phase_timing) cudaEventRecord(c->ev[k], s);
                             });
     };
-    const unsigned long long key[12] = {(unsigned long long)count, (unsigned long long)total,
+    const unsigned long long key[13] = {(unsigned long long)count, (unsigned long long)total,
                                         (unsigned long long)(uintptr_t)d_points, (unsigned long long)ld,
                                         (unsigned long long)dtype, (unsigned long long)(uintptr_t)d_core,
                                         (unsigned long long)(uintptr_t)d_labels,
@@ -807,6 +824,7 @@ dbscan_status dbscan_run_batch(dbscan_ctx *c, const dbscan_instance *hi, int cou
                                         (unsigned long long)(mode | (c->sched << 4) | (P.box << 8) | (P.stats << 9) |
                                                              ((c->log_cap > 0) << 10) | (c->cn_cells << 12) |
                                                              (c->waves << 20) | (c->blocks_per_sm << 24)),
+                                        (unsigned long long)c->mc_small_nbr,
                                         (unsigned long long)c->phase_timing, (unsigned long long)c->max_iters, 1ull};
     // phase timing records events between the steps: that run is enqueued
     // directly instead of replaying the graph

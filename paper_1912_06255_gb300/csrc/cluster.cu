@@ -30,6 +30,16 @@ __device__ __forceinline__ void flush_counter(unsigned long long *dst, unsigned 
 // and adds the vote count.  The lanes stay converged, the loads coalesce, and
 // the cell stops once all its points reached minPts.
 constexpr int MC_THREADS = 256, MC_WARPS = MC_THREADS / 32, MC_OWN = 128;
+// Sparse cells with fewer points than MC_SMALL and at most P.mc_small_nbr
+// points in their neighbouring cells (0: none) go to k_markcore_small (one
+// thread per point): a warp per cell would leave most of its lanes idle, and a
+// thread's serial scan stays short.  The autotuner picks the limit.
+constexpr int MC_SMALL = 8;
+constexpr int MC_SMALL_ALL = 1 << 30;  // no neighbourhood limit (nbr_pts is then not computed)
+__device__ __forceinline__ bool mc_small(const RunParams &P, int k, const int *nbr_pts, int c) {
+    if (P.mc_small_nbr <= 0 || k >= MC_SMALL) return false;  // 0: the warp kernel takes all
+    return P.mc_small_nbr >= MC_SMALL_ALL || nbr_pts[c] <= P.mc_small_nbr;
+}
 
 // One batch of kb <= 32*NS own points of a sparse cell whose k points start at
 // s0 (the batch starts at own index b0); own[] holds the batch.
@@ -128,11 +138,12 @@ __device__ __forceinline__ void mc_batch(const RunParams &P, const Thr &T, const
 }
 
 template <int D, int M>
-__global__ void __launch_bounds__(MC_THREADS)
+__global__ void __launch_bounds__(MC_THREADS, 4)  // 32 warps per SM (measured faster than 24)
 k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__ pd,
            const int *__restrict__ cell_start, const int *__restrict__ nbr_cnt, const int *__restrict__ nbr,
-           int stride, const long long *__restrict__ nbr_off, const float4 *__restrict__ blo,
-           const float4 *__restrict__ bhi, int *__restrict__ core_s, DevCounters *ctr) {
+           int stride, const long long *__restrict__ nbr_off, const int *__restrict__ nbr_pts,
+           const float4 *__restrict__ blo, const float4 *__restrict__ bhi, int *__restrict__ core_s,
+           DevCounters *ctr) {
     constexpr int OWN = D == 8 ? 64 : MC_OWN;  // 8-wide points: at most two slots in registers
     __shared__ Pt<D, M> own[MC_WARPS][OWN];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -146,6 +157,7 @@ k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__
             for (int i = lane; i < k; i += 32) core_s[s0 + i] = 1;
             continue;
         }
+        if (mc_small(P, k, nbr_pts, c)) continue;  // k_markcore_small
         const int ne = nbr_cnt[c];
         const int *nl = nbr_list<D>(nbr, nbr_off, stride, c);
         if (P.stats) {
@@ -176,12 +188,77 @@ k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__
     }
 }
 
+// MarkCore for the points of sparse cells with fewer than MC_SMALL points and
+// at most P.mc_small_nbr points in their neighbouring cells: each thread counts
+// for one point, walking its cell's neighbour list with the same per-point box
+// classification and early exit as the warp kernel.  Consecutive threads hold
+// consecutive points in cell order, so the threads of one cell read the same
+// neighbour entries.  Pays off on sparse inputs (a few points per cell).
+template <int D, int M>
+__global__ void __launch_bounds__(256)
+k_markcore_small(RunParams P, const float *__restrict__ pf, const double *__restrict__ pd,
+                 const int *__restrict__ cell_of, const int *__restrict__ cell_start, const int *__restrict__ nbr_cnt,
+                 const int *__restrict__ nbr, int stride, const long long *__restrict__ nbr_off,
+                 const int *__restrict__ nbr_pts, const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
+                 int *__restrict__ core_s, DevCounters *ctr) {
+    constexpr bool BOX = (M == kF32FromF32 || M == kF32FromF64);
+    const bool use_box = BOX && P.box;
+    unsigned rech = 0;
+    unsigned long long evals = 0, mc_bound = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+        const int c = cell_of[i];
+        const int s0 = cell_start[c], k = cell_start[c + 1] - s0;
+        const Thr T = P.inst[inst_of_cell(P, c)].thr;
+        if (k >= T.min_pts || !mc_small(P, k, nbr_pts, c)) continue;  // dense, or the warp kernel's
+        Pt<D, M> p;
+        load_pt(p, pf, pd, i);
+        int cnt = k;
+        const int ne = nbr_cnt[c];
+        const int *nl = nbr_list<D>(nbr, nbr_off, stride, c);
+        if (P.stats)
+            for (int e = 0; e < ne; ++e) mc_bound += cell_start[nl[e] + 1] - cell_start[nl[e]];
+        for (int e = 0; e < ne && cnt < T.min_pts; ++e) {
+            const int h = nl[e];
+            const int t0 = cell_start[h], t1 = cell_start[h + 1];
+            if constexpr (BOX) {
+                if (use_box) {
+                    const Bx<D> lo = load_box<D>(blo, h), hi = load_box<D>(bhi, h);
+                    if (box_max_d2<D>(p.f, lo, hi) <= T.lo) {
+                        cnt += t1 - t0;
+                        continue;
+                    }
+                    if (box_min_d2<D>(p.f, lo, hi) > T.hi) continue;
+                }
+            }
+            for (int t = t0; t < t1 && cnt < T.min_pts; ++t) {
+                Pt<D, M> q;
+                load_pt(q, pf, pd, t);
+                if (P.stats) ++evals;
+                if (within(p, q, T, pd, i, pd, t, rech)) ++cnt;
+            }
+        }
+        core_s[i] = cnt >= T.min_pts ? 1 : 0;
+    }
+    flush_counter(&ctr->band_rechecks, rech);
+    if (P.stats) {
+        flush_counter(&ctr->dist_evals[0], evals);
+        flush_counter(&ctr->mc_bound, mc_bound);
+    }
+}
+
 void launch_markcore(int D, int mode, const RunParams &P, const Bufs &B, DevCounters *ctr, cudaStream_t s) {
+    if (P.mc_small_nbr > 0) GBDB_DISPATCH(D, mode, {
+        auto ks = k_markcore_small<DD, MM>;
+        const int gs = grid_for((const void *)ks, 256);
+        ks<<<gs, 256, 0, s>>>(P, B.pf, B.pd, B.cell_of, B.cell_start, B.nbr_cnt, B.nbr, B.nbr_stride, B.nbr_off,
+                              B.nbr_pts, B.blo, B.bhi, B.core_s, ctr);
+        count_launch();
+    });
     GBDB_DISPATCH(D, mode, {
         auto k = k_markcore<DD, MM>;
         int g = grid_for((const void *)k, MC_THREADS);
         k<<<g, MC_THREADS, 0, s>>>(P, B.pf, B.pd, B.cell_start, B.nbr_cnt, B.nbr, B.nbr_stride, B.nbr_off,
-                                   B.blo, B.bhi, B.core_s, ctr);
+                                   B.nbr_pts, B.blo, B.bhi, B.core_s, ctr);
         count_launch();
     });
 }
@@ -295,7 +372,7 @@ const uint32_t *launch_schedule(int sched, const RunParams &P, const Bufs &B, De
 // Connectivity Queries").  A hit links the two cells.
 
 template <int D, int M, int WAVE>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 4)  // 64 registers: 32 warps per SM hide the union-find latency
 k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict__ rank,
           const int *__restrict__ ccs, const int *__restrict__ nbr_cnt, const int *__restrict__ nbr_near,
           const int *__restrict__ nbr, int stride, const long long *__restrict__ nbr_off,

@@ -32,6 +32,7 @@ struct dbscan_ctx {
     int cn_cells = 4;       // DBSCAN_OPT_CONNECT_CELLS
     int waves = 2;          // DBSCAN_OPT_CONNECT_WAVES
     int blocks_per_sm = 0;  // DBSCAN_OPT_BLOCKS_PER_SM
+    int mc_small_nbr = 0;   // DBSCAN_OPT_SMALL_CELLS
     cudaEvent_t ev[9] = {};
     // workspace
     void *arena = nullptr;
@@ -68,7 +69,7 @@ struct dbscan_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t cap_stream = nullptr;
     long long graph_launches = 0;  // kernel nodes of the captured graph
-    unsigned long long graph_key[12] = {0};
+    unsigned long long graph_key[13] = {0};
     float4 *blo = nullptr, *bhi = nullptr, *cblo = nullptr, *cbhi = nullptr;  // cell / core-point boxes
     float4 *ccent = nullptr;  // core-point centroids (learned schedule)
     // learned schedule: network (device), its Adam state, pair list, pair log
@@ -87,6 +88,9 @@ struct dbscan_ctx {
     long long *bbox_out = nullptr;  // [2*kMaxDim + 1], see launch_bbox
     signed char *offs = nullptr;  // [kMaxEnumDim][kMaxOffsets][kMaxEnumDim]
     int noff[gbdb::kMaxEnumDim + 1] = {0};
+    int *nbr_pts = nullptr;     // points in all neighbouring cells, per cell
+    unsigned *bloom = nullptr;  // Bloom filter of the cell keys of a hashed run (d <= 4)
+    int bloom_lg = 10;
     // 5 <= d <= 8: cells, tree and CSR neighbour lists (allocated at the first such run)
     gbdb::HdBufs hd{};
     void *hd_arena = nullptr;

@@ -302,6 +302,26 @@ __device__ __forceinline__ uint64_t hash_slot(uint64_t k, int lg) {
     return (k * 0x9e3779b97f4a7c15ull) >> (64 - lg);
 }
 
+// Bloom filter of the non-empty cells (two bits per key in a table of 2^lg
+// bits), kept in L2: probes for empty neighbouring cells stop here instead of
+// reaching the hash table.
+__device__ __forceinline__ void bloom_bits(uint64_t k, int lg, uint64_t &b0, uint64_t &b1) {
+    const uint64_t h = k * 0xd6e8feb86659fd93ull;
+    b0 = h >> (64 - lg);
+    b1 = (h * 0x9e3779b97f4a7c15ull + 0x632be59bd9b4e019ull) >> (64 - lg);
+}
+__device__ __forceinline__ void bloom_add(unsigned *bloom, uint64_t k, int lg) {
+    uint64_t b0, b1;
+    bloom_bits(k, lg, b0, b1);
+    atomicOr(bloom + (b0 >> 5), 1u << (b0 & 31));
+    atomicOr(bloom + (b1 >> 5), 1u << (b1 & 31));
+}
+__device__ __forceinline__ bool bloom_may_have(const unsigned *__restrict__ bloom, uint64_t k, int lg) {
+    uint64_t b0, b1;
+    bloom_bits(k, lg, b0, b1);
+    return ((bloom[b0 >> 5] >> (b0 & 31)) & 1u) && ((bloom[b1 >> 5] >> (b1 & 31)) & 1u);
+}
+
 // A slot is 16 bytes: .x the key (kEmptyKey when free), .y the cell id, so a
 // probe is one load.
 __device__ __forceinline__ int hash_find(const ulonglong2 *__restrict__ ht, uint64_t key, uint64_t mask, int lg) {

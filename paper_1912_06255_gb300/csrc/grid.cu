@@ -144,7 +144,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_insert(const T *__restrict__ X, RunParams P, ulonglong2 *__restrict__ ht, unsigned *__restrict__ hcnt,
          uint64_t hmask, int hlg, uint32_t *__restrict__ slot_of, uint32_t *__restrict__ rank_of,
-         uint32_t *__restrict__ slots, DevCounters *ctr) {
+         uint32_t *__restrict__ slots, unsigned *__restrict__ bloom, int blg, DevCounters *ctr) {
     const int T_ = gridDim.x * blockDim.x;
     for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < P.n; i0 += T_ * INS_U) {
         uint64_t key[INS_U], s[INS_U];
@@ -179,6 +179,7 @@ k_insert(const T *__restrict__ X, RunParams P, ulonglong2 *__restrict__ ht, unsi
                     cur[u] = atomicCAS(&ht[s[u]].x, (unsigned long long)kEmptyKey, (unsigned long long)key[u]);
                     if (cur[u] == kEmptyKey) {
                         slots[atomicAdd(&ctr->m, 1)] = (uint32_t)s[u];  // a new non-empty cell
+                        if (bloom) bloom_add(bloom, key[u], blg);
                         ok = true;
                         break;
                     }
@@ -295,11 +296,11 @@ void launch_semisort(const void *X, int dtype, const RunParams &P, int SD, const
     if (dtype == DBSCAN_F32) {
         int g = grid_for((const void *)k_insert<float>, 256);
         k_insert<float><<<g, 256, 0, s>>>((const float *)X, P, S.ht, S.hcnt, hmask, lg, S.slot_of, S.rank_of,
-                                          S.slots, ctr);
+                                          S.slots, S.bloom, S.bloom_lg, ctr);
     } else {
         int g = grid_for((const void *)k_insert<double>, 256);
         k_insert<double><<<g, 256, 0, s>>>((const double *)X, P, S.ht, S.hcnt, hmask, lg, S.slot_of, S.rank_of,
-                                           S.slots, ctr);
+                                           S.slots, S.bloom, S.bloom_lg, ctr);
     }
     count_launch();
     int g = grid_for((const void *)k_cell_keys, 256);
@@ -418,6 +419,8 @@ constexpr int NB_U = 4;
 template <int D>
 __global__ void __launch_bounds__(256)
 k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict__ ht, uint64_t mask, int lg,
+            const unsigned *__restrict__ bloom, int blg, const int *__restrict__ cell_start,
+            int *__restrict__ nbr_pts,
             RunParams P,
             const signed char *__restrict__ offs, int noff, int n_near, const float4 *__restrict__ blo,
             const float4 *__restrict__ bhi, int *__restrict__ nbr_cnt, int *__restrict__ nbr_near,
@@ -442,7 +445,7 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
         Bx<D> clo = zero_box<D>(), chi = clo;
         if (P.box) { clo = load_box<D>(blo, c); chi = load_box<D>(bhi, c); }
         const float hi_thr = I.thr.hi;
-        int cnt = 0, near = 0;
+        int cnt = 0, near = 0, pts = 0;
         for (int o0 = 0; o0 < noff; o0 += 32 * NB_U) {
             uint64_t key[NB_U], slot[NB_U];
             bool act[NB_U];
@@ -463,6 +466,7 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
                     if (act[u]) {
                         if constexpr (D == 2 || D == 3) key[u] = morton_offset<D>(ckey, dl) | ibits;
                         else key[u] = morton_encode(nc, D, I.bits) | ibits;
+                        if (bloom) act[u] = bloom_may_have(bloom, key[u], blg);  // most offsets hold no cell
                         slot[u] = hash_slot(key[u], lg);
                     }
                 }
@@ -486,27 +490,38 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
                         h = -1;
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, h >= 0);
-                if (h >= 0) nbr[base + cnt + __popc(bal & lt)] = h;
+                if (h >= 0) {
+                    nbr[base + cnt + __popc(bal & lt)] = h;
+                    if (nbr_pts) pts += cell_start[h + 1] - cell_start[h];
+                }
                 cnt += __popc(bal);
                 const int o_first = o0 + u * 32;
                 if (o_first < n_near)
                     near += __popc(bal & (n_near - o_first >= 32 ? 0xffffffffu : ((1u << (n_near - o_first)) - 1u)));
             }
         }
-        if (lane == 0) { nbr_cnt[c] = cnt; nbr_near[c] = near; }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pts += __shfl_xor_sync(0xffffffffu, pts, o);
+        if (lane == 0) {
+            nbr_cnt[c] = cnt;
+            nbr_near[c] = near;
+            if (nbr_pts) nbr_pts[c] = pts;
+        }
         total += cnt;
     }
     if (lane == 0 && total) atomicAdd((unsigned long long *)&ctr->E, (unsigned long long)total);
 }
 
-void launch_neighbors(const uint64_t *cell_key, const ulonglong2 *ht, uint64_t hcap, const RunParams &P,
-                      const signed char *offs, int noff, int n_near, const float4 *blo, const float4 *bhi,
-                      int *nbr_cnt, int *nbr_near, int *nbr, DevCounters *ctr, cudaStream_t s) {
+void launch_neighbors(const uint64_t *cell_key, const ulonglong2 *ht, uint64_t hcap, const unsigned *bloom,
+                      int bloom_lg, const RunParams &P, const signed char *offs, int noff, int n_near,
+                      const float4 *blo, const float4 *bhi, const int *cell_start, int *nbr_cnt, int *nbr_near,
+                      int *nbr_pts, int *nbr, DevCounters *ctr, cudaStream_t s) {
     const uint64_t mask = hcap - 1;
     const int lg = hash_log2(hcap);
     auto go = [&](auto k) {
         int g = grid_for((const void *)k, 256);
-        k<<<g, 256, 0, s>>>(cell_key, ht, mask, lg, P, offs, noff, n_near, blo, bhi, nbr_cnt, nbr_near, nbr, ctr);
+        k<<<g, 256, 0, s>>>(cell_key, ht, mask, lg, bloom, bloom_lg, cell_start, nbr_pts, P, offs, noff, n_near,
+                            blo, bhi, nbr_cnt, nbr_near, nbr, ctr);
         count_launch();
     };
     switch (P.d) {

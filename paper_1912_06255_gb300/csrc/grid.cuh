@@ -36,6 +36,8 @@ struct Semisort {
     int *orig, *cell_of;
     int *cell_inst;       // [m] instance of each cell (several instances only)
     int key_lo, key_bits; // key bits the cell sort orders by
+    unsigned *bloom;      // 2^bloom_lg bits: Bloom filter of the run's cell keys (cleared per run)
+    int bloom_lg;
 };
 // Group the points by cell: fills cell_key, cell_start, pf/pd, orig, cell_of,
 // ctr->m, and the slots' cell ids.
@@ -43,9 +45,16 @@ void launch_semisort(const void *X, int dtype, const RunParams &P, int SD, const
                      cudaStream_t s);
 // Empty the slots the run used (keeps the table clean for the next run).
 void launch_table_reset(const Semisort &S, DevCounters *ctr, cudaStream_t s);
-void launch_neighbors(const uint64_t *cell_key, const ulonglong2 *ht, uint64_t hcap, const RunParams &P,
-                      const signed char *offs, int noff, int n_near, const float4 *blo, const float4 *bhi,
-                      int *nbr_cnt, int *nbr_near, int *nbr, DevCounters *ctr, cudaStream_t s);
+void launch_neighbors(const uint64_t *cell_key, const ulonglong2 *ht, uint64_t hcap, const unsigned *bloom,
+                      int bloom_lg, const RunParams &P, const signed char *offs, int noff, int n_near,
+                      const float4 *blo, const float4 *bhi, const int *cell_start, int *nbr_cnt, int *nbr_near,
+                      int *nbr_pts, int *nbr, DevCounters *ctr, cudaStream_t s);
+// log2 of the Bloom filter's bit count for max_points points (4 to 8 bits per point)
+inline int bloom_log2(long long max_points) {
+    int lg = 10;
+    while ((1ll << lg) < 4 * max_points) ++lg;
+    return lg;
+}
 // per-cell FP32 bounding boxes of pts[start[c] .. start[c+1]) (and the
 // centroids when cent is not null)
 void launch_boxes(int SD, const float *pts, const int *start, const DevCounters *ctr, float4 *lo, float4 *hi,
@@ -62,6 +71,7 @@ struct Bufs {
     const int *nbr;
     int nbr_stride;
     const long long *nbr_off;  // [m] CSR offsets of the lists (d >= 5); null: fixed stride
+    const int *nbr_pts;        // [m] points in all neighbouring cells of c
     // MarkCore / compaction
     int *core_s;        // [n] 0/1 in cell order
     int *core_pos;      // [n+1] exclusive scan of core_s

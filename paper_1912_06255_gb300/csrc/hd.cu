@@ -299,8 +299,9 @@ template <bool FILL>
 __global__ void __launch_bounds__(32 * QW)
 k_lbvh_query(RunParams P, const int2 *__restrict__ child, const int4 *__restrict__ nlo, const int4 *__restrict__ nhi,
              const float4 *__restrict__ nblo, const float4 *__restrict__ nbhi, const int4 *__restrict__ ccoord,
-             const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
-             int *__restrict__ nbr_cnt, int *__restrict__ nbr_near, long long *__restrict__ cnt64,
+             const float4 *__restrict__ blo, const float4 *__restrict__ bhi, const int *__restrict__ cell_start,
+             int *__restrict__ nbr_pts, int *__restrict__ nbr_cnt, int *__restrict__ nbr_near,
+             long long *__restrict__ cnt64,
              const long long *__restrict__ off, int *__restrict__ nbr, DevCounters *ctr) {
     __shared__ int stk[QW][kStack];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -319,7 +320,7 @@ k_lbvh_query(RunParams P, const int2 *__restrict__ child, const int4 *__restrict
         }
         Bx<8> glo = zero_box<8>(), ghi = glo;
         if (P.box && valid) { glo = load_box<8>(blo, g); ghi = load_box<8>(bhi, g); }
-        int n_near = 0, n_far = 0, near_at = 0, far_at = 0;
+        int n_near = 0, n_far = 0, near_at = 0, far_at = 0, pts = 0;
         long long base = 0;
         if (FILL && valid) {
             base = off[g];
@@ -372,6 +373,7 @@ k_lbvh_query(RunParams P, const int2 *__restrict__ child, const int4 *__restrict
                             if (FILL) nbr[base + far_at++] = h;
                             ++n_far;
                         }
+                        if (!FILL && nbr_pts) pts += cell_start[h + 1] - cell_start[h];
                     } else {
                         bool enter = valid && gap2(c, nlo[q], nhi[q], d) <= d;
                         if (enter && P.box)
@@ -392,6 +394,7 @@ k_lbvh_query(RunParams P, const int2 *__restrict__ child, const int4 *__restrict
         if (!FILL && valid) {
             nbr_cnt[g] = n_near + n_far;
             nbr_near[g] = n_near;
+            if (nbr_pts) nbr_pts[g] = pts;
             cnt64[g] = n_near + n_far;
             total += n_near + n_far;
         }
@@ -467,6 +470,9 @@ void hd_cells_and_counts(const void *X, int dtype, const RunParams &P, int key_b
         count_launch();
         g = grid_for((const void *)k_lbvh_query<false>, 32 * QW);
         k_lbvh_query<false><<<g, 32 * QW, 0, s>>>(P, H.child, H.nlo, H.nhi, H.nblo, H.nbhi, H.ccoord, B.blo, B.bhi,
+                                                  B.cell_start, P.mc_small_nbr > 0 && P.mc_small_nbr < (1 << 30)
+                                                                    ? const_cast<int *>(B.nbr_pts)
+                                                                    : nullptr,
                                               const_cast<int *>(B.nbr_cnt), const_cast<int *>(B.nbr_near), H.cnt64,
                                               nullptr, nullptr, ctr);
         count_launch();
@@ -478,6 +484,7 @@ void hd_cells_and_counts(const void *X, int dtype, const RunParams &P, int key_b
 void hd_fill(const RunParams &P, const HdBufs &H, const Bufs &B, int *nbr, DevCounters *ctr, cudaStream_t s) {
     const int g = grid_for((const void *)k_lbvh_query<true>, 32 * QW);
     k_lbvh_query<true><<<g, 32 * QW, 0, s>>>(P, H.child, H.nlo, H.nhi, H.nblo, H.nbhi, H.ccoord, B.blo, B.bhi,
+                                             B.cell_start, nullptr,
                                          const_cast<int *>(B.nbr_cnt), const_cast<int *>(B.nbr_near), nullptr,
                                          H.nbr_off, nbr, ctr);
     count_launch();

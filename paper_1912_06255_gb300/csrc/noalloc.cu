@@ -68,6 +68,7 @@ size_t carve(dbscan_ctx *c, unsigned char *base) {
     const int64_t npart = scan_partials(N + 1) + 2;
     const uint64_t hcap = hash_capacity((int)N);
     c->sort_scratch_size = sort_scratch_bytes(N);
+    c->bloom_lg = bloom_log2(N);
     struct Item { void **p; size_t bytes; };
     const Item items[] = {
         {(void **)&c->k0, 8 * (size_t)N}, {(void **)&c->k1, 8 * (size_t)N},
@@ -79,8 +80,9 @@ size_t carve(dbscan_ctx *c, unsigned char *base) {
         {(void **)&c->cpf, 4 * (size_t)N * SD}, {(void **)&c->cpd, 8 * (size_t)N * SD},
         {(void **)&c->orig, 4 * (size_t)N}, {(void **)&c->cell_of, 4 * (size_t)N},
         {(void **)&c->cell_start, 4 * (size_t)(N + 1)}, {(void **)&c->cell_key, 8 * (size_t)N},
-        {(void **)&c->ht, 16 * (size_t)hcap},
+        {(void **)&c->ht, 16 * (size_t)hcap}, {(void **)&c->bloom, ((size_t)1 << bloom_log2(N)) / 8},
         {(void **)&c->nbr_cnt, 4 * (size_t)(N + 1)}, {(void **)&c->nbr_near, 4 * (size_t)(N + 1)},
+        {(void **)&c->nbr_pts, 4 * (size_t)(N + 1)},
         {(void **)&c->nbr, 4 * (size_t)c->nbr_cap},
         {(void **)&c->core_s, 4 * (size_t)N}, {(void **)&c->core_pos, 4 * (size_t)(N + 1)},
         {(void **)&c->ccs, 4 * (size_t)(N + 1)}, {(void **)&c->core_orig, 4 * (size_t)N},

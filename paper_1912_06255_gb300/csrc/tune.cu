@@ -1,7 +1,7 @@
 // Autotuner of the run configuration: which pair schedule, whether cell boxes
 // decide pairs, one or two connectivity waves, core cells per work item of
-// the connectivity kernel and resident blocks per SM of the persistent
-// kernels.  It times candidate configurations on the caller's own input (the
+// the connectivity kernel, resident blocks per SM of the persistent kernels
+// and which sparse cells MarkCore counts with one thread per point.  It times candidate configurations on the caller's own input (the
 // result does not depend on any of them, only the time does) by coordinate
 // descent from the context's current setting, keeps the fastest and leaves
 // it set in the context.
@@ -29,6 +29,7 @@ dbscan_status tune(dbscan_ctx *c, int reps, dbscan_tuning *out, RunFn run_once) 
         {DBSCAN_OPT_CONNECT_WAVES, {2, 1}},
         {DBSCAN_OPT_CONNECT_CELLS, {1, 2, 4, 8}},
         {DBSCAN_OPT_BLOCKS_PER_SM, {0, 1, 2, 4}},
+        {DBSCAN_OPT_SMALL_CELLS, {0, 128, 1 << 30}},
     };
     if (c->precision != DBSCAN_PREC_FP32_RECHECK) knobs.erase(knobs.begin() + 1);  // boxes need the FP32 band
     std::vector<int64_t> cur(knobs.size());
@@ -84,6 +85,7 @@ dbscan_status tune(dbscan_ctx *c, int reps, dbscan_tuning *out, RunFn run_once) 
         dbscan_get_option(c, DBSCAN_OPT_CONNECT_WAVES, &v); out->connect_waves = (int32_t)v;
         dbscan_get_option(c, DBSCAN_OPT_CONNECT_CELLS, &v); out->connect_cells = (int32_t)v;
         dbscan_get_option(c, DBSCAN_OPT_BLOCKS_PER_SM, &v); out->blocks_per_sm = (int32_t)v;
+        dbscan_get_option(c, DBSCAN_OPT_SMALL_CELLS, &v); out->small_cells = (int32_t)v;
         out->trials = trials;
         out->best_ms = best_ms;
         out->default_ms = default_ms;
