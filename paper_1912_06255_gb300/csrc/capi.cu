@@ -301,8 +301,11 @@ static dbscan_status enqueue_hash_cells(dbscan_ctx *c, const RunParams &P, int S
     S.orig = c->orig;
     S.cell_of = c->cell_of;
     S.cell_inst = c->cell_inst;
-    S.key_lo = sort_lo;
-    S.key_bits = sort_bits;
+    // whole 8-bit digits only: the (at most 7) lowest key bits left out of the
+    // order only shuffle cells inside a block of 2^7 consecutive Z positions
+    const int whole = sort_bits >= 8 ? sort_bits & ~7 : sort_bits;
+    S.key_lo = sort_lo + (sort_bits - whole);
+    S.key_bits = whole;
     // the Bloom filter pays only when the hash table does not fit in L2
     const bool use_bloom = 16 * c->hcap > ((uint64_t)96 << 20);
     S.bloom = use_bloom ? c->bloom : nullptr;
@@ -719,7 +722,8 @@ dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, 
         P.lo = I.thr.lo;
         P.hi = I.thr.hi;
         c->stats.key_bits = d * I.bits;
-        c->stats.radix_passes = (d * I.bits + 7) / 8;
+        // d <= 4: the m cell keys, whole digits only; d >= 5: the n point keys
+        c->stats.radix_passes = d <= kMaxEnumDim ? std::max(1, d * I.bits / 8) : (d * I.bits + 7) / 8;
         const int mode_sel = fp32 ? (f64 ? kF32FromF64 : kF32FromF32) : (f64 ? kF64FromF64 : kF64FromF32);
         c->last_mode_sel = mode_sel;
     }
@@ -795,7 +799,7 @@ dbscan_status dbscan_run_batch(dbscan_ctx *c, const dbscan_instance *hi, int cou
     P.cell_inst = c->cell_inst;
     c->stats.precision = fp32_all ? DBSCAN_PREC_FP32_RECHECK : DBSCAN_PREC_FP64;
     c->stats.key_bits = 63;
-    c->stats.radix_passes = 8;
+    c->stats.radix_passes = 7;
     const long long launches0 = g_launches;
     if (!c->table_clean) {
         CK(cudaMemsetAsync(c->ht, 0xff, sizeof(ulonglong2) * c->hcap, s));
