@@ -91,7 +91,7 @@ class SingleInstance:
 
     def autotune(self, ctx, dev):
         T, X = self.heldout(dev)
-        return ctx.autotune(X, T.eps, T.min_pts, reps=2), T.name
+        return ctx.autotune(X, T.eps, T.min_pts, reps=3), T.name
 
     def cpu_sample(self):
         X = np.ascontiguousarray(self.I.points[self.I.points[:, 0] < self.SLAB])
@@ -207,7 +207,7 @@ class Batch256:
 
     def autotune(self, ctx, dev):
         X, inst, name = self.heldout(dev)
-        return ctx.autotune_batch(X, inst, reps=2), name
+        return ctx.autotune_batch(X, inst, reps=3), name
 
     def cpu_sample(self):
         order = sorted(range(len(self.B)), key=lambda i: len(self.B[i].points))

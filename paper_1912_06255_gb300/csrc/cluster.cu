@@ -49,7 +49,7 @@ __device__ __forceinline__ void mc_batch(const RunParams &P, const Thr &T, const
                                          const int *__restrict__ cell_start, const int *__restrict__ nl, int ne,
                                          const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
                                          const Pt<D, M> *own, int s0, int b0, int k, int kb, int *__restrict__ core_s,
-                                         unsigned &rech, unsigned long long &evals) {
+                                         Bx<D> (*sbox)[2], unsigned &rech, unsigned long long &evals) {
     constexpr bool BOX = (M == kF32FromF32 || M == kF32FromF64);
     const int lane = threadIdx.x & 31;
     const bool use_box = BOX && P.box;
@@ -71,14 +71,19 @@ __device__ __forceinline__ void mc_batch(const RunParams &P, const Thr &T, const
             h = nl[e0 + lane];
             h_t0 = cell_start[h];
             h_t1 = cell_start[h + 1];
+            // and stage its box, so the loop below reads it from shared memory
+            if (use_box) {
+                sbox[lane][0] = load_box<D>(blo, h);
+                sbox[lane][1] = load_box<D>(bhi, h);
+            }
         }
+        __syncwarp();
         const int ecount = min(32, ne - e0);
         for (int j = 0; j < ecount && !all; ++j) {
             const int t0 = __shfl_sync(0xffffffffu, h_t0, j), t1 = __shfl_sync(0xffffffffu, h_t1, j);
             unsigned part[NS];
             if (use_box) {
-                const int hj = __shfl_sync(0xffffffffu, h, j);
-                const Bx<D> lo = load_box<D>(blo, hj), hi = load_box<D>(bhi, hj);
+                const Bx<D> lo = sbox[j][0], hi = sbox[j][1];
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
                     bool partial = false;
@@ -129,6 +134,7 @@ __device__ __forceinline__ void mc_batch(const RunParams &P, const Thr &T, const
                 all = all && done[s] == 0xffffffffu;
             }
         }
+        __syncwarp();  // the stage is rewritten for the next 32 neighbours
     }
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
@@ -146,6 +152,7 @@ k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__
            DevCounters *ctr) {
     constexpr int OWN = D == 8 ? 64 : MC_OWN;  // 8-wide points: at most two slots in registers
     __shared__ Pt<D, M> own[MC_WARPS][OWN];
+    __shared__ Bx<D> sbox[MC_WARPS][32][2];  // boxes of the next 32 neighbouring cells
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int m = ctr->m;
     unsigned rech = 0;
@@ -173,12 +180,14 @@ k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__
             for (int i = lane; i < kb; i += 32) load_pt(own[w][i], pf, pd, s0 + b0 + i);
             __syncwarp();
             if (kb <= 32)
-                mc_batch<D, M, 1>(P, T, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, rech, evals);
+                mc_batch<D, M, 1>(P, T, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, sbox[w], rech,
+                                  evals);
             else if (OWN <= 64 || kb <= 64)
-                mc_batch<D, M, 2>(P, T, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, rech, evals);
+                mc_batch<D, M, 2>(P, T, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, sbox[w], rech,
+                                  evals);
             else
                 mc_batch<D, M, (OWN > 64 ? 4 : 2)>(P, T, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb,
-                                                   core_s, rech, evals);
+                                                   core_s, sbox[w], rech, evals);
         }
     }
     flush_counter(&ctr->band_rechecks, rech);
