@@ -167,10 +167,11 @@ static Learned learned_state(dbscan_ctx *c) {
     return L;
 }
 
-// Pair list of the learned schedule: 16 pairs per point of capacity.
-static cudaError_t ensure_learned(dbscan_ctx *c) {
+// Pair list of the learned schedule: 16 pairs per point of capacity at first
+// (grown by grow_learned when a run needs more).
+static cudaError_t ensure_learned(dbscan_ctx *c, long long want = 0) {
     if (c->lpairs) return cudaSuccess;
-    const long long cap = 16 * std::max<int64_t>(c->max_points, 1);
+    const long long cap = want > 0 ? want : 16 * std::max<int64_t>(c->max_points, 1);
     cudaError_t e = cudaMalloc((void **)&c->lpairs, sizeof(int2) * cap);
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->lk0, sizeof(uint64_t) * cap);
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->lk1, sizeof(uint64_t) * cap);
@@ -650,9 +651,9 @@ dbscan_status dbscan_get_stats(const dbscan_ctx *c, dbscan_stats *out) {
 }
 
 
-dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, int dtype, double eps,
-                         int64_t min_pts, uint8_t *d_core, int32_t *d_labels, int64_t *d_border_offsets,
-                         int64_t *num_border_memberships, void *stream) {
+static dbscan_status run_once(dbscan_ctx *c, const void *d_points, int64_t n, int d, int dtype, double eps,
+                              int64_t min_pts, uint8_t *d_core, int32_t *d_labels, int64_t *d_border_offsets,
+                              int64_t *num_border_memberships, void *stream) {
     if (!c) return DBSCAN_ERR_INVALID_ARG;
     c->have_run = false;
     if (num_border_memberships) *num_border_memberships = 0;
@@ -743,7 +744,7 @@ dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, 
     return finish_run(c, P, D, mode, d_points, dtype, n, num_border_memberships, launches0);
 }
 
-dbscan_status dbscan_run_batch(dbscan_ctx *c, const dbscan_instance *hi, int count, const void *d_points, int ld,
+static dbscan_status run_batch_once(dbscan_ctx *c, const dbscan_instance *hi, int count, const void *d_points, int ld,
                                int dtype, uint8_t *d_core, int32_t *d_labels, int64_t *d_border_offsets,
                                int64_t *num_border_memberships, void *stream) {
     if (!c || !hi || count < 1) return DBSCAN_ERR_INVALID_ARG;
@@ -828,7 +829,7 @@ dbscan_status dbscan_run_batch(dbscan_ctx *c, const dbscan_instance *hi, int cou
                                         (unsigned long long)(mode | (c->sched << 4) | (P.box << 8) | (P.stats << 9) |
                                                              ((c->log_cap > 0) << 10) | (c->cn_cells << 12) |
                                                              (c->waves << 20) | (c->blocks_per_sm << 24)),
-                                        (unsigned long long)c->mc_small_nbr,
+                                        (unsigned long long)c->mc_small_nbr ^ ((unsigned long long)c->lcap << 31),
                                         (unsigned long long)c->phase_timing, (unsigned long long)c->max_iters, 1ull};
     // phase timing records events between the steps: that run is enqueued
     // directly instead of replaying the graph
@@ -868,6 +869,45 @@ dbscan_status dbscan_run_batch(dbscan_ctx *c, const dbscan_instance *hi, int cou
     }
     CK(cudaStreamSynchronize(s));
     return finish_run(c, P, D, mode, d_points, dtype, total, num_border_memberships, launches0);
+}
+
+// The learned schedule's pair list starts at 16 pairs per point; a run that
+// needs more reports CAPACITY with the demand, the list grows, and the run is
+// repeated once.
+static bool grow_learned(dbscan_ctx *c) {
+    if (!(c->h_ctr->err == DBSCAN_ERR_CAPACITY && c->h_ctr->err_info == 50)) return false;
+    const long long want = std::max<long long>(2 * c->lcap, (long long)c->h_ctr->P_demand * 5 / 4 + 1024);
+    cudaFree(c->lpairs);
+    cudaFree(c->lk0);
+    cudaFree(c->lk1);
+    cudaFree(c->lscratch);
+    c->lpairs = nullptr;
+    c->lk0 = c->lk1 = nullptr;
+    c->lscratch = nullptr;
+    c->lcap = 0;
+    return ensure_learned(c, want) == cudaSuccess;
+}
+
+dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, int dtype, double eps,
+                         int64_t min_pts, uint8_t *d_core, int32_t *d_labels, int64_t *d_border_offsets,
+                         int64_t *num_border_memberships, void *stream) {
+    dbscan_status st = run_once(c, d_points, n, d, dtype, eps, min_pts, d_core, d_labels, d_border_offsets,
+                                num_border_memberships, stream);
+    if (st == DBSCAN_ERR_CAPACITY && grow_learned(c))
+        st = run_once(c, d_points, n, d, dtype, eps, min_pts, d_core, d_labels, d_border_offsets,
+                      num_border_memberships, stream);
+    return st;
+}
+
+dbscan_status dbscan_run_batch(dbscan_ctx *c, const dbscan_instance *hi, int count, const void *d_points, int ld,
+                               int dtype, uint8_t *d_core, int32_t *d_labels, int64_t *d_border_offsets,
+                               int64_t *num_border_memberships, void *stream) {
+    dbscan_status st = run_batch_once(c, hi, count, d_points, ld, dtype, d_core, d_labels, d_border_offsets,
+                                      num_border_memberships, stream);
+    if (st == DBSCAN_ERR_CAPACITY && grow_learned(c))
+        st = run_batch_once(c, hi, count, d_points, ld, dtype, d_core, d_labels, d_border_offsets,
+                            num_border_memberships, stream);
+    return st;
 }
 
 dbscan_status dbscan_train_scheduler(dbscan_ctx *c, int epochs, int batch, float lr, uint64_t seed, float *h_losses) {

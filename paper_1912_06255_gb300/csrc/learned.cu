@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(256) k_uf_reset(int *parent, uint64_t *best, c
 
 // Clamp the pair count to the list capacity (the overflow is already an error).
 __global__ void k_clamp_pairs(DevCounters *ctr, long long cap) {
+    ctr->P_demand = ctr->P_list;
     if (ctr->P_list > cap) ctr->P_list = (int)cap;
 }
 

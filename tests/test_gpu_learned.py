@@ -102,3 +102,16 @@ def test_learned_schedule_other_dims(d):
     ctx = DBSCAN(len(X), d, precision="fp64", schedule="learned")
     for eps, mp in ((0.2, 6), (0.45, 25)):
         _check(ctx, X, eps, mp)
+
+
+def test_pair_list_grows_when_needed():
+    """More undecided pairs than the initial 16 per point: the list grows and
+    the run is repeated, with the same exact result."""
+    rng = np.random.default_rng(17)
+    X = (rng.random((20000, 3)) * 27.0).astype(np.float32)  # about one point per cell of side eps/sqrt(3)
+    eps, mp = 1.0 * np.sqrt(3.0), 2
+    ctx = DBSCAN(len(X), 3, schedule="learned", cell_bounds=False)
+    st = _check(ctx, X, eps, mp)
+    assert st["num_pairs_listed"] > 16 * len(X)
+    st2 = _check(ctx, X, eps, mp)  # the grown list is kept
+    assert st2["num_pairs_listed"] == st["num_pairs_listed"]
