@@ -152,6 +152,10 @@ typedef struct {
        cells with fewer than minPts points of |g| times the points of all their
        neighbouring cells, the distance tests a scan without early exit makes. */
     int64_t markcore_pair_bound;
+    /* Pair schedule the run used: the context's, or DBSCAN_SCHED_SIZE when the
+       learned schedule's pair list would exceed 2^31 pairs (its fallback). */
+    int32_t schedule_used;
+    int32_t reserved;
 } dbscan_stats;
 
 /*

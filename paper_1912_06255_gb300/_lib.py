@@ -45,6 +45,7 @@ class Stats(ctypes.Structure):
         ("distance_evals", ctypes.c_int64), ("distance_evals_phase", ctypes.c_int64 * 3), ("band_lo", ctypes.c_float), ("band_hi", ctypes.c_float),
         ("kernel_launches", ctypes.c_int64), ("phase_ms", ctypes.c_float * 8),
         ("markcore_pair_bound", ctypes.c_int64),
+        ("schedule_used", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

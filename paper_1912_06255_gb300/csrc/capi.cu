@@ -664,6 +664,7 @@ static dbscan_status run_once(dbscan_ctx *c, const void *d_points, int64_t n, in
     if (n > 0 && (!d_points || !d_core || !d_labels)) return DBSCAN_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     std::memset(&c->stats, 0, sizeof(c->stats));
+    c->stats.schedule_used = c->sched;
     c->stats.n = n;
     c->stats.d = d;
     if (n == 0) {
@@ -767,6 +768,7 @@ static dbscan_status run_batch_once(dbscan_ctx *c, const dbscan_instance *hi, in
     if (total > 0 && (!d_points || !d_core || !d_labels)) return DBSCAN_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     std::memset(&c->stats, 0, sizeof(c->stats));
+    c->stats.schedule_used = c->sched;
     c->stats.n = total;
     c->stats.d = ld;
     if (total == 0) {
@@ -873,10 +875,17 @@ static dbscan_status run_batch_once(dbscan_ctx *c, const dbscan_instance *hi, in
 
 // The learned schedule's pair list starts at 16 pairs per point; a run that
 // needs more reports CAPACITY with the demand, the list grows, and the run is
-// repeated once.
+// repeated once.  A demand beyond 2^31 pairs (the pair sort's limit), or one
+// the device cannot hold, falls back to the size schedule for that call.
+static bool pair_list_full(const dbscan_ctx *c) {
+    return c->h_ctr->err == DBSCAN_ERR_CAPACITY && c->h_ctr->err_info == 50;
+}
+
 static bool grow_learned(dbscan_ctx *c) {
-    if (!(c->h_ctr->err == DBSCAN_ERR_CAPACITY && c->h_ctr->err_info == 50)) return false;
-    const long long want = std::max<long long>(2 * c->lcap, (long long)c->h_ctr->P_demand * 5 / 4 + 1024);
+    const unsigned long long demand = c->h_ctr->P_demand;
+    if (demand >= (1ull << 31) - 1024) return false;
+    const long long want = std::min<long long>(std::max<long long>(2 * c->lcap, (long long)(demand * 5 / 4) + 1024),
+                                               (1ll << 31) - 1);
     cudaFree(c->lpairs);
     cudaFree(c->lk0);
     cudaFree(c->lk1);
@@ -885,29 +894,51 @@ static bool grow_learned(dbscan_ctx *c) {
     c->lk0 = c->lk1 = nullptr;
     c->lscratch = nullptr;
     c->lcap = 0;
-    return ensure_learned(c, want) == cudaSuccess;
+    if (ensure_learned(c, want) == cudaSuccess) return true;
+    (void)cudaGetLastError();
+    return false;
 }
+
+// Runs fn; on a full pair list, grows it and runs again, else runs once more
+// with the size schedule.
+extern "C++" {
+template <typename Fn> dbscan_status with_pair_list_retry(dbscan_ctx *c, Fn fn) {
+    dbscan_status st = fn();
+    if (st != DBSCAN_ERR_CAPACITY || !pair_list_full(c)) return st;
+    if (grow_learned(c)) {
+        st = fn();
+        if (st != DBSCAN_ERR_CAPACITY || !pair_list_full(c)) return st;
+    }
+    const int sched = c->sched;
+    const long long log_cap = c->log_cap;
+    c->sched = DBSCAN_SCHED_SIZE;
+    c->log_cap = 0;  // a logging run needs the full list: this call logs nothing
+    st = fn();
+    c->sched = sched;
+    c->log_cap = log_cap;
+    c->stats.schedule_used = DBSCAN_SCHED_SIZE;
+    return st;
+}
+}  // extern "C++"
 
 dbscan_status dbscan_run(dbscan_ctx *c, const void *d_points, int64_t n, int d, int dtype, double eps,
                          int64_t min_pts, uint8_t *d_core, int32_t *d_labels, int64_t *d_border_offsets,
                          int64_t *num_border_memberships, void *stream) {
-    dbscan_status st = run_once(c, d_points, n, d, dtype, eps, min_pts, d_core, d_labels, d_border_offsets,
-                                num_border_memberships, stream);
-    if (st == DBSCAN_ERR_CAPACITY && grow_learned(c))
-        st = run_once(c, d_points, n, d, dtype, eps, min_pts, d_core, d_labels, d_border_offsets,
-                      num_border_memberships, stream);
-    return st;
+    if (!c) return DBSCAN_ERR_INVALID_ARG;
+    return with_pair_list_retry(c, [&]() {
+        return run_once(c, d_points, n, d, dtype, eps, min_pts, d_core, d_labels, d_border_offsets,
+                        num_border_memberships, stream);
+    });
 }
 
 dbscan_status dbscan_run_batch(dbscan_ctx *c, const dbscan_instance *hi, int count, const void *d_points, int ld,
                                int dtype, uint8_t *d_core, int32_t *d_labels, int64_t *d_border_offsets,
                                int64_t *num_border_memberships, void *stream) {
-    dbscan_status st = run_batch_once(c, hi, count, d_points, ld, dtype, d_core, d_labels, d_border_offsets,
-                                      num_border_memberships, stream);
-    if (st == DBSCAN_ERR_CAPACITY && grow_learned(c))
-        st = run_batch_once(c, hi, count, d_points, ld, dtype, d_core, d_labels, d_border_offsets,
-                            num_border_memberships, stream);
-    return st;
+    if (!c) return DBSCAN_ERR_INVALID_ARG;
+    return with_pair_list_retry(c, [&]() {
+        return run_batch_once(c, hi, count, d_points, ld, dtype, d_core, d_labels, d_border_offsets,
+                              num_border_memberships, stream);
+    });
 }
 
 dbscan_status dbscan_train_scheduler(dbscan_ctx *c, int epochs, int batch, float lr, uint64_t seed, float *h_losses) {

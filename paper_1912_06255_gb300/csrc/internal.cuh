@@ -27,7 +27,7 @@ struct DevCounters {
     int cell_next2;
     int P_list;      // undecided pairs listed by the learned schedule
     int P_pos;       // ... of which the network predicts connected
-    int P_demand;    // pairs the learned schedule tried to list (sizes a retry)
+    unsigned long long P_demand;  // pairs the learned schedule tried to list (sizes a retry)
     long long E;     // neighbour list entries
     long long P;     // candidate core-cell pairs
     long long K;     // border memberships

@@ -37,8 +37,8 @@ __global__ void __launch_bounds__(256) k_uf_reset(int *parent, uint64_t *best, c
 
 // Clamp the pair count to the list capacity (the overflow is already an error).
 __global__ void k_clamp_pairs(DevCounters *ctr, long long cap) {
-    ctr->P_demand = ctr->P_list;
-    if (ctr->P_list > cap) ctr->P_list = (int)cap;
+    const unsigned long long d = ctr->P_demand;
+    ctr->P_list = (int)(d < (unsigned long long)cap ? d : (unsigned long long)cap);
 }
 
 // ----------------------------------------------------------------- features
@@ -192,25 +192,31 @@ void mlp_adam(float *w, const float *g, float *m1, float *m2, float lr, int t, c
 
 // ----------------------------------------------------------------- pairs
 // Every pair of neighbouring core cells (a, b), a < b, once.  The core-point
-// boxes settle some outright (all pairs within eps: link; none: drop); the
-// rest are appended to the pair list.
-template <int D>
+// boxes settle some outright (all pairs within eps: link; none: drop).
+//   PASS 0: the box decisions only (links), before any listing;
+//   PASS 1: after compression, the undecided pairs whose cells union-find has
+//           not joined yet are appended to the pair list (the others count as
+//           skipped);
+//   PASS 2: the logging run: box decisions and every undecided pair listed,
+//           in one pass (nothing may be skipped there).
+template <int D, int PASS>
 __global__ void __launch_bounds__(256)
 k_collect_pairs(RunParams P, const int *__restrict__ ccs, const int *__restrict__ nbr_cnt,
                 const int *__restrict__ nbr, int stride, const long long *__restrict__ nbr_off,
                 const float4 *__restrict__ cblo,
                 const float4 *__restrict__ cbhi, int *parent, int2 *__restrict__ pairs, long long cap,
-                DevCounters *ctr) {
+                int count_cands, DevCounters *ctr) {
     const int m = ctr->m;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    unsigned long long cand_pairs = 0, boxed = 0, linked = 0;
+    unsigned long long cand_pairs = 0, boxed = 0, linked = 0, skipped = 0;
     for (int a = warp_id_global(); a < m; a += warps_global()) {
         if (ccs[a + 1] == ccs[a]) continue;
         const Thr T = P.inst[inst_of_cell(P, a)].thr;
         const Bx<D> alo = load_box<D>(cblo, a), ahi = load_box<D>(cbhi, a);
         const int ne = nbr_cnt[a];
         const int *nl = nbr_list<D>(nbr, nbr_off, stride, a);
+        int ra = PASS == 1 ? uf_find(parent, a, P.max_iters, ctr) : a;
         for (int e0 = 0; e0 < ne; e0 += 32) {
             const int e = e0 + lane;
             int b = 0;
@@ -225,26 +231,35 @@ k_collect_pairs(RunParams P, const int *__restrict__ ccs, const int *__restrict_
                     else if (boxes_max_d2<D>(alo, ahi, blo, bhi) <= T.lo) verdict = 1;
                 }
             }
-            if (cand && verdict > 0) uf_link(parent, a, b, P.max_iters, ctr);
-            const bool keep = cand && verdict == 0;
+            if (PASS != 1 && cand && verdict > 0) uf_link(parent, a, b, P.max_iters, ctr);
+            bool keep = PASS != 0 && cand && verdict == 0;
+            if (PASS == 1 && keep && uf_find(parent, b, P.max_iters, ctr) == ra) {
+                keep = false;
+                ++skipped;
+            }
             const unsigned bal = __ballot_sync(0xffffffffu, keep);
             long long at = 0;
-            if (lane == 0 && bal) at = (long long)atomicAdd(&ctr->P_list, (int)__popc(bal));
+            if (lane == 0 && bal) at = (long long)atomicAdd(&ctr->P_demand, (unsigned long long)__popc(bal));
             at = __shfl_sync(0xffffffffu, at, 0);
             if (keep) {
                 const long long k = at + __popc(bal & lt);
                 if (k < cap) pairs[k] = make_int2(a, b);
                 else set_error(ctr, DBSCAN_ERR_CAPACITY, 50);
             }
-            cand_pairs += __popc(__ballot_sync(0xffffffffu, cand));
-            boxed += __popc(__ballot_sync(0xffffffffu, cand && verdict != 0));
-            linked += __popc(__ballot_sync(0xffffffffu, cand && verdict > 0));
+            if (count_cands) {  // the run's first pass over the pairs
+                cand_pairs += __popc(__ballot_sync(0xffffffffu, cand));
+                boxed += __popc(__ballot_sync(0xffffffffu, cand && verdict != 0));
+                linked += __popc(__ballot_sync(0xffffffffu, cand && verdict > 0));
+            }
         }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) skipped += __shfl_xor_sync(0xffffffffu, skipped, o);
     if (lane == 0) {
         if (cand_pairs) atomicAdd((unsigned long long *)&ctr->P, cand_pairs);
         if (boxed) atomicAdd(&ctr->pairs_box, boxed);
         if (linked) atomicAdd(&ctr->pairs_linked, linked);
+        if (skipped) atomicAdd(&ctr->pairs_skipped, skipped);
     }
 }
 
@@ -398,21 +413,39 @@ void launch_connect_learned(int D, int mode, bool log, const RunParams &P, const
     unsigned long long *best = reinterpret_cast<unsigned long long *>(B.sk0);  // per cell, free in this schedule
     int g = grid_for((const void *)k_uf_reset, 256);
     k_uf_reset<<<g, 256, 0, s>>>(B.parent, B.sk0, ctr); count_launch();
+    int count_cands = 1;
     auto collect = [&](auto k) {
         const int gc = grid_for((const void *)k, 256);
         k<<<gc, 256, 0, s>>>(P, B.ccs, B.nbr_cnt, B.nbr, B.nbr_stride, B.nbr_off, B.cblo, B.cbhi, B.parent, L.pairs,
-                             L.cap, ctr);
+                             L.cap, count_cands, ctr);
         count_launch();
+        count_cands = 0;
     };
     auto score = [&](auto k) {
         const int gs = grid_for((const void *)k, 256);
         k<<<gs, 256, 0, s>>>(P, L.pairs, L.w, B.ccs, B.ccent, B.cblo, B.cbhi, L.k0, best, ctr);
         count_launch();
     };
-    if (D == 8) collect(k_collect_pairs<8>);
-    else if (D == 4) collect(k_collect_pairs<4>);
-    else if (D == 3) collect(k_collect_pairs<3>);
-    else collect(k_collect_pairs<2>);
+    if (log) {
+        // the logging run lists every undecided pair in one pass
+        if (D == 8) collect(k_collect_pairs<8, 2>);
+        else if (D == 4) collect(k_collect_pairs<4, 2>);
+        else if (D == 3) collect(k_collect_pairs<3, 2>);
+        else collect(k_collect_pairs<2, 2>);
+    } else {
+        // box decisions first, then only the pairs union-find has not joined
+        if (P.box) {
+            if (D == 8) collect(k_collect_pairs<8, 0>);
+            else if (D == 4) collect(k_collect_pairs<4, 0>);
+            else if (D == 3) collect(k_collect_pairs<3, 0>);
+            else collect(k_collect_pairs<2, 0>);
+            launch_uf_compress(B.parent, ctr, P.max_iters, s);
+        }
+        if (D == 8) collect(k_collect_pairs<8, 1>);
+        else if (D == 4) collect(k_collect_pairs<4, 1>);
+        else if (D == 3) collect(k_collect_pairs<3, 1>);
+        else collect(k_collect_pairs<2, 1>);
+    }
     k_clamp_pairs<<<1, 1, 0, s>>>(ctr, L.cap); count_launch();
     if (log) {
         GBDB_DISPATCH(D, mode, {

@@ -115,3 +115,4 @@ def test_pair_list_grows_when_needed():
     assert st["num_pairs_listed"] > 16 * len(X)
     st2 = _check(ctx, X, eps, mp)  # the grown list is kept
     assert st2["num_pairs_listed"] == st["num_pairs_listed"]
+
