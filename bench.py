@@ -310,8 +310,9 @@ def _peaks():
 # same command (dram__bytes_read.sum + dram__bytes_write.sum); None when the
 # kernel changed after the capture.  Keyed by (kernel, workload name).
 TRAFFIC = {
-    # profiles/k_markcore_k_connect_spreader3d_n2m.md (default setting, 2 connect waves)
-    ("k_markcore", "spreader3d-n2000000-eps100-minpts100-f32"): 50528768 + 206592,
+    # profiles/launches_spreader3d_n2m.md (the autotuned setting: one connect wave)
+    ("k_markcore", "spreader3d-n2000000-eps100-minpts100-f32"): 55463680 + 535552,
+    ("k_connect", "spreader3d-n2000000-eps100-minpts100-f32"): 49888512 + 56320,
 }
 
 

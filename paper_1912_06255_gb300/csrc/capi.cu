@@ -206,7 +206,8 @@ static cudaError_t ensure_hd(dbscan_ctx *c) {
         {(void **)&H.klo, 8 * N}, {(void **)&H.khi, 8 * N}, {(void **)&H.ckey_lo, 8 * N},
         {(void **)&H.ckey_hi, 8 * N}, {(void **)&H.ccoord, 16 * N}, {(void **)&H.child, 8 * N},
         {(void **)&H.parent, 4 * 2 * N}, {(void **)&H.flag, 4 * N}, {(void **)&H.nlo, 16 * N},
-        {(void **)&H.nhi, 16 * N}, {(void **)&H.cnt64, 8 * N}, {(void **)&H.nbr_off, 8 * (N + 1)},
+        {(void **)&H.nhi, 16 * N}, {(void **)&H.nbr_off, 8 * (N + 1)},
+        {(void **)&H.scratch, sizeof(int) * (size_t)hd_scratch_ints()},
         {(void **)&H.nblo, 32 * N}, {(void **)&H.nbhi, 32 * N},
     };
     size_t total = 0;
@@ -225,8 +226,9 @@ static cudaError_t ensure_hd(dbscan_ctx *c) {
 }
 
 // Steps 3-4 for 5 <= d <= 8: cells by a 128-bit key sort, the tree over the
-// cells, neighbour counts, one read-back of the total to size the lists, then
-// the lists themselves (CSR).  Synchronises the stream once.
+// cells, then the neighbour lists in one walk per 32 cells into the larger of
+// the arena's list buffer and the grown one.  One read-back checks the total:
+// if the lists did not fit, the buffer grows and the walk runs again.
 template <typename MarkFn>
 static dbscan_status enqueue_hd_cells(dbscan_ctx *c, const RunParams &P, const void *d_points, int dtype,
                                       int key_bits, cudaStream_t s, MarkFn mark) {
@@ -237,34 +239,35 @@ static dbscan_status enqueue_hd_cells(dbscan_ctx *c, const RunParams &P, const v
     Bufs B = make_bufs(c, dtype == DBSCAN_F64);
     B.n_max = P.n;
     mark(2);
-    hd_cells_and_counts(d_points, dtype, P, key_bits, c->hd, B, c->ctr, s);
-    CK(cudaGetLastError());
+    hd_cells(d_points, dtype, P, key_bits, c->hd, B, c->ctr, s);
     mark(3);
-    CK(cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (c->h_ctr->err) return (dbscan_status)c->h_ctr->err;
-    const long long E = c->h_ctr->E;
-    int *nbr = c->nbr;
-    if (E > c->nbr_cap) {
-        if (E > c->hd_nbr_cap) {
-            cudaFree(c->hd_nbr);
-            c->hd_nbr = nullptr;
-            c->hd_nbr_cap = 0;
-            const long long cap = E + E / 4;
-            if (cudaMalloc((void **)&c->hd_nbr, sizeof(int) * (size_t)cap) != cudaSuccess) {
-                (void)cudaGetLastError();
-                c->hd_nbr = nullptr;
-                return DBSCAN_ERR_OOM;
-            }
-            c->hd_nbr_cap = cap;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        int *nbr = c->hd_nbr_cap > c->nbr_cap ? c->hd_nbr : c->nbr;
+        const long long cap = c->hd_nbr_cap > c->nbr_cap ? c->hd_nbr_cap : c->nbr_cap;
+        CK(cudaMemsetAsync(&c->ctr->E, 0, sizeof(long long), s));
+        hd_neighbors(P, c->hd, B, nbr, cap, c->ctr, s);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (c->h_ctr->err) return (dbscan_status)c->h_ctr->err;
+        const long long E = c->h_ctr->E;
+        if (E <= cap) {
+            c->nbr_cur = nbr;
+            c->nbr_off_cur = c->hd.nbr_off;
+            return DBSCAN_OK;
         }
-        nbr = c->hd_nbr;
+        cudaFree(c->hd_nbr);
+        c->hd_nbr = nullptr;
+        c->hd_nbr_cap = 0;
+        const long long grown = E + E / 4;
+        if (cudaMalloc((void **)&c->hd_nbr, sizeof(int) * (size_t)grown) != cudaSuccess) {
+            (void)cudaGetLastError();
+            c->hd_nbr = nullptr;
+            return DBSCAN_ERR_OOM;
+        }
+        c->hd_nbr_cap = grown;
     }
-    hd_fill(P, c->hd, B, nbr, c->ctr, s);
-    CK(cudaGetLastError());
-    c->nbr_cur = nbr;
-    c->nbr_off_cur = c->hd.nbr_off;
-    return DBSCAN_OK;
+    return DBSCAN_ERR_CAPACITY;
 }
 
 // Steps 3-4 for d <= 4: cells by the hash semisort, neighbour lists by

@@ -116,15 +116,17 @@ struct HdBufs {
     int *flag;                    // [m-1] arrival counters of the bottom-up pass
     int4 *nlo, *nhi;              // [m-1] node bounds in cell coordinates, 8 x 16 bits
     float4 *nblo, *nbhi;          // [m-1] x 2: node bounding boxes of the points (FP32-band mode)
-    long long *cnt64;             // [m] neighbours per cell
-    long long *nbr_off;           // [m+1] CSR offsets of the neighbour lists
+    long long *nbr_off;           // [m+1] offset of each cell's neighbour list
+    int *scratch;                 // per-warp leaf scratch of the neighbour kernel
 };
-// Cells of the sorted points, their tree and the neighbour counts; ctr->E
-// receives the total (read it back to size the lists).  key_bits = d * bits.
-void hd_cells_and_counts(const void *X, int dtype, const RunParams &P, int key_bits, const HdBufs &H,
-                         const Bufs &B, DevCounters *ctr, cudaStream_t s);
-// The neighbour lists at H.nbr_off into nbr.
-void hd_fill(const RunParams &P, const HdBufs &H, const Bufs &B, int *nbr, DevCounters *ctr, cudaStream_t s);
+// Cells of the sorted points and their tree.  key_bits = d * bits.
+void hd_cells(const void *X, int dtype, const RunParams &P, int key_bits, const HdBufs &H, const Bufs &B,
+              DevCounters *ctr, cudaStream_t s);
+// The neighbour lists into nbr (cap entries), one walk per 32 cells; ctr->E
+// (zero before) receives the total, which exceeds cap if nbr was too small.
+void hd_neighbors(const RunParams &P, const HdBufs &H, const Bufs &B, int *nbr, long long cap, DevCounters *ctr,
+                  cudaStream_t s);
+long long hd_scratch_ints();  // size of HdBufs::scratch
 
 // full path compression of the cell union-find
 void launch_uf_compress(int *parent, DevCounters *ctr, int max_iters, cudaStream_t s);

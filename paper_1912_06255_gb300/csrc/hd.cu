@@ -289,120 +289,183 @@ __device__ __forceinline__ int gap2(const int (&c)[8], const int4 &lo, const int
 // entered when it may hold a neighbour of any lane's cell; at a leaf every
 // lane applies the exact offset rule to its own cell.  In the FP32-band mode
 // nodes and cells whose point boxes are farther than eps apart are skipped,
-// as in the enumeration of low dimensions.  FILL = false: counts (nbr_cnt,
-// nbr_near, and as int64 in cnt64 for the offset scan); FILL = true: the ids
-// at off[g], cells at |delta|_inf <= 1 first.
-constexpr int QW = 4;  // warps per block of the query
-constexpr int QK = 1;  // nodes a warp expands per step (more did not pay: the walk is issue-bound)
+// as in the enumeration of low dimensions.
+//
+// One walk per packet: the leaves that pass for some lane go to the warp's
+// scratch (kScr entries in global memory), each lane counts its own, the
+// packet reserves its lists' space with one atomic on ctr->E, and the lanes
+// then fill their lists from the scratch, cells at |delta|_inf <= 1 first.
+// A packet whose leaves overflow the scratch walks the tree a second time to
+// fill.  Space beyond cap is not written: the host sees ctr->E > cap, grows
+// the list buffer and runs the kernel again.
+constexpr int QW = 4;         // warps per block of the query
+constexpr int kScr = 16384;   // scratch entries per warp
 
-template <bool FILL>
-__global__ void __launch_bounds__(32 * QW)
-k_lbvh_query(RunParams P, const int2 *__restrict__ child, const int4 *__restrict__ nlo, const int4 *__restrict__ nhi,
-             const float4 *__restrict__ nblo, const float4 *__restrict__ nbhi, const int4 *__restrict__ ccoord,
-             const float4 *__restrict__ blo, const float4 *__restrict__ bhi, const int *__restrict__ cell_start,
-             int *__restrict__ nbr_pts, int *__restrict__ nbr_cnt, int *__restrict__ nbr_near,
-             long long *__restrict__ cnt64,
-             const long long *__restrict__ off, int *__restrict__ nbr, DevCounters *ctr) {
-    __shared__ int stk[QW][kStack];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int m = ctr->m, d = P.d;
-    const float hi_thr = P.inst[0].thr.hi;
-    long long total = 0;
-    const int packets = (m + 31) >> 5;
-    for (int pk = warp_id_global(); pk < packets; pk += warps_global()) {
-        const int g = pk * 32 + lane;
-        const bool valid = g < m;
-        int c[8];
-        {
-            const int4 cg = valid ? ccoord[g] : make_int4(0, 0, 0, 0);
+struct Walk {
+    int c[8];
+    Bx<8> glo, ghi;
+    int g;
+    bool valid;
+};
+
+// The leaf test of one lane: offset rule (exact, integers), then the boxes.
+__device__ __forceinline__ int leaf_test(const Walk &W, int h, int d, const int4 *__restrict__ ccoord, bool box,
+                                         const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
+                                         float hi_thr) {
+    if (!W.valid || h == W.g) return 0;
+    const int4 ch4 = ccoord[h];
+    int s = 0, inf = 0;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) c[j] = unpack16(cg, j);
+    for (int j = 0; j < 8; ++j) {
+        if (j < d) {
+            const int dj = abs(unpack16(ch4, j) - W.c[j]);
+            inf = max(inf, dj);
+            const int gj = min(max(dj - 1, 0), 9);
+            s += gj * gj;
         }
-        Bx<8> glo = zero_box<8>(), ghi = glo;
-        if (P.box && valid) { glo = load_box<8>(blo, g); ghi = load_box<8>(bhi, g); }
-        int n_near = 0, n_far = 0, near_at = 0, far_at = 0, pts = 0;
-        long long base = 0;
-        if (FILL && valid) {
-            base = off[g];
-            far_at = nbr_near[g];
-        }
-        int sp = 0;
-        if (m > 1) {
-            if (lane == 0) stk[w][0] = 0;
-            sp = 1;
-        }
+    }
+    if (s > d) return 0;
+    if (box && boxes_min_d2<8>(W.glo, W.ghi, load_box<8>(blo, h), load_box<8>(bhi, h)) > hi_thr) return 0;
+    return inf <= 1 ? 1 : 2;  // 1: adjacent, 2: farther
+}
+
+// The walk of one packet.  EMIT: write each lane's hits at its list cursors;
+// otherwise append the leaves that pass for some lane to scr (up to kScr;
+// *ncand counts them all) and count each lane's hits.
+template <bool EMIT>
+__device__ __forceinline__ void walk(const Walk &W, int m, int d, bool box, float hi_thr, int *stk,
+                                     const int2 *__restrict__ child, const int4 *__restrict__ nlo,
+                                     const int4 *__restrict__ nhi, const float4 *__restrict__ nblo,
+                                     const float4 *__restrict__ nbhi, const int4 *__restrict__ ccoord,
+                                     const float4 *__restrict__ blo, const float4 *__restrict__ bhi, int *scr,
+                                     int &ncand, int &n_near, int &n_far, int *nbr, long long &near_at,
+                                     long long &far_at, DevCounters *ctr) {
+    const int lane = threadIdx.x & 31;
+    int sp = 0;
+    if (m > 1) {
+        if (lane == 0) stk[0] = 0;
+        sp = 1;
+    }
+    __syncwarp();
+    while (sp > 0) {
+        const int node = stk[--sp];
         __syncwarp();
-        while (sp > 0) {
-            // up to QK nodes per step, so their loads overlap
-            const int kk = sp < QK ? sp : QK;
-            int2 ch[QK];
+        const int2 ch = child[node];
 #pragma unroll
-            for (int u = 0; u < QK; ++u) {
-                const int node = u < kk ? stk[w][sp - 1 - u] : -1;
-                ch[u] = node >= 0 ? child[node] : make_int2(-1, -1);
-            }
-            sp -= kk;
-            __syncwarp();
-#pragma unroll
-            for (int u = 0; u < QK; ++u) {
-#pragma unroll
-                for (int k = 1; k >= 0; --k) {  // right child pushed first, so the left one is popped first
-                    const int q = k ? ch[u].y : ch[u].x;
-                    if (q < 0) continue;
-                    if (q >= m - 1) {
-                        const int h = q - (m - 1);
-                        if (!valid || h == g) continue;
-                        const int4 ch4 = ccoord[h];
-                        int s = 0, inf = 0;
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            if (j < d) {
-                                const int dj = abs(unpack16(ch4, j) - c[j]);
-                                inf = max(inf, dj);
-                                const int gj = min(max(dj - 1, 0), 9);
-                                s += gj * gj;
-                            }
-                        }
-                        if (s > d) continue;
-                        if (P.box && boxes_min_d2<8>(glo, ghi, load_box<8>(blo, h), load_box<8>(bhi, h)) > hi_thr)
-                            continue;
-                        if (inf <= 1) {
-                            if (FILL) nbr[base + near_at++] = h;
-                            ++n_near;
-                        } else {
-                            if (FILL) nbr[base + far_at++] = h;
-                            ++n_far;
-                        }
-                        if (!FILL && nbr_pts) pts += cell_start[h + 1] - cell_start[h];
-                    } else {
-                        bool enter = valid && gap2(c, nlo[q], nhi[q], d) <= d;
-                        if (enter && P.box)
-                            enter = boxes_min_d2<8>(glo, ghi, load_box<8>(nblo, q), load_box<8>(nbhi, q)) <= hi_thr;
-                        if (__any_sync(0xffffffffu, enter)) {
-                            if (sp < kStack) {
-                                if (lane == 0) stk[w][sp] = q;
-                                ++sp;
-                            } else if (lane == 0) {
-                                set_error(ctr, DBSCAN_ERR_CAPACITY, 72);
-                            }
-                        }
+        for (int k = 1; k >= 0; --k) {  // the right child pushed first, so the left one is popped first
+            const int q = k ? ch.y : ch.x;
+            if (q >= m - 1) {
+                const int h = q - (m - 1);
+                const int t = leaf_test(W, h, d, ccoord, box, blo, bhi, hi_thr);
+                if (EMIT) {
+                    if (t == 1) nbr[near_at++] = h;
+                    else if (t == 2) nbr[far_at++] = h;
+                } else {
+                    if (t == 1) ++n_near;
+                    else if (t == 2) ++n_far;
+                    if (__any_sync(0xffffffffu, t != 0)) {
+                        if (lane == 0 && ncand < kScr) scr[ncand] = h;
+                        ++ncand;
+                    }
+                }
+            } else {
+                bool enter = W.valid && gap2(W.c, nlo[q], nhi[q], d) <= d;
+                if (enter && box)
+                    enter = boxes_min_d2<8>(W.glo, W.ghi, load_box<8>(nblo, q), load_box<8>(nbhi, q)) <= hi_thr;
+                if (__any_sync(0xffffffffu, enter)) {
+                    if (sp < kStack) {
+                        if (lane == 0) stk[sp] = q;
+                        ++sp;
+                    } else if (lane == 0) {
+                        set_error(ctr, DBSCAN_ERR_CAPACITY, 72);
                     }
                 }
             }
-            __syncwarp();
         }
-        if (!FILL && valid) {
-            nbr_cnt[g] = n_near + n_far;
-            nbr_near[g] = n_near;
-            if (nbr_pts) nbr_pts[g] = pts;
-            cnt64[g] = n_near + n_far;
-            total += n_near + n_far;
-        }
+        __syncwarp();
     }
-    if (!FILL) {
+}
+
+__global__ void __launch_bounds__(32 * QW)
+k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int4 *__restrict__ nlo,
+                 const int4 *__restrict__ nhi, const float4 *__restrict__ nblo, const float4 *__restrict__ nbhi,
+                 const int4 *__restrict__ ccoord, const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
+                 const int *__restrict__ cell_start, int *__restrict__ scratch, int *__restrict__ nbr_pts,
+                 int *__restrict__ nbr_cnt, int *__restrict__ nbr_near, long long *__restrict__ off,
+                 int *__restrict__ nbr, long long cap, long long max_warps, DevCounters *ctr) {
+    __shared__ int stk[QW][kStack];
+    if (warps_global() > max_warps) {  // the scratch has no room for this grid (cannot happen: sized for the largest)
+        if (threadIdx.x == 0 && blockIdx.x == 0) set_error(ctr, DBSCAN_ERR_CAPACITY, 73);
+        return;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int m = ctr->m, d = P.d;
+    const bool box = P.box != 0;
+    const float hi_thr = P.inst[0].thr.hi;
+    int *scr = scratch + (long long)warp_id_global() * kScr;
+    const int packets = (m + 31) >> 5;
+    for (int pk = warp_id_global(); pk < packets; pk += warps_global()) {
+        Walk W;
+        W.g = pk * 32 + lane;
+        W.valid = W.g < m;
+        {
+            const int4 cg = W.valid ? ccoord[W.g] : make_int4(0, 0, 0, 0);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
-        if (lane == 0 && total) atomicAdd((unsigned long long *)&ctr->E, (unsigned long long)total);
+            for (int j = 0; j < 8; ++j) W.c[j] = unpack16(cg, j);
+        }
+        W.glo = zero_box<8>();
+        W.ghi = W.glo;
+        if (box && W.valid) {
+            W.glo = load_box<8>(blo, W.g);
+            W.ghi = load_box<8>(bhi, W.g);
+        }
+        int ncand = 0, n_near = 0, n_far = 0;
+        long long near_at = 0, far_at = 0;
+        walk<false>(W, m, d, box, hi_thr, stk[w], child, nlo, nhi, nblo, nbhi, ccoord, blo, bhi, scr, ncand, n_near,
+                    n_far, nbr, near_at, far_at, ctr);
+        // reserve the packet's space: lane offsets by an exclusive scan of the counts
+        const int mine = n_near + n_far;
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 0 && total) base = atomicAdd((unsigned long long *)&ctr->E, (unsigned long long)total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const long long at = (long long)base + (incl - mine);
+        if (W.valid) {
+            off[W.g] = at;
+            nbr_cnt[W.g] = mine;
+            nbr_near[W.g] = n_near;
+        }
+        if (nbr_pts) {
+            // points in the neighbouring cells, from the scratch (or 0 if it overflowed)
+            int pts = 0;
+            for (int i = 0; i < ncand && ncand <= kScr; ++i) {
+                const int h = scr[i];
+                if (leaf_test(W, h, d, ccoord, box, blo, bhi, hi_thr)) pts += cell_start[h + 1] - cell_start[h];
+            }
+            if (W.valid) nbr_pts[W.g] = ncand <= kScr ? pts : (1 << 30);
+        }
+        if ((long long)base + total > cap) continue;  // the host grows the buffer and runs again
+        near_at = at;
+        far_at = at + n_near;
+        if (ncand <= kScr) {
+            for (int i = 0; i < ncand; ++i) {
+                const int h = scr[i];  // the same address for every lane: one broadcast load
+                const int t = leaf_test(W, h, d, ccoord, box, blo, bhi, hi_thr);
+                if (t == 1) nbr[near_at++] = h;
+                else if (t == 2) nbr[far_at++] = h;
+            }
+        } else {
+            walk<true>(W, m, d, box, hi_thr, stk[w], child, nlo, nhi, nblo, nbhi, ccoord, blo, bhi, scr, ncand,
+                       n_near, n_far, nbr, near_at, far_at, ctr);
+        }
+        __syncwarp();
     }
 }
 
@@ -426,10 +489,9 @@ template <typename T> void hd_launch_cells(const void *X, const RunParams &P, co
 
 }  // namespace
 
-// Steps 1-3 above plus the count pass of step 4; the offsets are scanned into
-// H.nbr_off and the total neighbour count is left in ctr->E.
-void hd_cells_and_counts(const void *X, int dtype, const RunParams &P, int key_bits, const HdBufs &H,
-                         const Bufs &B, DevCounters *ctr, cudaStream_t s) {
+// Steps 1-3 above: keys, sort, cells, boxes and the tree.
+void hd_cells(const void *X, int dtype, const RunParams &P, int key_bits, const HdBufs &H, const Bufs &B,
+              DevCounters *ctr, cudaStream_t s) {
     const int n = P.n;
     const int bits = key_bits;
     if (dtype == DBSCAN_F32) hd_launch_keys<float>(X, P, H, B, s);
@@ -460,33 +522,35 @@ void hd_cells_and_counts(const void *X, int dtype, const RunParams &P, int key_b
     if (dtype == DBSCAN_F32) hd_launch_cells<float>(X, P, H, B, idx, ctr, s);
     else hd_launch_cells<double>(X, P, H, B, idx, ctr, s);
     if (P.box) launch_boxes(8, B.pf, B.cell_start, ctr, const_cast<float4 *>(B.blo), const_cast<float4 *>(B.bhi), s);
-    {
-        int g = grid_for((const void *)k_lbvh_nodes, 256);
-        k_lbvh_nodes<<<g, 256, 0, s>>>(H.ckey_lo, H.ckey_hi, H.child, H.parent, H.flag, ctr);
-        count_launch();
-        g = grid_for((const void *)k_lbvh_bounds, 256);
-        k_lbvh_bounds<<<g, 256, 0, s>>>(H.child, H.parent, H.flag, H.ccoord, H.nlo, H.nhi, P.d, B.blo, B.bhi,
-                                        P.box ? H.nblo : nullptr, P.box ? H.nbhi : nullptr, ctr);
-        count_launch();
-        g = grid_for((const void *)k_lbvh_query<false>, 32 * QW);
-        k_lbvh_query<false><<<g, 32 * QW, 0, s>>>(P, H.child, H.nlo, H.nhi, H.nblo, H.nbhi, H.ccoord, B.blo, B.bhi,
-                                                  B.cell_start, P.mc_small_nbr > 0 && P.mc_small_nbr < (1 << 30)
-                                                                    ? const_cast<int *>(B.nbr_pts)
-                                                                    : nullptr,
-                                              const_cast<int *>(B.nbr_cnt), const_cast<int *>(B.nbr_near), H.cnt64,
-                                              nullptr, nullptr, ctr);
-        count_launch();
-    }
-    scan_i64_to_i64(H.cnt64, H.nbr_off, 0, &ctr->m, n, B.part, s);
+    int g = grid_for((const void *)k_lbvh_nodes, 256);
+    k_lbvh_nodes<<<g, 256, 0, s>>>(H.ckey_lo, H.ckey_hi, H.child, H.parent, H.flag, ctr);
+    count_launch();
+    g = grid_for((const void *)k_lbvh_bounds, 256);
+    k_lbvh_bounds<<<g, 256, 0, s>>>(H.child, H.parent, H.flag, H.ccoord, H.nlo, H.nhi, P.d, B.blo, B.bhi,
+                                    P.box ? H.nblo : nullptr, P.box ? H.nbhi : nullptr, ctr);
+    count_launch();
 }
 
-// Step 4's fill pass, into nbr (which holds at least ctr->E entries).
-void hd_fill(const RunParams &P, const HdBufs &H, const Bufs &B, int *nbr, DevCounters *ctr, cudaStream_t s) {
-    const int g = grid_for((const void *)k_lbvh_query<true>, 32 * QW);
-    k_lbvh_query<true><<<g, 32 * QW, 0, s>>>(P, H.child, H.nlo, H.nhi, H.nblo, H.nbhi, H.ccoord, B.blo, B.bhi,
-                                             B.cell_start, nullptr,
-                                         const_cast<int *>(B.nbr_cnt), const_cast<int *>(B.nbr_near), nullptr,
-                                         H.nbr_off, nbr, ctr);
+// Warps of the neighbour kernel's largest grid (no blocks-per-SM cap): the
+// scratch holds kScr entries for each.
+static long long hd_max_warps() {
+    const int cap = grid_cap();
+    set_grid_cap(0);
+    const long long w = (long long)grid_for((const void *)k_lbvh_neighbors, 32 * QW) * QW;
+    set_grid_cap(cap);
+    return w;
+}
+long long hd_scratch_ints() { return hd_max_warps() * kScr; }
+
+// Step 4: the neighbour lists into nbr (cap entries); ctr->E must be 0 before.
+void hd_neighbors(const RunParams &P, const HdBufs &H, const Bufs &B, int *nbr, long long cap, DevCounters *ctr,
+                  cudaStream_t s) {
+    const int g = grid_for((const void *)k_lbvh_neighbors, 32 * QW);
+    const bool pts = P.mc_small_nbr > 0 && P.mc_small_nbr < (1 << 30);
+    k_lbvh_neighbors<<<g, 32 * QW, 0, s>>>(P, H.child, H.nlo, H.nhi, H.nblo, H.nbhi, H.ccoord, B.blo, B.bhi,
+                                          B.cell_start, H.scratch, pts ? const_cast<int *>(B.nbr_pts) : nullptr,
+                                          const_cast<int *>(B.nbr_cnt), const_cast<int *>(B.nbr_near), H.nbr_off,
+                                          nbr, cap, hd_max_warps(), ctr);
     count_launch();
 }
 

@@ -128,5 +128,6 @@ inline void count_launch() { ++g_launches; }
 // capped by the blocks-per-SM limit this thread set (0 = no cap).
 int grid_for(const void *kernel, int threads, size_t smem = 0);
 void set_grid_cap(int blocks_per_sm);
+int grid_cap();
 
 }  // namespace gbdb

@@ -14,6 +14,7 @@ thread_local long long g_launches = 0;
 
 static thread_local int t_grid_cap = 0;
 void set_grid_cap(int blocks_per_sm) { t_grid_cap = blocks_per_sm; }
+int grid_cap() { return t_grid_cap; }
 
 int grid_for(const void *kernel, int threads, size_t smem) {
     const int cap = t_grid_cap;
