@@ -323,17 +323,7 @@ __device__ __forceinline__ bool bloom_may_have(const unsigned *__restrict__ bloo
 }
 
 // A slot is 16 bytes: .x the key (kEmptyKey when free), .y the cell id, so a
-// probe is one load.
-__device__ __forceinline__ int hash_find(const ulonglong2 *__restrict__ ht, uint64_t key, uint64_t mask, int lg) {
-    uint64_t s = hash_slot(key, lg);
-    for (uint64_t it = 0; it <= mask; ++it) {
-        const ulonglong2 e = ht[s];
-        if (e.x == key) return (int)e.y;
-        if (e.x == kEmptyKey) return -1;
-        s = (s + 1) & mask;
-    }
-    return -1;
-}
+// probe is one load (k_insert, k_neighbors).
 
 // Morton key of the cell at c + delta from the key of c (D = 2 or 3), by
 // dilated-integer addition: per dimension, the key's bits of that dimension

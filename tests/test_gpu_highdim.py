@@ -161,3 +161,23 @@ def test_spreader_7d_full_size_sampled(eps):
     rng = np.random.default_rng(7)
     samples = np.sort(rng.choice(len(I.points), 2000, replace=False))
     _sampled_invariants(I.points, I.eps, I.min_pts, core, labels, off, ids, samples)
+
+
+def test_highdim_list_buffer_grows():
+    """More neighbour entries than the context's list buffer (840 per point):
+    the buffer grows and the walk runs again, with the exact result.  In 7D,
+    about one point per cell in a box of 5 cells a side gives each cell some
+    2,500 neighbouring cells."""
+    rng = np.random.default_rng(23)
+    n, d = 8000, 7
+    eps = 1.0
+    X = rng.random((n, d)) * (eps / np.sqrt(d)) * 5.0
+    ctx = DBSCAN(n, d, precision="fp64")
+    for eps_run, mp in ((eps, 2), (0.8 * eps, 30)):
+        r = ctx.run(torch.from_numpy(X).cuda(), eps_run, mp)
+        exp = oracle.dbscan(X, eps_run, mp)
+        assert np.array_equal(r.core.cpu().numpy(), exp[0])
+        assert np.array_equal(r.labels.cpu().numpy(), exp[1])
+        assert np.array_equal(r.border_ids.cpu().numpy(), exp[3])
+        if mp == 2:
+            assert ctx.stats()["num_neighbor_entries"] > 840 * n
