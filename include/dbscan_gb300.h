@@ -102,7 +102,12 @@ enum {
        sparse cells with fewer than 8 points and at most L points in their
        neighbouring cells with one thread per point instead of one warp per
        cell (faster on sparse inputs) */
-    DBSCAN_OPT_SMALL_CELLS = 11
+    DBSCAN_OPT_SMALL_CELLS = 11,
+    /* value: 1 (default) or 0: in the FP32-band mode with cell bounds, the
+       bounding boxes of two cells' core points settle whole pairs in
+       ClusterCore and whole cells in ClusterBorder; 0 leaves those to the
+       point tests (saves the core boxes where they rarely decide) */
+    DBSCAN_OPT_PAIR_BOXES = 12
 };
 enum { DBSCAN_PREC_FP64 = 0, DBSCAN_PREC_FP32_RECHECK = 1 };
 /* SIZE: core-cell pairs are tested in order of non-increasing core count of the
@@ -331,6 +336,7 @@ typedef struct {
     int32_t connect_cells;  /* DBSCAN_OPT_CONNECT_CELLS */
     int32_t blocks_per_sm;  /* DBSCAN_OPT_BLOCKS_PER_SM */
     int32_t small_cells;    /* DBSCAN_OPT_SMALL_CELLS */
+    int32_t pair_boxes;     /* DBSCAN_OPT_PAIR_BOXES */
     int32_t trials;         /* configurations timed */
     float best_ms;          /* wall time of one call with the chosen configuration (best of reps) */
     float default_ms;       /* the same for the configuration the context had before */

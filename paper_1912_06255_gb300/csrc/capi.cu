@@ -374,7 +374,9 @@ static dbscan_status enqueue_core(dbscan_ctx *c, const RunParams &P, int D, int 
     }
     mark(7);
     launch_labels(P, B, d_core, d_labels, c->ctr, s);
-    launch_border(D, mode, false, P, B, d_labels, nullptr, 0, c->ctr, s);
+    // the offsets only when the caller takes them now (else dbscan_border_ids scans them)
+    launch_border(D, mode, false, P, B, d_labels, nullptr, 0, c->ctr, s, d_border_offsets != nullptr);
+    c->boff_ready = d_border_offsets != nullptr;
     mark(8);
     if (hashed) launch_table_reset(S, c->ctr, s);
     if (d_border_offsets)
@@ -615,6 +617,10 @@ dbscan_status dbscan_set_option(dbscan_ctx *c, int option, int64_t value) {
         if (value < 0 || value > (1ll << 30)) return DBSCAN_ERR_INVALID_ARG;
         c->mc_small_nbr = (int)value;
         return DBSCAN_OK;
+    case DBSCAN_OPT_PAIR_BOXES:
+        if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
+        c->pair_box = (int)value;
+        return DBSCAN_OK;
     case DBSCAN_OPT_PHASE_TIMING:
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
         c->phase_timing = (int)value;
@@ -643,6 +649,7 @@ dbscan_status dbscan_get_option(const dbscan_ctx *c, int option, int64_t *value)
     case DBSCAN_OPT_CONNECT_WAVES: *value = c->waves; return DBSCAN_OK;
     case DBSCAN_OPT_BLOCKS_PER_SM: *value = c->blocks_per_sm; return DBSCAN_OK;
     case DBSCAN_OPT_SMALL_CELLS: *value = c->mc_small_nbr; return DBSCAN_OK;
+    case DBSCAN_OPT_PAIR_BOXES: *value = c->pair_box; return DBSCAN_OK;
     default: return DBSCAN_ERR_INVALID_ARG;
     }
 }
@@ -704,6 +711,7 @@ static dbscan_status run_once(dbscan_ctx *c, const void *d_points, int64_t n, in
     P.cn_cells = c->cn_cells;
     P.waves = c->waves;
     P.mc_small_nbr = c->mc_small_nbr;
+    P.pair_box = c->pair_box;
     set_grid_cap(c->blocks_per_sm);
     P.stats = c->collect_stats;
     P.ninst = 1;
@@ -796,6 +804,7 @@ static dbscan_status run_batch_once(dbscan_ctx *c, const dbscan_instance *hi, in
     P.cn_cells = c->cn_cells;
     P.waves = c->waves;
     P.mc_small_nbr = c->mc_small_nbr;
+    P.pair_box = c->pair_box;
     set_grid_cap(c->blocks_per_sm);
     P.stats = c->collect_stats;
     P.box = fp32_all && c->cell_bounds ? 1 : 0;
@@ -832,7 +841,7 @@ static dbscan_status run_batch_once(dbscan_ctx *c, const dbscan_instance *hi, in
                                         (unsigned long long)(uintptr_t)d_labels,
                                         (unsigned long long)(uintptr_t)d_border_offsets,
                                         (unsigned long long)(mode | (c->sched << 4) | (P.box << 8) | (P.stats << 9) |
-                                                             ((c->log_cap > 0) << 10) | (c->cn_cells << 12) |
+                                                             ((c->log_cap > 0) << 10) | (c->pair_box << 11) | (c->cn_cells << 12) |
                                                              (c->waves << 20) | (c->blocks_per_sm << 24)),
                                         (unsigned long long)c->mc_small_nbr ^ ((unsigned long long)c->lcap << 31),
                                         (unsigned long long)c->phase_timing, (unsigned long long)c->max_iters, 1ull};
@@ -1014,6 +1023,10 @@ dbscan_status dbscan_border_ids(dbscan_ctx *c, int32_t *d_ids, int64_t capacity,
     B.n_max = c->last.n;
     B.nbr_stride = c->last.d <= kMaxEnumDim ? c->noff[c->last.d] : 0;
     CK(cudaMemsetAsync(&c->ctr->err, 0, sizeof(int), s));
+    if (!c->boff_ready) {
+        launch_border_offsets(c->last, B, s);
+        c->boff_ready = true;
+    }
     launch_border(c->last_D, c->last_mode, true, c->last, B, nullptr, d_ids, capacity, c->ctr, s);
     CK(cudaGetLastError());
     int err = 0;

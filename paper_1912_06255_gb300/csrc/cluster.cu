@@ -324,7 +324,8 @@ void launch_core_compact(int SD, const RunParams &P, const Bufs &B, DevCounters 
     if (SD == 2) go(k_core_compact<2>);
     else if (SD == 4) go(k_core_compact<4>);
     else go(k_core_compact<8>);
-    if (P.box || B.ccent) launch_boxes(SD, B.cpf, B.ccs, ctr, B.cblo, B.cbhi, s, B.ccent);
+    // core-point boxes: pair verdicts and border tests, or the learned schedule's features
+    if ((P.box && P.pair_box) || B.ccent) launch_boxes(SD, B.cpf, B.ccs, ctr, B.cblo, B.cbhi, s, B.ccent);
 }
 
 // ----------------------------------------------------------------- schedule
@@ -390,7 +391,7 @@ k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict
     constexpr bool BOX = (M == kF32FromF32 || M == kF32FromF64);
     const int lane = threadIdx.x & 31;
     const int m = ctr->m;
-    const bool use_box = BOX && P.box;
+    const bool use_box = BOX && P.box && P.pair_box;
     // WAVE 0: adjacent-cell pairs (current parents compared); 1: farther pairs
     // after compression (finds); 2: all pairs in one wave (finds)
     int *next = WAVE == 1 ? &ctr->cell_next2 : &ctr->cell_next;
@@ -639,7 +640,7 @@ k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restr
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nn = ctr->n_noncore;
     unsigned rech = 0;
-    unsigned long long evals = 0, nborder = 0;
+    unsigned long long evals = 0, nborder = 0, members = 0;
     for (int t = warp_id_global(); t < nn; t += warps_global()) {
         const int i = B.noncore[t];
         const int g = B.cell_of[i];
@@ -662,7 +663,7 @@ k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restr
             if (__any_sync(0xffffffffu, have)) continue;
             bool found = false;
             if constexpr (M == kF32FromF32 || M == kF32FromF64) {
-                if (P.box) {
+                if (P.box && P.pair_box) {
                     const Bx<D> lo = load_box<D>(B.cblo, h), hi = load_box<D>(B.cbhi, h);
                     if (box_min_d2<D>(p.f, lo, hi) > T.hi) continue;  // no core point of h within eps
                     found = box_max_d2<D>(p.f, lo, hi) <= T.lo;      // every core point of h within eps
@@ -699,6 +700,7 @@ k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restr
                 labels_out[o] = ns ? sset[w][0] : -1;
             }
             nborder += ns ? 1 : 0;
+            members += ns;
         } else {
             const long long at = B.boff[o];
             if (at + ns <= ids_cap) {
@@ -713,13 +715,17 @@ k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restr
         flush_counter(&ctr->band_rechecks, rech);
         if (P.stats) flush_counter(&ctr->dist_evals[2], evals);
         if (lane == 0 && nborder) atomicAdd((unsigned *)&ctr->n_border, (unsigned)nborder);
+        if (lane == 0 && members) atomicAdd((unsigned long long *)&ctr->K, members);  // total set length
     }
 }
 
-__global__ void k_store_K(const long long *off, int n, DevCounters *ctr) { ctr->K = off[n]; }
+// CSR offsets of the border sets: exclusive scan of the per-point counts.
+void launch_border_offsets(const RunParams &P, const Bufs &B, cudaStream_t s) {
+    scan_i64_to_i64(B.bcount, B.boff, P.n, nullptr, P.n, B.part, s);
+}
 
 void launch_border(int D, int mode, bool fill, const RunParams &P, const Bufs &B, int32_t *labels_out,
-                   int32_t *ids, long long ids_cap, DevCounters *ctr, cudaStream_t s) {
+                   int32_t *ids, long long ids_cap, DevCounters *ctr, cudaStream_t s, bool offsets) {
     if (!fill) {
         GBDB_DISPATCH(D, mode, {
             auto k = k_border<DD, MM, false>;
@@ -727,8 +733,7 @@ void launch_border(int D, int mode, bool fill, const RunParams &P, const Bufs &B
             k<<<g, BD_THREADS, 0, s>>>(P, B, labels_out, nullptr, 0, ctr);
             count_launch();
         });
-        scan_i64_to_i64(B.bcount, B.boff, P.n, nullptr, P.n, B.part, s);
-        k_store_K<<<1, 1, 0, s>>>(B.boff, P.n, ctr); count_launch();
+        if (offsets) launch_border_offsets(P, B, s);
     } else {
         GBDB_DISPATCH(D, mode, {
             auto k = k_border<DD, MM, true>;

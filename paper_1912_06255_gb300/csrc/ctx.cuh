@@ -33,6 +33,7 @@ struct dbscan_ctx {
     int waves = 2;          // DBSCAN_OPT_CONNECT_WAVES
     int blocks_per_sm = 0;  // DBSCAN_OPT_BLOCKS_PER_SM
     int mc_small_nbr = 0;   // DBSCAN_OPT_SMALL_CELLS
+    int pair_box = 1;       // DBSCAN_OPT_PAIR_BOXES
     cudaEvent_t ev[9] = {};
     // workspace
     void *arena = nullptr;
@@ -109,6 +110,7 @@ struct dbscan_ctx {
     int32_t *d_lab_h = nullptr;
     // last run
     bool have_run = false;
+    bool boff_ready = false;  // the last run's border-set offsets are in boff
     gbdb::RunParams last{};
     int last_D = 0, last_mode = 0;
     const void *last_points = nullptr;

@@ -132,8 +132,10 @@ long long hd_scratch_ints();  // size of HdBufs::scratch
 void launch_uf_compress(int *parent, DevCounters *ctr, int max_iters, cudaStream_t s);
 void launch_labels(const RunParams &P, const Bufs &B, uint8_t *core_out, int32_t *labels_out,
                    DevCounters *ctr, cudaStream_t s);
-// count pass (fill = false) or fill pass (fill = true, ids != null)
+// count pass (fill = false; with the CSR offsets if offsets) or fill pass
+// (fill = true, ids != null)
 void launch_border(int D, int mode, bool fill, const RunParams &P, const Bufs &B, int32_t *labels_out,
-                   int32_t *ids, long long ids_cap, DevCounters *ctr, cudaStream_t s);
+                   int32_t *ids, long long ids_cap, DevCounters *ctr, cudaStream_t s, bool offsets = true);
+void launch_border_offsets(const RunParams &P, const Bufs &B, cudaStream_t s);
 
 }  // namespace gbdb

@@ -73,6 +73,7 @@ struct RunParams {
     int cn_cells;   // core cells per work item of the connectivity kernel
     int waves;      // 2: adjacent pairs, compression, farther pairs; 1: one wave
     int mc_small_nbr;  // neighbourhood limit of MarkCore's thread-per-point cells (0: off)
+    int pair_box;      // core-point boxes decide pairs in ClusterCore and ClusterBorder (with box)
     // copies of instance 0 for single runs (host side convenience)
     int min_pts;
     double eps2;

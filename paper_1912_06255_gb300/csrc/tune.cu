@@ -30,6 +30,7 @@ dbscan_status tune(dbscan_ctx *c, int reps, dbscan_tuning *out, RunFn run_once) 
         {DBSCAN_OPT_CONNECT_CELLS, {1, 2, 4, 8}},
         {DBSCAN_OPT_BLOCKS_PER_SM, {0, 1, 2, 4}},
         {DBSCAN_OPT_SMALL_CELLS, {0, 128, 1 << 30}},
+        {DBSCAN_OPT_PAIR_BOXES, {1, 0}},
     };
     if (c->precision != DBSCAN_PREC_FP32_RECHECK) knobs.erase(knobs.begin() + 1);  // boxes need the FP32 band
     std::vector<int64_t> cur(knobs.size());
@@ -86,6 +87,7 @@ dbscan_status tune(dbscan_ctx *c, int reps, dbscan_tuning *out, RunFn run_once) 
         dbscan_get_option(c, DBSCAN_OPT_CONNECT_CELLS, &v); out->connect_cells = (int32_t)v;
         dbscan_get_option(c, DBSCAN_OPT_BLOCKS_PER_SM, &v); out->blocks_per_sm = (int32_t)v;
         dbscan_get_option(c, DBSCAN_OPT_SMALL_CELLS, &v); out->small_cells = (int32_t)v;
+        dbscan_get_option(c, DBSCAN_OPT_PAIR_BOXES, &v); out->pair_boxes = (int32_t)v;
         out->trials = trials;
         out->best_ms = best_ms;
         out->default_ms = default_ms;

@@ -13,7 +13,8 @@ import math
 import os
 from pathlib import Path
 
-FIELDS = ("schedule", "cell_bounds", "connect_waves", "connect_cells", "blocks_per_sm", "small_cells")
+FIELDS = ("schedule", "cell_bounds", "connect_waves", "connect_cells", "blocks_per_sm", "small_cells",
+          "pair_boxes")
 
 
 def key(kind: str, n: int, d: int, dtype: str, precision: str) -> str:

@@ -208,3 +208,21 @@ def test_context_reuse_and_determinism():
     c = ctx.run(t[:5000], 0.35, 9)
     exp = oracle.dbscan(X[:5000], 0.35, 9)
     assert np.array_equal(c.labels.cpu().numpy(), exp[1])
+
+
+def test_border_ids_without_offsets_in_the_run():
+    """A run that skips the border offsets still serves dbscan_border_ids (the
+    offsets are scanned on demand) and reports the total set length."""
+    import ctypes
+    X = synth.random_small(33, 12000, 2, dtype=np.float32)
+    eps, mp = 0.12, 6
+    ctx = DBSCAN(len(X), 2)
+    r = ctx.run(torch.from_numpy(X).cuda(), eps, mp, border=False)
+    exp = oracle.dbscan(X, eps, mp)
+    K = ctx.stats()["num_border_memberships"]
+    assert K == len(exp[3]) and K > 0
+    ids = torch.empty(K, dtype=torch.int32, device="cuda")
+    st = ctx.lib.dbscan_border_ids(ctx.ctx, ids.data_ptr(), K, torch.cuda.current_stream().cuda_stream)
+    assert st == 0
+    assert np.array_equal(ids.cpu().numpy(), exp[3])
+    assert np.array_equal(r.labels.cpu().numpy(), exp[1])

@@ -33,10 +33,12 @@ def _check(ctx, X, eps, mp):
 @pytest.mark.parametrize("waves", [1, 2])
 @pytest.mark.parametrize("blocks", [0, 1, 3])
 @pytest.mark.parametrize("small", [0, 1 << 30])
-def test_knobs_keep_the_result(cells, waves, blocks, small):
+@pytest.mark.parametrize("pair_boxes", [0, 1])
+def test_knobs_keep_the_result(cells, waves, blocks, small, pair_boxes):
     X = synth.random_small(55, 15000, 3, dtype=np.float32)
     ctx = DBSCAN(len(X), 3)
-    ctx.set_tuning({"connect_cells": cells, "connect_waves": waves, "blocks_per_sm": blocks, "small_cells": small})
+    ctx.set_tuning({"connect_cells": cells, "connect_waves": waves, "blocks_per_sm": blocks, "small_cells": small,
+                    "pair_boxes": pair_boxes})
     assert ctx.tuning()["connect_cells"] == cells and ctx.tuning()["connect_waves"] == waves
     st = _check(ctx, X, 0.25, 10)
     assert st["num_pairs_tested"] + st["num_pairs_skipped"] + st["num_pairs_box_decided"] == st["num_candidate_pairs"]
@@ -45,7 +47,7 @@ def test_knobs_keep_the_result(cells, waves, blocks, small):
 def test_knob_validation():
     ctx = DBSCAN(100, 3)
     for opt, bad in ((_lib.OPT_CONNECT_CELLS, 3), (_lib.OPT_CONNECT_WAVES, 0), (_lib.OPT_BLOCKS_PER_SM, -1),
-                     (_lib.OPT_BLOCKS_PER_SM, 33), (_lib.OPT_SMALL_CELLS, -1)):
+                     (_lib.OPT_BLOCKS_PER_SM, 33), (_lib.OPT_SMALL_CELLS, -1), (_lib.OPT_PAIR_BOXES, 2)):
         with pytest.raises(DbscanError):
             ctx.set_option(opt, bad)
     with pytest.raises(DbscanError):
@@ -61,7 +63,7 @@ def test_autotune_single(d):
     assert t["trials"] >= 10 and 0 < t["best_ms"] <= t["default_ms"]
     assert t["connect_cells"] in (1, 2, 4, 8) and t["connect_waves"] in (1, 2) and t["schedule"] in (0, 1, 2)
     assert ctx.tuning() == {k: t[k] for k in ("schedule", "cell_bounds", "connect_waves", "connect_cells",
-                                                "blocks_per_sm", "small_cells")}
+                                                "blocks_per_sm", "small_cells", "pair_boxes")}
     _check(ctx, X, eps, 10)
 
 
@@ -90,11 +92,13 @@ def test_autotune_batch():
 
 @pytest.mark.parametrize("d", [2, 4, 6])
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_small_cells_kernel_all_dims(d, precision):
-    """MarkCore's thread-per-point path on sparse inputs (few points per cell)."""
+@pytest.mark.parametrize("pair_boxes", [0, 1])
+def test_small_cells_kernel_all_dims(d, precision, pair_boxes):
+    """MarkCore's thread-per-point path on sparse inputs (few points per cell),
+    with and without the core-point box decisions."""
     X = synth.random_small(90 + d, 12000, d, dtype=np.float32, clustered=False)
     ctx = DBSCAN(len(X), d, precision=precision)
-    ctx.set_tuning({"small_cells": 1 << 30})
+    ctx.set_tuning({"small_cells": 1 << 30, "pair_boxes": pair_boxes})
     cases = {2: ((0.04, 3), (0.08, 6)), 4: ((0.4, 3), (1.0, 6)), 6: ((1.5, 3), (2.5, 6))}[d]
     for eps, mp in cases:
         _check(ctx, X, eps, mp)

@@ -12,7 +12,7 @@ def test_key_buckets():
 def test_roundtrip(tmp_path):
     t = {}
     choice = {"schedule": 1, "cell_bounds": 1, "connect_waves": 2, "connect_cells": 8, "blocks_per_sm": 0,
-              "small_cells": 128, "trials": 11, "best_ms": 1.5}
+              "small_cells": 128, "pair_boxes": 0, "trials": 11, "best_ms": 1.5}
     k = tuning.key("single", 1000, 5, "f32", "fp32")
     tuning.record(t, k, choice)
     p = tmp_path / "tune.json"
