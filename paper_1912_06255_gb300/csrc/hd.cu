@@ -292,14 +292,15 @@ __device__ __forceinline__ int gap2(const int (&c)[8], const int4 &lo, const int
 // as in the enumeration of low dimensions.
 //
 // One walk per packet: the leaves that pass for some lane go to the warp's
-// scratch (kScr entries in global memory), each lane counts its own, the
+// scratch (kScr entries in global memory, each the leaf and the masks of the
+// lanes that found it adjacent or farther), each lane counts its own, the
 // packet reserves its lists' space with one atomic on ctr->E, and the lanes
 // then fill their lists from the scratch, cells at |delta|_inf <= 1 first.
 // A packet whose leaves overflow the scratch walks the tree a second time to
 // fill.  Space beyond cap is not written: the host sees ctr->E > cap, grows
 // the list buffer and runs the kernel again.
 constexpr int QW = 4;         // warps per block of the query
-constexpr int kScr = 16384;   // scratch entries per warp
+constexpr int kScr = 8192;    // scratch entries (16 bytes each) per warp
 
 struct Walk {
     int c[8];
@@ -363,8 +364,11 @@ __device__ __forceinline__ void walk(const Walk &W, int m, int d, bool box, floa
                 } else {
                     if (t == 1) ++n_near;
                     else if (t == 2) ++n_far;
-                    if (__any_sync(0xffffffffu, t != 0)) {
-                        if (lane == 0 && ncand < kScr) scr[ncand] = h;
+                    const unsigned near_m = __ballot_sync(0xffffffffu, t == 1);
+                    const unsigned far_m = __ballot_sync(0xffffffffu, t == 2);
+                    if (near_m | far_m) {
+                        if (lane == 0 && ncand < kScr) reinterpret_cast<int4 *>(scr)[ncand] =
+                            make_int4(h, (int)near_m, (int)far_m, 0);
                         ++ncand;
                     }
                 }
@@ -403,7 +407,7 @@ k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int4 *__rest
     const int m = ctr->m, d = P.d;
     const bool box = P.box != 0;
     const float hi_thr = P.inst[0].thr.hi;
-    int *scr = scratch + (long long)warp_id_global() * kScr;
+    int *scr = scratch + (long long)warp_id_global() * kScr * 4;
     const int packets = (m + 31) >> 5;
     for (int pk = warp_id_global(); pk < packets; pk += warps_global()) {
         Walk W;
@@ -446,8 +450,8 @@ k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int4 *__rest
             // points in the neighbouring cells, from the scratch (or 0 if it overflowed)
             int pts = 0;
             for (int i = 0; i < ncand && ncand <= kScr; ++i) {
-                const int h = scr[i];
-                if (leaf_test(W, h, d, ccoord, box, blo, bhi, hi_thr)) pts += cell_start[h + 1] - cell_start[h];
+                const int4 e = reinterpret_cast<const int4 *>(scr)[i];
+                if ((((unsigned)e.y | (unsigned)e.z) >> lane) & 1u) pts += cell_start[e.x + 1] - cell_start[e.x];
             }
             if (W.valid) nbr_pts[W.g] = ncand <= kScr ? pts : (1 << 30);
         }
@@ -456,10 +460,9 @@ k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int4 *__rest
         far_at = at + n_near;
         if (ncand <= kScr) {
             for (int i = 0; i < ncand; ++i) {
-                const int h = scr[i];  // the same address for every lane: one broadcast load
-                const int t = leaf_test(W, h, d, ccoord, box, blo, bhi, hi_thr);
-                if (t == 1) nbr[near_at++] = h;
-                else if (t == 2) nbr[far_at++] = h;
+                const int4 e = reinterpret_cast<const int4 *>(scr)[i];  // one broadcast load for the warp
+                if (((unsigned)e.y >> lane) & 1u) nbr[near_at++] = e.x;
+                else if (((unsigned)e.z >> lane) & 1u) nbr[far_at++] = e.x;
             }
         } else {
             walk<true>(W, m, d, box, hi_thr, stk[w], child, nlo, nhi, nblo, nbhi, ccoord, blo, bhi, scr, ncand,
@@ -540,7 +543,7 @@ static long long hd_max_warps() {
     set_grid_cap(cap);
     return w;
 }
-long long hd_scratch_ints() { return hd_max_warps() * kScr; }
+long long hd_scratch_ints() { return hd_max_warps() * kScr * 4; }
 
 // Step 4: the neighbour lists into nbr (cap entries); ctr->E must be 0 before.
 void hd_neighbors(const RunParams &P, const HdBufs &H, const Bufs &B, int *nbr, long long cap, DevCounters *ctr,
