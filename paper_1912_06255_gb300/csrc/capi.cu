@@ -120,6 +120,7 @@ static Bufs make_bufs(dbscan_ctx *c, bool f64) {
     B.noncore = c->noncore;
     B.bcount = c->bcount;
     B.boff = c->boff;
+    B.bbig = c->bbig;
     B.part = c->part;
     B.n_max = c->max_points;
     return B;
@@ -522,6 +523,7 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
         {(void **)&c->parent, 4 * (size_t)N}, {(void **)&c->compmin, 4 * (size_t)N},
         {(void **)&c->noncore, 4 * (size_t)N},
         {(void **)&c->bcount, 8 * (size_t)N}, {(void **)&c->boff, 8 * (size_t)(N + 1)},
+        {(void **)&c->bbig, (size_t)N},
         {(void **)&c->bbox_out, 8 * (2 * kMaxDim + 1)},
         {(void **)&c->offs, (size_t)kMaxEnumDim * kMaxOffsets * kMaxEnumDim},
         {(void **)&c->ctr, sizeof(DevCounters)},

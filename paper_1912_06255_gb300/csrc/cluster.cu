@@ -645,6 +645,10 @@ k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restr
         const int i = B.noncore[t];
         const int g = B.cell_of[i];
         const int o = B.orig[i];
+        // points of small cells were done by k_border_small, unless their set overflowed there
+        if (P.mc_small_nbr > 0 &&
+            mc_small(P, B.cell_start[g + 1] - B.cell_start[g], B.nbr_pts, g) && !B.bbig[o])
+            continue;
         const Inst &I = P.inst[inst_of_cell(P, g)];
         const Thr T = I.thr;
         const int row0 = I.row0;
@@ -724,8 +728,110 @@ void launch_border_offsets(const RunParams &P, const Bufs &B, cudaStream_t s) {
     scan_i64_to_i64(B.bcount, B.boff, P.n, nullptr, P.n, B.part, s);
 }
 
+// ClusterBorder for the non-core points of small cells (the cells
+// k_markcore_small takes): one thread per point, the set of cluster names in
+// registers (up to kSmallSet, sorted).  A point whose set would grow beyond
+// that is flagged in bbig and left to k_border; the fill pass takes the same
+// split from the flags of the count pass.
+constexpr int kSmallSet = 8;
+
+template <int D, int M, bool FILL>
+__global__ void __launch_bounds__(256)
+k_border_small(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restrict__ ids,
+               long long ids_cap, DevCounters *ctr) {
+    constexpr bool BOX = (M == kF32FromF32 || M == kF32FromF64);
+    const int nn = ctr->n_noncore;
+    unsigned rech = 0;
+    unsigned long long evals = 0, nborder = 0, members = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += gridDim.x * blockDim.x) {
+        const int i = B.noncore[t];
+        const int g = B.cell_of[i];
+        const int o = B.orig[i];
+        if (!mc_small(P, B.cell_start[g + 1] - B.cell_start[g], B.nbr_pts, g)) continue;
+        if (FILL && B.bbig[o]) continue;
+        const Inst &I = P.inst[inst_of_cell(P, g)];
+        const Thr T = I.thr;
+        const int row0 = I.row0;
+        Pt<D, M> p;
+        load_pt(p, B.pf, B.pd, i);
+        int set[kSmallSet];
+        int ns = 0;
+        bool big = false;
+        const int ne = B.nbr_cnt[g];
+        const int *nl = nbr_list<D>(B.nbr, B.nbr_off, B.nbr_stride, g);
+        for (int e = -1; e < ne && !big; ++e) {
+            const int h = e < 0 ? g : nl[e];
+            const int k0 = B.ccs[h], k1 = B.ccs[h + 1];
+            if (k0 == k1) continue;
+            const int L = B.compmin[B.parent[h]] - row0;
+            bool have = false;
+            for (int u = 0; u < ns; ++u) have = have || set[u] == L;
+            if (have) continue;
+            bool found = false;
+            if constexpr (BOX) {
+                if (P.box && P.pair_box) {
+                    const Bx<D> lo = load_box<D>(B.cblo, h), hi = load_box<D>(B.cbhi, h);
+                    if (box_min_d2<D>(p.f, lo, hi) > T.hi) continue;
+                    found = box_max_d2<D>(p.f, lo, hi) <= T.lo;
+                }
+            }
+            for (int k = k0; k < k1 && !found; ++k) {
+                Pt<D, M> q;
+                load_pt(q, B.cpf, B.cpd, k);
+                if (P.stats) ++evals;
+                found = within(p, q, T, B.pd, i, B.cpd, k, rech);
+            }
+            if (!found) continue;
+            if (ns == kSmallSet) {
+                big = true;
+                break;
+            }
+            int u = ns++;
+            while (u > 0 && set[u - 1] > L) { set[u] = set[u - 1]; --u; }
+            set[u] = L;
+        }
+        if (!FILL) {
+            B.bbig[o] = big ? 1 : 0;
+            if (big) continue;  // k_border redoes this point
+            B.bcount[o] = ns;
+            labels_out[o] = ns ? set[0] : -1;
+            nborder += ns ? 1 : 0;
+            members += ns;
+        } else {
+            const long long at = B.boff[o];
+            if (at + ns <= ids_cap) {
+                for (int u = 0; u < ns; ++u) ids[at + u] = set[u];
+            } else {
+                set_error(ctr, DBSCAN_ERR_CAPACITY, 32);
+            }
+        }
+    }
+    if (!FILL) {
+        flush_counter(&ctr->band_rechecks, rech);
+        if (P.stats) flush_counter(&ctr->dist_evals[2], evals);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nborder += __shfl_xor_sync(0xffffffffu, nborder, o);
+        if ((threadIdx.x & 31) == 0 && nborder) atomicAdd((unsigned *)&ctr->n_border, (unsigned)nborder);
+        flush_counter((unsigned long long *)&ctr->K, members);
+    }
+}
+
 void launch_border(int D, int mode, bool fill, const RunParams &P, const Bufs &B, int32_t *labels_out,
                    int32_t *ids, long long ids_cap, DevCounters *ctr, cudaStream_t s, bool offsets) {
+    if (P.mc_small_nbr > 0) {
+        GBDB_DISPATCH(D, mode, {
+            if (!fill) {
+                auto k = k_border_small<DD, MM, false>;
+                const int g = grid_for((const void *)k, 256);
+                k<<<g, 256, 0, s>>>(P, B, labels_out, nullptr, 0, ctr);
+            } else {
+                auto k = k_border_small<DD, MM, true>;
+                const int g = grid_for((const void *)k, 256);
+                k<<<g, 256, 0, s>>>(P, B, labels_out, ids, ids_cap, ctr);
+            }
+            count_launch();
+        });
+    }
     if (!fill) {
         GBDB_DISPATCH(D, mode, {
             auto k = k_border<DD, MM, false>;

@@ -86,6 +86,7 @@ struct dbscan_ctx {
     int *parent = nullptr, *compmin = nullptr;
     int *noncore = nullptr;
     long long *bcount = nullptr, *boff = nullptr;
+    unsigned char *bbig = nullptr;
     long long *bbox_out = nullptr;  // [2*kMaxDim + 1], see launch_bbox
     signed char *offs = nullptr;  // [kMaxEnumDim][kMaxOffsets][kMaxEnumDim]
     int noff[gbdb::kMaxEnumDim + 1] = {0};

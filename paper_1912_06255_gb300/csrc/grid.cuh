@@ -95,6 +95,7 @@ struct Bufs {
     // border
     int *noncore;       // [n_noncore] cell-order indices of the non-core points
     long long *bcount, *boff;
+    unsigned char *bbig;  // [N] by input index: the point's border set outgrew k_border_small's
     long long *part;
     int64_t n_max;
 };

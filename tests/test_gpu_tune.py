@@ -102,3 +102,36 @@ def test_small_cells_kernel_all_dims(d, precision, pair_boxes):
     cases = {2: ((0.04, 3), (0.08, 6)), 4: ((0.4, 3), (1.0, 6)), 6: ((1.5, 3), (2.5, 6))}[d]
     for eps, mp in cases:
         _check(ctx, X, eps, mp)
+
+
+def _twelve_chains():
+    """A point p at the origin and 12 chains of 20 points along the icosahedron
+    directions: each chain's first point at 0.99 (within eps = 1 of p, and
+    1.04 from the next chain's), the rest in [1.05, 1.5].  With minPts 14 the
+    chain points are core, p (13 points within eps) is not, and p joins 12
+    clusters."""
+    phi = (1 + 5 ** 0.5) / 2
+    v = []
+    for a in (-1, 1):
+        for b in (-phi, phi):
+            v += [(0, a, b), (a, b, 0), (b, 0, a)]
+    v = np.array(v, dtype=np.float64)
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    pts = [np.zeros(3)]
+    for u in v:
+        pts.append(0.99 * u)
+        for r in np.linspace(1.05, 1.5, 19):
+            pts.append(r * u)
+    return np.array(pts) + 10.0
+
+
+@pytest.mark.parametrize("small", [0, 1 << 30])
+def test_border_point_in_twelve_clusters(small):
+    """More clusters per border point than the thread-per-point border kernel
+    keeps (8): the point goes to the warp kernel, with the same result."""
+    X = _twelve_chains()
+    exp = oracle.dbscan(X, 1.0, 14)
+    assert exp[0][0] == 0 and exp[2][1] - exp[2][0] == 12  # p is a border point of 12 clusters
+    ctx = DBSCAN(len(X), 3, precision="fp64")
+    ctx.set_tuning({"small_cells": small})
+    _check(ctx, X, 1.0, 14)
