@@ -468,6 +468,7 @@ def run_gpu(args):
     W.run(cctx, X, out)
     ev_phase = cctx.stats()["distance_evals_phase"]
     mc_bound = cctx.stats()["markcore_pair_bound"]
+    band_rechecks = cctx.stats()["band_rechecks"]
     cctx.close()
 
     # timed region: device time per step with CUDA events; L2 flushed before each step.
@@ -583,6 +584,11 @@ def run_gpu(args):
         }
         if clk:
             line["clocks"] = clk
+        if stats["precision"] == 1:  # FP32 band + FP64 recheck ran
+            # pair tests whose FP32 distance fell inside the forward-error band and
+            # were decided again in FP64, over all FP32 pair tests of the same run
+            line["band_hits"] = {"rechecks": band_rechecks, "fp32_pair_tests": sum(ev_phase),
+                                 "fraction": band_rechecks / max(1, sum(ev_phase))}
         if not args.no_cpu_baseline:
             samples, desc = W.cpu_sample()
             npts, t, cores = _time_oracle(samples)

@@ -554,10 +554,31 @@ void launch_connect(int D, int mode, const uint32_t *order, const RunParams &P, 
 // clusters[p] := Find(g) for core p (Algorithm 3), renamed to the smallest
 // input index of a core point in the component.  The same pass lists the
 // non-core points for ClusterBorder.
-__global__ void __launch_bounds__(256) k_uf_flatten(int *parent, int *compmin, DevCounters *ctr, int max_iters) {
+// Flattening takes three passes.  A compressing find per cell (k_uf_compress)
+// leaves every cell within a step or two of its root, but not always on it: a
+// path-halving store of another thread may land after a cell's own store of its
+// root.  So the roots are then read without any store (the forest is static
+// during that pass), into compmin, and written to parent by a third pass.
+__global__ void __launch_bounds__(256) k_uf_roots(const int *__restrict__ parent, int *__restrict__ root,
+                                                  DevCounters *ctr, int max_iters) {
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
-        parent[c] = uf_find(parent, c, max_iters, ctr);
+        int x = c, it = 0;
+        for (; it < max_iters; ++it) {
+            const int p = parent[x];
+            if (p == x) break;
+            x = p;
+        }
+        if (it == max_iters) set_error(ctr, DBSCAN_ERR_DEVICE_TIMEOUT, 3);
+        root[c] = x;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_uf_flatten(int *__restrict__ parent, int *__restrict__ compmin,
+                                                    const DevCounters *ctr) {
+    const int m = ctr->m;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+        parent[c] = compmin[c];  // the root found by k_uf_roots
         compmin[c] = INT_MAX;
     }
 }
@@ -609,8 +630,11 @@ k_label_core(RunParams P, const int *__restrict__ core_s, const int *__restrict_
 
 void launch_labels(const RunParams &P, const Bufs &B, uint8_t *core_out, int32_t *labels_out,
                    DevCounters *ctr, cudaStream_t s) {
-    int g = grid_for((const void *)k_uf_flatten, 256);
-    k_uf_flatten<<<g, 256, 0, s>>>(B.parent, B.compmin, ctr, P.max_iters); count_launch();
+    launch_uf_compress(B.parent, ctr, P.max_iters, s);
+    int g = grid_for((const void *)k_uf_roots, 256);
+    k_uf_roots<<<g, 256, 0, s>>>(B.parent, B.compmin, ctr, P.max_iters); count_launch();
+    g = grid_for((const void *)k_uf_flatten, 256);
+    k_uf_flatten<<<g, 256, 0, s>>>(B.parent, B.compmin, ctr); count_launch();
     g = grid_for((const void *)k_comp_min, 256);
     k_comp_min<<<g, 256, 0, s>>>(B.ccs, B.core_orig, B.parent, B.compmin, ctr); count_launch();
     g = grid_for((const void *)k_label_core, 256);

@@ -146,40 +146,43 @@ k_insert(const T *__restrict__ X, RunParams P, ulonglong2 *__restrict__ ht, unsi
          uint64_t hmask, int hlg, uint32_t *__restrict__ slot_of, uint32_t *__restrict__ rank_of,
          uint32_t *__restrict__ slots, unsigned *__restrict__ bloom, int blg, DevCounters *ctr) {
     const int T_ = gridDim.x * blockDim.x;
-    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < P.n; i0 += T_ * INS_U) {
+    const int lane = threadIdx.x & 31;
+    // the loop bound is uniform across the warp (its first lane's index), so
+    // the warp stays whole for the ballots below
+    for (long long w0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < P.n;
+         w0 += (long long)T_ * INS_U) {
+        const long long i0 = w0 + lane;
         uint64_t key[INS_U], s[INS_U];
         unsigned long long cur[INS_U];
 #pragma unroll
         for (int u = 0; u < INS_U; ++u) {
-            const int i = i0 + u * T_;
+            const long long i = i0 + (long long)u * T_;
             key[u] = 0;
             s[u] = 0;
             if (i < P.n) {
-                const int ii = P.ninst > 1 ? inst_of_row(P, i) : 0;
+                const int ii = P.ninst > 1 ? inst_of_row(P, (int)i) : 0;
                 const Inst &I = P.inst[ii];
                 int c[kMaxDim];
 #pragma unroll
                 for (int j = 0; j < kMaxDim; ++j)
-                    c[j] = j < I.d ? cell_coord<T>(X[(int64_t)i * P.d + j], I, j) : 0;
+                    c[j] = j < I.d ? cell_coord<T>(X[i * P.d + j], I, j) : 0;
                 key[u] = cell_key_of(P, ii, c, I.bits);
                 s[u] = hash_slot(key[u], hlg);
             }
         }
 #pragma unroll
-        for (int u = 0; u < INS_U; ++u) cur[u] = i0 + u * T_ < P.n ? ht[s[u]].x : 0;
-        unsigned rk[INS_U];
+        for (int u = 0; u < INS_U; ++u) cur[u] = i0 + (long long)u * T_ < P.n ? ht[s[u]].x : 0;
+        bool fresh[INS_U];
 #pragma unroll
         for (int u = 0; u < INS_U; ++u) {
-            const int i = i0 + u * T_;
-            rk[u] = 0;
-            if (i >= P.n) continue;
+            fresh[u] = false;
+            if (i0 + (long long)u * T_ >= P.n) continue;
             bool ok = false;
             for (uint64_t it = 0; it <= hmask; ++it) {
                 if (cur[u] == kEmptyKey) {
                     cur[u] = atomicCAS(&ht[s[u]].x, (unsigned long long)kEmptyKey, (unsigned long long)key[u]);
-                    if (cur[u] == kEmptyKey) {
-                        slots[atomicAdd(&ctr->m, 1)] = (uint32_t)s[u];  // a new non-empty cell
-                        if (bloom) bloom_add(bloom, key[u], blg);
+                    if (cur[u] == kEmptyKey) {  // a new non-empty cell
+                        fresh[u] = true;
                         ok = true;
                         break;
                     }
@@ -193,14 +196,31 @@ k_insert(const T *__restrict__ X, RunParams P, ulonglong2 *__restrict__ ht, unsi
                 s[u] = ~0ull;
             }
         }
+        // the warp's new cells take consecutive places in the slot list with
+        // one counter increment
 #pragma unroll
         for (int u = 0; u < INS_U; ++u) {
-            const int i = i0 + u * T_;
+            const unsigned fm = __ballot_sync(0xffffffffu, fresh[u]);
+            if (fm == 0u) continue;
+            const int leader = __ffs(fm) - 1;
+            int at = 0;
+            if (lane == leader) at = atomicAdd(&ctr->m, __popc(fm));
+            at = __shfl_sync(0xffffffffu, at, leader);
+            if (fresh[u]) {
+                slots[at + __popc(fm & ((1u << lane) - 1u))] = (uint32_t)s[u];
+                if (bloom) bloom_add(bloom, key[u], blg);
+            }
+        }
+        unsigned rk[INS_U];
+#pragma unroll
+        for (int u = 0; u < INS_U; ++u) {
+            const long long i = i0 + (long long)u * T_;
+            rk[u] = 0;
             if (i < P.n && s[u] != ~0ull) rk[u] = atomicAdd(hcnt + s[u], 1u);
         }
 #pragma unroll
         for (int u = 0; u < INS_U; ++u) {
-            const int i = i0 + u * T_;
+            const long long i = i0 + (long long)u * T_;
             if (i < P.n && s[u] != ~0ull) {
                 slot_of[i] = (uint32_t)s[u];
                 rank_of[i] = rk[u];
@@ -337,10 +357,48 @@ void launch_table_reset(const Semisort &S, DevCounters *ctr, cudaStream_t s) {
 
 // ---------------------------------------------------------------- boxes
 // Per-cell FP32 bounding box of the points pts[start[c] .. start[c+1]) (exact
-// min/max of the stored FP32 coordinates), and optionally their centroid.  One
-// warp per cell.  Boxes hold BW = SD/4 float4 values per cell (at least one;
+// min/max of the stored FP32 coordinates), and optionally their centroid.
+// With many more cells than warps, a warp takes 32 consecutive cells: a lane
+// reduces its own cell when it holds at most kBoxSmall points (the loads of
+// neighbouring lanes are then nearly contiguous), and the warp reduces the
+// larger cells together, one at a time.  With fewer cells, every cell gets a
+// warp of its own.  Boxes hold BW = SD/4 float4 values per cell (at least one;
 // coordinates past the stored width are zero).  Empty ranges get an empty box
 // (+inf, -inf).
+constexpr int kBoxSmall = 8;
+
+template <int SD, int W>
+__device__ __forceinline__ void box_point(const float *__restrict__ pts, int t, float (&x)[W]) {
+    constexpr int BW = W / 4;
+#pragma unroll
+    for (int j = 0; j < W; ++j) x[j] = 0.f;
+    if constexpr (SD == 2) {
+        const float2 a = reinterpret_cast<const float2 *>(pts)[t];
+        x[0] = a.x;
+        x[1] = a.y;
+    } else {
+#pragma unroll
+        for (int b = 0; b < BW; ++b) {
+            const float4 a = reinterpret_cast<const float4 *>(pts)[(int64_t)t * BW + b];
+            x[4 * b] = a.x; x[4 * b + 1] = a.y; x[4 * b + 2] = a.z; x[4 * b + 3] = a.w;
+        }
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void box_store(int c, int npts, const float (&l)[W], const float (&h)[W],
+                                          const float (&sm)[W], int b, float4 *__restrict__ lo,
+                                          float4 *__restrict__ hi, float4 *__restrict__ cent) {
+    constexpr int BW = W / 4;
+    lo[(int64_t)c * BW + b] = make_float4(l[4 * b], l[4 * b + 1], l[4 * b + 2], l[4 * b + 3]);
+    hi[(int64_t)c * BW + b] = make_float4(h[4 * b], h[4 * b + 1], h[4 * b + 2], h[4 * b + 3]);
+    if (cent) {
+        const float inv = npts > 0 ? 1.f / (float)npts : 0.f;
+        cent[(int64_t)c * BW + b] =
+            make_float4(sm[4 * b] * inv, sm[4 * b + 1] * inv, sm[4 * b + 2] * inv, sm[4 * b + 3] * inv);
+    }
+}
+
 template <int SD>
 __global__ void __launch_bounds__(256)
 k_boxes(const float *__restrict__ pts, const int *__restrict__ start, const DevCounters *ctr,
@@ -348,47 +406,50 @@ k_boxes(const float *__restrict__ pts, const int *__restrict__ start, const DevC
     constexpr int W = SD == 8 ? 8 : 4, BW = W / 4;
     const int m = ctr->m;
     const int lane = threadIdx.x & 31;
-    for (int c = warp_id_global(); c < m; c += warps_global()) {
-        const int s0 = start[c], s1 = start[c + 1];
-        float l[W], h[W], sm[W];
+    // cells per warp work item: 32 (lane-wise small cells) or 1
+    const int chunk = (long long)m >= 32ll * warps_global() ? 32 : 1;
+    for (long long c0 = (long long)warp_id_global() * chunk; c0 < m; c0 += (long long)warps_global() * chunk) {
+        const bool own = lane < chunk && c0 + lane < m;
+        const int c = own ? (int)(c0 + lane) : 0;
+        int s0 = 0, s1 = 0;
+        if (own) { s0 = start[c]; s1 = start[c + 1]; }
+        const bool small = chunk == 32 && own && s1 - s0 <= kBoxSmall;
+        if (small) {
+            float l[W], h[W], sm[W];
 #pragma unroll
-        for (int j = 0; j < W; ++j) { l[j] = INFINITY; h[j] = -INFINITY; sm[j] = 0.f; }
-        for (int t = s0 + lane; t < s1; t += 32) {
-            float x[W];
+            for (int j = 0; j < W; ++j) { l[j] = INFINITY; h[j] = -INFINITY; sm[j] = 0.f; }
+            for (int t = s0; t < s1; ++t) {
+                float x[W];
+                box_point<SD, W>(pts, t, x);
 #pragma unroll
-            for (int j = 0; j < W; ++j) x[j] = 0.f;
-            if constexpr (SD == 2) {
-                const float2 a = reinterpret_cast<const float2 *>(pts)[t];
-                x[0] = a.x;
-                x[1] = a.y;
-            } else {
+                for (int j = 0; j < W; ++j) { l[j] = fminf(l[j], x[j]); h[j] = fmaxf(h[j], x[j]); sm[j] += x[j]; }
+            }
 #pragma unroll
-                for (int b = 0; b < BW; ++b) {
-                    const float4 a = reinterpret_cast<const float4 *>(pts)[(int64_t)t * BW + b];
-                    x[4 * b] = a.x; x[4 * b + 1] = a.y; x[4 * b + 2] = a.z; x[4 * b + 3] = a.w;
+            for (int b = 0; b < BW; ++b) box_store<W>(c, s1 - s0, l, h, sm, b, lo, hi, cent);
+        }
+        for (unsigned big = __ballot_sync(0xffffffffu, own && !small); big; big &= big - 1) {
+            const int src = __ffs(big) - 1;
+            const int cb = (int)(c0 + src);
+            const int b0 = __shfl_sync(0xffffffffu, s0, src), b1 = __shfl_sync(0xffffffffu, s1, src);
+            float l[W], h[W], sm[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) { l[j] = INFINITY; h[j] = -INFINITY; sm[j] = 0.f; }
+            for (int t = b0 + lane; t < b1; t += 32) {
+                float x[W];
+                box_point<SD, W>(pts, t, x);
+#pragma unroll
+                for (int j = 0; j < W; ++j) { l[j] = fminf(l[j], x[j]); h[j] = fmaxf(h[j], x[j]); sm[j] += x[j]; }
+            }
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    l[j] = fminf(l[j], __shfl_xor_sync(0xffffffffu, l[j], o));
+                    h[j] = fmaxf(h[j], __shfl_xor_sync(0xffffffffu, h[j], o));
+                    if (cent) sm[j] += __shfl_xor_sync(0xffffffffu, sm[j], o);
                 }
             }
-#pragma unroll
-            for (int j = 0; j < W; ++j) { l[j] = fminf(l[j], x[j]); h[j] = fmaxf(h[j], x[j]); sm[j] += x[j]; }
-        }
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                l[j] = fminf(l[j], __shfl_xor_sync(0xffffffffu, l[j], o));
-                h[j] = fmaxf(h[j], __shfl_xor_sync(0xffffffffu, h[j], o));
-                if (cent) sm[j] += __shfl_xor_sync(0xffffffffu, sm[j], o);
-            }
-        }
-        if (lane < BW) {
-            const int b = lane;
-            lo[(int64_t)c * BW + b] = make_float4(l[4 * b], l[4 * b + 1], l[4 * b + 2], l[4 * b + 3]);
-            hi[(int64_t)c * BW + b] = make_float4(h[4 * b], h[4 * b + 1], h[4 * b + 2], h[4 * b + 3]);
-            if (cent) {
-                const float inv = s1 > s0 ? 1.f / (float)(s1 - s0) : 0.f;
-                cent[(int64_t)c * BW + b] =
-                    make_float4(sm[4 * b] * inv, sm[4 * b + 1] * inv, sm[4 * b + 2] * inv, sm[4 * b + 3] * inv);
-            }
+            if (lane < BW) box_store<W>(cb, b1 - b0, l, h, sm, lane, lo, hi, cent);
         }
     }
 }
@@ -445,6 +506,17 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
         Bx<D> clo = zero_box<D>(), chi = clo;
         if (P.box) { clo = load_box<D>(blo, c); chi = load_box<D>(bhi, c); }
         const float hi_thr = I.thr.hi;
+        // cell geometry for the offset pre-test: the region of the cell at
+        // coordinate k is [o + k s, o + (k+1) s), widened by a margin far above
+        // the rounding of this FP32 reconstruction
+        float gorg[D], gmarg[D];
+        const float side = 1.f / I.inv_s32;
+        const float geo_thr = hi_thr * (1.f + 0x1p-12f);
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            gorg[j] = I.origin32[j];
+            gmarg[j] = 0x1p-16f * (fabsf(gorg[j]) + (float)(I.kmax[j] + 2) * side);
+        }
         int cnt = 0, near = 0, pts = 0;
         for (int o0 = 0; o0 < noff; o0 += 32 * NB_U) {
             uint64_t key[NB_U], slot[NB_U];
@@ -462,6 +534,18 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
                         dl[j] = (int)offs[o * kMaxEnumDim + j];
                         nc[j] = cc[j] + dl[j];
                         act[u] = act[u] && nc[j] >= 0 && nc[j] <= I.kmax[j];
+                    }
+                    // skip neighbouring cells whose whole region lies farther than
+                    // eps from c's point box: no point there can be within eps
+                    if (act[u] && P.box) {
+                        float d2 = 0.f;
+#pragma unroll
+                        for (int j = 0; j < D; ++j) {
+                            const float L = gorg[j] + (float)nc[j] * side;
+                            const float g = fmaxf(fmaxf(L - bget(chi, j), bget(clo, j) - (L + side)) - gmarg[j], 0.f);
+                            d2 += g * g;
+                        }
+                        act[u] = d2 <= geo_thr;
                     }
                     if (act[u]) {
                         if constexpr (D == 2 || D == 3) key[u] = morton_offset<D>(ckey, dl) | ibits;
