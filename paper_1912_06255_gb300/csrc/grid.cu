@@ -506,17 +506,6 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
         Bx<D> clo = zero_box<D>(), chi = clo;
         if (P.box) { clo = load_box<D>(blo, c); chi = load_box<D>(bhi, c); }
         const float hi_thr = I.thr.hi;
-        // cell geometry for the offset pre-test: the region of the cell at
-        // coordinate k is [o + k s, o + (k+1) s), widened by a margin far above
-        // the rounding of this FP32 reconstruction
-        float gorg[D], gmarg[D];
-        const float side = 1.f / I.inv_s32;
-        const float geo_thr = hi_thr * (1.f + 0x1p-12f);
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            gorg[j] = I.origin32[j];
-            gmarg[j] = 0x1p-16f * (fabsf(gorg[j]) + (float)(I.kmax[j] + 2) * side);
-        }
         int cnt = 0, near = 0, pts = 0;
         for (int o0 = 0; o0 < noff; o0 += 32 * NB_U) {
             uint64_t key[NB_U], slot[NB_U];
@@ -534,18 +523,6 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
                         dl[j] = (int)offs[o * kMaxEnumDim + j];
                         nc[j] = cc[j] + dl[j];
                         act[u] = act[u] && nc[j] >= 0 && nc[j] <= I.kmax[j];
-                    }
-                    // skip neighbouring cells whose whole region lies farther than
-                    // eps from c's point box: no point there can be within eps
-                    if (act[u] && P.box) {
-                        float d2 = 0.f;
-#pragma unroll
-                        for (int j = 0; j < D; ++j) {
-                            const float L = gorg[j] + (float)nc[j] * side;
-                            const float g = fmaxf(fmaxf(L - bget(chi, j), bget(clo, j) - (L + side)) - gmarg[j], 0.f);
-                            d2 += g * g;
-                        }
-                        act[u] = d2 <= geo_thr;
                     }
                     if (act[u]) {
                         if constexpr (D == 2 || D == 3) key[u] = morton_offset<D>(ckey, dl) | ibits;
