@@ -91,7 +91,7 @@ class SingleInstance:
 
     def autotune(self, ctx, dev):
         T, X = self.heldout(dev)
-        return ctx.autotune(X, T.eps, T.min_pts, reps=3), T.name
+        return ctx.autotune(X, T.eps, T.min_pts, reps=5), T.name
 
     def cpu_sample(self):
         X = np.ascontiguousarray(self.I.points[self.I.points[:, 0] < self.SLAB])
@@ -141,9 +141,11 @@ class Batch256:
     """256 independent 2D/3D instances in one batched call."""
     metric = "exact DBSCAN Mpts/s on 1 GB300 (batch of 256 2D/3D instances, about 36M points)"
 
+    INSTANCES = 256
+
     def __init__(self, n):
         from paper_1912_06255_gb300 import synth
-        self.B = synth.batch_256()
+        self.B = synth.batch_256(count=self.INSTANCES)
         self.n = sum(len(b.points) for b in self.B)
         P = np.zeros((self.n, 3), np.float32)
         row = 0
@@ -152,7 +154,7 @@ class Batch256:
             row += len(b.points)
         self.P = P
         self.inst = [(len(b.points), b.points.shape[1], b.eps, b.min_pts) for b in self.B]
-        self.name = f"batch256-n{self.n}-f32"
+        self.name = f"batch{len(self.B)}-n{self.n}-f32"
         self.config = {"workload": self.name, "instances": len(self.B), "n": self.n, "d": "2/3",
                        "eps": "U[0.2,1.0]", "min_pts": "U{5..50}"}
 
@@ -207,7 +209,7 @@ class Batch256:
 
     def autotune(self, ctx, dev):
         X, inst, name = self.heldout(dev)
-        return ctx.autotune_batch(X, inst, reps=3), name
+        return ctx.autotune_batch(X, inst, reps=5), name
 
     def cpu_sample(self):
         order = sorted(range(len(self.B)), key=lambda i: len(self.B[i].points))
@@ -310,13 +312,15 @@ def _peaks():
 # same command (dram__bytes_read.sum + dram__bytes_write.sum); None when the
 # kernel changed after the capture.  Keyed by (kernel, workload name).
 TRAFFIC = {
-    # profiles/launches_spreader3d_n2m.md (the autotuned setting: one connect wave)
-    ("k_markcore", "spreader3d-n2000000-eps100-minpts100-f32"): 55463680 + 535552,
-    ("k_connect", "spreader3d-n2000000-eps100-minpts100-f32"): 49888512 + 56320,
+    # profiles/launches_spreader3d_n2m.md: DRAM read + write per launch at the
+    # captured setting (list order, one connect wave, 8 cells per work item);
+    # the connect figure holds for one wave only
+    ("k_markcore", "spreader3d-n2000000-eps100-minpts100-f32", None): 55439872 + 457472,
+    ("k_connect", "spreader3d-n2000000-eps100-minpts100-f32", 1): 47500032 + 50688,
 }
 
 
-def _roofline(kernel, ms, work_pairs, d, workload, executed_pairs=None):
+def _roofline(kernel, ms, work_pairs, d, workload, executed_pairs=None, waves=None):
     """Roofline of the dominant kernel.  MarkCore and BCP are pair-distance
     loops bound by the FP32 pipe: achieved = algorithmic pair tests x 3d flop
     (d subtractions and d multiply-adds) / the kernel's time, measured with
@@ -332,7 +336,7 @@ def _roofline(kernel, ms, work_pairs, d, workload, executed_pairs=None):
         return None
     achieved = work_pairs * 3 * d / (ms * 1e-3) / 1e12
     out = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-           "frac": achieved / peak_tflops, "traffic": TRAFFIC.get((kernel, workload)), "kernel": kernel,
+           "frac": achieved / peak_tflops, "traffic": TRAFFIC.get((kernel, workload, waves)), "kernel": kernel,
            "work_pair_tests": int(work_pairs), "kernel_ms": ms}
     if executed_pairs is not None:
         ex = executed_pairs * 3 * d / (ms * 1e-3) / 1e12
@@ -471,22 +475,15 @@ def run_gpu(args):
     band_rechecks = cctx.stats()["band_rechecks"]
     cctx.close()
 
-    # timed region: device time per step with CUDA events; L2 flushed before each step.
-    # Phase timing records events inside the run; a batch runs its captured graph
-    # in the timed steps and takes its phase split from one extra direct run.
-    batched = isinstance(W, Batch256)
-    if batched:
-        ctx.set_option(4, 1)
-        step()
-        torch.cuda.synchronize()
-        batch_phases = ctx.stats()["phase_ms"]
-        ctx.set_option(4, 0)
-        step()
-    else:
-        ctx.set_option(4, 1)
+    # timed region: device time per step with CUDA events; L2 flushed before each
+    # step.  The library's phase timing (events between its phases, on the same
+    # stream) adds a little time to a step, so it runs in a second timed pass of
+    # the same steps, which gives phase_ms and the kernel times of the roofline;
+    # a batch replays its captured graph in the first pass and enqueues directly
+    # in the second.
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    phases, launches = [], 0
+    launches = 0
     clocks = ClockSampler(local) if rank == 0 else None
     barrier()
     torch.cuda.synchronize()
@@ -495,15 +492,21 @@ def run_gpu(args):
         evs[k][0].record(stream)
         step()
         evs[k][1].record(stream)
-        st = ctx.stats()
-        phases.append(batch_phases if batched else st["phase_ms"])
-        launches += st["kernel_launches"]
+        launches += ctx.stats()["kernel_launches"]
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop() if clocks else None
     ms = [a.elapsed_time(b) for a, b in evs]
     t_ms = sum(ms) / len(ms)
     stats = ctx.stats()
+    # second pass: per-phase CUDA events inside each step
+    ctx.set_option(4, 1)
+    phases = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        step()
+        phases.append(ctx.stats()["phase_ms"])
+    torch.cuda.synchronize()
     ctx.set_option(4, 0)
 
     # the plain FP64 path on the same input (a few steps, same flush rule)
@@ -553,7 +556,7 @@ def run_gpu(args):
         dd = getattr(W, "d", 3)
         roof_mc = _roofline("k_markcore", ph[4], mc_bound, dd, W.name, executed_pairs=ev_phase[0])
         roof_cn = _roofline("k_test_pairs" if setting["schedule"] == 2 else "k_connect", ph[6], ev_phase[1], dd,
-                            W.name)
+                            W.name, waves=setting["connect_waves"])
         roof = roof_mc if dom == 4 else roof_cn
         line = {
             "metric": W.metric,
@@ -565,7 +568,8 @@ def run_gpu(args):
             "config": dict(W.config, precision="fp32 band + fp64 recheck" if args.precision == "fp32" else "fp64",
                            schedule={v: k for k, v in SCHED_CODES.items()}[setting["schedule"]],
                            tuning=setting, parallelism=f"replicas{ws}",
-                           l2="flushed (256 MiB write) before every timed step"),
+                           l2="flushed (256 MiB write) before every timed step",
+                           phase_timing="a second timed pass of the same steps (phase_ms, roofline kernel times)"),
             "fp64_path": {"value": ws * n / (t64 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": t64},
             "e2e": {"value": ws * n / (te2e * 1e-3) / 1e6, "unit": UNIT,
                     "h2d_bytes_per_step": W.h2d_bytes(), "d2h_bytes_per_step": int(n * 5)},
@@ -618,10 +622,14 @@ def main():
     ap.add_argument("--points", type=int, default=None,
                     help="points of a single-instance workload (default: its defined size, 2e6 in 3D, 1e7 in 5D/7D)")
     ap.add_argument("--eps", type=float, default=None, help="eps of the 5D or 7D workload (default 200 / 1000)")
+    ap.add_argument("--instances", type=int, default=None,
+                    help="instances of the batch workload (default 256; fewer only for small profiling captures)")
     args = ap.parse_args()
     if args.eps is not None:
         for cls in (Mixed5D, VarDen7D):
             cls.EPS = args.eps
+    if args.instances is not None:
+        Batch256.INSTANCES = args.instances
     if args.impl == "reference":
         run_reference(args)
     else:
