@@ -101,7 +101,8 @@ enum {
     /* value: 0 (default: off) or a limit L: MarkCore counts for the points of
        sparse cells with fewer than 8 points and at most L points in their
        neighbouring cells with one thread per point instead of one warp per
-       cell (faster on sparse inputs) */
+       cell, and ClusterBorder assigns their non-core points the same way
+       (faster on sparse inputs); L >= 2^30 takes every such cell */
     DBSCAN_OPT_SMALL_CELLS = 11,
     /* value: 1 (default) or 0: in the FP32-band mode with cell bounds, the
        bounding boxes of two cells' core points settle whole pairs in
