@@ -76,6 +76,18 @@ def test_random_mixed(d, seed, precision, dtype):
         _assert_same(X, eps, mp, precision=precision)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_dyadic_translation(precision, dtype):
+    """Points on a 2^-4 grid, moved by multiples of 2^10: the coordinates stay
+    exact in both storage types, so every run matches the oracle (and each
+    other); larger coordinates widen the FP32 band for FP64 input."""
+    rng = np.random.default_rng(17)
+    X = rng.integers(0, 400, (6000, 3)).astype(np.float64) / 16.0  # 2k core, 300 clusters, 2k noise
+    for t in (0.0, 1024.0, -3072.0):
+        _assert_same((X + t).astype(dtype), 1.25, 5, precision=precision)
+
+
 @pytest.mark.parametrize("cell_bounds", [True, False])
 @pytest.mark.parametrize("schedule", ["size", "none"])
 def test_schedules_agree(schedule, cell_bounds):

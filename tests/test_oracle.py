@@ -70,6 +70,20 @@ def test_lattice_scaled_dyadic_invariance():
             assert np.array_equal(a, b)
 
 
+def test_dyadic_translation_invariance():
+    """Points on a 2^-4 grid moved by a multiple of 2^10: every coordinate
+    difference is the same exact number, so the result is unchanged (a dropped
+    or shifted origin term would show here)."""
+    rng = np.random.default_rng(17)
+    X = rng.integers(0, 160, (800, 3)).astype(np.float64) / 16.0
+    base = oracle.dbscan(X, 1.25, 5)
+    assert 0 < base[0].sum() < len(X) and len(np.unique(base[1][base[0] == 1])) > 1  # core, noise, clusters
+    for t in ((1024.0, 0.0, 0.0), (-3072.0, 2048.0, 1024.0)):
+        moved = oracle.dbscan(X + np.array(t), 1.25, 5)
+        for a, b in zip(base, moved):
+            assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("pts,eps", [(((0.0, 0.0), (3.0, 4.0)), 5.0),
                                      (((1.0, 2.0, 2.0), (0.0, 0.0, 0.0)), 3.0),
                                      (((0.5,), (2.0,)), 1.5)])
