@@ -268,17 +268,37 @@ k_lbvh_bounds(const int2 *__restrict__ child, const int *__restrict__ parent, in
     }
 }
 
-// Smallest sum over the node of max(|delta_j| - 1, 0)^2 against cell
-// coordinates c, with each term capped at 81 (any term above 8 already fails).
-__device__ __forceinline__ int gap2(const int (&c)[8], const int4 &lo, const int4 &hi, int d) {
+// Two 16-bit lanes per 32-bit word (the packed cell coordinates): unsigned
+// maximum and minimum per lane, and the sum of the squares of two lane values
+// below 128 added to s (a two-way dot product of the word with its own low
+// bytes).  Coordinates are below 2^15, so a difference biased by 2^15 stays
+// inside its lane: with x = a - b + 0x80008000 each lane holds a - b + 2^15.
+__device__ __forceinline__ unsigned vmax_u16x2(unsigned a, unsigned b) {
+    unsigned r;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned vmin_u16x2(unsigned a, unsigned b) {
+    unsigned r;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ int add_sq2(unsigned t, int s) { return __dp2a_lo((int)t, (int)(t | (t >> 8)), s); }
+__device__ __forceinline__ unsigned word(const int4 &v, int k) {
+    return (unsigned)(k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w)));
+}
+
+// Smallest sum over the node of max(|delta_j| - 1, 0)^2 against the packed
+// cell coordinates c, each term capped at 81 (any term above 8 already fails).
+// Unused dimensions are zero in c and in the bounds and add nothing.
+__device__ __forceinline__ int gap2(const int4 &c, const int4 &lo, const int4 &hi) {
     int s = 0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        if (j < d) {
-            int g = max(max(unpack16(lo, j) - c[j] - 1, c[j] - unpack16(hi, j) - 1), 0);
-            g = min(g, 9);
-            s += g * g;
-        }
+    for (int k = 0; k < 4; ++k) {
+        const unsigned x = word(lo, k) - word(c, k) + 0x7fff7fffu;  // lo - c - 1, biased
+        const unsigned y = word(c, k) - word(hi, k) + 0x7fff7fffu;  // c - hi - 1, biased
+        const unsigned g = vmin_u16x2(vmax_u16x2(vmax_u16x2(x, y), 0x80008000u), 0x80098009u) - 0x80008000u;
+        s = add_sq2(g, s);
     }
     return s;
 }
@@ -303,7 +323,7 @@ constexpr int QW = 4;         // warps per block of the query
 constexpr int kScr = 8192;    // scratch entries (16 bytes each) per warp
 
 struct Walk {
-    int c[8];
+    int4 c;  // packed cell coordinates
     Bx<8> glo, ghi;
     int g;
     bool valid;
@@ -315,16 +335,16 @@ __device__ __forceinline__ int leaf_test(const Walk &W, int h, int d, const int4
                                          float hi_thr) {
     if (!W.valid || h == W.g) return 0;
     const int4 ch4 = ccoord[h];
-    int s = 0, inf = 0;
+    unsigned a = 0;
+    int s = 0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        if (j < d) {
-            const int dj = abs(unpack16(ch4, j) - W.c[j]);
-            inf = max(inf, dj);
-            const int gj = min(max(dj - 1, 0), 9);
-            s += gj * gj;
-        }
+    for (int k = 0; k < 4; ++k) {
+        const unsigned dd = vmax_u16x2(word(ch4, k) - word(W.c, k) + 0x80008000u,
+                                       word(W.c, k) - word(ch4, k) + 0x80008000u);  // |delta| + 2^15
+        a = vmax_u16x2(a, dd);
+        s = add_sq2(vmin_u16x2(vmax_u16x2(dd, 0x80018001u) - 0x80018001u, 0x00090009u), s);
     }
+    const int inf = (int)max(a & 0xffffu, a >> 16) - 32768;
     if (s > d) return 0;
     if (box && boxes_min_d2<8>(W.glo, W.ghi, load_box<8>(blo, h), load_box<8>(bhi, h)) > hi_thr) return 0;
     return inf <= 1 ? 1 : 2;  // 1: adjacent, 2: farther
@@ -373,7 +393,7 @@ __device__ __forceinline__ void walk(const Walk &W, int m, int d, bool box, floa
                     }
                 }
             } else {
-                bool enter = W.valid && gap2(W.c, nlo[q], nhi[q], d) <= d;
+                bool enter = W.valid && gap2(W.c, nlo[q], nhi[q]) <= d;
                 if (enter && box)
                     enter = boxes_min_d2<8>(W.glo, W.ghi, load_box<8>(nblo, q), load_box<8>(nbhi, q)) <= hi_thr;
                 if (__any_sync(0xffffffffu, enter)) {
@@ -403,7 +423,6 @@ k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int4 *__rest
         return;
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
     const int m = ctr->m, d = P.d;
     const bool box = P.box != 0;
     const float hi_thr = P.inst[0].thr.hi;
@@ -413,11 +432,7 @@ k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int4 *__rest
         Walk W;
         W.g = pk * 32 + lane;
         W.valid = W.g < m;
-        {
-            const int4 cg = W.valid ? ccoord[W.g] : make_int4(0, 0, 0, 0);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) W.c[j] = unpack16(cg, j);
-        }
+        W.c = W.valid ? ccoord[W.g] : make_int4(0, 0, 0, 0);
         W.glo = zero_box<8>();
         W.ghi = W.glo;
         if (box && W.valid) {
