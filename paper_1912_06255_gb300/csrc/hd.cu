@@ -24,8 +24,9 @@ namespace gbdb {
 
 namespace {
 
-// Stack of the tree walks: a walk that expands up to 4 nodes a step keeps at
-// most 4 pending nodes per level of the tree (at most key bits + 1 levels).
+// Stack of the tree walks: a depth-first walk that pushes at most both
+// children of a node keeps at most one pending node per level of the tree
+// (at most key bits + 1 levels); the bound leaves a 4x margin.
 constexpr int kStack = 4 * 132;
 
 // Cell coordinates are packed as 8 unsigned 16-bit values in an int4
