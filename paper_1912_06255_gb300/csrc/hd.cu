@@ -12,10 +12,13 @@
 //   3. a linear BVH over the cells in that order (each internal node splits at
 //      the highest differing key bit, built for all nodes at once), with
 //      integer cell-coordinate bounds set bottom-up;
-//   4. one traversal per cell lists the cells that satisfy the offset rule
-//      exactly (integer arithmetic), in two passes: counts, then the lists at
-//      CSR offsets, cells at |delta|_inf <= 1 first.
+//   4. one packet walk per 32 Z-ordered cells lists the cells that satisfy
+//      the offset rule exactly (integer arithmetic), at CSR offsets reserved
+//      per packet, cells at |delta|_inf <= 1 first.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <initializer_list>
 
 #include "geom.cuh"
 #include "grid.cuh"
@@ -292,10 +295,11 @@ __device__ __forceinline__ unsigned word(const int4 &v, int k) {
 // Smallest sum over the node of max(|delta_j| - 1, 0)^2 against the packed
 // cell coordinates c, each term capped at 81 (any term above 8 already fails).
 // Unused dimensions are zero in c and in the bounds and add nothing.
+template <int DD>
 __device__ __forceinline__ int gap2(const int4 &c, const int4 &lo, const int4 &hi) {
     int s = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < (DD + 1) / 2; ++k) {
         const unsigned x = word(lo, k) - word(c, k) + 0x7fff7fffu;  // lo - c - 1, biased
         const unsigned y = word(c, k) - word(hi, k) + 0x7fff7fffu;  // c - hi - 1, biased
         const unsigned g = vmin_u16x2(vmax_u16x2(vmax_u16x2(x, y), 0x80008000u), 0x80098009u) - 0x80008000u;
@@ -330,8 +334,23 @@ struct Walk {
     bool valid;
 };
 
+// Smallest squared distance between two 8-wide boxes over their first DD
+// dimensions (the others are zero in both).
+template <int DD>
+__device__ __forceinline__ float boxes_min_d2_dd(const Bx<8> &alo, const Bx<8> &ahi, const Bx<8> &blo,
+                                                 const Bx<8> &bhi) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < DD; ++j) {
+        const float a = fmaxf(fmaxf(bget<8>(blo, j) - bget<8>(ahi, j), bget<8>(alo, j) - bget<8>(bhi, j)), 0.f);
+        s = j == 0 ? a * a : __fmaf_rn(a, a, s);
+    }
+    return s;
+}
+
 // The leaf test of one lane: offset rule (exact, integers), then the boxes.
-__device__ __forceinline__ int leaf_test(const Walk &W, int h, int d, const int4 *__restrict__ ccoord, bool box,
+template <int DD>
+__device__ __forceinline__ int leaf_test(const Walk &W, int h, const int4 *__restrict__ ccoord, bool box,
                                          const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
                                          float hi_thr) {
     if (!W.valid || h == W.g) return 0;
@@ -339,23 +358,23 @@ __device__ __forceinline__ int leaf_test(const Walk &W, int h, int d, const int4
     unsigned a = 0;
     int s = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < (DD + 1) / 2; ++k) {
         const unsigned dd = vmax_u16x2(word(ch4, k) - word(W.c, k) + 0x80008000u,
                                        word(W.c, k) - word(ch4, k) + 0x80008000u);  // |delta| + 2^15
         a = vmax_u16x2(a, dd);
         s = add_sq2(vmin_u16x2(vmax_u16x2(dd, 0x80018001u) - 0x80018001u, 0x00090009u), s);
     }
     const int inf = (int)max(a & 0xffffu, a >> 16) - 32768;
-    if (s > d) return 0;
-    if (box && boxes_min_d2<8>(W.glo, W.ghi, load_box<8>(blo, h), load_box<8>(bhi, h)) > hi_thr) return 0;
+    if (s > DD) return 0;
+    if (box && boxes_min_d2_dd<DD>(W.glo, W.ghi, load_box<8>(blo, h), load_box<8>(bhi, h)) > hi_thr) return 0;
     return inf <= 1 ? 1 : 2;  // 1: adjacent, 2: farther
 }
 
 // The walk of one packet.  EMIT: write each lane's hits at its list cursors;
 // otherwise append the leaves that pass for some lane to scr (up to kScr;
 // *ncand counts them all) and count each lane's hits.
-template <bool EMIT>
-__device__ __forceinline__ void walk(const Walk &W, int m, int d, bool box, float hi_thr, int *stk,
+template <int DD, bool EMIT>
+__device__ __forceinline__ void walk(const Walk &W, int m, bool box, float hi_thr, int *stk,
                                      const int2 *__restrict__ child, const int4 *__restrict__ nlo,
                                      const int4 *__restrict__ nhi, const float4 *__restrict__ nblo,
                                      const float4 *__restrict__ nbhi, const int4 *__restrict__ ccoord,
@@ -378,7 +397,7 @@ __device__ __forceinline__ void walk(const Walk &W, int m, int d, bool box, floa
             const int q = k ? ch.y : ch.x;
             if (q >= m - 1) {
                 const int h = q - (m - 1);
-                const int t = leaf_test(W, h, d, ccoord, box, blo, bhi, hi_thr);
+                const int t = leaf_test<DD>(W, h, ccoord, box, blo, bhi, hi_thr);
                 if (EMIT) {
                     if (t == 1) nbr[near_at++] = h;
                     else if (t == 2) nbr[far_at++] = h;
@@ -394,9 +413,9 @@ __device__ __forceinline__ void walk(const Walk &W, int m, int d, bool box, floa
                     }
                 }
             } else {
-                bool enter = W.valid && gap2(W.c, nlo[q], nhi[q]) <= d;
+                bool enter = W.valid && gap2<DD>(W.c, nlo[q], nhi[q]) <= DD;
                 if (enter && box)
-                    enter = boxes_min_d2<8>(W.glo, W.ghi, load_box<8>(nblo, q), load_box<8>(nbhi, q)) <= hi_thr;
+                    enter = boxes_min_d2_dd<DD>(W.glo, W.ghi, load_box<8>(nblo, q), load_box<8>(nbhi, q)) <= hi_thr;
                 if (__any_sync(0xffffffffu, enter)) {
                     if (sp < kStack) {
                         if (lane == 0) stk[sp] = q;
@@ -411,6 +430,7 @@ __device__ __forceinline__ void walk(const Walk &W, int m, int d, bool box, floa
     }
 }
 
+template <int DD>
 __global__ void __launch_bounds__(32 * QW)
 k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int4 *__restrict__ nlo,
                  const int4 *__restrict__ nhi, const float4 *__restrict__ nblo, const float4 *__restrict__ nbhi,
@@ -424,7 +444,7 @@ k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int4 *__rest
         return;
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int m = ctr->m, d = P.d;
+    const int m = ctr->m;
     const bool box = P.box != 0;
     const float hi_thr = P.inst[0].thr.hi;
     int *scr = scratch + (long long)warp_id_global() * kScr * 4;
@@ -442,7 +462,7 @@ k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int4 *__rest
         }
         int ncand = 0, n_near = 0, n_far = 0;
         long long near_at = 0, far_at = 0;
-        walk<false>(W, m, d, box, hi_thr, stk[w], child, nlo, nhi, nblo, nbhi, ccoord, blo, bhi, scr, ncand, n_near,
+        walk<DD, false>(W, m, box, hi_thr, stk[w], child, nlo, nhi, nblo, nbhi, ccoord, blo, bhi, scr, ncand, n_near,
                     n_far, nbr, near_at, far_at, ctr);
         // reserve the packet's space: lane offsets by an exclusive scan of the counts
         const int mine = n_near + n_far;
@@ -481,7 +501,7 @@ k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int4 *__rest
                 else if (((unsigned)e.z >> lane) & 1u) nbr[far_at++] = e.x;
             }
         } else {
-            walk<true>(W, m, d, box, hi_thr, stk[w], child, nlo, nhi, nblo, nbhi, ccoord, blo, bhi, scr, ncand,
+            walk<DD, true>(W, m, box, hi_thr, stk[w], child, nlo, nhi, nblo, nbhi, ccoord, blo, bhi, scr, ncand,
                        n_near, n_far, nbr, near_at, far_at, ctr);
         }
         __syncwarp();
@@ -555,7 +575,10 @@ void hd_cells(const void *X, int dtype, const RunParams &P, int key_bits, const 
 static long long hd_max_warps() {
     const int cap = grid_cap();
     set_grid_cap(0);
-    const long long w = (long long)grid_for((const void *)k_lbvh_neighbors, 32 * QW) * QW;
+    long long w = 0;
+    for (const void *k : {(const void *)k_lbvh_neighbors<5>, (const void *)k_lbvh_neighbors<6>,
+                          (const void *)k_lbvh_neighbors<7>, (const void *)k_lbvh_neighbors<8>})
+        w = std::max(w, (long long)grid_for(k, 32 * QW) * QW);
     set_grid_cap(cap);
     return w;
 }
@@ -564,12 +587,22 @@ long long hd_scratch_ints() { return hd_max_warps() * kScr * 4; }
 // Step 4: the neighbour lists into nbr (cap entries); ctr->E must be 0 before.
 void hd_neighbors(const RunParams &P, const HdBufs &H, const Bufs &B, int *nbr, long long cap, DevCounters *ctr,
                   cudaStream_t s) {
-    const int g = grid_for((const void *)k_lbvh_neighbors, 32 * QW);
     const bool pts = P.mc_small_nbr > 0 && P.mc_small_nbr < (1 << 30);
-    k_lbvh_neighbors<<<g, 32 * QW, 0, s>>>(P, H.child, H.nlo, H.nhi, H.nblo, H.nbhi, H.ccoord, B.blo, B.bhi,
-                                          B.cell_start, H.scratch, pts ? const_cast<int *>(B.nbr_pts) : nullptr,
-                                          const_cast<int *>(B.nbr_cnt), const_cast<int *>(B.nbr_near), H.nbr_off,
-                                          nbr, cap, hd_max_warps(), ctr);
+    const long long maxw = hd_max_warps();
+    auto go = [&](auto k) {
+        const int g = grid_for((const void *)k, 32 * QW);
+        k<<<g, 32 * QW, 0, s>>>(P, H.child, H.nlo, H.nhi, H.nblo, H.nbhi, H.ccoord, B.blo, B.bhi, B.cell_start,
+                                H.scratch, pts ? const_cast<int *>(B.nbr_pts) : nullptr,
+                                const_cast<int *>(B.nbr_cnt), const_cast<int *>(B.nbr_near), H.nbr_off, nbr, cap,
+                                maxw, ctr);
+    };
+    // one instantiation per dimension: the offset and box tests cover only the used coordinates
+    switch (P.d) {
+    case 5: go(k_lbvh_neighbors<5>); break;
+    case 6: go(k_lbvh_neighbors<6>); break;
+    case 7: go(k_lbvh_neighbors<7>); break;
+    default: go(k_lbvh_neighbors<8>); break;
+    }
     count_launch();
 }
 
