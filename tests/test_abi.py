@@ -65,3 +65,34 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.dbscan_create(ctypes.byref(out), -1, 3) == 1
     assert lib.dbscan_create(ctypes.byref(out), 10, 9) == 2
     assert not out.value
+
+
+def _c_layout(struct: str, fields: list, tmp_path) -> dict:
+    """sizeof and offsetof of a header struct, as the C compiler lays it out."""
+    import subprocess
+    src = tmp_path / "layout.c"
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "dbscan_gb300.h"', "int main(void) {",
+             f'  printf("size %zu\\n", sizeof({struct}));']
+    lines += [f'  printf("{f} %zu\\n", offsetof({struct}, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", f"-I{ROOT / 'include'}", str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    return {k: int(v) for k, v in (line.split() for line in out.splitlines())}
+
+
+@pytest.mark.parametrize("struct,cls", [("dbscan_stats", "Stats"), ("dbscan_instance", "Instance"),
+                                        ("dbscan_tuning", "Tuning")])
+def test_struct_layouts_match_the_c_compiler(struct, cls, tmp_path):
+    """The ctypes mirrors have the C compiler's size and field offsets."""
+    import shutil
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_1912_06255_gb300 import _lib
+    mirror = getattr(_lib, cls)
+    fields = [f for f, _ in mirror._fields_]
+    c = _c_layout(struct, fields, tmp_path)
+    assert c["size"] == ctypes.sizeof(mirror), struct
+    for f in fields:
+        assert c[f] == getattr(mirror, f).offset, (struct, f)
