@@ -108,7 +108,11 @@ enum {
        bounding boxes of two cells' core points settle whole pairs in
        ClusterCore and whole cells in ClusterBorder; 0 leaves those to the
        point tests (saves the core boxes where they rarely decide) */
-    DBSCAN_OPT_PAIR_BOXES = 12
+    DBSCAN_OPT_PAIR_BOXES = 12,
+    /* value: 0 (default) or 1: record a link witness for every union of two
+       clusters during the run (for dbscan_link_witnesses; a checking aid, the
+       result does not change) */
+    DBSCAN_OPT_WITNESS = 13
 };
 enum { DBSCAN_PREC_FP64 = 0, DBSCAN_PREC_FP32_RECHECK = 1 };
 /* SIZE: core-cell pairs are tested in order of non-increasing core count of the
@@ -170,7 +174,7 @@ typedef struct {
  * grows linearly with max_points and with the number of candidate
  * neighbouring cells of min(max_dim, 4)).  1 <= max_dim <= 8;
  * 0 <= max_points < 2^31-1.  Runs of d >= 5 find neighbouring cells with a
- * tree over the non-empty cells (Sec. 4.2) instead of offset enumeration;
+ * tree over the non-empty cells (Sec. 5.1) instead of offset enumeration;
  * their tree and neighbour-list buffers are allocated at the first such run
  * (OOM there if the device is full).
  * Returns OK, INVALID_ARG, UNSUPPORTED_DIM, OOM or CUDA.  *ctx is NULL on error.
@@ -216,6 +220,28 @@ dbscan_status dbscan_run(dbscan_ctx *ctx, const void *d_points, int64_t n, int d
  * Returns OK, STATE (no run), CAPACITY, INVALID_ARG or CUDA.  Synchronises.
  */
 dbscan_status dbscan_border_ids(dbscan_ctx *ctx, int32_t *d_ids, int64_t capacity, void *stream);
+
+/*
+ * Link witnesses of the last successful run (dbscan_run or dbscan_run_batch)
+ * made with DBSCAN_OPT_WITNESS = 1: a certificate that each cluster is
+ * connected through steps of at most eps between core points (Sec. 2), which
+ * a checker can verify pair by pair without rerunning the method.
+ *   d_rep [n] int32 (the run's n rows): for a core point, the input index of
+ *     the first core point of its cell (cells have side eps/sqrt(d), so any two
+ *     of their points are within eps, Sec. 3); -1 for other points;
+ *   d_links [2 * capacity] int32: pair i = (d_links[2i], d_links[2i+1]), input
+ *     indices of two core points within eps that joined two clusters of the
+ *     union-find (Algorithm 3): one pair per successful union;
+ *   *count (host) receives the number of pairs; capacity must be at least that
+ *     (CAPACITY otherwise; the number is at most the number of cells, and
+ *     exactly the number of core cells minus the number of clusters).
+ * For a batch the indices are rows of the whole batch.  The run's workspace
+ * must be untouched since (no other run on the context).  Returns OK, STATE
+ * (no run, or the run had the option off), CAPACITY, INVALID_ARG or CUDA.
+ * Synchronises the stream.
+ */
+dbscan_status dbscan_link_witnesses(dbscan_ctx *ctx, int32_t *d_rep, int32_t *d_links, int64_t capacity,
+                                    int64_t *count, void *stream);
 
 /* One problem of a batch: rows [row0, row0 + n) of the batch's point array,
  * using the first d of its ld columns. */
@@ -279,9 +305,11 @@ dbscan_status dbscan_run_host(dbscan_ctx *ctx, const void *h_points, int64_t n, 
  * Precision is the FP32 band with FP64 recheck, schedule SIZE.
  *
  * No cudaMalloc, cudaFree, pinned allocation or allocating library routine is
- * called.  The first call on a device sets the array up (resolves its device
- * address and copies the neighbour-offset tables into it, with synchronous
- * copies), so make that first call before any stream capture.  The array is
+ * called.  Every call resolves the array's device address
+ * (cudaGetSymbolAddress); the first call on a device, and any call after the
+ * address has changed (a device reset), sets the array up: it copies the
+ * neighbour-offset tables into it, clears the cell hash and synchronises the
+ * device, so make that first call before any stream capture.  The array is
  * shared by every call on a device and keeps the last call's contents (each
  * call clears what must start at zero): calls that overlap on the GPU, from
  * any thread or stream, race and corrupt each other.  Synchronises the stream

@@ -50,6 +50,8 @@ def _load():
         lib.oracle_sample_counts.restype = i32
         lib.oracle_neighbors.argtypes = [P, i64, i32, ctypes.c_double, i64, P, i64]
         lib.oracle_neighbors.restype = i64
+        lib.oracle_within_pairs.argtypes = [P, i64, i32, ctypes.c_double, P, i64, i32, P]
+        lib.oracle_within_pairs.restype = i32
         lib.oracle_num_threads.restype = i32
         lib.oracle_free.argtypes = [P]
         _lib = lib
@@ -121,3 +123,16 @@ def neighbors(points, eps: float, p: int) -> np.ndarray:
         if c <= cap:
             return out[:c]
         cap = int(c)
+
+
+def within_pairs(points, eps: float, pairs, threads: int = 0) -> np.ndarray:
+    """within(points[i], points[j]) (Sec. 2, FP64) for each row (i, j) of ``pairs`` [k, 2]."""
+    lib = _load()
+    X = _as_f64(points)
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int64).reshape(-1, 2))
+    out = np.zeros(pr.shape[0], np.uint8)
+    rc = lib.oracle_within_pairs(X.ctypes.data, X.shape[0], X.shape[1], float(eps), pr.ctypes.data,
+                                 pr.shape[0], int(threads), out.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"oracle_within_pairs failed ({rc})")
+    return out.astype(bool)

@@ -313,3 +313,22 @@ int64_t oracle_neighbors(const double *X, int64_t n, int d, double eps, int64_t 
         }
     return c;
 }
+
+/*
+ * The predicate of Sec. 2 on given pairs: out[k] = within(X[i_k], X[j_k]) for
+ * pairs[2k] = i_k, pairs[2k+1] = j_k.  Used to verify, one by one, pairs that a
+ * run claims are within eps (for instance the witnesses of its cluster
+ * links).  Returns 0, or -2 for bad arguments (an index outside [0, n)).
+ */
+int oracle_within_pairs(const double *X, int64_t n, int d, double eps, const int64_t *pairs, int64_t k,
+                        int nthreads, uint8_t *out) {
+    if (n < 0 || d < 1 || !(eps > 0.0) || k < 0) return -2;
+    for (int64_t t = 0; t < 2 * k; ++t)
+        if (pairs[t] < 0 || pairs[t] >= n) return -2;
+    set_threads(nthreads);
+    const double eps2 = eps * eps;
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < k; ++t)
+        out[t] = (uint8_t)within(X + pairs[2 * t] * d, X + pairs[2 * t + 1] * d, d, eps2);
+    return 0;
+}

@@ -184,6 +184,22 @@ class DBSCAN:
                                                        loss.ctypes.data, g.ctypes.data), "dbscan_scheduler_loss_grad")
         return float(loss[0]), g
 
+    def link_witnesses(self, stream=None):
+        """The link witnesses of the last run (made with DBSCAN_OPT_WITNESS on):
+        (rep int32 [n], links int32 [k, 2]) on the GPU, see dbscan_link_witnesses."""
+        torch = _torch()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        k = ctypes.c_int64(0)
+        st = self.lib.dbscan_link_witnesses(self.ctx, None, None, 0, ctypes.byref(k), s.cuda_stream)
+        if st not in (_lib.OK, 5):
+            _lib.check(st, "dbscan_link_witnesses")
+        n = int(self.stats()["n"])
+        rep = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        links = torch.empty((max(int(k.value), 1), 2), dtype=torch.int32, device="cuda")
+        _lib.check(self.lib.dbscan_link_witnesses(self.ctx, rep.data_ptr(), links.data_ptr(), int(k.value),
+                                                  ctypes.byref(k), s.cuda_stream), "dbscan_link_witnesses")
+        return rep[:n], links[: int(k.value)]
+
     def stats(self) -> dict:
         st = Stats()
         _lib.check(self.lib.dbscan_get_stats(self.ctx, ctypes.byref(st)), "dbscan_get_stats")

@@ -22,6 +22,7 @@ F32, F64 = 0, 1
 OPT_PRECISION, OPT_SCHEDULE, OPT_COLLECT_STATS, OPT_MAX_ITERS, OPT_PHASE_TIMING, OPT_CELL_BOUNDS = 0, 1, 2, 3, 4, 5
 OPT_BATCH_GRAPH, OPT_PAIR_LOG = 6, 7
 OPT_CONNECT_CELLS, OPT_CONNECT_WAVES, OPT_BLOCKS_PER_SM, OPT_SMALL_CELLS, OPT_PAIR_BOXES = 8, 9, 10, 11, 12
+OPT_WITNESS = 13
 MLP_PARAMS = 1313
 PREC_FP64, PREC_FP32_RECHECK = 0, 1
 SCHED_SIZE, SCHED_NONE, SCHED_LEARNED = 0, 1, 2
@@ -78,6 +79,7 @@ SIGNATURES = {
     "dbscan_set_option": (_I32, [_P, _I32, _I64]),
     "dbscan_run": (_I32, [_P, _P, _I64, _I32, _I32, _D, _I64, _P, _P, _P, ctypes.POINTER(_I64), _P]),
     "dbscan_border_ids": (_I32, [_P, _P, _I64, _P]),
+    "dbscan_link_witnesses": (_I32, [_P, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "dbscan_run_host": (_I32, [_P, _P, _I64, _I32, _I32, _D, _I64, _P, _P, _P]),
     "dbscan_run_static": (_I32, [_P, _I64, _I32, _I32, _D, _I64, _P, _P, _P]),
     "dbscan_run_batch": (_I32, [_P, ctypes.POINTER(Instance), _I32, _P, _I32, _I32, _P, _P, _P,

@@ -35,11 +35,12 @@ namespace gbdb {
 // the first pair within eps.  The warp tests a block of 32 point pairs per
 // step and leaves on a warp vote.  The smaller cell's points stay in
 // registers: with nc <= 32 columns, each lane holds one column point and the
-// warp covers 32/L rows per step (L = lanes per row).
+// warp covers 32/L rows per step (L = lanes per row).  On a hit, wit (the
+// same on every lane) receives the pair found, as compacted core indices.
 template <int D, int M>
 __device__ __forceinline__ bool bcp_warp(int r0, int nr, int c0, int nc, const float *__restrict__ cpf,
                                          const double *__restrict__ cpd, const RunParams &P, const Thr &T,
-                                         unsigned &rech, unsigned long long &evals) {
+                                         unsigned &rech, unsigned long long &evals, int2 &wit) {
     const int lane = threadIdx.x & 31;
     if (nc <= 32) {
         int lg = 0;
@@ -59,7 +60,12 @@ __device__ __forceinline__ bool bcp_warp(int r0, int nr, int c0, int nc, const f
                 if (P.stats) ++evals;
                 t = within(p, q, T, cpd, r0 + r, cpd, c0 + j, rech);
             }
-            if (__any_sync(0xffffffffu, t)) return true;
+            const unsigned hb = __ballot_sync(0xffffffffu, t);
+            if (hb) {
+                const int src = __ffs(hb) - 1;
+                wit = make_int2(r0 + rb + (src >> lg), c0 + (src & (L - 1)));
+                return true;
+            }
         }
         return false;
     }
@@ -76,7 +82,11 @@ __device__ __forceinline__ bool bcp_warp(int r0, int nr, int c0, int nc, const f
                 if (P.stats) ++evals;
                 t = within(p, q, T, cpd, r0 + r, cpd, c0 + j, rech);
             }
-            if (__any_sync(0xffffffffu, t)) return true;
+            const unsigned hb = __ballot_sync(0xffffffffu, t);
+            if (hb) {
+                wit = make_int2(r0 + r, c0 + cb + __ffs(hb) - 1);
+                return true;
+            }
         }
     }
     return false;

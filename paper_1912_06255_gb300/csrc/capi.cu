@@ -417,6 +417,8 @@ static dbscan_status finish_run(dbscan_ctx *c, const RunParams &P, int D, int mo
         (void)cudaGetLastError();
     }
     if (c->log_cap > 0) c->log_count = std::min<long long>(h.P_list, c->log_cap);
+    c->wit_count = (long long)h.n_wit;
+    c->have_wit = P.wit != nullptr && h.err == 0;
     st.num_pairs_listed = h.P_list;
     if (h.err) return (dbscan_status)h.err;
     if (num_border_memberships) *num_border_memberships = h.K;
@@ -467,6 +469,7 @@ void dbscan_destroy(dbscan_ctx *c) {
     cudaFree(c->hd_nbr);
     cudaFree(c->log_feat);
     cudaFree(c->log_lab);
+    cudaFree(c->wit);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
@@ -548,6 +551,9 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
     if (e == cudaSuccess) e = init_mlp(c, 1);
     if (e == cudaSuccess) e = cudaMemset(c->ht, 0xff, sizeof(ulonglong2) * hcap);
     if (e == cudaSuccess) e = cudaMemset(c->hcnt, 0, sizeof(unsigned) * hcap);
+    // the clears and copies above run on the legacy stream: finish them before
+    // a run on another (possibly non-blocking) stream reads the table
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     c->table_clean = e == cudaSuccess;
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
@@ -623,6 +629,23 @@ dbscan_status dbscan_set_option(dbscan_ctx *c, int option, int64_t value) {
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
         c->pair_box = (int)value;
         return DBSCAN_OK;
+    case DBSCAN_OPT_WITNESS:
+        if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
+        if (value && !c->wit) {
+            if (cudaMalloc((void **)&c->wit, sizeof(int2) * (size_t)std::max<int64_t>(c->max_points, 1)) !=
+                cudaSuccess) {
+                (void)cudaGetLastError();
+                c->wit = nullptr;
+                return DBSCAN_ERR_OOM;
+            }
+        }
+        if (!value && c->wit) {
+            cudaFree(c->wit);
+            c->wit = nullptr;
+        }
+        c->witness = (int)value;
+        c->have_wit = false;
+        return DBSCAN_OK;
     case DBSCAN_OPT_PHASE_TIMING:
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
         c->phase_timing = (int)value;
@@ -652,6 +675,7 @@ dbscan_status dbscan_get_option(const dbscan_ctx *c, int option, int64_t *value)
     case DBSCAN_OPT_BLOCKS_PER_SM: *value = c->blocks_per_sm; return DBSCAN_OK;
     case DBSCAN_OPT_SMALL_CELLS: *value = c->mc_small_nbr; return DBSCAN_OK;
     case DBSCAN_OPT_PAIR_BOXES: *value = c->pair_box; return DBSCAN_OK;
+    case DBSCAN_OPT_WITNESS: *value = c->witness; return DBSCAN_OK;
     default: return DBSCAN_ERR_INVALID_ARG;
     }
 }
@@ -668,6 +692,7 @@ static dbscan_status run_once(dbscan_ctx *c, const void *d_points, int64_t n, in
                               int64_t *num_border_memberships, void *stream) {
     if (!c) return DBSCAN_ERR_INVALID_ARG;
     c->have_run = false;
+    c->have_wit = false;
     if (num_border_memberships) *num_border_memberships = 0;
     if (n < 0 || n > c->max_points) return DBSCAN_ERR_INVALID_ARG;
     if (d < 1 || d > c->max_dim) return DBSCAN_ERR_UNSUPPORTED_DIM;
@@ -683,6 +708,8 @@ static dbscan_status run_once(dbscan_ctx *c, const void *d_points, int64_t n, in
         if (d_border_offsets) CK(cudaMemsetAsync(d_border_offsets, 0, sizeof(int64_t), s));
         CK(cudaStreamSynchronize(s));
         c->have_run = true;
+        c->have_wit = c->witness != 0;
+        c->wit_count = 0;
         c->last = RunParams{};
         return DBSCAN_OK;
     }
@@ -714,6 +741,8 @@ static dbscan_status run_once(dbscan_ctx *c, const void *d_points, int64_t n, in
     P.waves = c->waves;
     P.mc_small_nbr = c->mc_small_nbr;
     P.pair_box = c->pair_box;
+    P.wit = c->witness ? c->wit : nullptr;
+    P.wit_cap = std::max<int64_t>(c->max_points, 1);
     set_grid_cap(c->blocks_per_sm);
     P.stats = c->collect_stats;
     P.ninst = 1;
@@ -763,6 +792,7 @@ static dbscan_status run_batch_once(dbscan_ctx *c, const dbscan_instance *hi, in
                                int64_t *num_border_memberships, void *stream) {
     if (!c || !hi || count < 1) return DBSCAN_ERR_INVALID_ARG;
     c->have_run = false;
+    c->have_wit = false;
     if (num_border_memberships) *num_border_memberships = 0;
     if (ld < 1 || ld > c->max_dim || ld > 3) return DBSCAN_ERR_UNSUPPORTED_DIM;
     if (dtype != DBSCAN_F32 && dtype != DBSCAN_F64) return DBSCAN_ERR_INVALID_ARG;
@@ -788,6 +818,8 @@ static dbscan_status run_batch_once(dbscan_ctx *c, const dbscan_instance *hi, in
         if (d_border_offsets) CK(cudaMemsetAsync(d_border_offsets, 0, sizeof(int64_t), s));
         CK(cudaStreamSynchronize(s));
         c->have_run = true;
+        c->have_wit = c->witness != 0;
+        c->wit_count = 0;
         c->last = RunParams{};
         return DBSCAN_OK;
     }
@@ -807,6 +839,8 @@ static dbscan_status run_batch_once(dbscan_ctx *c, const dbscan_instance *hi, in
     P.waves = c->waves;
     P.mc_small_nbr = c->mc_small_nbr;
     P.pair_box = c->pair_box;
+    P.wit = c->witness ? c->wit : nullptr;
+    P.wit_cap = std::max<int64_t>(c->max_points, 1);
     set_grid_cap(c->blocks_per_sm);
     P.stats = c->collect_stats;
     P.box = fp32_all && c->cell_bounds ? 1 : 0;
@@ -846,7 +880,8 @@ static dbscan_status run_batch_once(dbscan_ctx *c, const dbscan_instance *hi, in
                                                              ((c->log_cap > 0) << 10) | (c->pair_box << 11) | (c->cn_cells << 12) |
                                                              (c->waves << 20) | (c->blocks_per_sm << 24)),
                                         (unsigned long long)c->mc_small_nbr ^ ((unsigned long long)c->lcap << 31),
-                                        (unsigned long long)c->phase_timing, (unsigned long long)c->max_iters, 1ull};
+                                        (unsigned long long)c->phase_timing, (unsigned long long)c->max_iters,
+                                        1ull | ((unsigned long long)c->witness << 1)};
     // phase timing records events between the steps: that run is enqueued
     // directly instead of replaying the graph
     if (!c->use_graph || c->phase_timing) {
@@ -1036,6 +1071,25 @@ dbscan_status dbscan_border_ids(dbscan_ctx *c, int32_t *d_ids, int64_t capacity,
     CK(cudaStreamSynchronize(s));
     err = c->h_ctr->err;
     return err ? (dbscan_status)err : DBSCAN_OK;
+}
+
+dbscan_status dbscan_link_witnesses(dbscan_ctx *c, int32_t *d_rep, int32_t *d_links, int64_t capacity,
+                                    int64_t *count, void *stream) {
+    if (!c || !count || capacity < 0) return DBSCAN_ERR_INVALID_ARG;
+    *count = 0;
+    if (!c->have_run || !c->have_wit) return DBSCAN_ERR_STATE;
+    *count = c->wit_count;
+    if (capacity < c->wit_count) return DBSCAN_ERR_CAPACITY;
+    const int64_t n = c->stats.n;
+    if (n == 0) return DBSCAN_OK;
+    if (!d_rep || (c->wit_count > 0 && !d_links)) return DBSCAN_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Bufs B = make_bufs(c, c->last_dtype == DBSCAN_F64);
+    CK(cudaMemsetAsync(d_rep, 0xff, sizeof(int32_t) * (size_t)n, s));
+    launch_witness_export(B, (int)c->stats.num_core_points, c->wit, c->wit_count, d_rep, d_links, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return DBSCAN_OK;
 }
 
 dbscan_status dbscan_run_host(dbscan_ctx *c, const void *h_points, int64_t n, int d, int dtype, double eps,

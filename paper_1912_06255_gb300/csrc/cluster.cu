@@ -463,7 +463,9 @@ k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict
                 if (WAVE == 0) same = uf_load(parent + a) == uf_load(parent + b);
                 else same = uf_find(parent, a, P.max_iters, ctr) == uf_find(parent, b, P.max_iters, ctr);
             }
-            if (cand && verdict > 0 && !same) uf_link(parent, a, b, P.max_iters, ctr);
+            // a box verdict: every pair of core points is within eps, so the
+            // first core points of the two cells witness the link
+            if (cand && verdict > 0 && !same && uf_link(parent, a, b, P.max_iters, ctr)) record_link(P, ctr, a0, b0);
             cand_pairs += __popc(__ballot_sync(0xffffffffu, cand));
             boxed += __popc(__ballot_sync(0xffffffffu, cand && (verdict < 0 || (verdict > 0 && !same))));
             linked += __popc(__ballot_sync(0xffffffffu, cand && verdict > 0 && !same));
@@ -481,11 +483,12 @@ k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict
                 if (__shfl_sync(0xffffffffu, again, 0)) { ++skipped; continue; }
                 ++tested;
                 const Thr T = P.inst[inst_of_cell(P, sa)].thr;
-                const bool hit = sna >= snb ? bcp_warp<D, M>(sa0, sna, sb0, snb, cpf, cpd, P, T, rech, evals)
-                                            : bcp_warp<D, M>(sb0, snb, sa0, sna, cpf, cpd, P, T, rech, evals);
+                int2 wp;
+                const bool hit = sna >= snb ? bcp_warp<D, M>(sa0, sna, sb0, snb, cpf, cpd, P, T, rech, evals, wp)
+                                            : bcp_warp<D, M>(sb0, snb, sa0, sna, cpf, cpd, P, T, rech, evals, wp);
                 if (hit) {
                     ++linked;
-                    if (lane == 0) uf_link(parent, sa, sb, P.max_iters, ctr);
+                    if (lane == 0 && uf_link(parent, sa, sb, P.max_iters, ctr)) record_link(P, ctr, wp.x, wp.y);
                 }
             }
         }
@@ -642,6 +645,32 @@ void launch_labels(const RunParams &P, const Bufs &B, uint8_t *core_out, int32_t
     cudaMemsetAsync(B.bcount, 0, sizeof(long long) * (size_t)P.n, s);
     k_label_core<<<g, 256, 0, s>>>(P, B.core_s, B.orig, B.cell_of, B.parent, B.compmin, core_out, labels_out,
                                    B.noncore, ctr);
+    count_launch();
+}
+
+// ----------------------------------------------------------------- witnesses
+// The link witnesses of a run in input indices.  rep[o] for every core point
+// (input index o): the input index of the first core point of its cell (any
+// two points of one cell are within eps, Sec. 3); links[2i], links[2i+1]: the
+// pair recorded for hook i of the union-find.
+__global__ void __launch_bounds__(256)
+k_witness_export(const int *__restrict__ ccs, const int *__restrict__ core_orig, const int *__restrict__ core_cell,
+                 int n_core, const int2 *__restrict__ wit, long long nwit, int32_t *__restrict__ rep,
+                 int32_t *__restrict__ links) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n_core; k += stride)
+        rep[core_orig[k]] = core_orig[ccs[core_cell[k]]];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nwit; i += stride) {
+        const int2 w = wit[i];
+        links[2 * i] = core_orig[w.x];
+        links[2 * i + 1] = core_orig[w.y];
+    }
+}
+
+void launch_witness_export(const Bufs &B, int n_core, const int2 *wit, long long nwit, int32_t *rep,
+                           int32_t *links, cudaStream_t s) {
+    const int g = grid_for((const void *)k_witness_export, 256);
+    k_witness_export<<<g, 256, 0, s>>>(B.ccs, B.core_orig, B.core_cell, n_core, wit, nwit, rep, links);
     count_launch();
 }
 

@@ -34,6 +34,10 @@ struct dbscan_ctx {
     int blocks_per_sm = 0;  // DBSCAN_OPT_BLOCKS_PER_SM
     int mc_small_nbr = 0;   // DBSCAN_OPT_SMALL_CELLS
     int pair_box = 1;       // DBSCAN_OPT_PAIR_BOXES
+    int witness = 0;        // DBSCAN_OPT_WITNESS
+    int2 *wit = nullptr;    // [max_points] link witnesses (allocated while the option is on)
+    long long wit_count = 0;
+    bool have_wit = false;  // the last run recorded link witnesses
     cudaEvent_t ev[9] = {};
     // workspace
     void *arena = nullptr;

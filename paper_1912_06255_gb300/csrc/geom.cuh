@@ -366,15 +366,30 @@ __device__ __forceinline__ int uf_find(int *parent, int x, int max_iters, DevCou
     return x;
 }
 
-__device__ __forceinline__ void uf_link(int *parent, int a, int b, int max_iters, DevCounters *ctr) {
+// Returns true iff this call hooked one root under another (the two sets
+// were separate and are now one).
+__device__ __forceinline__ bool uf_link(int *parent, int a, int b, int max_iters, DevCounters *ctr) {
     for (int it = 0; it < max_iters; ++it) {
         int ra = uf_find(parent, a, max_iters, ctr);
         int rb = uf_find(parent, b, max_iters, ctr);
-        if (ra == rb) return;
+        if (ra == rb) return false;
         if (ra < rb) { int t = ra; ra = rb; rb = t; }  // ra is the larger root
-        if (atomicCAS(parent + ra, ra, rb) == ra) return;
+        if (atomicCAS(parent + ra, ra, rb) == ra) return true;
     }
     set_error(ctr, DBSCAN_ERR_DEVICE_TIMEOUT, 2);
+    return false;
+}
+
+// Link witnesses (optional, P.wit non-null): every hook of the union-find is
+// recorded with one pair of core points (compacted indices) that the run
+// found within eps, so that a checker can verify each cluster as a connected
+// graph of eps-edges.  The hooks number m_core minus the components, so
+// wit_cap = m is never exceeded.
+__device__ __forceinline__ void record_link(const RunParams &P, DevCounters *ctr, int ka, int kb) {
+    if (!P.wit) return;
+    const unsigned long long k = atomicAdd(&ctr->n_wit, 1ull);
+    if (k < (unsigned long long)P.wit_cap) P.wit[k] = make_int2(ka, kb);
+    else set_error(ctr, DBSCAN_ERR_CAPACITY, 60);
 }
 
 // Neighbour list of cell c: CSR offsets for d >= 5 (compiled width 8), a

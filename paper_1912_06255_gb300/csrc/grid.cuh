@@ -138,5 +138,8 @@ void launch_labels(const RunParams &P, const Bufs &B, uint8_t *core_out, int32_t
 void launch_border(int D, int mode, bool fill, const RunParams &P, const Bufs &B, int32_t *labels_out,
                    int32_t *ids, long long ids_cap, DevCounters *ctr, cudaStream_t s, bool offsets = true);
 void launch_border_offsets(const RunParams &P, const Bufs &B, cudaStream_t s);
+// link witnesses of the last run in input indices (see k_witness_export)
+void launch_witness_export(const Bufs &B, int n_core, const int2 *wit, long long nwit, int32_t *rep,
+                           int32_t *links, cudaStream_t s);
 
 }  // namespace gbdb

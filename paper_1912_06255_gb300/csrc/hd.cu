@@ -2,7 +2,7 @@
 //
 // Enumerating neighbour offsets does not scale with d: the rule
 // sum_j max(|delta_j| - 1, 0)^2 <= d admits 6,095 offsets in 5D and 257,675
-// in 7D, almost all of them empty cells.  Sec. 4.2 therefore finds the
+// in 7D, almost all of them empty cells.  Sec. 5.1 therefore finds the
 // neighbouring cells of high-dimensional inputs with a spatial tree over the
 // non-empty cells.  This file builds that tree the GPU way:
 //   1. every point gets a 128-bit Morton key of its cell coordinates (at most

@@ -36,6 +36,7 @@ struct DevCounters {
     unsigned long long band_rechecks;
     unsigned long long dist_evals[3];  // MarkCore, BCP, border
     unsigned long long mc_bound;       // MarkCore pair tests without early exit
+    unsigned long long n_wit;          // union-find hooks recorded as link witnesses
 };
 
 // Decision thresholds of one problem instance.
@@ -74,6 +75,8 @@ struct RunParams {
     int waves;      // 2: adjacent pairs, compression, farther pairs; 1: one wave
     int mc_small_nbr;  // neighbourhood limit of MarkCore's thread-per-point cells (0: off)
     int pair_box;      // core-point boxes decide pairs in ClusterCore and ClusterBorder (with box)
+    int2 *wit;         // null, or [wit_cap]: per union-find hook, a pair of compacted core points within eps
+    long long wit_cap;
     // copies of instance 0 for single runs (host side convenience)
     int min_pts;
     double eps2;

@@ -231,7 +231,8 @@ k_collect_pairs(RunParams P, const int *__restrict__ ccs, const int *__restrict_
                     else if (boxes_max_d2<D>(alo, ahi, blo, bhi) <= T.lo) verdict = 1;
                 }
             }
-            if (PASS != 1 && cand && verdict > 0) uf_link(parent, a, b, P.max_iters, ctr);
+            if (PASS != 1 && cand && verdict > 0 && uf_link(parent, a, b, P.max_iters, ctr))
+                record_link(P, ctr, ccs[a], ccs[b]);  // every core pair is within eps
             bool keep = PASS != 0 && cand && verdict == 0;
             if (PASS == 1 && keep && uf_find(parent, b, P.max_iters, ctr) == ra) {
                 keep = false;
@@ -381,11 +382,12 @@ k_test_pairs(RunParams P, const int2 *__restrict__ pairs, const uint64_t *__rest
             ++tested;
             const Thr T = P.inst[inst_of_cell(P, sa)].thr;
             const int a0 = ccs[sa], na = ccs[sa + 1] - a0, b0 = ccs[sb], nb = ccs[sb + 1] - b0;
-            const bool hit = na >= nb ? bcp_warp<D, M>(a0, na, b0, nb, cpf, cpd, P, T, rech, evals)
-                                      : bcp_warp<D, M>(b0, nb, a0, na, cpf, cpd, P, T, rech, evals);
+            int2 wp;
+            const bool hit = na >= nb ? bcp_warp<D, M>(a0, na, b0, nb, cpf, cpd, P, T, rech, evals, wp)
+                                      : bcp_warp<D, M>(b0, nb, a0, na, cpf, cpd, P, T, rech, evals, wp);
             if (hit) {
                 ++linked;
-                if (lane == 0) uf_link(parent, sa, sb, P.max_iters, ctr);
+                if (lane == 0 && uf_link(parent, sa, sb, P.max_iters, ctr)) record_link(P, ctr, wp.x, wp.y);
             }
             if (LOG && lane == 0) {
                 const long long slot = (long long)base + src;

@@ -40,6 +40,7 @@ namespace {
 
 struct StaticState {
     bool ready = false;
+    unsigned char *base = nullptr;  // device address of g_static_scratch when set up
     dbscan_ctx ctx;                // views into g_static_scratch of this device
     gbdb::DevCounters h_ctr;       // host copies read back by the run
     long long h_bbox[2 * kMaxDim + 1];
@@ -106,19 +107,25 @@ size_t carve(dbscan_ctx *c, unsigned char *base) {
     return at <= kStaticScratchBytes ? at : 0;
 }
 
-// Once per device, with that device current: resolve the device address of
-// the scratch array, lay the workspace out over it and upload the neighbour
-// offset tables (plain copies into the array; nothing is allocated).
+// With the device current: resolve the device address of the scratch array
+// (every call: after a device reset or in another context the module is
+// loaded again, possibly at another address) and, the first time or when
+// the address moved, lay the workspace out over it and upload the neighbour
+// offset tables (plain copies into the array; nothing is allocated).  The
+// set-up ends with a device synchronisation, so its copies and clears are
+// complete before any stream of the caller (blocking or not) uses the array.
 dbscan_status setup_device(int dev) {
     std::lock_guard<std::mutex> lock(g_setup_mu);
     StaticState &st = g_state[dev];
-    if (st.ready) return DBSCAN_OK;
     unsigned char *base = nullptr;
     cudaError_t e = cudaGetSymbolAddress((void **)&base, g_static_scratch);
     if (e != cudaSuccess || base == nullptr) {
         (void)cudaGetLastError();
         return DBSCAN_ERR_CUDA;
     }
+    if (st.ready && st.base == base) return DBSCAN_OK;
+    st.ready = false;
+    st.ctx = dbscan_ctx();
     dbscan_ctx &c = st.ctx;
     c.device = dev;
     if (carve(&c, base) == 0) return DBSCAN_ERR_CAPACITY;
@@ -134,6 +141,7 @@ dbscan_status setup_device(int dev) {
     c.hcap = hash_capacity((int)kStaticMaxPoints);
     e = cudaMemset(c.ht, 0xff, sizeof(ulonglong2) * c.hcap);
     if (e == cudaSuccess) e = cudaMemset(c.hcnt, 0, sizeof(unsigned) * c.hcap);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return DBSCAN_ERR_CUDA;
@@ -142,6 +150,7 @@ dbscan_status setup_device(int dev) {
     c.h_ctr = &st.h_ctr;
     c.h_bbox = st.h_bbox;
     c.h_inst = &st.h_inst;
+    st.base = base;
     st.ready = true;
     return DBSCAN_OK;
 }

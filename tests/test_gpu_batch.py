@@ -16,7 +16,8 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
-from paper_1912_06255_gb300 import DBSCAN  # noqa: E402
+from paper_1912_06255_gb300 import DBSCAN, _lib  # noqa: E402
+from _certify import check_links  # noqa: E402
 
 
 def _instances(seed, count, lo, hi, dtype=np.float32):
@@ -102,11 +103,10 @@ def test_batch_of_one_equals_single_run():
         assert torch.equal(u, v)
 
 
-@pytest.mark.slow
-def test_batch256_full_size_sampled():
-    """The full 256-instance batch (about 36M points) in the configuration the
-    benchmark times; the oracle checks the largest and smallest instances and
-    every 32nd by size."""
+@pytest.fixture(scope="module")
+def batch_full():
+    """The full 256-instance batch (about 36M points) and the oracle run of
+    every instance (once)."""
     B = synth.batch_256()
     N = sum(len(b.points) for b in B)
     P = np.zeros((N, 3), np.float32)
@@ -115,15 +115,66 @@ def test_batch256_full_size_sampled():
         P[row:row + len(b.points), :b.points.shape[1]] = b.points
         rows.append(row)
         row += len(b.points)
-    ctx = DBSCAN(N, 3)
-    r = ctx.run_batch(torch.from_numpy(P).cuda(), [(len(b.points), b.points.shape[1], b.eps, b.min_pts) for b in B])
+    exp = [oracle.dbscan(b.points, b.eps, b.min_pts) for b in B]
+    return B, P, rows, exp
+
+
+def _check_all(B, rows, exp, r, tag):
     core, labels = r.core.cpu().numpy(), r.labels.cpu().numpy()
     off, ids = r.border_offsets.cpu().numpy(), r.border_ids.cpu().numpy()
-    order = sorted(range(len(B)), key=lambda i: len(B[i].points))
-    for i in sorted(set([order[0], order[-1]] + order[::32])):
-        b, r0, n = B[i], rows[i], len(B[i].points)
-        ec, el, eo, ei = oracle.dbscan(b.points, b.eps, b.min_pts)
-        assert np.array_equal(core[r0:r0 + n], ec), i
-        assert np.array_equal(labels[r0:r0 + n], el), i
-        assert np.array_equal(off[r0:r0 + n + 1] - off[r0], eo), i
-        assert np.array_equal(ids[off[r0]:off[r0 + n]], ei), i
+    for i, b in enumerate(B):
+        r0, n = rows[i], len(b.points)
+        ec, el, eo, ei = exp[i]
+        assert np.array_equal(core[r0:r0 + n], ec), (tag, i)
+        assert np.array_equal(labels[r0:r0 + n], el), (tag, i)
+        assert np.array_equal(off[r0:r0 + n + 1] - off[r0], eo), (tag, i)
+        assert np.array_equal(ids[off[r0]:off[r0 + n]], ei), (tag, i)
+
+
+# the defaults, the setting the benchmark's autotuner has picked on this family
+# (size order, thread-per-point MarkCore and ClusterBorder for all small cells)
+# and list order with one wave
+BATCH_SETTINGS = {
+    "default": {},
+    "size-smallcells-all": {"schedule": 0, "small_cells": 1 << 30},
+    "list-1wave-8cells-smallcells128": {"schedule": 1, "connect_waves": 1, "connect_cells": 8, "small_cells": 128},
+}
+
+
+@pytest.mark.slow
+def test_batch256_full_size_all_instances(batch_full):
+    """The full 256-instance batch (one replayed CUDA graph) against the oracle
+    run of every instance, element by element, in each setting above, in the
+    autotuner's own choice on the held-out batch (seed 2003, 48 instances) as
+    the benchmark runs it, and with link certificates."""
+    B, P, rows, exp = batch_full
+    ctx = DBSCAN(len(P), 3)
+    t = torch.from_numpy(P).cuda()
+    inst = [(len(b.points), b.points.shape[1], b.eps, b.min_pts) for b in B]
+    for tag, setting in BATCH_SETTINGS.items():
+        ctx.set_tuning(setting)
+        _check_all(B, rows, exp, ctx.run_batch(t, inst), tag)
+    H = synth.batch_256(seed=2003, count=48)
+    NH = sum(len(b.points) for b in H)
+    PH = np.zeros((NH, 3), np.float32)
+    row = 0
+    for b in H:
+        PH[row:row + len(b.points), :b.points.shape[1]] = b.points
+        row += len(b.points)
+    ctx.set_tuning(BATCH_SETTINGS["default"] | {"schedule": 0, "connect_waves": 2, "connect_cells": 4,
+                                                "blocks_per_sm": 0, "small_cells": 0, "pair_boxes": 1})
+    choice = ctx.autotune_batch(torch.from_numpy(PH).cuda(),
+                                [(len(b.points), b.points.shape[1], b.eps, b.min_pts) for b in H], reps=2)
+    ctx.set_option(_lib.OPT_WITNESS, 1)
+    r = ctx.run_batch(t, inst)
+    _check_all(B, rows, exp, r, f"autotuned {choice}")
+    rep, links = ctx.link_witnesses()
+    rep, links = rep.cpu().numpy(), links.cpu().numpy()
+    # links stay inside their instance; certify every instance on its own rows
+    inst_of = np.searchsorted(np.asarray(rows), links[:, 0], side="right") - 1
+    assert np.array_equal(inst_of, np.searchsorted(np.asarray(rows), links[:, 1], side="right") - 1)
+    for i, b in enumerate(B):
+        r0, n = rows[i], len(b.points)
+        rr = rep[r0:r0 + n].astype(np.int64)
+        rr[rr >= 0] -= r0
+        check_links(b.points, b.eps, exp[i][0], exp[i][1], rr, links[inst_of == i].astype(np.int64) - r0)

@@ -13,7 +13,8 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
-from paper_1912_06255_gb300 import DBSCAN, DbscanError, dbscan  # noqa: E402
+from paper_1912_06255_gb300 import DBSCAN, DbscanError, _lib, dbscan  # noqa: E402
+from _certify import check_links, sampled_invariants  # noqa: E402
 
 
 def _assert_same(X, eps, mp, **kw):
@@ -72,8 +73,10 @@ def test_highdim_uniform_sparse():
     _assert_same(np.full((300, 7), 2.5, np.float32), 0.1, 300)
 
 
-def test_spreader_5d_scaled():
-    I = synth.spreader_5d_10m(n=100_000, eps=800.0)
+@pytest.mark.parametrize("eps", [200.0, 400.0, 800.0])
+def test_spreader_5d_scaled(eps):
+    """The 5D mixed workload at 1/100 size, every eps of its sweep."""
+    I = synth.spreader_5d_10m(n=100_000, eps=eps)
     st = _assert_same(I.points, I.eps, I.min_pts)
     assert st["num_cells"] > 1000
 
@@ -112,55 +115,38 @@ def test_highdim_key_overflow_and_reuse():
         assert np.array_equal(r.border_ids.cpu().numpy(), exp[3]), d
 
 
-def _sampled_invariants(X, eps, mp, core, labels, off, ids, samples):
-    """Checks at any size: the core flag by a count, equal labels across core
-    pairs within eps, border sets, noise, and canonical cluster names."""
-    cnt = oracle.sample_counts(X, eps, samples)
-    assert np.array_equal(core[samples], (cnt >= mp).astype(np.uint8))
-    for p in samples[:300]:
-        nb = oracle.neighbors(X, eps, int(p))
-        cn = nb[core[nb] == 1]
-        if core[p]:
-            assert np.all(labels[cn] == labels[p]), p
-        else:
-            exp = np.unique(labels[cn])
-            assert np.array_equal(ids[off[p]:off[p + 1]], exp), p
-            assert labels[p] == (exp[0] if len(exp) else -1), p
-    # cluster names: the smallest core index of the cluster, itself core
-    cl = labels[core == 1]
-    idx = np.flatnonzero(core == 1)
-    first = np.full(len(X), np.iinfo(np.int64).max)
-    np.minimum.at(first, cl, idx)
-    names = np.unique(cl)
-    assert np.array_equal(first[names], names)
+def _full_size_checked(I, d, seed):
+    """One full-size run with link witnesses: sampled outputs against the
+    oracle and every cluster certified as a connected graph of verified
+    eps-edges."""
+    ctx = DBSCAN(len(I.points), d)
+    ctx.set_option(_lib.OPT_WITNESS, 1)
+    r = ctx.run(torch.from_numpy(I.points).cuda(), I.eps, I.min_pts)
+    core, labels = r.core.cpu().numpy(), r.labels.cpu().numpy()
+    off, ids = r.border_offsets.cpu().numpy(), r.border_ids.cpu().numpy()
+    rep, links = ctx.link_witnesses()
+    ncl = check_links(I.points, I.eps, core, labels, rep.cpu().numpy(), links.cpu().numpy(),
+                      num_core_cells=r.stats["num_core_cells"])
+    rng = np.random.default_rng(seed)
+    samples = np.sort(rng.choice(len(I.points), 2000, replace=False))
+    sampled_invariants(I.points, I.eps, I.min_pts, core, labels, off, ids, samples)
+    return ncl
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("eps", [200.0, 800.0])
+@pytest.mark.parametrize("eps", [200.0, 400.0, 800.0])
 def test_spreader_5d_full_size_sampled(eps):
-    """The 10M-point 5D mixed workload (FP32, minPts 10) on sampled outputs."""
-    I = synth.spreader_5d_10m(eps=eps)
-    ctx = DBSCAN(len(I.points), 5)
-    r = ctx.run(torch.from_numpy(I.points).cuda(), I.eps, I.min_pts)
-    core, labels = r.core.cpu().numpy(), r.labels.cpu().numpy()
-    off, ids = r.border_offsets.cpu().numpy(), r.border_ids.cpu().numpy()
-    rng = np.random.default_rng(5)
-    samples = np.sort(rng.choice(len(I.points), 2000, replace=False))
-    _sampled_invariants(I.points, I.eps, I.min_pts, core, labels, off, ids, samples)
+    """The 10M-point 5D mixed workload (FP32, minPts 10) on sampled outputs,
+    with the link certificate."""
+    assert _full_size_checked(synth.spreader_5d_10m(eps=eps), 5, 5) > 0
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("eps", [1000.0, 2000.0])
+@pytest.mark.parametrize("eps", [500.0, 1000.0, 2000.0])
 def test_spreader_7d_full_size_sampled(eps):
-    """The 10M-point 7D varying-density workload (FP32, minPts 100) on sampled outputs."""
-    I = synth.spreader_7d_10m(eps=eps)
-    ctx = DBSCAN(len(I.points), 7)
-    r = ctx.run(torch.from_numpy(I.points).cuda(), I.eps, I.min_pts)
-    core, labels = r.core.cpu().numpy(), r.labels.cpu().numpy()
-    off, ids = r.border_offsets.cpu().numpy(), r.border_ids.cpu().numpy()
-    rng = np.random.default_rng(7)
-    samples = np.sort(rng.choice(len(I.points), 2000, replace=False))
-    _sampled_invariants(I.points, I.eps, I.min_pts, core, labels, off, ids, samples)
+    """The 10M-point 7D varying-density workload (FP32, minPts 100) on sampled
+    outputs, with the link certificate (eps 500 needs 70-bit cell keys)."""
+    assert _full_size_checked(synth.spreader_7d_10m(eps=eps), 7, 7) > 0
 
 
 def test_highdim_list_buffer_grows():

@@ -18,7 +18,8 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
-from paper_1912_06255_gb300 import DBSCAN, DbscanError, dbscan  # noqa: E402
+from paper_1912_06255_gb300 import DBSCAN, DbscanError, _lib, dbscan  # noqa: E402
+from _certify import check_links  # noqa: E402
 
 
 def _run(X, eps, mp, **kw):
@@ -121,21 +122,70 @@ def test_spreader_3d_scaled():
     assert st["num_cells"] > 1000 and st["num_pairs_tested"] > 0
 
 
-@pytest.mark.slow
-def test_spreader_3d_full_size():
-    """The full 2,000,000-point 3D workload (FP32 input, FP32 band + FP64
-    recheck), in the configuration the benchmark times, against the full
-    oracle run."""
+@pytest.fixture(scope="module")
+def c1_full():
+    """The full 2,000,000-point 3D workload and its full oracle run (once)."""
     I = synth.spreader_3d_2m()
-    t = torch.from_numpy(I.points).cuda()
-    ctx = DBSCAN(len(I.points), 3)
-    r = ctx.run(t, I.eps, I.min_pts, border=True)
+    return I, oracle.dbscan(I.points, I.eps, I.min_pts)
+
+
+def _check_full(ctx, I, exp, tag):
+    r = ctx.run(torch.from_numpy(I.points).cuda(), I.eps, I.min_pts, border=True)
     torch.cuda.synchronize()
-    core, labels, off, ids = oracle.dbscan(I.points, I.eps, I.min_pts)
-    assert np.array_equal(r.core.cpu().numpy(), core)
-    assert np.array_equal(r.labels.cpu().numpy(), labels)
-    assert np.array_equal(r.border_offsets.cpu().numpy(), off)
-    assert np.array_equal(r.border_ids.cpu().numpy(), ids)
+    for name, g, e in zip(("core", "labels", "border_offsets", "border_ids"),
+                          (r.core, r.labels, r.border_offsets, r.border_ids), exp):
+        g = g.cpu().numpy()
+        if not np.array_equal(g, e):
+            bad = np.flatnonzero(g != e)[:10] if g.shape == e.shape else "shape"
+            raise AssertionError(f"{tag}: {name} differs at {bad}")
+    return r
+
+
+# Settings the benchmark's autotuner has chosen on this workload (list order, one
+# wave, 8 cells per work item), the defaults, and the other corners of the knobs.
+C1_SETTINGS = {
+    "default": {},
+    "list-1wave-8cells": {"schedule": 1, "connect_waves": 1, "connect_cells": 8},
+    "list-2waves-4cells": {"schedule": 1, "connect_waves": 2, "connect_cells": 4},
+    "size-1wave-1cell-2bps": {"schedule": 0, "connect_waves": 1, "connect_cells": 1, "blocks_per_sm": 2},
+    "small-cells-no-pairboxes": {"small_cells": 1 << 30, "pair_boxes": 0},
+    "no-cell-bounds": {"cell_bounds": 0},
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("setting", sorted(C1_SETTINGS))
+def test_spreader_3d_full_size(c1_full, setting):
+    """The full 2,000,000-point 3D workload (FP32 input, FP32 band + FP64
+    recheck) against the full oracle run, in each setting the benchmark can
+    time."""
+    I, exp = c1_full
+    ctx = DBSCAN(len(I.points), 3)
+    ctx.set_tuning(C1_SETTINGS[setting])
+    _check_full(ctx, I, exp, setting)
+
+
+@pytest.mark.slow
+def test_spreader_3d_full_size_as_benchmarked(c1_full):
+    """The benchmark's own procedure on the full 3D workload: log and train the
+    pair scheduler on the held-out input (seed 2001), autotune there, then run
+    the chosen setting and the learned schedule on the timed input; both
+    against the full oracle run, the learned one with its link certificate."""
+    I, exp = c1_full
+    H = synth.spreader_3d_2m(seed=2001)
+    ctx = DBSCAN(len(I.points), 3)
+    ctx.enable_pair_log(1 << 24)
+    ctx.run(torch.from_numpy(H.points).cuda(), H.eps, H.min_pts, border=False)
+    ctx.train_scheduler(epochs=30, batch=4096, lr=3e-3, seed=1)
+    ctx.enable_pair_log(0)
+    choice = ctx.autotune(torch.from_numpy(H.points).cuda(), H.eps, H.min_pts, reps=2)
+    _check_full(ctx, I, exp, f"autotuned {choice}")
+    ctx.set_option(1, 2)  # the learned schedule
+    ctx.set_option(_lib.OPT_WITNESS, 1)
+    r = _check_full(ctx, I, exp, "learned")
+    rep, links = ctx.link_witnesses()
+    check_links(I.points, I.eps, exp[0], exp[1], rep.cpu().numpy(), links.cpu().numpy(),
+                num_core_cells=r.stats["num_core_cells"])
 
 
 def test_edge_cases():
@@ -238,3 +288,30 @@ def test_border_ids_without_offsets_in_the_run():
     assert st == 0
     assert np.array_equal(ids.cpu().numpy(), exp[3])
     assert np.array_equal(r.labels.cpu().numpy(), exp[1])
+
+
+@pytest.mark.parametrize("schedule", ["size", "none", "learned"])
+@pytest.mark.parametrize("cell_bounds", [True, False])
+@pytest.mark.parametrize("d", [2, 3, 6])
+def test_link_witnesses(schedule, cell_bounds, d):
+    """Every union the run makes is recorded with a pair of core points within
+    eps; with the cell representatives they certify each cluster as one
+    connected graph of verified eps-edges, and the run still matches the
+    oracle with the recording on."""
+    X = synth.random_small(60 + d, 8000, d, dtype=np.float32)
+    eps, mp = {2: (0.2, 6), 3: (0.3, 8), 6: (0.9, 10)}[d]
+    ctx = DBSCAN(len(X), d, schedule=schedule, cell_bounds=cell_bounds)
+    ctx.set_option(_lib.OPT_WITNESS, 1)
+    r = ctx.run(torch.from_numpy(X).cuda(), eps, mp)
+    exp = oracle.dbscan(X, eps, mp)
+    assert np.array_equal(r.core.cpu().numpy(), exp[0]) and np.array_equal(r.labels.cpu().numpy(), exp[1])
+    rep, links = ctx.link_witnesses()
+    ncl = check_links(X, eps, exp[0], exp[1], rep.cpu().numpy(), links.cpu().numpy(),
+                      num_core_cells=r.stats["num_core_cells"])
+    assert ncl > 1
+    # without the option there is nothing to export
+    ctx.set_option(_lib.OPT_WITNESS, 0)
+    ctx.run(torch.from_numpy(X).cuda(), eps, mp)
+    with pytest.raises(DbscanError) as e:
+        ctx.link_witnesses()
+    assert e.value.status == 8

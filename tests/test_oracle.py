@@ -219,3 +219,36 @@ def test_sample_queries_agree_with_definition():
     assert (cnt == (D2 <= eps * eps).sum(1)).all()
     nb = oracle.neighbors(X, eps, 3)
     assert nb.tolist() == np.flatnonzero(((X - X[3]) ** 2).sum(1) <= eps * eps).tolist()
+
+
+def test_within_pairs_pins():
+    """The pairwise predicate (used to verify link witnesses of GPU runs):
+    exact-eps lattice pairs are in, their nextafter neighbours and diagonals
+    out (Sec. 2 is inclusive), SciPy's distances agree away from the boundary,
+    and each pair is taken in its own order (a swapped or shifted index would
+    fail the neighbour check)."""
+    from scipy.spatial.distance import cdist
+    # 3-4-5 and 1-2-2 pairs at exactly eps; nextafter below eps is out
+    X = np.array([[0.0, 0.0, 0.0], [3.0, 4.0, 0.0], [1.0, 2.0, 2.0], [0.0, 0.0, 5.0]])
+    got = oracle.within_pairs(X, 5.0, [[0, 1], [1, 0], [0, 3], [1, 3], [0, 2]])
+    assert got.tolist() == [True, True, True, False, True]
+    assert not oracle.within_pairs(X, math.nextafter(5.0, 0.0), [[0, 1]]).any()
+    assert oracle.within_pairs(X, 3.0, [[0, 2]]).all()
+    assert not oracle.within_pairs(X, math.nextafter(3.0, 0.0), [[0, 2]]).any()
+    # random pairs against SciPy, skipping the 1e-9 band around eps
+    rng = np.random.default_rng(41)
+    for d in (1, 3, 7):
+        Y = rng.random((400, d)) * 4.0
+        pr = rng.integers(0, 400, (5000, 2))
+        eps = 1.1
+        dist = cdist(Y, Y)[pr[:, 0], pr[:, 1]]
+        keep = np.abs(dist - eps) > 1e-9
+        got = oracle.within_pairs(Y, eps, pr)
+        assert np.array_equal(got[keep], (dist <= eps)[keep])
+    # against the neighbour scan: pairs (p, q) for all q select exactly neighbors(p)
+    Z = synth.random_small(6, 800, 3)
+    for p in (0, 17, 799):
+        pr = np.stack([np.full(800, p), np.arange(800)], 1)
+        assert np.flatnonzero(oracle.within_pairs(Z, 0.35, pr)).tolist() == oracle.neighbors(Z, 0.35, p).tolist()
+    with pytest.raises(RuntimeError):
+        oracle.within_pairs(Z, 0.35, [[0, 800]])
