@@ -166,6 +166,8 @@ typedef struct {
        learned schedule's pair list would exceed 2^31 pairs (its fallback). */
     int32_t schedule_used;
     int32_t reserved;
+    /* rho of the run's connectivity rule: 0 = exact DBSCAN (dbscan_set_approx) */
+    double rho;
 } dbscan_stats;
 
 /*
@@ -391,6 +393,24 @@ dbscan_status dbscan_autotune(dbscan_ctx *ctx, const void *d_points, int64_t n, 
 dbscan_status dbscan_autotune_batch(dbscan_ctx *ctx, const dbscan_instance *host_desc, int count,
                                     const void *d_points, int ld, int dtype, int reps, dbscan_tuning *out,
                                     void *stream);
+
+/*
+ * rho-approximate DBSCAN (the relaxed problem of Gan and Tao, Sec. 2): rho > 0
+ * lets core points farther apart than eps but within eps(1 + rho) connect, so
+ * several clusterings are valid; rho = 0 (the default) is exact DBSCAN.  The
+ * following runs and batches of the context keep the core rule and the
+ * border rule at eps and decide the connectivity of neighbouring core cells
+ * (Algorithm 3) with the threshold r = fl(eps * fl(1 + rho)): a pair of core
+ * points joins two cells iff sum_i (p_i - q_i)^2 <= fl(r * r) in FP64 (the
+ * FP32 band with recheck applies to r as it does to eps), and the core-point
+ * boxes settle a pair when all of their pairs are within r, or none is.
+ * Every pair of core points within eps lies in one cell or in neighbouring
+ * cells, so it is always joined, and no join is longer than r: the result is
+ * a valid rho-approximate clustering (Sec. 5.2 answers the same problem with
+ * approximate range counts on a quadtree).  Cluster names and border sets
+ * follow the exact conventions.  0 <= rho <= 1e6, else INVALID_ARG.
+ */
+dbscan_status dbscan_set_approx(dbscan_ctx *ctx, double rho);
 
 /* Counters of the last run (host copy; no device work). */
 dbscan_status dbscan_get_stats(const dbscan_ctx *ctx, dbscan_stats *out);

@@ -55,7 +55,7 @@ class DBSCAN:
 
     def __init__(self, max_points: int, max_dim: int, precision: str = "fp32",
                  schedule: str = "size", collect_stats: bool = False, max_iters: int | None = None,
-                 cell_bounds: bool = True, graph: bool = True):
+                 cell_bounds: bool = True, graph: bool = True, rho: float = 0.0):
         self.lib = _lib.load()
         self.ctx = ctypes.c_void_p()
         _lib.check(self.lib.dbscan_create(ctypes.byref(self.ctx), int(max_points), int(max_dim)),
@@ -70,6 +70,12 @@ class DBSCAN:
         self.set_option(_lib.OPT_BATCH_GRAPH, int(bool(graph)))
         if max_iters is not None:
             self.set_option(_lib.OPT_MAX_ITERS, int(max_iters))
+        if rho:
+            self.set_approx(rho)
+
+    def set_approx(self, rho: float) -> None:
+        """rho-approximate connectivity for the following runs (0 = exact DBSCAN)."""
+        _lib.check(self.lib.dbscan_set_approx(self.ctx, float(rho)), "dbscan_set_approx")
 
     def set_option(self, option: int, value: int) -> None:
         _lib.check(self.lib.dbscan_set_option(self.ctx, option, int(value)), "dbscan_set_option")
@@ -297,11 +303,12 @@ class DBSCAN:
 
 
 def dbscan(points, eps: float, min_pts: int, precision: str = "fp32", schedule: str = "size",
-           border: bool = True, collect_stats: bool = False, cell_bounds: bool = True) -> Result:
-    """One-shot exact DBSCAN of a CUDA tensor [n, d] (float32 or float64)."""
+           border: bool = True, collect_stats: bool = False, cell_bounds: bool = True, rho: float = 0.0) -> Result:
+    """One-shot DBSCAN of a CUDA tensor [n, d] (float32 or float64): exact, or
+    rho-approximate when rho > 0."""
     n, d = points.shape
     ctx = DBSCAN(max(int(n), 1), int(d), precision=precision, schedule=schedule,
-                 collect_stats=collect_stats, cell_bounds=cell_bounds)
+                 collect_stats=collect_stats, cell_bounds=cell_bounds, rho=rho)
     try:
         return ctx.run(points, eps, min_pts, border=border)
     finally:

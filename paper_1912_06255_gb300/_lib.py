@@ -47,6 +47,7 @@ class Stats(ctypes.Structure):
         ("kernel_launches", ctypes.c_int64), ("phase_ms", ctypes.c_float * 8),
         ("markcore_pair_bound", ctypes.c_int64),
         ("schedule_used", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("rho", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -85,6 +86,7 @@ SIGNATURES = {
     "dbscan_run_batch": (_I32, [_P, ctypes.POINTER(Instance), _I32, _P, _I32, _I32, _P, _P, _P,
                                 ctypes.POINTER(_I64), _P]),
     "dbscan_get_stats": (_I32, [_P, ctypes.POINTER(Stats)]),
+    "dbscan_set_approx": (_I32, [_P, _D]),
     "dbscan_train_scheduler": (_I32, [_P, _I32, _I32, ctypes.c_float, ctypes.c_uint64, _P]),
     "dbscan_scheduler_weights": (_I32, [_P, _P, _I32, _I32]),
     "dbscan_scheduler_loss_grad": (_I32, [_P, _P, _P, _I64, _P, _P]),

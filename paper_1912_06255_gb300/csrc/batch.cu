@@ -129,7 +129,8 @@ k_batch_bbox(const T *__restrict__ X, int ld, long long n_total, const dbscan_in
 
 // One thread per instance: its grid and thresholds from its box.
 __global__ void k_batch_inst(const dbscan_instance *__restrict__ desc, int count, const long long *__restrict__ bb,
-                             int want_fp32, int f64, int key_limit, Inst *__restrict__ inst, DevCounters *ctr) {
+                             int want_fp32, int f64, int key_limit, double rho, int ld, Inst *__restrict__ inst,
+                             DevCounters *ctr) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     const dbscan_instance D = desc[i];
@@ -142,8 +143,12 @@ __global__ void k_batch_inst(const dbscan_instance *__restrict__ desc, int count
     }
     if (D.n > 0 && b[2 * kMaxDim] != 0) set_error(ctr, DBSCAN_ERR_INVALID_ARG, i);
     int fp32 = 0;
-    const int st = build_inst(I, D.eps, D.min_pts, (int)D.n, D.d, lo, hi, f64 != 0, want_fp32 != 0, key_limit, &fp32);
+    const int st =
+        build_inst(I, D.eps, D.min_pts, (int)D.n, D.d, lo, hi, f64 != 0, want_fp32 != 0, key_limit, &fp32, rho);
     if (st != DBSCAN_OK) set_error(ctr, st, i);
+    // the key interleaves all ld stored coordinates (the unused ones are zero),
+    // so an instance of lower dimension still needs ld * bits key bits
+    else if (ld * I.bits > key_limit) set_error(ctr, DBSCAN_ERR_KEY_OVERFLOW, i);
     else if (want_fp32 && !fp32) set_error(ctr, DBSCAN_ERR_INVALID_ARG, i);
     I.row0 = (int)D.row0;
     inst[i] = I;
@@ -172,7 +177,8 @@ cudaError_t ensure_batch(dbscan_ctx *c, int count) {
 
 // Run-wide pieces shared with capi.cu.
 dbscan_status gbdb_enqueue_batch_prologue(dbscan_ctx *c, const void *d_points, int ld, int dtype, int count,
-                                          long long n_total, int want_fp32, int key_limit, cudaStream_t s) {
+                                          long long n_total, int want_fp32, int key_limit, double rho,
+                                          cudaStream_t s) {
     if (cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s) != cudaSuccess) return DBSCAN_ERR_CUDA;
     if (cudaMemcpyAsync(c->d_bdesc, c->h_bdesc, sizeof(dbscan_instance) * count, cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
@@ -188,7 +194,8 @@ dbscan_status gbdb_enqueue_batch_prologue(dbscan_ctx *c, const void *d_points, i
     }
     count_launch();
     k_batch_inst<<<(count + 127) / 128, 128, 0, s>>>(c->d_bdesc, count, c->d_bbox, want_fp32,
-                                                     dtype == DBSCAN_F64 ? 1 : 0, key_limit, c->d_binst, c->ctr);
+                                                     dtype == DBSCAN_F64 ? 1 : 0, key_limit, rho, ld, c->d_binst,
+                                                     c->ctr);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? DBSCAN_OK : DBSCAN_ERR_CUDA;
 }

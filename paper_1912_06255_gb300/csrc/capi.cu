@@ -193,7 +193,8 @@ static cudaError_t ensure_learned(dbscan_ctx *c, long long want = 0) {
 }
 
 dbscan_status gbdb_enqueue_batch_prologue(dbscan_ctx *c, const void *d_points, int ld, int dtype, int count,
-                                          long long n_total, int want_fp32, int key_limit, cudaStream_t s);
+                                          long long n_total, int want_fp32, int key_limit, double rho,
+                                          cudaStream_t s);
 dbscan_status gbdb_batch_buffers(dbscan_ctx *c, const dbscan_instance *h, int count);
 void gbdb_batch_free(dbscan_ctx *c);
 
@@ -306,14 +307,27 @@ static dbscan_status enqueue_hash_cells(dbscan_ctx *c, const RunParams &P, int S
     S.orig = c->orig;
     S.cell_of = c->cell_of;
     S.cell_inst = c->cell_inst;
-    // whole 8-bit digits only: the (at most 7) lowest key bits left out of the
-    // order only shuffle cells inside a block of 2^7 consecutive Z positions
-    const int whole = sort_bits >= 8 ? sort_bits & ~7 : sort_bits;
-    S.key_lo = sort_lo + (sort_bits - whole);
-    S.key_bits = whole;
-    // the Bloom filter pays only when the hash table does not fit in L2
-    const bool use_bloom = 16 * c->hcap > ((uint64_t)96 << 20);
+    // d = 2, 3: neighbours through supercells (blocks of 2^d cells), which
+    // must be consecutive in the cell order: every key bit above the lowest d
+    // is sorted, in whole 8-bit digits.  Otherwise whole digits only: the (at
+    // most 7) lowest key bits left out of the order only shuffle cells inside a
+    // block of 2^7 consecutive Z positions.
+    S.super = d_enum == 2 || d_enum == 3;
+    if (S.super) {
+        const int top = sort_lo + sort_bits;
+        const int digits = std::max(1, (sort_bits - d_enum + 7) / 8);
+        S.key_lo = std::max(sort_lo, top - 8 * digits);
+        S.key_bits = top - S.key_lo;
+    } else {
+        const int whole = sort_bits >= 8 ? sort_bits & ~7 : sort_bits;
+        S.key_lo = sort_lo + (sort_bits - whole);
+        S.key_bits = whole;
+    }
+    // the Bloom filter of the cell keys pays only when the hash table does not
+    // fit in L2 (the supercell path keeps its own filter in the same storage)
+    const bool use_bloom = !S.super && 16 * c->hcap > ((uint64_t)96 << 20);
     S.bloom = use_bloom ? c->bloom : nullptr;
+    S.bloom_all = c->bloom;
     S.bloom_lg = c->bloom_lg;
     if (use_bloom) CK(cudaMemsetAsync(c->bloom, 0, ((size_t)1 << c->bloom_lg) / 8, s));
     launch_semisort(d_points, dtype, P, SD, S, c->ctr, s);
@@ -321,11 +335,17 @@ static dbscan_status enqueue_hash_cells(dbscan_ctx *c, const RunParams &P, int S
     // 4. cell boxes, neighbour lists
     mark(3);
     if (P.box) launch_boxes(SD, c->pf, c->cell_start, c->ctr, c->blo, c->bhi, s);
-    int n_near = 1;
-    for (int j = 0; j < d_enum; ++j) n_near *= 3;
-    launch_neighbors(c->cell_key, c->ht, c->hcap, S.bloom, c->bloom_lg, P, offs_for(c, d_enum), c->noff[d_enum],
-                     n_near - 1, c->blo, c->bhi, c->cell_start, c->nbr_cnt, c->nbr_near,
-                     P.mc_small_nbr > 0 && P.mc_small_nbr < (1 << 30) ? c->nbr_pts : nullptr, c->nbr, c->ctr, s);
+    int *nbr_pts = P.mc_small_nbr > 0 && P.mc_small_nbr < (1 << 30) ? c->nbr_pts : nullptr;
+    if (S.super) {
+        launch_neighbors_super(S, P, c->noff[d_enum], c->blo, c->bhi, c->cell_start, c->nbr_cnt, c->nbr_near,
+                               nbr_pts, c->nbr, c->ctr, s);
+    } else {
+        int n_near = 1;
+        for (int j = 0; j < d_enum; ++j) n_near *= 3;
+        launch_neighbors(c->cell_key, c->ht, c->hcap, S.bloom, c->bloom_lg, P, offs_for(c, d_enum),
+                         c->noff[d_enum], n_near - 1, c->blo, c->bhi, c->cell_start, c->nbr_cnt, c->nbr_near,
+                         nbr_pts, c->nbr, c->ctr, s);
+    }
     c->nbr_cur = c->nbr;
     c->nbr_off_cur = nullptr;
     return DBSCAN_OK;
@@ -680,6 +700,12 @@ dbscan_status dbscan_get_option(const dbscan_ctx *c, int option, int64_t *value)
     }
 }
 
+dbscan_status dbscan_set_approx(dbscan_ctx *c, double rho) {
+    if (!c || !(rho >= 0.0) || !(rho <= 1e6)) return DBSCAN_ERR_INVALID_ARG;
+    c->rho = rho;
+    return DBSCAN_OK;
+}
+
 dbscan_status dbscan_get_stats(const dbscan_ctx *c, dbscan_stats *out) {
     if (!c || !out) return DBSCAN_ERR_INVALID_ARG;
     *out = c->stats;
@@ -702,6 +728,7 @@ static dbscan_status run_once(dbscan_ctx *c, const void *d_points, int64_t n, in
     cudaStream_t s = (cudaStream_t)stream;
     std::memset(&c->stats, 0, sizeof(c->stats));
     c->stats.schedule_used = c->sched;
+    c->stats.rho = c->rho;
     c->stats.n = n;
     c->stats.d = d;
     if (n == 0) {
@@ -758,7 +785,7 @@ static dbscan_status run_once(dbscan_ctx *c, const void *d_points, int64_t n, in
         // 64-bit keys below 5 dimensions, 128-bit keys of at most 15 bits per dimension above
         const int key_limit = d <= kMaxEnumDim ? 63 : 15 * d;
         const int st = build_inst(I, eps, min_pts, (int)n, d, lo, hi, f64, c->precision == DBSCAN_PREC_FP32_RECHECK,
-                                  key_limit, &fp32);
+                                  key_limit, &fp32, c->rho);
         if (st != DBSCAN_OK) return (dbscan_status)st;
         I.row0 = 0;
         P.min_pts = I.thr.min_pts;
@@ -767,7 +794,10 @@ static dbscan_status run_once(dbscan_ctx *c, const void *d_points, int64_t n, in
         P.hi = I.thr.hi;
         c->stats.key_bits = d * I.bits;
         // d <= 4: the m cell keys, whole digits only; d >= 5: the n point keys
-        c->stats.radix_passes = d <= kMaxEnumDim ? std::max(1, d * I.bits / 8) : (d * I.bits + 7) / 8;
+        c->stats.radix_passes = d <= kMaxEnumDim
+                                    ? ((d == 2 || d == 3) ? std::max(1, (d * I.bits - d + 7) / 8)
+                                                          : std::max(1, d * I.bits / 8))
+                                    : (d * I.bits + 7) / 8;
         const int mode_sel = fp32 ? (f64 ? kF32FromF64 : kF32FromF32) : (f64 ? kF64FromF64 : kF64FromF32);
         c->last_mode_sel = mode_sel;
     }
@@ -812,6 +842,7 @@ static dbscan_status run_batch_once(dbscan_ctx *c, const dbscan_instance *hi, in
     cudaStream_t s = (cudaStream_t)stream;
     std::memset(&c->stats, 0, sizeof(c->stats));
     c->stats.schedule_used = c->sched;
+    c->stats.rho = c->rho;
     c->stats.n = total;
     c->stats.d = ld;
     if (total == 0) {
@@ -850,7 +881,7 @@ static dbscan_status run_batch_once(dbscan_ctx *c, const dbscan_instance *hi, in
     P.cell_inst = c->cell_inst;
     c->stats.precision = fp32_all ? DBSCAN_PREC_FP32_RECHECK : DBSCAN_PREC_FP64;
     c->stats.key_bits = 63;
-    c->stats.radix_passes = 7;
+    c->stats.radix_passes = ld >= 2 ? 8 : 7;
     const long long launches0 = g_launches;
     if (!c->table_clean) {
         CK(cudaMemsetAsync(c->ht, 0xff, sizeof(ulonglong2) * c->hcap, s));
@@ -864,14 +895,16 @@ static dbscan_status run_batch_once(dbscan_ctx *c, const dbscan_instance *hi, in
         if (c->phase_timing) cudaEventRecord(c->ev[0], s);
         if (c->phase_timing) cudaEventRecord(c->ev[1], s);
         dbscan_status e = gbdb_enqueue_batch_prologue(c, d_points, ld, dtype, count, total, fp32_all ? 1 : 0,
-                                                      P.inst_shift, s);
+                                                      P.inst_shift, c->rho, s);
         if (e != DBSCAN_OK) return e;
         return enqueue_core(c, P, D, SD, mode, d_points, dtype, ld, 0, 63, d_core, d_labels, d_border_offsets, s,
                             [&](int k) {
                                 if (c->phase_timing) cudaEventRecord(c->ev[k], s);
                             });
     };
-    const unsigned long long key[13] = {(unsigned long long)count, (unsigned long long)total,
+    unsigned long long rho_bits = 0;
+    std::memcpy(&rho_bits, &c->rho, sizeof rho_bits);
+    const unsigned long long key[14] = {(unsigned long long)count, (unsigned long long)total,
                                         (unsigned long long)(uintptr_t)d_points, (unsigned long long)ld,
                                         (unsigned long long)dtype, (unsigned long long)(uintptr_t)d_core,
                                         (unsigned long long)(uintptr_t)d_labels,
@@ -881,7 +914,7 @@ static dbscan_status run_batch_once(dbscan_ctx *c, const dbscan_instance *hi, in
                                                              (c->waves << 20) | (c->blocks_per_sm << 24)),
                                         (unsigned long long)c->mc_small_nbr ^ ((unsigned long long)c->lcap << 31),
                                         (unsigned long long)c->phase_timing, (unsigned long long)c->max_iters,
-                                        1ull | ((unsigned long long)c->witness << 1)};
+                                        1ull | ((unsigned long long)c->witness << 1), rho_bits};
     // phase timing records events between the steps: that run is enqueued
     // directly instead of replaying the graph
     if (!c->use_graph || c->phase_timing) {

@@ -449,7 +449,7 @@ k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict
             // eps -> not connected; every pair within eps -> connected
             int verdict = 0;
             if (use_box && cand) {
-                const Thr T = P.inst[inst_of_cell(P, a)].thr;
+                const Thr T = P.inst[inst_of_cell(P, a)].cthr;
                 const Bx<D> alo = load_box<D>(cblo, a), ahi = load_box<D>(cbhi, a);
                 const Bx<D> blo = load_box<D>(cblo, b), bhi = load_box<D>(cbhi, b);
                 if (boxes_min_d2<D>(alo, ahi, blo, bhi) > T.hi) verdict = -1;
@@ -482,7 +482,7 @@ k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict
                 if (lane == 0) again = uf_find(parent, sa, P.max_iters, ctr) == uf_find(parent, sb, P.max_iters, ctr);
                 if (__shfl_sync(0xffffffffu, again, 0)) { ++skipped; continue; }
                 ++tested;
-                const Thr T = P.inst[inst_of_cell(P, sa)].thr;
+                const Thr T = P.inst[inst_of_cell(P, sa)].cthr;
                 int2 wp;
                 const bool hit = sna >= snb ? bcp_warp<D, M>(sa0, sna, sb0, snb, cpf, cpd, P, T, rech, evals, wp)
                                             : bcp_warp<D, M>(sb0, snb, sa0, sna, cpf, cpd, P, T, rech, evals, wp);

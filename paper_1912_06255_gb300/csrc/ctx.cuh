@@ -34,6 +34,7 @@ struct dbscan_ctx {
     int blocks_per_sm = 0;  // DBSCAN_OPT_BLOCKS_PER_SM
     int mc_small_nbr = 0;   // DBSCAN_OPT_SMALL_CELLS
     int pair_box = 1;       // DBSCAN_OPT_PAIR_BOXES
+    double rho = 0.0;       // dbscan_set_approx: 0 = exact DBSCAN
     int witness = 0;        // DBSCAN_OPT_WITNESS
     int2 *wit = nullptr;    // [max_points] link witnesses (allocated while the option is on)
     long long wit_count = 0;
@@ -74,7 +75,7 @@ struct dbscan_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t cap_stream = nullptr;
     long long graph_launches = 0;  // kernel nodes of the captured graph
-    unsigned long long graph_key[13] = {0};
+    unsigned long long graph_key[14] = {0};
     float4 *blo = nullptr, *bhi = nullptr, *cblo = nullptr, *cbhi = nullptr;  // cell / core-point boxes
     float4 *ccent = nullptr;  // core-point centroids (learned schedule)
     // learned schedule: network (device), its Adam state, pair list, pair log

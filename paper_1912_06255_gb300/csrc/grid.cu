@@ -350,7 +350,21 @@ void launch_semisort(const void *X, int dtype, const RunParams &P, int SD, const
     }
 }
 
-void launch_table_reset(const Semisort &S, DevCounters *ctr, cudaStream_t s) {
+// Empty the supercell slots (the cells' slots were emptied before).
+__global__ void __launch_bounds__(256)
+k_super_reset(ulonglong2 *__restrict__ ht, const uint32_t *__restrict__ sslots, const DevCounters *ctr) {
+    const int ms = ctr->ms;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ms; i += gridDim.x * blockDim.x)
+        ht[sslots[i]] = make_ulonglong2(kEmptyKey, 0);
+}
+
+void launch_table_reset(const Semisort &S, DevCounters *ctr, cudaStream_t s, bool end_of_run) {
+    if (end_of_run && S.super) {
+        const int g = grid_for((const void *)k_super_reset, 256);
+        k_super_reset<<<g, 256, 0, s>>>(S.ht, S.slots, ctr);
+        count_launch();
+        return;
+    }
     int g = grid_for((const void *)k_table_reset, 256);
     k_table_reset<<<g, 256, 0, s>>>(S.ht, S.hcnt, S.slots, ctr); count_launch();
 }
@@ -505,7 +519,9 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
         const long long base = (long long)c * noff;
         Bx<D> clo = zero_box<D>(), chi = clo;
         if (P.box) { clo = load_box<D>(blo, c); chi = load_box<D>(bhi, c); }
-        const float hi_thr = I.thr.hi;
+        // the wider of the two thresholds (rho-approximate connectivity keeps
+        // the cell pairs within eps(1 + rho); MarkCore and border test at eps)
+        const float hi_thr = I.cthr.hi;
         int cnt = 0, near = 0, pts = 0;
         for (int o0 = 0; o0 < noff; o0 += 32 * NB_U) {
             uint64_t key[NB_U], slot[NB_U];
@@ -546,7 +562,7 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
                         s = (s + 1) & mask;
                         e[u] = ht[s];
                     }
-                    // drop cells whose points are all farther than eps from all of c's
+                    // drop cells whose points are all farther than eps (eps(1 + rho)) from all of c's
                     if (h >= 0 && P.box && boxes_min_d2<D>(clo, chi, load_box<D>(blo, h), load_box<D>(bhi, h)) > hi_thr)
                         h = -1;
                 }
@@ -571,6 +587,303 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
         total += cnt;
     }
     if (lane == 0 && total) atomicAdd((unsigned long long *)&ctr->E, (unsigned long long)total);
+}
+
+// ------------------------------------------------------- neighbours, d = 2, 3
+// NeighborCells(g) through supercells.  A supercell is a block of 2^D cells
+// whose coordinates agree after >> 1; its key is the cell key without its
+// lowest D bits (sk = key >> D), so in Z order its cells are consecutive (the
+// cell sort orders every bit above the lowest D).  The candidate cells of any
+// cell of supercell S (|delta_j| <= 2, the offset rule) lie in the 3^D
+// supercells S + {-1, 0, 1}^D, so one warp per supercell probes those 3^D
+// supercells once in a hash of the non-empty supercells (sk -> first cell and
+// cell count), gathers their cells (at most 3^D * 2^D) and applies the exact
+// offset rule, sum_j max(|delta_j| - 1, 0)^2 <= d, and the box test to every
+// pair of an own cell and a candidate.  That is 9 (2D) or 27 (3D) probes per
+// supercell instead of 24 or 124 per cell.  The supercell hash takes the first
+// 2^ceil(log2 2 ms) slots of the cell hash table, whose cells' slots are
+// emptied first (the cells need no hash once they are grouped); a Bloom filter
+// of the supercell keys (8 bits per cell) keeps the probes of empty supercells
+// in L2 when that table does not fit there.
+__host__ __device__ __forceinline__ int super_bloom_lg(int m, int bloom_lg) {
+    const uint64_t cap = hash_capacity(m);  // bounds the supercell table (ms <= m)
+    if (cap * 16 <= (64ull << 20)) return -1;
+    const int lg = hash_log2(cap) + 2;
+    return lg < bloom_lg ? lg : bloom_lg;
+}
+
+// flag[c] = 1 iff cell c is the first of its supercell; clears the Bloom
+// filter of the supercell keys.
+template <int D>
+__global__ void __launch_bounds__(256)
+k_super_flags(const uint64_t *__restrict__ cell_key, int *__restrict__ flag, unsigned *__restrict__ bloom,
+              int bloom_lg, const DevCounters *ctr) {
+    if (ctr->err) return;
+    const int m = ctr->m;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (long long c = t0; c < m; c += stride)
+        flag[c] = (c == 0 || (cell_key[c] >> D) != (cell_key[c - 1] >> D)) ? 1 : 0;
+    const int blg = super_bloom_lg(m, bloom_lg);
+    if (blg > 0)
+        for (long long w = t0; w < (1ll << (blg - 5)); w += stride) bloom[w] = 0u;
+}
+
+// pos = exclusive scan of the flags (pos[m] = ms supercells).  Each supercell
+// enters the hash with value (first cell | cell count << 32); its first cell
+// goes to sc_first[pos] and its slot to sslots[pos] (for the reset).
+template <int D>
+__global__ void __launch_bounds__(256)
+k_super_insert(const uint64_t *__restrict__ cell_key, const int *__restrict__ pos, ulonglong2 *__restrict__ ht,
+               uint32_t *__restrict__ sslots, int *__restrict__ sc_first, unsigned *__restrict__ bloom, int bloom_lg,
+               DevCounters *ctr) {
+    if (ctr->err) return;
+    const int m = ctr->m;
+    const int ms = pos[m];
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr->ms = ms;
+    const uint64_t cap = hash_capacity(ms);
+    const int lg = hash_log2(cap);
+    const uint64_t mask = cap - 1;
+    const int blg = super_bloom_lg(m, bloom_lg);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+        const int p = pos[c];
+        if (pos[c + 1] == p) continue;  // not the first cell of its supercell
+        int k = 1;
+        while (c + k < m && k < (1 << D) && pos[c + k + 1] == pos[c + k]) ++k;
+        const uint64_t sk = cell_key[c] >> D;
+        sc_first[p] = c;
+        uint64_t s = hash_slot(sk, lg);
+        bool ok = false;
+        for (uint64_t it = 0; it <= mask; ++it) {
+            if (ht[s].x == kEmptyKey &&
+                atomicCAS(&ht[s].x, (unsigned long long)kEmptyKey, (unsigned long long)sk) == kEmptyKey) {
+                ht[s].y = (unsigned long long)(unsigned)c | ((unsigned long long)k << 32);
+                ok = true;
+                break;
+            }
+            s = (s + 1) & mask;
+        }
+        if (!ok) {
+            set_error(ctr, DBSCAN_ERR_CAPACITY, 12);
+            s = 0;
+        }
+        sslots[p] = (uint32_t)s;
+        if (blg > 0) bloom_add(bloom, sk, blg);
+    }
+}
+
+constexpr int NBS_WARPS = 8;  // warps per block of k_neighbors_super
+
+template <int D>
+__global__ void __launch_bounds__(32 * NBS_WARPS)
+k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict__ ht,
+                  const unsigned *__restrict__ bloom, int bloom_lg, const int *__restrict__ sc_first,
+                  const int *__restrict__ cell_start, int *__restrict__ nbr_pts, RunParams P, int stride,
+                  const float4 *__restrict__ blo, const float4 *__restrict__ bhi, int *__restrict__ nbr_cnt,
+                  int *__restrict__ nbr_near, int *__restrict__ nbr, DevCounters *ctr) {
+    constexpr int K = 1 << D;                  // cells per supercell
+    constexpr int NS = D == 2 ? 9 : 27;        // supercells probed, the own one included
+    constexpr int CH = (NS * K + 31) / 32;     // 32-candidate chunks
+    __shared__ int s_cc[NBS_WARPS][K][D];      // own cells' coordinates
+    __shared__ float4 s_lo[NBS_WARPS][K], s_hi[NBS_WARPS][K];
+    __shared__ unsigned s_near[NBS_WARPS][CH][K], s_far[NBS_WARPS][CH][K];
+    if (ctr->err) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int m = ctr->m, ms = ctr->ms;
+    const uint64_t cap = hash_capacity(ms);
+    const int lg = hash_log2(cap);
+    const uint64_t mask = cap - 1;
+    const int blg = super_bloom_lg(m, bloom_lg);
+    long long total = 0;
+    for (int si = warp_id_global(); si < ms; si += warps_global()) {
+        const int c0 = sc_first[si];
+        int k = (si + 1 < ms ? sc_first[si + 1] : m) - c0;
+        if (k > K || k < 1) {  // cannot happen for a sorted cell table
+            if (lane == 0) set_error(ctr, DBSCAN_ERR_CAPACITY, 13);
+            k = k < 1 ? 0 : K;
+        }
+        const int ii = inst_of_cell(P, c0);
+        const Inst &I = P.inst[ii];
+        const uint64_t ibits = P.ninst > 1 ? ((uint64_t)ii << P.inst_shift) : 0;
+        const float hi_thr = I.cthr.hi;  // eps, or eps(1 + rho) for approximate connectivity
+        __syncwarp();
+        if (lane < k) {
+            int cc[kMaxDim];
+            morton_decode(cell_key[c0 + lane] ^ ibits, D, I.bits, cc);
+#pragma unroll
+            for (int j = 0; j < D; ++j) s_cc[w][lane][j] = cc[j];
+            if (P.box) {
+                s_lo[w][lane] = blo[c0 + lane];
+                s_hi[w][lane] = bhi[c0 + lane];
+            }
+        }
+        __syncwarp();
+        // lane l < NS probes supercell S + o(l); lane 0 takes S itself
+        const uint64_t skey = (cell_key[c0] ^ ibits) >> D;
+        int t0 = 0, kt = 0;
+        if (lane < NS && k > 0) {
+            const int ctr_i = (NS - 1) / 2;
+            int t = lane == 0 ? ctr_i : (lane <= ctr_i ? lane - 1 : lane);
+            int o[D];
+            bool in = true;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                o[j] = t % 3 - 1;
+                t /= 3;
+                const int v = (s_cc[w][0][j] >> 1) + o[j];
+                in = in && v >= 0 && v <= (I.kmax[j] >> 1);
+            }
+            if (in) {
+                const uint64_t key = morton_offset<D>(skey, o) | (ibits >> D);
+                if (blg <= 0 || bloom_may_have(bloom, key, blg)) {
+                    uint64_t s = hash_slot(key, lg);
+                    for (uint64_t it = 0; it <= mask; ++it) {
+                        const ulonglong2 e = ht[s];
+                        if (e.x == key) {
+                            t0 = (int)(unsigned)(e.y & 0xffffffffu);
+                            kt = (int)(e.y >> 32);
+                            break;
+                        }
+                        if (e.x == kEmptyKey) break;
+                        s = (s + 1) & mask;
+                    }
+                }
+            }
+        }
+        // the candidates, flattened over the lanes in probe order
+        int incl = kt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        const int excl = incl - kt;
+        const int ncand = __shfl_sync(0xffffffffu, incl, 31);
+        const int nch = (ncand + 31) >> 5;
+        int hreg[CH];
+        int hsz[CH];
+#pragma unroll
+        for (int ch = 0; ch < CH; ++ch) {
+            hreg[ch] = -1;
+            hsz[ch] = 0;
+            if (ch >= nch) continue;
+            const int f = ch * 32 + lane;
+            int j = 0;  // owner lane: the last lane whose range starts at or before f
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int ex = __shfl_sync(0xffffffffu, excl, (j + step) & 31);
+                if (j + step < 32 && ex <= f) j += step;
+            }
+            const int h = __shfl_sync(0xffffffffu, t0, j) + f - __shfl_sync(0xffffffffu, excl, j);
+            const bool valid = f < ncand;
+            int hc[kMaxDim];
+            float4 hl = make_float4(0.f, 0.f, 0.f, 0.f), hh = hl;
+            if (valid) {
+                morton_decode(cell_key[h] ^ ibits, D, I.bits, hc);
+                if (P.box) {
+                    hl = blo[h];
+                    hh = bhi[h];
+                }
+                if (nbr_pts) hsz[ch] = cell_start[h + 1] - cell_start[h];
+                hreg[ch] = h;
+            }
+            for (int i = 0; i < k; ++i) {
+                bool near = false, far = false;
+                if (valid && h != c0 + i) {
+                    int g = 0, a = 0;
+#pragma unroll
+                    for (int jj = 0; jj < D; ++jj) {
+                        const int dl = abs(hc[jj] - s_cc[w][i][jj]);
+                        a = max(a, dl);
+                        const int e = max(dl - 1, 0);
+                        g += e * e;
+                    }
+                    bool pass = g <= I.d;
+                    if (pass && P.box) {
+                        Bx<D> al, ah, bl, bh;
+                        al.v[0] = s_lo[w][i];
+                        ah.v[0] = s_hi[w][i];
+                        bl.v[0] = hl;
+                        bh.v[0] = hh;
+                        pass = boxes_min_d2<D>(al, ah, bl, bh) <= hi_thr;
+                    }
+                    near = pass && a <= 1;
+                    far = pass && a > 1;
+                }
+                const unsigned nm = __ballot_sync(0xffffffffu, near);
+                const unsigned fm = __ballot_sync(0xffffffffu, far);
+                if (lane == 0) {
+                    s_near[w][ch][i] = nm;
+                    s_far[w][ch][i] = fm;
+                }
+            }
+        }
+        __syncwarp();
+        // counts per own cell (lane i), then the lists: adjacent cells first
+        int nn = 0, nf = 0;
+        if (lane < k) {
+            for (int ch = 0; ch < nch; ++ch) {
+                nn += __popc(s_near[w][ch][lane]);
+                nf += __popc(s_far[w][ch][lane]);
+            }
+            nbr_cnt[c0 + lane] = nn + nf;
+            nbr_near[c0 + lane] = nn;
+            total += nn + nf;
+        }
+        for (int i = 0; i < k; ++i) {
+            const long long base = (long long)(c0 + i) * stride;
+            int ncur = 0, fcur = __shfl_sync(0xffffffffu, nn, i);
+            int pts = 0;
+#pragma unroll
+            for (int ch = 0; ch < CH; ++ch) {
+                if (ch >= nch) break;
+                const unsigned nm = s_near[w][ch][i], fm = s_far[w][ch][i];
+                if ((nm >> lane) & 1u) {
+                    nbr[base + ncur + __popc(nm & lt)] = hreg[ch];
+                    pts += hsz[ch];
+                }
+                if ((fm >> lane) & 1u) {
+                    nbr[base + fcur + __popc(fm & lt)] = hreg[ch];
+                    pts += hsz[ch];
+                }
+                ncur += __popc(nm);
+                fcur += __popc(fm);
+            }
+            if (nbr_pts) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) pts += __shfl_xor_sync(0xffffffffu, pts, o);
+                if (lane == 0) nbr_pts[c0 + i] = pts;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+    if (lane == 0 && total) atomicAdd((unsigned long long *)&ctr->E, (unsigned long long)total);
+}
+
+void launch_neighbors_super(const Semisort &S, const RunParams &P, int stride, const float4 *blo,
+                            const float4 *bhi, const int *cell_start, int *nbr_cnt, int *nbr_near, int *nbr_pts,
+                            int *nbr, DevCounters *ctr, cudaStream_t s) {
+    // the cells' slots are free again: the supercells take the table
+    launch_table_reset(S, ctr, s, false);
+    int *pos = S.count;  // [m + 1], scratch until the compaction
+    int *sc_first = reinterpret_cast<int *>(S.rank_of);  // free once the points are scattered
+    auto go = [&](auto kf, auto ki, auto kn) {
+        int g = grid_for((const void *)kf, 256);
+        kf<<<g, 256, 0, s>>>(S.cell_key, pos, S.bloom_all, S.bloom_lg, ctr);
+        count_launch();
+        scan_i32_to_i32(pos, pos, 0, &ctr->m, P.n, S.part, s);
+        g = grid_for((const void *)ki, 256);
+        ki<<<g, 256, 0, s>>>(S.cell_key, pos, S.ht, S.slots, sc_first, S.bloom_all, S.bloom_lg, ctr);
+        count_launch();
+        g = grid_for((const void *)kn, 32 * NBS_WARPS);
+        kn<<<g, 32 * NBS_WARPS, 0, s>>>(S.cell_key, S.ht, S.bloom_all, S.bloom_lg, sc_first, cell_start, nbr_pts, P,
+                                        stride, blo, bhi, nbr_cnt, nbr_near, nbr, ctr);
+        count_launch();
+    };
+    if (P.d == 2) go(k_super_flags<2>, k_super_insert<2>, k_neighbors_super<2>);
+    else go(k_super_flags<3>, k_super_insert<3>, k_neighbors_super<3>);
 }
 
 void launch_neighbors(const uint64_t *cell_key, const ulonglong2 *ht, uint64_t hcap, const unsigned *bloom,

@@ -36,15 +36,23 @@ struct Semisort {
     int *orig, *cell_of;
     int *cell_inst;       // [m] instance of each cell (several instances only)
     int key_lo, key_bits; // key bits the cell sort orders by
-    unsigned *bloom;      // 2^bloom_lg bits: Bloom filter of the run's cell keys (cleared per run)
+    unsigned *bloom;      // 2^bloom_lg bits: Bloom filter of the run's cell keys (cleared per run), or null
     int bloom_lg;
+    bool super;           // d = 2, 3: neighbour lists through supercells (launch_neighbors_super)
+    unsigned *bloom_all;  // the Bloom filter's storage (supercell keys)
 };
 // Group the points by cell: fills cell_key, cell_start, pf/pd, orig, cell_of,
 // ctr->m, and the slots' cell ids.
 void launch_semisort(const void *X, int dtype, const RunParams &P, int SD, const Semisort &S, DevCounters *ctr,
                      cudaStream_t s);
-// Empty the slots the run used (keeps the table clean for the next run).
-void launch_table_reset(const Semisort &S, DevCounters *ctr, cudaStream_t s);
+// Empty the slots the run used (keeps the table clean for the next run): the
+// cells' slots, or at the end of a supercell run the supercells' slots.
+void launch_table_reset(const Semisort &S, DevCounters *ctr, cudaStream_t s, bool end_of_run = true);
+// Neighbour lists for d = 2, 3 through supercells (fixed stride per cell, as
+// launch_neighbors); empties the cells' slots of the hash first.
+void launch_neighbors_super(const Semisort &S, const RunParams &P, int stride, const float4 *blo,
+                            const float4 *bhi, const int *cell_start, int *nbr_cnt, int *nbr_near, int *nbr_pts,
+                            int *nbr, DevCounters *ctr, cudaStream_t s);
 void launch_neighbors(const uint64_t *cell_key, const ulonglong2 *ht, uint64_t hcap, const unsigned *bloom,
                       int bloom_lg, const RunParams &P, const signed char *offs, int noff, int n_near,
                       const float4 *blo, const float4 *bhi, const int *cell_start, int *nbr_cnt, int *nbr_near,

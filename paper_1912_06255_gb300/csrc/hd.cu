@@ -446,7 +446,7 @@ k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int4 *__rest
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int m = ctr->m;
     const bool box = P.box != 0;
-    const float hi_thr = P.inst[0].thr.hi;
+    const float hi_thr = P.inst[0].cthr.hi;  // eps, or eps(1 + rho) for approximate connectivity
     int *scr = scratch + (long long)warp_id_global() * kScr * 4;
     const int packets = (m + 31) >> 5;
     for (int pk = warp_id_global(); pk < packets; pk += warps_global()) {

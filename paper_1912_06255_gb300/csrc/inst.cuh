@@ -41,9 +41,13 @@ __host__ __device__ inline bool fp32_band(double T, int d, double E, float *lo, 
 // k_j = floor(fl(fl(x_j - lo_j) * fl(1/s))), kmax_j from the box; Morton bits
 // per dimension enough for the largest kmax.  key_limit bounds d * bits.
 // want_fp32: use the FP32 band if it is valid for this instance (fp32 = 1).
+// rho > 0: rho-approximate connectivity (Sec. 2, after Gan and Tao): core
+// cells are joined by pairs within fl(eps * fl(1 + rho)) (cthr), while core
+// points, neighbouring cells and border sets keep eps (thr).
 // Returns DBSCAN_OK or DBSCAN_ERR_KEY_OVERFLOW.
 __host__ __device__ inline int build_inst(Inst &I, double eps, long long min_pts, int n, int d, const double *lo,
-                                          const double *hi, bool f64, bool want_fp32, int key_limit, int *fp32) {
+                                          const double *hi, bool f64, bool want_fp32, int key_limit, int *fp32,
+                                          double rho = 0.0) {
     for (int j = 0; j < kMaxDim; ++j) {
         I.origin[j] = 0.0;
         I.origin32[j] = 0.f;
@@ -75,9 +79,21 @@ __host__ __device__ inline int build_inst(Inst &I, double eps, long long min_pts
     I.bits = bits;
     if (d * bits > key_limit) return DBSCAN_ERR_KEY_OVERFLOW;
     *fp32 = 0;
+    double E = 0.0;
     if (want_fp32) {
-        const double E = f64 ? sqrt((double)d) * (2.0 * M * 0x1p-24 + 0x1p-148) : 0.0;
+        E = f64 ? sqrt((double)d) * (2.0 * M * 0x1p-24 + 0x1p-148) : 0.0;
         *fp32 = fp32_band(I.thr.eps2, d, E, &I.thr.lo, &I.thr.hi) ? 1 : 0;
+    }
+    I.cthr = I.thr;
+    if (rho > 0.0) {
+        const double r = eps * (1.0 + rho);
+        I.cthr.eps2 = r * r;
+        // no valid band for the wider threshold: every FP32 value goes to the
+        // FP64 recheck (lo = 0 only admits coincident points)
+        if (*fp32 && !fp32_band(I.cthr.eps2, d, E, &I.cthr.lo, &I.cthr.hi)) {
+            I.cthr.lo = 0.f;
+            I.cthr.hi = INFINITY;
+        }
     }
     return DBSCAN_OK;
 }

@@ -19,6 +19,7 @@ struct DevCounters {
     int err;         // first error code (dbscan_status), 0 if none
     int err_info;    // kernel-specific detail of the first error
     int m;           // non-empty cells
+    int ms;          // non-empty supercells (d = 2, 3: blocks of 2^d cells)
     int m_core;      // core cells
     int n_core;      // core points
     int n_border;    // border points
@@ -57,7 +58,9 @@ struct Inst {
     int bits;                 // Morton bits per dimension
     int d;                    // the instance's dimension (<= the storage dimension)
     int row0, n;              // rows [row0, row0 + n) of the input
-    Thr thr;
+    Thr thr;                  // eps: MarkCore, ClusterBorder, neighbouring cells
+    Thr cthr;                 // connectivity of core cells (ClusterCore): eps, or
+                              // eps(1 + rho) for rho-approximate DBSCAN (Sec. 2)
 };
 
 // Per-run scalars passed by value to the kernels.

@@ -212,7 +212,7 @@ k_collect_pairs(RunParams P, const int *__restrict__ ccs, const int *__restrict_
     unsigned long long cand_pairs = 0, boxed = 0, linked = 0, skipped = 0;
     for (int a = warp_id_global(); a < m; a += warps_global()) {
         if (ccs[a + 1] == ccs[a]) continue;
-        const Thr T = P.inst[inst_of_cell(P, a)].thr;
+        const Thr T = P.inst[inst_of_cell(P, a)].cthr;
         const Bx<D> alo = load_box<D>(cblo, a), ahi = load_box<D>(cbhi, a);
         const int ne = nbr_cnt[a];
         const int *nl = nbr_list<D>(nbr, nbr_off, stride, a);
@@ -285,7 +285,7 @@ k_score_pairs(RunParams P, const int2 *__restrict__ pairs, const float *__restri
         bool positive = false;
         if (k < np) {
             const int2 pr = pairs[k];
-            const float eps = sqrtf((float)P.inst[inst_of_cell(P, pr.x)].thr.eps2);
+            const float eps = sqrtf((float)P.inst[inst_of_cell(P, pr.x)].cthr.eps2);
             float x[kMlpIn], h1[kMlpHid], h2[kMlpHid];
             pair_features<D>(pr.x, pr.y, ccs, cent, cblo, cbhi, eps, x);
             const float z = mlp_forward(sw, x, h1, h2);
@@ -380,7 +380,7 @@ k_test_pairs(RunParams P, const int2 *__restrict__ pairs, const uint64_t *__rest
                 if (__shfl_sync(0xffffffffu, again, 0)) { ++skipped; continue; }
             }
             ++tested;
-            const Thr T = P.inst[inst_of_cell(P, sa)].thr;
+            const Thr T = P.inst[inst_of_cell(P, sa)].cthr;
             const int a0 = ccs[sa], na = ccs[sa + 1] - a0, b0 = ccs[sb], nb = ccs[sb + 1] - b0;
             int2 wp;
             const bool hit = na >= nb ? bcp_warp<D, M>(a0, na, b0, nb, cpf, cpd, P, T, rech, evals, wp)

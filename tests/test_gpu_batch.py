@@ -178,3 +178,30 @@ def test_batch256_full_size_all_instances(batch_full):
         rr = rep[r0:r0 + n].astype(np.int64)
         rr[rr >= 0] -= r0
         check_links(b.points, b.eps, exp[i][0], exp[i][1], rr, links[inst_of == i].astype(np.int64) - r0)
+
+
+def test_batch_key_width_of_lower_dimensional_instances():
+    """A 2D instance inside a 3D batch interleaves three coordinates into its
+    cell key (the third is zero), so it needs 3 x bits key bits: 2^19 cells in
+    a dimension fit beside the instance id, 2^22 do not (KEY_OVERFLOW instead
+    of a key that runs into the instance bits)."""
+    from paper_1912_06255_gb300 import DbscanError
+    small = synth.random_small(5, 500, 3, dtype=np.float32)
+    for far, ok in ((3.0e5, True), (1.5e6, False)):
+        wide = np.array([[0.0, 0.0], [far, 0.0], [0.1, 0.1], [far, 0.3]], np.float32)
+        P = np.zeros((len(small) + len(wide), 3), np.float32)
+        P[:len(small)] = small
+        P[len(small):, :2] = wide
+        ctx = DBSCAN(len(P), 3)
+        inst = [(len(small), 3, 0.3, 5), (len(wide), 2, 1.0, 2)]
+        if not ok:
+            with pytest.raises(DbscanError) as e:
+                ctx.run_batch(torch.from_numpy(P).cuda(), inst)
+            assert e.value.status == 4
+            continue
+        r = ctx.run_batch(torch.from_numpy(P).cuda(), inst)
+        ec, el, _, _ = oracle.dbscan(wide, 1.0, 2)
+        assert np.array_equal(r.core.cpu().numpy()[len(small):], ec)
+        assert np.array_equal(r.labels.cpu().numpy()[len(small):], el)
+        ec, el, _, _ = oracle.dbscan(small, 0.3, 5)
+        assert np.array_equal(r.labels.cpu().numpy()[:len(small)], el)
