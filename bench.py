@@ -1,17 +1,23 @@
 """Benchmark: exact DBSCAN throughput (Mpts/s) on one GB300 per rank.
 
-Default workload (``--workload spreader3d``): 3D seed-spreader points,
-n = 2,000,000, stored FP32, eps = 100, minPts = 100 (100 random walkers in
-[0,1e5]^3, ball radius 100, step 50 per 100 points, 0.01% noise).  One step =
-one full run of the hot path (cells, MarkCore, BCP connectivity with
-union-find, labels, border counts) through the C ABI on inputs resident in
-device memory.  The 24 MB input fits in L2, so L2 is flushed (256 MiB write)
-before every timed step, outside the timed interval.
+Default workload (``--workload batch256``), the largest single-GPU one: 256
+independent 2D/3D blob-plus-noise instances with log-uniform sizes in
+[1e3, 1e6] (36,189,307 points), per-instance eps in [0.2, 1.0] and minPts in
+[5, 50], FP32, in one dbscan_run_batch call (one replayed CUDA graph).  One
+step = one full pass of the hot path over the batch: cells, neighbour lists,
+MarkCore, BCP connectivity with union-find, labels, border counts, and the
+border-set fill (dbscan_border_ids), on inputs resident in device memory.
 
-``--workload batch256``: 256 independent 2D/3D blob-plus-noise instances with
-log-uniform sizes in [1e3, 1e6] (about 36M points), per-instance eps in
-[0.2, 1.0] and minPts in [5, 50], FP32, in one dbscan_run_batch call (one
-replayed CUDA graph).
+``--workload spreader3d``: 3D seed-spreader points, n = 2,000,000, FP32,
+eps = 100, minPts = 100 (100 random walkers in [0,1e5]^3, ball radius 100,
+step 50 per 100 points, 0.01% noise); reported beside the batch as an extra
+line by default.  ``mixed5d`` / ``varden7d``: the 10M-point 5D and 7D
+workloads (``--eps`` picks the sweep point).
+
+L2 is flushed (256 MiB write) before every timed step, outside the timed
+interval.  ``e2e`` times the host-buffer C-ABI entry points (dbscan_run_host,
+dbscan_run_batch_host) from pinned memory: input upload, the run, and the
+download of core flags, labels and the border CSR, every step.
 
 ``--impl reference`` times the CPU oracle (FP64, OpenMP on the host cores) on
 a bounded sample of the same workload instead.
@@ -36,7 +42,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 UNIT = "Mpts/s"
-PHASES = ["bbox", "bbox_readback", "cells", "boxes_neighbors", "markcore", "compact_schedule",
+METRIC = "exact DBSCAN Mpts/s on 1 GB300: mixed/learned vs plain FP64 path; % roofline"
+PHASES = ["bbox", "bbox_readback", "cells", "boxes_lookup", "neighbor_lists", "markcore", "compact_schedule",
           "connect_bcp_uf", "labels_border"]
 
 
@@ -61,16 +68,19 @@ class SingleInstance:
         return torch.from_numpy(self.I.points).to(dev)
 
     def run(self, ctx, X, out):
-        ctx.run(X, self.I.eps, self.I.min_pts, border=False, out=out)
+        return ctx.run(X, self.I.eps, self.I.min_pts, border=True, out=out)
 
     def run_e2e(self, ctx, hbuf):
-        ctx.run_host(hbuf["X"], self.I.eps, self.I.min_pts, core=hbuf["core"], labels=hbuf["labels"])
+        return ctx.run_host(hbuf["X"], self.I.eps, self.I.min_pts, core=hbuf["core"], labels=hbuf["labels"],
+                            border=(hbuf["off"], hbuf["ids"]))[2]
 
-    def host_buffers(self):
+    def host_buffers(self, K):
         import torch
         return {"X": torch.from_numpy(self.I.points).pin_memory(),
                 "core": torch.empty(self.n, dtype=torch.uint8).pin_memory(),
-                "labels": torch.empty(self.n, dtype=torch.int32).pin_memory()}
+                "labels": torch.empty(self.n, dtype=torch.int32).pin_memory(),
+                "off": torch.empty(self.n + 1, dtype=torch.int64).pin_memory(),
+                "ids": torch.empty(max(2 * K, 1024), dtype=torch.int32).pin_memory()}
 
     def h2d_bytes(self):
         return int(self.I.points.nbytes)
@@ -102,7 +112,6 @@ class SingleInstance:
 
 class Spreader3D(SingleInstance):
     """The 2M-point 3D instance (eps 100, minPts 100)."""
-    metric = "exact DBSCAN Mpts/s on 1 GB300 (3D seed spreader n=2e6, eps=100, minPts=100)"
     TRAIN_SEED = 2001
     DEFAULT_N = 2_000_000
 
@@ -113,7 +122,6 @@ class Spreader3D(SingleInstance):
 
 class Mixed5D(SingleInstance):
     """The 10M-point 5D instance: half uniform, half seed spreader (minPts 10)."""
-    metric = "exact DBSCAN Mpts/s on 1 GB300 (5D mixed uniform + spreader n=1e7, minPts=10)"
     TRAIN_SEED = 2002
     DEFAULT_N = 10_000_000
     EPS = 200.0
@@ -126,7 +134,6 @@ class Mixed5D(SingleInstance):
 
 class VarDen7D(SingleInstance):
     """The 10M-point 7D varying-density instance (minPts 100)."""
-    metric = "exact DBSCAN Mpts/s on 1 GB300 (7D varying-density spreader n=1e7, minPts=100)"
     TRAIN_SEED = 2004
     DEFAULT_N = 10_000_000
     EPS = 1000.0
@@ -137,23 +144,26 @@ class VarDen7D(SingleInstance):
         return synth.spreader_7d_10m(seed=seed, n=n, eps=self.EPS)
 
 
+def _stack(B):
+    n = sum(len(b.points) for b in B)
+    P = np.zeros((n, 3), np.float32)
+    row = 0
+    for b in B:
+        P[row:row + len(b.points), :b.points.shape[1]] = b.points
+        row += len(b.points)
+    return P, [(len(b.points), b.points.shape[1], b.eps, b.min_pts) for b in B]
+
+
 class Batch256:
     """256 independent 2D/3D instances in one batched call."""
-    metric = "exact DBSCAN Mpts/s on 1 GB300 (batch of 256 2D/3D instances, about 36M points)"
-
     INSTANCES = 256
 
     def __init__(self, n):
         from paper_1912_06255_gb300 import synth
         self.B = synth.batch_256(count=self.INSTANCES)
-        self.n = sum(len(b.points) for b in self.B)
-        P = np.zeros((self.n, 3), np.float32)
-        row = 0
-        for b in self.B:
-            P[row:row + len(b.points), :b.points.shape[1]] = b.points
-            row += len(b.points)
-        self.P = P
-        self.inst = [(len(b.points), b.points.shape[1], b.eps, b.min_pts) for b in self.B]
+        self.P, self.inst = _stack(self.B)
+        self.n = len(self.P)
+        self.d = 3
         self.name = f"batch{len(self.B)}-n{self.n}-f32"
         self.config = {"workload": self.name, "instances": len(self.B), "n": self.n, "d": "2/3",
                        "eps": "U[0.2,1.0]", "min_pts": "U{5..50}"}
@@ -166,22 +176,19 @@ class Batch256:
         return torch.from_numpy(self.P).to(dev)
 
     def run(self, ctx, X, out):
-        ctx.run_batch(X, self.inst, border=False, out=out)
+        return ctx.run_batch(X, self.inst, border=True, out=out)
 
     def run_e2e(self, ctx, hbuf):
-        # the public API path: pinned host -> device, batched run, results -> pinned host
-        hbuf["dX"].copy_(hbuf["X"], non_blocking=True)
-        ctx.run_batch(hbuf["dX"], self.inst, border=False, out=hbuf["out"])
-        hbuf["core"].copy_(hbuf["out"][0], non_blocking=True)
-        hbuf["labels"].copy_(hbuf["out"][1], non_blocking=True)
+        return ctx.run_batch_host(hbuf["X"], self.inst, core=hbuf["core"], labels=hbuf["labels"],
+                                  border=(hbuf["off"], hbuf["ids"]))[2]
 
-    def host_buffers(self):
+    def host_buffers(self, K):
         import torch
-        return {"X": torch.from_numpy(self.P).pin_memory(), "dX": torch.empty_like(torch.from_numpy(self.P)).cuda(),
-                "out": (torch.empty(self.n, dtype=torch.uint8, device="cuda"),
-                        torch.empty(self.n, dtype=torch.int32, device="cuda"), None),
+        return {"X": torch.from_numpy(self.P).pin_memory(),
                 "core": torch.empty(self.n, dtype=torch.uint8).pin_memory(),
-                "labels": torch.empty(self.n, dtype=torch.int32).pin_memory()}
+                "labels": torch.empty(self.n, dtype=torch.int32).pin_memory(),
+                "off": torch.empty(self.n + 1, dtype=torch.int64).pin_memory(),
+                "ids": torch.empty(max(2 * K, 1024), dtype=torch.int32).pin_memory()}
 
     def h2d_bytes(self):
         return int(self.P.nbytes)
@@ -191,15 +198,8 @@ class Batch256:
         import torch
         from paper_1912_06255_gb300 import synth
         if getattr(self, "_held", None) is None:
-            B = synth.batch_256(seed=2003, count=48)
-            n = sum(len(b.points) for b in B)
-            P = np.zeros((n, 3), np.float32)
-            row = 0
-            for b in B:
-                P[row:row + len(b.points), :b.points.shape[1]] = b.points
-                row += len(b.points)
-            inst = [(len(b.points), b.points.shape[1], b.eps, b.min_pts) for b in B]
-            self._held = (torch.from_numpy(P).to(dev), inst, f"batch_256(seed=2003, count=48), {n} points")
+            P, inst = _stack(synth.batch_256(seed=2003, count=48))
+            self._held = (torch.from_numpy(P).to(dev), inst, f"batch_256(seed=2003, count=48), {len(P)} points")
         return self._held
 
     def log_run(self, ctx, dev):
@@ -244,15 +244,15 @@ def _max_over_ranks(x, dist, dev):
     return float(t.item())
 
 
-def _time_oracle(samples):
+def _time_oracle(samples, threads=0):
     import oracle
     oracle.build()
     n = 0
     t0 = time.perf_counter()
     for X, eps, mp in samples:
-        oracle.dbscan(X, eps, mp)
+        oracle.dbscan(X, eps, mp, threads=threads)
         n += len(X)
-    return n, time.perf_counter() - t0, oracle.num_threads()
+    return n, time.perf_counter() - t0, (threads if threads > 0 else oracle.num_threads())
 
 
 class ClockSampler:
@@ -308,40 +308,53 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# DRAM bytes per launch of the dominant kernel, from one ncu capture of the
-# same command (dram__bytes_read.sum + dram__bytes_write.sum); None when the
-# kernel changed after the capture.  Keyed by (kernel, workload name).
-TRAFFIC = {
-    # profiles/launches_spreader3d_n2m.md: DRAM read + write per launch at the
-    # captured setting (list order, one connect wave, 8 cells per work item);
-    # the connect figure holds for one wave only
-    ("k_markcore", "spreader3d-n2000000-eps100-minpts100-f32", None): 55439872 + 457472,
-    ("k_connect", "spreader3d-n2000000-eps100-minpts100-f32", 1): 47500032 + 50688,
-}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# kernel on a workload, from one ncu capture of this code; a kernel or
+# workload not listed reports traffic null.  Keyed by (kernel, workload).
+TRAFFIC = {}
 
 
-def _roofline(kernel, ms, work_pairs, d, workload, executed_pairs=None, waves=None):
-    """Roofline of the dominant kernel.  MarkCore and BCP are pair-distance
-    loops bound by the FP32 pipe: achieved = algorithmic pair tests x 3d flop
-    (d subtractions and d multiply-adds) / the kernel's time, measured with
-    CUDA events on the run's stream in the timed steps.  MarkCore's
-    algorithmic work is the scan without early exit (the sum over cells
-    with fewer than minPts points of |g| times the points of their
-    neighbouring cells); BCP's is the pair tests the schedule ran.
-    Peak = 152 SMs x 128 FP32 lanes x 2 flop x max SM clock."""
+def _neighbor_kernel(d):
+    return "k_neighbors_super" if d in (2, 3) else ("k_neighbors" if d <= 4 else "k_lbvh_neighbors")
+
+
+def _roofline_candidates(ph, run, dd, box, workload, ev_phase):
+    """Roofline of the three single-kernel phases; the caller reports the one
+    with the longest time.
+
+    Neighbour lists (phase 4, one launch): bound by memory.  Algorithmic bytes
+    per cell: its key (8 B; packed coordinates, 16 B, for d >= 5), its point
+    box when the FP32-band mode prunes by boxes (32 B; 64 B for d >= 5), the
+    two counts it writes (8 B; + an 8 B list offset for d >= 5); plus 4 B per
+    list entry written.  achieved = those bytes / the phase's CUDA-event time.
+
+    MarkCore (phase 5) and BCP connectivity (phase 7): bound by the FP32 pipe.
+    Work = the pair tests the kernel actually ran (counted in an untimed run
+    of the same setting) x 3d flop (d subtractions, d multiply-adds);
+    peak = 152 SMs x 128 FP32 lanes x 2 flop x the maximum SM clock."""
     peaks, kind = _peaks()
-    clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    peak_tflops = 152 * 128 * 2 * clk / 1e12
-    if not work_pairs or ms <= 0:
-        return None
-    achieved = work_pairs * 3 * d / (ms * 1e-3) / 1e12
-    out = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-           "frac": achieved / peak_tflops, "traffic": TRAFFIC.get((kernel, workload, waves)), "kernel": kernel,
-           "work_pair_tests": int(work_pairs), "kernel_ms": ms}
-    if executed_pairs is not None:
-        ex = executed_pairs * 3 * d / (ms * 1e-3) / 1e12
-        out.update(executed_pair_tests=int(executed_pairs), executed_achieved=ex, executed_frac=ex / peak_tflops)
-    out["peak_source"] = f"152 SMs x 128 FP32 lanes x 2 flop x max SM clock ({kind} clock)"
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    alu = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    m, E = run["num_cells"], run["num_neighbor_entries"]
+    hd = dd >= 5
+    per_cell = (16 if hd else 8) + ((64 if hd else 32) if box else 0) + (16 if hd else 8)
+    nbytes = m * per_cell + 4 * E
+    kn = _neighbor_kernel(dd)
+    out = {}
+    if ph[4] > 0:
+        a = nbytes / (ph[4] * 1e-3) / 1e9
+        out["neighbor_lists"] = {
+            "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+            "traffic": TRAFFIC.get((kn, workload)), "kernel": kn, "kernel_ms": ph[4],
+            "algorithmic_bytes": int(nbytes), "units": f"{m} cells, {E} list entries",
+            "peak_source": f"{kind} copy bandwidth (MEASURED_PEAKS hbm_gbs)" if kind == "measured" else "fallback"}
+    for key, kern, i, work in (("markcore", "k_markcore", 5, ev_phase[0]), ("connect", "k_connect", 7, ev_phase[1])):
+        if ph[i] > 0:
+            a = work * 3 * dd / (ph[i] * 1e-3) / 1e12
+            out[key] = {"bound": "alu", "achieved": a, "peak": alu, "unit": "TFLOP/s", "frac": a / alu,
+                        "traffic": TRAFFIC.get((kern, workload)), "kernel": kern, "kernel_ms": ph[i],
+                        "work_pair_tests": int(work),
+                        "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {kind} max SM clock"}
     return out
 
 
@@ -360,7 +373,7 @@ def run_reference(args):
     t = statistics.median(ts)
     v = npts / t / 1e6
     line = {
-        "impl": "reference", "metric": W.metric, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(W.config, sample_n=npts),
@@ -389,56 +402,53 @@ def _train_scheduler(W, ctx, dev):
             "seconds": round(time.perf_counter() - t0, 2)}
 
 
+def _timed(fn, flush, stream, steps):
+    """CUDA-event times (ms) of `steps` calls of fn, L2 flushed before each."""
+    import torch
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms
+
+
 def _compare_schedules(W, ctx, X, out, flush, stream, steps):
     """Device time and BCP test counts of each pair schedule on the timed input."""
-    import torch
     res = {}
     for name, code in SCHED_CODES.items():
         ctx.set_option(1, code)
         for _ in range(2):
             W.run(ctx, X, out)
-        ms = []
-        for k in range(steps):
-            flush.fill_(float(k))
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            W.run(ctx, X, out)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ms.append(a.elapsed_time(b))
+        ms = _timed(lambda: W.run(ctx, X, out), flush, stream, steps)
         st = ctx.stats()
-        res[name] = {"ms_per_step": round(sum(ms) / len(ms), 4), "value": round(W.n / (sum(ms) / len(ms) * 1e-3) / 1e6, 1),
+        t = sum(ms) / len(ms)
+        res[name] = {"ms_per_step": round(t, 4), "value": round(W.n / (t * 1e-3) / 1e6, 1),
                      "pairs_tested": st["num_pairs_tested"], "pairs_skipped": st["num_pairs_skipped"],
-                     "pairs_box_decided": st["num_pairs_box_decided"], "pairs_listed": st["num_pairs_listed"],
-                     "bcp_distance_evals": st["distance_evals_phase"][1]}
+                     "pairs_box_decided": st["num_pairs_box_decided"], "pairs_listed": st["num_pairs_listed"]}
     return res
 
 
-def run_gpu(args):
+def _measure(W, args, DBSCAN, dev, dist, rank, local, primary):
+    """Every number of one workload's line (device-timed steps, phases and
+    roofline, the FP64 path, the host-buffer end-to-end leg, schedules)."""
     import torch
-
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_1912_06255_gb300 import DBSCAN, build
-
-    build.build()
-    W = WORKLOADS[args.workload](args.points)
     n = W.n
-    dev = torch.device("cuda", local)
     X = W.device_input(dev)
     ctx = W.make_ctx(DBSCAN, precision=args.precision, schedule="size")
-    training = _train_scheduler(W, ctx, dev) if not args.profile or args.schedule == "learned" else None
+    training = _train_scheduler(W, ctx, dev) if primary else None
     ctx.set_option(1, SCHED_CODES[args.schedule])
     tuned = None
     if args.tuning:
         ctx.set_tuning(json.loads(args.tuning))
-    elif args.autotune and not args.profile:
-        # the autotuner picks schedule, box decisions, waves, work-item size
-        # and blocks per SM on the held-out input; the timed runs use its choice
+    elif args.autotune:
+        # the autotuner picks schedule, box decisions, waves, work-item size,
+        # blocks per SM and small-cell kernels on the held-out input; the timed
+        # runs use its choice
         choice, src = W.autotune(ctx, dev)
         tuned = dict(choice, tuned_on=src)
     setting = ctx.tuning()
@@ -447,45 +457,32 @@ def run_gpu(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
     def step():
-        W.run(ctx, X, out)
+        return W.run(ctx, X, out)
 
-    if args.profile:
-        # profiling mode (for ncu): warm-up and timed steps only, no extra runs
-        for _ in range(args.warmup + args.steps):
-            step()
-        torch.cuda.synchronize()
-        if rank == 0:
-            print(json.dumps({"profile": W.name, "steps": args.steps, "warmup": args.warmup}), flush=True)
-        return
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
-    # pair tests per kernel, counted once in an untimed run
+    # pair tests per kernel and band rechecks, counted once in an untimed run of the same setting
     cctx = W.make_ctx(DBSCAN, precision=args.precision, schedule=args.schedule, collect_stats=True)
     cctx.set_scheduler_weights(ctx.scheduler_weights())
     cctx.set_tuning(setting)
     W.run(cctx, X, out)
-    ev_phase = cctx.stats()["distance_evals_phase"]
-    mc_bound = cctx.stats()["markcore_pair_bound"]
-    band_rechecks = cctx.stats()["band_rechecks"]
+    cst = cctx.stats()
     cctx.close()
 
-    # timed region: device time per step with CUDA events; L2 flushed before each
-    # step.  The library's phase timing (events between its phases, on the same
-    # stream) adds a little time to a step, so it runs in a second timed pass of
-    # the same steps, which gives phase_ms and the kernel times of the roofline;
-    # a batch replays its captured graph in the first pass and enqueues directly
-    # in the second.
+    # timed region: device time per step with CUDA events, L2 flushed before
+    # each step.  The library's phase timing (events between its phases, on the
+    # same stream) adds a little time to a step, so it runs in a second timed
+    # pass of the same steps, which gives phase_ms and the kernel times of the
+    # roofline; a batch replays its captured graph in the first pass and
+    # enqueues directly in the second.
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches = 0
-    clocks = ClockSampler(local) if rank == 0 else None
-    barrier()
+    clocks = ClockSampler(local) if (rank == 0 and primary) else None
+    if dist is not None:
+        dist.barrier()
     torch.cuda.synchronize()
     for k in range(args.steps):
         flush.fill_(float(k))
@@ -494,12 +491,13 @@ def run_gpu(args):
         evs[k][1].record(stream)
         launches += ctx.stats()["kernel_launches"]
     torch.cuda.synchronize()
-    barrier()
+    if dist is not None:
+        dist.barrier()
     clk = clocks.stop() if clocks else None
     ms = [a.elapsed_time(b) for a, b in evs]
     t_ms = sum(ms) / len(ms)
     stats = ctx.stats()
-    # second pass: per-phase CUDA events inside each step
+    K = stats["num_border_memberships"]
     ctx.set_option(4, 1)
     phases = []
     for k in range(args.steps):
@@ -515,89 +513,117 @@ def run_gpu(args):
     ctx64.set_tuning({k: v for k, v in setting.items() if k != "cell_bounds"})
     for _ in range(3):
         W.run(ctx64, X, out)
-    ms64 = []
-    for k in range(max(3, min(args.steps, 5))):
-        flush.fill_(float(k))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        W.run(ctx64, X, out)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms64.append(a.elapsed_time(b))
+    ms64 = _timed(lambda: W.run(ctx64, X, out), flush, stream, max(3, min(args.steps, 5)))
     ctx64.close()
 
-    # end to end through the public API from pinned host memory
-    hbuf = W.host_buffers()
+    # end to end through the host-buffer C ABI from pinned memory: upload,
+    # run, download of core flags, labels and the border CSR
+    hbuf = W.host_buffers(K)
     for _ in range(2):
         W.run_e2e(ctx, hbuf)
     torch.cuda.synchronize()
-    e2e_ms = []
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        W.run_e2e(ctx, hbuf)
-        b.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms.append(a.elapsed_time(b))
+    e2e_ms = _timed(lambda: W.run_e2e(ctx, hbuf), flush, stream, args.steps)
+    d2h = n * 1 + n * 4 + 8 * (n + 1) + 4 * K
 
-    schedules = _compare_schedules(W, ctx, X, out, flush, stream, max(3, min(args.steps, 5)))
+    schedules = _compare_schedules(W, ctx, X, out, flush, stream, max(3, min(args.steps, 5))) if primary else None
     ctx.set_tuning(setting)
 
-    def max_over_ranks(x):
-        return _max_over_ranks(x, dist, dev)
+    t_ms = _max_over_ranks(t_ms, dist, dev)
+    t64 = _max_over_ranks(sum(ms64) / len(ms64), dist, dev)
+    te2e = _max_over_ranks(sum(e2e_ms) / len(e2e_ms), dist, dev)
+    ws = 1 if dist is None else dist.get_world_size()
+    ph = [sum(p[i] for p in phases) / len(phases) for i in range(len(PHASES))]
+    dd = getattr(W, "d", 3)
+    box = stats["precision"] == 1 and setting["cell_bounds"] == 1
+    ev = cst["distance_evals_phase"]
+    cands = _roofline_candidates(ph, stats, dd, box, W.name, ev)
+    dom = max(cands, key=lambda key: cands[key]["kernel_ms"]) if cands else None
+    res = {
+        "value": ws * n / (t_ms * 1e-3) / 1e6, "ms_per_step": t_ms,
+        "config": dict(W.config, precision="fp32 band + fp64 recheck" if args.precision == "fp32" else "fp64",
+                       schedule={v: k for k, v in SCHED_CODES.items()}[setting["schedule"]], tuning=setting,
+                       parallelism=f"replicas{ws}", l2="flushed (256 MiB write) before every timed step",
+                       step="one full pass with border sets (run + dbscan_border_ids)",
+                       phase_timing="a second timed pass of the same steps (phase_ms, roofline kernel times)"),
+        "fp64_path": {"value": ws * n / (t64 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": t64},
+        "e2e": {"value": ws * n / (te2e * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": W.h2d_bytes(),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": te2e,
+                "path": "dbscan_run_batch_host" if isinstance(W, Batch256) else "dbscan_run_host"},
+        "gpu_launches": int(launches),
+        "phase_ms": dict(zip(PHASES, [round(x, 4) for x in ph])),
+        "roofline": cands.get(dom) if dom else None,
+        "roofline_other": {k: v for k, v in cands.items() if k != dom},
+        "autotune": tuned,
+        "pair_tests": {"markcore": ev[0], "markcore_without_early_exit": cst["markcore_pair_bound"],
+                       "connect": ev[1], "border": ev[2]},
+        "run_stats": {k: stats[k] for k in ("num_cells", "num_core_cells", "num_neighbor_entries",
+                                             "num_candidate_pairs", "num_pairs_tested", "num_pairs_skipped",
+                                             "num_pairs_box_decided", "num_core_points", "num_border_points",
+                                             "num_border_memberships", "band_rechecks", "key_bits")},
+    }
+    if schedules is not None:
+        res["schedules"] = dict(schedules, training=training)
+    if clk:
+        res["clocks"] = clk
+    if stats["precision"] == 1:  # FP32 band + FP64 recheck ran
+        res["band_hits"] = {"rechecks": cst["band_rechecks"], "fp32_pair_tests": sum(ev),
+                            "fraction": cst["band_rechecks"] / max(1, sum(ev))}
+    ctx.close()
+    return res
 
-    t_ms = max_over_ranks(t_ms)
-    t64 = max_over_ranks(sum(ms64) / len(ms64))
-    te2e = max_over_ranks(sum(e2e_ms) / len(e2e_ms))
+
+def run_gpu(args):
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1912_06255_gb300 import DBSCAN, build
+
+    build.build()
+    dev = torch.device("cuda", local)
+    W = WORKLOADS[args.workload](args.points)
+    if args.profile:
+        # profiling mode (for ncu): warm-up and timed steps only, no extra runs
+        X = W.device_input(dev)
+        ctx = W.make_ctx(DBSCAN, precision=args.precision, schedule=args.schedule)
+        if args.tuning:
+            ctx.set_tuning(json.loads(args.tuning))
+        out = (torch.empty(W.n, dtype=torch.uint8, device=dev), torch.empty(W.n, dtype=torch.int32, device=dev),
+               torch.empty(W.n + 1, dtype=torch.int64, device=dev))
+        for _ in range(args.warmup + args.steps):
+            W.run(ctx, X, out)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile": W.name, "steps": args.steps, "warmup": args.warmup}), flush=True)
+        return
+    res = _measure(W, args, DBSCAN, dev, dist, rank, local, primary=True)
+    extra = {}
+    if args.extra and args.workload != "spreader3d":
+        E = Spreader3D(None)
+        r = _measure(E, args, DBSCAN, dev, dist, rank, local, primary=False)
+        extra[E.name] = {k: r[k] for k in ("value", "ms_per_step", "fp64_path", "e2e", "phase_ms", "roofline",
+                                           "autotune", "gpu_launches", "band_hits") if k in r}
+        extra[E.name]["unit"] = UNIT
     if rank == 0:
-        ph = [sum(p[i] for p in phases) / len(phases) for i in range(8)]
-        dom = 4 if ph[4] >= ph[6] else 6
-        dd = getattr(W, "d", 3)
-        roof_mc = _roofline("k_markcore", ph[4], mc_bound, dd, W.name, executed_pairs=ev_phase[0])
-        roof_cn = _roofline("k_test_pairs" if setting["schedule"] == 2 else "k_connect", ph[6], ev_phase[1], dd,
-                            W.name, waves=setting["connect_waves"])
-        roof = roof_mc if dom == 4 else roof_cn
-        line = {
-            "metric": W.metric,
-            "value": ws * n / (t_ms * 1e-3) / 1e6,
-            "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "f64",
-            "data": "synthetic",
-            "config": dict(W.config, precision="fp32 band + fp64 recheck" if args.precision == "fp32" else "fp64",
-                           schedule={v: k for k, v in SCHED_CODES.items()}[setting["schedule"]],
-                           tuning=setting, parallelism=f"replicas{ws}",
-                           l2="flushed (256 MiB write) before every timed step",
-                           phase_timing="a second timed pass of the same steps (phase_ms, roofline kernel times)"),
-            "fp64_path": {"value": ws * n / (t64 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": t64},
-            "e2e": {"value": ws * n / (te2e * 1e-3) / 1e6, "unit": UNIT,
-                    "h2d_bytes_per_step": W.h2d_bytes(), "d2h_bytes_per_step": int(n * 5)},
-            "gpu_launches": int(launches),
-            "phase_ms": dict(zip(PHASES, [round(x, 4) for x in ph])),
-            "roofline": roof,
-            "roofline_other": roof_cn if dom == 4 else roof_mc,
-            "schedules": dict(schedules, training=training),
-            "autotune": tuned,
-            "pair_tests": {"markcore": ev_phase[0], "markcore_without_early_exit": mc_bound,
-                           "connect": ev_phase[1], "border": ev_phase[2]},
-            "run_stats": {k: stats[k] for k in ("num_cells", "num_core_cells", "num_candidate_pairs",
-                                                 "num_pairs_tested", "num_pairs_skipped", "num_pairs_box_decided",
-                                                 "num_core_points", "num_border_points", "band_rechecks",
-                                                 "key_bits")},
-        }
-        if clk:
-            line["clocks"] = clk
-        if stats["precision"] == 1:  # FP32 band + FP64 recheck ran
-            # pair tests whose FP32 distance fell inside the forward-error band and
-            # were decided again in FP64, over all FP32 pair tests of the same run
-            line["band_hits"] = {"rechecks": band_rechecks, "fp32_pair_tests": sum(ev_phase),
-                                 "fraction": band_rechecks / max(1, sum(ev_phase))}
+        line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+                "data": "synthetic"}
+        line.update({k: v for k, v in res.items() if k not in ("value", "ms_per_step")})
+        if extra:
+            line["extra_workloads"] = extra
         if not args.no_cpu_baseline:
             samples, desc = W.cpu_sample()
             npts, t, cores = _time_oracle(samples)
             line["cpu_baseline"] = {"value": npts / t / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
                                     "sample": desc}
+            npts1, t1, _ = _time_oracle(samples, threads=1)
+            line["cpu_baseline_1thread"] = {"value": npts1 / t1 / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                            "sample": desc}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -609,10 +635,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="spreader3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="batch256", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--schedule", default="size", choices=["size", "none", "learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extra", action=argparse.BooleanOptionalAction, default=True,
+                    help="also measure the 2M-point 3D workload and report it under extra_workloads")
     ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
                     help="pick the run settings with the library's autotuner on a held-out input first")
     ap.add_argument("--tuning", default=None,

@@ -153,11 +153,12 @@ typedef struct {
     float band_lo, band_hi;         /* FP32 band around eps^2 (FP32 mode) */
     int64_t kernel_launches;        /* CUDA kernels the run launched */
     /* Phase durations in ms (only with PHASE_TIMING), from CUDA events on the
-       run's stream: 0 bounding box, 1 host read of the box, 2 keys and sort,
-       3 cells, hash and neighbour lists, 4 MarkCore, 5 core compaction and
-       pair schedule, 6 BCP connectivity with union-find, 7 labels and border
-       counts. */
-    float phase_ms[8];
+       run's stream: 0 bounding box, 1 host read of the box, 2 cell keys, sort
+       and grouping, 3 cell boxes and the lookup structure of the neighbour
+       search (supercell hash, or the tree for d >= 5), 4 the neighbour-list
+       kernel, 5 MarkCore, 6 core compaction and pair schedule, 7 BCP
+       connectivity with union-find, 8 labels and border counts. */
+    float phase_ms[9];
     /* Algorithmic work of MarkCore (only with COLLECT_STATS): the sum over the
        cells with fewer than minPts points of |g| times the points of all their
        neighbouring cells, the distance tests a scan without early exit makes. */
@@ -283,13 +284,26 @@ dbscan_status dbscan_run_batch(dbscan_ctx *ctx, const dbscan_instance *h_instanc
 
 /*
  * Same as dbscan_run() but with host buffers: copies h_points to the device,
- * runs, and copies core flags and labels back (pinned host memory gives
- * asynchronous copies; pageable memory works but is staged by the driver).
- * Border sets are not returned.  The device copies live in the context.
+ * runs, and copies core flags, labels and (when h_border_offsets is not NULL)
+ * the border-set offsets [n+1] back; with h_border_ids also the border ids,
+ * which need ids_capacity >= the run's set length (*num_border_memberships
+ * receives it; CAPACITY if the buffer is too small, and the caller may retry
+ * with a larger one).  Pinned host memory gives asynchronous copies; pageable
+ * memory works but is staged by the driver.  The device copies live in the
+ * context (allocated at the first call, the ids buffer grown as needed).
+ * Synchronises the stream.
  */
 dbscan_status dbscan_run_host(dbscan_ctx *ctx, const void *h_points, int64_t n, int d, int dtype,
                               double eps, int64_t min_pts, uint8_t *h_core, int32_t *h_labels,
-                              void *stream);
+                              int64_t *h_border_offsets, int32_t *h_border_ids, int64_t ids_capacity,
+                              int64_t *num_border_memberships, void *stream);
+
+/* dbscan_run_batch() with host buffers, like dbscan_run_host(): h_points [N,
+ * ld], outputs indexed by row (N = the instances' total). */
+dbscan_status dbscan_run_batch_host(dbscan_ctx *ctx, const dbscan_instance *h_instances, int count,
+                                    const void *h_points, int ld, int dtype, uint8_t *h_core, int32_t *h_labels,
+                                    int64_t *h_border_offsets, int32_t *h_border_ids, int64_t ids_capacity,
+                                    int64_t *num_border_memberships, void *stream);
 
 /*
  * Exact DBSCAN like dbscan_run(), without any allocation, for callers that

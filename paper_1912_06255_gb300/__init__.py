@@ -278,28 +278,57 @@ class DBSCAN:
             ids = ids[: int(k.value)]
         return Result(core, labels, offs, ids, self.stats())
 
-    def run_host(self, points, eps: float, min_pts: int, core=None, labels=None, stream=None):
+    def run_host(self, points, eps: float, min_pts: int, core=None, labels=None, border=None, stream=None):
         """Cluster host memory (numpy array or CPU tensor, ideally pinned) through
-        dbscan_run_host: the copies to and from the device are part of the call."""
+        dbscan_run_host: the copies to and from the device are part of the call.
+        ``border`` may be (offsets int64 [n+1], ids int32 [cap]) host tensors for
+        the border sets; returns (core, labels, number of border ids)."""
         torch = _torch()
-        import numpy as np
-        if isinstance(points, np.ndarray):
-            pts = torch.from_numpy(np.ascontiguousarray(points))
-        else:
-            pts = points.contiguous()
-        if pts.dtype not in (torch.float32, torch.float64) or pts.dim() != 2:
-            raise ValueError("points must be float32/float64 [n, d]")
+        pts = self._host_points(points)
         n, d = pts.shape
-        if core is None:
-            core = torch.empty(n, dtype=torch.uint8)
-        if labels is None:
-            labels = torch.empty(n, dtype=torch.int32)
+        core = torch.empty(n, dtype=torch.uint8) if core is None else core
+        labels = torch.empty(n, dtype=torch.int32) if labels is None else labels
         s = stream if stream is not None else torch.cuda.current_stream()
+        off, ids = border if border is not None else (None, None)
+        k = ctypes.c_int64(0)
         dtype = _lib.F32 if pts.dtype == torch.float32 else _lib.F64
         _lib.check(self.lib.dbscan_run_host(self.ctx, pts.data_ptr(), n, d, dtype, float(eps), int(min_pts),
-                                            core.data_ptr(), labels.data_ptr(), s.cuda_stream),
+                                            core.data_ptr(), labels.data_ptr(),
+                                            off.data_ptr() if off is not None else None,
+                                            ids.data_ptr() if ids is not None else None,
+                                            ids.numel() if ids is not None else 0, ctypes.byref(k), s.cuda_stream),
                    "dbscan_run_host")
-        return core, labels
+        return core, labels, int(k.value)
+
+    def run_batch_host(self, points, instances, core=None, labels=None, border=None, stream=None):
+        """dbscan_run_batch_host: run_batch on host memory [N, ld]; returns
+        (core, labels, number of border ids)."""
+        torch = _torch()
+        pts = self._host_points(points)
+        N, ld = pts.shape
+        arr = _instances(instances, N)
+        core = torch.empty(N, dtype=torch.uint8) if core is None else core
+        labels = torch.empty(N, dtype=torch.int32) if labels is None else labels
+        s = stream if stream is not None else torch.cuda.current_stream()
+        off, ids = border if border is not None else (None, None)
+        k = ctypes.c_int64(0)
+        dtype = _lib.F32 if pts.dtype == torch.float32 else _lib.F64
+        _lib.check(self.lib.dbscan_run_batch_host(self.ctx, arr, len(instances), pts.data_ptr(), ld, dtype,
+                                                  core.data_ptr(), labels.data_ptr(),
+                                                  off.data_ptr() if off is not None else None,
+                                                  ids.data_ptr() if ids is not None else None,
+                                                  ids.numel() if ids is not None else 0, ctypes.byref(k),
+                                                  s.cuda_stream), "dbscan_run_batch_host")
+        return core, labels, int(k.value)
+
+    @staticmethod
+    def _host_points(points):
+        torch = _torch()
+        import numpy as np
+        pts = torch.from_numpy(np.ascontiguousarray(points)) if isinstance(points, np.ndarray) else points.contiguous()
+        if pts.dtype not in (torch.float32, torch.float64) or pts.dim() != 2 or pts.is_cuda:
+            raise ValueError("points must be host float32/float64 [n, d]")
+        return pts
 
 
 def dbscan(points, eps: float, min_pts: int, precision: str = "fp32", schedule: str = "size",

@@ -44,7 +44,7 @@ class Stats(ctypes.Structure):
         ("num_border_points", ctypes.c_int64), ("num_noise_points", ctypes.c_int64),
         ("num_border_memberships", ctypes.c_int64), ("band_rechecks", ctypes.c_int64),
         ("distance_evals", ctypes.c_int64), ("distance_evals_phase", ctypes.c_int64 * 3), ("band_lo", ctypes.c_float), ("band_hi", ctypes.c_float),
-        ("kernel_launches", ctypes.c_int64), ("phase_ms", ctypes.c_float * 8),
+        ("kernel_launches", ctypes.c_int64), ("phase_ms", ctypes.c_float * 9),
         ("markcore_pair_bound", ctypes.c_int64),
         ("schedule_used", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("rho", ctypes.c_double),
@@ -81,7 +81,9 @@ SIGNATURES = {
     "dbscan_run": (_I32, [_P, _P, _I64, _I32, _I32, _D, _I64, _P, _P, _P, ctypes.POINTER(_I64), _P]),
     "dbscan_border_ids": (_I32, [_P, _P, _I64, _P]),
     "dbscan_link_witnesses": (_I32, [_P, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
-    "dbscan_run_host": (_I32, [_P, _P, _I64, _I32, _I32, _D, _I64, _P, _P, _P]),
+    "dbscan_run_host": (_I32, [_P, _P, _I64, _I32, _I32, _D, _I64, _P, _P, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
+    "dbscan_run_batch_host": (_I32, [_P, ctypes.POINTER(Instance), _I32, _P, _I32, _I32, _P, _P, _P, _P, _I64,
+                                     ctypes.POINTER(_I64), _P]),
     "dbscan_run_static": (_I32, [_P, _I64, _I32, _I32, _D, _I64, _P, _P, _P]),
     "dbscan_run_batch": (_I32, [_P, ctypes.POINTER(Instance), _I32, _P, _I32, _I32, _P, _P, _P,
                                 ctypes.POINTER(_I64), _P]),

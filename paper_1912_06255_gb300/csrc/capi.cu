@@ -243,6 +243,8 @@ static dbscan_status enqueue_hd_cells(dbscan_ctx *c, const RunParams &P, const v
     mark(2);
     hd_cells(d_points, dtype, P, key_bits, c->hd, B, c->ctr, s);
     mark(3);
+    hd_tree(P, c->hd, B, c->ctr, s);
+    mark(4);
     for (int attempt = 0; attempt < 2; ++attempt) {
         int *nbr = c->hd_nbr_cap > c->nbr_cap ? c->hd_nbr : c->nbr;
         const long long cap = c->hd_nbr_cap > c->nbr_cap ? c->hd_nbr_cap : c->nbr_cap;
@@ -337,9 +339,12 @@ static dbscan_status enqueue_hash_cells(dbscan_ctx *c, const RunParams &P, int S
     if (P.box) launch_boxes(SD, c->pf, c->cell_start, c->ctr, c->blo, c->bhi, s);
     int *nbr_pts = P.mc_small_nbr > 0 && P.mc_small_nbr < (1 << 30) ? c->nbr_pts : nullptr;
     if (S.super) {
+        launch_super_table(S, P, c->ctr, s);
+        mark(4);
         launch_neighbors_super(S, P, c->noff[d_enum], c->blo, c->bhi, c->cell_start, c->nbr_cnt, c->nbr_near,
                                nbr_pts, c->nbr, c->ctr, s);
     } else {
+        mark(4);
         int n_near = 1;
         for (int j = 0; j < d_enum; ++j) n_near *= 3;
         launch_neighbors(c->cell_key, c->ht, c->hcap, S.bloom, c->bloom_lg, P, offs_for(c, d_enum),
@@ -376,9 +381,9 @@ static dbscan_status enqueue_core(dbscan_ctx *c, const RunParams &P, int D, int 
     Bufs B = make_bufs(c, f64);
     B.n_max = n;
     B.nbr_stride = hashed ? c->noff[d_enum] : 0;
-    mark(4);
-    launch_markcore(D, mode, P, B, c->ctr, s);
     mark(5);
+    launch_markcore(D, mode, P, B, c->ctr, s);
+    mark(6);
     launch_core_compact(SD, P, B, c->ctr, s);
     if (B.ccent) {
         // learned schedule (or a logging run for its training)
@@ -386,19 +391,19 @@ static dbscan_status enqueue_core(dbscan_ctx *c, const RunParams &P, int D, int 
             (void)cudaGetLastError();
             return DBSCAN_ERR_OOM;
         }
-        mark(6);
+        mark(7);
         launch_connect_learned(D, mode, c->log_cap > 0, P, B, learned_state(c), c->ctr, s);
     } else {
         const uint32_t *order = launch_schedule(c->sched, P, B, c->ctr, s);
-        mark(6);
+        mark(7);
         launch_connect(D, mode, order, P, B, c->ctr, s);
     }
-    mark(7);
+    mark(8);
     launch_labels(P, B, d_core, d_labels, c->ctr, s);
     // the offsets only when the caller takes them now (else dbscan_border_ids scans them)
     launch_border(D, mode, false, P, B, d_labels, nullptr, 0, c->ctr, s, d_border_offsets != nullptr);
     c->boff_ready = d_border_offsets != nullptr;
-    mark(8);
+    mark(9);
     if (hashed) launch_table_reset(S, c->ctr, s);
     if (d_border_offsets)
         CK(cudaMemcpyAsync(d_border_offsets, c->boff, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
@@ -432,7 +437,7 @@ static dbscan_status finish_run(dbscan_ctx *c, const RunParams &P, int D, int mo
     st.markcore_pair_bound = (int64_t)h.mc_bound;
     st.kernel_launches = g_launches - launches0;
     if (c->phase_timing) {
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < kPhases; ++k)
             if (cudaEventElapsedTime(&st.phase_ms[k], c->ev[k], c->ev[k + 1]) != cudaSuccess) st.phase_ms[k] = 0.f;
         (void)cudaGetLastError();
     }
@@ -477,6 +482,8 @@ void dbscan_destroy(dbscan_ctx *c) {
     cudaFree(c->d_in);
     cudaFree(c->d_core_h);
     cudaFree(c->d_lab_h);
+    cudaFree(c->d_off_h);
+    cudaFree(c->d_ids_h);
     cudaFreeHost(c->h_ctr);
     cudaFreeHost(c->h_bbox);
     cudaFreeHost(c->h_inst);
@@ -561,7 +568,7 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
     e = cudaMallocHost((void **)&c->h_ctr, sizeof(DevCounters));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_bbox, sizeof(long long) * (2 * kMaxDim + 1));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_inst, sizeof(Inst));
-    for (int k = 0; k < 9 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
+    for (int k = 0; k <= kPhases && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
     for (int d = 1; d <= kMaxEnumDim && e == cudaSuccess; ++d) {
         std::vector<signed char> t = offset_table(d);
         e = cudaMemcpy(c->offs + (size_t)(d - 1) * kMaxOffsets * kMaxEnumDim, t.data(), t.size(),
@@ -1093,11 +1100,13 @@ dbscan_status dbscan_border_ids(dbscan_ctx *c, int32_t *d_ids, int64_t capacity,
     B.n_max = c->last.n;
     B.nbr_stride = c->last.d <= kMaxEnumDim ? c->noff[c->last.d] : 0;
     CK(cudaMemsetAsync(&c->ctr->err, 0, sizeof(int), s));
+    const long long l0 = g_launches;
     if (!c->boff_ready) {
         launch_border_offsets(c->last, B, s);
         c->boff_ready = true;
     }
     launch_border(c->last_D, c->last_mode, true, c->last, B, nullptr, d_ids, capacity, c->ctr, s);
+    c->stats.kernel_launches += g_launches - l0;  // the run's count includes its border fill
     CK(cudaGetLastError());
     int err = 0;
     CK(cudaMemcpyAsync(&c->h_ctr->err, &c->ctr->err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1125,31 +1134,106 @@ dbscan_status dbscan_link_witnesses(dbscan_ctx *c, int32_t *d_rep, int32_t *d_li
     return DBSCAN_OK;
 }
 
-dbscan_status dbscan_run_host(dbscan_ctx *c, const void *h_points, int64_t n, int d, int dtype, double eps,
-                              int64_t min_pts, uint8_t *h_core, int32_t *h_labels, void *stream) {
-    if (!c) return DBSCAN_ERR_INVALID_ARG;
-    if (n < 0 || n > c->max_points || d < 1 || d > c->max_dim) return DBSCAN_ERR_INVALID_ARG;
-    if (dtype != DBSCAN_F32 && dtype != DBSCAN_F64) return DBSCAN_ERR_INVALID_ARG;
-    if (n > 0 && (!h_points || !h_core || !h_labels)) return DBSCAN_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
-    const size_t bytes = (size_t)n * d * (dtype == DBSCAN_F64 ? 8 : 4);
-    const size_t need = (size_t)c->max_points * c->max_dim * 8;
+// Device buffers of the host-buffer entry points: input (max_points x
+// max_dim doubles), core flags, labels, border offsets (allocated at the first
+// call) and border ids (grown to the largest set length seen).
+static dbscan_status ensure_host_bufs(dbscan_ctx *c, int64_t ids_need) {
     if (!c->d_in) {
-        CK(cudaMalloc(&c->d_in, std::max<size_t>(need, 8)));
-        c->d_in_bytes = std::max<size_t>(need, 8);
-        CK(cudaMalloc((void **)&c->d_core_h, std::max<int64_t>(c->max_points, 1)));
-        CK(cudaMalloc((void **)&c->d_lab_h, 4 * std::max<int64_t>(c->max_points, 1)));
+        const size_t need = std::max<size_t>((size_t)c->max_points * c->max_dim * 8, 8);
+        const int64_t N = std::max<int64_t>(c->max_points, 1);
+        CK(cudaMalloc(&c->d_in, need));
+        c->d_in_bytes = need;
+        CK(cudaMalloc((void **)&c->d_core_h, (size_t)N));
+        CK(cudaMalloc((void **)&c->d_lab_h, 4 * (size_t)N));
+        CK(cudaMalloc((void **)&c->d_off_h, 8 * (size_t)(N + 1)));
     }
-    if (n > 0) CK(cudaMemcpyAsync(c->d_in, h_points, bytes, cudaMemcpyHostToDevice, s));
-    dbscan_status st = dbscan_run(c, c->d_in, n, d, dtype, eps, min_pts, c->d_core_h, c->d_lab_h, nullptr,
-                                  nullptr, stream);
-    if (st != DBSCAN_OK) return st;
+    if (ids_need > c->d_ids_cap) {
+        cudaFree(c->d_ids_h);
+        c->d_ids_h = nullptr;
+        c->d_ids_cap = 0;
+        const int64_t cap = std::max<int64_t>(ids_need + ids_need / 4, 1024);
+        CK(cudaMalloc((void **)&c->d_ids_h, 4 * (size_t)cap));
+        c->d_ids_cap = cap;
+    }
+    return DBSCAN_OK;
+}
+
+// After a run on the context's device buffers: core flags, labels and, when
+// asked for, the border CSR back to the host.
+static dbscan_status host_outputs(dbscan_ctx *c, int64_t n, uint8_t *h_core, int32_t *h_labels,
+                                  int64_t *h_border_offsets, int32_t *h_border_ids, int64_t ids_capacity, int64_t K,
+                                  cudaStream_t s) {
     if (n > 0) {
         CK(cudaMemcpyAsync(h_core, c->d_core_h, (size_t)n, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(h_labels, c->d_lab_h, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
+        if (h_border_offsets)
+            CK(cudaMemcpyAsync(h_border_offsets, c->d_off_h, 8 * (size_t)(n + 1), cudaMemcpyDeviceToHost, s));
+    } else if (h_border_offsets) {
+        h_border_offsets[0] = 0;
     }
+    if (h_border_ids && K > 0) {
+        if (K > ids_capacity) return DBSCAN_ERR_CAPACITY;
+        const dbscan_status st = ensure_host_bufs(c, K);
+        if (st != DBSCAN_OK) return st;
+        const dbscan_status sb = dbscan_border_ids(c, c->d_ids_h, c->d_ids_cap, s);
+        if (sb != DBSCAN_OK) return sb;
+        CK(cudaMemcpyAsync(h_border_ids, c->d_ids_h, 4 * (size_t)K, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
     return DBSCAN_OK;
+}
+
+dbscan_status dbscan_run_host(dbscan_ctx *c, const void *h_points, int64_t n, int d, int dtype, double eps,
+                              int64_t min_pts, uint8_t *h_core, int32_t *h_labels, int64_t *h_border_offsets,
+                              int32_t *h_border_ids, int64_t ids_capacity, int64_t *num_border_memberships,
+                              void *stream) {
+    if (!c) return DBSCAN_ERR_INVALID_ARG;
+    if (num_border_memberships) *num_border_memberships = 0;
+    if (n < 0 || n > c->max_points || d < 1 || d > c->max_dim) return DBSCAN_ERR_INVALID_ARG;
+    if (dtype != DBSCAN_F32 && dtype != DBSCAN_F64) return DBSCAN_ERR_INVALID_ARG;
+    if (n > 0 && (!h_points || !h_core || !h_labels)) return DBSCAN_ERR_INVALID_ARG;
+    if (h_border_ids && (!h_border_offsets || ids_capacity < 0)) return DBSCAN_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = (size_t)n * d * (dtype == DBSCAN_F64 ? 8 : 4);
+    dbscan_status st = ensure_host_bufs(c, 0);
+    if (st != DBSCAN_OK) return st;
+    if (n > 0) CK(cudaMemcpyAsync(c->d_in, h_points, bytes, cudaMemcpyHostToDevice, s));
+    int64_t K = 0;
+    st = dbscan_run(c, c->d_in, n, d, dtype, eps, min_pts, c->d_core_h, c->d_lab_h,
+                    h_border_offsets ? c->d_off_h : nullptr, &K, stream);
+    if (st != DBSCAN_OK) return st;
+    if (num_border_memberships) *num_border_memberships = K;
+    return host_outputs(c, n, h_core, h_labels, h_border_offsets, h_border_ids, ids_capacity, K, s);
+}
+
+dbscan_status dbscan_run_batch_host(dbscan_ctx *c, const dbscan_instance *h_instances, int count,
+                                    const void *h_points, int ld, int dtype, uint8_t *h_core, int32_t *h_labels,
+                                    int64_t *h_border_offsets, int32_t *h_border_ids, int64_t ids_capacity,
+                                    int64_t *num_border_memberships, void *stream) {
+    if (!c || !h_instances || count < 1) return DBSCAN_ERR_INVALID_ARG;
+    if (num_border_memberships) *num_border_memberships = 0;
+    if (ld < 1 || ld > c->max_dim) return DBSCAN_ERR_UNSUPPORTED_DIM;
+    if (dtype != DBSCAN_F32 && dtype != DBSCAN_F64) return DBSCAN_ERR_INVALID_ARG;
+    int64_t N = 0;
+    for (int i = 0; i < count; ++i) {
+        if (h_instances[i].n < 0) return DBSCAN_ERR_INVALID_ARG;
+        N += h_instances[i].n;
+    }
+    if (N > c->max_points) return DBSCAN_ERR_INVALID_ARG;
+    if (N > 0 && (!h_points || !h_core || !h_labels)) return DBSCAN_ERR_INVALID_ARG;
+    if (h_border_ids && (!h_border_offsets || ids_capacity < 0)) return DBSCAN_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    dbscan_status st = ensure_host_bufs(c, 0);
+    if (st != DBSCAN_OK) return st;
+    if (N > 0)
+        CK(cudaMemcpyAsync(c->d_in, h_points, (size_t)N * ld * (dtype == DBSCAN_F64 ? 8 : 4), cudaMemcpyHostToDevice,
+                           s));
+    int64_t K = 0;
+    st = dbscan_run_batch(c, h_instances, count, c->d_in, ld, dtype, c->d_core_h, c->d_lab_h,
+                          h_border_offsets ? c->d_off_h : nullptr, &K, stream);
+    if (st != DBSCAN_OK) return st;
+    if (num_border_memberships) *num_border_memberships = K;
+    return host_outputs(c, N, h_core, h_labels, h_border_offsets, h_border_ids, ids_capacity, K, s);
 }
 
 }  // extern "C"

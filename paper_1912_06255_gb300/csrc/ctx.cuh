@@ -15,6 +15,8 @@ std::vector<signed char> offset_table(int d);
 int num_offsets(int d);
 }  // namespace gbdb
 
+constexpr int kPhases = 9;  // dbscan_stats.phase_ms
+
 struct dbscan_ctx {
     int device = 0;
     int64_t max_points = 0;
@@ -39,7 +41,7 @@ struct dbscan_ctx {
     int2 *wit = nullptr;    // [max_points] link witnesses (allocated while the option is on)
     long long wit_count = 0;
     bool have_wit = false;  // the last run recorded link witnesses
-    cudaEvent_t ev[9] = {};
+    cudaEvent_t ev[kPhases + 1] = {};
     // workspace
     void *arena = nullptr;
     size_t arena_bytes = 0;
@@ -114,6 +116,9 @@ struct dbscan_ctx {
     size_t d_in_bytes = 0;
     uint8_t *d_core_h = nullptr;
     int32_t *d_lab_h = nullptr;
+    int64_t *d_off_h = nullptr;
+    int32_t *d_ids_h = nullptr;
+    int64_t d_ids_cap = 0;
     // last run
     bool have_run = false;
     bool boff_ready = false;  // the last run's border-set offsets are in boff

@@ -674,6 +674,26 @@ k_super_insert(const uint64_t *__restrict__ cell_key, const int *__restrict__ po
 
 constexpr int NBS_WARPS = 8;  // warps per block of k_neighbors_super
 
+// Distance class of a neighbouring cell with n1 coordinates at |delta| = 1,
+// n2 at |delta| = 2 and the rest at 0: its rank in the order of the offset
+// table, by (sum_j max(|delta_j| - 1, 0)^2, sum_j delta_j^2) = (n2, n1 + 4 n2),
+// i.e. by n2, then n1.  Classes 0 .. D-1 are the adjacent cells (n2 = 0).
+template <int D> __device__ __forceinline__ unsigned super_class(int n1, int n2) {
+    return n2 == 0 ? (unsigned)(n1 - 1) : (unsigned)(D + (n2 - 1) * (D + 1) - (n2 - 1) * n2 / 2 + n1);
+}
+template <int D> __host__ __device__ constexpr int super_classes() { return D == 2 ? 5 : 9; }
+constexpr unsigned kNoClass = 15u;
+__constant__ signed char kProbe2[9] = {4, 1, 3, 5, 7, 0, 2, 6, 8};
+__constant__ signed char kProbe3[27] = {13, 4, 10, 12, 14, 16, 22, 1, 3, 5, 7, 9, 11, 15,
+                                        17, 19, 21, 23, 25, 0, 2, 6, 8, 18, 20, 24, 26};
+// lanes whose 4-bit code is q, from the four bit-plane ballots of the codes
+__device__ __forceinline__ unsigned class_mask(const unsigned (&b)[4], unsigned q) {
+    unsigned m = ~0u;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) m &= ((q >> t) & 1u) ? b[t] : ~b[t];
+    return m;
+}
+
 template <int D>
 __global__ void __launch_bounds__(32 * NBS_WARPS)
 k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict__ ht,
@@ -686,7 +706,6 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
     constexpr int CH = (NS * K + 31) / 32;     // 32-candidate chunks
     __shared__ int s_cc[NBS_WARPS][K][D];      // own cells' coordinates
     __shared__ float4 s_lo[NBS_WARPS][K], s_hi[NBS_WARPS][K];
-    __shared__ unsigned s_near[NBS_WARPS][CH][K], s_far[NBS_WARPS][CH][K];
     if (ctr->err) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
@@ -695,6 +714,7 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
     const int lg = hash_log2(cap);
     const uint64_t mask = cap - 1;
     const int blg = super_bloom_lg(m, bloom_lg);
+    const bool ordered = (long long)P.n >= 4ll * m;
     long long total = 0;
     for (int si = warp_id_global(); si < ms; si += warps_global()) {
         const int c0 = sc_first[si];
@@ -719,12 +739,12 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
             }
         }
         __syncwarp();
-        // lane l < NS probes supercell S + o(l); lane 0 takes S itself
+        // lane l < NS probes supercell S + o(l): S itself, then the supercells
+        // sharing a face, an edge, a corner with it (ternary index of o + 1)
         const uint64_t skey = (cell_key[c0] ^ ibits) >> D;
         int t0 = 0, kt = 0;
         if (lane < NS && k > 0) {
-            const int ctr_i = (NS - 1) / 2;
-            int t = lane == 0 ? ctr_i : (lane <= ctr_i ? lane - 1 : lane);
+            int t = D == 2 ? kProbe2[lane] : kProbe3[lane];
             int o[D];
             bool in = true;
 #pragma unroll
@@ -761,12 +781,16 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
         const int excl = incl - kt;
         const int ncand = __shfl_sync(0xffffffffu, incl, 31);
         const int nch = (ncand + 31) >> 5;
+        // test pass: per candidate (lane, chunk) and own cell i, the 4-bit class
+        // code of the pair in cls[ch] bits 4i..4i+3 (kNoClass: not neighbours)
         int hreg[CH];
         int hsz[CH];
+        unsigned cls[CH];
 #pragma unroll
         for (int ch = 0; ch < CH; ++ch) {
             hreg[ch] = -1;
             hsz[ch] = 0;
+            cls[ch] = ~0u;
             if (ch >= nch) continue;
             const int f = ch * 32 + lane;
             int j = 0;  // owner lane: the last lane whose range starts at or before f
@@ -776,79 +800,122 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
                 if (j + step < 32 && ex <= f) j += step;
             }
             const int h = __shfl_sync(0xffffffffu, t0, j) + f - __shfl_sync(0xffffffffu, excl, j);
-            const bool valid = f < ncand;
+            if (f >= ncand) continue;
             int hc[kMaxDim];
+            morton_decode(cell_key[h] ^ ibits, D, I.bits, hc);
             float4 hl = make_float4(0.f, 0.f, 0.f, 0.f), hh = hl;
-            if (valid) {
-                morton_decode(cell_key[h] ^ ibits, D, I.bits, hc);
-                if (P.box) {
-                    hl = blo[h];
-                    hh = bhi[h];
-                }
-                if (nbr_pts) hsz[ch] = cell_start[h + 1] - cell_start[h];
-                hreg[ch] = h;
+            if (P.box) {
+                hl = blo[h];
+                hh = bhi[h];
             }
+            if (nbr_pts) hsz[ch] = cell_start[h + 1] - cell_start[h];
+            hreg[ch] = h;
             for (int i = 0; i < k; ++i) {
-                bool near = false, far = false;
-                if (valid && h != c0 + i) {
-                    int g = 0, a = 0;
+                if (h == c0 + i) continue;
+                int n1 = 0, n2 = 0, g = 0;
 #pragma unroll
-                    for (int jj = 0; jj < D; ++jj) {
-                        const int dl = abs(hc[jj] - s_cc[w][i][jj]);
-                        a = max(a, dl);
-                        const int e = max(dl - 1, 0);
-                        g += e * e;
-                    }
-                    bool pass = g <= I.d;
-                    if (pass && P.box) {
-                        Bx<D> al, ah, bl, bh;
-                        al.v[0] = s_lo[w][i];
-                        ah.v[0] = s_hi[w][i];
-                        bl.v[0] = hl;
-                        bh.v[0] = hh;
-                        pass = boxes_min_d2<D>(al, ah, bl, bh) <= hi_thr;
-                    }
-                    near = pass && a <= 1;
-                    far = pass && a > 1;
+                for (int jj = 0; jj < D; ++jj) {
+                    const int dl = abs(hc[jj] - s_cc[w][i][jj]);
+                    n1 += dl == 1;
+                    n2 += dl == 2;
+                    const int e = max(dl - 1, 0);
+                    g += e * e;
                 }
-                const unsigned nm = __ballot_sync(0xffffffffu, near);
-                const unsigned fm = __ballot_sync(0xffffffffu, far);
-                if (lane == 0) {
-                    s_near[w][ch][i] = nm;
-                    s_far[w][ch][i] = fm;
+                bool pass = g <= I.d;
+                if (pass && P.box) {
+                    Bx<D> al, ah, bl, bh;
+                    al.v[0] = s_lo[w][i];
+                    ah.v[0] = s_hi[w][i];
+                    bl.v[0] = hl;
+                    bh.v[0] = hh;
+                    pass = boxes_min_d2<D>(al, ah, bl, bh) <= hi_thr;
                 }
+                if (pass) cls[ch] &= ~(((unsigned)(kNoClass - super_class<D>(n1, n2))) << (4 * i));
             }
         }
-        __syncwarp();
-        // counts per own cell (lane i), then the lists: adjacent cells first
-        int nn = 0, nf = 0;
-        if (lane < k) {
-            for (int ch = 0; ch < nch; ++ch) {
-                nn += __popc(s_near[w][ch][lane]);
-                nf += __popc(s_far[w][ch][lane]);
+        // lists in the order of the offset table (nearest first): a counting
+        // sort over the classes, from four bit-plane ballots of the codes.
+        // MarkCore stops at minPts, so that order pays where cells hold many
+        // points; with fewer than 4 points per cell on average the lists only
+        // split adjacent and farther cells (each in probe order).
+        if (!ordered) {
+            for (int i = 0; i < k; ++i) {
+                int nn = 0, nf = 0;
+#pragma unroll
+                for (int ch = 0; ch < CH; ++ch) {
+                    if (ch >= nch) break;
+                    const unsigned code = (cls[ch] >> (4 * i)) & 15u;
+                    nn += __popc(__ballot_sync(0xffffffffu, code < (unsigned)D));
+                    nf += __popc(__ballot_sync(0xffffffffu, code != kNoClass && code >= (unsigned)D));
+                }
+                if (lane == 0) {
+                    nbr_cnt[c0 + i] = nn + nf;
+                    nbr_near[c0 + i] = nn;
+                }
+                total += lane == 0 ? nn + nf : 0;
+                const long long base = (long long)(c0 + i) * stride;
+                int ncur = 0, fcur = nn, pts = 0;
+#pragma unroll
+                for (int ch = 0; ch < CH; ++ch) {
+                    if (ch >= nch) break;
+                    const unsigned code = (cls[ch] >> (4 * i)) & 15u;
+                    const bool near = code < (unsigned)D, far = code != kNoClass && !near;
+                    const unsigned nb = __ballot_sync(0xffffffffu, near), fb = __ballot_sync(0xffffffffu, far);
+                    if (near) nbr[base + ncur + __popc(nb & lt)] = hreg[ch];
+                    if (far) nbr[base + fcur + __popc(fb & lt)] = hreg[ch];
+                    if (near || far) pts += hsz[ch];
+                    ncur += __popc(nb);
+                    fcur += __popc(fb);
+                }
+                if (nbr_pts) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) pts += __shfl_xor_sync(0xffffffffu, pts, o);
+                    if (lane == 0) nbr_pts[c0 + i] = pts;
+                }
             }
-            nbr_cnt[c0 + lane] = nn + nf;
-            nbr_near[c0 + lane] = nn;
-            total += nn + nf;
+            continue;
         }
         for (int i = 0; i < k; ++i) {
+            int cnt = 0;
+#pragma unroll
+            for (int ch = 0; ch < CH; ++ch) {
+                if (ch >= nch) break;
+                const unsigned code = (cls[ch] >> (4 * i)) & 15u;
+                unsigned b[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) b[q] = __ballot_sync(0xffffffffu, (code >> q) & 1u);
+                if (lane < super_classes<D>()) cnt += __popc(class_mask(b, (unsigned)lane));
+            }
+            int incl = cnt;  // lanes >= the class count add nothing
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            int run = incl - cnt;  // lane q: next position of class q
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            const int nn = __shfl_sync(0xffffffffu, incl, D - 1);  // classes 0 .. D-1: |delta|_inf = 1
+            if (lane == 0) {
+                nbr_cnt[c0 + i] = tot;
+                nbr_near[c0 + i] = nn;
+            }
+            total += lane == 0 ? tot : 0;
             const long long base = (long long)(c0 + i) * stride;
-            int ncur = 0, fcur = __shfl_sync(0xffffffffu, nn, i);
             int pts = 0;
 #pragma unroll
             for (int ch = 0; ch < CH; ++ch) {
                 if (ch >= nch) break;
-                const unsigned nm = s_near[w][ch][i], fm = s_far[w][ch][i];
-                if ((nm >> lane) & 1u) {
-                    nbr[base + ncur + __popc(nm & lt)] = hreg[ch];
+                const unsigned code = (cls[ch] >> (4 * i)) & 15u;
+                unsigned b[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) b[q] = __ballot_sync(0xffffffffu, (code >> q) & 1u);
+                const unsigned mine = class_mask(b, code);
+                const int at = __shfl_sync(0xffffffffu, run, (int)code);
+                if (code != kNoClass) {
+                    nbr[base + at + __popc(mine & lt)] = hreg[ch];
                     pts += hsz[ch];
                 }
-                if ((fm >> lane) & 1u) {
-                    nbr[base + fcur + __popc(fm & lt)] = hreg[ch];
-                    pts += hsz[ch];
-                }
-                ncur += __popc(nm);
-                fcur += __popc(fm);
+                if (lane < super_classes<D>()) run += __popc(class_mask(b, (unsigned)lane));
             }
             if (nbr_pts) {
 #pragma unroll
@@ -862,14 +929,12 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
     if (lane == 0 && total) atomicAdd((unsigned long long *)&ctr->E, (unsigned long long)total);
 }
 
-void launch_neighbors_super(const Semisort &S, const RunParams &P, int stride, const float4 *blo,
-                            const float4 *bhi, const int *cell_start, int *nbr_cnt, int *nbr_near, int *nbr_pts,
-                            int *nbr, DevCounters *ctr, cudaStream_t s) {
+void launch_super_table(const Semisort &S, const RunParams &P, DevCounters *ctr, cudaStream_t s) {
     // the cells' slots are free again: the supercells take the table
     launch_table_reset(S, ctr, s, false);
     int *pos = S.count;  // [m + 1], scratch until the compaction
     int *sc_first = reinterpret_cast<int *>(S.rank_of);  // free once the points are scattered
-    auto go = [&](auto kf, auto ki, auto kn) {
+    auto go = [&](auto kf, auto ki) {
         int g = grid_for((const void *)kf, 256);
         kf<<<g, 256, 0, s>>>(S.cell_key, pos, S.bloom_all, S.bloom_lg, ctr);
         count_launch();
@@ -877,13 +942,23 @@ void launch_neighbors_super(const Semisort &S, const RunParams &P, int stride, c
         g = grid_for((const void *)ki, 256);
         ki<<<g, 256, 0, s>>>(S.cell_key, pos, S.ht, S.slots, sc_first, S.bloom_all, S.bloom_lg, ctr);
         count_launch();
-        g = grid_for((const void *)kn, 32 * NBS_WARPS);
+    };
+    if (P.d == 2) go(k_super_flags<2>, k_super_insert<2>);
+    else go(k_super_flags<3>, k_super_insert<3>);
+}
+
+void launch_neighbors_super(const Semisort &S, const RunParams &P, int stride, const float4 *blo,
+                            const float4 *bhi, const int *cell_start, int *nbr_cnt, int *nbr_near, int *nbr_pts,
+                            int *nbr, DevCounters *ctr, cudaStream_t s) {
+    const int *sc_first = reinterpret_cast<const int *>(S.rank_of);
+    auto go = [&](auto kn) {
+        const int g = grid_for((const void *)kn, 32 * NBS_WARPS);
         kn<<<g, 32 * NBS_WARPS, 0, s>>>(S.cell_key, S.ht, S.bloom_all, S.bloom_lg, sc_first, cell_start, nbr_pts, P,
                                         stride, blo, bhi, nbr_cnt, nbr_near, nbr, ctr);
         count_launch();
     };
-    if (P.d == 2) go(k_super_flags<2>, k_super_insert<2>, k_neighbors_super<2>);
-    else go(k_super_flags<3>, k_super_insert<3>, k_neighbors_super<3>);
+    if (P.d == 2) go(k_neighbors_super<2>);
+    else go(k_neighbors_super<3>);
 }
 
 void launch_neighbors(const uint64_t *cell_key, const ulonglong2 *ht, uint64_t hcap, const unsigned *bloom,

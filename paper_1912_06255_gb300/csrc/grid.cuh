@@ -48,8 +48,10 @@ void launch_semisort(const void *X, int dtype, const RunParams &P, int SD, const
 // Empty the slots the run used (keeps the table clean for the next run): the
 // cells' slots, or at the end of a supercell run the supercells' slots.
 void launch_table_reset(const Semisort &S, DevCounters *ctr, cudaStream_t s, bool end_of_run = true);
-// Neighbour lists for d = 2, 3 through supercells (fixed stride per cell, as
-// launch_neighbors); empties the cells' slots of the hash first.
+// The supercell table of d = 2, 3 (empties the cells' slots of the hash
+// first), then the neighbour lists through it (fixed stride per cell, as
+// launch_neighbors).
+void launch_super_table(const Semisort &S, const RunParams &P, DevCounters *ctr, cudaStream_t s);
 void launch_neighbors_super(const Semisort &S, const RunParams &P, int stride, const float4 *blo,
                             const float4 *bhi, const int *cell_start, int *nbr_cnt, int *nbr_near, int *nbr_pts,
                             int *nbr, DevCounters *ctr, cudaStream_t s);
@@ -128,9 +130,10 @@ struct HdBufs {
     long long *nbr_off;           // [m+1] offset of each cell's neighbour list
     int *scratch;                 // per-warp leaf scratch of the neighbour kernel
 };
-// Cells of the sorted points and their tree.  key_bits = d * bits.
+// Cells of the sorted points (key_bits = d * bits), then their boxes and tree.
 void hd_cells(const void *X, int dtype, const RunParams &P, int key_bits, const HdBufs &H, const Bufs &B,
               DevCounters *ctr, cudaStream_t s);
+void hd_tree(const RunParams &P, const HdBufs &H, const Bufs &B, DevCounters *ctr, cudaStream_t s);
 // The neighbour lists into nbr (cap entries), one walk per 32 cells; ctr->E
 // (zero before) receives the total, which exceeds cap if nbr was too small.
 void hd_neighbors(const RunParams &P, const HdBufs &H, const Bufs &B, int *nbr, long long cap, DevCounters *ctr,

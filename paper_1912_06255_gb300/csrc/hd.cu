@@ -528,7 +528,7 @@ template <typename T> void hd_launch_cells(const void *X, const RunParams &P, co
 
 }  // namespace
 
-// Steps 1-3 above: keys, sort, cells, boxes and the tree.
+// Steps 1-2 above: keys, sort, cells.
 void hd_cells(const void *X, int dtype, const RunParams &P, int key_bits, const HdBufs &H, const Bufs &B,
               DevCounters *ctr, cudaStream_t s) {
     const int n = P.n;
@@ -560,6 +560,10 @@ void hd_cells(const void *X, int dtype, const RunParams &P, int key_bits, const 
     scan_i32_to_i32(B.core_s, B.core_pos, n, nullptr, n, B.part, s);
     if (dtype == DBSCAN_F32) hd_launch_cells<float>(X, P, H, B, idx, ctr, s);
     else hd_launch_cells<double>(X, P, H, B, idx, ctr, s);
+}
+
+// Step 3: the cells' point boxes and the tree over the cells.
+void hd_tree(const RunParams &P, const HdBufs &H, const Bufs &B, DevCounters *ctr, cudaStream_t s) {
     if (P.box) launch_boxes(8, B.pf, B.cell_start, ctr, const_cast<float4 *>(B.blo), const_cast<float4 *>(B.bhi), s);
     int g = grid_for((const void *)k_lbvh_nodes, 256);
     k_lbvh_nodes<<<g, 256, 0, s>>>(H.ckey_lo, H.ckey_hi, H.child, H.parent, H.flag, ctr);

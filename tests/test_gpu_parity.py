@@ -212,13 +212,39 @@ def test_edge_cases():
 
 
 def test_host_entry_point_matches_device():
+    """dbscan_run_host from pinned host buffers, with and without the border
+    sets (a too small ids buffer reports CAPACITY and the needed length), and
+    dbscan_run_batch_host on two instances."""
     X = synth.random_small(8, 10000, 3, dtype=np.float32)
     ctx = DBSCAN(len(X), 3)
     pinned = torch.from_numpy(X).pin_memory()
-    core, labels = ctx.run_host(pinned, 0.3, 8, core=torch.empty(len(X), dtype=torch.uint8).pin_memory(),
-                                labels=torch.empty(len(X), dtype=torch.int32).pin_memory())
     exp = oracle.dbscan(X, 0.3, 8)
+    core, labels, k = ctx.run_host(pinned, 0.3, 8, core=torch.empty(len(X), dtype=torch.uint8).pin_memory(),
+                                   labels=torch.empty(len(X), dtype=torch.int32).pin_memory())
     assert np.array_equal(core.numpy(), exp[0]) and np.array_equal(labels.numpy(), exp[1])
+    assert k == len(exp[3]) > 0
+    off = torch.empty(len(X) + 1, dtype=torch.int64).pin_memory()
+    with pytest.raises(DbscanError) as e:
+        ctx.run_host(pinned, 0.3, 8, border=(off, torch.empty(k - 1, dtype=torch.int32)))
+    assert e.value.status == 5
+    ids = torch.empty(k, dtype=torch.int32).pin_memory()
+    core, labels, k2 = ctx.run_host(pinned, 0.3, 8, border=(off, ids))
+    assert k2 == k and np.array_equal(off.numpy(), exp[2]) and np.array_equal(ids.numpy(), exp[3])
+    assert np.array_equal(labels.numpy(), exp[1])
+    # the batch form
+    Y = synth.random_small(9, 4000, 2, dtype=np.float32)
+    P = np.zeros((len(X) + len(Y), 3), np.float32)
+    P[:len(X)] = X
+    P[len(X):, :2] = Y
+    bctx = DBSCAN(len(P), 3)
+    boff = torch.empty(len(P) + 1, dtype=torch.int64)
+    bids = torch.empty(4 * len(P), dtype=torch.int32)
+    core, labels, kb = bctx.run_batch_host(P, [(len(X), 3, 0.3, 8), (len(Y), 2, 0.2, 5)], border=(boff, bids))
+    ey = oracle.dbscan(Y, 0.2, 5)
+    assert np.array_equal(labels.numpy()[:len(X)], exp[1]) and np.array_equal(labels.numpy()[len(X):], ey[1])
+    assert kb == len(exp[3]) + len(ey[3])
+    o = boff.numpy()
+    assert np.array_equal(bids.numpy()[o[len(X)]:o[-1]], ey[3])
 
 
 def test_invalid_arguments():
