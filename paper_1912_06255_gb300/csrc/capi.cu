@@ -327,7 +327,8 @@ static dbscan_status enqueue_hash_cells(dbscan_ctx *c, const RunParams &P, int S
     }
     // the Bloom filter of the cell keys pays only when the hash table does not
     // fit in L2 (the supercell path keeps its own filter in the same storage)
-    const bool use_bloom = !S.super && 16 * c->hcap > ((uint64_t)96 << 20);
+    const bool use_bloom = 16 * c->hcap > ((uint64_t)96 << 20);
+    S.n = P.n;
     S.bloom = use_bloom ? c->bloom : nullptr;
     S.bloom_all = c->bloom;
     S.bloom_lg = c->bloom_lg;
@@ -338,19 +339,17 @@ static dbscan_status enqueue_hash_cells(dbscan_ctx *c, const RunParams &P, int S
     mark(3);
     if (P.box) launch_boxes(SD, c->pf, c->cell_start, c->ctr, c->blo, c->bhi, s);
     int *nbr_pts = P.mc_small_nbr > 0 && P.mc_small_nbr < (1 << 30) ? c->nbr_pts : nullptr;
-    if (S.super) {
-        launch_super_table(S, P, c->ctr, s);
-        mark(4);
+    if (S.super) launch_super_table(S, P, c->ctr, s);  // returns at once on a dense grid
+    mark(4);
+    int n_near = 1;
+    for (int j = 0; j < d_enum; ++j) n_near *= 3;
+    // d = 2, 3: the offset enumeration runs only on a dense grid, the supercells only on a sparse one
+    launch_neighbors(c->cell_key, c->ht, c->hcap, S.bloom, c->bloom_lg, P, offs_for(c, d_enum), c->noff[d_enum],
+                     n_near - 1, c->blo, c->bhi, c->cell_start, c->nbr_cnt, c->nbr_near, nbr_pts, c->nbr, c->ctr,
+                     s, S.super);
+    if (S.super)
         launch_neighbors_super(S, P, c->noff[d_enum], c->blo, c->bhi, c->cell_start, c->nbr_cnt, c->nbr_near,
                                nbr_pts, c->nbr, c->ctr, s);
-    } else {
-        mark(4);
-        int n_near = 1;
-        for (int j = 0; j < d_enum; ++j) n_near *= 3;
-        launch_neighbors(c->cell_key, c->ht, c->hcap, S.bloom, c->bloom_lg, P, offs_for(c, d_enum),
-                         c->noff[d_enum], n_near - 1, c->blo, c->bhi, c->cell_start, c->nbr_cnt, c->nbr_near,
-                         nbr_pts, c->nbr, c->ctr, s);
-    }
     c->nbr_cur = c->nbr;
     c->nbr_off_cur = nullptr;
     return DBSCAN_OK;

@@ -138,6 +138,12 @@ __device__ __forceinline__ uint64_t cell_key_of(const RunParams &P, int inst, co
     return P.ninst > 1 ? (((uint64_t)inst << P.inst_shift) | k) : k;
 }
 
+// Grids with at least 8 points per cell on average take the offset
+// enumeration of k_neighbors (nearest cells first, so MarkCore's early exit
+// comes sooner); sparser ones the supercells.  Decided on the device, where m
+// is known; the kernels of the other path return at once.
+__device__ __forceinline__ bool grid_dense(long long n, int m) { return n >= 8ll * m; }
+
 constexpr int INS_U = 4;  // points per thread per step (their probes overlap)
 
 template <typename T>
@@ -300,8 +306,11 @@ k_scatter_points(const T *__restrict__ X, RunParams P, const ulonglong2 *__restr
 // Return the slots this run used to empty.
 __global__ void __launch_bounds__(256)
 k_table_reset(ulonglong2 *__restrict__ ht, unsigned *__restrict__ hcnt, const uint32_t *__restrict__ slots,
-              const DevCounters *ctr) {
+              const DevCounters *ctr, int n, int cond) {
     const int m = ctr->m;
+    // cond 1: only on a sparse grid (before its supercells take the table);
+    // cond 2: only on a dense grid (its cells kept the table to the end)
+    if (cond && (cond == 2) != grid_dense(n, m)) return;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
         const uint32_t s = slots[c];
         ht[s] = make_ulonglong2(kEmptyKey, 0);
@@ -359,14 +368,14 @@ k_super_reset(ulonglong2 *__restrict__ ht, const uint32_t *__restrict__ sslots, 
 }
 
 void launch_table_reset(const Semisort &S, DevCounters *ctr, cudaStream_t s, bool end_of_run) {
-    if (end_of_run && S.super) {
+    if (end_of_run && S.super) {  // the supercells' slots (none on a dense grid), or the cells' on a dense grid
         const int g = grid_for((const void *)k_super_reset, 256);
         k_super_reset<<<g, 256, 0, s>>>(S.ht, S.slots, ctr);
         count_launch();
-        return;
     }
+    const int cond = S.super ? (end_of_run ? 2 : 1) : 0;
     int g = grid_for((const void *)k_table_reset, 256);
-    k_table_reset<<<g, 256, 0, s>>>(S.ht, S.hcnt, S.slots, ctr); count_launch();
+    k_table_reset<<<g, 256, 0, s>>>(S.ht, S.hcnt, S.slots, ctr, S.n, cond); count_launch();
 }
 
 // ---------------------------------------------------------------- boxes
@@ -499,8 +508,9 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
             RunParams P,
             const signed char *__restrict__ offs, int noff, int n_near, const float4 *__restrict__ blo,
             const float4 *__restrict__ bhi, int *__restrict__ nbr_cnt, int *__restrict__ nbr_near,
-            int *__restrict__ nbr, DevCounters *ctr) {
+            int *__restrict__ nbr, int only_dense, DevCounters *ctr) {
     const int m = ctr->m;
+    if (only_dense && !grid_dense(P.n, m)) return;  // k_neighbors_super takes sparse grids
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     long long total = 0;
@@ -617,9 +627,10 @@ __host__ __device__ __forceinline__ int super_bloom_lg(int m, int bloom_lg) {
 template <int D>
 __global__ void __launch_bounds__(256)
 k_super_flags(const uint64_t *__restrict__ cell_key, int *__restrict__ flag, unsigned *__restrict__ bloom,
-              int bloom_lg, const DevCounters *ctr) {
+              int bloom_lg, const RunParams P, const DevCounters *ctr) {
     if (ctr->err) return;
     const int m = ctr->m;
+    if (grid_dense(P.n, m)) return;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     for (long long c = t0; c < m; c += stride)
@@ -636,9 +647,10 @@ template <int D>
 __global__ void __launch_bounds__(256)
 k_super_insert(const uint64_t *__restrict__ cell_key, const int *__restrict__ pos, ulonglong2 *__restrict__ ht,
                uint32_t *__restrict__ sslots, int *__restrict__ sc_first, unsigned *__restrict__ bloom, int bloom_lg,
-               DevCounters *ctr) {
+               const RunParams P, DevCounters *ctr) {
     if (ctr->err) return;
     const int m = ctr->m;
+    if (grid_dense(P.n, m)) return;
     const int ms = pos[m];
     if (blockIdx.x == 0 && threadIdx.x == 0) ctr->ms = ms;
     const uint64_t cap = hash_capacity(ms);
@@ -674,26 +686,19 @@ k_super_insert(const uint64_t *__restrict__ cell_key, const int *__restrict__ po
 
 constexpr int NBS_WARPS = 8;  // warps per block of k_neighbors_super
 
-// Distance class of a neighbouring cell with n1 coordinates at |delta| = 1,
-// n2 at |delta| = 2 and the rest at 0: its rank in the order of the offset
-// table, by (sum_j max(|delta_j| - 1, 0)^2, sum_j delta_j^2) = (n2, n1 + 4 n2),
-// i.e. by n2, then n1.  Classes 0 .. D-1 are the adjacent cells (n2 = 0).
-template <int D> __device__ __forceinline__ unsigned super_class(int n1, int n2) {
-    return n2 == 0 ? (unsigned)(n1 - 1) : (unsigned)(D + (n2 - 1) * (D + 1) - (n2 - 1) * n2 / 2 + n1);
-}
-template <int D> __host__ __device__ constexpr int super_classes() { return D == 2 ? 5 : 9; }
-constexpr unsigned kNoClass = 15u;
-__constant__ signed char kProbe2[9] = {4, 1, 3, 5, 7, 0, 2, 6, 8};
-__constant__ signed char kProbe3[27] = {13, 4, 10, 12, 14, 16, 22, 1, 3, 5, 7, 9, 11, 15,
-                                        17, 19, 21, 23, 25, 0, 2, 6, 8, 18, 20, 24, 26};
-// lanes whose 4-bit code is q, from the four bit-plane ballots of the codes
-__device__ __forceinline__ unsigned class_mask(const unsigned (&b)[4], unsigned q) {
-    unsigned m = ~0u;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) m &= ((q >> t) & 1u) ? b[t] : ~b[t];
-    return m;
-}
-
+// One warp per supercell S of a sparse grid.  Lane t < 3^D probes supercell
+// S + o(t) (o: the base-3 digits of t minus 1).  A candidate cell h of that
+// supercell has its coordinates, relative to S's first corner, at
+// 2 o + q(h), where q(h) are the lowest D bits of its key (one bit per
+// dimension); an own cell c sits at p(c), its own lowest bits, so the offset
+// is delta = 2 o + q(h) - p(c) without decoding any key.  Every candidate
+// coordinate differs by at most 3 per dimension, and the offset rule
+// sum_j max(|delta_j| - 1, 0)^2 <= d holds iff |delta_j| <= 2 in every
+// dimension (a coordinate at 2 adds 1; only the instance's own d
+// coordinates can differ).  Each candidate (a lane) tests all own cells;
+// the 2-bit outcomes (adjacent, farther, none) of own cell i sit in bits
+// 2i, 2i+1 of a register per 32-candidate chunk, and the lists are written
+// adjacent cells first, from two ballots per chunk.
 template <int D>
 __global__ void __launch_bounds__(32 * NBS_WARPS)
 k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict__ ht,
@@ -701,20 +706,20 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
                   const int *__restrict__ cell_start, int *__restrict__ nbr_pts, RunParams P, int stride,
                   const float4 *__restrict__ blo, const float4 *__restrict__ bhi, int *__restrict__ nbr_cnt,
                   int *__restrict__ nbr_near, int *__restrict__ nbr, DevCounters *ctr) {
-    constexpr int K = 1 << D;                  // cells per supercell
-    constexpr int NS = D == 2 ? 9 : 27;        // supercells probed, the own one included
-    constexpr int CH = (NS * K + 31) / 32;     // 32-candidate chunks
-    __shared__ int s_cc[NBS_WARPS][K][D];      // own cells' coordinates
+    constexpr int K = 1 << D;              // cells per supercell
+    constexpr int NS = D == 2 ? 9 : 27;    // supercells probed, the own one included
+    constexpr int CH = (NS * K + 31) / 32; // 32-candidate chunks
+    constexpr uint64_t QMASK = (1u << D) - 1u;
     __shared__ float4 s_lo[NBS_WARPS][K], s_hi[NBS_WARPS][K];
     if (ctr->err) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int m = ctr->m, ms = ctr->ms;
+    if (grid_dense(P.n, m)) return;  // k_neighbors takes dense grids
     const uint64_t cap = hash_capacity(ms);
     const int lg = hash_log2(cap);
     const uint64_t mask = cap - 1;
     const int blg = super_bloom_lg(m, bloom_lg);
-    const bool ordered = (long long)P.n >= 4ll * m;
     long long total = 0;
     for (int si = warp_id_global(); si < ms; si += warps_global()) {
         const int c0 = sc_first[si];
@@ -726,32 +731,40 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
         const int ii = inst_of_cell(P, c0);
         const Inst &I = P.inst[ii];
         const uint64_t ibits = P.ninst > 1 ? ((uint64_t)ii << P.inst_shift) : 0;
-        const float hi_thr = I.cthr.hi;  // eps, or eps(1 + rho) for approximate connectivity
+        const uint64_t key0 = cell_key[c0] ^ ibits;
+        // own cells: boxes to shared memory, the D-bit positions p(c) packed
+        // D bits per cell into pown (warp-uniform)
         __syncwarp();
+        unsigned pmine = 0;
         if (lane < k) {
-            int cc[kMaxDim];
-            morton_decode(cell_key[c0 + lane] ^ ibits, D, I.bits, cc);
-#pragma unroll
-            for (int j = 0; j < D; ++j) s_cc[w][lane][j] = cc[j];
+            pmine = (unsigned)(cell_key[c0 + lane] & QMASK);
             if (P.box) {
                 s_lo[w][lane] = blo[c0 + lane];
                 s_hi[w][lane] = bhi[c0 + lane];
             }
         }
+        unsigned pown = 0;
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            const unsigned bb = __ballot_sync(0xffffffffu, (pmine >> b) & 1u);
+#pragma unroll
+            for (int i = 0; i < K; ++i) pown |= ((bb >> i) & 1u) << (D * i + b);
+        }
         __syncwarp();
-        // lane l < NS probes supercell S + o(l): S itself, then the supercells
-        // sharing a face, an edge, a corner with it (ternary index of o + 1)
-        const uint64_t skey = (cell_key[c0] ^ ibits) >> D;
+        // the supercell's coordinates, for the bounds of the probes
+        int sc[kMaxDim];
+        morton_decode(key0 >> D, D, I.bits > 1 ? I.bits - 1 : 1, sc);
+        const uint64_t skey = key0 >> D;
         int t0 = 0, kt = 0;
         if (lane < NS && k > 0) {
-            int t = D == 2 ? kProbe2[lane] : kProbe3[lane];
             int o[D];
             bool in = true;
+            int t = lane;
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 o[j] = t % 3 - 1;
                 t /= 3;
-                const int v = (s_cc[w][0][j] >> 1) + o[j];
+                const int v = sc[j] + o[j];
                 in = in && v >= 0 && v <= (I.kmax[j] >> 1);
             }
             if (in) {
@@ -781,16 +794,13 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
         const int excl = incl - kt;
         const int ncand = __shfl_sync(0xffffffffu, incl, 31);
         const int nch = (ncand + 31) >> 5;
-        // test pass: per candidate (lane, chunk) and own cell i, the 4-bit class
-        // code of the pair in cls[ch] bits 4i..4i+3 (kNoClass: not neighbours)
+        const float hi_thr = I.cthr.hi;  // eps, or eps(1 + rho) for approximate connectivity
         int hreg[CH];
-        int hsz[CH];
-        unsigned cls[CH];
+        unsigned cls[CH];  // 2 bits per own cell: 1 adjacent, 2 farther, 0 not a neighbour
 #pragma unroll
         for (int ch = 0; ch < CH; ++ch) {
             hreg[ch] = -1;
-            hsz[ch] = 0;
-            cls[ch] = ~0u;
+            cls[ch] = 0u;
             if (ch >= nch) continue;
             const int f = ch * 32 + lane;
             int j = 0;  // owner lane: the last lane whose range starts at or before f
@@ -801,121 +811,68 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
             }
             const int h = __shfl_sync(0xffffffffu, t0, j) + f - __shfl_sync(0xffffffffu, excl, j);
             if (f >= ncand) continue;
-            int hc[kMaxDim];
-            morton_decode(cell_key[h] ^ ibits, D, I.bits, hc);
-            float4 hl = make_float4(0.f, 0.f, 0.f, 0.f), hh = hl;
-            if (P.box) {
-                hl = blo[h];
-                hh = bhi[h];
-            }
-            if (nbr_pts) hsz[ch] = cell_start[h + 1] - cell_start[h];
             hreg[ch] = h;
-            for (int i = 0; i < k; ++i) {
-                if (h == c0 + i) continue;
-                int n1 = 0, n2 = 0, g = 0;
+            const unsigned q = (unsigned)(cell_key[h] & QMASK);
+            int rel[D];  // 2 o + q, per dimension (o from the owner lane j)
+            {
+                int t = j;
 #pragma unroll
                 for (int jj = 0; jj < D; ++jj) {
-                    const int dl = abs(hc[jj] - s_cc[w][i][jj]);
-                    n1 += dl == 1;
-                    n2 += dl == 2;
-                    const int e = max(dl - 1, 0);
-                    g += e * e;
+                    rel[jj] = 2 * (t % 3 - 1) + (int)((q >> jj) & 1u);
+                    t /= 3;
                 }
-                bool pass = g <= I.d;
-                if (pass && P.box) {
-                    Bx<D> al, ah, bl, bh;
+            }
+            Bx<D> bl, bh;
+            if (P.box) {
+                bl.v[0] = blo[h];
+                bh.v[0] = bhi[h];
+            }
+            unsigned c = 0u;
+            for (int i = 0; i < k; ++i) {
+                if (h == c0 + i) continue;
+                const unsigned pi = (pown >> (D * i)) & (unsigned)QMASK;
+                int amax = 0;
+#pragma unroll
+                for (int jj = 0; jj < D; ++jj) amax = max(amax, abs(rel[jj] - (int)((pi >> jj) & 1u)));
+                if (amax > 2) continue;
+                if (P.box) {
+                    Bx<D> al, ah;
                     al.v[0] = s_lo[w][i];
                     ah.v[0] = s_hi[w][i];
-                    bl.v[0] = hl;
-                    bh.v[0] = hh;
-                    pass = boxes_min_d2<D>(al, ah, bl, bh) <= hi_thr;
+                    if (boxes_min_d2<D>(al, ah, bl, bh) > hi_thr) continue;
                 }
-                if (pass) cls[ch] &= ~(((unsigned)(kNoClass - super_class<D>(n1, n2))) << (4 * i));
+                c |= (amax <= 1 ? 1u : 2u) << (2 * i);
             }
+            cls[ch] = c;
         }
-        // lists in the order of the offset table (nearest first): a counting
-        // sort over the classes, from four bit-plane ballots of the codes.
-        // MarkCore stops at minPts, so that order pays where cells hold many
-        // points; with fewer than 4 points per cell on average the lists only
-        // split adjacent and farther cells (each in probe order).
-        if (!ordered) {
-            for (int i = 0; i < k; ++i) {
-                int nn = 0, nf = 0;
-#pragma unroll
-                for (int ch = 0; ch < CH; ++ch) {
-                    if (ch >= nch) break;
-                    const unsigned code = (cls[ch] >> (4 * i)) & 15u;
-                    nn += __popc(__ballot_sync(0xffffffffu, code < (unsigned)D));
-                    nf += __popc(__ballot_sync(0xffffffffu, code != kNoClass && code >= (unsigned)D));
-                }
-                if (lane == 0) {
-                    nbr_cnt[c0 + i] = nn + nf;
-                    nbr_near[c0 + i] = nn;
-                }
-                total += lane == 0 ? nn + nf : 0;
-                const long long base = (long long)(c0 + i) * stride;
-                int ncur = 0, fcur = nn, pts = 0;
-#pragma unroll
-                for (int ch = 0; ch < CH; ++ch) {
-                    if (ch >= nch) break;
-                    const unsigned code = (cls[ch] >> (4 * i)) & 15u;
-                    const bool near = code < (unsigned)D, far = code != kNoClass && !near;
-                    const unsigned nb = __ballot_sync(0xffffffffu, near), fb = __ballot_sync(0xffffffffu, far);
-                    if (near) nbr[base + ncur + __popc(nb & lt)] = hreg[ch];
-                    if (far) nbr[base + fcur + __popc(fb & lt)] = hreg[ch];
-                    if (near || far) pts += hsz[ch];
-                    ncur += __popc(nb);
-                    fcur += __popc(fb);
-                }
-                if (nbr_pts) {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) pts += __shfl_xor_sync(0xffffffffu, pts, o);
-                    if (lane == 0) nbr_pts[c0 + i] = pts;
-                }
-            }
-            continue;
-        }
+        // the lists: adjacent cells first, then the farther ones
         for (int i = 0; i < k; ++i) {
-            int cnt = 0;
+            int nn = 0, nf = 0;
 #pragma unroll
             for (int ch = 0; ch < CH; ++ch) {
                 if (ch >= nch) break;
-                const unsigned code = (cls[ch] >> (4 * i)) & 15u;
-                unsigned b[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) b[q] = __ballot_sync(0xffffffffu, (code >> q) & 1u);
-                if (lane < super_classes<D>()) cnt += __popc(class_mask(b, (unsigned)lane));
+                const unsigned code = (cls[ch] >> (2 * i)) & 3u;
+                nn += __popc(__ballot_sync(0xffffffffu, code == 1u));
+                nf += __popc(__ballot_sync(0xffffffffu, code == 2u));
             }
-            int incl = cnt;  // lanes >= the class count add nothing
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += u;
-            }
-            int run = incl - cnt;  // lane q: next position of class q
-            const int tot = __shfl_sync(0xffffffffu, incl, 31);
-            const int nn = __shfl_sync(0xffffffffu, incl, D - 1);  // classes 0 .. D-1: |delta|_inf = 1
             if (lane == 0) {
-                nbr_cnt[c0 + i] = tot;
+                nbr_cnt[c0 + i] = nn + nf;
                 nbr_near[c0 + i] = nn;
+                total += nn + nf;
             }
-            total += lane == 0 ? tot : 0;
             const long long base = (long long)(c0 + i) * stride;
-            int pts = 0;
+            int ncur = 0, fcur = nn, pts = 0;
 #pragma unroll
             for (int ch = 0; ch < CH; ++ch) {
                 if (ch >= nch) break;
-                const unsigned code = (cls[ch] >> (4 * i)) & 15u;
-                unsigned b[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) b[q] = __ballot_sync(0xffffffffu, (code >> q) & 1u);
-                const unsigned mine = class_mask(b, code);
-                const int at = __shfl_sync(0xffffffffu, run, (int)code);
-                if (code != kNoClass) {
-                    nbr[base + at + __popc(mine & lt)] = hreg[ch];
-                    pts += hsz[ch];
-                }
-                if (lane < super_classes<D>()) run += __popc(class_mask(b, (unsigned)lane));
+                const unsigned code = (cls[ch] >> (2 * i)) & 3u;
+                const unsigned nb = __ballot_sync(0xffffffffu, code == 1u);
+                const unsigned fb = __ballot_sync(0xffffffffu, code == 2u);
+                if (code == 1u) nbr[base + ncur + __popc(nb & lt)] = hreg[ch];
+                else if (code == 2u) nbr[base + fcur + __popc(fb & lt)] = hreg[ch];
+                if (nbr_pts && code) pts += cell_start[hreg[ch] + 1] - cell_start[hreg[ch]];
+                ncur += __popc(nb);
+                fcur += __popc(fb);
             }
             if (nbr_pts) {
 #pragma unroll
@@ -924,8 +881,6 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
             }
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
     if (lane == 0 && total) atomicAdd((unsigned long long *)&ctr->E, (unsigned long long)total);
 }
 
@@ -936,11 +891,11 @@ void launch_super_table(const Semisort &S, const RunParams &P, DevCounters *ctr,
     int *sc_first = reinterpret_cast<int *>(S.rank_of);  // free once the points are scattered
     auto go = [&](auto kf, auto ki) {
         int g = grid_for((const void *)kf, 256);
-        kf<<<g, 256, 0, s>>>(S.cell_key, pos, S.bloom_all, S.bloom_lg, ctr);
+        kf<<<g, 256, 0, s>>>(S.cell_key, pos, S.bloom_all, S.bloom_lg, P, ctr);
         count_launch();
         scan_i32_to_i32(pos, pos, 0, &ctr->m, P.n, S.part, s);
         g = grid_for((const void *)ki, 256);
-        ki<<<g, 256, 0, s>>>(S.cell_key, pos, S.ht, S.slots, sc_first, S.bloom_all, S.bloom_lg, ctr);
+        ki<<<g, 256, 0, s>>>(S.cell_key, pos, S.ht, S.slots, sc_first, S.bloom_all, S.bloom_lg, P, ctr);
         count_launch();
     };
     if (P.d == 2) go(k_super_flags<2>, k_super_insert<2>);
@@ -964,13 +919,13 @@ void launch_neighbors_super(const Semisort &S, const RunParams &P, int stride, c
 void launch_neighbors(const uint64_t *cell_key, const ulonglong2 *ht, uint64_t hcap, const unsigned *bloom,
                       int bloom_lg, const RunParams &P, const signed char *offs, int noff, int n_near,
                       const float4 *blo, const float4 *bhi, const int *cell_start, int *nbr_cnt, int *nbr_near,
-                      int *nbr_pts, int *nbr, DevCounters *ctr, cudaStream_t s) {
+                      int *nbr_pts, int *nbr, DevCounters *ctr, cudaStream_t s, bool only_dense) {
     const uint64_t mask = hcap - 1;
     const int lg = hash_log2(hcap);
     auto go = [&](auto k) {
         int g = grid_for((const void *)k, 256);
         k<<<g, 256, 0, s>>>(cell_key, ht, mask, lg, bloom, bloom_lg, cell_start, nbr_pts, P, offs, noff, n_near,
-                            blo, bhi, nbr_cnt, nbr_near, nbr, ctr);
+                            blo, bhi, nbr_cnt, nbr_near, nbr, only_dense ? 1 : 0, ctr);
         count_launch();
     };
     switch (P.d) {

@@ -38,7 +38,9 @@ struct Semisort {
     int key_lo, key_bits; // key bits the cell sort orders by
     unsigned *bloom;      // 2^bloom_lg bits: Bloom filter of the run's cell keys (cleared per run), or null
     int bloom_lg;
-    bool super;           // d = 2, 3: neighbour lists through supercells (launch_neighbors_super)
+    bool super;           // d = 2, 3: a dense grid keeps the offset enumeration, a sparse one
+                          // takes supercells (decided on the device from n and m)
+    int n;                // points of the run
     unsigned *bloom_all;  // the Bloom filter's storage (supercell keys)
 };
 // Group the points by cell: fills cell_key, cell_start, pf/pd, orig, cell_of,
@@ -58,7 +60,7 @@ void launch_neighbors_super(const Semisort &S, const RunParams &P, int stride, c
 void launch_neighbors(const uint64_t *cell_key, const ulonglong2 *ht, uint64_t hcap, const unsigned *bloom,
                       int bloom_lg, const RunParams &P, const signed char *offs, int noff, int n_near,
                       const float4 *blo, const float4 *bhi, const int *cell_start, int *nbr_cnt, int *nbr_near,
-                      int *nbr_pts, int *nbr, DevCounters *ctr, cudaStream_t s);
+                      int *nbr_pts, int *nbr, DevCounters *ctr, cudaStream_t s, bool only_dense = false);
 // log2 of the Bloom filter's bit count for max_points points (4 to 8 bits per point)
 inline int bloom_log2(long long max_points) {
     int lg = 10;
