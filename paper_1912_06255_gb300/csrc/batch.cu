@@ -165,9 +165,9 @@ cudaError_t ensure_batch(dbscan_ctx *c, int count) {
     c->d_bbox = nullptr;
     c->h_bdesc = nullptr;
     c->batch_cap = 0;
-    cudaError_t e = cudaMalloc((void **)&c->d_bdesc, sizeof(dbscan_instance) * count);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_binst, sizeof(Inst) * count);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_bbox, sizeof(long long) * BB_SLOTS * count);
+    cudaError_t e = ctx_malloc(c, (void **)&c->d_bdesc, sizeof(dbscan_instance) * count);
+    if (e == cudaSuccess) e = ctx_malloc(c, (void **)&c->d_binst, sizeof(Inst) * count);
+    if (e == cudaSuccess) e = ctx_malloc(c, (void **)&c->d_bbox, sizeof(long long) * BB_SLOTS * count);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_bdesc, sizeof(dbscan_instance) * count);
     if (e == cudaSuccess) c->batch_cap = count;
     return e;

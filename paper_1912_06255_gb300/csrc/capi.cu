@@ -121,6 +121,7 @@ static Bufs make_bufs(dbscan_ctx *c, bool f64) {
     B.bcount = c->bcount;
     B.boff = c->boff;
     B.bbig = c->bbig;
+    B.bcache = c->bcache;
     B.part = c->part;
     B.n_max = c->max_points;
     return B;
@@ -173,10 +174,10 @@ static Learned learned_state(dbscan_ctx *c) {
 static cudaError_t ensure_learned(dbscan_ctx *c, long long want = 0) {
     if (c->lpairs) return cudaSuccess;
     const long long cap = want > 0 ? want : 16 * std::max<int64_t>(c->max_points, 1);
-    cudaError_t e = cudaMalloc((void **)&c->lpairs, sizeof(int2) * cap);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&c->lk0, sizeof(uint64_t) * cap);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&c->lk1, sizeof(uint64_t) * cap);
-    if (e == cudaSuccess) e = cudaMalloc(&c->lscratch, sort_scratch_bytes(cap));
+    cudaError_t e = ctx_malloc(c, (void **)&c->lpairs, sizeof(int2) * cap);
+    if (e == cudaSuccess) e = ctx_malloc(c, (void **)&c->lk0, sizeof(uint64_t) * cap);
+    if (e == cudaSuccess) e = ctx_malloc(c, (void **)&c->lk1, sizeof(uint64_t) * cap);
+    if (e == cudaSuccess) e = ctx_malloc(c, (void **)&c->lscratch, sort_scratch_bytes(cap));
     if (e == cudaSuccess) {
         c->lscratch_size = sort_scratch_bytes(cap);
         c->lcap = cap;
@@ -214,7 +215,7 @@ static cudaError_t ensure_hd(dbscan_ctx *c) {
     };
     size_t total = 0;
     for (const auto &it : items) total += align_up(it.bytes);
-    const cudaError_t e = cudaMalloc(&c->hd_arena, total);
+    const cudaError_t e = ctx_malloc(c, (void **)&c->hd_arena, total);
     if (e != cudaSuccess) {
         c->hd_arena = nullptr;
         return e;
@@ -264,7 +265,7 @@ static dbscan_status enqueue_hd_cells(dbscan_ctx *c, const RunParams &P, const v
         c->hd_nbr = nullptr;
         c->hd_nbr_cap = 0;
         const long long grown = E + E / 4;
-        if (cudaMalloc((void **)&c->hd_nbr, sizeof(int) * (size_t)grown) != cudaSuccess) {
+        if (ctx_malloc(c, (void **)&c->hd_nbr, sizeof(int) * (size_t)grown) != cudaSuccess) {
             (void)cudaGetLastError();
             c->hd_nbr = nullptr;
             return DBSCAN_ERR_OOM;
@@ -507,8 +508,11 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
     *out = nullptr;
     if (max_points < 0 || max_points >= 0x7ffffffell) return DBSCAN_ERR_INVALID_ARG;
     if (max_dim < 1 || max_dim > kMaxDim) return DBSCAN_ERR_UNSUPPORTED_DIM;
+    const char *fault = std::getenv("DBSCAN_FAULT");
+    if (fault && std::strstr(fault, "create")) return DBSCAN_ERR_OOM;  // injected: as if the arena did not fit
     dbscan_ctx *c = new (std::nothrow) dbscan_ctx();
     if (!c) return DBSCAN_ERR_OOM;
+    c->fault_alloc = fault && std::strstr(fault, "alloc");
     cudaGetDevice(&c->device);
     const int64_t N = std::max<int64_t>(max_points, 1);
     c->max_points = max_points;
@@ -552,7 +556,7 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
         {(void **)&c->parent, 4 * (size_t)N}, {(void **)&c->compmin, 4 * (size_t)N},
         {(void **)&c->noncore, 4 * (size_t)N},
         {(void **)&c->bcount, 8 * (size_t)N}, {(void **)&c->boff, 8 * (size_t)(N + 1)},
-        {(void **)&c->bbig, (size_t)N},
+        {(void **)&c->bbig, (size_t)N}, {(void **)&c->bcache, 8 * (size_t)N},
         {(void **)&c->bbox_out, 8 * (2 * kMaxDim + 1)},
         {(void **)&c->offs, (size_t)kMaxEnumDim * kMaxOffsets * kMaxEnumDim},
         {(void **)&c->ctr, sizeof(DevCounters)},
@@ -619,8 +623,8 @@ dbscan_status dbscan_set_option(dbscan_ctx *c, int option, int64_t value) {
         c->log_cap = 0;
         c->log_count = 0;
         if (value > 0) {
-            cudaError_t e = cudaMalloc((void **)&c->log_feat, sizeof(float) * kMlpIn * value);
-            if (e == cudaSuccess) e = cudaMalloc((void **)&c->log_lab, (size_t)value);
+            cudaError_t e = ctx_malloc(c, (void **)&c->log_feat, sizeof(float) * kMlpIn * value);
+            if (e == cudaSuccess) e = ctx_malloc(c, (void **)&c->log_lab, (size_t)value);
             if (e != cudaSuccess) {
                 (void)cudaGetLastError();
                 cudaFree(c->log_feat);
@@ -658,7 +662,7 @@ dbscan_status dbscan_set_option(dbscan_ctx *c, int option, int64_t value) {
     case DBSCAN_OPT_WITNESS:
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
         if (value && !c->wit) {
-            if (cudaMalloc((void **)&c->wit, sizeof(int2) * (size_t)std::max<int64_t>(c->max_points, 1)) !=
+            if (ctx_malloc(c, (void **)&c->wit, sizeof(int2) * (size_t)std::max<int64_t>(c->max_points, 1)) !=
                 cudaSuccess) {
                 (void)cudaGetLastError();
                 c->wit = nullptr;
@@ -1140,18 +1144,30 @@ static dbscan_status ensure_host_bufs(dbscan_ctx *c, int64_t ids_need) {
     if (!c->d_in) {
         const size_t need = std::max<size_t>((size_t)c->max_points * c->max_dim * 8, 8);
         const int64_t N = std::max<int64_t>(c->max_points, 1);
-        CK(cudaMalloc(&c->d_in, need));
+        cudaError_t e = ctx_malloc(c, (void **)&c->d_in, need);
+        if (e == cudaSuccess) e = ctx_malloc(c, (void **)&c->d_core_h, (size_t)N);
+        if (e == cudaSuccess) e = ctx_malloc(c, (void **)&c->d_lab_h, 4 * (size_t)N);
+        if (e == cudaSuccess) e = ctx_malloc(c, (void **)&c->d_off_h, 8 * (size_t)(N + 1));
+        if (e != cudaSuccess) {  // all or nothing: a later call allocates again
+            (void)cudaGetLastError();
+            cudaFree(c->d_in);
+            cudaFree(c->d_core_h);
+            cudaFree(c->d_lab_h);
+            cudaFree(c->d_off_h);
+            c->d_in = nullptr;
+            c->d_core_h = nullptr;
+            c->d_lab_h = nullptr;
+            c->d_off_h = nullptr;
+            return cuda_status(e);
+        }
         c->d_in_bytes = need;
-        CK(cudaMalloc((void **)&c->d_core_h, (size_t)N));
-        CK(cudaMalloc((void **)&c->d_lab_h, 4 * (size_t)N));
-        CK(cudaMalloc((void **)&c->d_off_h, 8 * (size_t)(N + 1)));
     }
     if (ids_need > c->d_ids_cap) {
         cudaFree(c->d_ids_h);
         c->d_ids_h = nullptr;
         c->d_ids_cap = 0;
         const int64_t cap = std::max<int64_t>(ids_need + ids_need / 4, 1024);
-        CK(cudaMalloc((void **)&c->d_ids_h, 4 * (size_t)cap));
+        CK(ctx_malloc(c, (void **)&c->d_ids_h, 4 * (size_t)cap));
         c->d_ids_cap = cap;
     }
     return DBSCAN_OK;

@@ -150,6 +150,7 @@ k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__
            int stride, const long long *__restrict__ nbr_off, const int *__restrict__ nbr_pts,
            const float4 *__restrict__ blo, const float4 *__restrict__ bhi, int *__restrict__ core_s,
            DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     constexpr int OWN = D == 8 ? 64 : MC_OWN;  // 8-wide points: at most two slots in registers
     __shared__ Pt<D, M> own[MC_WARPS][OWN];
     __shared__ Bx<D> sbox[MC_WARPS][32][2];  // boxes of the next 32 neighbouring cells
@@ -210,6 +211,7 @@ k_markcore_small(RunParams P, const float *__restrict__ pf, const double *__rest
                  const int *__restrict__ nbr, int stride, const long long *__restrict__ nbr_off,
                  const int *__restrict__ nbr_pts, const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
                  int *__restrict__ core_s, DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     constexpr bool BOX = (M == kF32FromF32 || M == kF32FromF64);
     const bool use_box = BOX && P.box;
     unsigned rech = 0;
@@ -284,6 +286,7 @@ k_core_compact(RunParams P, const float *__restrict__ pf, const double *__restri
                const int *__restrict__ core_pos, float *__restrict__ cpf, double *__restrict__ cpd,
                int *__restrict__ core_orig, int *__restrict__ core_cell, int *__restrict__ ccs,
                DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     const int stride = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
@@ -337,6 +340,7 @@ constexpr int kSizeKeyBits = 16;
 
 __global__ void __launch_bounds__(256)
 k_size_keys(const int *__restrict__ ccs, uint64_t *__restrict__ keys, const DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
         const int nc = min(ccs[c + 1] - ccs[c], (1 << kSizeKeyBits) - 1);
@@ -348,6 +352,7 @@ k_size_keys(const int *__restrict__ ccs, uint64_t *__restrict__ keys, const DevC
 __global__ void __launch_bounds__(256)
 k_rank(const uint64_t *__restrict__ sorted, uint32_t *__restrict__ order, int *__restrict__ rank,
        const DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
         const int c = sorted ? (int)(sorted[r] & 0xffffffffu) : r;
@@ -388,6 +393,7 @@ k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict
           const int *__restrict__ nbr, int stride, const long long *__restrict__ nbr_off,
           const float *__restrict__ cpf, const double *__restrict__ cpd, const float4 *__restrict__ cblo,
           const float4 *__restrict__ cbhi, int *parent, DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     constexpr bool BOX = (M == kF32FromF32 || M == kF32FromF64);
     const int lane = threadIdx.x & 31;
     const int m = ctr->m;
@@ -458,10 +464,15 @@ k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict
             // union-find check: in the near wave only the current parents are
             // compared (trees are being built); the far wave runs after every
             // path was compressed, so its finds are short
+            // first on the L1 view of the forest (a "same" there is final), then fresh
             bool same = true;
             if (cand && verdict >= 0) {
-                if (WAVE == 0) same = uf_load(parent + a) == uf_load(parent + b);
-                else same = uf_find(parent, a, P.max_iters, ctr) == uf_find(parent, b, P.max_iters, ctr);
+                if (WAVE == 0) {
+                    same = __ldca(parent + a) == __ldca(parent + b) || uf_load(parent + a) == uf_load(parent + b);
+                } else {
+                    same = uf_find_stale(parent, a, P.max_iters) == uf_find_stale(parent, b, P.max_iters) ||
+                           uf_find(parent, a, P.max_iters, ctr) == uf_find(parent, b, P.max_iters, ctr);
+                }
             }
             // a box verdict: every pair of core points is within eps, so the
             // first core points of the two cells witness the link
@@ -506,6 +517,7 @@ k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict
 
 // Full path compression between the two waves.
 __global__ void __launch_bounds__(256) k_uf_compress(int *parent, DevCounters *ctr, int max_iters) {
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x)
         parent[c] = uf_find(parent, c, max_iters, ctr);
@@ -518,6 +530,7 @@ void launch_uf_compress(int *parent, DevCounters *ctr, int max_iters, cudaStream
 }
 
 __global__ void __launch_bounds__(256) k_uf_init(int *parent, const DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) parent[c] = c;
 }
@@ -564,6 +577,7 @@ void launch_connect(int D, int mode, const uint32_t *order, const RunParams &P, 
 // during that pass), into compmin, and written to parent by a third pass.
 __global__ void __launch_bounds__(256) k_uf_roots(const int *__restrict__ parent, int *__restrict__ root,
                                                   DevCounters *ctr, int max_iters) {
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
         int x = c, it = 0;
@@ -579,6 +593,7 @@ __global__ void __launch_bounds__(256) k_uf_roots(const int *__restrict__ parent
 
 __global__ void __launch_bounds__(256) k_uf_flatten(int *__restrict__ parent, int *__restrict__ compmin,
                                                     const DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
         parent[c] = compmin[c];  // the root found by k_uf_roots
@@ -589,6 +604,7 @@ __global__ void __launch_bounds__(256) k_uf_flatten(int *__restrict__ parent, in
 __global__ void __launch_bounds__(256)
 k_comp_min(const int *__restrict__ ccs, const int *__restrict__ core_orig, const int *__restrict__ parent,
            int *compmin, const DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
         const int k0 = ccs[c], k1 = ccs[c + 1];
@@ -604,6 +620,7 @@ k_label_core(RunParams P, const int *__restrict__ core_s, const int *__restrict_
              const int *__restrict__ cell_of, const int *__restrict__ parent, const int *__restrict__ compmin,
              uint8_t *__restrict__ core_out, int32_t *__restrict__ labels_out, int *__restrict__ noncore,
              DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     // trip count rounded up to whole warps so the ballot below is warp-uniform
@@ -689,6 +706,7 @@ template <int D, int M, bool FILL>
 __global__ void __launch_bounds__(BD_THREADS)
 k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restrict__ ids,
          long long ids_cap, DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     __shared__ int sset[BD_WARPS][kBorderSetCap];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nn = ctr->n_noncore;
@@ -702,6 +720,16 @@ k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restr
         if (P.mc_small_nbr > 0 &&
             mc_small(P, B.cell_start[g + 1] - B.cell_start[g], B.nbr_pts, g) && !B.bbig[o])
             continue;
+        if (FILL && B.bcount[o] <= 2) {  // the count pass kept sets of up to 2 names
+            const long long at = B.boff[o];
+            const int2 cs = B.bcache[o];
+            const int ns = (int)B.bcount[o];
+            if (lane < ns) {
+                if (at + ns <= ids_cap) ids[at + lane] = lane == 0 ? cs.x : cs.y;
+                else set_error(ctr, DBSCAN_ERR_CAPACITY, 31);
+            }
+            continue;
+        }
         const Inst &I = P.inst[inst_of_cell(P, g)];
         const Thr T = I.thr;
         const int row0 = I.row0;
@@ -755,6 +783,7 @@ k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restr
             if (lane == 0) {
                 B.bcount[o] = ns;
                 labels_out[o] = ns ? sset[w][0] : -1;
+                if (ns <= 2) B.bcache[o] = make_int2(ns > 0 ? sset[w][0] : -1, ns > 1 ? sset[w][1] : -1);
             }
             nborder += ns ? 1 : 0;
             members += ns;
@@ -792,6 +821,7 @@ template <int D, int M, bool FILL>
 __global__ void __launch_bounds__(256)
 k_border_small(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restrict__ ids,
                long long ids_cap, DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     constexpr bool BOX = (M == kF32FromF32 || M == kF32FromF64);
     const int nn = ctr->n_noncore;
     unsigned rech = 0;
@@ -802,6 +832,18 @@ k_border_small(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *_
         const int o = B.orig[i];
         if (!mc_small(P, B.cell_start[g + 1] - B.cell_start[g], B.nbr_pts, g)) continue;
         if (FILL && B.bbig[o]) continue;
+        if (FILL && B.bcount[o] <= 2) {  // the count pass kept sets of up to 2 names
+            const long long at = B.boff[o];
+            const int2 cs = B.bcache[o];
+            const int ns = (int)B.bcount[o];
+            if (at + ns <= ids_cap) {
+                if (ns > 0) ids[at] = cs.x;
+                if (ns > 1) ids[at + 1] = cs.y;
+            } else {
+                set_error(ctr, DBSCAN_ERR_CAPACITY, 32);
+            }
+            continue;
+        }
         const Inst &I = P.inst[inst_of_cell(P, g)];
         const Thr T = I.thr;
         const int row0 = I.row0;
@@ -848,6 +890,7 @@ k_border_small(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *_
             if (big) continue;  // k_border redoes this point
             B.bcount[o] = ns;
             labels_out[o] = ns ? set[0] : -1;
+            if (ns <= 2) B.bcache[o] = make_int2(ns > 0 ? set[0] : -1, ns > 1 ? set[1] : -1);
             nborder += ns ? 1 : 0;
             members += ns;
         } else {

@@ -94,6 +94,7 @@ struct dbscan_ctx {
     int *noncore = nullptr;
     long long *bcount = nullptr, *boff = nullptr;
     unsigned char *bbig = nullptr;
+    int2 *bcache = nullptr;
     long long *bbox_out = nullptr;  // [2*kMaxDim + 1], see launch_bbox
     signed char *offs = nullptr;  // [kMaxEnumDim][kMaxOffsets][kMaxEnumDim]
     int noff[gbdb::kMaxEnumDim + 1] = {0};
@@ -127,4 +128,18 @@ struct dbscan_ctx {
     const void *last_points = nullptr;
     int last_dtype = 0;
     dbscan_stats stats{};
+    // DBSCAN_FAULT in the environment when the context was created (host-side
+    // fault injection for the tests of the error paths): "alloc" makes every
+    // allocation after dbscan_create fail like an exhausted device
+    bool fault_alloc = false;
 };
+
+// Device allocation of a context's lazily allocated buffers (fails with
+// cudaErrorMemoryAllocation, allocating nothing, under DBSCAN_FAULT=alloc).
+inline cudaError_t ctx_malloc(const dbscan_ctx *c, void **p, size_t bytes) {
+    if (c->fault_alloc) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}

@@ -366,6 +366,20 @@ __device__ __forceinline__ int uf_find(int *parent, int x, int max_iters, DevCou
     return x;
 }
 
+// Find on a possibly stale view of the forest, through L1 (ld.global.ca),
+// without stores.  Every parent value ever written joins two cells of one set
+// and sets only merge, so two cells whose stale walks end at the same cell are
+// in one set now: a "same" answer is final, a "different" one needs uf_find.
+// Parents only decrease along a walk (parent[x] <= x), so the walk ends.
+__device__ __forceinline__ int uf_find_stale(const int *parent, int x, int max_iters) {
+    for (int it = 0; it < max_iters; ++it) {
+        const int p = __ldca(parent + x);
+        if (p == x) return x;
+        x = p;
+    }
+    return x;
+}
+
 // Returns true iff this call hooked one root under another (the two sets
 // were separate and are now one).
 __device__ __forceinline__ bool uf_link(int *parent, int a, int b, int max_iters, DevCounters *ctr) {

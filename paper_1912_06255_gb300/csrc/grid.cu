@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(256)
 k_insert(const T *__restrict__ X, RunParams P, ulonglong2 *__restrict__ ht, unsigned *__restrict__ hcnt,
          uint64_t hmask, int hlg, uint32_t *__restrict__ slot_of, uint32_t *__restrict__ rank_of,
          uint32_t *__restrict__ slots, unsigned *__restrict__ bloom, int blg, DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     const int T_ = gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     // the loop bound is uniform across the warp (its first lane's index), so
@@ -239,6 +240,7 @@ k_insert(const T *__restrict__ X, RunParams P, ulonglong2 *__restrict__ ht, unsi
 __global__ void __launch_bounds__(256)
 k_cell_keys(const ulonglong2 *__restrict__ ht, const uint32_t *__restrict__ slots, uint64_t *__restrict__ keys,
             uint32_t *__restrict__ vals, const DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
         const uint32_t s = slots[c];
@@ -253,6 +255,7 @@ __global__ void __launch_bounds__(256)
 k_cell_table(RunParams P, const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
              ulonglong2 *__restrict__ ht, const unsigned *__restrict__ hcnt, uint64_t *__restrict__ cell_key,
              int *__restrict__ count, int *__restrict__ cell_inst, const DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
         const uint32_t s = vals[c];
@@ -271,7 +274,7 @@ k_scatter_points(const T *__restrict__ X, RunParams P, const ulonglong2 *__restr
                  const uint32_t *__restrict__ slot_of, const uint32_t *__restrict__ rank_of,
                  const int *__restrict__ cell_start, float *__restrict__ pf, double *__restrict__ pd,
                  int *__restrict__ orig, int *__restrict__ cell_of, const DevCounters *ctr) {
-    if (ctr->err) return;  // a failed insert left slot_of undefined
+    if (run_failed(ctr)) return;
     const int n = P.n, ld = P.d;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int c = (int)ht[slot_of[i]].y;
@@ -307,6 +310,7 @@ k_scatter_points(const T *__restrict__ X, RunParams P, const ulonglong2 *__restr
 __global__ void __launch_bounds__(256)
 k_table_reset(ulonglong2 *__restrict__ ht, unsigned *__restrict__ hcnt, const uint32_t *__restrict__ slots,
               const DevCounters *ctr, int n, int cond) {
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     // cond 1: only on a sparse grid (before its supercells take the table);
     // cond 2: only on a dense grid (its cells kept the table to the end)
@@ -362,6 +366,7 @@ void launch_semisort(const void *X, int dtype, const RunParams &P, int SD, const
 // Empty the supercell slots (the cells' slots were emptied before).
 __global__ void __launch_bounds__(256)
 k_super_reset(ulonglong2 *__restrict__ ht, const uint32_t *__restrict__ sslots, const DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     const int ms = ctr->ms;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ms; i += gridDim.x * blockDim.x)
         ht[sslots[i]] = make_ulonglong2(kEmptyKey, 0);
@@ -426,6 +431,7 @@ template <int SD>
 __global__ void __launch_bounds__(256)
 k_boxes(const float *__restrict__ pts, const int *__restrict__ start, const DevCounters *ctr,
         float4 *__restrict__ lo, float4 *__restrict__ hi, float4 *__restrict__ cent) {
+    if (run_failed(ctr)) return;
     constexpr int W = SD == 8 ? 8 : 4, BW = W / 4;
     const int m = ctr->m;
     const int lane = threadIdx.x & 31;
@@ -509,6 +515,7 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
             const signed char *__restrict__ offs, int noff, int n_near, const float4 *__restrict__ blo,
             const float4 *__restrict__ bhi, int *__restrict__ nbr_cnt, int *__restrict__ nbr_near,
             int *__restrict__ nbr, int only_dense, DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     if (only_dense && !grid_dense(P.n, m)) return;  // k_neighbors_super takes sparse grids
     const int lane = threadIdx.x & 31;
@@ -628,7 +635,7 @@ template <int D>
 __global__ void __launch_bounds__(256)
 k_super_flags(const uint64_t *__restrict__ cell_key, int *__restrict__ flag, unsigned *__restrict__ bloom,
               int bloom_lg, const RunParams P, const DevCounters *ctr) {
-    if (ctr->err) return;
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     if (grid_dense(P.n, m)) return;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -648,7 +655,7 @@ __global__ void __launch_bounds__(256)
 k_super_insert(const uint64_t *__restrict__ cell_key, const int *__restrict__ pos, ulonglong2 *__restrict__ ht,
                uint32_t *__restrict__ sslots, int *__restrict__ sc_first, unsigned *__restrict__ bloom, int bloom_lg,
                const RunParams P, DevCounters *ctr) {
-    if (ctr->err) return;
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     if (grid_dense(P.n, m)) return;
     const int ms = pos[m];
@@ -706,12 +713,12 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
                   const int *__restrict__ cell_start, int *__restrict__ nbr_pts, RunParams P, int stride,
                   const float4 *__restrict__ blo, const float4 *__restrict__ bhi, int *__restrict__ nbr_cnt,
                   int *__restrict__ nbr_near, int *__restrict__ nbr, DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     constexpr int K = 1 << D;              // cells per supercell
     constexpr int NS = D == 2 ? 9 : 27;    // supercells probed, the own one included
     constexpr int CH = (NS * K + 31) / 32; // 32-candidate chunks
     constexpr uint64_t QMASK = (1u << D) - 1u;
     __shared__ float4 s_lo[NBS_WARPS][K], s_hi[NBS_WARPS][K];
-    if (ctr->err) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int m = ctr->m, ms = ctr->ms;

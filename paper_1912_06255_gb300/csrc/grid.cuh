@@ -108,6 +108,7 @@ struct Bufs {
     int *noncore;       // [n_noncore] cell-order indices of the non-core points
     long long *bcount, *boff;
     unsigned char *bbig;  // [N] by input index: the point's border set outgrew k_border_small's
+    int2 *bcache;         // [N] by input index: a border set of at most 2 names from the count pass
     long long *part;
     int64_t n_max;
 };

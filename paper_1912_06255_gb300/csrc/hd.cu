@@ -86,14 +86,17 @@ k_hd_keys(const T *__restrict__ X, RunParams P, uint64_t *__restrict__ klo, uint
 
 // kh[t] = khi[idx[t]]: the high words in the order of the low-word sort.
 __global__ void __launch_bounds__(256)
-k_hd_gather_hi(const uint64_t *__restrict__ khi, const uint32_t *__restrict__ idx, uint64_t *__restrict__ kh, int n) {
+k_hd_gather_hi(const uint64_t *__restrict__ khi, const uint32_t *__restrict__ idx, uint64_t *__restrict__ kh, int n,
+               const DevCounters *ctr) {
+    if (run_failed(ctr)) return;  // the sort gave up: idx is incomplete
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) kh[t] = khi[idx[t]];
 }
 
 // flag[t] = 1 where a new cell starts in the sorted order.
 __global__ void __launch_bounds__(256)
 k_hd_flags(const uint64_t *__restrict__ klo, const uint64_t *__restrict__ khi, const uint32_t *__restrict__ idx,
-           int *__restrict__ flag, int n) {
+           int *__restrict__ flag, int n, const DevCounters *ctr) {
+    if (run_failed(ctr)) return;  // the sort gave up: idx is incomplete
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         int f = 1;
         if (t > 0) {
@@ -113,6 +116,7 @@ k_hd_cells(const T *__restrict__ X, RunParams P, const uint32_t *__restrict__ id
            int *__restrict__ cell_start, uint64_t *__restrict__ ckey_lo, uint64_t *__restrict__ ckey_hi,
            int4 *__restrict__ ccoord, float *__restrict__ pf, double *__restrict__ pd, int *__restrict__ orig,
            int *__restrict__ cell_of, DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     const int n = P.n, d = P.d;
     const Inst &I = P.inst[0];
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
@@ -167,6 +171,7 @@ __device__ __forceinline__ int prefix(const uint64_t *__restrict__ lo, const uin
 __global__ void __launch_bounds__(256)
 k_lbvh_nodes(const uint64_t *__restrict__ klo, const uint64_t *__restrict__ khi, int2 *__restrict__ child,
              int *__restrict__ parent, int *__restrict__ flag, const DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m - 1; i += gridDim.x * blockDim.x) {
         flag[i] = 0;
@@ -203,6 +208,7 @@ k_lbvh_bounds(const int2 *__restrict__ child, const int *__restrict__ parent, in
               const int4 *__restrict__ ccoord, int4 *__restrict__ nlo, int4 *__restrict__ nhi, int d,
               const float4 *__restrict__ blo, const float4 *__restrict__ bhi, float4 *__restrict__ nblo,
               float4 *__restrict__ nbhi, DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
         int node = (m - 1) + c;
@@ -438,6 +444,7 @@ k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int4 *__rest
                  const int *__restrict__ cell_start, int *__restrict__ scratch, int *__restrict__ nbr_pts,
                  int *__restrict__ nbr_cnt, int *__restrict__ nbr_near, long long *__restrict__ off,
                  int *__restrict__ nbr, long long cap, long long max_warps, DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     __shared__ int stk[QW][kStack];
     if (warps_global() > max_warps) {  // the scratch has no room for this grid (cannot happen: sized for the largest)
         if (threadIdx.x == 0 && blockIdx.x == 0) set_error(ctr, DBSCAN_ERR_CAPACITY, 73);
@@ -546,7 +553,7 @@ void hd_cells(const void *X, int dtype, const RunParams &P, int key_bits, const 
         uint32_t *vout = which ? B.sv0 : B.sv1;
         uint64_t *kother = which ? B.sk1 : B.sk0;
         int g = grid_for((const void *)k_hd_gather_hi, 256);
-        k_hd_gather_hi<<<g, 256, 0, s>>>(H.khi, vin, kh, n);
+        k_hd_gather_hi<<<g, 256, 0, s>>>(H.khi, vin, kh, n, ctr);
         count_launch();
         const int w2 = radix_sort_u64(kh, vin, kother, vout, n, nullptr, n, 0, bits - 64, B.sort_scratch,
                                       B.sort_scratch_size, ctr, P.max_iters, s);
@@ -554,7 +561,7 @@ void hd_cells(const void *X, int dtype, const RunParams &P, int key_bits, const 
     }
     {
         int g = grid_for((const void *)k_hd_flags, 256);
-        k_hd_flags<<<g, 256, 0, s>>>(H.klo, H.khi, idx, B.core_s, n);
+        k_hd_flags<<<g, 256, 0, s>>>(H.klo, H.khi, idx, B.core_s, n, ctr);
         count_launch();
     }
     scan_i32_to_i32(B.core_s, B.core_pos, n, nullptr, n, B.part, s);

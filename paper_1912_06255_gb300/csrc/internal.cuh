@@ -105,6 +105,23 @@ __device__ __forceinline__ void set_error(DevCounters *c, int code, int info) {
     if (atomicCAS(&c->err, 0, code) == 0) c->err_info = info;
 }
 
+// Once a step has failed (a bounded wait gave up, a buffer was too small),
+// the kernels after it leave at entry: their inputs may be incomplete, and
+// values taken from them must not be used as indices.  One lane reads the
+// status word and the warp follows it, so a warp never splits before its
+// full-warp collectives; run_failed_block makes the same decision for a whole
+// block (kernels with __syncthreads).
+__device__ __forceinline__ bool run_failed(const DevCounters *ctr) {
+    return __shfl_sync(0xffffffffu, *(const volatile int *)&ctr->err, 0) != 0;
+}
+__device__ __forceinline__ bool run_failed_block(const DevCounters *ctr) {
+    __shared__ int s_failed;
+    __syncthreads();
+    if (threadIdx.x == 0) s_failed = *(const volatile int *)&ctr->err;
+    __syncthreads();
+    return s_failed != 0;
+}
+
 // ---------------------------------------------------------------- primitives
 // Exclusive scan of in[0..n) into out[0..n], out[n] = total.  n = *n_dev when
 // n_dev is non-null, else n_host; n_max bounds n and sizes the grid.  out may

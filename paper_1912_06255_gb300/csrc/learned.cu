@@ -28,6 +28,7 @@ __device__ __forceinline__ void flush_warp_counter(unsigned long long *dst, unsi
 }
 
 __global__ void __launch_bounds__(256) k_uf_reset(int *parent, uint64_t *best, const DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
         parent[c] = c;
@@ -206,6 +207,7 @@ k_collect_pairs(RunParams P, const int *__restrict__ ccs, const int *__restrict_
                 const float4 *__restrict__ cblo,
                 const float4 *__restrict__ cbhi, int *parent, int2 *__restrict__ pairs, long long cap,
                 int count_cands, DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     const int m = ctr->m;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -274,6 +276,7 @@ __global__ void __launch_bounds__(256)
 k_score_pairs(RunParams P, const int2 *__restrict__ pairs, const float *__restrict__ w, const int *__restrict__ ccs,
               const float4 *__restrict__ cent, const float4 *__restrict__ cblo, const float4 *__restrict__ cbhi,
               uint64_t *__restrict__ keys, unsigned long long *__restrict__ best, DevCounters *ctr) {
+    if (run_failed_block(ctr)) return;
     __shared__ float sw[kMlpParams];
     for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) sw[i] = w[i];
     __syncthreads();
@@ -322,6 +325,7 @@ k_test_pairs(RunParams P, const int2 *__restrict__ pairs, const uint64_t *__rest
              const double *__restrict__ cpd, const float4 *__restrict__ cent, const float4 *__restrict__ cblo,
              const float4 *__restrict__ cbhi, int *parent, float *__restrict__ log_feat,
              unsigned char *__restrict__ log_lab, long long log_cap, DevCounters *ctr) {
+    if (run_failed(ctr)) return;
     constexpr bool LOG = WAVE == 3;
     const int lane = threadIdx.x & 31;
     long long lo = 0, hi = 0;

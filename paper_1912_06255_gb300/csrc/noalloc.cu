@@ -94,7 +94,7 @@ size_t carve(dbscan_ctx *c, unsigned char *base) {
         {(void **)&c->parent, 4 * (size_t)N}, {(void **)&c->compmin, 4 * (size_t)N},
         {(void **)&c->noncore, 4 * (size_t)N},
         {(void **)&c->bcount, 8 * (size_t)N}, {(void **)&c->boff, 8 * (size_t)(N + 1)},
-        {(void **)&c->bbig, (size_t)N},
+        {(void **)&c->bbig, (size_t)N}, {(void **)&c->bcache, 8 * (size_t)N},
         {(void **)&c->bbox_out, 8 * (2 * kMaxDim + 1)},
         {(void **)&c->offs, (size_t)kMaxEnumDim * kMaxOffsets * kMaxEnumDim},
         {(void **)&c->ctr, sizeof(DevCounters)},

@@ -228,6 +228,7 @@ k_radix_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ v
                 uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int n_host, const int *n_dev,
                 int shift, const unsigned *__restrict__ goff, unsigned long long *status, int *tile_ctr,
                 DevCounters *ctr, int max_iters) {
+    if (run_failed_block(ctr)) return;
     __shared__ int wcnt[RS_WARPS][RS_BINS];
     __shared__ int s_tile;
     const int n = n_dev ? *n_dev : n_host;

@@ -96,3 +96,11 @@ def test_struct_layouts_match_the_c_compiler(struct, cls, tmp_path):
     assert c["size"] == ctypes.sizeof(mirror), struct
     for f in fields:
         assert c[f] == getattr(mirror, f).offset, (struct, f)
+
+
+def test_injected_create_failure_needs_no_device(lib, monkeypatch):
+    """DBSCAN_FAULT=create makes dbscan_create report OOM before any CUDA call."""
+    monkeypatch.setenv("DBSCAN_FAULT", "create")
+    out = ctypes.c_void_p()
+    assert lib.dbscan_create(ctypes.byref(out), 10, 3) == 3
+    assert not out.value
