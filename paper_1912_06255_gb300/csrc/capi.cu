@@ -122,6 +122,7 @@ static Bufs make_bufs(dbscan_ctx *c, bool f64) {
     B.boff = c->boff;
     B.bbig = c->bbig;
     B.bcache = c->bcache;
+    B.bheavy = c->bheavy;
     B.part = c->part;
     B.n_max = c->max_points;
     return B;
@@ -285,12 +286,10 @@ static dbscan_status enqueue_hash_cells(dbscan_ctx *c, const RunParams &P, int S
     // 3. cells: group the points by cell (semisort, Sec. 4.1) through the cell hash
     mark(2);
     if (!c->table_clean) {
-        CK(cudaMemsetAsync(c->ht, 0xff, sizeof(ulonglong2) * c->hcap, s));
-        CK(cudaMemsetAsync(c->hcnt, 0, sizeof(unsigned) * c->hcap, s));
+        launch_table_clear(c->ht, c->hcap, s);
     }
     c->table_clean = false;
     S.ht = c->ht;
-    S.hcnt = c->hcnt;
     S.hcap = c->hcap;
     S.slot_of = c->slot_of;
     S.rank_of = c->rank_of;
@@ -537,7 +536,7 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
         {(void **)&c->v0, 4 * (size_t)N}, {(void **)&c->v1, 4 * (size_t)N},
         {(void **)&c->sort_scratch, sort_scratch_bytes(N)}, {(void **)&c->part, 8 * (size_t)npart},
         {(void **)&c->slot_of, 4 * (size_t)N}, {(void **)&c->rank_of, 4 * (size_t)N},
-        {(void **)&c->slots, 4 * (size_t)N}, {(void **)&c->hcnt, 4 * (size_t)hcap},
+        {(void **)&c->slots, 4 * (size_t)N},
         {(void **)&c->pf, 4 * (size_t)N * SD}, {(void **)&c->pd, 8 * (size_t)N * SD},
         {(void **)&c->cpf, 4 * (size_t)N * SD}, {(void **)&c->cpd, 8 * (size_t)N * SD},
         {(void **)&c->orig, 4 * (size_t)N}, {(void **)&c->cell_of, 4 * (size_t)N},
@@ -557,6 +556,7 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
         {(void **)&c->noncore, 4 * (size_t)N},
         {(void **)&c->bcount, 8 * (size_t)N}, {(void **)&c->boff, 8 * (size_t)(N + 1)},
         {(void **)&c->bbig, (size_t)N}, {(void **)&c->bcache, 8 * (size_t)N},
+        {(void **)&c->bheavy, 4 * (size_t)N},
         {(void **)&c->bbox_out, 8 * (2 * kMaxDim + 1)},
         {(void **)&c->offs, (size_t)kMaxEnumDim * kMaxOffsets * kMaxEnumDim},
         {(void **)&c->ctr, sizeof(DevCounters)},
@@ -579,8 +579,10 @@ dbscan_status dbscan_create(dbscan_ctx **out, int64_t max_points, int max_dim) {
     }
     c->hcap = hcap;
     if (e == cudaSuccess) e = init_mlp(c, 1);
-    if (e == cudaSuccess) e = cudaMemset(c->ht, 0xff, sizeof(ulonglong2) * hcap);
-    if (e == cudaSuccess) e = cudaMemset(c->hcnt, 0, sizeof(unsigned) * hcap);
+    if (e == cudaSuccess) {
+        launch_table_clear(c->ht, hcap, 0);
+        e = cudaGetLastError();
+    }
     // the clears and copies above run on the legacy stream: finish them before
     // a run on another (possibly non-blocking) stream reads the table
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -894,8 +896,7 @@ static dbscan_status run_batch_once(dbscan_ctx *c, const dbscan_instance *hi, in
     c->stats.radix_passes = ld >= 2 ? 8 : 7;
     const long long launches0 = g_launches;
     if (!c->table_clean) {
-        CK(cudaMemsetAsync(c->ht, 0xff, sizeof(ulonglong2) * c->hcap, s));
-        CK(cudaMemsetAsync(c->hcnt, 0, sizeof(unsigned) * c->hcap, s));
+        launch_table_clear(c->ht, c->hcap, s);
         c->table_clean = true;
     }
     // The cell sort orders by all 63 key bits: instance, then Z order inside

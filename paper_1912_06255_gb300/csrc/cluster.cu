@@ -700,7 +700,17 @@ void launch_witness_export(const Bufs &B, int n_core, const int2 *wit, long long
 // points of distinct clusters seen by p are pairwise farther than eps apart
 // and all within eps of p, so there are at most kissing-number many of them
 // (240 in R^8), under kBorderSetCap.
+//
+// The count pass (inside the run) keeps every set of at most 2 names in
+// bcache and lists the other points (the "heavy" ones) in bheavy; the fill
+// pass (dbscan_border_ids) copies the cached sets with one thread per point
+// and recomputes only the heavy points, with this kernel.
 constexpr int BD_THREADS = 256, BD_WARPS = BD_THREADS / 32;
+
+__device__ __forceinline__ void note_heavy(const Bufs &B, DevCounters *ctr, int t) {
+    const int k = atomicAdd(&ctr->n_heavy, 1);
+    B.bheavy[k] = t;  // k < n_noncore <= N
+}
 
 template <int D, int M, bool FILL>
 __global__ void __launch_bounds__(BD_THREADS)
@@ -709,27 +719,19 @@ k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restr
     if (run_failed(ctr)) return;
     __shared__ int sset[BD_WARPS][kBorderSetCap];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nn = ctr->n_noncore;
+    const int nn = FILL ? ctr->n_heavy : ctr->n_noncore;
     unsigned rech = 0;
     unsigned long long evals = 0, nborder = 0, members = 0;
-    for (int t = warp_id_global(); t < nn; t += warps_global()) {
+    for (int u0 = warp_id_global(); u0 < nn; u0 += warps_global()) {
+        const int t = FILL ? B.bheavy[u0] : u0;
         const int i = B.noncore[t];
         const int g = B.cell_of[i];
         const int o = B.orig[i];
-        // points of small cells were done by k_border_small, unless their set overflowed there
-        if (P.mc_small_nbr > 0 &&
+        // the count pass leaves the points of small cells to k_border_small,
+        // unless their set overflowed there
+        if (!FILL && P.mc_small_nbr > 0 &&
             mc_small(P, B.cell_start[g + 1] - B.cell_start[g], B.nbr_pts, g) && !B.bbig[o])
             continue;
-        if (FILL && B.bcount[o] <= 2) {  // the count pass kept sets of up to 2 names
-            const long long at = B.boff[o];
-            const int2 cs = B.bcache[o];
-            const int ns = (int)B.bcount[o];
-            if (lane < ns) {
-                if (at + ns <= ids_cap) ids[at + lane] = lane == 0 ? cs.x : cs.y;
-                else set_error(ctr, DBSCAN_ERR_CAPACITY, 31);
-            }
-            continue;
-        }
         const Inst &I = P.inst[inst_of_cell(P, g)];
         const Thr T = I.thr;
         const int row0 = I.row0;
@@ -784,6 +786,7 @@ k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restr
                 B.bcount[o] = ns;
                 labels_out[o] = ns ? sset[w][0] : -1;
                 if (ns <= 2) B.bcache[o] = make_int2(ns > 0 ? sset[w][0] : -1, ns > 1 ? sset[w][1] : -1);
+                else note_heavy(B, ctr, t);
             }
             nborder += ns ? 1 : 0;
             members += ns;
@@ -805,22 +808,41 @@ k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restr
     }
 }
 
+// Fill pass, cached part: the sets of at most 2 names kept by the count pass,
+// one thread per non-core point.
+__global__ void __launch_bounds__(256)
+k_border_fill_cached(Bufs B, int32_t *__restrict__ ids, long long ids_cap, DevCounters *ctr) {
+    if (run_failed(ctr)) return;
+    const int nn = ctr->n_noncore;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += gridDim.x * blockDim.x) {
+        const int o = B.orig[B.noncore[t]];
+        const long long ns = B.bcount[o];
+        if (ns == 0 || ns > 2) continue;
+        const long long at = B.boff[o];
+        if (at + ns > ids_cap) {
+            set_error(ctr, DBSCAN_ERR_CAPACITY, 33);
+            continue;
+        }
+        const int2 cs = B.bcache[o];
+        ids[at] = cs.x;
+        if (ns > 1) ids[at + 1] = cs.y;
+    }
+}
+
 // CSR offsets of the border sets: exclusive scan of the per-point counts.
 void launch_border_offsets(const RunParams &P, const Bufs &B, cudaStream_t s) {
     scan_i64_to_i64(B.bcount, B.boff, P.n, nullptr, P.n, B.part, s);
 }
 
-// ClusterBorder for the non-core points of small cells (the cells
+// ClusterBorder's count pass for the non-core points of small cells (the cells
 // k_markcore_small takes): one thread per point, the set of cluster names in
 // registers (up to kSmallSet, sorted).  A point whose set would grow beyond
-// that is flagged in bbig and left to k_border; the fill pass takes the same
-// split from the flags of the count pass.
+// that is flagged in bbig and left to k_border.
 constexpr int kSmallSet = 8;
 
-template <int D, int M, bool FILL>
+template <int D, int M>
 __global__ void __launch_bounds__(256)
-k_border_small(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restrict__ ids,
-               long long ids_cap, DevCounters *ctr) {
+k_border_small(RunParams P, Bufs B, int32_t *__restrict__ labels_out, DevCounters *ctr) {
     if (run_failed(ctr)) return;
     constexpr bool BOX = (M == kF32FromF32 || M == kF32FromF64);
     const int nn = ctr->n_noncore;
@@ -831,19 +853,6 @@ k_border_small(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *_
         const int g = B.cell_of[i];
         const int o = B.orig[i];
         if (!mc_small(P, B.cell_start[g + 1] - B.cell_start[g], B.nbr_pts, g)) continue;
-        if (FILL && B.bbig[o]) continue;
-        if (FILL && B.bcount[o] <= 2) {  // the count pass kept sets of up to 2 names
-            const long long at = B.boff[o];
-            const int2 cs = B.bcache[o];
-            const int ns = (int)B.bcount[o];
-            if (at + ns <= ids_cap) {
-                if (ns > 0) ids[at] = cs.x;
-                if (ns > 1) ids[at + 1] = cs.y;
-            } else {
-                set_error(ctr, DBSCAN_ERR_CAPACITY, 32);
-            }
-            continue;
-        }
         const Inst &I = P.inst[inst_of_cell(P, g)];
         const Thr T = I.thr;
         const int row0 = I.row0;
@@ -885,50 +894,33 @@ k_border_small(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *_
             while (u > 0 && set[u - 1] > L) { set[u] = set[u - 1]; --u; }
             set[u] = L;
         }
-        if (!FILL) {
-            B.bbig[o] = big ? 1 : 0;
-            if (big) continue;  // k_border redoes this point
-            B.bcount[o] = ns;
-            labels_out[o] = ns ? set[0] : -1;
-            if (ns <= 2) B.bcache[o] = make_int2(ns > 0 ? set[0] : -1, ns > 1 ? set[1] : -1);
-            nborder += ns ? 1 : 0;
-            members += ns;
-        } else {
-            const long long at = B.boff[o];
-            if (at + ns <= ids_cap) {
-                for (int u = 0; u < ns; ++u) ids[at + u] = set[u];
-            } else {
-                set_error(ctr, DBSCAN_ERR_CAPACITY, 32);
-            }
-        }
+        B.bbig[o] = big ? 1 : 0;
+        if (big) continue;  // k_border redoes this point
+        B.bcount[o] = ns;
+        labels_out[o] = ns ? set[0] : -1;
+        if (ns <= 2) B.bcache[o] = make_int2(ns > 0 ? set[0] : -1, ns > 1 ? set[1] : -1);
+        else note_heavy(B, ctr, t);
+        nborder += ns ? 1 : 0;
+        members += ns;
     }
-    if (!FILL) {
-        flush_counter(&ctr->band_rechecks, rech);
-        if (P.stats) flush_counter(&ctr->dist_evals[2], evals);
+    flush_counter(&ctr->band_rechecks, rech);
+    if (P.stats) flush_counter(&ctr->dist_evals[2], evals);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) nborder += __shfl_xor_sync(0xffffffffu, nborder, o);
-        if ((threadIdx.x & 31) == 0 && nborder) atomicAdd((unsigned *)&ctr->n_border, (unsigned)nborder);
-        flush_counter((unsigned long long *)&ctr->K, members);
-    }
+    for (int o = 16; o > 0; o >>= 1) nborder += __shfl_xor_sync(0xffffffffu, nborder, o);
+    if ((threadIdx.x & 31) == 0 && nborder) atomicAdd((unsigned *)&ctr->n_border, (unsigned)nborder);
+    flush_counter((unsigned long long *)&ctr->K, members);
 }
 
 void launch_border(int D, int mode, bool fill, const RunParams &P, const Bufs &B, int32_t *labels_out,
                    int32_t *ids, long long ids_cap, DevCounters *ctr, cudaStream_t s, bool offsets) {
-    if (P.mc_small_nbr > 0) {
-        GBDB_DISPATCH(D, mode, {
-            if (!fill) {
-                auto k = k_border_small<DD, MM, false>;
-                const int g = grid_for((const void *)k, 256);
-                k<<<g, 256, 0, s>>>(P, B, labels_out, nullptr, 0, ctr);
-            } else {
-                auto k = k_border_small<DD, MM, true>;
-                const int g = grid_for((const void *)k, 256);
-                k<<<g, 256, 0, s>>>(P, B, labels_out, ids, ids_cap, ctr);
-            }
-            count_launch();
-        });
-    }
     if (!fill) {
+        if (P.mc_small_nbr > 0)
+            GBDB_DISPATCH(D, mode, {
+                auto k = k_border_small<DD, MM>;
+                const int g = grid_for((const void *)k, 256);
+                k<<<g, 256, 0, s>>>(P, B, labels_out, ctr);
+                count_launch();
+            });
         GBDB_DISPATCH(D, mode, {
             auto k = k_border<DD, MM, false>;
             int g = grid_for((const void *)k, BD_THREADS);
@@ -937,6 +929,9 @@ void launch_border(int D, int mode, bool fill, const RunParams &P, const Bufs &B
         });
         if (offsets) launch_border_offsets(P, B, s);
     } else {
+        const int gc = grid_for((const void *)k_border_fill_cached, 256);
+        k_border_fill_cached<<<gc, 256, 0, s>>>(B, ids, ids_cap, ctr);
+        count_launch();
         GBDB_DISPATCH(D, mode, {
             auto k = k_border<DD, MM, true>;
             int g = grid_for((const void *)k, BD_THREADS);

@@ -51,9 +51,8 @@ struct dbscan_ctx {
     size_t sort_scratch_size = 0;
     long long *part = nullptr;
     uint32_t *slot_of = nullptr, *rank_of = nullptr, *slots = nullptr;  // cell grouping
-    unsigned *hcnt = nullptr;
     uint64_t hcap = 0;
-    bool table_clean = false;  // every slot of ht empty and every hcnt zero
+    bool table_clean = false;  // every slot of ht empty ({kEmptyKey, 0})
     float *pf = nullptr, *cpf = nullptr;
     double *pd = nullptr, *cpd = nullptr;
     int *orig = nullptr, *cell_of = nullptr, *cell_start = nullptr;
@@ -95,6 +94,7 @@ struct dbscan_ctx {
     long long *bcount = nullptr, *boff = nullptr;
     unsigned char *bbig = nullptr;
     int2 *bcache = nullptr;
+    int *bheavy = nullptr;
     long long *bbox_out = nullptr;  // [2*kMaxDim + 1], see launch_bbox
     signed char *offs = nullptr;  // [kMaxEnumDim][kMaxOffsets][kMaxEnumDim]
     int noff[gbdb::kMaxEnumDim + 1] = {0};

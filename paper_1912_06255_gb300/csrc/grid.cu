@@ -148,7 +148,7 @@ constexpr int INS_U = 4;  // points per thread per step (their probes overlap)
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_insert(const T *__restrict__ X, RunParams P, ulonglong2 *__restrict__ ht, unsigned *__restrict__ hcnt,
+k_insert(const T *__restrict__ X, RunParams P, ulonglong2 *__restrict__ ht,
          uint64_t hmask, int hlg, uint32_t *__restrict__ slot_of, uint32_t *__restrict__ rank_of,
          uint32_t *__restrict__ slots, unsigned *__restrict__ bloom, int blg, DevCounters *ctr) {
     if (run_failed(ctr)) return;
@@ -223,7 +223,7 @@ k_insert(const T *__restrict__ X, RunParams P, ulonglong2 *__restrict__ ht, unsi
         for (int u = 0; u < INS_U; ++u) {
             const long long i = i0 + (long long)u * T_;
             rk[u] = 0;
-            if (i < P.n && s[u] != ~0ull) rk[u] = atomicAdd(hcnt + s[u], 1u);
+            if (i < P.n && s[u] != ~0ull) rk[u] = (unsigned)atomicAdd(&ht[s[u]].y, 1ull);  // the slot counts its points
         }
 #pragma unroll
         for (int u = 0; u < INS_U; ++u) {
@@ -253,15 +253,15 @@ k_cell_keys(const ulonglong2 *__restrict__ ht, const uint32_t *__restrict__ slot
 // and its point count.
 __global__ void __launch_bounds__(256)
 k_cell_table(RunParams P, const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
-             ulonglong2 *__restrict__ ht, const unsigned *__restrict__ hcnt, uint64_t *__restrict__ cell_key,
+             ulonglong2 *__restrict__ ht, uint64_t *__restrict__ cell_key,
              int *__restrict__ count, int *__restrict__ cell_inst, const DevCounters *ctr) {
     if (run_failed(ctr)) return;
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
         const uint32_t s = vals[c];
+        count[c] = (int)ht[s].y;  // the points k_insert counted in the slot
         ht[s].y = (unsigned long long)c;
         cell_key[c] = keys[c];
-        count[c] = (int)hcnt[s];
         if (P.ninst > 1) cell_inst[c] = (int)(keys[c] >> P.inst_shift);
     }
 }
@@ -308,7 +308,7 @@ k_scatter_points(const T *__restrict__ X, RunParams P, const ulonglong2 *__restr
 
 // Return the slots this run used to empty.
 __global__ void __launch_bounds__(256)
-k_table_reset(ulonglong2 *__restrict__ ht, unsigned *__restrict__ hcnt, const uint32_t *__restrict__ slots,
+k_table_reset(ulonglong2 *__restrict__ ht, const uint32_t *__restrict__ slots,
               const DevCounters *ctr, int n, int cond) {
     if (run_failed(ctr)) return;
     const int m = ctr->m;
@@ -318,8 +318,20 @@ k_table_reset(ulonglong2 *__restrict__ ht, unsigned *__restrict__ hcnt, const ui
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
         const uint32_t s = slots[c];
         ht[s] = make_ulonglong2(kEmptyKey, 0);
-        hcnt[s] = 0;
     }
+}
+
+// Every slot of the cell hash empty: {kEmptyKey, 0} (a slot's second word
+// counts its points during the insert, then holds the cell id).
+__global__ void __launch_bounds__(256) k_table_clear(ulonglong2 *__restrict__ ht, uint64_t cap) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cap; i += (uint64_t)gridDim.x * blockDim.x)
+        ht[i] = make_ulonglong2(kEmptyKey, 0);
+}
+
+void launch_table_clear(ulonglong2 *ht, uint64_t cap, cudaStream_t s) {
+    const int g = grid_for((const void *)k_table_clear, 256);
+    k_table_clear<<<g, 256, 0, s>>>(ht, cap);
+    count_launch();
 }
 
 void launch_semisort(const void *X, int dtype, const RunParams &P, int SD, const Semisort &S, DevCounters *ctr,
@@ -328,11 +340,11 @@ void launch_semisort(const void *X, int dtype, const RunParams &P, int SD, const
     const uint64_t hmask = S.hcap - 1;
     if (dtype == DBSCAN_F32) {
         int g = grid_for((const void *)k_insert<float>, 256);
-        k_insert<float><<<g, 256, 0, s>>>((const float *)X, P, S.ht, S.hcnt, hmask, lg, S.slot_of, S.rank_of,
+        k_insert<float><<<g, 256, 0, s>>>((const float *)X, P, S.ht, hmask, lg, S.slot_of, S.rank_of,
                                           S.slots, S.bloom, S.bloom_lg, ctr);
     } else {
         int g = grid_for((const void *)k_insert<double>, 256);
-        k_insert<double><<<g, 256, 0, s>>>((const double *)X, P, S.ht, S.hcnt, hmask, lg, S.slot_of, S.rank_of,
+        k_insert<double><<<g, 256, 0, s>>>((const double *)X, P, S.ht, hmask, lg, S.slot_of, S.rank_of,
                                            S.slots, S.bloom, S.bloom_lg, ctr);
     }
     count_launch();
@@ -343,7 +355,7 @@ void launch_semisort(const void *X, int dtype, const RunParams &P, int SD, const
     const uint64_t *K = which ? S.k1 : S.k0;
     const uint32_t *V = which ? S.v1 : S.v0;
     g = grid_for((const void *)k_cell_table, 256);
-    k_cell_table<<<g, 256, 0, s>>>(P, K, V, S.ht, S.hcnt, S.cell_key, S.count, S.cell_inst, ctr); count_launch();
+    k_cell_table<<<g, 256, 0, s>>>(P, K, V, S.ht, S.cell_key, S.count, S.cell_inst, ctr); count_launch();
     scan_i32_to_i32(S.count, S.cell_start, 0, &ctr->m, P.n, S.part, s);
     auto scat = [&](auto k, auto xp) {
         int gg = grid_for((const void *)k, 256);
@@ -380,7 +392,7 @@ void launch_table_reset(const Semisort &S, DevCounters *ctr, cudaStream_t s, boo
     }
     const int cond = S.super ? (end_of_run ? 2 : 1) : 0;
     int g = grid_for((const void *)k_table_reset, 256);
-    k_table_reset<<<g, 256, 0, s>>>(S.ht, S.hcnt, S.slots, ctr, S.n, cond); count_launch();
+    k_table_reset<<<g, 256, 0, s>>>(S.ht, S.slots, ctr, S.n, cond); count_launch();
 }
 
 // ---------------------------------------------------------------- boxes

@@ -18,8 +18,7 @@ inline double bbox_key_to_double(long long k) {
 // Buffers of the cell grouping (semisort) of one run.
 struct Semisort {
     const void *unused;
-    ulonglong2 *ht;       // cell hash, hcap slots {key, cell id}; empty between runs
-    unsigned *hcnt;       // points per slot; zero between runs
+    ulonglong2 *ht;       // cell hash, hcap slots {key, point count, then cell id}; empty between runs
     uint64_t hcap;        // power of two >= 2 * max points
     uint32_t *slot_of, *rank_of;  // [n] slot of each point, its position in the cell
     uint32_t *slots;      // [m] slots of the non-empty cells, in insertion order
@@ -47,6 +46,8 @@ struct Semisort {
 // ctr->m, and the slots' cell ids.
 void launch_semisort(const void *X, int dtype, const RunParams &P, int SD, const Semisort &S, DevCounters *ctr,
                      cudaStream_t s);
+// Empty every slot of the cell hash (first use, or after a failed run).
+void launch_table_clear(ulonglong2 *ht, uint64_t cap, cudaStream_t s);
 // Empty the slots the run used (keeps the table clean for the next run): the
 // cells' slots, or at the end of a supercell run the supercells' slots.
 void launch_table_reset(const Semisort &S, DevCounters *ctr, cudaStream_t s, bool end_of_run = true);
@@ -109,6 +110,7 @@ struct Bufs {
     long long *bcount, *boff;
     unsigned char *bbig;  // [N] by input index: the point's border set outgrew k_border_small's
     int2 *bcache;         // [N] by input index: a border set of at most 2 names from the count pass
+    int *bheavy;          // [N] non-core list positions whose sets have more than 2 names
     long long *part;
     int64_t n_max;
 };

@@ -24,6 +24,7 @@ struct DevCounters {
     int n_core;      // core points
     int n_border;    // border points
     int n_noncore;   // non-core points (border candidates)
+    int n_heavy;     // of which with more than 2 cluster names (recomputed by the fill pass)
     int cell_next;   // BCP work counters (ranked cells taken), near and far wave
     int cell_next2;
     int P_list;      // undecided pairs listed by the learned schedule

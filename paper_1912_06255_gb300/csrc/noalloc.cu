@@ -76,7 +76,7 @@ size_t carve(dbscan_ctx *c, unsigned char *base) {
         {(void **)&c->v0, 4 * (size_t)N}, {(void **)&c->v1, 4 * (size_t)N},
         {(void **)&c->sort_scratch, sort_scratch_bytes(N)}, {(void **)&c->part, 8 * (size_t)npart},
         {(void **)&c->slot_of, 4 * (size_t)N}, {(void **)&c->rank_of, 4 * (size_t)N},
-        {(void **)&c->slots, 4 * (size_t)N}, {(void **)&c->hcnt, 4 * (size_t)hcap},
+        {(void **)&c->slots, 4 * (size_t)N},
         {(void **)&c->pf, 4 * (size_t)N * SD}, {(void **)&c->pd, 8 * (size_t)N * SD},
         {(void **)&c->cpf, 4 * (size_t)N * SD}, {(void **)&c->cpd, 8 * (size_t)N * SD},
         {(void **)&c->orig, 4 * (size_t)N}, {(void **)&c->cell_of, 4 * (size_t)N},
@@ -95,6 +95,7 @@ size_t carve(dbscan_ctx *c, unsigned char *base) {
         {(void **)&c->noncore, 4 * (size_t)N},
         {(void **)&c->bcount, 8 * (size_t)N}, {(void **)&c->boff, 8 * (size_t)(N + 1)},
         {(void **)&c->bbig, (size_t)N}, {(void **)&c->bcache, 8 * (size_t)N},
+        {(void **)&c->bheavy, 4 * (size_t)N},
         {(void **)&c->bbox_out, 8 * (2 * kMaxDim + 1)},
         {(void **)&c->offs, (size_t)kMaxEnumDim * kMaxOffsets * kMaxEnumDim},
         {(void **)&c->ctr, sizeof(DevCounters)},
@@ -139,8 +140,8 @@ dbscan_status setup_device(int dev) {
         }
     }
     c.hcap = hash_capacity((int)kStaticMaxPoints);
-    e = cudaMemset(c.ht, 0xff, sizeof(ulonglong2) * c.hcap);
-    if (e == cudaSuccess) e = cudaMemset(c.hcnt, 0, sizeof(unsigned) * c.hcap);
+    launch_table_clear(c.ht, c.hcap, 0);
+    e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
