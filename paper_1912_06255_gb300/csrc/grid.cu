@@ -719,7 +719,7 @@ constexpr int NBS_WARPS = 8;  // warps per block of k_neighbors_super
 // 2i, 2i+1 of a register per 32-candidate chunk, and the lists are written
 // adjacent cells first, from two ballots per chunk.
 template <int D>
-__global__ void __launch_bounds__(32 * NBS_WARPS)
+__global__ void __launch_bounds__(32 * NBS_WARPS, 4)  // 64 registers: 4 blocks (32 warps) per SM
 k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict__ ht,
                   const unsigned *__restrict__ bloom, int bloom_lg, const int *__restrict__ sc_first,
                   const int *__restrict__ cell_start, int *__restrict__ nbr_pts, RunParams P, int stride,
@@ -739,6 +739,16 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
     const int lg = hash_log2(cap);
     const uint64_t mask = cap - 1;
     const int blg = super_bloom_lg(m, bloom_lg);
+    // this lane's probe offset o(lane) + 1, 2 bits per dimension
+    unsigned odig = 0;
+    {
+        int t = lane;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            odig |= (unsigned)(t % 3) << (2 * j);
+            t /= 3;
+        }
+    }
     long long total = 0;
     for (int si = warp_id_global(); si < ms; si += warps_global()) {
         const int c0 = sc_first[si];
@@ -762,13 +772,7 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
                 s_hi[w][lane] = bhi[c0 + lane];
             }
         }
-        unsigned pown = 0;
-#pragma unroll
-        for (int b = 0; b < D; ++b) {
-            const unsigned bb = __ballot_sync(0xffffffffu, (pmine >> b) & 1u);
-#pragma unroll
-            for (int i = 0; i < K; ++i) pown |= ((bb >> i) & 1u) << (D * i + b);
-        }
+        const unsigned pown = __reduce_or_sync(0xffffffffu, lane < k ? pmine << (D * lane) : 0u);
         __syncwarp();
         // the supercell's coordinates, for the bounds of the probes
         int sc[kMaxDim];
@@ -778,11 +782,9 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
         if (lane < NS && k > 0) {
             int o[D];
             bool in = true;
-            int t = lane;
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                o[j] = t % 3 - 1;
-                t /= 3;
+                o[j] = (int)((odig >> (2 * j)) & 3u) - 1;
                 const int v = sc[j] + o[j];
                 in = in && v >= 0 && v <= (I.kmax[j] >> 1);
             }
@@ -829,17 +831,14 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
                 if (j + step < 32 && ex <= f) j += step;
             }
             const int h = __shfl_sync(0xffffffffu, t0, j) + f - __shfl_sync(0xffffffffu, excl, j);
+            const unsigned oj = __shfl_sync(0xffffffffu, odig, j);
             if (f >= ncand) continue;
             hreg[ch] = h;
             const unsigned q = (unsigned)(cell_key[h] & QMASK);
             int rel[D];  // 2 o + q, per dimension (o from the owner lane j)
             {
-                int t = j;
 #pragma unroll
-                for (int jj = 0; jj < D; ++jj) {
-                    rel[jj] = 2 * (t % 3 - 1) + (int)((q >> jj) & 1u);
-                    t /= 3;
-                }
+                for (int jj = 0; jj < D; ++jj) rel[jj] = 2 * ((int)((oj >> (2 * jj)) & 3u) - 1) + (int)((q >> jj) & 1u);
             }
             Bx<D> bl, bh;
             if (P.box) {
