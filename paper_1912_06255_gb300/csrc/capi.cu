@@ -213,6 +213,8 @@ static cudaError_t ensure_hd(dbscan_ctx *c) {
         {(void **)&H.nhi, 16 * N}, {(void **)&H.nbr_off, 8 * (N + 1)},
         {(void **)&H.scratch, sizeof(int) * (size_t)hd_scratch_ints()},
         {(void **)&H.nblo, 32 * N}, {(void **)&H.nbhi, 32 * N},
+        {(void **)&H.nmax, 4 * N}, {(void **)&H.fwd_off, 8 * N},
+        {(void **)&H.fn, 4 * N}, {(void **)&H.ff, 4 * N}, {(void **)&H.bn, 4 * N}, {(void **)&H.bf, 4 * N},
     };
     size_t total = 0;
     for (const auto &it : items) total += align_up(it.bytes);
@@ -247,25 +249,32 @@ static dbscan_status enqueue_hd_cells(dbscan_ctx *c, const RunParams &P, const v
     mark(3);
     hd_tree(P, c->hd, B, c->ctr, s);
     mark(4);
+    // one buffer of 4 F entries: the forward lists [F], their ranks in the
+    // backward lists [F], the full lists [2 F]
     for (int attempt = 0; attempt < 2; ++attempt) {
-        int *nbr = c->hd_nbr_cap > c->nbr_cap ? c->hd_nbr : c->nbr;
-        const long long cap = c->hd_nbr_cap > c->nbr_cap ? c->hd_nbr_cap : c->nbr_cap;
+        int *buf = c->hd_nbr_cap > c->nbr_cap ? c->hd_nbr : c->nbr;
+        const long long capF = (c->hd_nbr_cap > c->nbr_cap ? c->hd_nbr_cap : c->nbr_cap) / 4;
         CK(cudaMemsetAsync(&c->ctr->E, 0, sizeof(long long), s));
-        hd_neighbors(P, c->hd, B, nbr, cap, c->ctr, s);
+        hd_neighbors(P, c->hd, B, buf, capF, c->ctr, s);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (c->h_ctr->err) return (dbscan_status)c->h_ctr->err;
         const long long E = c->h_ctr->E;
-        if (E <= cap) {
-            c->nbr_cur = nbr;
+        if (E <= capF) {
+            const size_t m = (size_t)c->h_ctr->m;
+            CK(cudaMemsetAsync(c->hd.bn, 0, 4 * m, s));
+            CK(cudaMemsetAsync(c->hd.bf, 0, 4 * m, s));
+            if (P.mc_small_nbr > 0 && P.mc_small_nbr < (1 << 30)) CK(cudaMemsetAsync(c->nbr_pts, 0, 4 * m, s));
+            hd_transpose(P, c->hd, B, buf, buf + capF, buf + 2 * capF, c->ctr, s);
+            c->nbr_cur = buf + 2 * capF;
             c->nbr_off_cur = c->hd.nbr_off;
             return DBSCAN_OK;
         }
         cudaFree(c->hd_nbr);
         c->hd_nbr = nullptr;
         c->hd_nbr_cap = 0;
-        const long long grown = E + E / 4;
+        const long long grown = 4 * (E + E / 4);
         if (ctx_malloc(c, (void **)&c->hd_nbr, sizeof(int) * (size_t)grown) != cudaSuccess) {
             (void)cudaGetLastError();
             c->hd_nbr = nullptr;

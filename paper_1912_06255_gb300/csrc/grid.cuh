@@ -134,15 +134,24 @@ struct HdBufs {
     float4 *nblo, *nbhi;          // [m-1] x 2: node bounding boxes of the points (FP32-band mode)
     long long *nbr_off;           // [m+1] offset of each cell's neighbour list
     int *scratch;                 // per-warp leaf scratch of the neighbour kernel
+    int *nmax;                    // [m-1] last cell (leaf) under each internal node
+    long long *fwd_off;           // [m] offset of each cell's forward list (cells after it only)
+    int *fn, *ff;                 // [m] forward adjacent / farther counts
+    int *bn, *bf;                 // [m] backward adjacent / farther counts (zero before the transpose)
 };
 // Cells of the sorted points (key_bits = d * bits), then their boxes and tree.
 void hd_cells(const void *X, int dtype, const RunParams &P, int key_bits, const HdBufs &H, const Bufs &B,
               DevCounters *ctr, cudaStream_t s);
 void hd_tree(const RunParams &P, const HdBufs &H, const Bufs &B, DevCounters *ctr, cudaStream_t s);
-// The neighbour lists into nbr (cap entries), one walk per 32 cells; ctr->E
-// (zero before) receives the total, which exceeds cap if nbr was too small.
-void hd_neighbors(const RunParams &P, const HdBufs &H, const Bufs &B, int *nbr, long long cap, DevCounters *ctr,
+// The forward neighbour lists (each unordered pair once, from its lower cell)
+// into fwd (cap entries), one walk per 32 cells; ctr->E (zero before)
+// receives their total, which exceeds cap if fwd was too small.
+void hd_neighbors(const RunParams &P, const HdBufs &H, const Bufs &B, int *fwd, long long cap, DevCounters *ctr,
                   cudaStream_t s);
+// The full lists from the forward ones (rank: as many entries as fwd; nbr:
+// twice as many; H.bn, H.bf and, when used, B.nbr_pts zero before).
+void hd_transpose(const RunParams &P, const HdBufs &H, const Bufs &B, const int *fwd, int *rank, int *nbr,
+                  DevCounters *ctr, cudaStream_t s);
 long long hd_scratch_ints();  // size of HdBufs::scratch
 
 // full path compression of the cell union-find

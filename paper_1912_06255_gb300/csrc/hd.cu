@@ -170,7 +170,7 @@ __device__ __forceinline__ int prefix(const uint64_t *__restrict__ lo, const uin
 
 __global__ void __launch_bounds__(256)
 k_lbvh_nodes(const uint64_t *__restrict__ klo, const uint64_t *__restrict__ khi, int2 *__restrict__ child,
-             int *__restrict__ parent, int *__restrict__ flag, const DevCounters *ctr) {
+             int *__restrict__ parent, int *__restrict__ flag, int *__restrict__ nmax, const DevCounters *ctr) {
     if (run_failed(ctr)) return;
     const int m = ctr->m;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m - 1; i += gridDim.x * blockDim.x) {
@@ -194,6 +194,7 @@ k_lbvh_nodes(const uint64_t *__restrict__ klo, const uint64_t *__restrict__ khi,
         const int left = lo == g ? (m - 1) + g : g;
         const int right = hi == g + 1 ? (m - 1) + g + 1 : g + 1;
         child[i] = make_int2(left, right);
+        nmax[i] = hi;  // the node covers the cells lo .. hi
         parent[left] = i;
         parent[right] = i;
     }
@@ -359,7 +360,7 @@ template <int DD>
 __device__ __forceinline__ int leaf_test(const Walk &W, int h, const int4 *__restrict__ ccoord, bool box,
                                          const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
                                          float hi_thr) {
-    if (!W.valid || h == W.g) return 0;
+    if (!W.valid || h <= W.g) return 0;  // each unordered pair once: from the lower cell
     const int4 ch4 = ccoord[h];
     unsigned a = 0;
     int s = 0;
@@ -381,7 +382,8 @@ __device__ __forceinline__ int leaf_test(const Walk &W, int h, const int4 *__res
 // *ncand counts them all) and count each lane's hits.
 template <int DD, bool EMIT>
 __device__ __forceinline__ void walk(const Walk &W, int m, bool box, float hi_thr, int *stk,
-                                     const int2 *__restrict__ child, const int4 *__restrict__ nlo,
+                                     const int2 *__restrict__ child, const int *__restrict__ nmax,
+                                     const int4 *__restrict__ nlo,
                                      const int4 *__restrict__ nhi, const float4 *__restrict__ nblo,
                                      const float4 *__restrict__ nbhi, const int4 *__restrict__ ccoord,
                                      const float4 *__restrict__ blo, const float4 *__restrict__ bhi, int *scr,
@@ -419,7 +421,8 @@ __device__ __forceinline__ void walk(const Walk &W, int m, bool box, float hi_th
                     }
                 }
             } else {
-                bool enter = W.valid && gap2<DD>(W.c, nlo[q], nhi[q]) <= DD;
+                // only subtrees holding a cell after the lane's own (forward pairs)
+                bool enter = W.valid && nmax[q] > W.g && gap2<DD>(W.c, nlo[q], nhi[q]) <= DD;
                 if (enter && box)
                     enter = boxes_min_d2_dd<DD>(W.glo, W.ghi, load_box<8>(nblo, q), load_box<8>(nbhi, q)) <= hi_thr;
                 if (__any_sync(0xffffffffu, enter)) {
@@ -438,12 +441,12 @@ __device__ __forceinline__ void walk(const Walk &W, int m, bool box, float hi_th
 
 template <int DD>
 __global__ void __launch_bounds__(32 * QW)
-k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int4 *__restrict__ nlo,
-                 const int4 *__restrict__ nhi, const float4 *__restrict__ nblo, const float4 *__restrict__ nbhi,
-                 const int4 *__restrict__ ccoord, const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
-                 const int *__restrict__ cell_start, int *__restrict__ scratch, int *__restrict__ nbr_pts,
-                 int *__restrict__ nbr_cnt, int *__restrict__ nbr_near, long long *__restrict__ off,
-                 int *__restrict__ nbr, long long cap, long long max_warps, DevCounters *ctr) {
+k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int *__restrict__ nmax,
+                 const int4 *__restrict__ nlo, const int4 *__restrict__ nhi, const float4 *__restrict__ nblo,
+                 const float4 *__restrict__ nbhi, const int4 *__restrict__ ccoord, const float4 *__restrict__ blo,
+                 const float4 *__restrict__ bhi, int *__restrict__ scratch, int *__restrict__ fn,
+                 int *__restrict__ ff, long long *__restrict__ off, int *__restrict__ nbr, long long cap,
+                 long long max_warps, DevCounters *ctr) {
     if (run_failed(ctr)) return;
     __shared__ int stk[QW][kStack];
     if (warps_global() > max_warps) {  // the scratch has no room for this grid (cannot happen: sized for the largest)
@@ -469,8 +472,8 @@ k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int4 *__rest
         }
         int ncand = 0, n_near = 0, n_far = 0;
         long long near_at = 0, far_at = 0;
-        walk<DD, false>(W, m, box, hi_thr, stk[w], child, nlo, nhi, nblo, nbhi, ccoord, blo, bhi, scr, ncand, n_near,
-                    n_far, nbr, near_at, far_at, ctr);
+        walk<DD, false>(W, m, box, hi_thr, stk[w], child, nmax, nlo, nhi, nblo, nbhi, ccoord, blo, bhi, scr, ncand,
+                        n_near, n_far, nbr, near_at, far_at, ctr);
         // reserve the packet's space: lane offsets by an exclusive scan of the counts
         const int mine = n_near + n_far;
         int incl = mine;
@@ -486,17 +489,8 @@ k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int4 *__rest
         const long long at = (long long)base + (incl - mine);
         if (W.valid) {
             off[W.g] = at;
-            nbr_cnt[W.g] = mine;
-            nbr_near[W.g] = n_near;
-        }
-        if (nbr_pts) {
-            // points in the neighbouring cells, from the scratch (or 0 if it overflowed)
-            int pts = 0;
-            for (int i = 0; i < ncand && ncand <= kScr; ++i) {
-                const int4 e = reinterpret_cast<const int4 *>(scr)[i];
-                if ((((unsigned)e.y | (unsigned)e.z) >> lane) & 1u) pts += cell_start[e.x + 1] - cell_start[e.x];
-            }
-            if (W.valid) nbr_pts[W.g] = ncand <= kScr ? pts : (1 << 30);
+            fn[W.g] = n_near;
+            ff[W.g] = n_far;
         }
         if ((long long)base + total > cap) continue;  // the host grows the buffer and runs again
         near_at = at;
@@ -508,8 +502,8 @@ k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int4 *__rest
                 else if (((unsigned)e.z >> lane) & 1u) nbr[far_at++] = e.x;
             }
         } else {
-            walk<DD, true>(W, m, box, hi_thr, stk[w], child, nlo, nhi, nblo, nbhi, ccoord, blo, bhi, scr, ncand,
-                       n_near, n_far, nbr, near_at, far_at, ctr);
+            walk<DD, true>(W, m, box, hi_thr, stk[w], child, nmax, nlo, nhi, nblo, nbhi, ccoord, blo, bhi, scr,
+                           ncand, n_near, n_far, nbr, near_at, far_at, ctr);
         }
         __syncwarp();
     }
@@ -573,7 +567,7 @@ void hd_cells(const void *X, int dtype, const RunParams &P, int key_bits, const 
 void hd_tree(const RunParams &P, const HdBufs &H, const Bufs &B, DevCounters *ctr, cudaStream_t s) {
     if (P.box) launch_boxes(8, B.pf, B.cell_start, ctr, const_cast<float4 *>(B.blo), const_cast<float4 *>(B.bhi), s);
     int g = grid_for((const void *)k_lbvh_nodes, 256);
-    k_lbvh_nodes<<<g, 256, 0, s>>>(H.ckey_lo, H.ckey_hi, H.child, H.parent, H.flag, ctr);
+    k_lbvh_nodes<<<g, 256, 0, s>>>(H.ckey_lo, H.ckey_hi, H.child, H.parent, H.flag, H.nmax, ctr);
     count_launch();
     g = grid_for((const void *)k_lbvh_bounds, 256);
     k_lbvh_bounds<<<g, 256, 0, s>>>(H.child, H.parent, H.flag, H.ccoord, H.nlo, H.nhi, P.d, B.blo, B.bhi,
@@ -596,16 +590,13 @@ static long long hd_max_warps() {
 long long hd_scratch_ints() { return hd_max_warps() * kScr * 4; }
 
 // Step 4: the neighbour lists into nbr (cap entries); ctr->E must be 0 before.
-void hd_neighbors(const RunParams &P, const HdBufs &H, const Bufs &B, int *nbr, long long cap, DevCounters *ctr,
+void hd_neighbors(const RunParams &P, const HdBufs &H, const Bufs &B, int *fwd, long long cap, DevCounters *ctr,
                   cudaStream_t s) {
-    const bool pts = P.mc_small_nbr > 0 && P.mc_small_nbr < (1 << 30);
     const long long maxw = hd_max_warps();
     auto go = [&](auto k) {
         const int g = grid_for((const void *)k, 32 * QW);
-        k<<<g, 32 * QW, 0, s>>>(P, H.child, H.nlo, H.nhi, H.nblo, H.nbhi, H.ccoord, B.blo, B.bhi, B.cell_start,
-                                H.scratch, pts ? const_cast<int *>(B.nbr_pts) : nullptr,
-                                const_cast<int *>(B.nbr_cnt), const_cast<int *>(B.nbr_near), H.nbr_off, nbr, cap,
-                                maxw, ctr);
+        k<<<g, 32 * QW, 0, s>>>(P, H.child, H.nmax, H.nlo, H.nhi, H.nblo, H.nbhi, H.ccoord, B.blo, B.bhi, H.scratch,
+                                H.fn, H.ff, H.fwd_off, fwd, cap, maxw, ctr);
     };
     // one instantiation per dimension: the offset and box tests cover only the used coordinates
     switch (P.d) {
@@ -614,6 +605,99 @@ void hd_neighbors(const RunParams &P, const HdBufs &H, const Bufs &B, int *nbr, 
     case 7: go(k_lbvh_neighbors<7>); break;
     default: go(k_lbvh_neighbors<8>); break;
     }
+    count_launch();
+}
+
+// ------------------------------------------------------------ transpose
+// The walk lists every unordered pair once, from its lower cell (forward
+// lists: adjacent cells first).  The full lists add each pair to the higher
+// cell too: a warp per cell g counts, for every forward entry h, its place in
+// h's backward list (an atomic per entry, also the number of points in the
+// neighbouring cells when MarkCore needs it); the totals are scanned into the
+// final offsets; a second pass writes every cell's list as [forward adjacent,
+// backward adjacent, forward farther, backward farther].
+__global__ void __launch_bounds__(256)
+k_hd_back_count(const long long *__restrict__ fo, const int *__restrict__ fn, const int *__restrict__ ff,
+                const int *__restrict__ fwd, int *__restrict__ rank, int *__restrict__ bn, int *__restrict__ bf,
+                const int *__restrict__ cell_start, int *__restrict__ nbr_pts, DevCounters *ctr) {
+    if (run_failed(ctr)) return;
+    const int lane = threadIdx.x & 31;
+    const int m = ctr->m;
+    for (int g = warp_id_global(); g < m; g += warps_global()) {
+        const long long f0 = fo[g];
+        const int a = fn[g], cnt = a + ff[g];
+        const int gsz = nbr_pts ? cell_start[g + 1] - cell_start[g] : 0;
+        int pts = 0;
+        for (int e = lane; e < cnt; e += 32) {
+            const int h = fwd[f0 + e];
+            rank[f0 + e] = atomicAdd(e < a ? bn + h : bf + h, 1);
+            if (nbr_pts) {
+                pts += cell_start[h + 1] - cell_start[h];
+                atomicAdd(nbr_pts + h, gsz);
+            }
+        }
+        if (nbr_pts) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pts += __shfl_xor_sync(0xffffffffu, pts, o);
+            if (lane == 0 && pts) atomicAdd(nbr_pts + g, pts);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_hd_totals(const int *__restrict__ fn, const int *__restrict__ ff, const int *__restrict__ bn,
+            const int *__restrict__ bf, long long *__restrict__ tot, int *__restrict__ nbr_cnt,
+            int *__restrict__ nbr_near, DevCounters *ctr) {
+    if (run_failed(ctr)) return;
+    const int m = ctr->m;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < m; g += gridDim.x * blockDim.x) {
+        const int t = fn[g] + ff[g] + bn[g] + bf[g];
+        tot[g] = t;
+        nbr_cnt[g] = t;
+        nbr_near[g] = fn[g] + bn[g];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr->E *= 2;  // every pair now in both lists
+}
+
+__global__ void __launch_bounds__(256)
+k_hd_fill(const long long *__restrict__ fo, const int *__restrict__ fn, const int *__restrict__ ff,
+          const int *__restrict__ bn, const int *__restrict__ fwd, const int *__restrict__ rank,
+          const long long *__restrict__ off, int *__restrict__ nbr, DevCounters *ctr) {
+    if (run_failed(ctr)) return;
+    const int lane = threadIdx.x & 31;
+    const int m = ctr->m;
+    for (int g = warp_id_global(); g < m; g += warps_global()) {
+        const long long f0 = fo[g], o = off[g];
+        const int a = fn[g], cnt = a + ff[g], bng = bn[g];
+        for (int e = lane; e < cnt; e += 32) {
+            const int h = fwd[f0 + e];
+            const int r = rank[f0 + e];
+            const long long oh = off[h] + fn[h];
+            if (e < a) {
+                nbr[o + e] = h;
+                nbr[oh + r] = g;
+            } else {
+                nbr[o + bng + e] = h;
+                nbr[oh + bn[h] + ff[h] + r] = g;
+            }
+        }
+    }
+}
+
+void hd_transpose(const RunParams &P, const HdBufs &H, const Bufs &B, const int *fwd, int *rank, int *nbr,
+                  DevCounters *ctr, cudaStream_t s) {
+    const bool pts = P.mc_small_nbr > 0 && P.mc_small_nbr < (1 << 30);
+    int g = grid_for((const void *)k_hd_back_count, 256);
+    k_hd_back_count<<<g, 256, 0, s>>>(H.fwd_off, H.fn, H.ff, fwd, rank, H.bn, H.bf, B.cell_start,
+                                      pts ? const_cast<int *>(B.nbr_pts) : nullptr, ctr);
+    count_launch();
+    g = grid_for((const void *)k_hd_totals, 256);
+    k_hd_totals<<<g, 256, 0, s>>>(H.fn, H.ff, H.bn, H.bf, H.nbr_off, const_cast<int *>(B.nbr_cnt),
+                                  const_cast<int *>(B.nbr_near), ctr);
+    count_launch();
+    scan_i64_to_i64(H.nbr_off, H.nbr_off, 0, &ctr->m, B.n_max, B.part, s);
+    g = grid_for((const void *)k_hd_fill, 256);
+    k_hd_fill<<<g, 256, 0, s>>>(H.fwd_off, H.fn, H.ff, H.bn, fwd, rank, H.nbr_off, nbr, ctr);
     count_launch();
 }
 
