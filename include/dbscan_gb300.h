@@ -112,7 +112,14 @@ enum {
     /* value: 0 (default) or 1: record a link witness for every union of two
        clusters during the run (for dbscan_link_witnesses; a checking aid, the
        result does not change) */
-    DBSCAN_OPT_WITNESS = 13
+    DBSCAN_OPT_WITNESS = 13,
+    /* value: 0 (default) or L = 1..3: for 5 <= d <= 8 in the FP32-band mode
+       with cell bounds, MarkCore counts the points of a neighbouring cell of
+       at least 32 points by descending a quadtree of L levels below the cell
+       (the range counting of Sec. 5.2): nodes whose points are all within eps
+       count whole, nodes with none are skipped, only the leaves in between
+       are scanned.  Ignored below 5 dimensions and in the FP64 mode. */
+    DBSCAN_OPT_QUADTREE = 14
 };
 enum { DBSCAN_PREC_FP64 = 0, DBSCAN_PREC_FP32_RECHECK = 1 };
 /* SIZE: core-cell pairs are tested in order of non-increasing core count of the
@@ -382,6 +389,7 @@ typedef struct {
     int32_t blocks_per_sm;  /* DBSCAN_OPT_BLOCKS_PER_SM */
     int32_t small_cells;    /* DBSCAN_OPT_SMALL_CELLS */
     int32_t pair_boxes;     /* DBSCAN_OPT_PAIR_BOXES */
+    int32_t quadtree;       /* DBSCAN_OPT_QUADTREE */
     int32_t trials;         /* configurations timed */
     float best_ms;          /* wall time of one call with the chosen configuration (best of reps) */
     float default_ms;       /* the same for the configuration the context had before */

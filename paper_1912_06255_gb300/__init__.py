@@ -104,13 +104,14 @@ class DBSCAN:
                 "connect_cells": self.get_option(_lib.OPT_CONNECT_CELLS),
                 "blocks_per_sm": self.get_option(_lib.OPT_BLOCKS_PER_SM),
                 "small_cells": self.get_option(_lib.OPT_SMALL_CELLS),
-                "pair_boxes": self.get_option(_lib.OPT_PAIR_BOXES)}
+                "pair_boxes": self.get_option(_lib.OPT_PAIR_BOXES),
+                "quadtree": self.get_option(_lib.OPT_QUADTREE)}
 
     def set_tuning(self, t: dict) -> None:
         for key, opt in (("schedule", _lib.OPT_SCHEDULE), ("cell_bounds", _lib.OPT_CELL_BOUNDS),
                          ("connect_waves", _lib.OPT_CONNECT_WAVES), ("connect_cells", _lib.OPT_CONNECT_CELLS),
                          ("blocks_per_sm", _lib.OPT_BLOCKS_PER_SM), ("small_cells", _lib.OPT_SMALL_CELLS),
-                         ("pair_boxes", _lib.OPT_PAIR_BOXES)):
+                         ("pair_boxes", _lib.OPT_PAIR_BOXES), ("quadtree", _lib.OPT_QUADTREE)):
             if key in t:
                 self.set_option(opt, int(t[key]))
 

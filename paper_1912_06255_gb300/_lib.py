@@ -22,7 +22,7 @@ F32, F64 = 0, 1
 OPT_PRECISION, OPT_SCHEDULE, OPT_COLLECT_STATS, OPT_MAX_ITERS, OPT_PHASE_TIMING, OPT_CELL_BOUNDS = 0, 1, 2, 3, 4, 5
 OPT_BATCH_GRAPH, OPT_PAIR_LOG = 6, 7
 OPT_CONNECT_CELLS, OPT_CONNECT_WAVES, OPT_BLOCKS_PER_SM, OPT_SMALL_CELLS, OPT_PAIR_BOXES = 8, 9, 10, 11, 12
-OPT_WITNESS = 13
+OPT_WITNESS, OPT_QUADTREE = 13, 14
 MLP_PARAMS = 1313
 PREC_FP64, PREC_FP32_RECHECK = 0, 1
 SCHED_SIZE, SCHED_NONE, SCHED_LEARNED = 0, 1, 2
@@ -61,7 +61,7 @@ class Tuning(ctypes.Structure):
     """dbscan_tuning."""
     _fields_ = [("schedule", ctypes.c_int32), ("cell_bounds", ctypes.c_int32), ("connect_waves", ctypes.c_int32),
                 ("connect_cells", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("small_cells", ctypes.c_int32),
-                ("pair_boxes", ctypes.c_int32),
+                ("pair_boxes", ctypes.c_int32), ("quadtree", ctypes.c_int32),
                 ("trials", ctypes.c_int32),
                 ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float)]
 

@@ -125,6 +125,14 @@ static Bufs make_bufs(dbscan_ctx *c, bool f64) {
     B.bheavy = c->bheavy;
     B.part = c->part;
     B.n_max = c->max_points;
+    B.qt.levels = 0;
+    if (c->qt_arena)
+        for (int l = 0; l < 3; ++l) {
+            B.qt.qpos[l] = c->hd.qpos[l];
+            B.qt.qstart[l] = c->hd.qstart[l];
+            B.qt.qlo[l] = c->hd.qlo[l];
+            B.qt.qhi[l] = c->hd.qhi[l];
+        }
     return B;
 }
 
@@ -227,6 +235,34 @@ static cudaError_t ensure_hd(dbscan_ctx *c) {
     for (const auto &it : items) {
         *it.p = (char *)c->hd_arena + at;
         at += align_up(it.bytes);
+    }
+    return cudaSuccess;
+}
+
+// Buffers of the quadtree below the cells (5 <= d <= 8, MarkCore's range
+// counts), one allocation for all three levels.
+static cudaError_t ensure_qt(dbscan_ctx *c) {
+    if (c->qt_arena) return cudaSuccess;
+    const size_t N = (size_t)std::max<int64_t>(c->max_points, 1);
+    HdBufs &H = c->hd;
+    std::vector<std::pair<void **, size_t>> items = {{(void **)&H.qsub_in, 4 * N}, {(void **)&H.qsub, 4 * N}};
+    for (int l = 0; l < 3; ++l) {
+        items.push_back({(void **)&H.qpos[l], 4 * (N + 1)});
+        items.push_back({(void **)&H.qstart[l], 4 * (N + 1)});
+        items.push_back({(void **)&H.qlo[l], 32 * N});
+        items.push_back({(void **)&H.qhi[l], 32 * N});
+    }
+    size_t total = 0;
+    for (const auto &it : items) total += align_up(it.second);
+    const cudaError_t e = ctx_malloc(c, &c->qt_arena, total);
+    if (e != cudaSuccess) {
+        c->qt_arena = nullptr;
+        return e;
+    }
+    size_t at = 0;
+    for (const auto &it : items) {
+        *it.first = (char *)c->qt_arena + at;
+        at += align_up(it.second);
     }
     return cudaSuccess;
 }
@@ -389,6 +425,7 @@ static dbscan_status enqueue_core(dbscan_ctx *c, const RunParams &P, int D, int 
     Bufs B = make_bufs(c, f64);
     B.n_max = n;
     B.nbr_stride = hashed ? c->noff[d_enum] : 0;
+    B.qt.levels = P.qt;
     mark(5);
     launch_markcore(D, mode, P, B, c->ctr, s);
     mark(6);
@@ -501,6 +538,7 @@ void dbscan_destroy(dbscan_ctx *c) {
     cudaFree(c->lk1);
     cudaFree(c->lscratch);
     cudaFree(c->hd_arena);
+    cudaFree(c->qt_arena);
     cudaFree(c->hd_nbr);
     cudaFree(c->log_feat);
     cudaFree(c->log_lab);
@@ -670,6 +708,10 @@ dbscan_status dbscan_set_option(dbscan_ctx *c, int option, int64_t value) {
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
         c->pair_box = (int)value;
         return DBSCAN_OK;
+    case DBSCAN_OPT_QUADTREE:
+        if (value < 0 || value > 3) return DBSCAN_ERR_INVALID_ARG;
+        c->qt_levels = (int)value;
+        return DBSCAN_OK;
     case DBSCAN_OPT_WITNESS:
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
         if (value && !c->wit) {
@@ -717,6 +759,7 @@ dbscan_status dbscan_get_option(const dbscan_ctx *c, int option, int64_t *value)
     case DBSCAN_OPT_SMALL_CELLS: *value = c->mc_small_nbr; return DBSCAN_OK;
     case DBSCAN_OPT_PAIR_BOXES: *value = c->pair_box; return DBSCAN_OK;
     case DBSCAN_OPT_WITNESS: *value = c->witness; return DBSCAN_OK;
+    case DBSCAN_OPT_QUADTREE: *value = c->qt_levels; return DBSCAN_OK;
     default: return DBSCAN_ERR_INVALID_ARG;
     }
 }
@@ -828,6 +871,12 @@ static dbscan_status run_once(dbscan_ctx *c, const void *d_points, int64_t n, in
     P.cell_inst = c->cell_inst;
     c->stats.precision = (mode == kF32FromF32 || mode == kF32FromF64) ? DBSCAN_PREC_FP32_RECHECK : DBSCAN_PREC_FP64;
     P.box = c->stats.precision == DBSCAN_PREC_FP32_RECHECK && c->cell_bounds ? 1 : 0;
+    // the quadtree of the cells (Sec. 5.2) for MarkCore: d >= 5 with box bounds
+    P.qt = d > kMaxEnumDim && P.box ? c->qt_levels : 0;
+    if (P.qt > 0 && ensure_qt(c) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return DBSCAN_ERR_OOM;
+    }
     c->stats.band_lo = P.lo;
     c->stats.band_hi = P.hi;
 

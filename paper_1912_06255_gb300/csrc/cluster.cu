@@ -41,6 +41,56 @@ __device__ __forceinline__ bool mc_small(const RunParams &P, int k, const int *n
     return P.mc_small_nbr >= MC_SMALL_ALL || nbr_pts[c] <= P.mc_small_nbr;
 }
 
+// RangeCount(p, eps, h) of Sec. 5.2 on the quadtree of cell h (points
+// [t0, t1)): the points within eps of p, counted until `need` is reached.  A
+// depth-first descent over the node boxes: a node whose points are all within
+// eps counts whole, one with none is skipped, a leaf in between is scanned with
+// the exact test (FP32 band, FP64 recheck).  Only for d >= 5 in the FP32-band
+// mode; cells below QT_MIN points are scanned directly.
+constexpr int QT_MIN = 32;
+
+template <int D, int M>
+__device__ __forceinline__ int qt_range_count(const Pt<D, M> &p, int t0, int t1, const QtView &Q, const Thr &T,
+                                              const RunParams &P, const float *__restrict__ pf,
+                                              const double *__restrict__ pd, int64_t ip, int need, unsigned &rech,
+                                              unsigned long long &evals) {
+    int cnt = 0;
+    if constexpr (D == 8 && (M == kF32FromF32 || M == kF32FromF64)) {
+        int cur[4], end[4];
+        int lv = 1;
+        cur[1] = Q.qpos[0][t0];
+        end[1] = Q.qpos[0][t1];
+        while (lv > 0) {
+            if (cur[lv] >= end[lv]) {
+                --lv;
+                continue;
+            }
+            const int k = cur[lv]++;
+            const int a = Q.qstart[lv - 1][k], b = Q.qstart[lv - 1][k + 1];
+            const Bx<8> lo = load_box<8>(Q.qlo[lv - 1], k), hi = load_box<8>(Q.qhi[lv - 1], k);
+            if (box_max_d2<8>(p.f, lo, hi) <= T.lo) {  // every point of the node within eps
+                cnt += b - a;
+                if (cnt >= need) return cnt;
+                continue;
+            }
+            if (box_min_d2<8>(p.f, lo, hi) > T.hi) continue;  // none
+            if (lv == Q.levels) {
+                for (int u = a; u < b; ++u) {
+                    Pt<D, M> q;
+                    load_pt(q, pf, pd, u);
+                    if (P.stats) ++evals;
+                    if (within(p, q, T, pd, ip, pd, u, rech) && ++cnt >= need) return cnt;
+                }
+                continue;
+            }
+            ++lv;
+            cur[lv] = Q.qpos[lv - 1][a];
+            end[lv] = Q.qpos[lv - 1][b];
+        }
+    }
+    return cnt;
+}
+
 // One batch of kb <= 32*NS own points of a sparse cell whose k points start at
 // s0 (the batch starts at own index b0); own[] holds the batch.
 template <int D, int M, int NS>
@@ -49,7 +99,8 @@ __device__ __forceinline__ void mc_batch(const RunParams &P, const Thr &T, const
                                          const int *__restrict__ cell_start, const int *__restrict__ nl, int ne,
                                          const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
                                          const Pt<D, M> *own, int s0, int b0, int k, int kb, int *__restrict__ core_s,
-                                         Bx<D> (*sbox)[2], unsigned &rech, unsigned long long &evals) {
+                                         Bx<D> (*sbox)[2], const QtView &Q, unsigned &rech,
+                                         unsigned long long &evals) {
     constexpr bool BOX = (M == kF32FromF32 || M == kF32FromF64);
     const int lane = threadIdx.x & 31;
     const bool use_box = BOX && P.box;
@@ -102,6 +153,18 @@ __device__ __forceinline__ void mc_batch(const RunParams &P, const Thr &T, const
             unsigned any = 0;
 #pragma unroll
             for (int s = 0; s < NS; ++s) any |= part[s];
+            if constexpr (D == 8 && BOX) {
+                // a large neighbouring cell: each lane left undecided by the
+                // cell box descends its quadtree on its own
+                if (any && Q.levels > 0 && t1 - t0 >= QT_MIN) {
+#pragma unroll
+                    for (int s = 0; s < NS; ++s)
+                        if ((part[s] >> lane) & 1u)
+                            cnt[s] += qt_range_count<D, M>(mine[s], t0, t1, Q, T, P, pf, pd, s0 + b0 + s * 32 + lane,
+                                                           T.min_pts - cnt[s], rech, evals);
+                    any = 0;
+                }
+            }
             for (int tb = t0; tb < t1 && any; tb += 32) {
                 const int t = tb + lane;
                 const bool qv = t < t1;
@@ -149,7 +212,7 @@ k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__
            const int *__restrict__ cell_start, const int *__restrict__ nbr_cnt, const int *__restrict__ nbr,
            int stride, const long long *__restrict__ nbr_off, const int *__restrict__ nbr_pts,
            const float4 *__restrict__ blo, const float4 *__restrict__ bhi, int *__restrict__ core_s,
-           DevCounters *ctr) {
+           QtView Q, DevCounters *ctr) {
     if (run_failed(ctr)) return;
     constexpr int OWN = D == 8 ? 64 : MC_OWN;  // 8-wide points: at most two slots in registers
     __shared__ Pt<D, M> own[MC_WARPS][OWN];
@@ -181,14 +244,14 @@ k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__
             for (int i = lane; i < kb; i += 32) load_pt(own[w][i], pf, pd, s0 + b0 + i);
             __syncwarp();
             if (kb <= 32)
-                mc_batch<D, M, 1>(P, T, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, sbox[w], rech,
-                                  evals);
+                mc_batch<D, M, 1>(P, T, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, sbox[w], Q,
+                                  rech, evals);
             else if (OWN <= 64 || kb <= 64)
-                mc_batch<D, M, 2>(P, T, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, sbox[w], rech,
-                                  evals);
+                mc_batch<D, M, 2>(P, T, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb, core_s, sbox[w], Q,
+                                  rech, evals);
             else
                 mc_batch<D, M, (OWN > 64 ? 4 : 2)>(P, T, pf, pd, cell_start, nl, ne, blo, bhi, own[w], s0, b0, k, kb,
-                                                   core_s, sbox[w], rech, evals);
+                                                   core_s, sbox[w], Q, rech, evals);
         }
     }
     flush_counter(&ctr->band_rechecks, rech);
@@ -210,7 +273,7 @@ k_markcore_small(RunParams P, const float *__restrict__ pf, const double *__rest
                  const int *__restrict__ cell_of, const int *__restrict__ cell_start, const int *__restrict__ nbr_cnt,
                  const int *__restrict__ nbr, int stride, const long long *__restrict__ nbr_off,
                  const int *__restrict__ nbr_pts, const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
-                 int *__restrict__ core_s, DevCounters *ctr) {
+                 int *__restrict__ core_s, QtView Q, DevCounters *ctr) {
     if (run_failed(ctr)) return;
     constexpr bool BOX = (M == kF32FromF32 || M == kF32FromF64);
     const bool use_box = BOX && P.box;
@@ -239,6 +302,10 @@ k_markcore_small(RunParams P, const float *__restrict__ pf, const double *__rest
                         continue;
                     }
                     if (box_min_d2<D>(p.f, lo, hi) > T.hi) continue;
+                    if (D == 8 && Q.levels > 0 && t1 - t0 >= QT_MIN) {  // a large cell: its quadtree
+                        cnt += qt_range_count<D, M>(p, t0, t1, Q, T, P, pf, pd, i, T.min_pts - cnt, rech, evals);
+                        continue;
+                    }
                 }
             }
             for (int t = t0; t < t1 && cnt < T.min_pts; ++t) {
@@ -262,14 +329,14 @@ void launch_markcore(int D, int mode, const RunParams &P, const Bufs &B, DevCoun
         auto ks = k_markcore_small<DD, MM>;
         const int gs = grid_for((const void *)ks, 256);
         ks<<<gs, 256, 0, s>>>(P, B.pf, B.pd, B.cell_of, B.cell_start, B.nbr_cnt, B.nbr, B.nbr_stride, B.nbr_off,
-                              B.nbr_pts, B.blo, B.bhi, B.core_s, ctr);
+                              B.nbr_pts, B.blo, B.bhi, B.core_s, B.qt, ctr);
         count_launch();
     });
     GBDB_DISPATCH(D, mode, {
         auto k = k_markcore<DD, MM>;
         int g = grid_for((const void *)k, MC_THREADS);
         k<<<g, MC_THREADS, 0, s>>>(P, B.pf, B.pd, B.cell_start, B.nbr_cnt, B.nbr, B.nbr_stride, B.nbr_off,
-                                   B.nbr_pts, B.blo, B.bhi, B.core_s, ctr);
+                                   B.nbr_pts, B.blo, B.bhi, B.core_s, B.qt, ctr);
         count_launch();
     });
 }

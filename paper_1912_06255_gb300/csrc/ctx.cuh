@@ -38,6 +38,7 @@ struct dbscan_ctx {
     int pair_box = 1;       // DBSCAN_OPT_PAIR_BOXES
     double rho = 0.0;       // dbscan_set_approx: 0 = exact DBSCAN
     int witness = 0;        // DBSCAN_OPT_WITNESS
+    int qt_levels = 0;      // DBSCAN_OPT_QUADTREE
     int2 *wit = nullptr;    // [max_points] link witnesses (allocated while the option is on)
     long long wit_count = 0;
     bool have_wit = false;  // the last run recorded link witnesses
@@ -104,6 +105,7 @@ struct dbscan_ctx {
     // 5 <= d <= 8: cells, tree and CSR neighbour lists (allocated at the first such run)
     gbdb::HdBufs hd{};
     void *hd_arena = nullptr;
+    void *qt_arena = nullptr;  // quadtree below the cells (allocated at the first run that uses it)
     int *hd_nbr = nullptr;  // lists that outgrow the arena's nbr buffer
     long long hd_nbr_cap = 0;
     int *nbr_cur = nullptr;                  // where the last run's neighbour lists live

@@ -73,6 +73,16 @@ inline int bloom_log2(long long max_points) {
 void launch_boxes(int SD, const float *pts, const int *start, const DevCounters *ctr, float4 *lo, float4 *hi,
                   cudaStream_t s, float4 *cent = nullptr);
 
+// The quadtree below the cells (d >= 5), read by MarkCore: per level l =
+// 1..levels, qpos[l-1][t] nodes start before point t, qstart[l-1][k] is the
+// first point of node k, qlo/qhi[l-1] its FP32 box (two float4 per node).
+struct QtView {
+    int levels;
+    const int *qpos[3];
+    const int *qstart[3];
+    const float4 *qlo[3], *qhi[3];
+};
+
 // Device arrays of one run, shared by the cluster phases.
 struct Bufs {
     // sorted points and cell table
@@ -113,6 +123,7 @@ struct Bufs {
     int *bheavy;          // [N] non-core list positions whose sets have more than 2 names
     long long *part;
     int64_t n_max;
+    QtView qt;
 };
 
 // ---- clusters (cluster.cu)
@@ -138,6 +149,11 @@ struct HdBufs {
     long long *fwd_off;           // [m] offset of each cell's forward list (cells after it only)
     int *fn, *ff;                 // [m] forward adjacent / farther counts
     int *bn, *bf;                 // [m] backward adjacent / farther counts (zero before the transpose)
+    // quadtree below the cells (MarkCore's range counts), allocated when used
+    unsigned *qsub_in, *qsub;     // [n] sub-cell key of each point, by input index / in cell order
+    int *qpos[3];                 // per level: [n+1] nodes starting before each point
+    int *qstart[3];               // per level: [n+1] first point of each node (then n)
+    float4 *qlo[3], *qhi[3];      // per level: [n][2] FP32 box of each node's points
 };
 // Cells of the sorted points (key_bits = d * bits), then their boxes and tree.
 void hd_cells(const void *X, int dtype, const RunParams &P, int key_bits, const HdBufs &H, const Bufs &B,

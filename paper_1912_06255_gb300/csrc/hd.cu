@@ -69,8 +69,9 @@ __device__ __forceinline__ void unmorton128(uint64_t lo, uint64_t hi, int d, int
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_hd_keys(const T *__restrict__ X, RunParams P, uint64_t *__restrict__ klo, uint64_t *__restrict__ khi,
-          uint64_t *__restrict__ k0, uint32_t *__restrict__ v0) {
+          uint64_t *__restrict__ k0, uint32_t *__restrict__ v0, unsigned *__restrict__ qsub) {
     const Inst &I = P.inst[0];
+    const int L = P.qt;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
         int c[8];
 #pragma unroll
@@ -79,12 +80,27 @@ k_hd_keys(const T *__restrict__ X, RunParams P, uint64_t *__restrict__ klo, uint
         morton128(c, P.d, I.bits, lo, hi);
         klo[i] = lo;
         khi[i] = hi;
-        k0[i] = lo;
+        if (L > 0) {
+            // quadtree sub-cell of the point, L levels below its cell, Morton
+            // interleaved with the coarsest level in the top bits; only the
+            // grouping matters (node boxes bound the points), so FP32 suffices
+            unsigned q = 0;
+            for (int j = 0; j < P.d; ++j) {
+                const float t = ((float)X[(int64_t)i * P.d + j] - I.origin32[j]) * I.inv_s32;
+                int u = (int)floorf(t * (float)(1 << L)) - (c[j] << L);
+                u = u < 0 ? 0 : (u >= (1 << L) ? (1 << L) - 1 : u);
+                for (int b = 0; b < L; ++b) q |= (unsigned)((u >> b) & 1) << (b * P.d + j);
+            }
+            qsub[i] = q;
+            k0[i] = q;
+        } else {
+            k0[i] = lo;
+        }
         v0[i] = (uint32_t)i;
     }
 }
 
-// kh[t] = khi[idx[t]]: the high words in the order of the low-word sort.
+// kh[t] = khi[idx[t]]: a key word in the order of the previous sort pass.
 __global__ void __launch_bounds__(256)
 k_hd_gather_hi(const uint64_t *__restrict__ khi, const uint32_t *__restrict__ idx, uint64_t *__restrict__ kh, int n,
                const DevCounters *ctr) {
@@ -112,7 +128,8 @@ k_hd_flags(const uint64_t *__restrict__ klo, const uint64_t *__restrict__ khi, c
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_hd_cells(const T *__restrict__ X, RunParams P, const uint32_t *__restrict__ idx, const uint64_t *__restrict__ klo,
-           const uint64_t *__restrict__ khi, const int *__restrict__ flag, const int *__restrict__ cpos,
+           const uint64_t *__restrict__ khi, const unsigned *__restrict__ qsub_in, unsigned *__restrict__ qsub,
+           const int *__restrict__ flag, const int *__restrict__ cpos,
            int *__restrict__ cell_start, uint64_t *__restrict__ ckey_lo, uint64_t *__restrict__ ckey_hi,
            int4 *__restrict__ ccoord, float *__restrict__ pf, double *__restrict__ pd, int *__restrict__ orig,
            int *__restrict__ cell_of, DevCounters *ctr) {
@@ -125,6 +142,7 @@ k_hd_cells(const T *__restrict__ X, RunParams P, const uint32_t *__restrict__ id
         const int c = cpos[t] + f - 1;
         orig[t] = i;
         cell_of[t] = c;
+        if (qsub) qsub[t] = qsub_in[i];
         float x32[8];
         double x64[8];
 #pragma unroll
@@ -512,7 +530,7 @@ k_lbvh_neighbors(RunParams P, const int2 *__restrict__ child, const int *__restr
 template <typename T> void hd_launch_keys(const void *X, const RunParams &P, const HdBufs &H, const Bufs &B,
                                        cudaStream_t s) {
     const int g = grid_for((const void *)k_hd_keys<T>, 256);
-    k_hd_keys<T><<<g, 256, 0, s>>>((const T *)X, P, H.klo, H.khi, B.sk0, B.sv0);
+    k_hd_keys<T><<<g, 256, 0, s>>>((const T *)X, P, H.klo, H.khi, B.sk0, B.sv0, H.qsub_in);
     count_launch();
 }
 
@@ -520,7 +538,8 @@ template <typename T> void hd_launch_cells(const void *X, const RunParams &P, co
                                         const uint32_t *idx, DevCounters *ctr, cudaStream_t s) {
     const int g = grid_for((const void *)k_hd_cells<T>, 256);
     // the cell table and the sorted points are this step's outputs
-    k_hd_cells<T><<<g, 256, 0, s>>>((const T *)X, P, idx, H.klo, H.khi, B.core_s, B.core_pos,
+    k_hd_cells<T><<<g, 256, 0, s>>>((const T *)X, P, idx, H.klo, H.khi, H.qsub_in, P.qt > 0 ? H.qsub : nullptr,
+                                    B.core_s, B.core_pos,
                                     const_cast<int *>(B.cell_start), H.ckey_lo, H.ckey_hi, H.ccoord,
                                     const_cast<float *>(B.pf), const_cast<double *>(B.pd),
                                     const_cast<int *>(B.orig), const_cast<int *>(B.cell_of), ctr);
@@ -536,23 +555,37 @@ void hd_cells(const void *X, int dtype, const RunParams &P, int key_bits, const 
     const int bits = key_bits;
     if (dtype == DBSCAN_F32) hd_launch_keys<float>(X, P, H, B, s);
     else hd_launch_keys<double>(X, P, H, B, s);
-    // stable LSD sort by (hi, lo): the low word first, then the high word
+    // stable LSD sort: the quadtree sub-cell key first (when used), then the
+    // low word of the cell key, then its high word.  k_hd_keys left the first
+    // pass's (key, index) in buffer 0; kc / vc name the buffers that hold the
+    // current keys and values, the others are free.
     const int lo_bits = bits < 64 ? bits : 64;
-    int which = radix_sort_u64(B.sk0, B.sv0, B.sk1, B.sv1, n, nullptr, n, 0, lo_bits, B.sort_scratch,
-                               B.sort_scratch_size, ctr, P.max_iters, s);
-    const uint32_t *idx = which ? B.sv1 : B.sv0;
-    if (bits > 64) {
-        uint64_t *kh = which ? B.sk0 : B.sk1;  // the free key buffer
-        uint32_t *vin = which ? B.sv1 : B.sv0;
-        uint32_t *vout = which ? B.sv0 : B.sv1;
-        uint64_t *kother = which ? B.sk1 : B.sk0;
-        int g = grid_for((const void *)k_hd_gather_hi, 256);
-        k_hd_gather_hi<<<g, 256, 0, s>>>(H.khi, vin, kh, n, ctr);
+    uint64_t *kbuf[2] = {B.sk0, B.sk1};
+    uint32_t *vbuf[2] = {B.sv0, B.sv1};
+    int kc = 0, vc = 0;
+    auto sort_pass = [&](int nbits) {
+        if (radix_sort_u64(kbuf[kc], vbuf[vc], kbuf[kc ^ 1], vbuf[vc ^ 1], n, nullptr, n, 0, nbits, B.sort_scratch,
+                           B.sort_scratch_size, ctr, P.max_iters, s)) {
+            kc ^= 1;
+            vc ^= 1;
+        }
+    };
+    auto regather = [&](const uint64_t *src) {  // the keys of the current order into the free key buffer
+        const int g = grid_for((const void *)k_hd_gather_hi, 256);
+        k_hd_gather_hi<<<g, 256, 0, s>>>(src, vbuf[vc], kbuf[kc ^ 1], n, ctr);
         count_launch();
-        const int w2 = radix_sort_u64(kh, vin, kother, vout, n, nullptr, n, 0, bits - 64, B.sort_scratch,
-                                      B.sort_scratch_size, ctr, P.max_iters, s);
-        idx = w2 ? vout : vin;
+        kc ^= 1;
+    };
+    if (P.qt > 0) {
+        sort_pass(P.d * P.qt);
+        regather(H.klo);
     }
+    sort_pass(lo_bits);
+    if (bits > 64) {
+        regather(H.khi);
+        sort_pass(bits - 64);
+    }
+    const uint32_t *idx = vbuf[vc];
     {
         int g = grid_for((const void *)k_hd_flags, 256);
         k_hd_flags<<<g, 256, 0, s>>>(H.klo, H.khi, idx, B.core_s, n, ctr);
@@ -563,8 +596,71 @@ void hd_cells(const void *X, int dtype, const RunParams &P, int key_bits, const 
     else hd_launch_cells<double>(X, P, H, B, idx, ctr, s);
 }
 
-// Step 3: the cells' point boxes and the tree over the cells.
+// ------------------------------------------------------------ quadtree
+// The range-counting quadtree of Sec. 5.2, L levels below each cell.  The
+// points are sorted by (cell, sub-cell key), so a node of level l (the points
+// of one cell whose sub-cell keys share their top d*l bits) is a run of
+// consecutive points, and its children are runs inside it.  Per level:
+// qpos[t] = the number of level-l nodes that start before point t (so node k
+// starts at the point t with qpos[t] = k and qpos[t+1] = k+1), qstart[k] its
+// first point (qstart[count] = n), and the FP32 box of its points.
+__global__ void __launch_bounds__(256)
+k_qt_flags(const int *__restrict__ cell_of, const unsigned *__restrict__ qsub, int shift, int n, int *__restrict__ flag,
+           const DevCounters *ctr) {
+    if (run_failed(ctr)) return;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+        flag[t] = (t == 0 || cell_of[t] != cell_of[t - 1] || (qsub[t] >> shift) != (qsub[t - 1] >> shift)) ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(256)
+k_qt_nodes(const int *__restrict__ pos, int n, const float *__restrict__ pf, int *__restrict__ qstart,
+           float4 *__restrict__ qlo, float4 *__restrict__ qhi, const DevCounters *ctr) {
+    if (run_failed(ctr)) return;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= n; t += gridDim.x * blockDim.x) {
+        if (t == n) {
+            qstart[pos[n]] = n;
+            continue;
+        }
+        const int k = pos[t];
+        if (pos[t + 1] == k) continue;  // not the first point of its node
+        qstart[k] = t;
+        int e = t + 1;
+        while (e < n && pos[e + 1] == pos[e]) ++e;  // the node's points are [t, e)
+        float lo[8], hi[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) { lo[j] = INFINITY; hi[j] = -INFINITY; }
+        for (int u = t; u < e; ++u) {
+            const float4 a = reinterpret_cast<const float4 *>(pf)[(int64_t)u * 2];
+            const float4 b = reinterpret_cast<const float4 *>(pf)[(int64_t)u * 2 + 1];
+            const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int j = 0; j < 8; ++j) { lo[j] = fminf(lo[j], x[j]); hi[j] = fmaxf(hi[j], x[j]); }
+        }
+        qlo[(int64_t)k * 2] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+        qlo[(int64_t)k * 2 + 1] = make_float4(lo[4], lo[5], lo[6], lo[7]);
+        qhi[(int64_t)k * 2] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        qhi[(int64_t)k * 2 + 1] = make_float4(hi[4], hi[5], hi[6], hi[7]);
+    }
+}
+
+static void hd_quadtree(const RunParams &P, const HdBufs &H, const Bufs &B, DevCounters *ctr, cudaStream_t s) {
+    const int n = P.n;
+    for (int l = 1; l <= P.qt; ++l) {
+        int *pos = H.qpos[l - 1];
+        int g = grid_for((const void *)k_qt_flags, 256);
+        k_qt_flags<<<g, 256, 0, s>>>(B.cell_of, H.qsub, P.d * (P.qt - l), n, pos, ctr);
+        count_launch();
+        scan_i32_to_i32(pos, pos, n, nullptr, n, B.part, s);
+        g = grid_for((const void *)k_qt_nodes, 256);
+        k_qt_nodes<<<g, 256, 0, s>>>(pos, n, B.pf, H.qstart[l - 1], H.qlo[l - 1], H.qhi[l - 1], ctr);
+        count_launch();
+    }
+}
+
+// Step 3: the cells' point boxes, the tree over the cells, and the
+// quadtrees of the cells when MarkCore counts with them.
 void hd_tree(const RunParams &P, const HdBufs &H, const Bufs &B, DevCounters *ctr, cudaStream_t s) {
+    if (P.qt > 0) hd_quadtree(P, H, B, ctr, s);
     if (P.box) launch_boxes(8, B.pf, B.cell_start, ctr, const_cast<float4 *>(B.blo), const_cast<float4 *>(B.bhi), s);
     int g = grid_for((const void *)k_lbvh_nodes, 256);
     k_lbvh_nodes<<<g, 256, 0, s>>>(H.ckey_lo, H.ckey_hi, H.child, H.parent, H.flag, H.nmax, ctr);

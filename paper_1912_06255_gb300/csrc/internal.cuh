@@ -79,6 +79,7 @@ struct RunParams {
     int waves;      // 2: adjacent pairs, compression, farther pairs; 1: one wave
     int mc_small_nbr;  // neighbourhood limit of MarkCore's thread-per-point cells (0: off)
     int pair_box;      // core-point boxes decide pairs in ClusterCore and ClusterBorder (with box)
+    int qt;            // quadtree levels below the cell for MarkCore's range counts (d >= 5, box mode), 0: off
     int2 *wit;         // null, or [wit_cap]: per union-find hook, a pair of compacted core points within eps
     long long wit_cap;
     // copies of instance 0 for single runs (host side convenience)

@@ -21,7 +21,7 @@ struct Knob {
 };
 
 template <typename RunFn>
-dbscan_status tune(dbscan_ctx *c, int reps, dbscan_tuning *out, RunFn run_once) {
+dbscan_status tune(dbscan_ctx *c, int reps, dbscan_tuning *out, bool high_dim, RunFn run_once) {
     if (reps < 1 || reps > 100) return DBSCAN_ERR_INVALID_ARG;
     std::vector<Knob> knobs = {
         {DBSCAN_OPT_SCHEDULE, {DBSCAN_SCHED_SIZE, DBSCAN_SCHED_NONE, DBSCAN_SCHED_LEARNED}},
@@ -32,6 +32,7 @@ dbscan_status tune(dbscan_ctx *c, int reps, dbscan_tuning *out, RunFn run_once) 
         {DBSCAN_OPT_SMALL_CELLS, {0, 128, 1 << 30}},
         {DBSCAN_OPT_PAIR_BOXES, {1, 0}},
     };
+    if (high_dim && c->precision == DBSCAN_PREC_FP32_RECHECK) knobs.push_back({DBSCAN_OPT_QUADTREE, {0, 2}});
     if (c->precision != DBSCAN_PREC_FP32_RECHECK) knobs.erase(knobs.begin() + 1);  // boxes need the FP32 band
     std::vector<int64_t> cur(knobs.size());
     for (size_t k = 0; k < knobs.size(); ++k) dbscan_get_option(c, knobs[k].option, &cur[k]);
@@ -88,6 +89,7 @@ dbscan_status tune(dbscan_ctx *c, int reps, dbscan_tuning *out, RunFn run_once) 
         dbscan_get_option(c, DBSCAN_OPT_BLOCKS_PER_SM, &v); out->blocks_per_sm = (int32_t)v;
         dbscan_get_option(c, DBSCAN_OPT_SMALL_CELLS, &v); out->small_cells = (int32_t)v;
         dbscan_get_option(c, DBSCAN_OPT_PAIR_BOXES, &v); out->pair_boxes = (int32_t)v;
+        dbscan_get_option(c, DBSCAN_OPT_QUADTREE, &v); out->quadtree = (int32_t)v;
         out->trials = trials;
         out->best_ms = best_ms;
         out->default_ms = default_ms;
@@ -108,7 +110,7 @@ dbscan_status dbscan_autotune(dbscan_ctx *c, const void *d_points, int64_t n, in
         cudaFree(core);
         return DBSCAN_ERR_OOM;
     }
-    const dbscan_status st = tune(c, reps, out, [&]() {
+    const dbscan_status st = tune(c, reps, out, d >= 5, [&]() {
         return dbscan_run(c, d_points, n, d, dtype, eps, min_pts, core, labels, nullptr, nullptr, stream);
     });
     cudaFree(core);
@@ -131,7 +133,7 @@ dbscan_status dbscan_autotune_batch(dbscan_ctx *c, const dbscan_instance *host_d
         cudaFree(core);
         return DBSCAN_ERR_OOM;
     }
-    const dbscan_status st = tune(c, reps, out, [&]() {
+    const dbscan_status st = tune(c, reps, out, false, [&]() {
         return dbscan_run_batch(c, host_desc, count, d_points, ld, dtype, core, labels, nullptr, nullptr, stream);
     });
     cudaFree(core);

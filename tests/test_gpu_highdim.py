@@ -167,3 +167,44 @@ def test_highdim_list_buffer_grows():
         assert np.array_equal(r.border_ids.cpu().numpy(), exp[3])
         if mp == 2:
             assert ctx.stats()["num_neighbor_entries"] > 840 * n
+
+
+@pytest.mark.parametrize("levels", [1, 2, 3])
+@pytest.mark.parametrize("d", [5, 6, 7, 8])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_quadtree_range_counts(levels, d, dtype):
+    """MarkCore's range counts through the quadtree below the cells (Sec. 5.2)
+    give the exact result, with the warp kernel and with the thread-per-point
+    kernel for small cells."""
+    X = synth.random_small(900 + d, 12000, d, dtype=dtype)
+    X = np.concatenate([X, X[:3000] + 0.01])  # denser cells, so large neighbouring cells exist
+    for eps, mp in ((0.8, 12), (1.6, 60)):
+        exp = oracle.dbscan(X, eps, mp)
+        for small in (0, 1 << 30):
+            ctx = DBSCAN(len(X), d)
+            ctx.set_option(_lib.OPT_QUADTREE, levels)
+            ctx.set_option(_lib.OPT_SMALL_CELLS, small)
+            r = ctx.run(torch.from_numpy(X).cuda(), eps, mp)
+            for g, e in zip((r.core, r.labels, r.border_offsets, r.border_ids), exp):
+                assert np.array_equal(g.cpu().numpy(), e), (levels, d, eps, small)
+
+
+@pytest.mark.parametrize("which,eps", [("5d", 200.0), ("5d", 800.0), ("7d", 500.0), ("7d", 1000.0), ("7d", 2000.0)])
+def test_quadtree_on_the_workloads(which, eps):
+    I = synth.spreader_5d_10m(n=100_000, eps=eps) if which == "5d" else synth.spreader_7d_10m(n=100_000, eps=eps)
+    d = I.points.shape[1]
+    exp = oracle.dbscan(I.points, I.eps, I.min_pts)
+    ctx = DBSCAN(len(I.points), d)
+    ctx.set_option(_lib.OPT_QUADTREE, 2)
+    r = ctx.run(torch.from_numpy(I.points).cuda(), I.eps, I.min_pts)
+    for g, e in zip((r.core, r.labels, r.border_offsets, r.border_ids), exp):
+        assert np.array_equal(g.cpu().numpy(), e)
+
+
+def test_quadtree_option_values():
+    ctx = DBSCAN(100, 5)
+    for bad in (-1, 4):
+        with pytest.raises(DbscanError):
+            ctx.set_option(_lib.OPT_QUADTREE, bad)
+    ctx.set_option(_lib.OPT_QUADTREE, 3)
+    assert ctx.get_option(_lib.OPT_QUADTREE) == 3
