@@ -63,7 +63,8 @@ def test_autotune_single(d):
     assert t["trials"] >= 10 and 0 < t["best_ms"] <= t["default_ms"]
     assert t["connect_cells"] in (1, 2, 4, 8) and t["connect_waves"] in (1, 2) and t["schedule"] in (0, 1, 2)
     assert ctx.tuning() == {k: t[k] for k in ("schedule", "cell_bounds", "connect_waves", "connect_cells",
-                                                "blocks_per_sm", "small_cells", "pair_boxes")}
+                                                "blocks_per_sm", "small_cells", "pair_boxes", "quadtree")}
+    assert t["quadtree"] in ((0, 2) if d >= 5 else (0,))  # the quadtree knob is tried for d >= 5 only
     _check(ctx, X, eps, 10)
 
 
