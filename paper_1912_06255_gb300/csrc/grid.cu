@@ -166,8 +166,17 @@ k_insert(const T *__restrict__ X, RunParams P, ulonglong2 *__restrict__ ht,
             const long long i = i0 + (long long)u * T_;
             key[u] = 0;
             s[u] = 0;
+            // the instance of the row: lane 0 searches, the others step on from
+            // its answer (a warp's 32 consecutive rows seldom cross an instance)
+            int ib = 0;
+            if (P.ninst > 1) {
+                const long long r0 = w0 + (long long)u * T_;
+                if (lane == 0 && r0 < P.n) ib = inst_of_row(P, (int)r0);
+                ib = __shfl_sync(0xffffffffu, ib, 0);
+            }
             if (i < P.n) {
-                const int ii = P.ninst > 1 ? inst_of_row(P, (int)i) : 0;
+                int ii = ib;
+                while (ii + 1 < P.ninst && P.inst[ii + 1].row0 <= i) ++ii;
                 const Inst &I = P.inst[ii];
                 int c[kMaxDim];
 #pragma unroll
@@ -666,7 +675,8 @@ template <int D>
 __global__ void __launch_bounds__(256)
 k_super_insert(const uint64_t *__restrict__ cell_key, const int *__restrict__ pos, ulonglong2 *__restrict__ ht,
                uint32_t *__restrict__ sslots, int *__restrict__ sc_first, unsigned *__restrict__ bloom, int bloom_lg,
-               const RunParams P, DevCounters *ctr) {
+               const float4 *__restrict__ blo, const float4 *__restrict__ bhi, float4 *__restrict__ sblo,
+               float4 *__restrict__ sbhi, const RunParams P, DevCounters *ctr) {
     if (run_failed(ctr)) return;
     const int m = ctr->m;
     if (grid_dense(P.n, m)) return;
@@ -683,12 +693,22 @@ k_super_insert(const uint64_t *__restrict__ cell_key, const int *__restrict__ po
         while (c + k < m && k < (1 << D) && pos[c + k + 1] == pos[c + k]) ++k;
         const uint64_t sk = cell_key[c] >> D;
         sc_first[p] = c;
+        if (P.box) {  // the box of the supercell's points: the union of its cells' boxes
+            float4 lo = blo[c], hi = bhi[c];
+            for (int j = 1; j < k; ++j) {
+                const float4 a = blo[c + j], b = bhi[c + j];
+                lo = make_float4(fminf(lo.x, a.x), fminf(lo.y, a.y), fminf(lo.z, a.z), fminf(lo.w, a.w));
+                hi = make_float4(fmaxf(hi.x, b.x), fmaxf(hi.y, b.y), fmaxf(hi.z, b.z), fmaxf(hi.w, b.w));
+            }
+            sblo[p] = lo;
+            sbhi[p] = hi;
+        }
         uint64_t s = hash_slot(sk, lg);
         bool ok = false;
         for (uint64_t it = 0; it <= mask; ++it) {
             if (ht[s].x == kEmptyKey &&
                 atomicCAS(&ht[s].x, (unsigned long long)kEmptyKey, (unsigned long long)sk) == kEmptyKey) {
-                ht[s].y = (unsigned long long)(unsigned)c | ((unsigned long long)k << 32);
+                ht[s].y = (unsigned long long)(unsigned)p | ((unsigned long long)k << 32);  // supercell index, cells
                 ok = true;
                 break;
             }
@@ -723,8 +743,9 @@ __global__ void __launch_bounds__(32 * NBS_WARPS, 4)  // 64 registers: 4 blocks 
 k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict__ ht,
                   const unsigned *__restrict__ bloom, int bloom_lg, const int *__restrict__ sc_first,
                   const int *__restrict__ cell_start, int *__restrict__ nbr_pts, RunParams P, int stride,
-                  const float4 *__restrict__ blo, const float4 *__restrict__ bhi, int *__restrict__ nbr_cnt,
-                  int *__restrict__ nbr_near, int *__restrict__ nbr, DevCounters *ctr) {
+                  const float4 *__restrict__ blo, const float4 *__restrict__ bhi, const float4 *__restrict__ sblo,
+                  const float4 *__restrict__ sbhi, int *__restrict__ nbr_cnt, int *__restrict__ nbr_near,
+                  int *__restrict__ nbr, DevCounters *ctr) {
     if (run_failed(ctr)) return;
     constexpr int K = 1 << D;              // cells per supercell
     constexpr int NS = D == 2 ? 9 : 27;    // supercells probed, the own one included
@@ -795,8 +816,17 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
                     for (uint64_t it = 0; it <= mask; ++it) {
                         const ulonglong2 e = ht[s];
                         if (e.x == key) {
-                            t0 = (int)(unsigned)(e.y & 0xffffffffu);
+                            const int sp = (int)(unsigned)(e.y & 0xffffffffu);
                             kt = (int)(e.y >> 32);
+                            t0 = sc_first[sp];
+                            if (P.box) {  // no point of that supercell within eps of any own point: skip it
+                                Bx<D> al, ah, bl, bh;
+                                al.v[0] = sblo[si];
+                                ah.v[0] = sbhi[si];
+                                bl.v[0] = sblo[sp];
+                                bh.v[0] = sbhi[sp];
+                                if (boxes_min_d2<D>(al, ah, bl, bh) > I.cthr.hi) kt = 0;
+                            }
                             break;
                         }
                         if (e.x == kEmptyKey) break;
@@ -902,7 +932,8 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
     if (lane == 0 && total) atomicAdd((unsigned long long *)&ctr->E, (unsigned long long)total);
 }
 
-void launch_super_table(const Semisort &S, const RunParams &P, DevCounters *ctr, cudaStream_t s) {
+void launch_super_table(const Semisort &S, const RunParams &P, const float4 *blo, const float4 *bhi, float4 *sblo,
+                        float4 *sbhi, DevCounters *ctr, cudaStream_t s) {
     // the cells' slots are free again: the supercells take the table
     launch_table_reset(S, ctr, s, false);
     int *pos = S.count;  // [m + 1], scratch until the compaction
@@ -913,7 +944,8 @@ void launch_super_table(const Semisort &S, const RunParams &P, DevCounters *ctr,
         count_launch();
         scan_i32_to_i32(pos, pos, 0, &ctr->m, P.n, S.part, s);
         g = grid_for((const void *)ki, 256);
-        ki<<<g, 256, 0, s>>>(S.cell_key, pos, S.ht, S.slots, sc_first, S.bloom_all, S.bloom_lg, P, ctr);
+        ki<<<g, 256, 0, s>>>(S.cell_key, pos, S.ht, S.slots, sc_first, S.bloom_all, S.bloom_lg, blo, bhi, sblo, sbhi,
+                             P, ctr);
         count_launch();
     };
     if (P.d == 2) go(k_super_flags<2>, k_super_insert<2>);
@@ -921,13 +953,13 @@ void launch_super_table(const Semisort &S, const RunParams &P, DevCounters *ctr,
 }
 
 void launch_neighbors_super(const Semisort &S, const RunParams &P, int stride, const float4 *blo,
-                            const float4 *bhi, const int *cell_start, int *nbr_cnt, int *nbr_near, int *nbr_pts,
-                            int *nbr, DevCounters *ctr, cudaStream_t s) {
+                            const float4 *bhi, const float4 *sblo, const float4 *sbhi, const int *cell_start,
+                            int *nbr_cnt, int *nbr_near, int *nbr_pts, int *nbr, DevCounters *ctr, cudaStream_t s) {
     const int *sc_first = reinterpret_cast<const int *>(S.rank_of);
     auto go = [&](auto kn) {
         const int g = grid_for((const void *)kn, 32 * NBS_WARPS);
         kn<<<g, 32 * NBS_WARPS, 0, s>>>(S.cell_key, S.ht, S.bloom_all, S.bloom_lg, sc_first, cell_start, nbr_pts, P,
-                                        stride, blo, bhi, nbr_cnt, nbr_near, nbr, ctr);
+                                        stride, blo, bhi, sblo, sbhi, nbr_cnt, nbr_near, nbr, ctr);
         count_launch();
     };
     if (P.d == 2) go(k_neighbors_super<2>);
