@@ -384,8 +384,7 @@ static dbscan_status enqueue_hash_cells(dbscan_ctx *c, const RunParams &P, int S
     mark(3);
     if (P.box) launch_boxes(SD, c->pf, c->cell_start, c->ctr, c->blo, c->bhi, s);
     int *nbr_pts = P.mc_small_nbr > 0 && P.mc_small_nbr < (1 << 30) ? c->nbr_pts : nullptr;
-    // the supercells' boxes go to the core-box arrays, free until the compaction
-    if (S.super) launch_super_table(S, P, c->blo, c->bhi, c->cblo, c->cbhi, c->ctr, s);  // at once on a dense grid
+    if (S.super) launch_super_table(S, P, c->ctr, s);  // returns at once on a dense grid
     mark(4);
     int n_near = 1;
     for (int j = 0; j < d_enum; ++j) n_near *= 3;
@@ -394,8 +393,8 @@ static dbscan_status enqueue_hash_cells(dbscan_ctx *c, const RunParams &P, int S
                      n_near - 1, c->blo, c->bhi, c->cell_start, c->nbr_cnt, c->nbr_near, nbr_pts, c->nbr, c->ctr,
                      s, S.super);
     if (S.super)
-        launch_neighbors_super(S, P, c->noff[d_enum], c->blo, c->bhi, c->cblo, c->cbhi, c->cell_start, c->nbr_cnt,
-                               c->nbr_near, nbr_pts, c->nbr, c->ctr, s);
+        launch_neighbors_super(S, P, c->noff[d_enum], c->blo, c->bhi, c->cell_start, c->nbr_cnt, c->nbr_near,
+                               nbr_pts, c->nbr, c->ctr, s);
     c->nbr_cur = c->nbr;
     c->nbr_off_cur = nullptr;
     return DBSCAN_OK;

@@ -675,8 +675,7 @@ template <int D>
 __global__ void __launch_bounds__(256)
 k_super_insert(const uint64_t *__restrict__ cell_key, const int *__restrict__ pos, ulonglong2 *__restrict__ ht,
                uint32_t *__restrict__ sslots, int *__restrict__ sc_first, unsigned *__restrict__ bloom, int bloom_lg,
-               const float4 *__restrict__ blo, const float4 *__restrict__ bhi, float4 *__restrict__ sblo,
-               float4 *__restrict__ sbhi, const RunParams P, DevCounters *ctr) {
+               const RunParams P, DevCounters *ctr) {
     if (run_failed(ctr)) return;
     const int m = ctr->m;
     if (grid_dense(P.n, m)) return;
@@ -693,22 +692,12 @@ k_super_insert(const uint64_t *__restrict__ cell_key, const int *__restrict__ po
         while (c + k < m && k < (1 << D) && pos[c + k + 1] == pos[c + k]) ++k;
         const uint64_t sk = cell_key[c] >> D;
         sc_first[p] = c;
-        if (P.box) {  // the box of the supercell's points: the union of its cells' boxes
-            float4 lo = blo[c], hi = bhi[c];
-            for (int j = 1; j < k; ++j) {
-                const float4 a = blo[c + j], b = bhi[c + j];
-                lo = make_float4(fminf(lo.x, a.x), fminf(lo.y, a.y), fminf(lo.z, a.z), fminf(lo.w, a.w));
-                hi = make_float4(fmaxf(hi.x, b.x), fmaxf(hi.y, b.y), fmaxf(hi.z, b.z), fmaxf(hi.w, b.w));
-            }
-            sblo[p] = lo;
-            sbhi[p] = hi;
-        }
         uint64_t s = hash_slot(sk, lg);
         bool ok = false;
         for (uint64_t it = 0; it <= mask; ++it) {
             if (ht[s].x == kEmptyKey &&
                 atomicCAS(&ht[s].x, (unsigned long long)kEmptyKey, (unsigned long long)sk) == kEmptyKey) {
-                ht[s].y = (unsigned long long)(unsigned)p | ((unsigned long long)k << 32);  // supercell index, cells
+                ht[s].y = (unsigned long long)(unsigned)c | ((unsigned long long)k << 32);
                 ok = true;
                 break;
             }
@@ -743,9 +732,8 @@ __global__ void __launch_bounds__(32 * NBS_WARPS, 4)  // 64 registers: 4 blocks 
 k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict__ ht,
                   const unsigned *__restrict__ bloom, int bloom_lg, const int *__restrict__ sc_first,
                   const int *__restrict__ cell_start, int *__restrict__ nbr_pts, RunParams P, int stride,
-                  const float4 *__restrict__ blo, const float4 *__restrict__ bhi, const float4 *__restrict__ sblo,
-                  const float4 *__restrict__ sbhi, int *__restrict__ nbr_cnt, int *__restrict__ nbr_near,
-                  int *__restrict__ nbr, DevCounters *ctr) {
+                  const float4 *__restrict__ blo, const float4 *__restrict__ bhi, int *__restrict__ nbr_cnt,
+                  int *__restrict__ nbr_near, int *__restrict__ nbr, DevCounters *ctr) {
     if (run_failed(ctr)) return;
     constexpr int K = 1 << D;              // cells per supercell
     constexpr int NS = D == 2 ? 9 : 27;    // supercells probed, the own one included
@@ -816,17 +804,8 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
                     for (uint64_t it = 0; it <= mask; ++it) {
                         const ulonglong2 e = ht[s];
                         if (e.x == key) {
-                            const int sp = (int)(unsigned)(e.y & 0xffffffffu);
+                            t0 = (int)(unsigned)(e.y & 0xffffffffu);
                             kt = (int)(e.y >> 32);
-                            t0 = sc_first[sp];
-                            if (P.box) {  // no point of that supercell within eps of any own point: skip it
-                                Bx<D> al, ah, bl, bh;
-                                al.v[0] = sblo[si];
-                                ah.v[0] = sbhi[si];
-                                bl.v[0] = sblo[sp];
-                                bh.v[0] = sbhi[sp];
-                                if (boxes_min_d2<D>(al, ah, bl, bh) > I.cthr.hi) kt = 0;
-                            }
                             break;
                         }
                         if (e.x == kEmptyKey) break;
@@ -932,8 +911,7 @@ k_neighbors_super(const uint64_t *__restrict__ cell_key, const ulonglong2 *__res
     if (lane == 0 && total) atomicAdd((unsigned long long *)&ctr->E, (unsigned long long)total);
 }
 
-void launch_super_table(const Semisort &S, const RunParams &P, const float4 *blo, const float4 *bhi, float4 *sblo,
-                        float4 *sbhi, DevCounters *ctr, cudaStream_t s) {
+void launch_super_table(const Semisort &S, const RunParams &P, DevCounters *ctr, cudaStream_t s) {
     // the cells' slots are free again: the supercells take the table
     launch_table_reset(S, ctr, s, false);
     int *pos = S.count;  // [m + 1], scratch until the compaction
@@ -944,8 +922,7 @@ void launch_super_table(const Semisort &S, const RunParams &P, const float4 *blo
         count_launch();
         scan_i32_to_i32(pos, pos, 0, &ctr->m, P.n, S.part, s);
         g = grid_for((const void *)ki, 256);
-        ki<<<g, 256, 0, s>>>(S.cell_key, pos, S.ht, S.slots, sc_first, S.bloom_all, S.bloom_lg, blo, bhi, sblo, sbhi,
-                             P, ctr);
+        ki<<<g, 256, 0, s>>>(S.cell_key, pos, S.ht, S.slots, sc_first, S.bloom_all, S.bloom_lg, P, ctr);
         count_launch();
     };
     if (P.d == 2) go(k_super_flags<2>, k_super_insert<2>);
@@ -953,13 +930,13 @@ void launch_super_table(const Semisort &S, const RunParams &P, const float4 *blo
 }
 
 void launch_neighbors_super(const Semisort &S, const RunParams &P, int stride, const float4 *blo,
-                            const float4 *bhi, const float4 *sblo, const float4 *sbhi, const int *cell_start,
-                            int *nbr_cnt, int *nbr_near, int *nbr_pts, int *nbr, DevCounters *ctr, cudaStream_t s) {
+                            const float4 *bhi, const int *cell_start, int *nbr_cnt, int *nbr_near, int *nbr_pts,
+                            int *nbr, DevCounters *ctr, cudaStream_t s) {
     const int *sc_first = reinterpret_cast<const int *>(S.rank_of);
     auto go = [&](auto kn) {
         const int g = grid_for((const void *)kn, 32 * NBS_WARPS);
         kn<<<g, 32 * NBS_WARPS, 0, s>>>(S.cell_key, S.ht, S.bloom_all, S.bloom_lg, sc_first, cell_start, nbr_pts, P,
-                                        stride, blo, bhi, sblo, sbhi, nbr_cnt, nbr_near, nbr, ctr);
+                                        stride, blo, bhi, nbr_cnt, nbr_near, nbr, ctr);
         count_launch();
     };
     if (P.d == 2) go(k_neighbors_super<2>);

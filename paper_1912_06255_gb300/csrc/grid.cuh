@@ -54,12 +54,10 @@ void launch_table_reset(const Semisort &S, DevCounters *ctr, cudaStream_t s, boo
 // The supercell table of d = 2, 3 (empties the cells' slots of the hash
 // first), then the neighbour lists through it (fixed stride per cell, as
 // launch_neighbors).
-// sblo/sbhi: [N] scratch for the supercells' point boxes (box mode).
-void launch_super_table(const Semisort &S, const RunParams &P, const float4 *blo, const float4 *bhi, float4 *sblo,
-                        float4 *sbhi, DevCounters *ctr, cudaStream_t s);
+void launch_super_table(const Semisort &S, const RunParams &P, DevCounters *ctr, cudaStream_t s);
 void launch_neighbors_super(const Semisort &S, const RunParams &P, int stride, const float4 *blo,
-                            const float4 *bhi, const float4 *sblo, const float4 *sbhi, const int *cell_start,
-                            int *nbr_cnt, int *nbr_near, int *nbr_pts, int *nbr, DevCounters *ctr, cudaStream_t s);
+                            const float4 *bhi, const int *cell_start, int *nbr_cnt, int *nbr_near, int *nbr_pts,
+                            int *nbr, DevCounters *ctr, cudaStream_t s);
 void launch_neighbors(const uint64_t *cell_key, const ulonglong2 *ht, uint64_t hcap, const unsigned *bloom,
                       int bloom_lg, const RunParams &P, const signed char *offs, int noff, int n_near,
                       const float4 *blo, const float4 *bhi, const int *cell_start, int *nbr_cnt, int *nbr_near,
