@@ -12,7 +12,11 @@ border-set fill (dbscan_border_ids), on inputs resident in device memory.
 eps = 100, minPts = 100 (100 random walkers in [0,1e5]^3, ball radius 100,
 step 50 per 100 points, 0.01% noise); reported beside the batch as an extra
 line by default.  ``mixed5d`` / ``varden7d``: the 10M-point 5D and 7D
-workloads (``--eps`` picks the sweep point).
+workloads (``--eps`` picks the sweep point).  ``slabs3d``: one 3D instance of
+1e9 points (the seed spreader at the 2M-point workload's local density) on a
+context sized for 2.5e8, through dbscan_run_slabs (slabs with halos, merged
+exactly); value with device-resident input and outputs, e2e from pinned host
+memory to pinned host memory.
 
 L2 is flushed (256 MiB write) before every timed step, outside the timed
 interval.  ``e2e`` times the host-buffer C-ABI entry points (dbscan_run_host,
@@ -223,7 +227,38 @@ class Batch256:
         return [(self.B[i].points, self.B[i].eps, self.B[i].min_pts) for i in pick], desc
 
 
-WORKLOADS = {"spreader3d": Spreader3D, "batch256": Batch256, "mixed5d": Mixed5D, "varden7d": VarDen7D}
+class Slabs3D:
+    """One 3D instance larger than a context's workspace (dbscan_run_slabs):
+    the seed spreader scaled to n = 1e9 points at the 2M-point workload's local
+    density, eps 100, minPts 100, on a context sized for 2.5e8 points."""
+    DEFAULT_N = 1_000_000_000
+    CAP = 250_000_000
+
+    def __init__(self, n):
+        self.n = int(n) if n else self.DEFAULT_N
+        self.d = 3
+        self.eps, self.min_pts = 100.0, 100
+        self.name = f"slabs3d-spreader-scaled-n{self.n}-eps100-minpts100-f32"
+        self.config = {"workload": self.name, "n": self.n, "d": 3, "eps": self.eps, "min_pts": self.min_pts,
+                       "context_max_points": min(self.CAP, self.n)}
+
+    def host_input(self):
+        """The instance in pinned host memory (generated in place)."""
+        import torch
+        from paper_1912_06255_gb300 import synth
+        X = torch.empty((self.n, 3), dtype=torch.float32, pin_memory=True)
+        synth.spreader_3d_scaled(self.n, out=X.numpy())
+        return X
+
+    def cpu_sample(self):
+        from paper_1912_06255_gb300 import synth
+        T = synth.spreader_3d_scaled(100_000, seed=2005)
+        desc = "a 100,000-point instance of the same generator (same local density, seed 2005), one oracle run"
+        return [(T.points, T.eps, T.min_pts)], desc
+
+
+WORKLOADS = {"spreader3d": Spreader3D, "batch256": Batch256, "mixed5d": Mixed5D, "varden7d": VarDen7D,
+             "slabs3d": Slabs3D}
 
 
 # ----------------------------------------------------------------- helpers
@@ -577,6 +612,91 @@ def _measure(W, args, DBSCAN, dev, dist, rank, local, primary):
     return res
 
 
+def _measure_slabs(W, args, DBSCAN, dev, dist, rank, local):
+    """Every number of the slab-partition line: device-resident input and
+    outputs (value), pinned host input and outputs (e2e), the call's phases,
+    and the rooflines of the slab selection and of the slab runs' kernels."""
+    import torch
+    from paper_1912_06255_gb300 import _lib
+    n = W.n
+    Xh = W.host_input()
+    Xd = Xh.to(dev)
+    ctx = DBSCAN(min(W.CAP, n), 3)
+    outd = (torch.empty(n, dtype=torch.uint8, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
+            torch.empty(n + 1, dtype=torch.int64, device=dev))
+    outh = (torch.empty(n, dtype=torch.uint8, pin_memory=True), torch.empty(n, dtype=torch.int32, pin_memory=True),
+            torch.empty(n + 1, dtype=torch.int64, pin_memory=True))
+    r, st = ctx.run_slabs(Xd, W.eps, W.min_pts, out=outd)
+    K = int(r.border_ids.numel())
+    idsd = torch.empty(max(2 * K, 1024), dtype=torch.int32, device=dev)
+    idsh = torch.empty(max(2 * K, 1024), dtype=torch.int32, pin_memory=True)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, steps):
+        ms = []
+        for _ in range(steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return ms
+
+    dev_step = lambda: ctx.run_slabs(Xd, W.eps, W.min_pts, out=outd, ids=idsd)  # noqa: E731
+    host_step = lambda: ctx.run_slabs(Xh, W.eps, W.min_pts, out=outh, ids=idsh)  # noqa: E731
+    for _ in range(max(3, args.warmup)):
+        dev_step()
+    clocks = ClockSampler(local) if rank == 0 else None
+    torch.cuda.synchronize()
+    ms = timed(dev_step, args.steps)
+    clk = clocks.stop() if clocks else None
+    _, st = dev_step()
+    for _ in range(2):
+        host_step()
+    ms_e2e = timed(host_step, args.steps)
+    _, st_e2e = host_step()
+    # one untimed call with phase timing and pair-test counts: the last slab's
+    # run gives the per-slab kernel times of the roofline
+    ctx.set_option(_lib.OPT_PHASE_TIMING, 1)
+    ctx.set_option(_lib.OPT_COLLECT_STATS, 1)
+    dev_step()
+    run = ctx.stats()
+    ctx.set_option(_lib.OPT_PHASE_TIMING, 0)
+    ctx.set_option(_lib.OPT_COLLECT_STATS, 0)
+    ph = run["phase_ms"]
+    cands = _roofline_candidates(ph, run, 3, run["precision"] == 1, W.name, run["distance_evals_phase"])
+    dom = max(cands, key=lambda key: cands[key]["kernel_ms"]) if cands else None
+    peaks, kind = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    sel_bytes = st["slabs"] * n * 12 + (n + st["halo_points"]) * 16
+    a = sel_bytes / (st["ms"][1] * 1e-3) / 1e9
+    cands["slab_select"] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                            "traffic": None, "kernel": "k_sl_select", "kernel_ms": st["ms"][1],
+                            "algorithmic_bytes": int(sel_bytes),
+                            "units": f"{st['slabs']} passes over {n} points, {n + st['halo_points']} selected",
+                            "timing": "host-timed selection phase of one call (kernels + count readback)",
+                            "peak_source": f"{kind} copy bandwidth (MEASURED_PEAKS hbm_gbs)"}
+    t = _max_over_ranks(sum(ms) / len(ms), dist, dev)
+    te = _max_over_ranks(sum(ms_e2e) / len(ms_e2e), dist, dev)
+    ws = 1 if dist is None else dist.get_world_size()
+    line = {"metric": METRIC, "value": ws * n / (t * 1e-3) / 1e6, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(W.config, precision="fp32 band + fp64 recheck", l2="inputs (12 GB) larger than L2",
+                           step="one dbscan_run_slabs call with device input and outputs, plus the border-id fetch"),
+            "e2e": {"value": ws * n / (te * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(Xh.numel() * 4),
+                    "d2h_bytes_per_step": int(n * 13 + 8 + 4 * K), "ms_per_step": te,
+                    "path": "dbscan_run_slabs from pinned host memory, outputs to pinned host memory"},
+            "gpu_launches": int(st["kernel_launches"]) * args.steps, "slab_stats": st, "e2e_slab_stats": st_e2e,
+            "roofline": dict(cands[dom], note="per-slab kernel: the last slab's run of one call") if dom else None,
+            "roofline_other": {k: v for k, v in cands.items() if k != dom}}
+    if clk:
+        line["clocks"] = clk
+    ctx.close()
+    return line
+
+
 def run_gpu(args):
     import torch
 
@@ -591,6 +711,18 @@ def run_gpu(args):
     build.build()
     dev = torch.device("cuda", local)
     W = WORKLOADS[args.workload](args.points)
+    if isinstance(W, Slabs3D):
+        line = _measure_slabs(W, args, DBSCAN, dev, dist, rank, local)
+        if rank == 0:
+            if not args.no_cpu_baseline:
+                samples, desc = W.cpu_sample()
+                npts, t, cores = _time_oracle(samples)
+                line["cpu_baseline"] = {"value": npts / t / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                        "sample": desc}
+            print(json.dumps(line), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if args.profile:
         # profiling mode (for ncu): warm-up and timed steps only, no extra runs
         X = W.device_input(dev)
@@ -653,7 +785,10 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run warm-up + timed steps only and print no bench line (for ncu)")
     ap.add_argument("--points", type=int, default=None,
-                    help="points of a single-instance workload (default: its defined size, 2e6 in 3D, 1e7 in 5D/7D)")
+                    help="points of a single-instance workload (default: its defined size, 2e6 in 3D, 1e7 in 5D/7D, "
+                         "1e9 for slabs3d)")
+    ap.add_argument("--slab-capacity", type=int, default=None,
+                    help="max_points of the slabs3d context (default 2.5e8)")
     ap.add_argument("--eps", type=float, default=None, help="eps of the 5D or 7D workload (default 200 / 1000)")
     ap.add_argument("--instances", type=int, default=None,
                     help="instances of the batch workload (default 256; fewer only for small profiling captures)")
@@ -663,6 +798,8 @@ def main():
             cls.EPS = args.eps
     if args.instances is not None:
         Batch256.INSTANCES = args.instances
+    if args.slab_capacity is not None:
+        Slabs3D.CAP = args.slab_capacity
     if args.impl == "reference":
         run_reference(args)
     else:

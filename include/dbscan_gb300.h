@@ -119,7 +119,12 @@ enum {
        (the range counting of Sec. 5.2): nodes whose points are all within eps
        count whole, nodes with none are skipped, only the leaves in between
        are scanned.  Ignored below 5 dimensions and in the FP64 mode. */
-    DBSCAN_OPT_QUADTREE = 14
+    DBSCAN_OPT_QUADTREE = 14,
+    /* value: 1 (default) or 0: dbscan_run_slabs copies host input into device
+       memory once when it fits (free memory above its size plus 4 GiB) and
+       reads every pass from there; 0 reads pinned host input in place and
+       stages pageable input chunk by chunk in every pass */
+    DBSCAN_OPT_SLAB_STAGE = 15
 };
 enum { DBSCAN_PREC_FP64 = 0, DBSCAN_PREC_FP32_RECHECK = 1 };
 /* SIZE: core-cell pairs are tested in order of non-increasing core count of the
@@ -311,6 +316,67 @@ dbscan_status dbscan_run_batch_host(dbscan_ctx *ctx, const dbscan_instance *h_in
                                     const void *h_points, int ld, int dtype, uint8_t *h_core, int32_t *h_labels,
                                     int64_t *h_border_offsets, int32_t *h_border_ids, int64_t ids_capacity,
                                     int64_t *num_border_memberships, void *stream);
+
+/* What a dbscan_run_slabs() call did. */
+typedef struct {
+    int32_t slabs;            /* slabs run (cuts that coincide are merged) */
+    int32_t axis;             /* partition dimension: the widest of the bounding box */
+    int64_t max_slab_points;  /* largest slab with its halo */
+    int64_t halo_points;      /* points run as halo, summed over slabs */
+    int64_t border_pairs;     /* (border point, cluster) pairs merged before deduplication */
+    int64_t kernel_launches;  /* kernels this call launched, the slab runs' included */
+    double ms[5];             /* host-timed: extremes and histogram passes, slab selection,
+                                 slab runs (with their border sets), merges, names and copies out */
+} dbscan_slab_stats;
+
+/*
+ * Exact DBSCAN of one instance larger than the context's workspace, as the
+ * paper's billion-point runs (Sec. 7) need: the points are split into slabs
+ * along the widest dimension of their bounding box, each slab is run through
+ * dbscan_run() with every point within a halo of 2 eps (plus rounding margin)
+ * on either side, and the runs are merged on the device into the result of
+ * dbscan_run() on the whole input (same core flags, names and border sets):
+ * owned points' core flags are exact in their slab, a point a slab calls core
+ * is core, and each edge between core points lies inside the run of the slab
+ * that owns one of its ends (Sec. 2, Algorithm 1).
+ *   points   [n, d] row-major, DBSCAN_F32 or DBSCAN_F64; device memory, or
+ *            host memory, copied to the device once if it fits there (see
+ *            DBSCAN_OPT_SLAB_STAGE), else read in place when pinned or staged
+ *            in 256 MiB chunks when pageable;  0 <= n < 2^31 - 1 (no bound
+ *            from max_points);  d <= max_dim;  eps, min_pts as in dbscan_run();
+ *   num_slabs  1..4096 slabs cut at equal point counts, or 0: the fewest
+ *            whose slab-with-halo counts (bounded from an 8192-bin histogram
+ *            of the axis coordinate) fit max_points;
+ *   core [n] uint8, labels [n] int32, border_offsets [n+1] int64 (or NULL):
+ *            the outputs of dbscan_run(), in host or device memory;
+ *            *num_border_memberships receives the border sets' total length,
+ *            the capacity dbscan_slab_border_ids() needs;
+ *   stats    may be NULL.
+ * Device memory beyond the context's workspace, kept for later calls: 17n
+ * bytes of global state, one slab-sized input copy with its outputs
+ * (max_points x (row + 17) bytes), 16 bytes per border pair, and the staged
+ * input (n x row bytes) when host input is staged.  The input is read once
+ * per slab plus two passes (extremes, histogram).  Returns
+ * INVALID_ARG (also for a non-finite coordinate), CAPACITY (a slab with its
+ * halo exceeds max_points: too many points share one histogram bin, or the
+ * halo is wider than the slabs), OOM, DEVICE_TIMEOUT, CUDA, or what a slab's
+ * dbscan_run() returns.  Synchronises the stream.  Afterwards the context
+ * holds no run for dbscan_border_ids() or dbscan_link_witnesses().
+ */
+dbscan_status dbscan_run_slabs(dbscan_ctx *ctx, const void *points, int64_t n, int d, int dtype, double eps,
+                               int64_t min_pts, int32_t num_slabs, uint8_t *core, int32_t *labels,
+                               int64_t *border_offsets, int64_t *num_border_memberships, dbscan_slab_stats *stats,
+                               void *stream);
+
+/*
+ * The border sets of the last successful dbscan_run_slabs() on this context
+ * (Algorithm 4), in the CSR layout of its border_offsets: ascending cluster
+ * names.  border_ids (host or device) holds capacity entries, at least the
+ * call's num_border_memberships (CAPACITY otherwise; NULL is allowed when that
+ * is 0).  Returns OK, STATE (no such call, or a later one failed), CAPACITY,
+ * INVALID_ARG or CUDA.  Synchronises the stream.
+ */
+dbscan_status dbscan_slab_border_ids(dbscan_ctx *ctx, int32_t *border_ids, int64_t capacity, void *stream);
 
 /*
  * Exact DBSCAN like dbscan_run(), without any allocation, for callers that

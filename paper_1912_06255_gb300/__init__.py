@@ -322,6 +322,51 @@ class DBSCAN:
                                                   s.cuda_stream), "dbscan_run_batch_host")
         return core, labels, int(k.value)
 
+    def run_slabs(self, points, eps: float, min_pts: int, slabs: int = 0, border: bool = True, out=None,
+                  ids=None, stream=None):
+        """dbscan_run_slabs: one instance larger than this context's max_points,
+        run slab by slab along its widest dimension and merged exactly.
+        ``points`` is host memory (numpy array or CPU tensor) or a CUDA tensor;
+        ``slabs`` = 0 picks the fewest that fit.  ``out`` may be (core uint8
+        [n], labels int32 [n], offsets int64 [n+1]) tensors in host or device
+        memory (default: new pinned host tensors); ``ids`` an int32 tensor for
+        the border ids, used when large enough.  Returns (Result, stats dict)."""
+        torch = _torch()
+        import numpy as np
+        if isinstance(points, np.ndarray):
+            points = torch.from_numpy(np.ascontiguousarray(points))
+        pts = points.contiguous()
+        if pts.dtype not in (torch.float32, torch.float64) or pts.dim() != 2:
+            raise ValueError("points must be float32/float64 [n, d]")
+        n, d = pts.shape
+        pin = torch.cuda.is_available()
+        if out is None:
+            core = torch.empty(n, dtype=torch.uint8, pin_memory=pin)
+            labels = torch.empty(n, dtype=torch.int32, pin_memory=pin)
+            off = torch.empty(n + 1, dtype=torch.int64, pin_memory=pin) if border else None
+        else:
+            core, labels, off = out
+            if not border:
+                off = None
+        s = stream if stream is not None else torch.cuda.current_stream()
+        k = ctypes.c_int64(0)
+        st = _lib.SlabStats()
+        dtype = _lib.F32 if pts.dtype == torch.float32 else _lib.F64
+        _lib.check(self.lib.dbscan_run_slabs(self.ctx, pts.data_ptr(), n, d, dtype, float(eps), int(min_pts),
+                                             int(slabs), core.data_ptr(), labels.data_ptr(),
+                                             off.data_ptr() if off is not None else None, ctypes.byref(k),
+                                             ctypes.byref(st), s.cuda_stream), "dbscan_run_slabs")
+        res_ids = None
+        if border:
+            K = int(k.value)
+            if ids is not None and ids.numel() >= K:
+                res_ids = ids[:K]
+            else:
+                res_ids = torch.empty(K, dtype=torch.int32, pin_memory=pin and K > 0)
+            _lib.check(self.lib.dbscan_slab_border_ids(self.ctx, res_ids.data_ptr() if K > 0 else None,
+                                                       res_ids.numel(), s.cuda_stream), "dbscan_slab_border_ids")
+        return Result(core, labels, off, res_ids), st.as_dict()
+
     @staticmethod
     def _host_points(points):
         torch = _torch()

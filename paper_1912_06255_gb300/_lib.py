@@ -22,7 +22,7 @@ F32, F64 = 0, 1
 OPT_PRECISION, OPT_SCHEDULE, OPT_COLLECT_STATS, OPT_MAX_ITERS, OPT_PHASE_TIMING, OPT_CELL_BOUNDS = 0, 1, 2, 3, 4, 5
 OPT_BATCH_GRAPH, OPT_PAIR_LOG = 6, 7
 OPT_CONNECT_CELLS, OPT_CONNECT_WAVES, OPT_BLOCKS_PER_SM, OPT_SMALL_CELLS, OPT_PAIR_BOXES = 8, 9, 10, 11, 12
-OPT_WITNESS, OPT_QUADTREE = 13, 14
+OPT_WITNESS, OPT_QUADTREE, OPT_SLAB_STAGE = 13, 14, 15
 MLP_PARAMS = 1313
 PREC_FP64, PREC_FP32_RECHECK = 0, 1
 SCHED_SIZE, SCHED_NONE, SCHED_LEARNED = 0, 1, 2
@@ -74,6 +74,18 @@ class Instance(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("eps", ctypes.c_double), ("min_pts", ctypes.c_int64)]
 
 
+class SlabStats(ctypes.Structure):
+    """dbscan_slab_stats."""
+    _fields_ = [("slabs", ctypes.c_int32), ("axis", ctypes.c_int32), ("max_slab_points", ctypes.c_int64),
+                ("halo_points", ctypes.c_int64), ("border_pairs", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("ms", ctypes.c_double * 5)]
+
+    def as_dict(self) -> dict:
+        out = {name: getattr(self, name) for name, _ in self._fields_}
+        out["ms"] = list(self.ms)
+        return out
+
+
 SIGNATURES = {
     "dbscan_create": (_I32, [ctypes.POINTER(_P), _I64, _I32]),
     "dbscan_destroy": (None, [_P]),
@@ -84,6 +96,9 @@ SIGNATURES = {
     "dbscan_run_host": (_I32, [_P, _P, _I64, _I32, _I32, _D, _I64, _P, _P, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "dbscan_run_batch_host": (_I32, [_P, ctypes.POINTER(Instance), _I32, _P, _I32, _I32, _P, _P, _P, _P, _I64,
                                      ctypes.POINTER(_I64), _P]),
+    "dbscan_run_slabs": (_I32, [_P, _P, _I64, _I32, _I32, _D, _I64, _I32, _P, _P, _P, ctypes.POINTER(_I64),
+                                ctypes.POINTER(SlabStats), _P]),
+    "dbscan_slab_border_ids": (_I32, [_P, _P, _I64, _P]),
     "dbscan_run_static": (_I32, [_P, _I64, _I32, _I32, _D, _I64, _P, _P, _P]),
     "dbscan_run_batch": (_I32, [_P, ctypes.POINTER(Instance), _I32, _P, _I32, _I32, _P, _P, _P,
                                 ctypes.POINTER(_I64), _P]),

@@ -207,6 +207,7 @@ dbscan_status gbdb_enqueue_batch_prologue(dbscan_ctx *c, const void *d_points, i
                                           cudaStream_t s);
 dbscan_status gbdb_batch_buffers(dbscan_ctx *c, const dbscan_instance *h, int count);
 void gbdb_batch_free(dbscan_ctx *c);
+void gbdb_slab_free(dbscan_ctx *c);
 
 // Buffers of the tree-based neighbour search (5 <= d <= 8), one allocation.
 static cudaError_t ensure_hd(dbscan_ctx *c) {
@@ -533,6 +534,7 @@ void dbscan_destroy(dbscan_ctx *c) {
     cudaFreeHost(c->h_bbox);
     cudaFreeHost(c->h_inst);
     gbdb_batch_free(c);
+    gbdb_slab_free(c);
     cudaFree(c->lpairs);
     cudaFree(c->lk0);
     cudaFree(c->lk1);
@@ -712,6 +714,10 @@ dbscan_status dbscan_set_option(dbscan_ctx *c, int option, int64_t value) {
         if (value < 0 || value > 3) return DBSCAN_ERR_INVALID_ARG;
         c->qt_levels = (int)value;
         return DBSCAN_OK;
+    case DBSCAN_OPT_SLAB_STAGE:
+        if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
+        c->slab_stage = (int)value;
+        return DBSCAN_OK;
     case DBSCAN_OPT_WITNESS:
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
         if (value && !c->wit) {
@@ -760,6 +766,7 @@ dbscan_status dbscan_get_option(const dbscan_ctx *c, int option, int64_t *value)
     case DBSCAN_OPT_PAIR_BOXES: *value = c->pair_box; return DBSCAN_OK;
     case DBSCAN_OPT_WITNESS: *value = c->witness; return DBSCAN_OK;
     case DBSCAN_OPT_QUADTREE: *value = c->qt_levels; return DBSCAN_OK;
+    case DBSCAN_OPT_SLAB_STAGE: *value = c->slab_stage; return DBSCAN_OK;
     default: return DBSCAN_ERR_INVALID_ARG;
     }
 }

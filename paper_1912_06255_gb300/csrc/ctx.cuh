@@ -9,6 +9,7 @@
 #include "learned.cuh"
 
 namespace gbdb {
+struct SlabState;  // dbscan_run_slabs buffers (slab.cu)
 // Neighbour-offset table of dimension d (<= kMaxEnumDim), kMaxEnumDim bytes per
 // offset, nearest first; and its number of offsets.
 std::vector<signed char> offset_table(int d);
@@ -39,6 +40,7 @@ struct dbscan_ctx {
     double rho = 0.0;       // dbscan_set_approx: 0 = exact DBSCAN
     int witness = 0;        // DBSCAN_OPT_WITNESS
     int qt_levels = 0;      // DBSCAN_OPT_QUADTREE
+    int slab_stage = 1;     // DBSCAN_OPT_SLAB_STAGE
     int2 *wit = nullptr;    // [max_points] link witnesses (allocated while the option is on)
     long long wit_count = 0;
     bool have_wit = false;  // the last run recorded link witnesses
@@ -111,6 +113,7 @@ struct dbscan_ctx {
     int *nbr_cur = nullptr;                  // where the last run's neighbour lists live
     const long long *nbr_off_cur = nullptr;  // their CSR offsets (null: fixed stride)
     gbdb::DevCounters *ctr = nullptr;
+    gbdb::SlabState *slab = nullptr;  // allocated at the first dbscan_run_slabs call
     // pinned host
     gbdb::DevCounters *h_ctr = nullptr;
     long long *h_bbox = nullptr;

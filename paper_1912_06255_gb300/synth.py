@@ -170,3 +170,74 @@ def random_small(seed: int, n: int, d: int, dtype=np.float64, clustered: bool = 
         return (rng.random((n, d)) * 10.0).astype(dtype)
     k = max(1, n // 60)
     return gaussian_blobs(rng, n, d, k, 10.0, 0.35, 0.15).astype(dtype)
+
+
+def spreader_3d_scaled(n: int, seed: int = 1005, threads: int = 0, out: np.ndarray | None = None) -> Instance:
+    """The 3D seed spreader at any size with the 2M-point workload's local
+    density, as a stand-in for the paper's largest 3D inputs (Sec. 6 uses
+    Cosmo50, 321M points, and billion-point sets): one walker per 20,000
+    points (ball radius 100, a step of 50 every 100 points) in a box of side
+    1e5 (n / 2e6)^(1/3), 0.01% uniform noise; FP32; eps 100, minPts 100.
+
+    Built for hundreds of millions of points: the walkers are generated in
+    blocks of 256, block k from its own PCG64 stream seeded by (seed, k), on
+    ``threads`` threads (0: all cores); the points are then shuffled in
+    parallel by sending each to a uniformly random one of 256 buckets and
+    shuffling every bucket uniformly, which is a uniform random permutation.
+    ``out`` may be a float32 [n, 3] array (e.g. pinned memory) to fill."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    threads = threads or os.cpu_count() or 1
+    n_walkers = max(1, n // 20000)
+    n_noise = max(1, int(round(n * 1e-4)))
+    per = (n - n_noise) // n_walkers
+    n_noise = n - per * n_walkers
+    box = 1e5 * (n / 2e6) ** (1.0 / 3.0)
+    WB, NBK = 256, 256
+    blocks = [(k, min(WB, n_walkers - k * WB)) for k in range(-(-n_walkers // WB))]
+    noise_id = len(blocks)
+
+    def gen(k):
+        rng = np.random.Generator(np.random.PCG64([seed, k]))
+        if k == noise_id:
+            pts = (rng.random((n_noise, 3)) * box).astype(np.float32)
+        else:
+            w = blocks[k][1]
+            n_seg = -(-per // 100)
+            moves = _unit(rng, w * n_seg, 3).reshape(w, n_seg, 3) * 50.0
+            moves[:, 0] = 0.0
+            pos = rng.random((w, 1, 3)) * box + np.cumsum(moves, axis=1)
+            centre = np.repeat(pos, 100, axis=1)[:, :per].reshape(-1, 3)
+            pts = (centre + _ball(rng, w * per, 3, 100.0)).astype(np.float32)
+        bucket = rng.integers(0, NBK, len(pts), dtype=np.int32)
+        order = np.argsort(bucket, kind="stable")
+        return pts[order], np.bincount(bucket, minlength=NBK)
+
+    with ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(gen, range(noise_id + 1)))
+    counts = np.stack([c for _, c in parts])            # [block, bucket]
+    bucket_start = np.concatenate([[0], np.cumsum(counts.sum(0))])
+    within = np.cumsum(counts, axis=0) - counts         # earlier blocks' share of each bucket
+    res = np.empty((n, 3), np.float32) if out is None else out
+
+    def place(k):
+        pts, c = parts[k]
+        src = np.concatenate([[0], np.cumsum(c)])
+        for b in range(NBK):
+            if c[b]:
+                at = bucket_start[b] + within[k, b]
+                res[at:at + c[b]] = pts[src[b]:src[b + 1]]
+
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(place, range(len(parts))))
+    parts.clear()
+
+    def shuffle(b):
+        rng = np.random.Generator(np.random.PCG64([seed, 1 << 20, b]))
+        lo, hi = bucket_start[b], bucket_start[b + 1]
+        res[lo:hi] = res[lo:hi][rng.permutation(hi - lo)]
+
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(shuffle, range(NBK)))
+    return Instance(res, 100.0, 100, f"spreader3d-scaled-n{n}-eps100-minpts100-f32")

@@ -83,7 +83,7 @@ def _c_layout(struct: str, fields: list, tmp_path) -> dict:
 
 
 @pytest.mark.parametrize("struct,cls", [("dbscan_stats", "Stats"), ("dbscan_instance", "Instance"),
-                                        ("dbscan_tuning", "Tuning")])
+                                        ("dbscan_tuning", "Tuning"), ("dbscan_slab_stats", "SlabStats")])
 def test_struct_layouts_match_the_c_compiler(struct, cls, tmp_path):
     """The ctypes mirrors have the C compiler's size and field offsets."""
     import shutil
