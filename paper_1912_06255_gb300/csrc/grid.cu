@@ -188,43 +188,63 @@ k_insert(const T *__restrict__ X, RunParams P, ulonglong2 *__restrict__ ht,
         }
 #pragma unroll
         for (int u = 0; u < INS_U; ++u) cur[u] = i0 + (long long)u * T_ < P.n ? ht[s[u]].x : 0;
-        bool fresh[INS_U];
+        // linear probing for the INS_U keys side by side: each step issues the
+        // compare-and-swaps of all unresolved keys that see an empty slot
+        // before it waits for any of them
+        bool fresh[INS_U], done[INS_U];
 #pragma unroll
         for (int u = 0; u < INS_U; ++u) {
             fresh[u] = false;
-            if (i0 + (long long)u * T_ >= P.n) continue;
-            bool ok = false;
-            for (uint64_t it = 0; it <= hmask; ++it) {
-                if (cur[u] == kEmptyKey) {
-                    cur[u] = atomicCAS(&ht[s[u]].x, (unsigned long long)kEmptyKey, (unsigned long long)key[u]);
-                    if (cur[u] == kEmptyKey) {  // a new non-empty cell
-                        fresh[u] = true;
-                        ok = true;
-                        break;
-                    }
+            done[u] = i0 + (long long)u * T_ >= P.n;
+        }
+        for (uint64_t it = 0;; ++it) {
+            unsigned long long old[INS_U];
+#pragma unroll
+            for (int u = 0; u < INS_U; ++u)
+                old[u] = (!done[u] && cur[u] == kEmptyKey)
+                             ? atomicCAS(&ht[s[u]].x, (unsigned long long)kEmptyKey, (unsigned long long)key[u])
+                             : cur[u];
+            bool open = false;
+#pragma unroll
+            for (int u = 0; u < INS_U; ++u) {
+                if (done[u]) continue;
+                if (cur[u] == kEmptyKey && old[u] == kEmptyKey) {  // a new non-empty cell
+                    fresh[u] = true;
+                    done[u] = true;
+                } else if (old[u] == key[u]) {
+                    done[u] = true;
+                } else if (it >= hmask) {  // the table is full
+                    set_error(ctr, DBSCAN_ERR_CAPACITY, 10);
+                    s[u] = ~0ull;
+                    done[u] = true;
+                } else {
+                    s[u] = (s[u] + 1) & hmask;
+                    cur[u] = ht[s[u]].x;
+                    open = true;
                 }
-                if (cur[u] == key[u]) { ok = true; break; }
-                s[u] = (s[u] + 1) & hmask;
-                cur[u] = ht[s[u]].x;
             }
-            if (!ok) {
-                set_error(ctr, DBSCAN_ERR_CAPACITY, 10);
-                s[u] = ~0ull;
-            }
+            if (!open) break;
         }
         // the warp's new cells take consecutive places in the slot list with
-        // one counter increment
+        // one counter increment per step
+        unsigned fm[INS_U];
+        int nf = 0;
 #pragma unroll
         for (int u = 0; u < INS_U; ++u) {
-            const unsigned fm = __ballot_sync(0xffffffffu, fresh[u]);
-            if (fm == 0u) continue;
-            const int leader = __ffs(fm) - 1;
+            fm[u] = __ballot_sync(0xffffffffu, fresh[u]);
+            nf += __popc(fm[u]);
+        }
+        if (nf > 0) {
             int at = 0;
-            if (lane == leader) at = atomicAdd(&ctr->m, __popc(fm));
-            at = __shfl_sync(0xffffffffu, at, leader);
-            if (fresh[u]) {
-                slots[at + __popc(fm & ((1u << lane) - 1u))] = (uint32_t)s[u];
-                if (bloom) bloom_add(bloom, key[u], blg);
+            if (lane == 0) at = atomicAdd(&ctr->m, nf);
+            at = __shfl_sync(0xffffffffu, at, 0);
+#pragma unroll
+            for (int u = 0; u < INS_U; ++u) {
+                if (fresh[u]) {
+                    slots[at + __popc(fm[u] & ((1u << lane) - 1u))] = (uint32_t)s[u];
+                    if (bloom) bloom_add(bloom, key[u], blg);
+                }
+                at += __popc(fm[u]);
             }
         }
         unsigned rk[INS_U];
