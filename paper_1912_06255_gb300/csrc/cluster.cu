@@ -207,7 +207,7 @@ __device__ __forceinline__ void mc_batch(const RunParams &P, const Thr &T, const
 }
 
 template <int D, int M>
-__global__ void __launch_bounds__(MC_THREADS, 4)  // 32 warps per SM (measured faster than 24)
+__global__ void __launch_bounds__(MC_THREADS, 5)  // 40 warps per SM (measured faster than 24 and 32)
 k_markcore(RunParams P, const float *__restrict__ pf, const double *__restrict__ pd,
            const int *__restrict__ cell_start, const int *__restrict__ nbr_cnt, const int *__restrict__ nbr,
            int stride, const long long *__restrict__ nbr_off, const int *__restrict__ nbr_pts,
@@ -454,7 +454,7 @@ const uint32_t *launch_schedule(int sched, const RunParams &P, const Bufs &B, De
 // Connectivity Queries").  A hit links the two cells.
 
 template <int D, int M, int WAVE>
-__global__ void __launch_bounds__(256, 4)  // 64 registers: 32 warps per SM hide the union-find latency
+__global__ void __launch_bounds__(256, 6)  // 48 warps per SM hide the union-find latency (measured faster than 32, 40)
 k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict__ rank,
           const int *__restrict__ ccs, const int *__restrict__ nbr_cnt, const int *__restrict__ nbr_near,
           const int *__restrict__ nbr, int stride, const long long *__restrict__ nbr_off,
@@ -516,24 +516,16 @@ k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict
                 b = nbr_list<D>(nbr, nbr_off, stride, a)[e];
                 b0 = ccs[b];
                 nb = ccs[b + 1] - b0;
-                cand = nb > 0 && rank[b] > r;
+                // in cell order (no order array) the rank of a cell is its index
+                cand = nb > 0 && (order ? rank[b] > r : b > a);
             }
-            // bounding boxes of the two cells' core points: every pair beyond
-            // eps -> not connected; every pair within eps -> connected
-            int verdict = 0;
-            if (use_box && cand) {
-                const Thr T = P.inst[inst_of_cell(P, a)].cthr;
-                const Bx<D> alo = load_box<D>(cblo, a), ahi = load_box<D>(cbhi, a);
-                const Bx<D> blo = load_box<D>(cblo, b), bhi = load_box<D>(cbhi, b);
-                if (boxes_min_d2<D>(alo, ahi, blo, bhi) > T.hi) verdict = -1;
-                else if (boxes_max_d2<D>(alo, ahi, blo, bhi) <= T.lo) verdict = 1;
-            }
-            // union-find check: in the near wave only the current parents are
-            // compared (trees are being built); the far wave runs after every
-            // path was compressed, so its finds are short
-            // first on the L1 view of the forest (a "same" there is final), then fresh
+            // union-find check first (most candidate pairs are already joined):
+            // in the near wave only the current parents are compared (trees are
+            // being built); the far wave runs after every path was compressed,
+            // so its finds are short.  First on the L1 view of the forest (a
+            // "same" there is final), then fresh
             bool same = true;
-            if (cand && verdict >= 0) {
+            if (cand) {
                 if (WAVE == 0) {
                     same = __ldca(parent + a) == __ldca(parent + b) || uf_load(parent + a) == uf_load(parent + b);
                 } else {
@@ -541,13 +533,23 @@ k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict
                            uf_find(parent, a, P.max_iters, ctr) == uf_find(parent, b, P.max_iters, ctr);
                 }
             }
+            // then the bounding boxes of the two cells' core points: every pair
+            // beyond eps -> not connected; every pair within eps -> connected
+            int verdict = 0;
+            if (use_box && cand && !same) {
+                const Thr T = P.inst[inst_of_cell(P, a)].cthr;
+                const Bx<D> alo = load_box<D>(cblo, a), ahi = load_box<D>(cbhi, a);
+                const Bx<D> blo = load_box<D>(cblo, b), bhi = load_box<D>(cbhi, b);
+                if (boxes_min_d2<D>(alo, ahi, blo, bhi) > T.hi) verdict = -1;
+                else if (boxes_max_d2<D>(alo, ahi, blo, bhi) <= T.lo) verdict = 1;
+            }
             // a box verdict: every pair of core points is within eps, so the
             // first core points of the two cells witness the link
             if (cand && verdict > 0 && !same && uf_link(parent, a, b, P.max_iters, ctr)) record_link(P, ctr, a0, b0);
             cand_pairs += __popc(__ballot_sync(0xffffffffu, cand));
-            boxed += __popc(__ballot_sync(0xffffffffu, cand && (verdict < 0 || (verdict > 0 && !same))));
+            boxed += __popc(__ballot_sync(0xffffffffu, cand && !same && verdict != 0));
             linked += __popc(__ballot_sync(0xffffffffu, cand && verdict > 0 && !same));
-            skipped += __popc(__ballot_sync(0xffffffffu, cand && verdict >= 0 && same));
+            skipped += __popc(__ballot_sync(0xffffffffu, cand && same));
             unsigned todo = __ballot_sync(0xffffffffu, cand && verdict == 0 && !same);
             while (todo) {
                 const int src = __ffs(todo) - 1;
@@ -908,7 +910,7 @@ void launch_border_offsets(const RunParams &P, const Bufs &B, cudaStream_t s) {
 constexpr int kSmallSet = 8;
 
 template <int D, int M>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 5)  // 40 warps per SM (measured faster than 32)
 k_border_small(RunParams P, Bufs B, int32_t *__restrict__ labels_out, DevCounters *ctr) {
     if (run_failed(ctr)) return;
     constexpr bool BOX = (M == kF32FromF32 || M == kF32FromF64);
