@@ -278,8 +278,7 @@ k_cell_keys(const ulonglong2 *__restrict__ ht, const uint32_t *__restrict__ slot
     }
 }
 
-// Cell c (in key order) owns slot vals[c]: record its id in the slot, its key
-// and its point count.
+// Cell c (in key order) owns slot vals[c]: record its key and its point count.
 __global__ void __launch_bounds__(256)
 k_cell_table(RunParams P, const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
              ulonglong2 *__restrict__ ht, uint64_t *__restrict__ cell_key,
@@ -288,12 +287,24 @@ k_cell_table(RunParams P, const uint64_t *__restrict__ keys, const uint32_t *__r
     const int m = ctr->m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
         const uint32_t s = vals[c];
-        count[c] = (int)ht[s].y;  // the points k_insert counted in the slot
-        ht[s].y = (unsigned long long)c;
+        count[c] = (int)ht[s].y;  // the points k_insert counted in the slot (k_slot_start rewrites it)
         cell_key[c] = keys[c];
         if (P.ninst > 1) cell_inst[c] = (int)(keys[c] >> P.inst_shift);
     }
 }
+
+// After the scan of the counts: slot value = cell id | first point << 32, so
+// the scatter finds both with the one load of its slot.
+__global__ void __launch_bounds__(256)
+k_slot_start(const uint32_t *__restrict__ vals, const int *__restrict__ cell_start, ulonglong2 *__restrict__ ht,
+             const DevCounters *ctr) {
+    if (run_failed(ctr)) return;
+    const int m = ctr->m;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x)
+        ht[vals[c]].y = (unsigned long long)(unsigned)c | ((unsigned long long)(unsigned)cell_start[c] << 32);
+}
+
+constexpr int SC_U = 4;  // points per thread per step of the scatter (their loads overlap)
 
 // Move every point to its cell's range: coalesced reads of the input, one
 // scattered write per point.  Points are stored zero padded to SD coordinates.
@@ -305,32 +316,44 @@ k_scatter_points(const T *__restrict__ X, RunParams P, const ulonglong2 *__restr
                  int *__restrict__ orig, int *__restrict__ cell_of, const DevCounters *ctr) {
     if (run_failed(ctr)) return;
     const int n = P.n, ld = P.d;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int c = (int)ht[slot_of[i]].y;
-        const int dst = cell_start[c] + (int)rank_of[i];
-        // coordinates beyond the instance's own dimension are stored as zero
-        const int d = P.ninst > 1 ? P.inst[P.cell_inst[c]].d : ld;
-        orig[dst] = i;
-        cell_of[dst] = c;
-        float f[SD];
-        double x[SD];
+    const int T_ = gridDim.x * blockDim.x;
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += (long long)T_ * SC_U) {
+        unsigned long long e[SC_U];
 #pragma unroll
-        for (int j = 0; j < SD; ++j) {
-            x[j] = j < d ? (double)X[(int64_t)i * ld + j] : 0.0;
-            f[j] = (float)x[j];
+        for (int u = 0; u < SC_U; ++u) {
+            const long long i = i0 + (long long)u * T_;
+            e[u] = i < n ? ht[slot_of[i]].y : 0ull;
         }
-        if constexpr (SD == 2) {
-            reinterpret_cast<float2 *>(pf)[dst] = make_float2(f[0], f[1]);
-        } else {
 #pragma unroll
-            for (int j = 0; j < SD; j += 4)
-                reinterpret_cast<float4 *>(pf)[(int64_t)dst * (SD / 4) + j / 4] =
-                    make_float4(f[j], f[j + 1], f[j + 2], f[j + 3]);
-        }
-        if (pd) {
+        for (int u = 0; u < SC_U; ++u) {
+            const long long i = i0 + (long long)u * T_;
+            if (i >= n) break;
+            const int c = (int)(unsigned)e[u];
+            const int dst = (int)(e[u] >> 32) + (int)rank_of[i];
+            // coordinates beyond the instance's own dimension are stored as zero
+            const int d = P.ninst > 1 ? P.inst[P.cell_inst[c]].d : ld;
+            orig[dst] = (int)i;
+            cell_of[dst] = c;
+            float f[SD];
+            double x[SD];
 #pragma unroll
-            for (int j = 0; j < SD; j += 2)
-                reinterpret_cast<double2 *>(pd)[(int64_t)dst * (SD / 2) + j / 2] = make_double2(x[j], x[j + 1]);
+            for (int j = 0; j < SD; ++j) {
+                x[j] = j < d ? (double)X[i * ld + j] : 0.0;
+                f[j] = (float)x[j];
+            }
+            if constexpr (SD == 2) {
+                reinterpret_cast<float2 *>(pf)[dst] = make_float2(f[0], f[1]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < SD; j += 4)
+                    reinterpret_cast<float4 *>(pf)[(int64_t)dst * (SD / 4) + j / 4] =
+                        make_float4(f[j], f[j + 1], f[j + 2], f[j + 3]);
+            }
+            if (pd) {
+#pragma unroll
+                for (int j = 0; j < SD; j += 2)
+                    reinterpret_cast<double2 *>(pd)[(int64_t)dst * (SD / 2) + j / 2] = make_double2(x[j], x[j + 1]);
+            }
         }
     }
 }
@@ -386,6 +409,8 @@ void launch_semisort(const void *X, int dtype, const RunParams &P, int SD, const
     g = grid_for((const void *)k_cell_table, 256);
     k_cell_table<<<g, 256, 0, s>>>(P, K, V, S.ht, S.cell_key, S.count, S.cell_inst, ctr); count_launch();
     scan_i32_to_i32(S.count, S.cell_start, 0, &ctr->m, P.n, S.part, s);
+    g = grid_for((const void *)k_slot_start, 256);
+    k_slot_start<<<g, 256, 0, s>>>(V, S.cell_start, S.ht, ctr); count_launch();
     auto scat = [&](auto k, auto xp) {
         int gg = grid_for((const void *)k, 256);
         k<<<gg, 256, 0, s>>>(xp, P, S.ht, S.slot_of, S.rank_of, S.cell_start, S.pf, S.pd, S.orig, S.cell_of, ctr);
@@ -615,7 +640,7 @@ k_neighbors(const uint64_t *__restrict__ cell_key, const ulonglong2 *__restrict_
                 if (act[u]) {
                     uint64_t s = slot[u];
                     for (uint64_t it = 0; it <= mask; ++it) {
-                        if (e[u].x == key[u]) { h = (int)e[u].y; break; }
+                        if (e[u].x == key[u]) { h = (int)(unsigned)e[u].y; break; }  // low word: the cell id
                         if (e[u].x == kEmptyKey) break;
                         s = (s + 1) & mask;
                         e[u] = ht[s];

@@ -226,3 +226,37 @@ def test_repeated_calls_reuse_the_context():
             _same(r, oracle.dbscan(X, 100.0, 100))
     finally:
         ctx.close()
+
+
+def test_timeout_and_allocation_failures_leave_the_context_usable():
+    """A bounded wait that runs out inside a slab's run, and allocations that
+    fail (host-side injection), end the call with their status; the same
+    context then gives the exact result."""
+    import os
+    I = synth.spreader_3d_2m(n=60_000)
+    exp = oracle.dbscan(I.points, I.eps, I.min_pts)
+    ctx = DBSCAN(30_000, 3)
+    try:
+        ctx.set_option(_lib.OPT_MAX_ITERS, 1)
+        with pytest.raises(DbscanError) as e:
+            ctx.run_slabs(I.points, I.eps, I.min_pts, slabs=3)
+        assert e.value.status == 7  # DBSCAN_ERR_DEVICE_TIMEOUT
+        ctx.set_option(_lib.OPT_MAX_ITERS, 1 << 22)
+        r, _ = ctx.run_slabs(I.points, I.eps, I.min_pts, slabs=3)
+        _same(r, exp)
+    finally:
+        ctx.close()
+    os.environ["DBSCAN_FAULT"] = "alloc"
+    try:
+        ctx = DBSCAN(30_000, 3)
+    finally:
+        del os.environ["DBSCAN_FAULT"]
+    try:
+        with pytest.raises(DbscanError) as e:
+            ctx.run_slabs(I.points, I.eps, I.min_pts, slabs=3)
+        assert e.value.status == 3  # DBSCAN_ERR_OOM: the slab buffers are allocated at the first call
+        X = synth.random_small(9, 2000, 3, dtype=np.float32)
+        r = ctx.run(torch.from_numpy(X).cuda(), 0.3, 8)
+        assert np.array_equal(r.labels.cpu().numpy(), oracle.dbscan(X, 0.3, 8)[1])
+    finally:
+        ctx.close()
