@@ -132,11 +132,13 @@ __global__ void k_sl_bounds_init(long long *b) {
 }
 
 // Per-dimension extremes of n points, merged into b as ordered FP64 keys.
+// Extremes are kept in the input's type (FP32 min/max is exact and stays off
+// the FP64 pipe) and widened once per warp.
 template <typename T>
 __global__ void __launch_bounds__(SL_THREADS) k_sl_bounds(const T *__restrict__ X, long long n, int d, long long *b) {
-    long long mn[kMaxDim], mx[kMaxDim];
+    T mn[kMaxDim], mx[kMaxDim];
 #pragma unroll
-    for (int j = 0; j < kMaxDim; ++j) { mn[j] = 0x7fffffffffffffffll; mx[j] = (long long)0x8000000000000000ull; }
+    for (int j = 0; j < kMaxDim; ++j) { mn[j] = (T)INFINITY; mx[j] = (T)-INFINITY; }
     bool bad = false;
     const long long step = (long long)gridDim.x * SL_THREADS;
     for (long long i0 = (long long)blockIdx.x * SL_THREADS + threadIdx.x; i0 < n; i0 += 2 * step) {
@@ -147,11 +149,10 @@ __global__ void __launch_bounds__(SL_THREADS) k_sl_bounds(const T *__restrict__ 
 #pragma unroll
             for (int j = 0; j < kMaxDim; ++j) {
                 if (j < d) {
-                    const double x = (double)X[i * d + j];
+                    const T x = X[i * d + j];
                     bad |= !isfinite(x);
-                    const long long k = okey(x);
-                    mn[j] = min(mn[j], k);
-                    mx[j] = max(mx[j], k);
+                    mn[j] = x < mn[j] ? x : mn[j];
+                    mx[j] = x > mx[j] ? x : mx[j];
                 }
             }
         }
@@ -159,14 +160,15 @@ __global__ void __launch_bounds__(SL_THREADS) k_sl_bounds(const T *__restrict__ 
 #pragma unroll
     for (int j = 0; j < kMaxDim; ++j) {
         if (j < d) {
+            long long kn = okey((double)mn[j]), kx = okey((double)mx[j]);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                mn[j] = min(mn[j], __shfl_xor_sync(0xffffffffu, mn[j], o));
-                mx[j] = max(mx[j], __shfl_xor_sync(0xffffffffu, mx[j], o));
+                kn = min(kn, __shfl_xor_sync(0xffffffffu, kn, o));
+                kx = max(kx, __shfl_xor_sync(0xffffffffu, kx, o));
             }
             if ((threadIdx.x & 31) == 0) {
-                atomicMin(b + j, mn[j]);
-                atomicMax(b + kMaxDim + j, mx[j]);
+                atomicMin(b + j, kn);
+                atomicMax(b + kMaxDim + j, kx);
             }
         }
     }
@@ -177,25 +179,28 @@ __global__ void __launch_bounds__(SL_THREADS) k_sl_bounds(const T *__restrict__ 
 // Counts go to shared memory first; each block flushes its non-zero bins once.
 // Four points per thread per step keep enough loads in flight with the few
 // blocks the shared histogram allows.
+// The bins only steer the cuts and bound the slab sizes (with a margin of two
+// bins), so they are computed in the input's type: for FP32 input, lo is an
+// input value and the binning error stays far below one bin.
 template <typename T>
 __global__ void __launch_bounds__(SL_THREADS) k_sl_hist(const T *__restrict__ X, long long n, int d, int axis,
-                                                        double lo, double scale, unsigned long long *hist) {
+                                                        T lo, T scale, unsigned long long *hist) {
     __shared__ unsigned sh[kSlabBins];
     for (int j = threadIdx.x; j < kSlabBins; j += SL_THREADS) sh[j] = 0;
     __syncthreads();
     const long long step = (long long)gridDim.x * SL_THREADS;
     for (long long i0 = (long long)blockIdx.x * SL_THREADS + threadIdx.x; i0 < n; i0 += 4 * step) {
-        double x[4];
+        T x[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const long long i = i0 + u * step;
-            x[u] = i < n ? (double)X[i * d + axis] : lo;
+            x[u] = i < n ? X[i * d + axis] : lo;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (i0 + u * step < n) {
-                const double t = (x[u] - lo) * scale;
-                const int b = t <= 0.0 ? 0 : (t >= (double)(kSlabBins - 1) ? kSlabBins - 1 : (int)t);
+                const T t = (x[u] - lo) * scale;
+                const int b = t <= (T)0 ? 0 : (t >= (T)(kSlabBins - 1) ? kSlabBins - 1 : (int)t);
                 atomicAdd(sh + b, 1u);
             }
         }
@@ -206,6 +211,10 @@ __global__ void __launch_bounds__(SL_THREADS) k_sl_hist(const T *__restrict__ X,
 }
 
 // Appends the points with L <= x <= U (x on the axis) to the slab buffer,
+// comparing in the input's own type: the host rounds each FP64 bound
+// outward or inward to an FP32 value that gives the same answer for every
+// FP32 x (x >= t iff x >= t rounded up; x <= t iff x <= t rounded down;
+// x < t iff x < t rounded up), so FP32 input needs no FP64 instruction here;
 // with their global index (~index unless c_lo <= x < c_hi).  A block takes
 // tiles of SEL_ITEMS x 256 points (item k of thread t is point k*256 + t of
 // the tile, so the reads coalesce), ranks its selected points with a block
@@ -215,8 +224,8 @@ constexpr int SEL_ITEMS = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(SL_THREADS)
-k_sl_select(const T *__restrict__ X, long long n, int d, int axis, long long g0, double L, double U, double c_lo,
-            double c_hi, T *__restrict__ out, int *__restrict__ gid, long long cap, long long *cnt) {
+k_sl_select(const T *__restrict__ X, long long n, int d, int axis, long long g0, T L, T U, T c_lo, T c_hi,
+            T *__restrict__ out, int *__restrict__ gid, long long cap, long long *cnt) {
     constexpr int W = SL_THREADS / 32;
     __shared__ int s_warp[W];
     __shared__ long long s_base;
@@ -228,7 +237,7 @@ k_sl_select(const T *__restrict__ X, long long n, int d, int axis, long long g0,
         for (int k = 0; k < SEL_ITEMS; ++k) {
             const long long i = t0 + (long long)k * SL_THREADS + threadIdx.x;
             if (i < n) {
-                const double x = (double)X[i * d + axis];
+                const T x = X[i * d + axis];
                 if (x >= L && x <= U) selm |= 1u << k;
                 if (x >= c_lo && x < c_hi) ownm |= 1u << k;
             }
@@ -499,12 +508,36 @@ template <typename T>
 void launch_hist(const T *X, long long n, int d, int axis, double lo, double scale, unsigned long long *h,
                  cudaStream_t s) {
     const int g = (int)std::max<long long>(1, std::min<long long>((n + 65535) / 65536, 152 * 4));
-    k_sl_hist<T><<<g, SL_THREADS, 0, s>>>(X, n, d, axis, lo, scale, h); count_launch();
+    k_sl_hist<T><<<g, SL_THREADS, 0, s>>>(X, n, d, axis, (T)lo, (T)scale, h); count_launch();
 }
+// FP32 bounds equivalent to FP64 ones for every FP32 x (see k_sl_select).
+float f32_up(double t) {
+    float f = (float)t;
+    if ((double)f < t) f = std::nextafter(f, INFINITY);
+    return f;
+}
+float f32_down(double t) {
+    float f = (float)t;
+    if ((double)f > t) f = std::nextafter(f, -INFINITY);
+    return f;
+}
+
 template <typename T>
 void launch_select(const T *X, long long n, int d, int axis, long long g0, double L, double U, double clo,
                    double chi, void *out, int *gid, long long cap, long long *cnt, cudaStream_t s) {
-    k_sl_select<T><<<grid_of(n, SL_THREADS * SEL_ITEMS), SL_THREADS, 0, s>>>(X, n, d, axis, g0, L, U, clo, chi,
+    T l, u, a, b;
+    if constexpr (sizeof(T) == 4) {
+        l = f32_up(L);
+        u = f32_down(U);
+        a = f32_up(clo);
+        b = f32_up(chi);
+    } else {
+        l = L;
+        u = U;
+        a = clo;
+        b = chi;
+    }
+    k_sl_select<T><<<grid_of(n, SL_THREADS * SEL_ITEMS), SL_THREADS, 0, s>>>(X, n, d, axis, g0, l, u, a, b,
                                                                           (T *)out, gid, cap, cnt);
     count_launch();
 }
