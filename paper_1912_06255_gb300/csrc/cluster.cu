@@ -454,9 +454,9 @@ const uint32_t *launch_schedule(int sched, const RunParams &P, const Bufs &B, De
 // Connectivity Queries").  A hit links the two cells.
 
 template <int D, int M, int WAVE>
-// d <= 4: 64 warps per SM hide the union-find latency (measured faster than 32-48 on the
-// 2D/3D batch); d >= 5 keeps 32 (its BCP tiles need the registers)
-__global__ void __launch_bounds__(256, D <= 4 ? 8 : 4)
+// 64 warps per SM hide the union-find latency (measured faster than 32-48 on the 2D/3D
+// batch and than 32 on the 5D/7D workloads)
+__global__ void __launch_bounds__(256, 8)
 k_connect(RunParams P, const uint32_t *__restrict__ order, const int *__restrict__ rank,
           const int *__restrict__ ccs, const int *__restrict__ nbr_cnt, const int *__restrict__ nbr_near,
           const int *__restrict__ nbr, int stride, const long long *__restrict__ nbr_off,
@@ -784,7 +784,7 @@ __device__ __forceinline__ void note_heavy(const Bufs &B, DevCounters *ctr, int 
 }
 
 template <int D, int M, bool FILL>
-__global__ void __launch_bounds__(BD_THREADS, D <= 4 ? 8 : 1)  // d <= 4: 64 warps per SM (measured faster than 40, 48)
+__global__ void __launch_bounds__(BD_THREADS, D <= 4 ? 8 : 6)  // 64 (d <= 4) or 48 warps per SM (measured faster than 40, 48 / than unbounded)
 k_border(RunParams P, Bufs B, int32_t *__restrict__ labels_out, int32_t *__restrict__ ids,
          long long ids_cap, DevCounters *ctr) {
     if (run_failed(ctr)) return;
@@ -912,7 +912,7 @@ void launch_border_offsets(const RunParams &P, const Bufs &B, cudaStream_t s) {
 constexpr int kSmallSet = 8;
 
 template <int D, int M>
-__global__ void __launch_bounds__(256, D <= 4 ? 5 : 1)  // d <= 4: 40 warps per SM (measured faster than 32)
+__global__ void __launch_bounds__(256, 5)  // 40 warps per SM (measured faster than 32)
 k_border_small(RunParams P, Bufs B, int32_t *__restrict__ labels_out, DevCounters *ctr) {
     if (run_failed(ctr)) return;
     constexpr bool BOX = (M == kF32FromF32 || M == kF32FromF64);
