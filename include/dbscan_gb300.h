@@ -124,7 +124,12 @@ enum {
        memory once when it fits (free memory above its size plus 4 GiB) and
        reads every pass from there; 0 reads pinned host input in place and
        stages pageable input chunk by chunk in every pass */
-    DBSCAN_OPT_SLAB_STAGE = 15
+    DBSCAN_OPT_SLAB_STAGE = 15,
+    /* value: 0 (default) or 1: open an NVTX range per phase of every run (the
+       phases of dbscan_stats.phase_ms, named "dbscan:<phase>") and per step of
+       dbscan_run_slabs, for profilers that filter or group by NVTX ranges; host
+       calls only, no effect on the result */
+    DBSCAN_OPT_NVTX = 16
 };
 enum { DBSCAN_PREC_FP64 = 0, DBSCAN_PREC_FP32_RECHECK = 1 };
 /* SIZE: core-cell pairs are tested in order of non-increasing core count of the

@@ -22,7 +22,7 @@ F32, F64 = 0, 1
 OPT_PRECISION, OPT_SCHEDULE, OPT_COLLECT_STATS, OPT_MAX_ITERS, OPT_PHASE_TIMING, OPT_CELL_BOUNDS = 0, 1, 2, 3, 4, 5
 OPT_BATCH_GRAPH, OPT_PAIR_LOG = 6, 7
 OPT_CONNECT_CELLS, OPT_CONNECT_WAVES, OPT_BLOCKS_PER_SM, OPT_SMALL_CELLS, OPT_PAIR_BOXES = 8, 9, 10, 11, 12
-OPT_WITNESS, OPT_QUADTREE, OPT_SLAB_STAGE = 13, 14, 15
+OPT_WITNESS, OPT_QUADTREE, OPT_SLAB_STAGE, OPT_NVTX = 13, 14, 15, 16
 MLP_PARAMS = 1313
 PREC_FP64, PREC_FP32_RECHECK = 0, 1
 SCHED_SIZE, SCHED_NONE, SCHED_LEARNED = 0, 1, 2

@@ -1,5 +1,6 @@
 // C ABI: context, workspace and the run sequence of Algorithm 1.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -70,6 +71,27 @@ size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
+
+static const char *const kPhaseRange[kPhases] = {
+    "dbscan:bbox", "dbscan:bbox_readback", "dbscan:cells", "dbscan:boxes_lookup", "dbscan:neighbor_lists",
+    "dbscan:markcore", "dbscan:compact_schedule", "dbscan:connect", "dbscan:labels_border"};
+
+void phase_range(const dbscan_ctx *c, int k) {
+    if (c->nvtx_open) {  // the previous phase's range, or one left open by a failed run
+        nvtxRangePop();
+        c->nvtx_open = 0;
+    }
+    if (c->nvtx && k >= 0 && k < kPhases) {
+        nvtxRangePushA(kPhaseRange[k]);
+        c->nvtx_open = 1;
+    }
+}
+void range_push(const dbscan_ctx *c, const char *name) {
+    if (c->nvtx) nvtxRangePushA(name);
+}
+void range_pop(const dbscan_ctx *c) {
+    if (c->nvtx) nvtxRangePop();
+}
 
 static dbscan_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return DBSCAN_OK;
@@ -718,6 +740,10 @@ dbscan_status dbscan_set_option(dbscan_ctx *c, int option, int64_t value) {
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
         c->slab_stage = (int)value;
         return DBSCAN_OK;
+    case DBSCAN_OPT_NVTX:
+        if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
+        c->nvtx = (int)value;
+        return DBSCAN_OK;
     case DBSCAN_OPT_WITNESS:
         if (value != 0 && value != 1) return DBSCAN_ERR_INVALID_ARG;
         if (value && !c->wit) {
@@ -767,6 +793,7 @@ dbscan_status dbscan_get_option(const dbscan_ctx *c, int option, int64_t *value)
     case DBSCAN_OPT_WITNESS: *value = c->witness; return DBSCAN_OK;
     case DBSCAN_OPT_QUADTREE: *value = c->qt_levels; return DBSCAN_OK;
     case DBSCAN_OPT_SLAB_STAGE: *value = c->slab_stage; return DBSCAN_OK;
+    case DBSCAN_OPT_NVTX: *value = c->nvtx; return DBSCAN_OK;
     default: return DBSCAN_ERR_INVALID_ARG;
     }
 }
@@ -816,6 +843,7 @@ static dbscan_status run_once(dbscan_ctx *c, const void *d_points, int64_t n, in
     const long long launches0 = g_launches;
     auto mark = [&](int k) {
         if (c->phase_timing) cudaEventRecord(c->ev[k], s);
+        phase_range(c, k);
     };
     mark(0);
     const int SD = D == 2 ? 2 : (D == 8 ? 8 : 4);  // storage width of Store<D>

@@ -41,6 +41,8 @@ struct dbscan_ctx {
     int witness = 0;        // DBSCAN_OPT_WITNESS
     int qt_levels = 0;      // DBSCAN_OPT_QUADTREE
     int slab_stage = 1;     // DBSCAN_OPT_SLAB_STAGE
+    int nvtx = 0;           // DBSCAN_OPT_NVTX
+    mutable int nvtx_open = 0;  // a phase range is open (closed by the next phase or an early return)
     int2 *wit = nullptr;    // [max_points] link witnesses (allocated while the option is on)
     long long wit_count = 0;
     bool have_wit = false;  // the last run recorded link witnesses
@@ -138,6 +140,13 @@ struct dbscan_ctx {
     // allocation after dbscan_create fail like an exhausted device
     bool fault_alloc = false;
 };
+
+// NVTX range k of the run's phases (DBSCAN_OPT_NVTX): phase_range(c, k)
+// closes the previous phase's range and opens phase k's; k = kPhases closes.
+void phase_range(const dbscan_ctx *c, int k);
+// A named range of its own (the slab steps), closed by range_pop.
+void range_push(const dbscan_ctx *c, const char *name);
+void range_pop(const dbscan_ctx *c);
 
 // Device allocation of a context's lazily allocated buffers (fails with
 // cudaErrorMemoryAllocation, allocating nothing, under DBSCAN_FAULT=alloc).

@@ -665,6 +665,7 @@ dbscan_status run_slabs(dbscan_ctx *c, SlabState &S, const Source &src, int64_t 
     double ms_sel = 0, ms_run = 0, ms_merge = 0;
     for (int sl = 0; sl < Se; ++sl) {
         // -------- pass 3: the slab's points with their halo
+        range_push(c, "dbscan_slabs:select");
         const double clo = C.c[sl], chi = C.c[sl + 1];
         const double L = sl == 0 ? -INFINITY : down2(clo - H);
         const double U = sl == Se - 1 ? INFINITY : up2(chi + H);
@@ -683,6 +684,7 @@ dbscan_status run_slabs(dbscan_ctx *c, SlabState &S, const Source &src, int64_t 
         biggest = std::max<long long>(biggest, ns);
         halo += ns;
         ms_sel += tm.lap();
+        range_pop(c);
         // -------- the slab's run (Algorithm 1 on the slab)
         int64_t K = 0;
         dbscan_status r = dbscan_run(c, S.s_pts, ns, d, dtype, eps, min_pts, S.s_core, S.s_lab, (int64_t *)S.s_off, &K, s);
@@ -694,6 +696,7 @@ dbscan_status run_slabs(dbscan_ctx *c, SlabState &S, const Source &src, int64_t 
         }
         ms_run += tm.lap();
         // -------- merge into the global state
+        range_push(c, "dbscan_slabs:merge");
         SCK(ensure_pend(c, S, pending + K, pending, s));
         S.h_small[3] = pending;
         SCK(cudaMemcpyAsync(S.cnt + 1, S.h_small + 3, sizeof(long long), cudaMemcpyHostToDevice, s));
@@ -708,6 +711,7 @@ dbscan_status run_slabs(dbscan_ctx *c, SlabState &S, const Source &src, int64_t 
         if (S.h_ctr->err) return (dbscan_status)S.h_ctr->err;
         pending = S.h_small[1];
         ms_merge += tm.lap();
+        range_pop(c);
     }
     // -------- names: roots of the core points, then the border sets
     const int gm = grid_of(n, SL_THREADS * 8);

@@ -341,3 +341,26 @@ def test_link_witnesses(schedule, cell_bounds, d):
     with pytest.raises(DbscanError) as e:
         ctx.link_witnesses()
     assert e.value.status == 8
+
+
+def test_nvtx_ranges_change_nothing():
+    """NVTX phase ranges (host calls only) leave every output as it was, also
+    after a failed run left a range open, and in the slab path."""
+    X = synth.random_small(77, 6000, 3, dtype=np.float32)
+    exp = oracle.dbscan(X, 0.3, 8)
+    ctx = DBSCAN(len(X), 3)
+    ctx.set_option(_lib.OPT_NVTX, 1)
+    assert ctx.get_option(_lib.OPT_NVTX) == 1
+    t = torch.from_numpy(X).cuda()
+    ctx.set_option(_lib.OPT_MAX_ITERS, 1)
+    with pytest.raises(DbscanError):
+        ctx.run(t, 0.3, 8)
+    ctx.set_option(_lib.OPT_MAX_ITERS, 1 << 22)
+    for _ in range(2):
+        r = ctx.run(t, 0.3, 8)
+        for g, e in zip((r.core, r.labels, r.border_offsets, r.border_ids), exp):
+            assert np.array_equal(g.cpu().numpy(), e)
+    r, _ = ctx.run_slabs(X, 0.3, 8, slabs=3)
+    for g, e in zip((r.core, r.labels, r.border_offsets, r.border_ids), exp):
+        assert np.array_equal(g.numpy(), e)
+    ctx.close()
