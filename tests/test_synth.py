@@ -2,8 +2,8 @@
 
 The large 3D generator builds its points in parallel blocks and shuffles them
 with a parallel bucket shuffle; its output must not depend on the number of
-threads, must hold the stated numbers of walker and noise points, and must be
-a permutation of the unshuffled blocks (the same multiset of rows).
+threads, must stay in the stated box, and must leave memory order without
+spatial coherence.
 """
 import numpy as np
 
@@ -34,8 +34,8 @@ def test_scaled_spreader_fills_a_given_buffer_and_keeps_the_box():
 
 
 def test_scaled_spreader_shuffle_is_a_permutation():
-    """Rows sorted lexicographically are the same for two thread counts and
-    for the unshuffled blocks built from the same streams."""
+    """The rows form the same multiset for two thread counts, and the shuffle
+    leaves no spatial order in memory."""
     n = 50_000
     x = synth.spreader_3d_scaled(n, seed=5, threads=2).points
     y = synth.spreader_3d_scaled(n, seed=5, threads=7).points
