@@ -61,6 +61,13 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.dbscan_set_option(None, 0, 1) == 1
     assert lib.dbscan_get_stats(None, None) == 1
     assert lib.dbscan_border_ids(None, None, 0, None) == 1
+    assert lib.dbscan_set_approx(None, 0.1) == 1
+    n = ctypes.c_int64(-5)
+    assert lib.dbscan_link_witnesses(None, None, None, 0, ctypes.byref(n), None) == 1
+    n = ctypes.c_int64(-5)
+    assert lib.dbscan_run_slabs(None, None, 10, 3, 0, 1.0, 5, 0, None, None, None, ctypes.byref(n), None, None) == 1
+    assert n.value == -5  # nothing is written through a call that has no context
+    assert lib.dbscan_slab_border_ids(None, None, 0, None) == 1
     out = ctypes.c_void_p()
     assert lib.dbscan_create(ctypes.byref(out), -1, 3) == 1
     assert lib.dbscan_create(ctypes.byref(out), 10, 9) == 2
